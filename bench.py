@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark: PIC particle-steps/s of the GB300 PIC/MCC step (deposit + solve +
+push + MCC + injection + sort + ionization + compaction) on the 128x128x256-cell,
+~1e7-macroparticle workload (h = 2.5 nm, emitter radius 40 nm, 60/30/10 % e/Cu/Cu+),
+mixed precision (FP32 particles/deposit/gather/smoothing, FP64 CG residual and
+refinement) as `value`, the FP64 plain path measured beside it.
+
+One JSON line on rank 0. Under torchrun every rank runs an independent replica
+(its own seed, no collective in the data path): value = all ranks' particle
+pushes / max-over-ranks time ("scaling": "weak").
+
+--impl reference times the FP64 CPU oracle on the host cores instead (a bounded
+sample of the same workload per step: the 64x64x128-cell sub-box of the same
+cell size and particle density).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "PIC particle-steps/s (deposit+solve+push+MCC), 1 GB300, vs FP64 plain; HBM %"
+UNIT = "particle-steps/s"
+WORKLOAD = "128x128x256 cells h=2.5nm, 1e7 macroparticles (60% e, 30% Cu, 10% Cu+), J~U[5e11,5e12] A/m2, Cu flux 1e28, sort every 20"
+FALLBACK_HBM_GBS = 6800.0
+
+# Algorithmic bytes per particle of the fused gather/push/collide/compact kernel:
+# read the particle record and write it once (the node field is gathered from L2).
+BYTES_PER_PARTICLE = {"mixed": 32 + 32, "fp64": 52 + 52}
+# dram bytes per pushed particle of the same kernel from one ncu capture (None until measured
+# on the current kernel version)
+NCU_TRAFFIC_PER_PARTICLE = {"mixed": None, "fp64": None}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.tmp.read().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.tmp.name)
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(smax)
+            out["samples"] = len(sm)
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def make_workload(seed, n_preload):
+    from paper_2606_05893_gb300 import workloads as W
+    return W.config_scale(seed=seed, n_preload=n_preload)
+
+
+def run_gpu(args, rank, ws, local):
+    import torch
+    import paper_2606_05893_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    wl = make_workload(args.seed + rank, args.n_preload)
+    results = {}
+    precisions = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
+    stream = torch.cuda.current_stream()
+    for prec in precisions:
+        p = pkg.PIC_MIXED if prec == "mixed" else pkg.PIC_FP64
+        sim = pkg.Simulation(wl, precision=p)
+        for _ in range(args.warmup):
+            sim.step(1)
+        m0 = sim.moments()
+        l0 = pkg.pic_launch_count()
+        clocks = ClockSampler(local)
+        barrier()
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sim.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        launches = pkg.pic_launch_count() - l0
+        m1 = sim.moments()
+        pushes = sum(m1["pushed"]) - sum(m0["pushed"])
+        push_e = m1["pushed"][0] - m0["pushed"][0]
+        # profiled pass: per-phase CUDA-event times on the library's stream
+        pkg.pic_set_profiling(sim.h, True)
+        mp0 = sim.moments()
+        for _ in range(args.profile_steps):
+            sim.step(1)
+        torch.cuda.synchronize()
+        phases = pkg.pic_get_phase_times(sim.h, 0)
+        mp1 = sim.moments()
+        pkg.pic_set_profiling(sim.h, False)
+        prof_push_e = mp1["pushed"][0] - mp0["pushed"][0]
+        # end to end through the public API with host buffers: every step uploads a
+        # batch of particles handed over by the surface model (pinned host arrays),
+        # steps, and reads the moments back.
+        batch = args.e2e_batch
+        rng = np.random.default_rng(1234 + rank)
+        Lx, Ly, Lz = wl.L
+        hx = torch.empty((batch, 3), dtype=torch.float64, pin_memory=True)
+        hv = torch.empty((batch, 3), dtype=torch.float64, pin_memory=True)
+        xb = np.stack([Lx / 2 + (rng.random(batch) - 0.5) * 40e-9, Ly / 2 + (rng.random(batch) - 0.5) * 40e-9,
+                       rng.random(batch) * 5e-9], 1)
+        hx.numpy()[:] = xb
+        hv.numpy()[:] = rng.standard_normal((batch, 3)) * 800.0
+        me0 = sim.moments()
+        barrier()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        t2 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            pkg.pic_inject_particles(sim.h, 0, 1, hx.numpy(), hv.numpy())
+            sim.step(1)
+            _ = pkg.pic_moments(sim.h, 0)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        me1 = sim.moments()
+        e2e_pushes = sum(me1["pushed"]) - sum(me0["pushed"])
+        results[prec] = dict(ms=ms, wall=wall, pushes=pushes, push_e=push_e, launches=launches, clocks=clk,
+                             phases=phases, prof_push_e=prof_push_e, prof_steps=args.profile_steps,
+                             e2e_s=(t3 - t2), e2e_pushes=e2e_pushes, cg_iters=m1["cg_iters"],
+                             counts=m1["count"], moments=m1)
+        sim.close()
+        torch.cuda.synchronize()
+
+    # max over ranks of time, sum of pushes
+    def reduce(v, op):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    agg = {}
+    for prec, r in results.items():
+        from torch.distributed import ReduceOp  # noqa
+        agg[prec] = dict(ms=reduce(r["ms"], dist.ReduceOp.MAX if dist else None),
+                         pushes=reduce(float(r["pushes"]), dist.ReduceOp.SUM if dist else None),
+                         e2e_s=reduce(r["e2e_s"], dist.ReduceOp.MAX if dist else None),
+                         e2e_pushes=reduce(float(r["e2e_pushes"]), dist.ReduceOp.SUM if dist else None))
+    if dist is not None:
+        dist.barrier()
+    return results, agg, wl
+
+
+def cpu_baseline(seconds_target=15.0, steps_max=6):
+    """The FP64 oracle as it stands, single thread, on a bounded sample of the workload:
+    the 64x64x128-cell sub-box (1/8 of the volume, same h and particle density)."""
+    import oracle
+    from paper_2606_05893_gb300 import workloads as W
+    wl = W.config_scale(seed=0, n_preload=1_250_000, nx=64, ny=64, nz=128, h=2.5e-9)
+    o = oracle.Oracle(wl)
+    t0 = time.perf_counter()
+    pushes = 0
+    steps = 0
+    while steps < steps_max:
+        n = sum(o.count(s) for s in range(3))
+        o.step()
+        pushes += n + 0  # particles present at the start of the step (injected ones added below)
+        steps += 1
+        if time.perf_counter() - t0 > seconds_target:
+            break
+    dt = time.perf_counter() - t0
+    m = o.moments()
+    pushes += sum(m["injected"])
+    o.close()
+    return {"value": pushes / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle steps of the 64x64x128-cell sub-box (same h = 2.5 nm and particle "
+                      f"density, 1.25e6 macroparticles), FP64, single thread, {dt:.1f} s"}
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2606_05893_gb300 import workloads as W
+    wl = W.config_scale(seed=args.seed, n_preload=1_250_000, nx=64, ny=64, nz=128, h=2.5e-9)
+    o = oracle.Oracle(wl)
+    for _ in range(args.warmup):
+        o.step()
+    m0 = o.moments()
+    n_start = sum(m0["count"])
+    t0 = time.perf_counter()
+    pushes = 0
+    for _ in range(args.steps):
+        n = sum(o.count(s) for s in range(3))
+        inj0 = sum(o.moments()["injected"])
+        o.step()
+        pushes += n + (sum(o.moments()["injected"]) - inj0)
+    dt = time.perf_counter() - t0
+    o.close()
+    value = pushes / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "64x64x128-cell sub-box, 1.25e6 macroparticles"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed oracle steps of the 64x64x128-cell sub-box "
+                                       f"(same h and particle density), started with {n_start} particles"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--n-preload", type=int, default=10_000_000)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--profile-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-batch", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, ws)
+
+    results, agg, wl = run_gpu(args, rank, ws, local)
+    if rank != 0:
+        return 0
+    peak, peak_kind = peaks()
+    head = "mixed" if "mixed" in results else "fp64"
+    r, a = results[head], agg[head]
+    value = a["pushes"] / (a["ms"] * 1e-3)
+    ph = r["phases"]
+    push_ms, push_n = ph["push_electron"]
+    per_launch_ms = push_ms / max(push_n, 1)
+    e_per_launch = r["prof_push_e"] / max(push_n, 1)
+    bpp = BYTES_PER_PARTICLE[head]
+    achieved = bpp * e_per_launch / (per_launch_ms * 1e-3) / 1e9
+    traffic_pp = NCU_TRAFFIC_PER_PARTICLE[head]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": (traffic_pp * e_per_launch if traffic_pp else None),
+                "kernel": "k_push (electrons: gather+push+absorb+MCC+compact)",
+                "peak_kind": peak_kind, "bytes_per_particle": bpp, "particles_per_launch": e_per_launch,
+                "launch_ms": per_launch_ms}
+    steps_total = r["prof_steps"]
+    phase_ms = {k: round(v[0] / max(steps_total, 1), 4) for k, v in ph.items()}
+    h2d = args.e2e_batch * 48
+    import ctypes
+    import paper_2606_05893_gb300 as pkg
+    d2h = ctypes.sizeof(pkg.pic_moments_t) + 600 + 512
+    e2e = {"value": a["e2e_pushes"] / a["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h,
+           "api": "pic_inject_particles(host batch) + pic_step(1) + pic_moments per step"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": a["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": head, "n_preload": args.n_preload,
+                       "grid": [wl.nx, wl.ny, wl.nz], "h": wl.h, "dt": wl.dt,
+                       "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (particle stores 0.3-0.5 GB per buffer)"},
+            "e2e": e2e, "gpu_launches": r["launches"], "clocks": r["clocks"], "roofline": roofline,
+            "phase_ms_per_step": phase_ms, "cg_iters_last_step": r["cg_iters"]}
+    if "fp64" in results and head != "fp64":
+        f, fa = results["fp64"], agg["fp64"]
+        fph = f["phases"]
+        fpush_ms, fpush_n = fph["push_electron"]
+        line["fp64_plain"] = {"value": fa["pushes"] / (fa["ms"] * 1e-3), "ms_per_step": fa["ms"] / args.steps,
+                              "speedup_mixed_over_fp64": value / (fa["pushes"] / (fa["ms"] * 1e-3)),
+                              "phase_ms_per_step": {k: round(v[0] / max(f["prof_steps"], 1), 4) for k, v in fph.items()},
+                              "push_kernel_ms": fpush_ms / max(fpush_n, 1), "clocks": f["clocks"]}
+    if not args.no_cpu_baseline and ws >= 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,259 @@
+/*
+ * pic.h -- C ABI of the GB300 electrostatic PIC/MCC library (libpic_gb300.so).
+ *
+ * The library advances the plasma domain of the coupled cathode-plasma model of
+ * Koitermaa et al. ("Coupled simulation of plasma-surface interactions during
+ * early stages of vacuum arcing"): superparticles (electrons, Cu neutrals,
+ * Cu+ ions) injected from the cathode, moved by the electric field of Poisson's
+ * equation Eq. (1) with Dirichlet electrode potentials, colliding by Monte Carlo
+ * collisions with probability Eq. (4), P = 1 - exp(-u n sigma(E) dt), and leaving
+ * the domain at the electrodes (the PIC/MCC paragraph of the model description
+ * and Appendix A, particle transfer).
+ *
+ * One step n -> n+1 of an instance runs, on the GPU, in this order:
+ *   inject (surface sources)  -> cell sort (every sort_interval steps)
+ *   -> cloud-in-cell deposit  -> Poisson solve (multigrid-preconditioned CG)
+ *   -> field gather + leapfrog push + absorption + MCC -> ionization resolve
+ *   -> compaction.
+ *
+ * Conventions
+ *  - SI units throughout; cross-section energies in eV.
+ *  - Grid: nx x ny x nz cells of side h. Nodes i in [0,nx) and j in [0,ny) are
+ *    periodic, k in [0,nz]; k = 0 is the cathode (phi_cathode_V), k = nz the anode
+ *    (phi_anode_V). Node and cell arrays are laid out [k][j][i] (i fastest):
+ *    nodes (nz+1)*ny*nx, cells nz*ny*nx.
+ *  - Every entry point returns a pic_status. Inputs are copied before return;
+ *    the library owns all device memory of a handle. After an error the
+ *    handle keeps its last consistent state where possible; otherwise it
+ *    reports PIC_ESTATE until destroyed. pic_last_error() gives text.
+ *  - All GPU work is enqueued on the stream given to pic_create (a
+ *    cudaStream_t passed as void*, e.g. torch.cuda.current_stream().cuda_stream;
+ *    NULL = legacy default stream). Calls that return data to host memory
+ *    synchronise that stream.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *  - pids (superparticle identifiers) are 32-bit and assigned monotonically:
+ *    preloaded particles in call order, then per step the injected particles
+ *    in (source, k) order, then secondary electrons in parent-pid order.
+ */
+#ifndef PIC_GB300_H
+#define PIC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_MAX_SPECIES 8
+#define PIC_MAX_XSEC 8
+#define PIC_MAX_SOURCES 16
+
+typedef struct pic_handle pic_handle; /* opaque */
+
+typedef enum {
+  PIC_OK = 0,
+  PIC_EINVAL = -1,     /* invalid argument or configuration */
+  PIC_ENOMEM = -2,     /* device or host allocation failed */
+  PIC_ECAPACITY = -3,  /* a species store (or the event buffer) overflowed; the step's
+                          state is kept but the overflowing particles were dropped */
+  PIC_ENOCONV = -4,    /* Poisson solve hit cg_maxit; non-fatal, phi is used */
+  PIC_ECUDA = -5,      /* a CUDA call failed */
+  PIC_ETIMEOUT = -6,   /* a bounded device-side wait gave up */
+  PIC_ESTATE = -7      /* handle unusable after an earlier fatal error */
+} pic_status;
+
+enum { PIC_ELECTRON = 0, PIC_NEUTRAL = 1, PIC_ION = 2 };
+enum { PIC_XS_IONIZATION = 0, PIC_XS_ELASTIC = 1 };
+enum { PIC_FP64 = 0, PIC_MIXED = 1 };
+enum { PIC_WARM_PREV = 0, PIC_WARM_ZERO = 1 };
+enum { PIC_FIELD_RHO = 0, PIC_FIELD_PHI = 1, PIC_FIELD_NCOUNT = 2 };
+
+/* One species of superparticles (PIC/MCC paragraph: SPs of weight w_SP). */
+typedef struct {
+  double charge_C;  /* charge of one physical particle */
+  double mass_kg;
+  double weight;    /* physical particles per superparticle (> 0) */
+  int32_t role;     /* PIC_ELECTRON | PIC_NEUTRAL | PIC_ION */
+  int64_t capacity; /* maximum superparticles held; >= 1 */
+} pic_species;
+
+/* One collision channel of Eq. (4). The table is copied at pic_create.
+ * sigma(E) = 0 for E <= threshold_eV; n == 1: constant sigma_m2[0];
+ * n >= 2: E_eV strictly increasing, linear interpolation on E_i <= E < E_{i+1},
+ * clamped to the end values outside [E_0, E_{n-1}].
+ * IONIZATION: projectile (electron) + target (neutral) -> 2 projectiles + product
+ *   (ion); the weights of projectile, target and product must be equal.
+ * ELASTIC: projectile scattered isotropically by target, speed kept. */
+typedef struct {
+  int32_t kind;
+  int32_t projectile, target, product; /* species indices */
+  double threshold_eV;
+  int32_t n;
+  const double* E_eV;
+  const double* sigma_m2;
+} pic_xsec;
+
+/* One independent instance (grid, physics, species, collisions). */
+typedef struct {
+  int32_t nx, ny, nz;      /* cells; nx, ny >= 1, nz >= 2 */
+  double h;                /* cell side (m) */
+  double dt;               /* PIC time step (s) */
+  double phi_cathode_V;    /* Dirichlet potential of the plane k = 0 */
+  double phi_anode_V;      /* Dirichlet potential of the plane k = nz */
+  double rho_background;   /* uniform background charge density (C/m^3) */
+  int32_t sort_interval;   /* cell sort every this many steps (0 = never) */
+  double cg_rtol;          /* stop when ||r||_2 <= cg_rtol ||b||_2 */
+  int32_t cg_maxit;        /* iteration limit of the solve (PIC_ENOCONV beyond) */
+  int32_t precision;       /* PIC_FP64 | PIC_MIXED */
+  uint64_t seed;           /* Philox4x32-10 key */
+  int32_t nspecies;        /* 1..PIC_MAX_SPECIES */
+  const pic_species* species;
+  int32_t nxsec;           /* 0..PIC_MAX_XSEC */
+  const pic_xsec* xsec;
+  int32_t warm_start;      /* PIC_WARM_PREV (previous phi) | PIC_WARM_ZERO */
+} pic_instance_cfg;
+
+/* Moments of one instance (a11). Cumulative counters run from pic_create. */
+typedef struct {
+  int64_t step;                                   /* steps completed */
+  int64_t count[PIC_MAX_SPECIES];                 /* live superparticles */
+  int64_t injected[PIC_MAX_SPECIES];              /* cumulative, by sources */
+  int64_t absorbed_cathode[PIC_MAX_SPECIES];      /* cumulative, z < 0 */
+  int64_t absorbed_anode[PIC_MAX_SPECIES];        /* cumulative, z >= Lz */
+  double absorbed_energy_cathode_J[PIC_MAX_SPECIES]; /* cumulative, physical */
+  double absorbed_energy_anode_J[PIC_MAX_SPECIES];
+  int64_t ionizations, elastic, suppressed;       /* cumulative MCC events */
+  int32_t cg_iters;                               /* last solve */
+  double cg_resid_rel;                            /* last solve, true ||r||/||b|| */
+  double total_charge_C;                          /* sum q w N over species */
+  double kinetic_J[PIC_MAX_SPECIES];              /* sum (1/2) m w |v|^2 */
+  double field_energy_J;                          /* (1/2) eps0 h sum_edges (dphi)^2 */
+  double charge_to_cathode_C;                     /* absorbed in the last step */
+  double charge_to_anode_C;
+  uint32_t next_pid;
+  int32_t error_flags;                            /* device-side error bits seen */
+  int64_t pushed[PIC_MAX_SPECIES];                /* cumulative particle pushes (one per
+                                                     live particle per step) */
+} pic_moments_t;
+
+/* Phases of a step, for pic_get_phase_times. */
+enum {
+  PIC_PH_INJECT = 0,
+  PIC_PH_SORT = 1,
+  PIC_PH_DEPOSIT = 2,
+  PIC_PH_SOLVE = 3,
+  PIC_PH_EFIELD = 4,
+  PIC_PH_PUSH_ELECTRON = 5, /* gather/push/absorb/MCC of electron species */
+  PIC_PH_PUSH_ION = 6,
+  PIC_PH_PUSH_NEUTRAL = 7,
+  PIC_PH_RESOLVE = 8,
+  PIC_NPHASES = 9
+};
+
+/* Create n_instances independent instances on the current CUDA device.
+ * cfgs: array of n_instances configurations (copied). cuda_stream: the stream
+ * all work is enqueued on. Errors: PIC_EINVAL (bad geometry, species, tables,
+ * weights), PIC_ENOMEM, PIC_ECUDA. */
+pic_status pic_create(const pic_instance_cfg* cfgs, int32_t n_instances, void* cuda_stream,
+                      pic_handle** out);
+
+/* Add (flux > 0) or remove (flux == 0) a persistent surface source of species
+ * `species` on the cathode: a disk of radius radius_m centred at (cx, cy).
+ * Every step it injects floor(acc) superparticles, acc += flux pi R^2 dt / w,
+ * uniform on the disk with a half-Maxwellian velocity at temperature T_K
+ * (vx, vy ~ N(0, kT/m), vz = |N(0, kT/m)|) and z = U vz dt. The carry
+ * accumulator acc is kept on the host. Up to PIC_MAX_SOURCES sources per
+ * instance; a source with the same (species, cx, cy, radius) is replaced. */
+pic_status pic_inject(pic_handle* h, int32_t inst, int32_t species, double cx, double cy,
+                      double radius_m, double flux_m2s, double T_K);
+
+/* Append n superparticles of `species` (host arrays x[n][3], v[n][3], copied;
+ * v is taken as v^{n-1/2}). Positions must lie in [0,Lx) x [0,Ly) x [0,Lz).
+ * pids continue from next_pid in array order. PIC_ECAPACITY if the store
+ * would overflow (nothing is appended then). */
+pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
+                                const double* x, const double* v);
+
+/* Advance every instance by nsteps steps (asynchronous on the stream). The
+ * returned status covers argument checks, launch errors and the device error
+ * flags of earlier completed steps (PIC_ECAPACITY, PIC_ENOCONV, PIC_ETIMEOUT). */
+pic_status pic_step(pic_handle* h, int32_t nsteps);
+
+/* Fill *out (caller-owned) with the moments of instance inst. Synchronises. */
+pic_status pic_moments(pic_handle* h, int32_t inst, pic_moments_t* out);
+
+/* Release all device and host memory of the handle (NULL is accepted). */
+pic_status pic_destroy(pic_handle* h);
+
+/* Text of the last error on this handle (static storage, never NULL). */
+const char* pic_last_error(pic_handle* h);
+
+/* ---- inspection and test hooks (synchronous) ------------------------------ */
+
+/* Number of live superparticles of a species. */
+pic_status pic_get_count(pic_handle* h, int32_t inst, int32_t species, int64_t* n);
+
+/* Copy a species out in store order: pid[n], x[n][3], v[n][3] (any may be
+ * NULL). cap is the capacity of the caller's arrays; *n receives the count
+ * (PIC_EINVAL if cap < count, nothing copied). Right after a cell sort the
+ * store order is (cell, pid). Positions and velocities are FP64 in both
+ * precisions (in PIC_MIXED they are converted from cell + FP32 offset). */
+pic_status pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t cap, int64_t* n,
+                             uint32_t* pid, double* x, double* v);
+
+/* Copy a grid array to host memory: PIC_FIELD_RHO (double, nodes, the charge
+ * density of the last deposit), PIC_FIELD_PHI (double, nodes, the last solve),
+ * PIC_FIELD_NCOUNT (int32, cells, neutral counts of species `species` at the
+ * last deposit; for RHO/PHI `species` is ignored). */
+pic_status pic_get_field(pic_handle* h, int32_t inst, int32_t which, int32_t species, void* host_out);
+
+/* Replace phi (double, nodes) of an instance, e.g. to set the warm start. */
+pic_status pic_set_phi(pic_handle* h, int32_t inst, const double* host_phi);
+
+/* Solve Eq. (1) for a given charge density with the instance's solver and
+ * electrodes: rho and phi are host arrays over the nodes; phi's interior is
+ * the initial guess on entry and the solution on exit. Does not touch the
+ * instance's own phi. iters/resid_rel may be NULL. */
+pic_status pic_solve(pic_handle* h, int32_t inst, const double* rho, double* phi, int32_t* iters,
+                     double* resid_rel);
+
+/* Sort every species of an instance by (cell, pid) now. */
+pic_status pic_sort_now(pic_handle* h, int32_t inst);
+
+/* Per-cell offsets of the last cell sort of a species: ncells + 1 int64. */
+pic_status pic_get_cell_start(pic_handle* h, int32_t inst, int32_t species, int64_t* host_out);
+
+/* Ionization events of the last step: rows (primary pid, victim pid, secondary
+ * pid) in increasing primary pid; cap rows at most, *n receives the number. */
+pic_status pic_get_ionization_log(pic_handle* h, int32_t inst, int64_t cap, int64_t* n, uint32_t* rows);
+
+/* Philox4x32-10 on the device for n consecutive counters
+ * (c0 + i, c1, c2, c3) with key (k0, k1); out[4 n] host array. */
+pic_status pic_philox(pic_handle* h, int64_t n, const uint32_t ctr[4], const uint32_t key[2],
+                      uint32_t* out);
+
+/* Test mode for the collision rates of Eq. (4): with density_m3 > 0 every
+ * collision channel sees this fixed target density instead of the neutral
+ * counts, and ionizations are counted without consuming neutrals or creating
+ * particles. 0 restores the normal mode. */
+pic_status pic_set_mcc_background(pic_handle* h, int32_t inst, double density_m3);
+
+/* Phase timing: with on != 0 every later step records CUDA events on the
+ * handle's stream around each phase (and waits for them at the end of the step).
+ * pic_get_phase_times adds up, per phase, the elapsed milliseconds (ms[PIC_NPHASES])
+ * and the number of timed phase executions (count[PIC_NPHASES]) since profiling
+ * was switched on; either pointer may be NULL. Switching on resets the sums. */
+pic_status pic_set_profiling(pic_handle* h, int32_t on);
+pic_status pic_get_phase_times(pic_handle* h, int32_t inst, double* ms, int64_t* count);
+
+/* Kernel launches issued by the library in this process so far. */
+uint64_t pic_launch_count(void);
+
+/* Library version string. */
+const char* pic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_GB300_H */

@@ -1,0 +1,421 @@
+"""GB300-native electrostatic PIC/MCC library: thin Python binding of libpic_gb300.so.
+
+The C ABI (include/pic.h) is mirrored name for name: ``pic_create``,
+``pic_inject``, ``pic_inject_particles``, ``pic_step``, ``pic_moments``,
+``pic_destroy`` and the inspection hooks. This module only marshals arguments
+(numpy arrays, ctypes structures, the torch CUDA stream); every step of the
+PIC/MCC cycle runs in the library's CUDA kernels. There is no CPU fallback:
+importing the binding without the built library, or calling it without a GPU,
+raises.
+
+``Simulation`` wraps one handle built from a ``workloads.Workload``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads  # noqa: F401  (seeded input generators)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpic_gb300.so")
+
+PIC_MAX_SPECIES = 8
+PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECAPACITY, PIC_ENOCONV, PIC_ECUDA, PIC_ETIMEOUT, PIC_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+STATUS_NAMES = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECAPACITY", -4: "PIC_ENOCONV",
+                -5: "PIC_ECUDA", -6: "PIC_ETIMEOUT", -7: "PIC_ESTATE"}
+PIC_ELECTRON, PIC_NEUTRAL, PIC_ION = 0, 1, 2
+PIC_XS_IONIZATION, PIC_XS_ELASTIC = 0, 1
+PIC_FP64, PIC_MIXED = 0, 1
+PIC_WARM_PREV, PIC_WARM_ZERO = 0, 1
+PIC_FIELD_RHO, PIC_FIELD_PHI, PIC_FIELD_NCOUNT = 0, 1, 2
+
+
+class pic_species(C.Structure):
+    _fields_ = [("charge_C", C.c_double), ("mass_kg", C.c_double), ("weight", C.c_double),
+                ("role", C.c_int32), ("capacity", C.c_int64)]
+
+
+class pic_xsec(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("projectile", C.c_int32), ("target", C.c_int32), ("product", C.c_int32),
+                ("threshold_eV", C.c_double), ("n", C.c_int32),
+                ("E_eV", C.POINTER(C.c_double)), ("sigma_m2", C.POINTER(C.c_double))]
+
+
+class pic_instance_cfg(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("h", C.c_double), ("dt", C.c_double), ("phi_cathode_V", C.c_double), ("phi_anode_V", C.c_double),
+                ("rho_background", C.c_double),
+                ("sort_interval", C.c_int32),
+                ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32),
+                ("precision", C.c_int32),
+                ("seed", C.c_uint64),
+                ("nspecies", C.c_int32), ("species", C.POINTER(pic_species)),
+                ("nxsec", C.c_int32), ("xsec", C.POINTER(pic_xsec)),
+                ("warm_start", C.c_int32)]
+
+
+class pic_moments_t(C.Structure):
+    _fields_ = [("step", C.c_int64),
+                ("count", C.c_int64 * PIC_MAX_SPECIES),
+                ("injected", C.c_int64 * PIC_MAX_SPECIES),
+                ("absorbed_cathode", C.c_int64 * PIC_MAX_SPECIES),
+                ("absorbed_anode", C.c_int64 * PIC_MAX_SPECIES),
+                ("absorbed_energy_cathode_J", C.c_double * PIC_MAX_SPECIES),
+                ("absorbed_energy_anode_J", C.c_double * PIC_MAX_SPECIES),
+                ("ionizations", C.c_int64), ("elastic", C.c_int64), ("suppressed", C.c_int64),
+                ("cg_iters", C.c_int32), ("cg_resid_rel", C.c_double),
+                ("total_charge_C", C.c_double),
+                ("kinetic_J", C.c_double * PIC_MAX_SPECIES),
+                ("field_energy_J", C.c_double),
+                ("charge_to_cathode_C", C.c_double), ("charge_to_anode_C", C.c_double),
+                ("next_pid", C.c_uint32), ("error_flags", C.c_int32),
+                ("pushed", C.c_int64 * PIC_MAX_SPECIES)]
+
+
+PHASES = ["inject", "sort", "deposit", "solve", "efield", "push_electron", "push_ion", "push_neutral", "resolve"]
+PIC_NPHASES = len(PHASES)
+
+
+EXPORTED = ["pic_create", "pic_inject", "pic_inject_particles", "pic_step", "pic_moments", "pic_destroy",
+            "pic_last_error", "pic_get_count", "pic_get_particles", "pic_get_field", "pic_set_phi", "pic_solve",
+            "pic_sort_now", "pic_get_cell_start", "pic_get_ionization_log", "pic_philox",
+            "pic_set_mcc_background", "pic_version", "pic_set_profiling", "pic_get_phase_times",
+            "pic_launch_count"]
+
+_lib = None
+
+
+class PicError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpic_gb300.so (built by ``_build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libpic_gb300.so not built ({path}); run __graft_entry__.build() or "
+                          "python -m paper_2606_05893_gb300._build")
+    L = C.CDLL(path)
+    P = C.c_void_p
+    d = C.POINTER(C.c_double)
+    u32 = C.POINTER(C.c_uint32)
+    i64 = C.POINTER(C.c_int64)
+    st = C.c_int
+    sig = {
+        "pic_create": ([C.POINTER(pic_instance_cfg), C.c_int32, P, C.POINTER(P)], st),
+        "pic_inject": ([P, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double], st),
+        "pic_inject_particles": ([P, C.c_int32, C.c_int32, C.c_int64, d, d], st),
+        "pic_step": ([P, C.c_int32], st),
+        "pic_moments": ([P, C.c_int32, C.POINTER(pic_moments_t)], st),
+        "pic_destroy": ([P], st),
+        "pic_last_error": ([P], C.c_char_p),
+        "pic_get_count": ([P, C.c_int32, C.c_int32, i64], st),
+        "pic_get_particles": ([P, C.c_int32, C.c_int32, C.c_int64, i64, u32, d, d], st),
+        "pic_get_field": ([P, C.c_int32, C.c_int32, C.c_int32, P], st),
+        "pic_set_phi": ([P, C.c_int32, d], st),
+        "pic_solve": ([P, C.c_int32, d, d, C.POINTER(C.c_int32), d], st),
+        "pic_sort_now": ([P, C.c_int32], st),
+        "pic_get_cell_start": ([P, C.c_int32, C.c_int32, i64], st),
+        "pic_get_ionization_log": ([P, C.c_int32, C.c_int64, i64, u32], st),
+        "pic_philox": ([P, C.c_int64, u32, u32, u32], st),
+        "pic_set_mcc_background": ([P, C.c_int32, C.c_double], st),
+        "pic_version": ([], C.c_char_p),
+        "pic_set_profiling": ([P, C.c_int32], st),
+        "pic_get_phase_times": ([P, C.c_int32, d, i64], st),
+        "pic_launch_count": ([], C.c_uint64),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(h, status):
+    if status != PIC_OK:
+        msg = load_library().pic_last_error(h)
+        raise PicError(status, msg.decode() if msg else "")
+    return status
+
+
+# ----------------------------------------------------------------------------
+# name-for-name wrappers of the C ABI
+# ----------------------------------------------------------------------------
+def pic_create(cfgs, stream=None):
+    """cfgs: list of pic_instance_cfg (their arrays must stay alive during the call)."""
+    L = load_library()
+    arr = (pic_instance_cfg * len(cfgs))(*cfgs)
+    h = C.c_void_p()
+    if stream is None:
+        stream = _torch_stream()
+    _check(None, L.pic_create(arr, len(cfgs), C.c_void_p(stream), C.byref(h)))
+    return h
+
+
+def pic_inject(h, inst, species, cx, cy, radius_m, flux_m2s, T_K):
+    return _check(h, load_library().pic_inject(h, inst, species, cx, cy, radius_m, flux_m2s, T_K))
+
+
+def pic_inject_particles(h, inst, species, x, v):
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+    if x.shape != v.shape:
+        raise ValueError("x and v must have the same shape [n, 3]")
+    return _check(h, load_library().pic_inject_particles(h, inst, species, x.shape[0], _dp(x), _dp(v)))
+
+
+def pic_step(h, nsteps=1, check=True):
+    s = load_library().pic_step(h, nsteps)
+    return _check(h, s) if check else s
+
+
+def pic_moments(h, inst=0):
+    m = pic_moments_t()
+    _check(h, load_library().pic_moments(h, inst, C.byref(m)))
+    return m
+
+
+def pic_destroy(h):
+    if h:
+        load_library().pic_destroy(h)
+
+
+def pic_last_error(h):
+    r = load_library().pic_last_error(h)
+    return r.decode() if r else ""
+
+
+def pic_version():
+    return load_library().pic_version().decode()
+
+
+def pic_get_count(h, inst, species):
+    n = C.c_int64()
+    _check(h, load_library().pic_get_count(h, inst, species, C.byref(n)))
+    return n.value
+
+
+def pic_get_particles(h, inst, species):
+    n = pic_get_count(h, inst, species)
+    cap = max(n, 1)
+    pid = np.zeros(cap, dtype=np.uint32)
+    x = np.zeros((cap, 3))
+    v = np.zeros((cap, 3))
+    got = C.c_int64()
+    _check(h, load_library().pic_get_particles(h, inst, species, cap, C.byref(got),
+                                               pid.ctypes.data_as(C.POINTER(C.c_uint32)), _dp(x), _dp(v)))
+    k = got.value
+    return x[:k], v[:k], pid[:k]
+
+
+def pic_get_field(h, inst, which, shape, species=0):
+    dtype = np.int32 if which == PIC_FIELD_NCOUNT else np.float64
+    out = np.zeros(shape, dtype=dtype)
+    _check(h, load_library().pic_get_field(h, inst, which, species, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def pic_set_phi(h, inst, phi):
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    return _check(h, load_library().pic_set_phi(h, inst, _dp(phi)))
+
+
+def pic_solve(h, inst, rho, phi0):
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    phi = np.array(phi0, dtype=np.float64, copy=True, order="C")
+    it = C.c_int32()
+    rel = C.c_double()
+    s = load_library().pic_solve(h, inst, _dp(rho), _dp(phi), C.byref(it), C.byref(rel))
+    _check(h, s)
+    return phi, it.value, rel.value
+
+
+def pic_sort_now(h, inst=0):
+    return _check(h, load_library().pic_sort_now(h, inst))
+
+
+def pic_get_cell_start(h, inst, species, ncell):
+    out = np.zeros(ncell + 1, dtype=np.int64)
+    _check(h, load_library().pic_get_cell_start(h, inst, species, out.ctypes.data_as(C.POINTER(C.c_int64))))
+    return out
+
+
+def pic_get_ionization_log(h, inst=0, cap=1 << 20):
+    rows = np.zeros((cap, 3), dtype=np.uint32)
+    n = C.c_int64()
+    _check(h, load_library().pic_get_ionization_log(h, inst, cap, C.byref(n),
+                                                    rows.ctypes.data_as(C.POINTER(C.c_uint32))))
+    return rows[: n.value].copy()
+
+
+def pic_philox(h, n, ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4 * n, dtype=np.uint32)
+    _check(h, load_library().pic_philox(h, n, c.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                        k.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                        out.ctypes.data_as(C.POINTER(C.c_uint32))))
+    return out.reshape(n, 4)
+
+
+def pic_set_mcc_background(h, inst, density):
+    return _check(h, load_library().pic_set_mcc_background(h, inst, density))
+
+
+def pic_set_profiling(h, on=True):
+    return _check(h, load_library().pic_set_profiling(h, 1 if on else 0))
+
+
+def pic_get_phase_times(h, inst=0):
+    ms = np.zeros(PIC_NPHASES)
+    cnt = np.zeros(PIC_NPHASES, dtype=np.int64)
+    _check(h, load_library().pic_get_phase_times(h, inst, _dp(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64))))
+    return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(PHASES)}
+
+
+def pic_launch_count():
+    return int(load_library().pic_launch_count())
+
+
+def _torch_stream():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the PIC/MCC library needs a CUDA GPU; none is visible")
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ----------------------------------------------------------------------------
+# convenience: one handle built from a workload
+# ----------------------------------------------------------------------------
+class _CfgHolder:
+    """Keeps the ctypes arrays a pic_instance_cfg points to alive."""
+
+    def __init__(self, wl, precision, cg_rtol, cg_maxit, warm_start, sort_interval):
+        sp = (pic_species * len(wl.species))()
+        for i, s in enumerate(wl.species):
+            sp[i].charge_C, sp[i].mass_kg, sp[i].weight = s.charge_C, s.mass_kg, s.weight
+            sp[i].role, sp[i].capacity = s.role, int(s.capacity)
+        self.tables = []
+        xs = (pic_xsec * max(len(wl.xsec), 1))()
+        for i, x in enumerate(wl.xsec):
+            E = np.ascontiguousarray(x.E_eV, dtype=np.float64)
+            s = np.ascontiguousarray(x.sigma_m2, dtype=np.float64)
+            self.tables += [E, s]
+            xs[i].kind, xs[i].projectile, xs[i].target, xs[i].product = x.kind, x.projectile, x.target, x.product
+            xs[i].threshold_eV, xs[i].n = x.threshold_eV, E.size
+            xs[i].E_eV, xs[i].sigma_m2 = _dp(E), _dp(s)
+        c = pic_instance_cfg()
+        c.nx, c.ny, c.nz = wl.nx, wl.ny, wl.nz
+        c.h, c.dt, c.phi_cathode_V, c.phi_anode_V = wl.h, wl.dt, wl.phi_cathode, wl.phi_anode
+        c.rho_background = wl.rho_background
+        c.sort_interval = wl.sort_interval if sort_interval is None else sort_interval
+        c.cg_rtol = wl.cg_rtol if cg_rtol is None else cg_rtol
+        c.cg_maxit = wl.cg_maxit if cg_maxit is None else cg_maxit
+        c.precision = precision
+        c.seed = wl.seed
+        c.nspecies = len(wl.species)
+        c.species = sp
+        c.nxsec = len(wl.xsec)
+        c.xsec = xs
+        c.warm_start = warm_start
+        self.sp, self.xs, self.cfg = sp, xs, c
+
+
+class Simulation:
+    """One or more instances of the GB300 PIC/MCC step driven through the C ABI."""
+
+    def __init__(self, workloads_, precision=PIC_FP64, cg_rtol=None, cg_maxit=None, warm_start=PIC_WARM_PREV,
+                 preload=True, sort_interval=None, stream=None, background_density=0.0):
+        if not isinstance(workloads_, (list, tuple)):
+            workloads_ = [workloads_]
+        self.wls = list(workloads_)
+        self.wl = self.wls[0]
+        self._holders = [_CfgHolder(w, precision, cg_rtol, cg_maxit, warm_start, sort_interval) for w in self.wls]
+        self.h = pic_create([hd.cfg for hd in self._holders], stream)
+        for i, w in enumerate(self.wls):
+            for q in w.sources:
+                pic_inject(self.h, i, q.species, q.cx, q.cy, q.radius, q.flux_m2s, q.T_K)
+            if background_density > 0:
+                pic_set_mcc_background(self.h, i, background_density)
+            if preload and w.preload:
+                for sp, (x, v) in enumerate(w.preload):
+                    if len(x):
+                        pic_inject_particles(self.h, i, sp, x, v)
+
+    def close(self):
+        if self.h:
+            pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1, check=True):
+        return pic_step(self.h, n, check)
+
+    def moments(self, inst=0):
+        m = pic_moments(self.h, inst)
+        ns = len(self.wls[inst].species)
+        return {
+            "step": m.step, "count": list(m.count[:ns]), "injected": list(m.injected[:ns]),
+            "abs_cathode": list(m.absorbed_cathode[:ns]), "abs_anode": list(m.absorbed_anode[:ns]),
+            "abs_energy_cathode": list(m.absorbed_energy_cathode_J[:ns]),
+            "abs_energy_anode": list(m.absorbed_energy_anode_J[:ns]),
+            "n_ionization": m.ionizations, "n_elastic": m.elastic, "n_suppressed": m.suppressed,
+            "cg_iters": m.cg_iters, "cg_resid_rel": m.cg_resid_rel, "total_charge": m.total_charge_C,
+            "kinetic": list(m.kinetic_J[:ns]), "field_energy": m.field_energy_J,
+            "charge_to_cathode_last": m.charge_to_cathode_C, "charge_to_anode_last": m.charge_to_anode_C,
+            "next_pid": m.next_pid, "error_flags": m.error_flags, "pushed": list(m.pushed[:ns]),
+        }
+
+    def particles(self, sp, inst=0):
+        return pic_get_particles(self.h, inst, sp)
+
+    def count(self, sp, inst=0):
+        return pic_get_count(self.h, inst, sp)
+
+    def rho(self, inst=0):
+        w = self.wls[inst]
+        return pic_get_field(self.h, inst, PIC_FIELD_RHO, (w.nz + 1, w.ny, w.nx))
+
+    def phi(self, inst=0):
+        w = self.wls[inst]
+        return pic_get_field(self.h, inst, PIC_FIELD_PHI, (w.nz + 1, w.ny, w.nx))
+
+    def set_phi(self, phi, inst=0):
+        pic_set_phi(self.h, inst, phi)
+
+    def ncount(self, sp, inst=0):
+        w = self.wls[inst]
+        return pic_get_field(self.h, inst, PIC_FIELD_NCOUNT, (w.nz, w.ny, w.nx), species=sp)
+
+    def cell_start(self, sp, inst=0):
+        w = self.wls[inst]
+        return pic_get_cell_start(self.h, inst, sp, w.nx * w.ny * w.nz)
+
+    def sort_now(self, inst=0):
+        pic_sort_now(self.h, inst)
+
+    def solve(self, rho, phi0=None, inst=0):
+        w = self.wls[inst]
+        if phi0 is None:
+            phi0 = np.zeros((w.nz + 1, w.ny, w.nx))
+        return pic_solve(self.h, inst, rho, phi0)
+
+    def ionization_log(self, inst=0):
+        return pic_get_ionization_log(self.h, inst)

@@ -1,0 +1,370 @@
+// k_grid.cu -- grid-side kernels: deposition (a3), Poisson right-hand side,
+// node field E = -grad phi (a5), fills, host transfer helpers, moments (a11).
+#include "pic_internal.cuh"
+#include "pic_kernels.cuh"
+
+namespace pic {
+
+constexpr int kBlock = 256;
+
+static int grid_for(long long n, int per_block = kBlock, int max_blocks = 152 * 16) {
+  long long b = (n + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_fill(T* p, long long n, T v) {
+  for (long long i = gtid(); i < n; i += gstride()) p[i] = v;
+}
+void launch_fill64(double* p, long long n, double v, cudaStream_t st) {
+  PIC_LAUNCH(grid_for(n), kBlock, 0, st, k_fill<double>)(p, n, v);
+}
+void launch_fill32(float* p, long long n, float v, cudaStream_t st) {
+  PIC_LAUNCH(grid_for(n), kBlock, 0, st, k_fill<float>)(p, n, v);
+}
+void launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t st) {
+  PIC_LAUNCH(grid_for(n), kBlock, 0, st, k_fill<int32_t>)(p, n, v);
+}
+
+// ---------------------------------------------------------------------------
+// a3: cloud-in-cell deposition. Charged species add q w S / h^3 to the 8
+// corner nodes; neutral species add 1 to the count of their cell (NGP).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void deposit_one(const Grid& g, const Particle64& p, const DepositArgs<Store64>& a) {
+  long long idx[8];
+  corner_nodes(g, p.l.i, p.l.j, p.l.k, idx);
+  double w[8];
+  cic_weights(p.l.fx, p.l.fy, p.l.fz, w);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) atomicAdd(&a.rho64[idx[c]], a.qw_h3 * w[c]);
+}
+__device__ __forceinline__ void deposit_one(const Grid& g, const ParticleMx& p, const DepositArgs<StoreMx>& a) {
+  int i, j, k;
+  cell_ijk(g, p.cell, i, j, k);
+  long long idx[8];
+  corner_nodes(g, i, j, k, idx);
+  float w[8];
+  cic_weights(p.ox, p.oy, p.oz, w);
+  const float q = (float)a.qw_h3;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) atomicAdd(&a.rho32[idx[c]], q * w[c]);
+}
+
+template <class S>
+__global__ void __launch_bounds__(kBlock) k_deposit(DepositArgs<S> a) {
+  const long long n = (long long)a.cnt->n[a.cur][a.species];
+  const Grid& g = a.g;
+  for (long long i = gtid(); i < n; i += gstride()) {
+    const auto p = store_read(a.st, g, i);
+    if (a.neutral) {
+      if (p.pid != kPidDead) atomicAdd(&a.ncount[particle_cell(p)], 1);
+      continue;
+    }
+    deposit_one(g, p, a);
+  }
+}
+
+template <class S>
+void launch_deposit(const DepositArgs<S>& a, int grid, cudaStream_t st) {
+  PIC_LAUNCH(grid, kBlock, 0, st, k_deposit<S>)(a);
+}
+template void launch_deposit<Store64>(const DepositArgs<Store64>&, int, cudaStream_t);
+template void launch_deposit<StoreMx>(const DepositArgs<StoreMx>&, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// a4 right-hand side of Eq. (1) scaled by h^2 over the unknown nodes k = 1..nz-1:
+//   b = h^2 rho / eps0 (+ phi_c on k = 1) (+ phi_a on k = nz-1)
+// ---------------------------------------------------------------------------
+__global__ void k_rhs(Grid g, const double* __restrict__ rho64, const float* __restrict__ rho32, double* __restrict__ b) {
+  const long long nu = (long long)(g.nz - 1) * g.nplane;
+  const double s = g.h * g.h / kEps0;
+  for (long long u = gtid(); u < nu; u += gstride()) {
+    const long long node = u + g.nplane;
+    const int k = (int)(node / g.nplane);
+    double v = s * (rho64 ? rho64[node] : (double)rho32[node]);
+    if (k == 1) v += g.phi_c;
+    if (k == g.nz - 1) v += g.phi_a;
+    b[u] = v;
+  }
+}
+void launch_rhs(const Grid& g, const double* rho64, const float* rho32, double* b, cudaStream_t st) {
+  PIC_LAUNCH(grid_for((long long)(g.nz - 1) * g.nplane), kBlock, 0, st, k_rhs)(g, rho64, rho32, b);
+}
+
+__global__ void k_phi_planes(Grid g, double* phi) {
+  for (long long p = gtid(); p < g.nplane; p += gstride()) {
+    phi[p] = g.phi_c;
+    phi[(long long)g.nz * g.nplane + p] = g.phi_a;
+  }
+}
+void launch_phi_planes(const Grid& g, double* phi, cudaStream_t st) {
+  PIC_LAUNCH(grid_for(g.nplane), kBlock, 0, st, k_phi_planes)(g, phi);
+}
+
+// ---------------------------------------------------------------------------
+// a5: node field E = -grad phi. Central differences (periodic in x, y); in z
+// central inside, second-order one-sided on the electrode planes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double3 node_field(const Grid& g, const double* __restrict__ f, long long n) {
+  const long long pl = g.nplane;
+  const int k = (int)(n / pl);
+  const long long r = n - (long long)k * pl;
+  const int j = (int)(r / g.nx);
+  const int i = (int)(r - (long long)j * g.nx);
+  const int im = i == 0 ? g.nx - 1 : i - 1, ip = i == g.nx - 1 ? 0 : i + 1;
+  const int jm = j == 0 ? g.ny - 1 : j - 1, jp = j == g.ny - 1 ? 0 : j + 1;
+  const long long row = (long long)k * pl + (long long)j * g.nx;
+  const double c = 0.5 * g.inv_h;
+  double3 e;
+  e.x = (f[row + im] - f[row + ip]) * c;
+  e.y = (f[(long long)k * pl + (long long)jm * g.nx + i] - f[(long long)k * pl + (long long)jp * g.nx + i]) * c;
+  if (k == 0)
+    e.z = (3.0 * f[n] - 4.0 * f[n + pl] + f[n + 2 * pl]) * c;
+  else if (k == g.nz)
+    e.z = (-3.0 * f[n] + 4.0 * f[n - pl] - f[n - 2 * pl]) * c;
+  else
+    e.z = (f[n - pl] - f[n + pl]) * c;
+  return e;
+}
+
+__global__ void k_efield64(Grid g, const double* __restrict__ phi, double4_32a* __restrict__ E) {
+  for (long long n = gtid(); n < g.nnode; n += gstride()) {
+    const double3 e = node_field(g, phi, n);
+    double4_32a v;
+    v.x = e.x;
+    v.y = e.y;
+    v.z = e.z;
+    v.w = 0.0;
+    E[n] = v;
+  }
+}
+__global__ void k_efield32(Grid g, const double* __restrict__ phi, float4* __restrict__ E) {
+  for (long long n = gtid(); n < g.nnode; n += gstride()) {
+    const double3 e = node_field(g, phi, n);
+    E[n] = make_float4((float)e.x, (float)e.y, (float)e.z, 0.f);
+  }
+}
+void launch_efield64(const Grid& g, const double* phi, double4_32a* E, cudaStream_t st) {
+  PIC_LAUNCH(grid_for(g.nnode), kBlock, 0, st, k_efield64)(g, phi, E);
+}
+void launch_efield32(const Grid& g, const double* phi, float4* E, cudaStream_t st) {
+  PIC_LAUNCH(grid_for(g.nnode), kBlock, 0, st, k_efield32)(g, phi, E);
+}
+
+// ---------------------------------------------------------------------------
+// per-step counter reset
+// ---------------------------------------------------------------------------
+__global__ void k_step_begin(DevCounters* cnt, StepBegin sb) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int s = 0; s < sb.nsp; ++s) cnt->n[sb.out[s]][s] = 0;
+  cnt->n_events = 0;
+  cnt->n_success = 0;
+  cnt->n_cands = 0;
+  cnt->q_cathode_step = 0.0;
+  cnt->q_anode_step = 0.0;
+}
+void launch_step_begin(DevCounters* cnt, const int* out_buf, int nsp, cudaStream_t st) {
+  StepBegin sb;
+  sb.nsp = nsp;
+  for (int s = 0; s < kMaxSpecies; ++s) sb.out[s] = s < nsp ? out_buf[s] : 0;
+  PIC_LAUNCH(1, 1, 0, st, k_step_begin)(cnt, sb);
+}
+
+// ---------------------------------------------------------------------------
+// host transfer helpers (staging arrays of FP64 x[n][3], v[n][3])
+// ---------------------------------------------------------------------------
+template <class S>
+__global__ void k_load(Grid g, S st, DevCounters* cnt, int cur, int species, long long cap, const double* __restrict__ x,
+                       const double* __restrict__ v, long long n) {
+  const unsigned long long base = cnt->n[cur][species];
+  const uint32_t pid0 = cnt->next_pid;
+  for (long long i = gtid(); i < n; i += gstride()) {
+    const unsigned long long slot = base + i;
+    if (slot >= (unsigned long long)cap) continue;
+    store_write(st, g, slot, x[3 * i], x[3 * i + 1], x[3 * i + 2], v[3 * i], v[3 * i + 1], v[3 * i + 2],
+                pid0 + (uint32_t)i);
+  }
+}
+__global__ void k_load_commit(DevCounters* cnt, int cur, int species, long long n) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  cnt->n[cur][species] += n;
+  cnt->next_pid += (unsigned int)n;
+}
+template <class S>
+void launch_load(const Grid& g, S st, DevCounters* cnt, int cur, int species, long long cap, const double* x,
+                 const double* v, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  PIC_LAUNCH(grid_for(n), kBlock, 0, s, k_load<S>)(g, st, cnt, cur, species, cap, x, v, n);
+  PIC_LAUNCH(1, 1, 0, s, k_load_commit)(cnt, cur, species, n);
+}
+
+template <class S>
+__global__ void k_download(Grid g, S st, long long n, double* x, double* v, uint32_t* pid) {
+  for (long long i = gtid(); i < n; i += gstride()) store_get(st, g, i, x + 3 * i, v + 3 * i, pid + i);
+}
+template <class S>
+void launch_download(const Grid& g, S st, long long n, double* x, double* v, uint32_t* pid, cudaStream_t s) {
+  if (n <= 0) return;
+  PIC_LAUNCH(grid_for(n), kBlock, 0, s, k_download<S>)(g, st, n, x, v, pid);
+}
+template void launch_load<Store64>(const Grid&, Store64, DevCounters*, int, int, long long, const double*,
+                                   const double*, long long, cudaStream_t);
+template void launch_load<StoreMx>(const Grid&, StoreMx, DevCounters*, int, int, long long, const double*,
+                                   const double*, long long, cudaStream_t);
+template void launch_download<Store64>(const Grid&, Store64, long long, double*, double*, uint32_t*, cudaStream_t);
+template void launch_download<StoreMx>(const Grid&, StoreMx, long long, double*, double*, uint32_t*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// a2 helpers: sort keys (cell << pid_bits | pid; tombstones sort last) and the
+// payload gather through the permutation.
+// ---------------------------------------------------------------------------
+template <class S>
+__global__ void k_cell_keys(Grid g, S st, long long n_max, const unsigned long long* n_dev, int pid_bits,
+                            unsigned long long* keys, uint32_t* vals, int32_t* cell_count) {
+  const long long n = (long long)*n_dev;
+  const unsigned long long pmask = pid_bits >= 32 ? 0xFFFFFFFFull : ((1ull << pid_bits) - 1ull);
+  for (long long i = gtid(); i < n && i < n_max; i += gstride()) {
+    const auto p = store_read(st, g, i);
+    const unsigned long long cell = p.pid == kPidDead ? (unsigned long long)g.ncell : (unsigned long long)particle_cell(p);
+    keys[i] = (cell << pid_bits) | ((unsigned long long)p.pid & pmask);
+    vals[i] = (uint32_t)i;
+    if (p.pid != kPidDead) atomicAdd(&cell_count[cell], 1);
+  }
+}
+template <class S>
+void launch_cell_keys(const Grid& g, S st, long long n_max, const unsigned long long* n_dev, int pid_bits,
+                      unsigned long long* keys, uint32_t* vals, int32_t* cell_count, cudaStream_t s) {
+  PIC_LAUNCH(grid_for(n_max), kBlock, 0, s, k_cell_keys<S>)(g, st, n_max, n_dev, pid_bits, keys, vals, cell_count);
+}
+
+__device__ __forceinline__ void copy_slot(const Store64& s, const Store64& d, long long from, long long to) {
+  d.x[to] = s.x[from];
+  d.y[to] = s.y[from];
+  d.z[to] = s.z[from];
+  d.vx[to] = s.vx[from];
+  d.vy[to] = s.vy[from];
+  d.vz[to] = s.vz[from];
+  d.pid[to] = s.pid[from];
+}
+__device__ __forceinline__ void copy_slot(const StoreMx& s, const StoreMx& d, long long from, long long to) {
+  d.cell[to] = s.cell[from];
+  d.ox[to] = s.ox[from];
+  d.oy[to] = s.oy[from];
+  d.oz[to] = s.oz[from];
+  d.vx[to] = s.vx[from];
+  d.vy[to] = s.vy[from];
+  d.vz[to] = s.vz[from];
+  d.pid[to] = s.pid[from];
+}
+template <class S>
+__global__ void k_gather(S src, S dst, const uint32_t* __restrict__ perm, const unsigned long long* n_dev, long long n_max) {
+  const long long n = (long long)*n_dev;
+  for (long long i = gtid(); i < n && i < n_max; i += gstride()) copy_slot(src, dst, perm[i], i);
+}
+template <class S>
+void launch_gather(S src, S dst, const uint32_t* perm, const unsigned long long* n_dev, long long n_max,
+                   cudaStream_t s) {
+  PIC_LAUNCH(grid_for(n_max), kBlock, 0, s, k_gather<S>)(src, dst, perm, n_dev, n_max);
+}
+template void launch_cell_keys<Store64>(const Grid&, Store64, long long, const unsigned long long*, int,
+                                        unsigned long long*, uint32_t*, int32_t*, cudaStream_t);
+template void launch_cell_keys<StoreMx>(const Grid&, StoreMx, long long, const unsigned long long*, int,
+                                        unsigned long long*, uint32_t*, int32_t*, cudaStream_t);
+template void launch_gather<Store64>(Store64, Store64, const uint32_t*, const unsigned long long*, long long,
+                                     cudaStream_t);
+template void launch_gather<StoreMx>(StoreMx, StoreMx, const uint32_t*, const unsigned long long*, long long,
+                                     cudaStream_t);
+
+// after a cell sort into buffer c^1: tombstones (sorted last) are dropped
+__global__ void k_sort_commit(DevCounters* cnt, int c, int s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  cnt->n[c ^ 1][s] = cnt->n[c][s] - cnt->n_tomb[s];
+  cnt->n_tomb[s] = 0;
+}
+void launch_sort_commit(DevCounters* cnt, int c, int s, cudaStream_t st) { PIC_LAUNCH(1, 1, 0, st, k_sort_commit)(cnt, c, s); }
+
+// ---------------------------------------------------------------------------
+// a11 moments: FP64 reductions (block sums, one atomic per block)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sm[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sm[w] = v;
+  __syncthreads();
+  v = 0.0;
+  if (w == 0) {
+    v = l < (int)(blockDim.x >> 5) ? sm[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+__device__ __forceinline__ double v2_of(const Store64& s, long long i) {
+  return s.vx[i] * s.vx[i] + s.vy[i] * s.vy[i] + s.vz[i] * s.vz[i];
+}
+__device__ __forceinline__ double v2_of(const StoreMx& s, long long i) {
+  const double a = s.vx[i], b = s.vy[i], c = s.vz[i];
+  return a * a + b * b + c * c;
+}
+template <class S>
+__global__ void k_kinetic(S st, const unsigned long long* n_dev, long long n_max, double* out) {
+  const long long n = (long long)*n_dev;
+  double acc = 0.0;
+  for (long long i = gtid(); i < n && i < n_max; i += gstride())
+    if (st.pid[i] != kPidDead) acc += v2_of(st, i);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+template <class S>
+void launch_kinetic(S st, const unsigned long long* n_dev, long long n_max, double* out, cudaStream_t s) {
+  PIC_LAUNCH(grid_for(n_max), kBlock, 0, s, k_kinetic<S>)(st, n_dev, n_max, out);
+}
+template void launch_kinetic<Store64>(Store64, const unsigned long long*, long long, double*, cudaStream_t);
+template void launch_kinetic<StoreMx>(StoreMx, const unsigned long long*, long long, double*, cudaStream_t);
+
+// sum over edges of (delta phi)^2
+__global__ void k_field_energy(Grid g, const double* __restrict__ f, double* out) {
+  double acc = 0.0;
+  for (long long n = gtid(); n < g.nnode; n += gstride()) {
+    const long long pl = g.nplane;
+    const int k = (int)(n / pl);
+    const long long r = n - (long long)k * pl;
+    const int j = (int)(r / g.nx);
+    const int i = (int)(r - (long long)j * g.nx);
+    const double c = f[n];
+    const double dx = f[(long long)k * pl + (long long)j * g.nx + (i + 1 == g.nx ? 0 : i + 1)] - c;
+    const double dy = f[(long long)k * pl + (long long)(j + 1 == g.ny ? 0 : j + 1) * g.nx + i] - c;
+    acc += dx * dx + dy * dy;
+    if (k < g.nz) {
+      const double dz = f[n + pl] - c;
+      acc += dz * dz;
+    }
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+void launch_field_energy(const Grid& g, const double* phi, double* out, cudaStream_t s) {
+  PIC_LAUNCH(grid_for(g.nnode), kBlock, 0, s, k_field_energy)(g, phi, out);
+}
+
+// Philox on the device (test hook)
+__global__ void k_philox(long long n, uint4 ctr, uint2 key, uint32_t* out) {
+  for (long long i = gtid(); i < n; i += gstride()) {
+    const uint4 r = philox(make_uint4(ctr.x + (uint32_t)i, ctr.y, ctr.z, ctr.w), key);
+    out[4 * i] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
+  }
+}
+void launch_philox(long long n, uint4 ctr, uint2 key, uint32_t* out, cudaStream_t s) {
+  PIC_LAUNCH(grid_for(n), kBlock, 0, s, k_philox)(n, ctr, key, out);
+}
+
+}  // namespace pic

@@ -1,0 +1,386 @@
+// k_particles.cu -- particle kernels of the PIC/MCC step (FP64 and MIXED stores).
+//
+//   a1 inject            k_inject<Store>
+//   a5+a6+a7+a8 (+a10)   k_push<Store>: field gather at x^n, leapfrog kick/drift,
+//                        absorption at the electrodes, Monte Carlo collisions
+//                        (Eq. 4), warp-aggregated compaction into the other buffer
+//   a9 ionization        k_resolve_rank / k_resolve_apply / k_resolve_cleanup
+//
+// Collision test (Eq. 4): P = 1 - exp(-u dt sum_c n_c sigma_c(E)), decided with the
+// FP64 uniform U1 of Philox(pid, step, TAG_MCC). Because 1 - exp(-x) <= x and
+// sigma_c(E) <= max sigma_c, every electron whose FP32 draw exceeds an FP32 upper
+// bound of x (with a safety margin) cannot collide; only the remainder (a fraction
+// of about P of the electrons) evaluates P and the channel choice exactly in FP64.
+#include "pic_internal.cuh"
+#include "pic_kernels.cuh"
+
+namespace pic {
+
+// ---------------------------------------------------------------------------
+// cross sections
+// ---------------------------------------------------------------------------
+// Exact FP64 lookup: bisection for E_lo <= E < E_hi, then the interpolation
+// sigma_lo + t (sigma_hi - sigma_lo), t = (E - E_lo)/(E_hi - E_lo).
+__device__ double xs_sigma64(const XsDev& c, double E) {
+  if (!(E > c.thr)) return 0.0;
+  if (c.n == 1) return c.sig[0];
+  if (E <= c.E[0]) return c.sig[0];
+  if (E >= c.E[c.n - 1]) return c.sig[c.n - 1];
+  int lo = 0, hi = c.n - 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (E < c.E[mid]) hi = mid; else lo = mid;
+  }
+  const double t = (E - c.E[lo]) / (c.E[lo + 1] - c.E[lo]);
+  return c.sig[lo] + t * (c.sig[lo + 1] - c.sig[lo]);
+}
+
+// Exact FP64 collision test of Eq. (4); returns -1 (none) or the channel slot.
+__device__ int mcc_exact_dt(const McArgs& m, long long cell, double v2, double U, double dt, double* E_eV_out) {
+  const double u = sqrt(v2);
+  const double E = m.half_m_over_e * v2;
+  *E_eV_out = E;
+  double cum[kMaxXsec];
+  double nu = 0.0;
+  for (int a = 0; a < m.nch; ++a) {
+    const double nt = m.bg_mode ? m.bg_density : (double)m.ncount[a][cell] * m.dens[a];
+    nu += nt * xs_sigma64(m.ch[a], E);
+    cum[a] = nu;
+  }
+  if (!(nu > 0.0)) return -1;
+  const double P = -expm1(-u * dt * nu);
+  if (!(U < P)) return -1;
+  int a = 0;
+  while (a < m.nch - 1 && !(U < P * (cum[a] / nu))) ++a;
+  return a;
+}
+
+// FP32 filter: true when the electron certainly does not collide.
+__device__ __forceinline__ bool mcc_cannot_collide(const McArgs& m, long long cell, float v2f, float U32, float dt_f) {
+  float nb = 0.f;
+  for (int a = 0; a < m.nch; ++a) {
+    const float cnt = m.bg_mode ? 1.f : (float)m.ncount[a][cell];
+    nb = fmaf(cnt, m.bound_f[a], nb);
+  }
+  // x_upper = u dt sum n_a max sigma_a >= x >= P; 1.001 covers FP32 rounding
+  const float xu = sqrtf(v2f) * dt_f * nb * 1.001f;
+  return U32 - 0x1p-25f > xu;
+}
+
+// ---------------------------------------------------------------------------
+// a1: injection
+// ---------------------------------------------------------------------------
+template <class S>
+__global__ void k_inject(InjectArgs<S> a) {
+  const long long total = a.total;
+  for (long long t = gtid(); t < total; t += gstride()) {
+    // source of this particle
+    int q = 0;
+    while (q + 1 < a.nsrc && t >= a.src_first[q + 1]) ++q;
+    const InjSrc& s = a.src[q];
+    const long long kth = t - a.src_first[q];
+    const uint32_t pid = a.cnt->next_pid + (uint32_t)t;
+    const unsigned long long base = a.cnt->n[a.cur[s.species]][s.species];
+    const unsigned long long slot = base + a.species_offset[q] + kth;
+    if (slot >= (unsigned long long)a.cap[s.species]) {
+      atomicOr(&a.cnt->error, ERR_CAPACITY);
+      continue;
+    }
+    const uint4 dp = draw(a.key, pid, a.step, TAG_INJ_POS);
+    const uint4 d1 = draw(a.key, pid, a.step, TAG_INJ_VXY);
+    const uint4 d2 = draw(a.key, pid, a.step, TAG_INJ_VZ);
+    const uint4 d3 = draw(a.key, pid, a.step, TAG_INJ_Z);
+    const double r = s.R * sqrt(u01_64(dp.x, dp.y));
+    const double th = 2.0 * kPi * u01_64(dp.z, dp.w);
+    const double x = wrap_coord(s.cx + r * cos(th), a.g.Lx, a.g.inv_Lx);
+    const double y = wrap_coord(s.cy + r * sin(th), a.g.Ly, a.g.inv_Ly);
+    const double rad1 = sqrt(-2.0 * log(u01_64(d1.x, d1.y)));
+    const double ph1 = 2.0 * kPi * u01_64(d1.z, d1.w);
+    const double n1 = rad1 * cos(ph1), n2 = rad1 * sin(ph1);
+    const double n3 = sqrt(-2.0 * log(u01_64(d2.x, d2.y))) * cos(2.0 * kPi * u01_64(d2.z, d2.w));
+    const double vx = s.sig * n1, vy = s.sig * n2, vz = s.sig * fabs(n3);
+    const double z = u01_64(d3.x, d3.y) * vz * a.g.dt;
+    store_write(a.st[s.species], a.g, slot, x, y, z, vx, vy, vz, pid);
+  }
+}
+
+__global__ void k_inject_commit(DevCounters* cnt, InjectCommit c) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int s = 0; s < c.nsp; ++s) {
+    if (c.add[s] == 0) continue;
+    unsigned long long nn = cnt->n[c.cur[s]][s] + c.add[s];
+    if (nn > (unsigned long long)c.cap[s]) nn = c.cap[s];
+    cnt->injected[s] += nn - cnt->n[c.cur[s]][s];
+    cnt->n[c.cur[s]][s] = nn;
+  }
+  cnt->next_pid += (unsigned int)c.total;
+}
+
+// ---------------------------------------------------------------------------
+// a5-a8 + a10: gather / push / absorb / collide / compact
+// ---------------------------------------------------------------------------
+template <class S, bool CHARGED, bool MCC, bool NEUTRAL>
+__global__ void __launch_bounds__(256) k_push(PushArgs<S> a) {
+  const long long n = (long long)a.cnt->n[a.cur_in][a.species];
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    a.cnt->pushed[a.species] += (unsigned long long)n - (NEUTRAL ? a.cnt->n_tomb[a.species] : 0ull);
+  const Grid& g = a.g;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += gstride()) {
+    const long long i = base + threadIdx.x;
+    const bool valid = i < n;
+    bool keep = false, ionize = false;
+    using Particle = typename PTraits<S>::P;
+    Particle p;
+    long long cell_n = 0;
+    int ch_ion = -1;
+    double E_eV = 0.0;
+    if (valid) {
+      p = store_read(a.in, g, i);
+      if (NEUTRAL && p.pid == kPidDead) {
+        // converted neutral from the previous step: dropped here
+      } else {
+        cell_n = particle_cell(p);
+        if (CHARGED) {
+          const auto e = p.gather(g, a);
+          p.kick(a, e);
+        }
+        const int side = p.drift(g);  // -1 cathode, +1 anode, 0 inside
+        if (side != 0) {
+          const double v2 = p.v2();
+          const double ke = 0.5 * a.mass * a.weight * v2;
+          if (side < 0) {
+            atomicAdd(&a.cnt->abs_cathode[a.species], 1ull);
+            atomicAdd(&a.cnt->abs_energy_cathode[a.species], ke);
+            atomicAdd(&a.cnt->q_cathode_step, a.charge * a.weight);
+          } else {
+            atomicAdd(&a.cnt->abs_anode[a.species], 1ull);
+            atomicAdd(&a.cnt->abs_energy_anode[a.species], ke);
+            atomicAdd(&a.cnt->q_anode_step, a.charge * a.weight);
+          }
+        } else {
+          keep = true;
+          if (MCC) {
+            const uint4 d = draw(a.mc.key, p.pid, a.mc.step, TAG_MCC);
+            const float v2f = p.v2f();
+            if (!mcc_cannot_collide(a.mc, cell_n, v2f, u01_32(d.x), (float)g.dt)) {
+              const double U = u01_64(d.x, d.y);
+              const double v2 = p.v2();
+              const int ch = mcc_exact_dt(a.mc, cell_n, v2, U, g.dt, &E_eV);
+              if (ch >= 0) {
+                if (a.mc.ch[ch].kind == XS_ELASTIC) {
+                  const uint4 s = draw(a.mc.key, p.pid, a.mc.step, TAG_SCATTER);
+                  const double ct = 2.0 * u01_64(s.x, s.y) - 1.0;
+                  const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+                  const double ph = 2.0 * kPi * u01_64(s.z, s.w);
+                  const double u = sqrt(v2);
+                  p.set_v(u * st * cos(ph), u * st * sin(ph), u * ct);
+                  atomicAdd(&a.cnt->n_el, 1ull);
+                } else if (a.mc.bg_mode) {
+                  // fixed-background test mode: counted, nothing consumed or created
+                  atomicAdd(&a.cnt->n_ion, 1ull);
+                } else {
+                  ionize = true;
+                  ch_ion = ch;
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    const unsigned long long slot = warp_reserve(&a.cnt->n[a.cur_in ^ 1][a.species], keep);
+    if (keep) {
+      if (slot < (unsigned long long)a.cap) {
+        store_write_p(a.out, slot, p);
+        if (ionize) {
+          const unsigned int e = atomicAdd(&a.cnt->n_events, 1u);
+          if (e < (unsigned int)a.ev_cap) {
+            Event ev;
+            ev.pid = p.pid;
+            ev.cell = (uint32_t)cell_n;
+            ev.slot = (uint32_t)slot;
+            ev.ch = ch_ion;
+            ev.E_eV = E_eV;
+            ev.victim = -1;
+            ev.next = atomicExch(&a.ev_head[cell_n], (int)e);
+            a.ev[e] = ev;
+          } else {
+            atomicOr(&a.cnt->error, ERR_EVENTS);
+          }
+        }
+        if (NEUTRAL && a.ev_head != nullptr && a.ev_head[cell_n] >= 0) {
+          // candidate victim of an ionization in its cell at x^n
+          const unsigned int c = atomicAdd(&a.cnt->n_cands, 1u);
+          if (c < (unsigned int)a.cand_cap) {
+            const uint4 k = draw(a.mc.key, p.pid, a.mc.step, TAG_VICTIM);
+            Cand cd;
+            cd.key = ((unsigned long long)k.x << 32) | (unsigned long long)p.pid;
+            cd.slot = (uint32_t)slot;
+            cd.next = atomicExch(&a.cand_head[cell_n], (int)c);
+            a.cand[c] = cd;
+          } else {
+            atomicOr(&a.cnt->error, ERR_EVENTS);
+          }
+        }
+      } else {
+        atomicOr(&a.cnt->error, ERR_CAPACITY);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a9: ionization resolve
+// ---------------------------------------------------------------------------
+// Rank of each event among the events of its cell by primary pid, then its
+// victim: the rank-th smallest (key, pid) candidate of that cell.
+__global__ void k_resolve_rank(ResolveArgs a) {
+  const unsigned int ne = min(a.cnt->n_events, (unsigned int)a.ev_cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.cnt->ev_sort_n = ne;
+  for (long long e = gtid(); e < ne; e += gstride()) {
+    Event& ev = a.ev[e];
+    int r = 0;
+    int guard = 0;
+    for (int j = a.ev_head[ev.cell]; j >= 0 && guard < (1 << 22); j = a.ev[j].next, ++guard)
+      if (a.ev[j].pid < ev.pid) ++r;
+    // r-th smallest candidate key (0-based) by repeated minimum selection
+    unsigned long long prev = 0;
+    bool have_prev = false;
+    int victim = -1;
+    for (int s = 0; s <= r; ++s) {
+      unsigned long long best = ~0ull;
+      int bi = -1;
+      int g2 = 0;
+      for (int c = a.cand_head[ev.cell]; c >= 0 && g2 < (1 << 22); c = a.cand[c].next, ++g2) {
+        const unsigned long long k = a.cand[c].key;
+        if ((!have_prev || k > prev) && k < best) { best = k; bi = c; }
+      }
+      if (bi < 0) { victim = -1; break; }
+      prev = best;
+      have_prev = true;
+      victim = bi;
+    }
+    ev.victim = victim;
+    // sort key for the apply order: successful events first, by primary pid
+    a.sort_keys[e] = ((unsigned long long)(victim < 0 ? 1 : 0) << 32) | ev.pid;
+    a.sort_vals[e] = (uint32_t)e;
+    if (victim >= 0) atomicAdd(&a.cnt->n_success, 1u);
+  }
+}
+
+template <class S>
+__global__ void k_resolve_apply(ApplyArgs<S> a) {
+  const unsigned int ns = a.cnt->n_success;
+  const unsigned int ne = min(a.cnt->n_events, (unsigned int)a.ev_cap);
+  const unsigned long long ne_out = a.cnt->n[a.e_out][a.e_species];
+  const unsigned long long ni_out = a.cnt->n[a.i_out][a.i_species];
+  const uint32_t pid0 = a.cnt->next_pid;
+  for (long long r = gtid(); r < ns; r += gstride()) {
+    const Event ev = a.ev[a.sorted_vals[r]];
+    const Cand cd = a.cand[ev.victim];
+    const XsDev& X = a.ch[ev.ch];
+    const uint4 g0 = draw(a.key, ev.pid, a.step, TAG_IONIZE, 0);
+    const uint4 g1 = draw(a.key, ev.pid, a.step, TAG_IONIZE, 1);
+    const double Eex = ev.E_eV - X.thr;
+    const double Us = u01_64(g0.x, g0.y);
+    const double E2 = Us * Eex;
+    const double E1 = (1.0 - Us) * Eex;
+    const double sc = sqrt(E1 / ev.E_eV);
+    // primary: direction kept, energy (1-U) (E - thr)
+    auto pr = store_read(a.e_st, a.g, ev.slot);
+    pr.scale_v(sc);
+    store_write_v(a.e_st, ev.slot, pr);
+    // secondary at the primary's new position
+    const double us = sqrt(2.0 * E2 * kQe / a.e_mass);
+    const double ct = 2.0 * u01_64(g0.z, g0.w) - 1.0;
+    const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    const double ph = 2.0 * kPi * u01_64(g1.x, g1.y);
+    const uint32_t spid = pid0 + (uint32_t)r;
+    auto sec = pr;
+    sec.set_v(us * st * cos(ph), us * st * sin(ph), us * ct);
+    sec.pid = spid;
+    const unsigned long long es = ne_out + r;
+    if (es < (unsigned long long)a.e_cap) store_write_p(a.e_st, es, sec);
+    else atomicOr(&a.cnt->error, ERR_CAPACITY);
+    // victim neutral -> ion (position x^{n+1}, velocity and pid kept)
+    const auto vn = store_read(a.n_st, a.g, cd.slot);
+    const unsigned long long is = ni_out + r;
+    if (is < (unsigned long long)a.i_cap) store_write_p(a.i_st, is, vn);
+    else atomicOr(&a.cnt->error, ERR_CAPACITY);
+    store_kill(a.n_st, cd.slot);
+    if (a.log) {
+      a.log[3 * r] = ev.pid;
+      a.log[3 * r + 1] = vn.pid;
+      a.log[3 * r + 2] = spid;
+    }
+  }
+  (void)ne;
+}
+
+__global__ void k_resolve_commit(DevCounters* cnt, int e_out, int e_sp, long long e_cap, int i_out, int i_sp,
+                                 long long i_cap, int n_sp, int ev_cap) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const unsigned int ne = min(cnt->n_events, (unsigned int)ev_cap);
+  const unsigned int ns = cnt->n_success;
+  cnt->n_ion += ns;
+  cnt->n_supp += ne - ns;
+  unsigned long long a = cnt->n[e_out][e_sp] + ns;
+  cnt->n[e_out][e_sp] = a > (unsigned long long)e_cap ? e_cap : a;
+  unsigned long long b = cnt->n[i_out][i_sp] + ns;
+  cnt->n[i_out][i_sp] = b > (unsigned long long)i_cap ? i_cap : b;
+  cnt->n_tomb[n_sp] = ns;
+  cnt->next_pid += ns;
+}
+
+__global__ void k_resolve_cleanup(ResolveArgs a) {
+  const unsigned int ne = min(a.cnt->n_events, (unsigned int)a.ev_cap);
+  for (long long e = gtid(); e < ne; e += gstride()) {
+    const uint32_t c = a.ev[e].cell;
+    a.ev_head[c] = -1;
+    a.cand_head[c] = -1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// explicit instantiations through launchers
+// ---------------------------------------------------------------------------
+template <class S>
+void launch_inject(const InjectArgs<S>& a, int grid, cudaStream_t st) {
+  PIC_LAUNCH(grid, 256, 0, st, k_inject<S>)(a);
+}
+
+template <class S>
+void launch_push(const PushArgs<S>& a, int role, bool mcc, int grid, cudaStream_t st) {
+  if (role == ROLE_NEUTRAL)
+    PIC_LAUNCH(grid, 256, 0, st, k_push<S, false, false, true>)(a);
+  else if (mcc)
+    PIC_LAUNCH(grid, 256, 0, st, k_push<S, true, true, false>)(a);
+  else
+    PIC_LAUNCH(grid, 256, 0, st, k_push<S, true, false, false>)(a);
+}
+
+void launch_inject_commit(DevCounters* cnt, const InjectCommit& c, cudaStream_t st) {
+  PIC_LAUNCH(1, 1, 0, st, k_inject_commit)(cnt, c);
+}
+
+void launch_resolve_rank(const ResolveArgs& a, int grid, cudaStream_t st) { PIC_LAUNCH(grid, 256, 0, st, k_resolve_rank)(a); }
+void launch_resolve_cleanup(const ResolveArgs& a, int grid, cudaStream_t st) {
+  PIC_LAUNCH(grid, 256, 0, st, k_resolve_cleanup)(a);
+}
+template <class S>
+void launch_resolve_apply(const ApplyArgs<S>& a, int grid, cudaStream_t st) {
+  PIC_LAUNCH(grid, 256, 0, st, k_resolve_apply<S>)(a);
+}
+void launch_resolve_commit(DevCounters* cnt, int e_out, int e_sp, long long e_cap, int i_out, int i_sp,
+                           long long i_cap, int n_sp, int ev_cap, cudaStream_t st) {
+  PIC_LAUNCH(1, 1, 0, st, k_resolve_commit)(cnt, e_out, e_sp, e_cap, i_out, i_sp, i_cap, n_sp, ev_cap);
+}
+
+template void launch_inject<Store64>(const InjectArgs<Store64>&, int, cudaStream_t);
+template void launch_inject<StoreMx>(const InjectArgs<StoreMx>&, int, cudaStream_t);
+template void launch_push<Store64>(const PushArgs<Store64>&, int, bool, int, cudaStream_t);
+template void launch_push<StoreMx>(const PushArgs<StoreMx>&, int, bool, int, cudaStream_t);
+template void launch_resolve_apply<Store64>(const ApplyArgs<Store64>&, int, cudaStream_t);
+template void launch_resolve_apply<StoreMx>(const ApplyArgs<StoreMx>&, int, cudaStream_t);
+
+}  // namespace pic

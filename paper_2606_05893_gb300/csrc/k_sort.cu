@@ -1,0 +1,228 @@
+// k_sort.cu -- stable LSD radix sort of (u64 key, u32 value) pairs with the
+// element count read from device memory, and an exclusive scan. Used by the
+// cell sort (a2: key = cell << pid_bits | pid, unique, so the order is unique)
+// and by the ionization resolve (events ordered by primary pid).
+//
+// One pass per 8-bit digit: (1) per-tile digit histograms, (2) per-digit scan of
+// the tile histograms plus the digit totals, (3) stable scatter: tiles are
+// processed in rounds of 256 consecutive elements; within a round the rank of an
+// element among equal digits comes from __match_any_sync inside its warp and a
+// prefix over the warps, so equal digits keep their input order.
+#include "pic_internal.cuh"
+#include "pic_kernels.cuh"
+
+namespace pic {
+
+constexpr int kSortBlock = 256;
+constexpr int kSortRounds = 16;
+constexpr int kSortTile = kSortBlock * kSortRounds;  // 4096 elements per tile
+constexpr int kWarps = kSortBlock / 32;
+
+static long long sort_blocks(long long n_max) { return (n_max + kSortTile - 1) / kSortTile > 0 ? (n_max + kSortTile - 1) / kSortTile : 1; }
+long long sort_hist_entries(long long n_max) { return 256 * sort_blocks(n_max); }
+
+__global__ void __launch_bounds__(kSortBlock) k_radix_hist(const unsigned long long* __restrict__ keys,
+                                                           const unsigned long long* n_dev, long long n_max, int shift,
+                                                           uint32_t* __restrict__ hist, int nblocks) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const long long n = min((long long)*n_dev, n_max);
+  const long long t0 = (long long)blockIdx.x * kSortTile;
+  const long long t1 = min(t0 + kSortTile, n);
+  for (long long i = t0 + threadIdx.x; i < t1; i += kSortBlock) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+  __syncthreads();
+  hist[(long long)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// One block per digit: exclusive scan of that digit's row over the tiles, and
+// the digit total.
+__global__ void __launch_bounds__(kSortBlock) k_radix_scan_rows(uint32_t* __restrict__ hist, int nblocks,
+                                                                uint32_t* __restrict__ digit_tot) {
+  __shared__ uint32_t part[kSortBlock];
+  uint32_t* row = hist + (long long)blockIdx.x * nblocks;
+  const int per = (nblocks + kSortBlock - 1) / kSortBlock;
+  const int b0 = threadIdx.x * per;
+  uint32_t s = 0;
+  for (int b = b0; b < min(b0 + per, nblocks); ++b) s += row[b];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  // inclusive scan of the partials (Hillis-Steele)
+  for (int o = 1; o < kSortBlock; o <<= 1) {
+    const uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+  for (int b = b0; b < min(b0 + per, nblocks); ++b) {
+    const uint32_t v = row[b];
+    row[b] = run;
+    run += v;
+  }
+  if (threadIdx.x == kSortBlock - 1) digit_tot[blockIdx.x] = part[kSortBlock - 1];
+}
+
+__global__ void __launch_bounds__(kSortBlock) k_radix_scatter(const unsigned long long* __restrict__ kin,
+                                                              const uint32_t* __restrict__ vin,
+                                                              unsigned long long* __restrict__ kout,
+                                                              uint32_t* __restrict__ vout, const unsigned long long* n_dev,
+                                                              long long n_max, int shift, const uint32_t* __restrict__ hist,
+                                                              int nblocks, const uint32_t* __restrict__ digit_tot) {
+  __shared__ uint32_t base[256];           // global start of each digit for this tile
+  __shared__ uint32_t wc[kWarps][256];     // per-warp digit counts -> offsets
+  __shared__ uint32_t tot[256];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  // digit offsets: exclusive scan of the digit totals (256 entries)
+  tot[t] = digit_tot[t];
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    const uint32_t v = t >= o ? tot[t - o] : 0u;
+    __syncthreads();
+    tot[t] += v;
+    __syncthreads();
+  }
+  base[t] = (t ? tot[t - 1] : 0u) + hist[(long long)t * nblocks + blockIdx.x];
+  for (int ww = 0; ww < kWarps; ++ww) wc[ww][t] = 0;
+  __syncthreads();
+  const long long n = min((long long)*n_dev, n_max);
+  const long long t0 = (long long)blockIdx.x * kSortTile;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < kSortRounds; ++r) {
+    const long long i = t0 + (long long)r * kSortBlock + t;
+    const bool valid = i < n;
+    unsigned long long key = 0;
+    uint32_t val = 0;
+    uint32_t d = 256;
+    if (valid) {
+      key = kin[i];
+      val = vin[i];
+      d = (uint32_t)((key >> shift) & 255u);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t lrank = __popc(peers & lt);
+    if (valid && lrank == 0) wc[w][d] = __popc(peers);
+    __syncthreads();
+    {
+      // thread t owns digit t: turn per-warp counts into offsets, advance base
+      uint32_t s = base[t];
+      for (int ww = 0; ww < kWarps; ++ww) {
+        const uint32_t c = wc[ww][t];
+        wc[ww][t] = s;
+        s += c;
+      }
+      base[t] = s;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = wc[w][d] + lrank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    for (int ww = 0; ww < kWarps; ++ww) wc[ww][t] = 0;
+    __syncthreads();
+  }
+}
+
+int radix_sort_pairs(const SortBuffers& b, const unsigned long long* n_dev, int bit0, int bit1, cudaStream_t s) {
+  const int nblocks = (int)sort_blocks(b.n_max);
+  int src = 0;
+  for (int shift = bit0; shift < bit1; shift += 8) {
+    const unsigned long long* kin = src ? b.kb : b.ka;
+    const uint32_t* vin = src ? b.vb : b.va;
+    unsigned long long* kout = src ? b.ka : b.kb;
+    uint32_t* vout = src ? b.va : b.vb;
+    PIC_LAUNCH(nblocks, kSortBlock, 0, s, k_radix_hist)(kin, n_dev, b.n_max, shift, b.hist, nblocks);
+    PIC_LAUNCH(256, kSortBlock, 0, s, k_radix_scan_rows)(b.hist, nblocks, b.digit_tot);
+    PIC_LAUNCH(nblocks, kSortBlock, 0, s, k_radix_scatter)(kin, vin, kout, vout, n_dev, b.n_max, shift, b.hist, nblocks,
+                                                   b.digit_tot);
+    src ^= 1;
+  }
+  return src;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan int32 -> int64 (three kernels: tile sums, scan of sums, tiles)
+// ---------------------------------------------------------------------------
+constexpr int kScanBlock = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+size_t scan_temp_bytes(long long n) {
+  const long long tiles = (n + kScanTile - 1) / kScanTile + 1;
+  return (size_t)tiles * sizeof(long long);
+}
+
+__device__ __forceinline__ long long block_incl_scan(long long v, long long* sm) {
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 1; o < kScanBlock; o <<= 1) {
+    const long long a = threadIdx.x >= o ? sm[threadIdx.x - o] : 0;
+    __syncthreads();
+    sm[threadIdx.x] += a;
+    __syncthreads();
+  }
+  return sm[threadIdx.x];
+}
+
+__global__ void k_scan_tiles(const int32_t* __restrict__ c, long long n, long long* __restrict__ tile_sum) {
+  __shared__ long long sm[kScanBlock];
+  const long long t0 = (long long)blockIdx.x * kScanTile;
+  long long s = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    const long long i = t0 + (long long)threadIdx.x * kScanItems + k;
+    if (i < n) s += c[i];
+  }
+  const long long inc = block_incl_scan(s, sm);
+  if (threadIdx.x == kScanBlock - 1) tile_sum[blockIdx.x] = inc;
+}
+
+__global__ void k_scan_sums(long long* tile_sum, int ntiles) {
+  __shared__ long long sm[kScanBlock];
+  long long carry = 0;
+  for (int b0 = 0; b0 < ntiles; b0 += kScanBlock) {
+    const int i = b0 + threadIdx.x;
+    const long long v = i < ntiles ? tile_sum[i] : 0;
+    const long long inc = block_incl_scan(v, sm);
+    if (i < ntiles) tile_sum[i] = carry + inc - v;  // exclusive
+    __syncthreads();
+    carry += sm[kScanBlock - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tile_sum[ntiles] = carry;
+}
+
+__global__ void k_scan_apply(const int32_t* __restrict__ c, long long n, const long long* __restrict__ tile_sum,
+                             long long* __restrict__ out, int ntiles) {
+  __shared__ long long sm[kScanBlock];
+  const long long t0 = (long long)blockIdx.x * kScanTile;
+  long long loc[kScanItems];
+  long long s = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    const long long i = t0 + (long long)threadIdx.x * kScanItems + k;
+    loc[k] = s;
+    if (i < n) s += c[i];
+  }
+  const long long inc = block_incl_scan(s, sm);
+  const long long off = tile_sum[blockIdx.x] + inc - s;
+  for (int k = 0; k < kScanItems; ++k) {
+    const long long i = t0 + (long long)threadIdx.x * kScanItems + k;
+    if (i < n) out[i] = off + loc[k];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_sum[ntiles];
+}
+
+void exclusive_scan_i32_i64(const int32_t* counts, long long n, long long* out, void* temp, cudaStream_t s) {
+  const int ntiles = (int)((n + kScanTile - 1) / kScanTile);
+  long long* ts = (long long*)temp;
+  if (ntiles == 0) {
+    cudaMemsetAsync(out, 0, sizeof(long long), s);
+    return;
+  }
+  PIC_LAUNCH(ntiles, kScanBlock, 0, s, k_scan_tiles)(counts, n, ts);
+  PIC_LAUNCH(1, kScanBlock, 0, s, k_scan_sums)(ts, ntiles);
+  PIC_LAUNCH(ntiles, kScanBlock, 0, s, k_scan_apply)(counts, n, ts, out, ntiles);
+}
+
+}  // namespace pic

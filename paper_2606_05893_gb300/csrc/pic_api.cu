@@ -1,0 +1,1182 @@
+// pic_api.cu -- C ABI and host runtime of the GB300 PIC/MCC library.
+//
+// Each instance owns: two ping-pong particle stores per species (FP64 or MIXED
+// layout), the node grids (rho, phi, node field E), per-cell neutral counts, the
+// ionization event/candidate buffers with per-cell list heads, the sort
+// buffers and the Poisson solver. Host state is limited to configuration, the
+// injection carry accumulators and which buffer of each species is current.
+// All device work goes to the caller's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "pic_internal.cuh"
+#include "pic_kernels.cuh"
+#include "pic_solver.cuh"
+
+using namespace pic;
+
+namespace pic {
+unsigned long long g_launches = 0;
+}
+
+namespace {
+
+constexpr int kPushBlocksPerSM = 8;
+constexpr int kPhases = PIC_NPHASES;
+
+// CUDA-event timing of the phases of a step on the handle's stream.
+struct PhaseTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  struct Mark {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  double ms[kPhases] = {0};
+  long long count[kPhases] = {0};
+  int open_phase = -1;
+  cudaEvent_t open_ev = nullptr;
+
+  cudaEvent_t next() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void begin(int phase, cudaStream_t s) {
+    if (!on) return;
+    open_phase = phase;
+    open_ev = next();
+    cudaEventRecord(open_ev, s);
+  }
+  void end(cudaStream_t s) {
+    if (!on || open_phase < 0) return;
+    cudaEvent_t b = next();
+    cudaEventRecord(b, s);
+    marks.push_back(Mark{open_phase, open_ev, b});
+    open_phase = -1;
+  }
+  void collect() {
+    if (!on || marks.empty()) {
+      used = 0;
+      return;
+    }
+    cudaEventSynchronize(marks.back().b);
+    for (auto& m : marks) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess) {
+        ms[m.phase] += t;
+        count[m.phase] += 1;
+      }
+    }
+    marks.clear();
+    used = 0;
+  }
+  void reset() {
+    for (int i = 0; i < kPhases; ++i) {
+      ms[i] = 0;
+      count[i] = 0;
+    }
+    marks.clear();
+    used = 0;
+  }
+  void release() {
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+};
+
+struct HostXsec {
+  pic_xsec c;
+  std::vector<double> E, sig;
+  double sig_max = 0.0;
+  // device tables
+  double *dE = nullptr, *dsig = nullptr;
+  float *dEf = nullptr, *dsigf = nullptr;
+  int* dbucket = nullptr;
+  XsDev dev{};
+};
+
+struct Source {
+  int species;
+  double cx, cy, R, flux, T;
+  double acc;
+};
+
+struct Instance {
+  pic_instance_cfg cfg{};
+  std::vector<pic_species> species;
+  std::vector<HostXsec> xs;
+  Grid g{};
+  int nsp = 0;
+  bool mixed = false;
+  DevCounters* cnt = nullptr;
+  DevCounters* host_cnt = nullptr;  // pinned mirror
+  Store64 s64[kMaxSpecies][2]{};
+  StoreMx smx[kMaxSpecies][2]{};
+  void* mem[kMaxSpecies][2]{};
+  int cur[kMaxSpecies]{};
+  long long cap[kMaxSpecies]{};
+  double* rho64 = nullptr;
+  float* rho32 = nullptr;
+  double* phi = nullptr;
+  double4_32a* E64 = nullptr;
+  float4* E32 = nullptr;
+  int32_t* ncount[kMaxSpecies]{};
+  // ionization bookkeeping
+  int ion_ch = -1;  // index into xs of the ionization channel
+  int ev_cap = 0, cand_cap = 0;
+  Event* ev = nullptr;
+  Cand* cand = nullptr;
+  int32_t* ev_head = nullptr;
+  int32_t* cand_head = nullptr;
+  uint32_t* ion_log = nullptr;
+  SortBuffers evsort{};
+  // cell sort
+  SortBuffers csort{};
+  int32_t* cell_count = nullptr;
+  long long* cell_start[kMaxSpecies]{};
+  void* scan_tmp = nullptr;
+  double* red = nullptr;  // reduction scratch (moments)
+  Solver solver;
+  std::vector<Source> sources;
+  uint32_t step = 0;
+  SolveResult last{0, 0.0, true};
+  double bg_density = 0.0;
+  bool sorted_once = false;
+  PhaseTimer timer;
+  double* stage_x = nullptr;  // device staging of pic_inject_particles
+  double* stage_v = nullptr;
+  long long stage_cap = 0;
+};
+
+}  // namespace
+
+struct pic_handle {
+  std::vector<Instance*> inst;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  bool dead = false;
+  int sticky = 0;  // sticky non-fatal status bits (ENOCONV)
+};
+
+namespace {
+
+static thread_local std::string g_static_err;
+
+pic_status fail(pic_handle* h, pic_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  else g_static_err = buf;
+  return st;
+}
+
+#define CK(h, call)                                                                             \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) return fail(h, PIC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
+
+int bits_for(unsigned long long v) {
+  int b = 0;
+  while (b < 64 && (v >> b) != 0) ++b;
+  return b;
+}
+
+void free_instance(Instance* I) {
+  if (!I) return;
+  for (int s = 0; s < kMaxSpecies; ++s) {
+    for (int b = 0; b < 2; ++b) cudaFree(I->mem[s][b]);
+    cudaFree(I->ncount[s]);
+    cudaFree(I->cell_start[s]);
+  }
+  for (auto& x : I->xs) {
+    cudaFree(x.dE);
+    cudaFree(x.dsig);
+    cudaFree(x.dEf);
+    cudaFree(x.dsigf);
+    cudaFree(x.dbucket);
+  }
+  cudaFree(I->cnt);
+  if (I->host_cnt) cudaFreeHost(I->host_cnt);
+  cudaFree(I->rho64);
+  cudaFree(I->rho32);
+  cudaFree(I->phi);
+  cudaFree(I->E64);
+  cudaFree(I->E32);
+  cudaFree(I->ev);
+  cudaFree(I->cand);
+  cudaFree(I->ev_head);
+  cudaFree(I->cand_head);
+  cudaFree(I->ion_log);
+  cudaFree(I->evsort.ka);
+  cudaFree(I->evsort.kb);
+  cudaFree(I->evsort.va);
+  cudaFree(I->evsort.vb);
+  cudaFree(I->evsort.hist);
+  cudaFree(I->evsort.digit_tot);
+  cudaFree(I->csort.ka);
+  cudaFree(I->csort.kb);
+  cudaFree(I->csort.va);
+  cudaFree(I->csort.vb);
+  cudaFree(I->csort.hist);
+  cudaFree(I->csort.digit_tot);
+  cudaFree(I->cell_count);
+  cudaFree(I->scan_tmp);
+  cudaFree(I->red);
+  cudaFree(I->stage_x);
+  cudaFree(I->stage_v);
+  I->timer.release();
+  I->solver.release();
+  delete I;
+}
+
+cudaError_t alloc_sort(SortBuffers& b, long long n_max) {
+  b.n_max = n_max;
+  cudaError_t e;
+  if ((e = dalloc(&b.ka, n_max))) return e;
+  if ((e = dalloc(&b.kb, n_max))) return e;
+  if ((e = dalloc(&b.va, n_max))) return e;
+  if ((e = dalloc(&b.vb, n_max))) return e;
+  if ((e = dalloc(&b.hist, sort_hist_entries(n_max)))) return e;
+  if ((e = dalloc(&b.digit_tot, 256))) return e;
+  return cudaSuccess;
+}
+
+pic_status validate(pic_handle* h, const pic_instance_cfg& c, int idx) {
+  if (c.nx < 1 || c.ny < 1 || c.nz < 2) return fail(h, PIC_EINVAL, "instance %d: grid must have nx, ny >= 1, nz >= 2", idx);
+  const double ncell = (double)c.nx * c.ny * c.nz;
+  if (ncell > 2.0e9) return fail(h, PIC_EINVAL, "instance %d: grid too large", idx);
+  if (!(c.h > 0) || !(c.dt > 0)) return fail(h, PIC_EINVAL, "instance %d: h and dt must be positive", idx);
+  if (c.nspecies < 1 || c.nspecies > PIC_MAX_SPECIES || !c.species)
+    return fail(h, PIC_EINVAL, "instance %d: nspecies must be 1..%d", idx, PIC_MAX_SPECIES);
+  if (c.nxsec < 0 || c.nxsec > PIC_MAX_XSEC || (c.nxsec > 0 && !c.xsec))
+    return fail(h, PIC_EINVAL, "instance %d: nxsec must be 0..%d", idx, PIC_MAX_XSEC);
+  if (c.precision != PIC_FP64 && c.precision != PIC_MIXED) return fail(h, PIC_EINVAL, "instance %d: bad precision", idx);
+  if (c.warm_start != PIC_WARM_PREV && c.warm_start != PIC_WARM_ZERO)
+    return fail(h, PIC_EINVAL, "instance %d: bad warm_start", idx);
+  if (!(c.cg_rtol > 0) || c.cg_maxit < 1) return fail(h, PIC_EINVAL, "instance %d: cg_rtol > 0 and cg_maxit >= 1 required", idx);
+  if (c.sort_interval < 0) return fail(h, PIC_EINVAL, "instance %d: sort_interval >= 0 required", idx);
+  for (int s = 0; s < c.nspecies; ++s) {
+    const pic_species& p = c.species[s];
+    if (!(p.mass_kg > 0) || !(p.weight > 0) || p.capacity < 1 || p.role < 0 || p.role > 2)
+      return fail(h, PIC_EINVAL, "instance %d species %d: mass, weight > 0, capacity >= 1, role 0..2", idx, s);
+    if (p.capacity > 0x7FFFFFFFLL) return fail(h, PIC_EINVAL, "instance %d species %d: capacity above 2^31-1", idx, s);
+    if (p.role == PIC_NEUTRAL && p.charge_C != 0.0)
+      return fail(h, PIC_EINVAL, "instance %d species %d: neutral species must have zero charge", idx, s);
+  }
+  int nion = 0;
+  for (int x = 0; x < c.nxsec; ++x) {
+    const pic_xsec& X = c.xsec[x];
+    if (X.kind != PIC_XS_IONIZATION && X.kind != PIC_XS_ELASTIC) return fail(h, PIC_EINVAL, "xsec %d: bad kind", x);
+    if (X.projectile < 0 || X.projectile >= c.nspecies || X.target < 0 || X.target >= c.nspecies)
+      return fail(h, PIC_EINVAL, "xsec %d: bad species index", x);
+    if (c.species[X.projectile].role != PIC_ELECTRON || c.species[X.target].role != PIC_NEUTRAL)
+      return fail(h, PIC_EINVAL, "xsec %d: projectile must be an electron species, target a neutral species", x);
+    if (X.n < 1 || !X.E_eV || !X.sigma_m2) return fail(h, PIC_EINVAL, "xsec %d: empty table", x);
+    for (int i = 0; i < X.n; ++i) {
+      if (!(X.sigma_m2[i] >= 0) || !std::isfinite(X.sigma_m2[i])) return fail(h, PIC_EINVAL, "xsec %d: sigma must be >= 0", x);
+      if (i > 0 && !(X.E_eV[i] > X.E_eV[i - 1])) return fail(h, PIC_EINVAL, "xsec %d: E_eV must increase", x);
+    }
+    if (X.kind == PIC_XS_IONIZATION) {
+      ++nion;
+      if (X.product < 0 || X.product >= c.nspecies || c.species[X.product].role != PIC_ION)
+        return fail(h, PIC_EINVAL, "xsec %d: ionization product must be an ion species", x);
+      const double w = c.species[X.projectile].weight;
+      if (c.species[X.target].weight != w || c.species[X.product].weight != w)
+        return fail(h, PIC_EINVAL, "xsec %d: ionization needs equal weights of projectile, target, product", x);
+      if (!(X.threshold_eV > 0)) return fail(h, PIC_EINVAL, "xsec %d: ionization threshold must be > 0", x);
+    }
+  }
+  if (nion > 1) return fail(h, PIC_EINVAL, "instance %d: at most one ionization channel is supported", idx);
+  return PIC_OK;
+}
+
+pic_status build_xsec(pic_handle* h, HostXsec& X) {
+  const int n = X.c.n;
+  X.sig_max = 0.0;
+  for (double s : X.sig) X.sig_max = std::max(X.sig_max, s);
+  CK(h, dalloc(&X.dE, n));
+  CK(h, dalloc(&X.dsig, n));
+  CK(h, dalloc(&X.dEf, n));
+  CK(h, dalloc(&X.dsigf, n));
+  CK(h, dalloc(&X.dbucket, kXsBuckets));
+  std::vector<float> Ef(X.E.begin(), X.E.end()), sf(X.sig.begin(), X.sig.end());
+  CK(h, cudaMemcpy(X.dE, X.E.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(X.dsig, X.sig.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(X.dEf, Ef.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(X.dsigf, sf.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+  std::vector<int> bucket(kXsBuckets, 0);
+  float lnE0 = 0.f, inv = 0.f;
+  if (n >= 2 && X.E[0] > 0) {
+    lnE0 = (float)std::log(X.E[0]);
+    const double span = std::log(X.E[n - 1]) - std::log(X.E[0]);
+    inv = span > 0 ? (float)(kXsBuckets / span) : 0.f;
+    int i = 0;
+    for (int b = 0; b < kXsBuckets; ++b) {
+      const double lo = X.E[0] * std::exp(b * span / kXsBuckets);
+      while (i + 1 < n - 1 && X.E[i + 1] <= lo) ++i;
+      bucket[b] = std::max(0, i - 1);
+    }
+  }
+  CK(h, cudaMemcpy(X.dbucket, bucket.data(), sizeof(int) * kXsBuckets, cudaMemcpyHostToDevice));
+  X.dev.kind = X.c.kind;
+  X.dev.projectile = X.c.projectile;
+  X.dev.target = X.c.target;
+  X.dev.product = X.c.product;
+  X.dev.n = n;
+  X.dev.thr = X.c.threshold_eV;
+  X.dev.thr_f = (float)X.c.threshold_eV;
+  X.dev.E = X.dE;
+  X.dev.sig = X.dsig;
+  X.dev.Ef = X.dEf;
+  X.dev.sigf = X.dsigf;
+  X.dev.bucket = X.dbucket;
+  X.dev.lnE0 = lnE0;
+  X.dev.inv_dln = inv;
+  return PIC_OK;
+}
+
+pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** out) {
+  Instance* I = new Instance();
+  *out = I;
+  I->cfg = c;
+  I->nsp = c.nspecies;
+  I->species.assign(c.species, c.species + c.nspecies);
+  I->cfg.species = nullptr;
+  I->cfg.xsec = nullptr;
+  I->mixed = c.precision == PIC_MIXED;
+  Grid& g = I->g;
+  g.nx = c.nx;
+  g.ny = c.ny;
+  g.nz = c.nz;
+  g.h = c.h;
+  g.inv_h = 1.0 / c.h;
+  g.dt = c.dt;
+  g.Lx = c.nx * c.h;
+  g.Ly = c.ny * c.h;
+  g.Lz = c.nz * c.h;
+  g.inv_Lx = 1.0 / g.Lx;
+  g.inv_Ly = 1.0 / g.Ly;
+  g.phi_c = c.phi_cathode_V;
+  g.phi_a = c.phi_anode_V;
+  g.h_f = (float)c.h;
+  g.inv_h_f = (float)(1.0 / c.h);
+  g.dt_over_h_f = (float)(c.dt / c.h);
+  g.nplane = (long long)c.nx * c.ny;
+  g.ncell = g.nplane * c.nz;
+  g.nnode = g.nplane * (c.nz + 1);
+
+  for (int x = 0; x < c.nxsec; ++x) {
+    HostXsec X;
+    X.c = c.xsec[x];
+    X.E.assign(c.xsec[x].E_eV, c.xsec[x].E_eV + c.xsec[x].n);
+    X.sig.assign(c.xsec[x].sigma_m2, c.xsec[x].sigma_m2 + c.xsec[x].n);
+    X.c.E_eV = nullptr;
+    X.c.sigma_m2 = nullptr;
+    I->xs.push_back(X);
+    if (X.c.kind == PIC_XS_IONIZATION) I->ion_ch = x;
+  }
+  for (auto& X : I->xs) {
+    pic_status st = build_xsec(h, X);
+    if (st != PIC_OK) return st;
+  }
+
+  CK(h, dalloc(&I->cnt, 1));
+  CK(h, cudaMemset(I->cnt, 0, sizeof(DevCounters)));
+  CK(h, cudaMallocHost((void**)&I->host_cnt, sizeof(DevCounters)));
+  memset(I->host_cnt, 0, sizeof(DevCounters));
+
+  long long maxcap = 1;
+  for (int s = 0; s < I->nsp; ++s) {
+    const long long cap = I->species[s].capacity;
+    I->cap[s] = cap;
+    maxcap = std::max(maxcap, cap);
+    for (int b = 0; b < 2; ++b) {
+      if (!I->mixed) {
+        const size_t bytes = (size_t)cap * (6 * sizeof(double) + sizeof(uint32_t));
+        CK(h, cudaMalloc(&I->mem[s][b], bytes));
+        char* p = (char*)I->mem[s][b];
+        Store64& S = I->s64[s][b];
+        S.x = (double*)p;
+        S.y = S.x + cap;
+        S.z = S.y + cap;
+        S.vx = S.z + cap;
+        S.vy = S.vx + cap;
+        S.vz = S.vy + cap;
+        S.pid = (uint32_t*)(S.vz + cap);
+      } else {
+        const size_t bytes = (size_t)cap * (sizeof(int32_t) + 6 * sizeof(float) + sizeof(uint32_t));
+        CK(h, cudaMalloc(&I->mem[s][b], bytes));
+        char* p = (char*)I->mem[s][b];
+        StoreMx& S = I->smx[s][b];
+        S.cell = (int32_t*)p;
+        S.ox = (float*)(S.cell + cap);
+        S.oy = S.ox + cap;
+        S.oz = S.oy + cap;
+        S.vx = S.oz + cap;
+        S.vy = S.vx + cap;
+        S.vz = S.vy + cap;
+        S.pid = (uint32_t*)(S.vz + cap);
+      }
+    }
+    if (I->species[s].role == PIC_NEUTRAL) CK(h, dalloc(&I->ncount[s], g.ncell));
+    CK(h, dalloc(&I->cell_start[s], g.ncell + 1));
+    CK(h, cudaMemset(I->cell_start[s], 0, sizeof(long long) * (g.ncell + 1)));
+  }
+  if (!I->mixed) {
+    CK(h, dalloc(&I->rho64, g.nnode));
+    CK(h, dalloc(&I->E64, g.nnode));
+  } else {
+    CK(h, dalloc(&I->rho32, g.nnode));
+    CK(h, dalloc(&I->E32, g.nnode));
+  }
+  CK(h, dalloc(&I->phi, g.nnode));
+  CK(h, cudaMemset(I->phi, 0, sizeof(double) * g.nnode));
+
+  // events: bounded by the electron population; candidates by the neutral population
+  long long ecap = 1, ncap = 1;
+  for (int s = 0; s < I->nsp; ++s) {
+    if (I->species[s].role == PIC_ELECTRON) ecap = std::max(ecap, I->cap[s]);
+    if (I->species[s].role == PIC_NEUTRAL) ncap = std::max(ncap, I->cap[s]);
+  }
+  if (I->ion_ch >= 0) {
+    I->ev_cap = (int)std::min<long long>(std::max<long long>(ecap / 16, 4096), 1 << 24);
+    I->cand_cap = (int)std::min<long long>(std::max<long long>(ncap / 4, 16384), 1 << 26);
+    CK(h, dalloc(&I->ev, I->ev_cap));
+    CK(h, dalloc(&I->cand, I->cand_cap));
+    CK(h, dalloc(&I->ev_head, g.ncell));
+    CK(h, dalloc(&I->cand_head, g.ncell));
+    CK(h, cudaMemset(I->ev_head, 0xFF, sizeof(int32_t) * g.ncell));
+    CK(h, cudaMemset(I->cand_head, 0xFF, sizeof(int32_t) * g.ncell));
+    CK(h, dalloc(&I->ion_log, 3 * (size_t)I->ev_cap));
+    if (alloc_sort(I->evsort, I->ev_cap)) return fail(h, PIC_ENOMEM, "event sort buffers");
+  }
+  if (alloc_sort(I->csort, maxcap)) return fail(h, PIC_ENOMEM, "sort buffers");
+  CK(h, dalloc(&I->cell_count, g.ncell));
+  CK(h, cudaMalloc(&I->scan_tmp, scan_temp_bytes(g.ncell)));
+  CK(h, dalloc(&I->red, 64));
+
+  cudaError_t se = I->solver.init(c.nx, c.ny, c.nz, c.precision == PIC_MIXED ? 1 : 0);
+  if (se != cudaSuccess) return fail(h, PIC_ENOMEM, "solver allocation: %s", cudaGetErrorString(se));
+  return PIC_OK;
+}
+
+template <class S>
+S store_of(Instance* I, int s, int b);
+template <>
+Store64 store_of<Store64>(Instance* I, int s, int b) {
+  return I->s64[s][b];
+}
+template <>
+StoreMx store_of<StoreMx>(Instance* I, int s, int b) {
+  return I->smx[s][b];
+}
+
+McArgs mc_args(Instance* I, int proj) {
+  McArgs m{};
+  const double inv_h3 = 1.0 / (I->g.h * I->g.h * I->g.h);
+  for (size_t x = 0; x < I->xs.size(); ++x) {
+    const HostXsec& X = I->xs[x];
+    if (X.c.projectile != proj || m.nch >= kMaxXsec) continue;
+    const int a = m.nch++;
+    m.ch[a] = X.dev;
+    m.ncount[a] = I->ncount[X.c.target];
+    m.dens[a] = I->species[X.c.target].weight * inv_h3;
+    const double bd = I->bg_density > 0 ? I->bg_density : m.dens[a];
+    m.bound_f[a] = (float)(X.sig_max * bd * 1.0001);
+  }
+  m.half_m_over_e = 0.5 * I->species[proj].mass_kg / kQe;
+  m.mass = I->species[proj].mass_kg;
+  m.key = make_uint2((uint32_t)I->cfg.seed, (uint32_t)(I->cfg.seed >> 32));
+  m.step = I->step;
+  m.bg_mode = I->bg_density > 0 ? 1 : 0;
+  m.bg_density = I->bg_density;
+  return m;
+}
+
+// a2: sort every species by (cell, pid)
+template <class S>
+pic_status sort_instance(pic_handle* h, Instance* I) {
+  cudaStream_t st = h->stream;
+  CK(h, cudaMemcpyAsync(I->host_cnt, I->cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  const int pid_bits = std::max(1, bits_for(I->host_cnt->next_pid));
+  const int cell_bits = bits_for((unsigned long long)I->g.ncell);
+  const int key_bits = std::min(64, cell_bits + pid_bits);
+  for (int s = 0; s < I->nsp; ++s) {
+    const int c = I->cur[s];
+    unsigned long long* ndev = &I->cnt->n[c][s];
+    CK(h, cudaMemsetAsync(I->cell_count, 0, sizeof(int32_t) * I->g.ncell, st));
+    launch_cell_keys<S>(I->g, store_of<S>(I, s, c), I->cap[s], ndev, pid_bits, I->csort.ka, I->csort.va,
+                        I->cell_count, st);
+    SortBuffers b = I->csort;
+    b.n_max = I->cap[s];
+    const int where = radix_sort_pairs(b, ndev, 0, ((key_bits + 7) / 8) * 8, st);
+    const uint32_t* perm = where ? b.vb : b.va;
+    launch_gather<S>(store_of<S>(I, s, c), store_of<S>(I, s, c ^ 1), perm, ndev, I->cap[s], st);
+    exclusive_scan_i32_i64(I->cell_count, I->g.ncell, I->cell_start[s], I->scan_tmp, st);
+    launch_sort_commit(I->cnt, c, s, st);
+    I->cur[s] = c ^ 1;
+  }
+  I->sorted_once = true;
+  CK(h, cudaGetLastError());
+  return PIC_OK;
+}
+
+template <class S>
+pic_status step_instance(pic_handle* h, Instance* I) {
+  cudaStream_t st = h->stream;
+  const Grid& g = I->g;
+  const uint2 key = make_uint2((uint32_t)I->cfg.seed, (uint32_t)(I->cfg.seed >> 32));
+  const int blocks = sm_count() * kPushBlocksPerSM;
+
+  PhaseTimer& T = I->timer;
+  // a1 injection: integer counts from the carry accumulators (host)
+  T.begin(PIC_PH_INJECT, st);
+  {
+    InjectArgs<S> a{};
+    InjectCommit cm{};
+    a.g = g;
+    a.cnt = I->cnt;
+    a.key = key;
+    a.step = I->step;
+    cm.nsp = I->nsp;
+    for (int s = 0; s < I->nsp; ++s) {
+      a.st[s] = store_of<S>(I, s, I->cur[s]);
+      a.cur[s] = I->cur[s];
+      a.cap[s] = I->cap[s];
+      cm.cur[s] = I->cur[s];
+      cm.cap[s] = I->cap[s];
+    }
+    long long total = 0;
+    long long per_species[kMaxSpecies] = {0};
+    int q = 0;
+    for (auto& src : I->sources) {
+      const pic_species& sp = I->species[src.species];
+      const double mu = src.flux * kPi * src.R * src.R * g.dt / sp.weight;
+      src.acc += mu;
+      const double nf = std::floor(src.acc);
+      src.acc -= nf;
+      const long long n = (long long)nf;
+      a.src[q].species = src.species;
+      a.src[q].cx = src.cx;
+      a.src[q].cy = src.cy;
+      a.src[q].R = src.R;
+      a.src[q].sig = std::sqrt(kKB * src.T / sp.mass_kg);
+      a.src_first[q] = total;
+      a.species_offset[q] = per_species[src.species];
+      per_species[src.species] += n;
+      total += n;
+      ++q;
+    }
+    a.nsrc = q;
+    a.src_first[q] = total;
+    a.total = total;
+    if (total > 0) {
+      for (int s = 0; s < I->nsp; ++s) cm.add[s] = per_species[s];
+      cm.total = total;
+      launch_inject<S>(a, (int)std::min<long long>((total + 255) / 256, blocks), st);
+      launch_inject_commit(I->cnt, cm, st);
+    }
+  }
+  T.end(st);
+
+  // a2 cell sort
+  if (I->cfg.sort_interval > 0 && I->step % (uint32_t)I->cfg.sort_interval == 0) {
+    T.begin(PIC_PH_SORT, st);
+    pic_status ps = sort_instance<S>(h, I);
+    if (ps != PIC_OK) return ps;
+    T.end(st);
+  }
+
+  // a3 deposit
+  T.begin(PIC_PH_DEPOSIT, st);
+  if (I->mixed)
+    launch_fill32(I->rho32, g.nnode, (float)I->cfg.rho_background, st);
+  else
+    launch_fill64(I->rho64, g.nnode, I->cfg.rho_background, st);
+  for (int s = 0; s < I->nsp; ++s) {
+    DepositArgs<S> d{};
+    d.g = g;
+    d.cnt = I->cnt;
+    d.st = store_of<S>(I, s, I->cur[s]);
+    d.cur = I->cur[s];
+    d.species = s;
+    d.neutral = I->species[s].role == PIC_NEUTRAL;
+    d.qw_h3 = I->species[s].charge_C * I->species[s].weight / (g.h * g.h * g.h);
+    d.rho64 = I->rho64;
+    d.rho32 = I->rho32;
+    d.ncount = I->ncount[s];
+    if (d.neutral) CK(h, cudaMemsetAsync(I->ncount[s], 0, sizeof(int32_t) * g.ncell, st));
+    if (!d.neutral && d.qw_h3 == 0.0) continue;
+    launch_deposit<S>(d, blocks, st);
+  }
+
+  T.end(st);
+  // a4 Poisson solve
+  T.begin(PIC_PH_SOLVE, st);
+  launch_rhs(g, I->rho64, I->rho32, I->solver.b, st);
+  double* x = I->phi + g.nplane;
+  if (I->cfg.warm_start == PIC_WARM_ZERO) CK(h, cudaMemsetAsync(x, 0, sizeof(double) * I->solver.n, st));
+  I->last = I->solver.solve(x, I->cfg.cg_rtol, I->cfg.cg_maxit, st);
+  if (!I->last.converged) h->sticky |= 1;
+  T.end(st);
+  // a5 node field
+  T.begin(PIC_PH_EFIELD, st);
+  if (I->mixed)
+    launch_efield32(g, I->phi, I->E32, st);
+  else
+    launch_efield64(g, I->phi, I->E64, st);
+  T.end(st);
+
+  // a6-a8 + a10 push / absorb / collide / compact: charged species first, then neutrals
+  int outb[kMaxSpecies];
+  for (int s = 0; s < I->nsp; ++s) outb[s] = I->cur[s] ^ 1;
+  launch_step_begin(I->cnt, outb, I->nsp, st);
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int s = 0; s < I->nsp; ++s) {
+      const bool neutral = I->species[s].role == PIC_NEUTRAL;
+      if ((pass == 0) == neutral) continue;
+      PushArgs<S> a{};
+      a.g = g;
+      a.cnt = I->cnt;
+      a.in = store_of<S>(I, s, I->cur[s]);
+      a.out = store_of<S>(I, s, I->cur[s] ^ 1);
+      a.cur_in = I->cur[s];
+      a.species = s;
+      a.cap = I->cap[s];
+      const pic_species& sp = I->species[s];
+      a.qm_dt = sp.charge_C / sp.mass_kg * g.dt;
+      a.qm_dt_f = (float)a.qm_dt;
+      a.mass = sp.mass_kg;
+      a.weight = sp.weight;
+      a.charge = sp.charge_C;
+      a.E64 = I->E64;
+      a.E32 = I->E32;
+      a.mc = mc_args(I, s);
+      a.mc.step = I->step;
+      a.ev = I->ev;
+      a.ev_cap = I->ev_cap;
+      a.ev_head = I->ev_head;
+      a.cand = I->cand;
+      a.cand_cap = I->cand_cap;
+      a.cand_head = I->cand_head;
+      const bool mcc = a.mc.nch > 0;
+      if (neutral && I->ion_ch < 0) {
+        a.ev_head = nullptr;
+      }
+      const int role = I->species[s].role;
+      T.begin(role == PIC_ELECTRON ? PIC_PH_PUSH_ELECTRON : (role == PIC_ION ? PIC_PH_PUSH_ION : PIC_PH_PUSH_NEUTRAL), st);
+      launch_push<S>(a, neutral ? ROLE_NEUTRAL : ROLE_ELECTRON, mcc, blocks, st);
+      T.end(st);
+    }
+  }
+
+  // a9 ionization resolve
+  if (I->ion_ch >= 0) {
+    T.begin(PIC_PH_RESOLVE, st);
+    const HostXsec& X = I->xs[I->ion_ch];
+    ResolveArgs r{};
+    r.cnt = I->cnt;
+    r.ev = I->ev;
+    r.ev_cap = I->ev_cap;
+    r.ev_head = I->ev_head;
+    r.cand = I->cand;
+    r.cand_head = I->cand_head;
+    r.sort_keys = I->evsort.ka;
+    r.sort_vals = I->evsort.va;
+    const int rb = std::min(blocks, (I->ev_cap + 255) / 256);
+    launch_resolve_rank(r, rb, st);
+    const int where = radix_sort_pairs(I->evsort, &I->cnt->ev_sort_n, 0, 40, st);
+    ApplyArgs<S> ap{};
+    ap.g = g;
+    ap.cnt = I->cnt;
+    ap.ev = I->ev;
+    ap.ev_cap = I->ev_cap;
+    ap.cand = I->cand;
+    ap.sorted_vals = where ? I->evsort.vb : I->evsort.va;
+    McArgs m = mc_args(I, X.c.projectile);
+    for (int a2 = 0; a2 < kMaxXsec; ++a2) ap.ch[a2] = m.ch[a2];
+    ap.key = key;
+    ap.step = I->step;
+    const int e_sp = X.c.projectile, n_sp = X.c.target, i_sp = X.c.product;
+    ap.e_st = store_of<S>(I, e_sp, I->cur[e_sp] ^ 1);
+    ap.e_out = I->cur[e_sp] ^ 1;
+    ap.e_species = e_sp;
+    ap.e_cap = I->cap[e_sp];
+    ap.e_mass = I->species[e_sp].mass_kg;
+    ap.n_st = store_of<S>(I, n_sp, I->cur[n_sp] ^ 1);
+    ap.i_st = store_of<S>(I, i_sp, I->cur[i_sp] ^ 1);
+    ap.i_out = I->cur[i_sp] ^ 1;
+    ap.i_species = i_sp;
+    ap.i_cap = I->cap[i_sp];
+    ap.log = I->ion_log;
+    launch_resolve_apply<S>(ap, rb, st);
+    launch_resolve_commit(I->cnt, ap.e_out, e_sp, ap.e_cap, ap.i_out, i_sp, ap.i_cap, n_sp, I->ev_cap, st);
+    launch_resolve_cleanup(r, rb, st);
+    T.end(st);
+  }
+  for (int s = 0; s < I->nsp; ++s) I->cur[s] ^= 1;
+  I->step += 1;
+  T.collect();
+  CK(h, cudaGetLastError());
+  return PIC_OK;
+}
+
+pic_status check(pic_handle* h, int inst) {
+  if (!h) return fail(nullptr, PIC_EINVAL, "null handle");
+  if (h->dead) return fail(h, PIC_ESTATE, "handle unusable after an earlier fatal error: %s", h->err.c_str());
+  if (inst < 0 || inst >= (int)h->inst.size()) return fail(h, PIC_EINVAL, "instance %d out of range", inst);
+  return PIC_OK;
+}
+
+pic_status sync_counters(pic_handle* h, Instance* I) {
+  CK(h, cudaMemcpyAsync(I->host_cnt, I->cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+long long live_count(const Instance* I, int s) {
+  return (long long)I->host_cnt->n[I->cur[s]][s] - (long long)I->host_cnt->n_tomb[s];
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* pic_version(void) { return "pic_gb300 1.0 (sm_103a)"; }
+
+const char* pic_last_error(pic_handle* h) {
+  if (!h) return g_static_err.c_str();
+  return h->err.c_str();
+}
+
+pic_status pic_create(const pic_instance_cfg* cfgs, int32_t n_instances, void* cuda_stream, pic_handle** out) {
+  if (!out) return fail(nullptr, PIC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfgs || n_instances < 1) return fail(nullptr, PIC_EINVAL, "need at least one instance configuration");
+  for (int i = 0; i < n_instances; ++i) {
+    pic_status st = validate(nullptr, cfgs[i], i);
+    if (st != PIC_OK) return st;
+  }
+  pic_handle* h = new pic_handle();
+  h->stream = (cudaStream_t)cuda_stream;
+  for (int i = 0; i < n_instances; ++i) {
+    Instance* I = nullptr;
+    pic_status st = create_instance(h, cfgs[i], &I);
+    h->inst.push_back(I);
+    if (st != PIC_OK) {
+      g_static_err = h->err;
+      for (auto* p : h->inst) free_instance(p);
+      delete h;
+      return st;
+    }
+    launch_phi_planes(I->g, I->phi, h->stream);
+  }
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    g_static_err = std::string("initialisation failed: ") + cudaGetErrorString(e);
+    for (auto* p : h->inst) free_instance(p);
+    delete h;
+    return PIC_ECUDA;
+  }
+  *out = h;
+  return PIC_OK;
+}
+
+pic_status pic_destroy(pic_handle* h) {
+  if (!h) return PIC_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  for (auto* I : h->inst) free_instance(I);
+  delete h;
+  return PIC_OK;
+}
+
+pic_status pic_inject(pic_handle* h, int32_t inst, int32_t species, double cx, double cy, double radius_m,
+                      double flux_m2s, double T_K) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  Instance* I = h->inst[inst];
+  if (species < 0 || species >= I->nsp) return fail(h, PIC_EINVAL, "species %d out of range", species);
+  if (!(radius_m > 0) || !(flux_m2s >= 0) || !(T_K >= 0) || !std::isfinite(cx) || !std::isfinite(cy))
+    return fail(h, PIC_EINVAL, "source needs radius > 0, flux >= 0, T >= 0");
+  for (size_t q = 0; q < I->sources.size(); ++q) {
+    Source& s = I->sources[q];
+    if (s.species == species && s.cx == cx && s.cy == cy && s.R == radius_m) {
+      if (flux_m2s == 0) I->sources.erase(I->sources.begin() + q);
+      else {
+        s.flux = flux_m2s;
+        s.T = T_K;
+      }
+      return PIC_OK;
+    }
+  }
+  if (flux_m2s == 0) return PIC_OK;
+  if ((int)I->sources.size() >= PIC_MAX_SOURCES) return fail(h, PIC_EINVAL, "at most %d sources", PIC_MAX_SOURCES);
+  I->sources.push_back(Source{species, cx, cy, radius_m, flux_m2s, T_K, 0.0});
+  return PIC_OK;
+}
+
+pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n, const double* x,
+                                const double* v) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  Instance* I = h->inst[inst];
+  if (species < 0 || species >= I->nsp) return fail(h, PIC_EINVAL, "species %d out of range", species);
+  if (n < 0 || (n > 0 && (!x || !v))) return fail(h, PIC_EINVAL, "bad particle arrays");
+  if (n == 0) return PIC_OK;
+  for (int64_t i = 0; i < n; ++i) {
+    const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
+    if (!(px >= 0 && px < I->g.Lx && py >= 0 && py < I->g.Ly && pz >= 0 && pz < I->g.Lz))
+      return fail(h, PIC_EINVAL, "particle %lld outside the domain", (long long)i);
+    for (int c = 0; c < 3; ++c)
+      if (!std::isfinite(v[3 * i + c])) return fail(h, PIC_EINVAL, "particle %lld has a non-finite velocity", (long long)i);
+  }
+  st = sync_counters(h, I);
+  if (st != PIC_OK) return st;
+  const long long have = (long long)I->host_cnt->n[I->cur[species]][species];
+  if (have + n > I->cap[species]) return fail(h, PIC_ECAPACITY, "species %d: %lld + %lld exceeds capacity %lld", species, have, (long long)n, I->cap[species]);
+  if ((unsigned long long)I->host_cnt->next_pid + (unsigned long long)n > 0xFFFFFFFEull)
+    return fail(h, PIC_ECAPACITY, "pid space exhausted");
+  if (n > I->stage_cap) {
+    cudaFree(I->stage_x);
+    cudaFree(I->stage_v);
+    I->stage_x = I->stage_v = nullptr;
+    I->stage_cap = 0;
+    CK(h, dalloc(&I->stage_x, 3 * (size_t)n));
+    CK(h, dalloc(&I->stage_v, 3 * (size_t)n));
+    I->stage_cap = n;
+  }
+  double* dx = I->stage_x;
+  double* dv = I->stage_v;
+  CK(h, cudaMemcpyAsync(dx, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(dv, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+  const int c = I->cur[species];
+  if (I->mixed)
+    launch_load<StoreMx>(I->g, I->smx[species][c], I->cnt, c, species, I->cap[species], dx, dv, n, h->stream);
+  else
+    launch_load<Store64>(I->g, I->s64[species][c], I->cnt, c, species, I->cap[species], dx, dv, n, h->stream);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    h->dead = true;
+    return fail(h, PIC_ECUDA, "upload failed: %s", cudaGetErrorString(e));
+  }
+  return PIC_OK;
+}
+
+pic_status pic_step(pic_handle* h, int32_t nsteps) {
+  if (!h) return fail(nullptr, PIC_EINVAL, "null handle");
+  if (h->dead) return fail(h, PIC_ESTATE, "handle unusable after an earlier fatal error: %s", h->err.c_str());
+  if (nsteps < 0) return fail(h, PIC_EINVAL, "nsteps must be >= 0");
+  h->sticky = 0;
+  for (int n = 0; n < nsteps; ++n) {
+    for (auto* I : h->inst) {
+      pic_status st = I->mixed ? step_instance<StoreMx>(h, I) : step_instance<Store64>(h, I);
+      if (st != PIC_OK) {
+        if (st == PIC_ECUDA) h->dead = true;
+        return st;
+      }
+    }
+  }
+  // device-side error flags (capacity, event overflow) of the completed steps
+  for (auto* I : h->inst) {
+    if (I->host_cnt) {
+      pic_status st = sync_counters(h, I);
+      if (st != PIC_OK) {
+        h->dead = true;
+        return st;
+      }
+      const int e = I->host_cnt->error;
+      if (e & (ERR_CAPACITY | ERR_EVENTS)) return fail(h, PIC_ECAPACITY, "store or event capacity exceeded (flags %d)", e);
+      if (e & ERR_TIMEOUT) return fail(h, PIC_ETIMEOUT, "device wait timed out");
+    }
+  }
+  if (h->sticky & 1) return fail(h, PIC_ENOCONV, "Poisson solve hit cg_maxit");
+  return PIC_OK;
+}
+
+pic_status pic_moments(pic_handle* h, int32_t inst, pic_moments_t* out) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  if (!out) return fail(h, PIC_EINVAL, "out is NULL");
+  Instance* I = h->inst[inst];
+  cudaStream_t s = h->stream;
+  CK(h, cudaMemsetAsync(I->red, 0, sizeof(double) * 64, s));
+  for (int sp = 0; sp < I->nsp; ++sp) {
+    const int c = I->cur[sp];
+    if (I->mixed) launch_kinetic<StoreMx>(I->smx[sp][c], &I->cnt->n[c][sp], I->cap[sp], I->red + sp, s);
+    else launch_kinetic<Store64>(I->s64[sp][c], &I->cnt->n[c][sp], I->cap[sp], I->red + sp, s);
+  }
+  launch_field_energy(I->g, I->phi, I->red + 16, s);
+  double red[64];
+  CK(h, cudaMemcpyAsync(red, I->red, sizeof(red), cudaMemcpyDeviceToHost, s));
+  st = sync_counters(h, I);
+  if (st != PIC_OK) return st;
+  const DevCounters& c = *I->host_cnt;
+  memset(out, 0, sizeof(*out));
+  out->step = I->step;
+  double q = 0.0;
+  for (int sp = 0; sp < I->nsp; ++sp) {
+    const pic_species& S = I->species[sp];
+    out->count[sp] = live_count(I, sp);
+    out->injected[sp] = (int64_t)c.injected[sp];
+    out->absorbed_cathode[sp] = (int64_t)c.abs_cathode[sp];
+    out->absorbed_anode[sp] = (int64_t)c.abs_anode[sp];
+    out->absorbed_energy_cathode_J[sp] = c.abs_energy_cathode[sp];
+    out->absorbed_energy_anode_J[sp] = c.abs_energy_anode[sp];
+    out->kinetic_J[sp] = 0.5 * S.mass_kg * S.weight * red[sp];
+    q += S.charge_C * S.weight * (double)out->count[sp];
+  }
+  out->ionizations = (int64_t)c.n_ion;
+  out->elastic = (int64_t)c.n_el;
+  out->suppressed = (int64_t)c.n_supp;
+  out->cg_iters = I->last.iters;
+  out->cg_resid_rel = I->last.resid_rel;
+  out->total_charge_C = q;
+  out->field_energy_J = 0.5 * kEps0 * I->g.h * red[16];
+  out->charge_to_cathode_C = c.q_cathode_step;
+  out->charge_to_anode_C = c.q_anode_step;
+  out->next_pid = c.next_pid;
+  out->error_flags = c.error;
+  for (int sp = 0; sp < I->nsp; ++sp) out->pushed[sp] = (int64_t)c.pushed[sp];
+  return PIC_OK;
+}
+
+pic_status pic_get_count(pic_handle* h, int32_t inst, int32_t species, int64_t* n) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  Instance* I = h->inst[inst];
+  if (species < 0 || species >= I->nsp || !n) return fail(h, PIC_EINVAL, "bad species or output");
+  st = sync_counters(h, I);
+  if (st != PIC_OK) return st;
+  *n = live_count(I, species);
+  return PIC_OK;
+}
+
+pic_status pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t cap, int64_t* n, uint32_t* pid,
+                             double* x, double* v) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  Instance* I = h->inst[inst];
+  if (species < 0 || species >= I->nsp || !n) return fail(h, PIC_EINVAL, "bad species or output");
+  st = sync_counters(h, I);
+  if (st != PIC_OK) return st;
+  const long long slots = (long long)I->host_cnt->n[I->cur[species]][species];
+  const long long live = live_count(I, species);
+  *n = live;
+  if (cap < live) return fail(h, PIC_EINVAL, "cap %lld below count %lld", (long long)cap, live);
+  if (slots == 0) return PIC_OK;
+  double *dx = nullptr, *dv = nullptr;
+  uint32_t* dp = nullptr;
+  CK(h, dalloc(&dx, 3 * (size_t)slots));
+  CK(h, dalloc(&dv, 3 * (size_t)slots));
+  CK(h, dalloc(&dp, (size_t)slots));
+  const int c = I->cur[species];
+  if (I->mixed) launch_download<StoreMx>(I->g, I->smx[species][c], slots, dx, dv, dp, h->stream);
+  else launch_download<Store64>(I->g, I->s64[species][c], slots, dx, dv, dp, h->stream);
+  std::vector<double> hx(3 * slots), hv(3 * slots);
+  std::vector<uint32_t> hp(slots);
+  cudaMemcpyAsync(hx.data(), dx, sizeof(double) * 3 * slots, cudaMemcpyDeviceToHost, h->stream);
+  cudaMemcpyAsync(hv.data(), dv, sizeof(double) * 3 * slots, cudaMemcpyDeviceToHost, h->stream);
+  cudaMemcpyAsync(hp.data(), dp, sizeof(uint32_t) * slots, cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  cudaFree(dx);
+  cudaFree(dv);
+  cudaFree(dp);
+  if (e != cudaSuccess) return fail(h, PIC_ECUDA, "download failed: %s", cudaGetErrorString(e));
+  long long w = 0;
+  for (long long i = 0; i < slots; ++i) {
+    if (hp[i] == kPidDead) continue;
+    if (w >= live) break;
+    if (pid) pid[w] = hp[i];
+    if (x) memcpy(x + 3 * w, &hx[3 * i], 3 * sizeof(double));
+    if (v) memcpy(v + 3 * w, &hv[3 * i], 3 * sizeof(double));
+    ++w;
+  }
+  return PIC_OK;
+}
+
+pic_status pic_get_field(pic_handle* h, int32_t inst, int32_t which, int32_t species, void* host_out) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  Instance* I = h->inst[inst];
+  if (!host_out) return fail(h, PIC_EINVAL, "host_out is NULL");
+  const Grid& g = I->g;
+  if (which == PIC_FIELD_PHI) {
+    CK(h, cudaMemcpyAsync(host_out, I->phi, sizeof(double) * g.nnode, cudaMemcpyDeviceToHost, h->stream));
+  } else if (which == PIC_FIELD_RHO) {
+    if (I->mixed) {
+      std::vector<float> t(g.nnode);
+      CK(h, cudaMemcpyAsync(t.data(), I->rho32, sizeof(float) * g.nnode, cudaMemcpyDeviceToHost, h->stream));
+      CK(h, cudaStreamSynchronize(h->stream));
+      for (long long i = 0; i < g.nnode; ++i) ((double*)host_out)[i] = t[i];
+      return PIC_OK;
+    }
+    CK(h, cudaMemcpyAsync(host_out, I->rho64, sizeof(double) * g.nnode, cudaMemcpyDeviceToHost, h->stream));
+  } else if (which == PIC_FIELD_NCOUNT) {
+    if (species < 0 || species >= I->nsp || !I->ncount[species]) return fail(h, PIC_EINVAL, "species %d has no counts", species);
+    CK(h, cudaMemcpyAsync(host_out, I->ncount[species], sizeof(int32_t) * g.ncell, cudaMemcpyDeviceToHost, h->stream));
+  } else {
+    return fail(h, PIC_EINVAL, "unknown field %d", which);
+  }
+  CK(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+pic_status pic_set_phi(pic_handle* h, int32_t inst, const double* host_phi) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  Instance* I = h->inst[inst];
+  if (!host_phi) return fail(h, PIC_EINVAL, "host_phi is NULL");
+  CK(h, cudaMemcpyAsync(I->phi, host_phi, sizeof(double) * I->g.nnode, cudaMemcpyHostToDevice, h->stream));
+  launch_phi_planes(I->g, I->phi, h->stream);
+  CK(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+pic_status pic_solve(pic_handle* h, int32_t inst, const double* rho, double* phi, int32_t* iters, double* resid_rel) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  Instance* I = h->inst[inst];
+  if (!rho || !phi) return fail(h, PIC_EINVAL, "rho and phi are required");
+  const Grid& g = I->g;
+  double *drho = nullptr, *dphi = nullptr;
+  CK(h, dalloc(&drho, g.nnode));
+  CK(h, dalloc(&dphi, g.nnode));
+  CK(h, cudaMemcpyAsync(drho, rho, sizeof(double) * g.nnode, cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(dphi, phi, sizeof(double) * g.nnode, cudaMemcpyHostToDevice, h->stream));
+  launch_phi_planes(g, dphi, h->stream);
+  launch_rhs(g, drho, nullptr, I->solver.b, h->stream);
+  SolveResult r = I->solver.solve(dphi + g.nplane, I->cfg.cg_rtol, I->cfg.cg_maxit, h->stream);
+  CK(h, cudaMemcpyAsync(phi, dphi, sizeof(double) * g.nnode, cudaMemcpyDeviceToHost, h->stream));
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  cudaFree(drho);
+  cudaFree(dphi);
+  if (e != cudaSuccess) return fail(h, PIC_ECUDA, "solve failed: %s", cudaGetErrorString(e));
+  if (iters) *iters = r.iters;
+  if (resid_rel) *resid_rel = r.resid_rel;
+  if (!r.converged) return fail(h, PIC_ENOCONV, "solve did not reach cg_rtol (%g after %d iterations)", r.resid_rel, r.iters);
+  return PIC_OK;
+}
+
+pic_status pic_sort_now(pic_handle* h, int32_t inst) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  Instance* I = h->inst[inst];
+  st = I->mixed ? sort_instance<StoreMx>(h, I) : sort_instance<Store64>(h, I);
+  if (st != PIC_OK) return st;
+  CK(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+pic_status pic_get_cell_start(pic_handle* h, int32_t inst, int32_t species, int64_t* host_out) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  Instance* I = h->inst[inst];
+  if (species < 0 || species >= I->nsp || !host_out) return fail(h, PIC_EINVAL, "bad species or output");
+  CK(h, cudaMemcpyAsync(host_out, I->cell_start[species], sizeof(int64_t) * (I->g.ncell + 1), cudaMemcpyDeviceToHost,
+                        h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+pic_status pic_get_ionization_log(pic_handle* h, int32_t inst, int64_t cap, int64_t* n, uint32_t* rows) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  Instance* I = h->inst[inst];
+  if (!n) return fail(h, PIC_EINVAL, "n is NULL");
+  st = sync_counters(h, I);
+  if (st != PIC_OK) return st;
+  const long long ns = I->ion_ch >= 0 ? I->host_cnt->n_success : 0;
+  *n = ns;
+  if (ns == 0) return PIC_OK;
+  if (!rows || cap < ns) return fail(h, PIC_EINVAL, "cap %lld below %lld rows", (long long)cap, ns);
+  CK(h, cudaMemcpyAsync(rows, I->ion_log, sizeof(uint32_t) * 3 * ns, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+pic_status pic_philox(pic_handle* h, int64_t n, const uint32_t ctr[4], const uint32_t key[2], uint32_t* out) {
+  if (!h) return fail(nullptr, PIC_EINVAL, "null handle");
+  if (n < 0 || !ctr || !key || (n > 0 && !out)) return fail(h, PIC_EINVAL, "bad arguments");
+  if (n == 0) return PIC_OK;
+  uint32_t* d = nullptr;
+  CK(h, dalloc(&d, 4 * (size_t)n));
+  launch_philox(n, make_uint4(ctr[0], ctr[1], ctr[2], ctr[3]), make_uint2(key[0], key[1]), d, h->stream);
+  CK(h, cudaMemcpyAsync(out, d, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost, h->stream));
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(h, PIC_ECUDA, "philox failed: %s", cudaGetErrorString(e));
+  return PIC_OK;
+}
+
+pic_status pic_set_profiling(pic_handle* h, int32_t on) {
+  if (!h) return fail(nullptr, PIC_EINVAL, "null handle");
+  for (auto* I : h->inst) {
+    I->timer.on = on != 0;
+    I->timer.reset();
+  }
+  return PIC_OK;
+}
+
+pic_status pic_get_phase_times(pic_handle* h, int32_t inst, double* ms, int64_t* count) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  Instance* I = h->inst[inst];
+  CK(h, cudaStreamSynchronize(h->stream));
+  I->timer.collect();
+  for (int p = 0; p < kPhases; ++p) {
+    if (ms) ms[p] = I->timer.ms[p];
+    if (count) count[p] = I->timer.count[p];
+  }
+  return PIC_OK;
+}
+
+uint64_t pic_launch_count(void) { return (uint64_t)pic::g_launches; }
+
+pic_status pic_set_mcc_background(pic_handle* h, int32_t inst, double density_m3) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  if (!(density_m3 >= 0)) return fail(h, PIC_EINVAL, "density must be >= 0");
+  h->inst[inst]->bg_density = density_m3;
+  return PIC_OK;
+}
+
+}  // extern "C"

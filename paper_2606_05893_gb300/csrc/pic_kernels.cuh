@@ -1,0 +1,507 @@
+// pic_kernels.cuh -- particle views, kernel argument blocks and launcher
+// declarations shared by the kernel translation units and the host runtime.
+#pragma once
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+// ---------------------------------------------------------------------------
+// cell location (FP64 store): g = x * (1/h), cell = floor(g) clamped, fraction g - cell
+// ---------------------------------------------------------------------------
+struct Loc {
+  int i, j, k;
+  double fx, fy, fz;
+};
+
+__device__ __forceinline__ Loc locate64(const Grid& g, double x, double y, double z) {
+  Loc l;
+  const double gx = x * g.inv_h, gy = y * g.inv_h, gz = z * g.inv_h;
+  int i = (int)floor(gx), j = (int)floor(gy), k = (int)floor(gz);
+  i = min(max(i, 0), g.nx - 1);
+  j = min(max(j, 0), g.ny - 1);
+  k = min(max(k, 0), g.nz - 1);
+  l.i = i;
+  l.j = j;
+  l.k = k;
+  l.fx = gx - i;
+  l.fy = gy - j;
+  l.fz = gz - k;
+  return l;
+}
+
+// The 8 node indices of cell (i,j,k), periodic in i and j: order (a,b,c) with
+// a fastest, node = (k+c, j+b, i+a).
+__device__ __forceinline__ void corner_nodes(const Grid& g, int i, int j, int k, long long idx[8]) {
+  const int i1 = i + 1 == g.nx ? 0 : i + 1;
+  const int j1 = j + 1 == g.ny ? 0 : j + 1;
+  const long long pl = g.nplane;
+  const long long r00 = (long long)k * pl + (long long)j * g.nx;
+  const long long r10 = (long long)k * pl + (long long)j1 * g.nx;
+  idx[0] = r00 + i;
+  idx[1] = r00 + i1;
+  idx[2] = r10 + i;
+  idx[3] = r10 + i1;
+  idx[4] = r00 + pl + i;
+  idx[5] = r00 + pl + i1;
+  idx[6] = r10 + pl + i;
+  idx[7] = r10 + pl + i1;
+}
+
+template <class T>
+__device__ __forceinline__ void cic_weights(T fx, T fy, T fz, T w[8]) {
+  const T wx0 = T(1) - fx, wy0 = T(1) - fy, wz0 = T(1) - fz;
+  w[0] = wx0 * wy0 * wz0;
+  w[1] = fx * wy0 * wz0;
+  w[2] = wx0 * fy * wz0;
+  w[3] = fx * fy * wz0;
+  w[4] = wx0 * wy0 * fz;
+  w[5] = fx * wy0 * fz;
+  w[6] = wx0 * fy * fz;
+  w[7] = fx * fy * fz;
+}
+
+__device__ __forceinline__ void cell_ijk(const Grid& g, int cell, int& i, int& j, int& k) {
+  i = cell % g.nx;
+  const int t = cell / g.nx;
+  j = t % g.ny;
+  k = t / g.ny;
+}
+
+// ---------------------------------------------------------------------------
+// particle views
+// ---------------------------------------------------------------------------
+struct Particle64 {
+  double x, y, z, vx, vy, vz;
+  uint32_t pid;
+  long long cell;  // cell at read time (x^n)
+  Loc l;
+
+  template <class A>
+  __device__ __forceinline__ double3 gather(const Grid& g, const A& a) const {
+    long long idx[8];
+    corner_nodes(g, l.i, l.j, l.k, idx);
+    double w[8];
+    cic_weights(l.fx, l.fy, l.fz, w);
+    double3 e = make_double3(0.0, 0.0, 0.0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const double4_32a en = a.E64[idx[c]];
+      e.x += w[c] * en.x;
+      e.y += w[c] * en.y;
+      e.z += w[c] * en.z;
+    }
+    return e;
+  }
+  template <class A>
+  __device__ __forceinline__ void kick(const A& a, const double3& e) {
+    vx += a.qm_dt * e.x;
+    vy += a.qm_dt * e.y;
+    vz += a.qm_dt * e.z;
+  }
+  // x^{n+1} = x^n + v dt; returns -1 (z < 0), +1 (z >= Lz) or 0 (inside, x/y wrapped)
+  __device__ __forceinline__ int drift(const Grid& g) {
+    const double xn = x + vx * g.dt, yn = y + vy * g.dt, zn = z + vz * g.dt;
+    if (zn < 0.0) return -1;
+    if (zn >= g.Lz) return 1;
+    x = wrap_coord(xn, g.Lx, g.inv_Lx);
+    y = wrap_coord(yn, g.Ly, g.inv_Ly);
+    z = zn;
+    return 0;
+  }
+  __device__ __forceinline__ double v2() const { return vx * vx + vy * vy + vz * vz; }
+  __device__ __forceinline__ float v2f() const { return (float)v2(); }
+  __device__ __forceinline__ void set_v(double a, double b, double c) {
+    vx = a;
+    vy = b;
+    vz = c;
+  }
+  __device__ __forceinline__ void scale_v(double s) {
+    vx *= s;
+    vy *= s;
+    vz *= s;
+  }
+};
+
+struct ParticleMx {
+  int32_t cell;
+  float ox, oy, oz, vx, vy, vz;
+  uint32_t pid;
+
+  template <class A>
+  __device__ __forceinline__ float3 gather(const Grid& g, const A& a) const {
+    int i, j, k;
+    cell_ijk(g, cell, i, j, k);
+    long long idx[8];
+    corner_nodes(g, i, j, k, idx);
+    float w[8];
+    cic_weights(ox, oy, oz, w);
+    float3 e = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float4 en = __ldg(&a.E32[idx[c]]);
+      e.x = fmaf(w[c], en.x, e.x);
+      e.y = fmaf(w[c], en.y, e.y);
+      e.z = fmaf(w[c], en.z, e.z);
+    }
+    return e;
+  }
+  template <class A>
+  __device__ __forceinline__ void kick(const A& a, const float3& e) {
+    vx = fmaf(a.qm_dt_f, e.x, vx);
+    vy = fmaf(a.qm_dt_f, e.y, vy);
+    vz = fmaf(a.qm_dt_f, e.z, vz);
+  }
+  // offset += v dt / h; whole cells move the integer index (periodic in x, y)
+  __device__ __forceinline__ static int split(float& o) {
+    const float f = floorf(o);
+    o -= f;
+    int d = (int)f;
+    if (o >= 1.f) {
+      o -= 1.f;
+      d += 1;
+    }
+    return d;
+  }
+  __device__ __forceinline__ int drift(const Grid& g) {
+    ox = fmaf(vx, g.dt_over_h_f, ox);
+    oy = fmaf(vy, g.dt_over_h_f, oy);
+    oz = fmaf(vz, g.dt_over_h_f, oz);
+    const int di = split(ox), dj = split(oy), dk = split(oz);
+    int i, j, k;
+    cell_ijk(g, cell, i, j, k);
+    k += dk;
+    if (k < 0) return -1;
+    if (k >= g.nz) return 1;
+    i = (i + di) % g.nx;
+    if (i < 0) i += g.nx;
+    j = (j + dj) % g.ny;
+    if (j < 0) j += g.ny;
+    cell = (k * g.ny + j) * g.nx + i;
+    return 0;
+  }
+  __device__ __forceinline__ double v2() const {
+    return (double)vx * (double)vx + (double)vy * (double)vy + (double)vz * (double)vz;
+  }
+  __device__ __forceinline__ float v2f() const { return fmaf(vx, vx, fmaf(vy, vy, vz * vz)); }
+  __device__ __forceinline__ void set_v(double a, double b, double c) {
+    vx = (float)a;
+    vy = (float)b;
+    vz = (float)c;
+  }
+  __device__ __forceinline__ void scale_v(double s) {
+    const float f = (float)s;
+    vx *= f;
+    vy *= f;
+    vz *= f;
+  }
+};
+
+template <class S>
+struct PTraits;
+template <>
+struct PTraits<Store64> {
+  using P = Particle64;
+};
+template <>
+struct PTraits<StoreMx> {
+  using P = ParticleMx;
+};
+
+__device__ __forceinline__ Particle64 store_read(const Store64& s, const Grid& g, long long i) {
+  Particle64 p;
+  p.x = s.x[i];
+  p.y = s.y[i];
+  p.z = s.z[i];
+  p.vx = s.vx[i];
+  p.vy = s.vy[i];
+  p.vz = s.vz[i];
+  p.pid = s.pid[i];
+  p.l = locate64(g, p.x, p.y, p.z);
+  p.cell = ((long long)p.l.k * g.ny + p.l.j) * g.nx + p.l.i;
+  return p;
+}
+__device__ __forceinline__ ParticleMx store_read(const StoreMx& s, const Grid& g, long long i) {
+  ParticleMx p;
+  p.cell = s.cell[i];
+  p.ox = s.ox[i];
+  p.oy = s.oy[i];
+  p.oz = s.oz[i];
+  p.vx = s.vx[i];
+  p.vy = s.vy[i];
+  p.vz = s.vz[i];
+  p.pid = s.pid[i];
+  return p;
+}
+__device__ __forceinline__ long long particle_cell(const Particle64& p) { return p.cell; }
+__device__ __forceinline__ long long particle_cell(const ParticleMx& p) { return p.cell; }
+
+__device__ __forceinline__ void store_write_p(const Store64& s, long long i, const Particle64& p) {
+  s.x[i] = p.x;
+  s.y[i] = p.y;
+  s.z[i] = p.z;
+  s.vx[i] = p.vx;
+  s.vy[i] = p.vy;
+  s.vz[i] = p.vz;
+  s.pid[i] = p.pid;
+}
+__device__ __forceinline__ void store_write_p(const StoreMx& s, long long i, const ParticleMx& p) {
+  s.cell[i] = p.cell;
+  s.ox[i] = p.ox;
+  s.oy[i] = p.oy;
+  s.oz[i] = p.oz;
+  s.vx[i] = p.vx;
+  s.vy[i] = p.vy;
+  s.vz[i] = p.vz;
+  s.pid[i] = p.pid;
+}
+__device__ __forceinline__ void store_write_v(const Store64& s, long long i, const Particle64& p) {
+  s.vx[i] = p.vx;
+  s.vy[i] = p.vy;
+  s.vz[i] = p.vz;
+}
+__device__ __forceinline__ void store_write_v(const StoreMx& s, long long i, const ParticleMx& p) {
+  s.vx[i] = p.vx;
+  s.vy[i] = p.vy;
+  s.vz[i] = p.vz;
+}
+__device__ __forceinline__ void store_kill(const Store64& s, long long i) { s.pid[i] = kPidDead; }
+__device__ __forceinline__ void store_kill(const StoreMx& s, long long i) { s.pid[i] = kPidDead; }
+
+// Write from FP64 values (injection, host upload).
+__device__ __forceinline__ void store_write(const Store64& s, const Grid& g, long long i, double x, double y, double z,
+                                            double vx, double vy, double vz, uint32_t pid) {
+  (void)g;
+  s.x[i] = x;
+  s.y[i] = y;
+  s.z[i] = z;
+  s.vx[i] = vx;
+  s.vy[i] = vy;
+  s.vz[i] = vz;
+  s.pid[i] = pid;
+}
+__device__ __forceinline__ float offset_of(double gcoord, int cell) {
+  float o = (float)(gcoord - (double)cell);
+  if (o >= 1.f) o = 0x1.fffffep-1f;
+  if (o < 0.f) o = 0.f;
+  return o;
+}
+__device__ __forceinline__ void store_write(const StoreMx& s, const Grid& g, long long i, double x, double y, double z,
+                                            double vx, double vy, double vz, uint32_t pid) {
+  const Loc l = locate64(g, x, y, z);
+  s.cell[i] = (l.k * g.ny + l.j) * g.nx + l.i;
+  s.ox[i] = offset_of(x * g.inv_h, l.i);
+  s.oy[i] = offset_of(y * g.inv_h, l.j);
+  s.oz[i] = offset_of(z * g.inv_h, l.k);
+  s.vx[i] = (float)vx;
+  s.vy[i] = (float)vy;
+  s.vz[i] = (float)vz;
+  s.pid[i] = pid;
+}
+// Read as FP64 values (host download).
+__device__ __forceinline__ void store_get(const Store64& s, const Grid& g, long long i, double* x, double* v,
+                                          uint32_t* pid) {
+  (void)g;
+  x[0] = s.x[i];
+  x[1] = s.y[i];
+  x[2] = s.z[i];
+  v[0] = s.vx[i];
+  v[1] = s.vy[i];
+  v[2] = s.vz[i];
+  *pid = s.pid[i];
+}
+__device__ __forceinline__ void store_get(const StoreMx& s, const Grid& g, long long i, double* x, double* v,
+                                          uint32_t* pid) {
+  int ci, cj, ck;
+  cell_ijk(g, s.cell[i], ci, cj, ck);
+  x[0] = ((double)ci + (double)s.ox[i]) * g.h;
+  x[1] = ((double)cj + (double)s.oy[i]) * g.h;
+  x[2] = ((double)ck + (double)s.oz[i]) * g.h;
+  v[0] = s.vx[i];
+  v[1] = s.vy[i];
+  v[2] = s.vz[i];
+  *pid = s.pid[i];
+}
+
+// ---------------------------------------------------------------------------
+// argument blocks
+// ---------------------------------------------------------------------------
+struct McArgs {
+  int nch;
+  XsDev ch[kMaxXsec];
+  const int32_t* ncount[kMaxXsec];  // neutral counts of each channel's target
+  double dens[kMaxXsec];            // w_target / h^3
+  float bound_f[kMaxXsec];          // (max sigma) w_target / h^3, FP32 filter
+  double half_m_over_e;             // E_eV = v^2 m / (2 e)
+  double mass;
+  uint2 key;
+  uint32_t step;
+  int bg_mode;  // fixed background density (test mode)
+  double bg_density;
+};
+
+struct StepBegin {
+  int nsp;
+  int out[kMaxSpecies];
+};
+
+struct InjSrc {
+  int species;
+  double cx, cy, R, sig;
+};
+
+template <class S>
+struct InjectArgs {
+  Grid g;
+  DevCounters* cnt;
+  S st[kMaxSpecies];
+  int cur[kMaxSpecies];
+  long long cap[kMaxSpecies];
+  int nsrc;
+  InjSrc src[kMaxSources];
+  long long src_first[kMaxSources + 1];
+  long long species_offset[kMaxSources];
+  long long total;
+  uint2 key;
+  uint32_t step;
+};
+
+struct InjectCommit {
+  int nsp;
+  int cur[kMaxSpecies];
+  long long add[kMaxSpecies];
+  long long cap[kMaxSpecies];
+  long long total;
+};
+
+template <class S>
+struct PushArgs {
+  Grid g;
+  DevCounters* cnt;
+  S in, out;
+  int cur_in, species;
+  long long cap;
+  double qm_dt;
+  float qm_dt_f;
+  double mass, weight, charge;
+  const double4_32a* E64;
+  const float4* E32;
+  McArgs mc;
+  Event* ev;
+  int ev_cap;
+  int32_t* ev_head;
+  Cand* cand;
+  int cand_cap;
+  int32_t* cand_head;
+};
+
+struct ResolveArgs {
+  DevCounters* cnt;
+  Event* ev;
+  int ev_cap;
+  int32_t* ev_head;
+  Cand* cand;
+  int32_t* cand_head;
+  unsigned long long* sort_keys;
+  uint32_t* sort_vals;
+};
+
+template <class S>
+struct ApplyArgs {
+  Grid g;
+  DevCounters* cnt;
+  const Event* ev;
+  int ev_cap;
+  const Cand* cand;
+  const uint32_t* sorted_vals;
+  XsDev ch[kMaxXsec];
+  uint2 key;
+  uint32_t step;
+  S e_st;
+  int e_out, e_species;
+  long long e_cap;
+  double e_mass;
+  S n_st;
+  S i_st;
+  int i_out, i_species;
+  long long i_cap;
+  uint32_t* log;
+};
+
+template <class S>
+struct DepositArgs {
+  Grid g;
+  DevCounters* cnt;
+  S st;
+  int cur, species;
+  int neutral;       // 1: count into ncount, 0: charge into rho
+  double qw_h3;      // q w / h^3
+  double* rho64;
+  float* rho32;
+  int32_t* ncount;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the kernel translation units)
+// ---------------------------------------------------------------------------
+template <class S>
+void launch_inject(const InjectArgs<S>& a, int grid, cudaStream_t st);
+void launch_inject_commit(DevCounters* cnt, const InjectCommit& c, cudaStream_t st);
+template <class S>
+void launch_push(const PushArgs<S>& a, int role, bool mcc, int grid, cudaStream_t st);
+void launch_resolve_rank(const ResolveArgs& a, int grid, cudaStream_t st);
+void launch_resolve_cleanup(const ResolveArgs& a, int grid, cudaStream_t st);
+template <class S>
+void launch_resolve_apply(const ApplyArgs<S>& a, int grid, cudaStream_t st);
+void launch_resolve_commit(DevCounters* cnt, int e_out, int e_sp, long long e_cap, int i_out, int i_sp,
+                           long long i_cap, int n_sp, int ev_cap, cudaStream_t st);
+
+template <class S>
+void launch_deposit(const DepositArgs<S>& a, int grid, cudaStream_t st);
+void launch_fill64(double* p, long long n, double v, cudaStream_t st);
+void launch_fill32(float* p, long long n, float v, cudaStream_t st);
+void launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t st);
+void launch_rhs(const Grid& g, const double* rho64, const float* rho32, double* b, cudaStream_t st);
+void launch_efield64(const Grid& g, const double* phi, double4_32a* E, cudaStream_t st);
+void launch_efield32(const Grid& g, const double* phi, float4* E, cudaStream_t st);
+void launch_phi_planes(const Grid& g, double* phi, cudaStream_t st);
+void launch_step_begin(DevCounters* cnt, const int* out_buf, int nsp, cudaStream_t st);
+
+template <class S>
+void launch_load(const Grid& g, S st, DevCounters* cnt, int cur, int species, long long cap, const double* x,
+                 const double* v, long long n, cudaStream_t s);
+template <class S>
+void launch_download(const Grid& g, S st, long long n, double* x, double* v, uint32_t* pid, cudaStream_t s);
+
+template <class S>
+void launch_cell_keys(const Grid& g, S st, long long n_max, const unsigned long long* n_dev, int pid_bits,
+                      unsigned long long* keys, uint32_t* vals, int32_t* cell_count, cudaStream_t s);
+
+// radix sort of (u64 key, u32 value) pairs over bits [bit0, bit1); n read from
+// the device (at most n_max). Returns 0 if the result is in (ka, va), 1 if in (kb, vb).
+struct SortBuffers {
+  unsigned long long *ka, *kb;
+  uint32_t *va, *vb;
+  uint32_t* hist;      // 256 * nblocks(n_max)
+  uint32_t* digit_tot; // 256
+  long long n_max;
+};
+long long sort_hist_entries(long long n_max);
+int radix_sort_pairs(const SortBuffers& b, const unsigned long long* n_dev, int bit0, int bit1, cudaStream_t s);
+// exclusive scan of int32 counts[n] into int64 out[n+1] (out[n] = total)
+size_t scan_temp_bytes(long long n);
+void exclusive_scan_i32_i64(const int32_t* counts, long long n, long long* out, void* temp, cudaStream_t s);
+template <class S>
+void launch_gather(S src, S dst, const uint32_t* perm, const unsigned long long* n_dev, long long n_max,
+                   cudaStream_t s);
+
+void launch_sort_commit(DevCounters* cnt, int c, int s, cudaStream_t st);
+
+// moments
+template <class S>
+void launch_kinetic(S st, const unsigned long long* n_dev, long long n_max, double* out, cudaStream_t s);
+void launch_field_energy(const Grid& g, const double* phi, double* out, cudaStream_t s);
+
+void launch_philox(long long n, uint4 ctr, uint2 key, uint32_t* out, cudaStream_t s);
+
+}  // namespace pic

@@ -1,0 +1,192 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+FP64 path, one step from an identical state: integer outputs (counts per
+species, injected/absorbed/ionization/elastic/suppressed counts, pids, sort
+permutations, neutral cell counts, the ionization log) are bit-exact; floats
+agree within 1e-10 relative (positions / L, velocities / max|v|, rho and phi in
+the max norm), with both Poisson solves run to a 1e-13 relative residual so
+that the solver tolerance does not mask the comparison.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2606_05893_gb300 import workloads as W
+from tests._cases import bare, const_xsec, ionization_cells_case, isotropic, speed_of_eV
+from tests.gpu_compare import compare_integer_moments, compare_particles, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+RTOL_SOLVE = 1e-13
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2606_05893_gb300 as p
+    p.load_library()
+    return p
+
+
+def run_pair(pkg, wl, steps, precision=0, **kw):
+    sim = pkg.Simulation(wl, precision=precision, cg_rtol=RTOL_SOLVE, cg_maxit=5000, **kw)
+    ref = O.Oracle(wl, cg_rtol=RTOL_SOLVE, **({"background_density": kw["background_density"]}
+                                               if "background_density" in kw else {}))
+    for _ in range(steps):
+        sim.step()
+        ref.step()
+    return sim, ref
+
+
+def full_compare(sim, ref, wl, tol=TOL):
+    mg, mo = sim.moments(), ref.moments()
+    compare_integer_moments(mg, mo)
+    for sp in range(len(wl.species)):
+        compare_particles(sim, ref, wl, sp, tol, tol)
+    # max-norm comparison, floored at one superparticle's charge density and
+    # potential scale (the grids can cancel to rounding noise, e.g. when
+    # electrons and ions sit on the same spot)
+    qw = max(abs(s.charge_C * s.weight) for s in wl.species)
+    rho_g, rho_o = sim.rho(), ref.rho()
+    assert np.abs(rho_g - rho_o).max() <= tol * max(np.abs(rho_o).max(), qw / wl.h ** 3)
+    phi_g, phi_o = sim.phi(), ref.phi()
+    assert np.abs(phi_g - phi_o).max() <= tol * max(np.abs(phi_o).max(), qw / (W.EPS0 * wl.h))
+    for sp, s in enumerate(wl.species):
+        if s.role == W.NEUTRAL:
+            assert np.array_equal(sim.ncount(sp), ref.ncount(sp))
+    return mg, mo
+
+
+def test_device_philox_matches_oracle(pkg):
+    sim = pkg.Simulation(W.config_tiny(), preload=False)
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        ctr = rng.integers(0, 2 ** 32, 4, dtype=np.uint64).astype(np.uint32)
+        key = rng.integers(0, 2 ** 32, 2, dtype=np.uint64).astype(np.uint32)
+        out = pkg.pic_philox(sim.h, 64, ctr, key)
+        for i in (0, 1, 31, 63):
+            c = ctr.copy()
+            c[0] = np.uint32((int(ctr[0]) + i) & 0xFFFFFFFF)
+            assert np.array_equal(out[i], O.philox(c, key))
+    sim.close()
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 32), (8, 8, 16), (6, 10, 12), (5, 7, 9), (32, 32, 64)])
+def test_poisson_solve_matches_oracle(pkg, shape):
+    nx, ny, nz = shape
+    wl = bare(nx=nx, ny=ny, nz=nz, h=2.5e-9, phi_c=-3.0, phi_a=250.0)
+    rng = np.random.default_rng(nx * 100 + nz)
+    rho = rng.standard_normal((nz + 1, ny, nx)) * 3e6
+    sim = pkg.Simulation(wl, cg_rtol=RTOL_SOLVE, cg_maxit=20000, preload=False)
+    phi_g, it, rel = sim.solve(rho)
+    assert rel <= RTOL_SOLVE
+    phi_o, ito, relo = O.poisson(nx, ny, nz, wl.h, wl.phi_cathode, wl.phi_anode, rho, rtol=RTOL_SOLVE)
+    assert rel_inf(phi_g, phi_o) <= TOL
+    if nx % 2 == 0 and ny % 2 == 0 and nx >= 16:
+        # the multigrid preconditioner needs far fewer iterations than plain CG
+        assert it < ito / 3, (it, ito)
+    sim.close()
+
+
+def test_poisson_solve_mixed_precision(pkg):
+    nx, ny, nz = 32, 32, 64
+    wl = bare(nx=nx, ny=ny, nz=nz, h=2.5e-9, phi_c=0.0, phi_a=600.0)
+    rng = np.random.default_rng(4)
+    rho = rng.standard_normal((nz + 1, ny, nx)) * 3e6
+    sim = pkg.Simulation(wl, precision=pkg.PIC_MIXED, cg_rtol=1e-12, cg_maxit=20000, preload=False)
+    phi_g, it, rel = sim.solve(rho)
+    assert rel <= 1e-12
+    phi_o, _, _ = O.poisson(nx, ny, nz, wl.h, wl.phi_cathode, wl.phi_anode, rho, rtol=1e-13)
+    assert rel_inf(phi_g, phi_o) <= 1e-9
+    sim.close()
+
+
+def test_one_step_tiny(pkg):
+    wl = W.config_tiny(seed=3)
+    sim, ref = run_pair(pkg, wl, 1)
+    full_compare(sim, ref, wl)
+
+
+def test_ten_steps_tiny_with_sorting_and_injection(pkg):
+    wl = W.config_tiny(seed=5)
+    sim, ref = run_pair(pkg, wl, 10)
+    mg, mo = full_compare(sim, ref, wl, tol=1e-9)
+    assert sum(mg["injected"]) > 0 and sum(mg["abs_anode"]) > 0
+
+
+def test_ionization_and_suppression_step(pkg):
+    wl = ionization_cells_case(seed=3)
+    sim, ref = run_pair(pkg, wl, 1)
+    mg, mo = full_compare(sim, ref, wl)
+    assert mg["n_ionization"] > 50 and mg["n_suppressed"] >= 10
+    lg, lo = sim.ionization_log(), ref.ionization_log()
+    assert np.array_equal(lg, lo)
+
+
+def test_ionization_several_steps(pkg):
+    wl = ionization_cells_case(seed=8)
+    sim, ref = run_pair(pkg, wl, 4)
+    mg, mo = full_compare(sim, ref, wl, tol=1e-9)
+    assert np.array_equal(sim.ionization_log(), ref.ionization_log())
+
+
+def test_small_workload_one_step(pkg):
+    wl = W.config_small()
+    sim, ref = run_pair(pkg, wl, 1)
+    full_compare(sim, ref, wl)
+
+
+def test_small_workload_five_steps(pkg):
+    wl = W.config_small(seed=42)
+    sim, ref = run_pair(pkg, wl, 5)
+    mg, mo = full_compare(sim, ref, wl, tol=1e-9)
+    assert mg["n_ionization"] + mg["n_elastic"] > 0
+
+
+def test_background_rates_bit_exact(pkg):
+    n, E = 20000, 50.0
+    u = speed_of_eV(E)
+    s_ion, s_el = 2e-20, 6e-20
+    n0 = 0.05 / (u * (s_ion + s_el) * 1e-16)
+    wl = bare(nx=8, ny=8, nz=8, h=1e-8, dt=1e-16, weight=1e-30, capacity=1 << 16,
+              xsec=[const_xsec(W.XS_IONIZATION, s_ion, threshold=7.73), const_xsec(W.XS_ELASTIC, s_el)])
+    rng = np.random.default_rng(2)
+    x = (0.25 + 0.5 * rng.random((n, 3))) * np.array(wl.L)
+    wl.preload = [(x, isotropic(rng, n, u)), (np.zeros((0, 3)), np.zeros((0, 3))), (np.zeros((0, 3)), np.zeros((0, 3)))]
+    sim, ref = run_pair(pkg, wl, 3, background_density=n0)
+    mg, mo = sim.moments(), ref.moments()
+    assert mg["n_elastic"] == mo["n_elastic"] and mg["n_ionization"] == mo["n_ionization"]
+    P = -math.expm1(-u * n0 * (s_ion + s_el) * wl.dt)
+    assert abs(mg["n_elastic"] + mg["n_ionization"] - 3 * n * P) < 5 * math.sqrt(3 * n * P)
+    compare_particles(sim, ref, wl, 0, TOL, TOL)
+
+
+def test_sort_permutation_and_offsets_bit_exact(pkg):
+    wl = W.config_tiny(seed=9)
+    sim = pkg.Simulation(wl)
+    ref = O.Oracle(wl)
+    sim.sort_now()
+    ref.sort()
+    for sp in range(3):
+        _, _, pg = sim.particles(sp)
+        _, _, po = ref.particles(sp)
+        assert np.array_equal(pg, po)
+        assert np.array_equal(sim.cell_start(sp), ref.cell_start(sp))
+    sim.close()
+
+
+def test_vacuum_uniform_field_push_exact(pkg):
+    wl = bare(nx=4, ny=4, nz=16, h=5e-9, dt=1e-16, phi_c=0.0, phi_a=100.0, weight=1e-30)
+    rng = np.random.default_rng(1)
+    L = np.array(wl.L)
+    n = 64
+    x0 = rng.random((n, 3)) * L * np.array([1, 1, 0.3]) + np.array([0, 0, 0.2 * L[2]])
+    v0 = rng.standard_normal((n, 3)) * 1e5
+    wl.preload = [(x0, v0), (np.zeros((0, 3)), np.zeros((0, 3))), (x0.copy(), -v0)]
+    sim, ref = run_pair(pkg, wl, 30)
+    for sp in (0, 2):
+        compare_particles(sim, ref, wl, sp, 1e-12, 1e-12)
