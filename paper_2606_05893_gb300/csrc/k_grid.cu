@@ -1,5 +1,7 @@
 // k_grid.cu -- grid-side kernels: deposition (a3), Poisson right-hand side,
 // node field E = -grad phi (a5), fills, host transfer helpers, moments (a11).
+#include <algorithm>
+
 #include "pic_internal.cuh"
 #include "pic_kernels.cuh"
 
@@ -32,47 +34,111 @@ void launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // a3: cloud-in-cell deposition. Charged species add q w S / h^3 to the 8
 // corner nodes; neutral species add 1 to the count of their cell (NGP).
+// Lanes of a warp that sit in the same cell (the store is cell-sorted every
+// few steps and particles stay spatially coherent in between) first combine
+// their 8 corner weights with shuffles; one lane per cell then issues the 8
+// atomics to rho in L2.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void deposit_one(const Grid& g, const Particle64& p, const DepositArgs<Store64>& a) {
-  long long idx[8];
-  corner_nodes(g, p.l.i, p.l.j, p.l.k, idx);
-  double w[8];
-  cic_weights(p.l.fx, p.l.fy, p.l.fz, w);
+constexpr int kDepBlock = 256;
+
+template <class V>
+__device__ __forceinline__ void warp_combine_cell(int cell, V w[8]) {
+  const unsigned peers = __match_any_sync(0xffffffffu, cell);
+  if (__popc(peers) == 1) return;
+  const int leader = __ffs(peers) - 1;
+  unsigned rest = peers & ~(1u << leader);
+  V acc[8];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) atomicAdd(&a.rho64[idx[c]], a.qw_h3 * w[c]);
-}
-__device__ __forceinline__ void deposit_one(const Grid& g, const ParticleMx& p, const DepositArgs<StoreMx>& a) {
-  int i, j, k;
-  cell_ijk(g, p.cell, i, j, k);
-  long long idx[8];
-  corner_nodes(g, i, j, k, idx);
-  float w[8];
-  cic_weights(p.ox, p.oy, p.oz, w);
-  const float q = (float)a.qw_h3;
+  for (int c = 0; c < 8; ++c) acc[c] = w[c];
+  while (rest) {
+    const int src = __ffs(rest) - 1;
+    rest &= rest - 1;
 #pragma unroll
-  for (int c = 0; c < 8; ++c) atomicAdd(&a.rho32[idx[c]], q * w[c]);
+    for (int c = 0; c < 8; ++c) acc[c] += __shfl_sync(peers, w[c], src);
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) w[c] = acc[c];
 }
 
-template <class S>
-__global__ void __launch_bounds__(kBlock) k_deposit(DepositArgs<S> a) {
+__global__ void __launch_bounds__(kDepBlock) k_deposit_fp64(DepositArgs<Store64> a) {
   const long long n = (long long)a.cnt->n[a.cur][a.species];
   const Grid& g = a.g;
-  for (long long i = gtid(); i < n; i += gstride()) {
-    const auto p = store_read(a.st, g, i);
-    if (a.neutral) {
-      if (p.pid != kPidDead) atomicAdd(&a.ncount[particle_cell(p)], 1);
-      continue;
+  const int lane = threadIdx.x & 31;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += gstride()) {
+    const long long i = base + threadIdx.x;
+    const bool valid = i < n;
+    int cell = -1;
+    long long idx[8];
+    double w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (valid) {
+      const Particle64 p = store_read(a.st, g, i);
+      cell = (int)p.cell;
+      corner_nodes(g, p.l.i, p.l.j, p.l.k, idx);
+      cic_weights(p.l.fx, p.l.fy, p.l.fz, w);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) w[c] *= a.qw_h3;
     }
-    deposit_one(g, p, a);
+    warp_combine_cell(cell, w);
+    const unsigned peers = __match_any_sync(0xffffffffu, cell);
+    if (valid && lane == __ffs(peers) - 1) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) atomicAdd(&a.rho64[idx[c]], w[c]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kDepBlock) k_deposit_mx(DepositArgs<StoreMx> a) {
+  const long long n = (long long)a.cnt->n[a.cur][a.species];
+  const Grid& g = a.g;
+  const float q = (float)a.qw_h3;
+  const int lane = threadIdx.x & 31;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += gstride()) {
+    const long long i = base + threadIdx.x;
+    const bool valid = i < n;
+    int cell = -1;
+    float w[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+      cell = a.st.cell[i];
+      cic_weights(a.st.ox[i], a.st.oy[i], a.st.oz[i], w);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) w[c] *= q;
+    }
+    warp_combine_cell(cell, w);
+    const unsigned peers = __match_any_sync(0xffffffffu, cell);
+    if (valid && lane == __ffs(peers) - 1) {
+      int ci, cj, ck;
+      cell_ijk(g, cell, ci, cj, ck);
+      long long idx[8];
+      corner_nodes(g, ci, cj, ck, idx);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) atomicAdd(&a.rho32[idx[c]], w[c]);
+    }
   }
 }
 
 template <class S>
-void launch_deposit(const DepositArgs<S>& a, int grid, cudaStream_t st) {
-  PIC_LAUNCH(grid, kBlock, 0, st, k_deposit<S>)(a);
+__global__ void __launch_bounds__(kDepBlock) k_count_neutrals(DepositArgs<S> a) {
+  const long long n = (long long)a.cnt->n[a.cur][a.species];
+  const Grid& g = a.g;
+  for (long long i = gtid(); i < n; i += gstride()) {
+    const auto p = store_read(a.st, g, i);
+    if (p.pid != kPidDead) atomicAdd(&a.ncount[particle_cell(p)], 1);
+  }
 }
-template void launch_deposit<Store64>(const DepositArgs<Store64>&, int, cudaStream_t);
-template void launch_deposit<StoreMx>(const DepositArgs<StoreMx>&, int, cudaStream_t);
+
+template <class S>
+void launch_deposit(const DepositArgs<S>& a, int grid, cudaStream_t st);
+template <>
+void launch_deposit<Store64>(const DepositArgs<Store64>& a, int grid, cudaStream_t st) {
+  if (a.neutral) PIC_LAUNCH(grid, kDepBlock, 0, st, k_count_neutrals<Store64>)(a);
+  else PIC_LAUNCH(grid, kDepBlock, 0, st, k_deposit_fp64)(a);
+}
+template <>
+void launch_deposit<StoreMx>(const DepositArgs<StoreMx>& a, int grid, cudaStream_t st) {
+  if (a.neutral) PIC_LAUNCH(grid, kDepBlock, 0, st, k_count_neutrals<StoreMx>)(a);
+  else PIC_LAUNCH(grid, kDepBlock, 0, st, k_deposit_mx)(a);
+}
+
 
 // ---------------------------------------------------------------------------
 // a4 right-hand side of Eq. (1) scaled by h^2 over the unknown nodes k = 1..nz-1:
@@ -81,10 +147,12 @@ template void launch_deposit<StoreMx>(const DepositArgs<StoreMx>&, int, cudaStre
 __global__ void k_rhs(Grid g, const double* __restrict__ rho64, const float* __restrict__ rho32, double* __restrict__ b) {
   const long long nu = (long long)(g.nz - 1) * g.nplane;
   const double s = g.h * g.h / kEps0;
+  const float s32 = (float)s;
   for (long long u = gtid(); u < nu; u += gstride()) {
     const long long node = u + g.nplane;
     const int k = (int)(node / g.nplane);
-    double v = s * (rho64 ? rho64[node] : (double)rho32[node]);
+    // MIXED: the density is FP32 already; scale it in FP32 and widen once
+    double v = rho64 ? s * rho64[node] : (double)(s32 * rho32[node]);
     if (k == 1) v += g.phi_c;
     if (k == g.nz - 1) v += g.phi_a;
     b[u] = v;
@@ -146,6 +214,33 @@ __global__ void k_efield32(Grid g, const double* __restrict__ phi, float4* __res
     const double3 e = node_field(g, phi, n);
     E[n] = make_float4((float)e.x, (float)e.y, (float)e.z, 0.f);
   }
+}
+// MIXED: E from the FP32 deviation from the vacuum potential, plus the vacuum field
+__global__ void k_efield32f(Grid g, const float* __restrict__ f, float4* __restrict__ E, float c, float ez_vac) {
+  for (long long n = gtid(); n < g.nnode; n += gstride()) {
+    const long long pl = g.nplane;
+    const int k = (int)(n / pl);
+    const long long r = n - (long long)k * pl;
+    const int j = (int)(r / g.nx);
+    const int i = (int)(r - (long long)j * g.nx);
+    const int im = i == 0 ? g.nx - 1 : i - 1, ip = i == g.nx - 1 ? 0 : i + 1;
+    const int jm = j == 0 ? g.ny - 1 : j - 1, jp = j == g.ny - 1 ? 0 : j + 1;
+    const long long row = (long long)k * pl + (long long)j * g.nx;
+    const float ex = (f[row + im] - f[row + ip]) * c;
+    const float ey = (f[(long long)k * pl + (long long)jm * g.nx + i] - f[(long long)k * pl + (long long)jp * g.nx + i]) * c;
+    float ez;
+    if (k == 0)
+      ez = (3.f * f[n] - 4.f * f[n + pl] + f[n + 2 * pl]) * c;
+    else if (k == g.nz)
+      ez = (-3.f * f[n] + 4.f * f[n - pl] - f[n - 2 * pl]) * c;
+    else
+      ez = (f[n - pl] - f[n + pl]) * c;
+    E[n] = make_float4(ex, ey, ez + ez_vac, 0.f);
+  }
+}
+void launch_efield32f(const Grid& g, const float* phi32, float4* E, cudaStream_t st) {
+  const float ez_vac = (float)(-(g.phi_a - g.phi_c) / g.Lz);
+  PIC_LAUNCH(grid_for(g.nnode), kBlock, 0, st, k_efield32f)(g, phi32, E, (float)(0.5 * g.inv_h), ez_vac);
 }
 void launch_efield64(const Grid& g, const double* phi, double4_32a* E, cudaStream_t st) {
   PIC_LAUNCH(grid_for(g.nnode), kBlock, 0, st, k_efield64)(g, phi, E);

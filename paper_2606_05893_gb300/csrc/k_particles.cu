@@ -16,6 +16,9 @@
 
 namespace pic {
 
+constexpr int kPushBlock = 256;
+constexpr int kPushWarps = kPushBlock / 32;
+
 // ---------------------------------------------------------------------------
 // cross sections
 // ---------------------------------------------------------------------------
@@ -120,11 +123,28 @@ __global__ void k_inject_commit(DevCounters* cnt, InjectCommit c) {
 // a5-a8 + a10: gather / push / absorb / collide / compact
 // ---------------------------------------------------------------------------
 template <class S, bool CHARGED, bool MCC, bool NEUTRAL>
-__global__ void __launch_bounds__(256) k_push(PushArgs<S> a) {
+__global__ void __launch_bounds__(kPushBlock) k_push(PushArgs<S> a) {
+  // Block-level bookkeeping: absorbed-particle statistics and elastic counts
+  // accumulate in shared memory and reach HBM once per block; output slots are
+  // reserved once per block and round (one global atomic per 256 particles).
+  __shared__ unsigned long long s_abs[2];
+  __shared__ double s_eabs[2], s_q[2];
+  __shared__ unsigned long long s_el;
+  __shared__ unsigned int s_wcnt[kPushWarps];
+  __shared__ unsigned long long s_base;
+  if (threadIdx.x == 0) {
+    s_abs[0] = s_abs[1] = 0ull;
+    s_eabs[0] = s_eabs[1] = 0.0;
+    s_q[0] = s_q[1] = 0.0;
+    s_el = 0ull;
+  }
+  __syncthreads();
   const long long n = (long long)a.cnt->n[a.cur_in][a.species];
   if (blockIdx.x == 0 && threadIdx.x == 0)
     a.cnt->pushed[a.species] += (unsigned long long)n - (NEUTRAL ? a.cnt->n_tomb[a.species] : 0ull);
   const Grid& g = a.g;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long* out_count = &a.cnt->n[a.cur_in ^ 1][a.species];
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += gstride()) {
     const long long i = base + threadIdx.x;
     const bool valid = i < n;
@@ -136,9 +156,7 @@ __global__ void __launch_bounds__(256) k_push(PushArgs<S> a) {
     double E_eV = 0.0;
     if (valid) {
       p = store_read(a.in, g, i);
-      if (NEUTRAL && p.pid == kPidDead) {
-        // converted neutral from the previous step: dropped here
-      } else {
+      if (!(NEUTRAL && p.pid == kPidDead)) {  // converted neutrals of the last step are dropped here
         cell_n = particle_cell(p);
         if (CHARGED) {
           const auto e = p.gather(g, a);
@@ -146,35 +164,28 @@ __global__ void __launch_bounds__(256) k_push(PushArgs<S> a) {
         }
         const int side = p.drift(g);  // -1 cathode, +1 anode, 0 inside
         if (side != 0) {
-          const double v2 = p.v2();
-          const double ke = 0.5 * a.mass * a.weight * v2;
-          if (side < 0) {
-            atomicAdd(&a.cnt->abs_cathode[a.species], 1ull);
-            atomicAdd(&a.cnt->abs_energy_cathode[a.species], ke);
-            atomicAdd(&a.cnt->q_cathode_step, a.charge * a.weight);
-          } else {
-            atomicAdd(&a.cnt->abs_anode[a.species], 1ull);
-            atomicAdd(&a.cnt->abs_energy_anode[a.species], ke);
-            atomicAdd(&a.cnt->q_anode_step, a.charge * a.weight);
-          }
+          const int b = side < 0 ? 0 : 1;
+          const double ke = 0.5 * a.mass * a.weight * p.v2();
+          atomicAdd(&s_abs[b], 1ull);
+          atomicAdd(&s_eabs[b], ke);
+          atomicAdd(&s_q[b], a.charge * a.weight);
         } else {
           keep = true;
           if (MCC) {
             const uint4 d = draw(a.mc.key, p.pid, a.mc.step, TAG_MCC);
-            const float v2f = p.v2f();
-            if (!mcc_cannot_collide(a.mc, cell_n, v2f, u01_32(d.x), (float)g.dt)) {
+            if (!mcc_cannot_collide(a.mc, cell_n, p.v2f(), u01_32(d.x), (float)g.dt)) {
               const double U = u01_64(d.x, d.y);
               const double v2 = p.v2();
               const int ch = mcc_exact_dt(a.mc, cell_n, v2, U, g.dt, &E_eV);
               if (ch >= 0) {
                 if (a.mc.ch[ch].kind == XS_ELASTIC) {
-                  const uint4 s = draw(a.mc.key, p.pid, a.mc.step, TAG_SCATTER);
-                  const double ct = 2.0 * u01_64(s.x, s.y) - 1.0;
+                  const uint4 sc = draw(a.mc.key, p.pid, a.mc.step, TAG_SCATTER);
+                  const double ct = 2.0 * u01_64(sc.x, sc.y) - 1.0;
                   const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
-                  const double ph = 2.0 * kPi * u01_64(s.z, s.w);
+                  const double ph = 2.0 * kPi * u01_64(sc.z, sc.w);
                   const double u = sqrt(v2);
                   p.set_v(u * st * cos(ph), u * st * sin(ph), u * ct);
-                  atomicAdd(&a.cnt->n_el, 1ull);
+                  atomicAdd(&s_el, 1ull);
                 } else if (a.mc.bg_mode) {
                   // fixed-background test mode: counted, nothing consumed or created
                   atomicAdd(&a.cnt->n_ion, 1ull);
@@ -188,7 +199,22 @@ __global__ void __launch_bounds__(256) k_push(PushArgs<S> a) {
         }
       }
     }
-    const unsigned long long slot = warp_reserve(&a.cnt->n[a.cur_in ^ 1][a.species], keep);
+    // block-wide slot reservation
+    const unsigned ball = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) s_wcnt[warp] = __popc(ball);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned int tot = 0;
+      for (int w = 0; w < kPushWarps; ++w) {
+        const unsigned int c = s_wcnt[w];
+        s_wcnt[w] = tot;
+        tot += c;
+      }
+      s_base = tot ? atomicAdd(out_count, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    const unsigned long long slot = s_base + s_wcnt[warp] + __popc(ball & ((1u << lane) - 1u));
+    __syncthreads();  // s_wcnt / s_base are rewritten in the next round
     if (keep) {
       if (slot < (unsigned long long)a.cap) {
         store_write_p(a.out, slot, p);
@@ -226,6 +252,21 @@ __global__ void __launch_bounds__(256) k_push(PushArgs<S> a) {
         atomicOr(&a.cnt->error, ERR_CAPACITY);
       }
     }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int s = a.species;
+    if (s_abs[0]) {
+      atomicAdd(&a.cnt->abs_cathode[s], s_abs[0]);
+      atomicAdd(&a.cnt->abs_energy_cathode[s], s_eabs[0]);
+      atomicAdd(&a.cnt->q_cathode_step, s_q[0]);
+    }
+    if (s_abs[1]) {
+      atomicAdd(&a.cnt->abs_anode[s], s_abs[1]);
+      atomicAdd(&a.cnt->abs_energy_anode[s], s_eabs[1]);
+      atomicAdd(&a.cnt->q_anode_step, s_q[1]);
+    }
+    if (s_el) atomicAdd(&a.cnt->n_el, s_el);
   }
 }
 

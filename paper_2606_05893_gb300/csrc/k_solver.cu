@@ -15,6 +15,8 @@
 // device; the host reads one residual norm per iteration to stop.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "pic_internal.cuh"
@@ -112,48 +114,6 @@ __global__ void __launch_bounds__(kSB) k_dot(long long n, const T* __restrict__ 
   block_partial<T, T>(acc, part);
 }
 
-// x += alpha p ; r -= alpha q ; part = r . r
-template <class T>
-__global__ void __launch_bounds__(kSB) k_update(long long n, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-                                                const T* __restrict__ q, const CgScalars* sc, double* part) {
-  const T alpha = (T)sc->alpha;
-  T acc = 0;
-  for (long long u = gtid(); u < n; u += gstride()) {
-    x[u] += alpha * p[u];
-    const T rv = r[u] - alpha * q[u];
-    r[u] = rv;
-    acc += rv * rv;
-  }
-  block_partial<T, T>(acc, part);
-}
-
-// p = z + beta p
-template <class T>
-__global__ void __launch_bounds__(kSB) k_pupdate(long long n, T* __restrict__ p, const T* __restrict__ z, const CgScalars* sc) {
-  const T beta = (T)sc->beta;
-  for (long long u = gtid(); u < n; u += gstride()) p[u] = z[u] + beta * p[u];
-}
-
-// scalar updates from the block partials (single thread, fixed order)
-enum { SC_RZ = 0, SC_PQ = 1, SC_RR = 2, SC_BB = 3 };
-__global__ void k_scalars(const double* part, int nparts, int which, CgScalars* sc) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double s = 0.0;
-  for (int i = 0; i < nparts; ++i) s += part[i];
-  if (which == SC_RZ) {
-    sc->beta = sc->it > 0 ? s / sc->rz : 0.0;
-    sc->rz = s;
-  } else if (which == SC_PQ) {
-    sc->pq = s;
-    sc->alpha = s != 0.0 ? sc->rz / s : 0.0;
-    sc->it += 1;
-  } else if (which == SC_RR) {
-    sc->rr = s;
-  } else {
-    sc->bb = s;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // multigrid pieces
 // ---------------------------------------------------------------------------
@@ -223,15 +183,16 @@ __global__ void __launch_bounds__(kSB) k_prolong(Lv F, Lv Cc, const T* __restric
     const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (kn & 1) ? 2 : 1;
     const T w = (T)1 / (T)(ni * nj * nk);
     T s = 0;
+    const int I1 = I0 + 1 == Cc.nx ? 0 : I0 + 1;
+    const int J1 = J0 + 1 == Cc.ny ? 0 : J0 + 1;
     for (int c = 0; c < nk; ++c) {
       const int K = K0 + c;  // coarse node
       if (K <= 0 || K >= Cc.nz) continue;
+      const long long pk = (long long)(K - 1) * Cc.pl;
       for (int b2 = 0; b2 < nj; ++b2) {
-        const int J = (J0 + b2) % Cc.ny;
-        for (int a2 = 0; a2 < ni; ++a2) {
-          const int I = (I0 + a2) % Cc.nx;
-          s += ec[(long long)(K - 1) * Cc.pl + (long long)J * Cc.nx + I];
-        }
+        const long long row = pk + (long long)(b2 ? J1 : J0) * Cc.nx;
+        s += ec[row + I0];
+        if (ni == 2) s += ec[row + I1];
       }
     }
     ef[u] += w * s;
@@ -444,7 +405,144 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// PCG on level 0: x (in/out), b; vectors r, z, p, q (type T)
+// Device-controlled solve. All scalars live in SolveCtl on the device; the
+// stopping decisions set the conditional handles of two nested WHILE nodes of a
+// CUDA graph (outer: FP64 true residual / refinement; inner: PCG iterations),
+// so a solve is one graph launch with no host round trip.
+// ---------------------------------------------------------------------------
+constexpr int kFinBlock = 512;
+// Sum of the block partials by one block of kFinBlock threads, in a fixed order
+// (strided per-thread sums, then a shared-memory tree); returns the total in
+// every thread.
+__device__ __forceinline__ double sum_parts(const double* part, int n) {
+  __shared__ double sm[kFinBlock];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += kFinBlock) s += part[i];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kFinBlock / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double t = sm[0];
+  __syncthreads();
+  return t;
+}
+
+__global__ void k_fin_bb(const double* part, int nparts, SolveCtl* c, double rtol, int maxit) {
+  const double bb = sum_parts(part, nparts);
+  if (threadIdx.x != 0) return;
+  c->bb = bb;
+  c->tol2 = rtol * rtol * bb;
+  c->it_total = 0;
+  c->outer = 0;
+  c->converged = bb == 0.0 ? 1 : 0;
+  c->maxit = maxit;
+  c->rr_true = 0.0;
+  c->resid_rel = 0.0;
+}
+
+// r_in = (Tin)(b - A x) with x, b FP64; d = 0; partial sums of r.r (FP64)
+template <class Tin>
+__global__ void __launch_bounds__(kSB) k_residual_prep(Lv L, const double* __restrict__ x, const double* __restrict__ b,
+                                                       Tin* __restrict__ r_in, Tin* __restrict__ d, double* part,
+                                                       const SolveCtl* c) {
+  double acc = 0.0;
+  const bool zero_x = c->bb == 0.0;
+  for (long long u = gtid(); u < L.nu; u += gstride()) {
+    int i, j, k;
+    uijk(L, u, i, j, k);
+    const double rv = zero_x ? 0.0 : b[u] - (6.0 * x[u] - nb_sum(L, x, u, i, j, k));
+    r_in[u] = (Tin)rv;
+    d[u] = (Tin)0;
+    acc += rv * rv;
+  }
+  block_partial<double, double>(acc, part);
+}
+
+__global__ void k_fin_outer(const double* part, int nparts, SolveCtl* c, cudaGraphConditionalHandle h_outer,
+                            cudaGraphConditionalHandle h_inner, double inner_rtol, int mixed, int max_outer, int use_graph) {
+  const double rr = sum_parts(part, nparts);
+  if (threadIdx.x != 0) return;
+  c->rr_true = rr;
+  c->resid_rel = c->bb > 0.0 ? sqrt(rr / c->bb) : 0.0;
+  const bool done = c->bb == 0.0 || rr <= c->tol2 || !(rr == rr) || c->it_total >= c->maxit || c->outer >= max_outer;
+  c->converged = (c->bb == 0.0 || rr <= c->tol2) ? 1 : 0;
+  c->rr = rr;
+  c->it_inner = 0;
+  c->tol_in2 = mixed ? fmax(inner_rtol * inner_rtol * rr, 0.25 * c->tol2) : c->tol2;
+  c->outer += 1;
+  c->more = done ? 0 : 1;
+  if (use_graph) {
+    cudaGraphSetConditional(h_outer, done ? 0u : 1u);
+    cudaGraphSetConditional(h_inner, done ? 0u : 1u);
+  }
+}
+
+__global__ void k_fin_rz(const double* part, int nparts, SolveCtl* c) {
+  const double rz = sum_parts(part, nparts);
+  if (threadIdx.x != 0) return;
+  c->beta = c->it_inner > 0 ? rz / c->rz : 0.0;
+  c->rz = rz;
+}
+
+__global__ void k_fin_pq(const double* part, int nparts, SolveCtl* c) {
+  const double pq = sum_parts(part, nparts);
+  if (threadIdx.x != 0) return;
+  c->pq = pq;
+  c->alpha = pq != 0.0 ? c->rz / pq : 0.0;
+}
+
+__global__ void k_fin_rr(const double* part, int nparts, SolveCtl* c, cudaGraphConditionalHandle h_inner, int use_graph) {
+  const double rr = sum_parts(part, nparts);
+  if (threadIdx.x != 0) return;
+  c->rr = rr;
+  c->it_inner += 1;
+  c->it_total += 1;
+  const bool more = rr > c->tol_in2 && c->it_total < c->maxit && (rr == rr);
+  c->more = more ? 1 : 0;
+  if (use_graph) cudaGraphSetConditional(h_inner, more ? 1u : 0u);
+}
+
+// p = z (first iteration of this inner solve) or z + beta p
+template <class T>
+__global__ void __launch_bounds__(kSB) k_pupdate_c(long long n, T* __restrict__ p, const T* __restrict__ z, const SolveCtl* c) {
+  const bool first = c->it_inner == 0;
+  const T beta = (T)c->beta;
+  for (long long u = gtid(); u < n; u += gstride()) p[u] = first ? z[u] : z[u] + beta * p[u];
+}
+
+// d += alpha p ; r -= alpha q ; partial r.r
+template <class T>
+__global__ void __launch_bounds__(kSB) k_update_c(long long n, T* __restrict__ d, T* __restrict__ r, const T* __restrict__ p,
+                                                  const T* __restrict__ q, const SolveCtl* c, double* part) {
+  const T alpha = (T)c->alpha;
+  T acc = 0;
+  for (long long u = gtid(); u < n; u += gstride()) {
+    d[u] += alpha * p[u];
+    const T rv = r[u] - alpha * q[u];
+    r[u] = rv;
+    acc += rv * rv;
+  }
+  block_partial<T, T>(acc, part);
+}
+
+// x += d (FP64); optionally phi32 = (float)(x - phi_vac(z)) on the same nodes
+template <class T>
+__global__ void __launch_bounds__(kSB) k_axpy_out(Lv L, double* __restrict__ x, const T* __restrict__ d, float* __restrict__ phi32,
+                                                  double phi_c, double dphi_dk) {
+  for (long long u = gtid(); u < L.nu; u += gstride()) {
+    const double v = x[u] + (double)d[u];
+    x[u] = v;
+    if (phi32) {
+      const int k = (int)(u / L.pl) + 1;  // node plane
+      phi32[u] = (float)(v - (phi_c + dphi_dk * (double)k));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side: buffers
 // ---------------------------------------------------------------------------
 template <class T>
 cudaError_t Pcg<T>::init(const std::vector<MgLevel>& plan) {
@@ -455,9 +553,9 @@ cudaError_t Pcg<T>::init(const std::vector<MgLevel>& plan) {
   if ((err = cudaMalloc(&z, bytes))) return err;
   if ((err = cudaMalloc(&p, bytes))) return err;
   if ((err = cudaMalloc(&q, bytes))) return err;
-  if ((err = cudaMalloc(&part, sizeof(double) * kMaxRedBlocks))) return err;
-  if ((err = cudaMalloc(&sc, sizeof(CgScalars)))) return err;
-  if ((err = cudaMallocHost(&host_sc, sizeof(CgScalars)))) return err;
+  if ((err = cudaMalloc(&d, bytes))) return err;
+  if ((err = cudaMemset(p, 0, bytes))) return err;
+  if ((err = cudaMemset(d, 0, bytes))) return err;
   return mg.init(plan);
 }
 
@@ -467,48 +565,9 @@ void Pcg<T>::release() {
   cudaFree(z);
   cudaFree(p);
   cudaFree(q);
-  cudaFree(part);
-  cudaFree(sc);
-  if (host_sc) cudaFreeHost(host_sc);
-  host_sc = nullptr;
+  cudaFree(d);
+  r = z = p = q = d = nullptr;
   mg.release();
-}
-
-template <class T>
-double Pcg<T>::read_scalar(int which, cudaStream_t s) {
-  cudaMemcpyAsync(host_sc, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
-  cudaStreamSynchronize(s);
-  return which == SC_RR ? host_sc->rr : host_sc->bb;
-}
-
-// Solve A x = b from the initial x until sqrt(r.r) <= tol_abs (recursive
-// residual) or maxit; r must hold b - A x on entry and rr its squared norm.
-template <class T>
-int Pcg<T>::iterate(T* x, double rr0, double tol_abs, int maxit, cudaStream_t s, double* rr_out) {
-  const Lv L = lv_of(mg.levels[0]);
-  const int G = sgrid(n);
-  CgScalars zero{};
-  cudaMemcpyAsync(sc, &zero, sizeof(CgScalars), cudaMemcpyHostToDevice, s);
-  double rr = rr0;
-  int it = 0;
-  while (std::sqrt(rr) > tol_abs && it < maxit) {
-    mg.vcycle(r, z, s);
-    PIC_LAUNCH(G, kSB, 0, s, k_dot<T>)(n, r, z, part);
-    PIC_LAUNCH(1, 1, 0, s, k_scalars)(part, G, SC_RZ, sc);
-    if (it == 0)
-      PIC_LAUNCH(G, kSB, 0, s, k_copy<T>)(n, p, z);
-    else
-      PIC_LAUNCH(G, kSB, 0, s, k_pupdate<T>)(n, p, z, sc);
-    PIC_LAUNCH(G, kSB, 0, s, k_apply_dot<T>)(L, p, q, part);
-    PIC_LAUNCH(1, 1, 0, s, k_scalars)(part, G, SC_PQ, sc);
-    PIC_LAUNCH(G, kSB, 0, s, k_update<T>)(n, x, r, p, q, sc, part);
-    PIC_LAUNCH(1, 1, 0, s, k_scalars)(part, G, SC_RR, sc);
-    rr = read_scalar(SC_RR, s);
-    ++it;
-    if (!std::isfinite(rr)) break;
-  }
-  *rr_out = rr;
-  return it;
 }
 
 template struct Mg<double>;
@@ -516,89 +575,223 @@ template struct Mg<float>;
 template struct Pcg<double>;
 template struct Pcg<float>;
 
-// ---------------------------------------------------------------------------
-// Solver front ends
-// ---------------------------------------------------------------------------
 cudaError_t Solver::init(int nx, int ny, int nz, int precision_) {
   precision = precision_;
   plan = mg_plan(nx, ny, nz);
   n = plan[0].nu;
   cudaError_t err;
   if ((err = cudaMalloc(&b, sizeof(double) * (size_t)(n > 0 ? n : 1)))) return err;
+  if ((err = cudaMemset(b, 0, sizeof(double) * (size_t)(n > 0 ? n : 1)))) return err;
   if ((err = cudaMalloc(&part, sizeof(double) * kMaxRedBlocks))) return err;
-  if ((err = cudaMalloc(&sc, sizeof(CgScalars)))) return err;
-  if ((err = cudaMallocHost(&host_sc, sizeof(CgScalars)))) return err;
+  if ((err = cudaMalloc(&ctl, sizeof(SolveCtl)))) return err;
+  if ((err = cudaMemset(ctl, 0, sizeof(SolveCtl)))) return err;
+  if ((err = cudaMallocHost(&host_ctl, sizeof(SolveCtl)))) return err;
+  memset(host_ctl, 0, sizeof(SolveCtl));
   if (precision == 0) return p64.init(plan);
-  if ((err = cudaMalloc(&r64, sizeof(double) * (size_t)(n > 0 ? n : 1)))) return err;
-  if ((err = cudaMalloc(&d32, sizeof(float) * (size_t)(n > 0 ? n : 1)))) return err;
   return p32.init(plan);
 }
 
 void Solver::release() {
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  exec = nullptr;
+  graph = nullptr;
   cudaFree(b);
   cudaFree(part);
-  cudaFree(sc);
-  if (host_sc) cudaFreeHost(host_sc);
-  host_sc = nullptr;
-  cudaFree(r64);
-  cudaFree(d32);
+  cudaFree(ctl);
+  if (host_ctl) cudaFreeHost(host_ctl);
+  host_ctl = nullptr;
+  b = nullptr;
+  part = nullptr;
+  ctl = nullptr;
   p64.release();
   p32.release();
 }
 
-double Solver::reduce_host(int G, cudaStream_t s) {
-  PIC_LAUNCH(1, 1, 0, s, k_scalars)(part, G, SC_BB, sc);
-  cudaMemcpyAsync(host_sc, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
-  cudaStreamSynchronize(s);
-  return host_sc->bb;
+// One PCG iteration on the level-0 vectors of `pc` (captured into the inner body).
+template <class T>
+static void capture_pcg_iteration(Pcg<T>& pc, const Lv& L, double* part, SolveCtl* ctl,
+                                  cudaGraphConditionalHandle h_inner, cudaStream_t s, int use_graph = 1) {
+  const int G = sgrid(L.nu);
+  pc.mg.vcycle(pc.r, pc.z, s);
+  PIC_LAUNCH(G, kSB, 0, s, k_dot<T>)(L.nu, pc.r, pc.z, part);
+  PIC_LAUNCH(1, kFinBlock, 0, s, k_fin_rz)(part, G, ctl);
+  PIC_LAUNCH(G, kSB, 0, s, k_pupdate_c<T>)(L.nu, pc.p, pc.z, ctl);
+  PIC_LAUNCH(G, kSB, 0, s, k_apply_dot<T>)(L, pc.p, pc.q, part);
+  PIC_LAUNCH(1, kFinBlock, 0, s, k_fin_pq)(part, G, ctl);
+  PIC_LAUNCH(G, kSB, 0, s, k_update_c<T>)(L.nu, pc.d, pc.r, pc.p, pc.q, ctl, part);
+  PIC_LAUNCH(1, kFinBlock, 0, s, k_fin_rr)(part, G, ctl, h_inner, use_graph);
 }
 
-// x: unknown-node view of phi (nodes k = 1..nz-1, contiguous); b must be set.
-SolveResult Solver::solve(double* x, double rtol, int maxit, cudaStream_t s) {
-  SolveResult res{0, 0.0, true};
+// Add a WHILE node at the current capture position of `s`; returns its body graph.
+static cudaError_t add_while(cudaStream_t s, cudaGraphConditionalHandle* h, unsigned default_value, cudaGraph_t* body) {
+  cudaStreamCaptureStatus status;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &status, nullptr, &g, &deps, &edges, &ndeps);
+  if (e != cudaSuccess) return e;
+  if (status != cudaStreamCaptureStatusActive) return cudaErrorIllegalState;
+  e = cudaGraphConditionalHandleCreate(h, g, default_value, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = *h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, edges, ndeps, &np);
+  if (e != cudaSuccess) return e;
+  *body = np.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// Record the solve of A x = b (x = unknown view of phi) for this instance.
+cudaError_t Solver::build_graph(double* x, float* phi32, double phi_c, double phi_a, int nz, double rtol, int maxit) {
+  if (exec) return cudaSuccess;
+  hx = x;
+  hphi32 = phi32;
+  h_phi_c = phi_c;
+  h_dphi_dk = (phi_a - phi_c) / (double)nz;
+  h_rtol = rtol;
+  h_maxit = maxit;
+  const char* env = getenv("PIC_SOLVER_GRAPH");
+  if (env && env[0] == '0') return cudaSuccess;  // host-driven loop (profilers cannot see conditional graphs)
   const Lv L = lv_of(plan[0]);
-  const int G = sgrid(n);
-  if (n == 0) return res;
-  PIC_LAUNCH(G, kSB, 0, s, k_dot<double>)(n, b, b, part);
-  const double bb = reduce_host(G, s);
-  if (bb == 0.0) {
-    PIC_LAUNCH(G, kSB, 0, s, k_zero<double>)(n, x);
-    return res;
-  }
-  const double tol = rtol * std::sqrt(bb);
-  int total = 0;
-  double rr_true = 0.0;
-  if (precision == 0) {
-    for (int restart = 0; restart < 8; ++restart) {
-      PIC_LAUNCH(G, kSB, 0, s, k_residual<double, double>)(L, x, b, p64.r, part);
-      const double rr = reduce_host(G, s);
-      rr_true = rr;
-      if (std::sqrt(rr) <= tol || total >= maxit) break;
-      double rr_end = 0.0;
-      total += p64.iterate(x, rr, tol, maxit - total, s, &rr_end);
-      if (!std::isfinite(rr_end)) break;
+  const int G = sgrid(L.nu);
+  const int mixed = precision != 0;
+  const double dphi_dk = (phi_a - phi_c) / (double)nz;
+  cudaStream_t s0 = nullptr, s1 = nullptr, s2 = nullptr;
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking))) return e;
+  if ((e = cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking))) return e;
+  if ((e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking))) return e;
+  cudaGraphConditionalHandle h_outer, h_inner;
+  cudaGraph_t outer_body = nullptr, inner_body = nullptr;
+  e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    PIC_LAUNCH(G, kSB, 0, s0, k_dot<double>)(L.nu, b, b, part);
+    PIC_LAUNCH(1, kFinBlock, 0, s0, k_fin_bb)(part, G, ctl, rtol, maxit);
+    e = add_while(s0, &h_outer, 1u, &outer_body);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s1, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      if (mixed) {
+        PIC_LAUNCH(G, kSB, 0, s1, k_residual_prep<float>)(L, x, b, p32.r, p32.d, part, ctl);
+      } else {
+        PIC_LAUNCH(G, kSB, 0, s1, k_residual_prep<double>)(L, x, b, p64.r, p64.d, part, ctl);
+      }
+      e = cudaGraphConditionalHandleCreate(&h_inner, outer_body, 0u, 0);
+      if (e == cudaSuccess)
+        PIC_LAUNCH(1, kFinBlock, 0, s1, k_fin_outer)(part, G, ctl, h_outer, h_inner, inner_rtol, mixed, max_outer, 1);
+      if (e == cudaSuccess) {
+        // inner WHILE node in the outer body
+        cudaStreamCaptureStatus status;
+        cudaGraph_t g;
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* edges = nullptr;
+        size_t ndeps = 0;
+        e = cudaStreamGetCaptureInfo(s1, &status, nullptr, &g, &deps, &edges, &ndeps);
+        if (e == cudaSuccess) {
+          cudaGraphNodeParams np = {};
+          np.type = cudaGraphNodeTypeConditional;
+          np.conditional.handle = h_inner;
+          np.conditional.type = cudaGraphCondTypeWhile;
+          np.conditional.size = 1;
+          cudaGraphNode_t node;
+          e = cudaGraphAddNode(&node, g, deps, edges, ndeps, &np);
+          if (e == cudaSuccess) {
+            inner_body = np.conditional.phGraph_out[0];
+            e = cudaStreamUpdateCaptureDependencies(s1, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+          }
+        }
+      }
+      if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s2, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        if (mixed) capture_pcg_iteration(p32, L, part, ctl, h_inner, s2);
+        else capture_pcg_iteration(p64, L, part, ctl, h_inner, s2);
+        cudaGraph_t tmp;
+        e = cudaStreamEndCapture(s2, &tmp);
+      }
+      if (e == cudaSuccess) {
+        if (mixed) {
+          PIC_LAUNCH(G, kSB, 0, s1, k_axpy_out<float>)(L, x, p32.d, phi32, phi_c, dphi_dk);
+        } else {
+          PIC_LAUNCH(G, kSB, 0, s1, k_axpy_out<double>)(L, x, p64.d, nullptr, phi_c, dphi_dk);
+        }
+      }
+      cudaGraph_t tmp1;
+      cudaError_t e1 = cudaStreamEndCapture(s1, &tmp1);
+      if (e == cudaSuccess) e = e1;
     }
-  } else {
-    // iterative refinement: FP64 residual and update, FP32 correction solve
-    for (int outer = 0; outer < 40; ++outer) {
-      PIC_LAUNCH(G, kSB, 0, s, k_residual<double, double>)(L, x, b, r64, part);
-      const double rr = reduce_host(G, s);
-      rr_true = rr;
-      if (std::sqrt(rr) <= tol || total >= maxit || !std::isfinite(rr)) break;
-      // r32 = r64, d = 0; inner PCG on A d = r to inner_rtol relative
-      PIC_LAUNCH(G, kSB, 0, s, k_copy_cast)(n, p32.r, r64);
-      PIC_LAUNCH(G, kSB, 0, s, k_zero<float>)(n, d32);
-      double rr_end = 0.0;
-      const double tol_in = std::max(inner_rtol * std::sqrt(rr), 0.5 * tol);
-      total += p32.iterate(d32, rr, tol_in, maxit - total, s, &rr_end);
-      PIC_LAUNCH(G, kSB, 0, s, k_axpy_cast<float>)(n, x, d32);
-    }
+    cudaGraph_t whole = nullptr;
+    cudaError_t e0 = cudaStreamEndCapture(s0, &whole);
+    if (e == cudaSuccess) e = e0;
+    graph = whole;
   }
-  res.iters = total;
-  res.resid_rel = std::sqrt(rr_true / bb);
-  res.converged = res.resid_rel <= rtol;
-  return res;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaStreamDestroy(s0);
+  cudaStreamDestroy(s1);
+  cudaStreamDestroy(s2);
+  if (e != cudaSuccess) {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    cudaGetLastError();
+  }
+  return e;
 }
 
+cudaError_t Solver::launch(cudaStream_t s) {
+  if (exec) {
+    ++g_launches;
+    return cudaGraphLaunch(exec, s);
+  }
+  return run_host(s);
+}
+
+// The same kernels driven from the host, one read-back per decision.
+cudaError_t Solver::run_host(cudaStream_t s) {
+  const Lv L = lv_of(plan[0]);
+  const int G = sgrid(L.nu);
+  const int mixed = precision != 0;
+  const cudaGraphConditionalHandle none = 0;
+  auto read = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(host_ctl, ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+  };
+  PIC_LAUNCH(G, kSB, 0, s, k_dot<double>)(L.nu, b, b, part);
+  PIC_LAUNCH(1, kFinBlock, 0, s, k_fin_bb)(part, G, ctl, h_rtol, h_maxit);
+  for (int outer = 0; outer < max_outer + 1; ++outer) {
+    if (mixed) PIC_LAUNCH(G, kSB, 0, s, k_residual_prep<float>)(L, hx, b, p32.r, p32.d, part, ctl);
+    else PIC_LAUNCH(G, kSB, 0, s, k_residual_prep<double>)(L, hx, b, p64.r, p64.d, part, ctl);
+    PIC_LAUNCH(1, kFinBlock, 0, s, k_fin_outer)(part, G, ctl, none, none, inner_rtol, mixed, max_outer, 0);
+    cudaError_t e = read();
+    if (e != cudaSuccess) return e;
+    const bool go = host_ctl->more != 0;
+    while (go) {
+      if (mixed) capture_pcg_iteration(p32, L, part, ctl, none, s, 0);
+      else capture_pcg_iteration(p64, L, part, ctl, none, s, 0);
+      if ((e = read()) != cudaSuccess) return e;
+      if (!host_ctl->more) break;
+    }
+    if (mixed) PIC_LAUNCH(G, kSB, 0, s, k_axpy_out<float>)(L, hx, p32.d, hphi32, h_phi_c, h_dphi_dk);
+    else PIC_LAUNCH(G, kSB, 0, s, k_axpy_out<double>)(L, hx, p64.d, nullptr, h_phi_c, h_dphi_dk);
+    if (!go) break;
+  }
+  return cudaGetLastError();
+}
+
+SolveResult Solver::result(cudaStream_t s) {
+  cudaMemcpyAsync(host_ctl, ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  SolveResult r;
+  r.iters = host_ctl->it_total;
+  r.resid_rel = host_ctl->resid_rel;
+  r.converged = host_ctl->converged != 0;
+  return r;
+}
 
 }  // namespace pic

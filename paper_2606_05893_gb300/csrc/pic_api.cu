@@ -132,6 +132,8 @@ struct Instance {
   double* phi = nullptr;
   double4_32a* E64 = nullptr;
   float4* E32 = nullptr;
+  float* phi32 = nullptr;  // MIXED: (float)(phi - vacuum potential) at nodes
+  float* acc8 = nullptr;   // MIXED: cell-centric deposit accumulator (8 per cell)
   int32_t* ncount[kMaxSpecies]{};
   // ionization bookkeeping
   int ion_ch = -1;  // index into xs of the ionization channel
@@ -236,6 +238,8 @@ void free_instance(Instance* I) {
   cudaFree(I->phi);
   cudaFree(I->E64);
   cudaFree(I->E32);
+  cudaFree(I->phi32);
+  cudaFree(I->acc8);
   cudaFree(I->ev);
   cudaFree(I->cand);
   cudaFree(I->ev_head);
@@ -489,8 +493,15 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
   CK(h, cudaMalloc(&I->scan_tmp, scan_temp_bytes(g.ncell)));
   CK(h, dalloc(&I->red, 64));
 
+  if (I->mixed) {
+    CK(h, dalloc(&I->phi32, g.nnode));
+    CK(h, cudaMemset(I->phi32, 0, sizeof(float) * g.nnode));
+  }
   cudaError_t se = I->solver.init(c.nx, c.ny, c.nz, c.precision == PIC_MIXED ? 1 : 0);
   if (se != cudaSuccess) return fail(h, PIC_ENOMEM, "solver allocation: %s", cudaGetErrorString(se));
+  se = I->solver.build_graph(I->phi + g.nplane, I->mixed ? I->phi32 + g.nplane : nullptr, c.phi_cathode_V,
+                             c.phi_anode_V, c.nz, c.cg_rtol, c.cg_maxit);
+  if (se != cudaSuccess) return fail(h, PIC_ECUDA, "recording the solver graph failed: %s", cudaGetErrorString(se));
   return PIC_OK;
 }
 
@@ -651,13 +662,12 @@ pic_status step_instance(pic_handle* h, Instance* I) {
   launch_rhs(g, I->rho64, I->rho32, I->solver.b, st);
   double* x = I->phi + g.nplane;
   if (I->cfg.warm_start == PIC_WARM_ZERO) CK(h, cudaMemsetAsync(x, 0, sizeof(double) * I->solver.n, st));
-  I->last = I->solver.solve(x, I->cfg.cg_rtol, I->cfg.cg_maxit, st);
-  if (!I->last.converged) h->sticky |= 1;
+  CK(h, I->solver.launch(st));
   T.end(st);
   // a5 node field
   T.begin(PIC_PH_EFIELD, st);
   if (I->mixed)
-    launch_efield32(g, I->phi, I->E32, st);
+    launch_efield32f(g, I->phi32, I->E32, st);
   else
     launch_efield64(g, I->phi, I->E64, st);
   T.end(st);
@@ -917,6 +927,10 @@ pic_status pic_step(pic_handle* h, int32_t nsteps) {
   }
   // device-side error flags (capacity, event overflow) of the completed steps
   for (auto* I : h->inst) {
+    if (nsteps > 0) {
+      I->last = I->solver.result(h->stream);
+      if (!I->last.converged) h->sticky |= 1;
+    }
     if (I->host_cnt) {
       pic_status st = sync_counters(h, I);
       if (st != PIC_OK) {
@@ -1082,11 +1096,20 @@ pic_status pic_solve(pic_handle* h, int32_t inst, const double* rho, double* phi
   CK(h, dalloc(&dphi, g.nnode));
   CK(h, cudaMemcpyAsync(drho, rho, sizeof(double) * g.nnode, cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaMemcpyAsync(dphi, phi, sizeof(double) * g.nnode, cudaMemcpyHostToDevice, h->stream));
+  // the recorded solver works on the instance's phi: keep it in dphi meanwhile
   launch_phi_planes(g, dphi, h->stream);
-  launch_rhs(g, drho, nullptr, I->solver.b, h->stream);
-  SolveResult r = I->solver.solve(dphi + g.nplane, I->cfg.cg_rtol, I->cfg.cg_maxit, h->stream);
-  CK(h, cudaMemcpyAsync(phi, dphi, sizeof(double) * g.nnode, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaMemcpyAsync(drho, I->phi, sizeof(double) * g.nnode, cudaMemcpyDeviceToDevice, h->stream));
+  double* drho_in = nullptr;
+  CK(h, dalloc(&drho_in, g.nnode));
+  CK(h, cudaMemcpyAsync(drho_in, rho, sizeof(double) * g.nnode, cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(I->phi, dphi, sizeof(double) * g.nnode, cudaMemcpyDeviceToDevice, h->stream));
+  launch_rhs(g, drho_in, nullptr, I->solver.b, h->stream);
+  CK(h, I->solver.launch(h->stream));
+  CK(h, cudaMemcpyAsync(phi, I->phi, sizeof(double) * g.nnode, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaMemcpyAsync(I->phi, drho, sizeof(double) * g.nnode, cudaMemcpyDeviceToDevice, h->stream));
+  SolveResult r = I->solver.result(h->stream);
   cudaError_t e = cudaStreamSynchronize(h->stream);
+  cudaFree(drho_in);
   cudaFree(drho);
   cudaFree(dphi);
   if (e != cudaSuccess) return fail(h, PIC_ECUDA, "solve failed: %s", cudaGetErrorString(e));

@@ -464,6 +464,7 @@ void launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t st);
 void launch_rhs(const Grid& g, const double* rho64, const float* rho32, double* b, cudaStream_t st);
 void launch_efield64(const Grid& g, const double* phi, double4_32a* E, cudaStream_t st);
 void launch_efield32(const Grid& g, const double* phi, float4* E, cudaStream_t st);
+void launch_efield32f(const Grid& g, const float* phi32, float4* E, cudaStream_t st);
 void launch_phi_planes(const Grid& g, double* phi, cudaStream_t st);
 void launch_step_begin(DevCounters* cnt, const int* out_buf, int nsp, cudaStream_t st);
 

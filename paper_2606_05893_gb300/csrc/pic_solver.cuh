@@ -1,4 +1,5 @@
-// pic_solver.cuh -- multigrid-preconditioned CG for the scaled 7-point operator.
+// pic_solver.cuh -- multigrid-preconditioned CG for the scaled 7-point operator,
+// recorded once per instance as a CUDA graph with device-side stopping.
 #pragma once
 
 #include <vector>
@@ -12,10 +13,11 @@ struct MgLevel {
   long long nu;
 };
 
-struct CgScalars {
-  double rz, pq, alpha, beta, rr, bb;
-  int it;
-  int pad;
+// Solver scalars (device resident)
+struct SolveCtl {
+  double bb, tol2, rr_true, resid_rel;
+  double rr, rz, pq, alpha, beta, tol_in2;
+  int it_total, it_inner, outer, maxit, converged, more;
 };
 
 struct SolveResult {
@@ -42,34 +44,41 @@ struct Mg {
 template <class T>
 struct Pcg {
   long long n = 0;
-  T *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
-  double* part = nullptr;
-  CgScalars* sc = nullptr;
-  CgScalars* host_sc = nullptr;
+  T *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *d = nullptr;
   Mg<T> mg;
   cudaError_t init(const std::vector<MgLevel>& plan);
   void release();
-  double read_scalar(int which, cudaStream_t s);
-  int iterate(T* x, double rr0, double tol_abs, int maxit, cudaStream_t s, double* rr_out);
 };
 
+// Solve of A x = b on the unknown nodes. FP64 path: outer loop of FP64 true
+// residuals around an FP64 PCG on the correction (plain restarted PCG).
+// Mixed path: the same loop is iterative refinement, the correction solved by
+// an FP32 PCG to inner_rtol relative to the current residual.
 struct Solver {
   int precision = 0;  // 0 FP64, 1 mixed
   long long n = 0;
   std::vector<MgLevel> plan;
   double* b = nullptr;  // right-hand side over the unknowns
   double* part = nullptr;
-  CgScalars* sc = nullptr;
-  CgScalars* host_sc = nullptr;
-  double* r64 = nullptr;
-  float* d32 = nullptr;
+  SolveCtl* ctl = nullptr;
+  SolveCtl* host_ctl = nullptr;
   double inner_rtol = 1e-4;
+  int max_outer = 40;
   Pcg<double> p64;
   Pcg<float> p32;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
   cudaError_t init(int nx, int ny, int nz, int precision);
   void release();
-  double reduce_host(int G, cudaStream_t s);
-  SolveResult solve(double* x, double rtol, int maxit, cudaStream_t s);
+  cudaError_t build_graph(double* x, float* phi32, double phi_c, double phi_a, int nz, double rtol, int maxit);
+  cudaError_t launch(cudaStream_t s);
+  cudaError_t run_host(cudaStream_t s);
+  // arguments of the recorded solve (also used by the host-driven loop)
+  double* hx = nullptr;
+  float* hphi32 = nullptr;
+  double h_phi_c = 0.0, h_dphi_dk = 0.0, h_rtol = 1e-8;
+  int h_maxit = 1;
+  SolveResult result(cudaStream_t s);
 };
 
 }  // namespace pic
