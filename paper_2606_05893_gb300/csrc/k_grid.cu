@@ -198,14 +198,17 @@ __device__ __forceinline__ double3 node_field(const Grid& g, const double* __res
   return e;
 }
 
-__global__ void k_efield64(Grid g, const double* __restrict__ phi, double4_32a* __restrict__ E) {
+// E.w carries the neutral count of the cell whose lower corner is this node
+// (cell and node indices coincide for k < nz), read by the collision filter.
+__global__ void k_efield64(Grid g, const double* __restrict__ phi, double4_32a* __restrict__ E,
+                           const int32_t* __restrict__ ncount) {
   for (long long n = gtid(); n < g.nnode; n += gstride()) {
     const double3 e = node_field(g, phi, n);
     double4_32a v;
     v.x = e.x;
     v.y = e.y;
     v.z = e.z;
-    v.w = 0.0;
+    v.w = (ncount && n < g.ncell) ? (double)ncount[n] : 0.0;
     E[n] = v;
   }
 }
@@ -216,7 +219,8 @@ __global__ void k_efield32(Grid g, const double* __restrict__ phi, float4* __res
   }
 }
 // MIXED: E from the FP32 deviation from the vacuum potential, plus the vacuum field
-__global__ void k_efield32f(Grid g, const float* __restrict__ f, float4* __restrict__ E, float c, float ez_vac) {
+__global__ void k_efield32f(Grid g, const float* __restrict__ f, float4* __restrict__ E, float c, float ez_vac,
+                            const int32_t* __restrict__ ncount) {
   for (long long n = gtid(); n < g.nnode; n += gstride()) {
     const long long pl = g.nplane;
     const int k = (int)(n / pl);
@@ -235,15 +239,15 @@ __global__ void k_efield32f(Grid g, const float* __restrict__ f, float4* __restr
       ez = (-3.f * f[n] + 4.f * f[n - pl] - f[n - 2 * pl]) * c;
     else
       ez = (f[n - pl] - f[n + pl]) * c;
-    E[n] = make_float4(ex, ey, ez + ez_vac, 0.f);
+    E[n] = make_float4(ex, ey, ez + ez_vac, (ncount && n < g.ncell) ? (float)ncount[n] : 0.f);
   }
 }
-void launch_efield32f(const Grid& g, const float* phi32, float4* E, cudaStream_t st) {
+void launch_efield32f(const Grid& g, const float* phi32, float4* E, const int32_t* ncount, cudaStream_t st) {
   const float ez_vac = (float)(-(g.phi_a - g.phi_c) / g.Lz);
-  PIC_LAUNCH(grid_for(g.nnode), kBlock, 0, st, k_efield32f)(g, phi32, E, (float)(0.5 * g.inv_h), ez_vac);
+  PIC_LAUNCH(grid_for(g.nnode), kBlock, 0, st, k_efield32f)(g, phi32, E, (float)(0.5 * g.inv_h), ez_vac, ncount);
 }
-void launch_efield64(const Grid& g, const double* phi, double4_32a* E, cudaStream_t st) {
-  PIC_LAUNCH(grid_for(g.nnode), kBlock, 0, st, k_efield64)(g, phi, E);
+void launch_efield64(const Grid& g, const double* phi, double4_32a* E, const int32_t* ncount, cudaStream_t st) {
+  PIC_LAUNCH(grid_for(g.nnode), kBlock, 0, st, k_efield64)(g, phi, E, ncount);
 }
 void launch_efield32(const Grid& g, const double* phi, float4* E, cudaStream_t st) {
   PIC_LAUNCH(grid_for(g.nnode), kBlock, 0, st, k_efield32)(g, phi, E);

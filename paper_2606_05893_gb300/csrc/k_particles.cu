@@ -18,6 +18,7 @@ namespace pic {
 
 constexpr int kPushBlock = 256;
 constexpr int kPushWarps = kPushBlock / 32;
+constexpr int kIlp = 2;  // particles per thread and round
 
 // ---------------------------------------------------------------------------
 // cross sections
@@ -58,11 +59,14 @@ __device__ int mcc_exact_dt(const McArgs& m, long long cell, double v2, double U
   return a;
 }
 
-// FP32 filter: true when the electron certainly does not collide.
-__device__ __forceinline__ bool mcc_cannot_collide(const McArgs& m, long long cell, float v2f, float U32, float dt_f) {
+// FP32 filter: true when the electron certainly does not collide. cnt0 >= 0 is
+// the target count of the cell taken from the node field (all channels share
+// that target); otherwise the counts are read per channel.
+__device__ __forceinline__ bool mcc_cannot_collide(const McArgs& m, long long cell, float v2f, float U32, float dt_f,
+                                                   float cnt0) {
   float nb = 0.f;
   for (int a = 0; a < m.nch; ++a) {
-    const float cnt = m.bg_mode ? 1.f : (float)m.ncount[a][cell];
+    const float cnt = m.bg_mode ? 1.f : (cnt0 >= 0.f ? cnt0 : (float)m.ncount[a][cell]);
     nb = fmaf(cnt, m.bound_f[a], nb);
   }
   // x_upper = u dt sum n_a max sigma_a >= x >= P; 1.001 covers FP32 rounding
@@ -124,9 +128,11 @@ __global__ void k_inject_commit(DevCounters* cnt, InjectCommit c) {
 // ---------------------------------------------------------------------------
 template <class S, bool CHARGED, bool MCC, bool NEUTRAL>
 __global__ void __launch_bounds__(kPushBlock) k_push(PushArgs<S> a) {
-  // Block-level bookkeeping: absorbed-particle statistics and elastic counts
-  // accumulate in shared memory and reach HBM once per block; output slots are
-  // reserved once per block and round (one global atomic per 256 particles).
+  // Each thread advances kIlp particles per round (their loads are issued
+  // together, so the memory latency of one hides behind the others). Output
+  // slots are reserved once per block and round (one global atomic per
+  // kIlp * 256 particles); absorption statistics and elastic counts accumulate
+  // in shared memory and reach HBM once per block.
   __shared__ unsigned long long s_abs[2];
   __shared__ double s_eabs[2], s_q[2];
   __shared__ unsigned long long s_el;
@@ -143,65 +149,82 @@ __global__ void __launch_bounds__(kPushBlock) k_push(PushArgs<S> a) {
   if (blockIdx.x == 0 && threadIdx.x == 0)
     a.cnt->pushed[a.species] += (unsigned long long)n - (NEUTRAL ? a.cnt->n_tomb[a.species] : 0ull);
   const Grid& g = a.g;
+  const float dt_f = (float)g.dt;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long* out_count = &a.cnt->n[a.cur_in ^ 1][a.species];
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += gstride()) {
-    const long long i = base + threadIdx.x;
-    const bool valid = i < n;
-    bool keep = false, ionize = false;
-    using Particle = typename PTraits<S>::P;
-    Particle p;
-    long long cell_n = 0;
-    int ch_ion = -1;
-    double E_eV = 0.0;
-    if (valid) {
-      p = store_read(a.in, g, i);
-      if (!(NEUTRAL && p.pid == kPidDead)) {  // converted neutrals of the last step are dropped here
-        cell_n = particle_cell(p);
-        if (CHARGED) {
-          const auto e = p.gather(g, a);
-          p.kick(a, e);
-        }
-        const int side = p.drift(g);  // -1 cathode, +1 anode, 0 inside
-        if (side != 0) {
-          const int b = side < 0 ? 0 : 1;
-          const double ke = 0.5 * a.mass * a.weight * p.v2();
-          atomicAdd(&s_abs[b], 1ull);
-          atomicAdd(&s_eabs[b], ke);
-          atomicAdd(&s_q[b], a.charge * a.weight);
-        } else {
-          keep = true;
-          if (MCC) {
-            const uint4 d = draw(a.mc.key, p.pid, a.mc.step, TAG_MCC);
-            if (!mcc_cannot_collide(a.mc, cell_n, p.v2f(), u01_32(d.x), (float)g.dt)) {
-              const double U = u01_64(d.x, d.y);
-              const double v2 = p.v2();
-              const int ch = mcc_exact_dt(a.mc, cell_n, v2, U, g.dt, &E_eV);
-              if (ch >= 0) {
-                if (a.mc.ch[ch].kind == XS_ELASTIC) {
-                  const uint4 sc = draw(a.mc.key, p.pid, a.mc.step, TAG_SCATTER);
-                  const double ct = 2.0 * u01_64(sc.x, sc.y) - 1.0;
-                  const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
-                  const double ph = 2.0 * kPi * u01_64(sc.z, sc.w);
-                  const double u = sqrt(v2);
-                  p.set_v(u * st * cos(ph), u * st * sin(ph), u * ct);
-                  atomicAdd(&s_el, 1ull);
-                } else if (a.mc.bg_mode) {
-                  // fixed-background test mode: counted, nothing consumed or created
-                  atomicAdd(&a.cnt->n_ion, 1ull);
-                } else {
-                  ionize = true;
-                  ch_ion = ch;
-                }
-              }
+  using Particle = typename PTraits<S>::P;
+  const long long round = (long long)kPushBlock * kIlp;
+  for (long long base = (long long)blockIdx.x * round; base < n; base += (long long)gridDim.x * round) {
+    Particle p[kIlp];
+    bool valid[kIlp], keep[kIlp], ionize[kIlp];
+    long long cell_n[kIlp];
+    int ch_ion[kIlp];
+    double E_eV[kIlp];
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+      const long long i = base + (long long)u * kPushBlock + threadIdx.x;
+      valid[u] = i < n;
+      keep[u] = ionize[u] = false;
+      ch_ion[u] = -1;
+      E_eV[u] = 0.0;
+      cell_n[u] = 0;
+      if (valid[u]) p[u] = store_read(a.in, g, i);
+    }
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+      if (!valid[u]) continue;
+      if (NEUTRAL && p[u].pid == kPidDead) continue;  // converted neutrals of the last step are dropped here
+      cell_n[u] = particle_cell(p[u]);
+      if (CHARGED) {
+        const auto e = p[u].gather(g, a);
+        p[u].kick(a, e);
+      }
+      const int side = p[u].drift(g);  // -1 cathode, +1 anode, 0 inside
+      if (side != 0) {
+        const int b = side < 0 ? 0 : 1;
+        const double ke = 0.5 * a.mass * a.weight * p[u].v2();
+        atomicAdd(&s_abs[b], 1ull);
+        atomicAdd(&s_eabs[b], ke);
+        atomicAdd(&s_q[b], a.charge * a.weight);
+        continue;
+      }
+      keep[u] = true;
+      if (MCC) {
+        const uint4 d = draw(a.mc.key, p[u].pid, a.mc.step, TAG_MCC);
+        const float cnt0 = a.mc.count_in_field ? p[u].nc : -1.f;
+        if (!mcc_cannot_collide(a.mc, cell_n[u], p[u].v2f(), u01_32(d.x), dt_f, cnt0)) {
+          const double U = u01_64(d.x, d.y);
+          const double v2 = p[u].v2();
+          const int ch = mcc_exact_dt(a.mc, cell_n[u], v2, U, g.dt, &E_eV[u]);
+          if (ch >= 0) {
+            if (a.mc.ch[ch].kind == XS_ELASTIC) {
+              const uint4 sc = draw(a.mc.key, p[u].pid, a.mc.step, TAG_SCATTER);
+              const double ct = 2.0 * u01_64(sc.x, sc.y) - 1.0;
+              const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+              const double ph = 2.0 * kPi * u01_64(sc.z, sc.w);
+              const double uu = sqrt(v2);
+              p[u].set_v(uu * st * cos(ph), uu * st * sin(ph), uu * ct);
+              atomicAdd(&s_el, 1ull);
+            } else if (a.mc.bg_mode) {
+              // fixed-background test mode: counted, nothing consumed or created
+              atomicAdd(&a.cnt->n_ion, 1ull);
+            } else {
+              ionize[u] = true;
+              ch_ion[u] = ch;
             }
           }
         }
       }
     }
-    // block-wide slot reservation
-    const unsigned ball = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) s_wcnt[warp] = __popc(ball);
+    // block-wide slot reservation for the whole round
+    unsigned ball[kIlp];
+    unsigned wtot = 0;
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+      ball[u] = __ballot_sync(0xffffffffu, keep[u]);
+      wtot += __popc(ball[u]);
+    }
+    if (lane == 0) s_wcnt[warp] = wtot;
     __syncthreads();
     if (threadIdx.x == 0) {
       unsigned int tot = 0;
@@ -213,43 +236,47 @@ __global__ void __launch_bounds__(kPushBlock) k_push(PushArgs<S> a) {
       s_base = tot ? atomicAdd(out_count, (unsigned long long)tot) : 0ull;
     }
     __syncthreads();
-    const unsigned long long slot = s_base + s_wcnt[warp] + __popc(ball & ((1u << lane) - 1u));
+    unsigned long long wbase = s_base + s_wcnt[warp];
     __syncthreads();  // s_wcnt / s_base are rewritten in the next round
-    if (keep) {
-      if (slot < (unsigned long long)a.cap) {
-        store_write_p(a.out, slot, p);
-        if (ionize) {
-          const unsigned int e = atomicAdd(&a.cnt->n_events, 1u);
-          if (e < (unsigned int)a.ev_cap) {
-            Event ev;
-            ev.pid = p.pid;
-            ev.cell = (uint32_t)cell_n;
-            ev.slot = (uint32_t)slot;
-            ev.ch = ch_ion;
-            ev.E_eV = E_eV;
-            ev.victim = -1;
-            ev.next = atomicExch(&a.ev_head[cell_n], (int)e);
-            a.ev[e] = ev;
-          } else {
-            atomicOr(&a.cnt->error, ERR_EVENTS);
-          }
-        }
-        if (NEUTRAL && a.ev_head != nullptr && a.ev_head[cell_n] >= 0) {
-          // candidate victim of an ionization in its cell at x^n
-          const unsigned int c = atomicAdd(&a.cnt->n_cands, 1u);
-          if (c < (unsigned int)a.cand_cap) {
-            const uint4 k = draw(a.mc.key, p.pid, a.mc.step, TAG_VICTIM);
-            Cand cd;
-            cd.key = ((unsigned long long)k.x << 32) | (unsigned long long)p.pid;
-            cd.slot = (uint32_t)slot;
-            cd.next = atomicExch(&a.cand_head[cell_n], (int)c);
-            a.cand[c] = cd;
-          } else {
-            atomicOr(&a.cnt->error, ERR_EVENTS);
-          }
-        }
-      } else {
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+      const unsigned long long slot = wbase + __popc(ball[u] & ((1u << lane) - 1u));
+      wbase += __popc(ball[u]);
+      if (!keep[u]) continue;
+      if (slot >= (unsigned long long)a.cap) {
         atomicOr(&a.cnt->error, ERR_CAPACITY);
+        continue;
+      }
+      store_write_p(a.out, slot, p[u]);
+      if (ionize[u]) {
+        const unsigned int e = atomicAdd(&a.cnt->n_events, 1u);
+        if (e < (unsigned int)a.ev_cap) {
+          Event ev;
+          ev.pid = p[u].pid;
+          ev.cell = (uint32_t)cell_n[u];
+          ev.slot = (uint32_t)slot;
+          ev.ch = ch_ion[u];
+          ev.E_eV = E_eV[u];
+          ev.victim = -1;
+          ev.next = atomicExch(&a.ev_head[cell_n[u]], (int)e);
+          a.ev[e] = ev;
+        } else {
+          atomicOr(&a.cnt->error, ERR_EVENTS);
+        }
+      }
+      if (NEUTRAL && a.ev_head != nullptr && a.ev_head[cell_n[u]] >= 0) {
+        // candidate victim of an ionization in its cell at x^n
+        const unsigned int c = atomicAdd(&a.cnt->n_cands, 1u);
+        if (c < (unsigned int)a.cand_cap) {
+          const uint4 k = draw(a.mc.key, p[u].pid, a.mc.step, TAG_VICTIM);
+          Cand cd;
+          cd.key = ((unsigned long long)k.x << 32) | (unsigned long long)p[u].pid;
+          cd.slot = (uint32_t)slot;
+          cd.next = atomicExch(&a.cand_head[cell_n[u]], (int)c);
+          a.cand[c] = cd;
+        } else {
+          atomicOr(&a.cnt->error, ERR_EVENTS);
+        }
       }
     }
   }

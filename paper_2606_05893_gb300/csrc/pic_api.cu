@@ -516,6 +516,17 @@ StoreMx store_of<StoreMx>(Instance* I, int s, int b) {
   return I->smx[s][b];
 }
 
+// The neutral species targeted by every collision channel, if there is exactly
+// one (its per-cell count then travels in the 4th component of the node field).
+int field_count_target(const Instance* I) {
+  int t = -1;
+  for (const auto& X : I->xs) {
+    if (t < 0) t = X.c.target;
+    else if (t != X.c.target) return -1;
+  }
+  return t;
+}
+
 McArgs mc_args(Instance* I, int proj) {
   McArgs m{};
   const double inv_h3 = 1.0 / (I->g.h * I->g.h * I->g.h);
@@ -535,6 +546,10 @@ McArgs mc_args(Instance* I, int proj) {
   m.step = I->step;
   m.bg_mode = I->bg_density > 0 ? 1 : 0;
   m.bg_density = I->bg_density;
+  const int ft = field_count_target(I);
+  m.count_in_field = 1;
+  for (int a = 0; a < m.nch; ++a)
+    if (ft < 0 || m.ncount[a] != I->ncount[ft]) m.count_in_field = 0;
   return m;
 }
 
@@ -666,10 +681,14 @@ pic_status step_instance(pic_handle* h, Instance* I) {
   T.end(st);
   // a5 node field
   T.begin(PIC_PH_EFIELD, st);
-  if (I->mixed)
-    launch_efield32f(g, I->phi32, I->E32, st);
-  else
-    launch_efield64(g, I->phi, I->E64, st);
+  {
+    const int ft = field_count_target(I);
+    const int32_t* nc = ft >= 0 ? I->ncount[ft] : nullptr;
+    if (I->mixed)
+      launch_efield32f(g, I->phi32, I->E32, nc, st);
+    else
+      launch_efield64(g, I->phi, I->E64, nc, st);
+  }
   T.end(st);
 
   // a6-a8 + a10 push / absorb / collide / compact: charged species first, then neutrals

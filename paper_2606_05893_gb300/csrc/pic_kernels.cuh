@@ -76,9 +76,10 @@ struct Particle64 {
   uint32_t pid;
   long long cell;  // cell at read time (x^n)
   Loc l;
+  float nc;        // neutral count of the cell (4th component of the node field)
 
   template <class A>
-  __device__ __forceinline__ double3 gather(const Grid& g, const A& a) const {
+  __device__ __forceinline__ double3 gather(const Grid& g, const A& a) {
     long long idx[8];
     corner_nodes(g, l.i, l.j, l.k, idx);
     double w[8];
@@ -90,6 +91,7 @@ struct Particle64 {
       e.x += w[c] * en.x;
       e.y += w[c] * en.y;
       e.z += w[c] * en.z;
+      if (c == 0) nc = (float)en.w;
     }
     return e;
   }
@@ -127,9 +129,10 @@ struct ParticleMx {
   int32_t cell;
   float ox, oy, oz, vx, vy, vz;
   uint32_t pid;
+  float nc;  // neutral count of the cell (4th component of the node field)
 
   template <class A>
-  __device__ __forceinline__ float3 gather(const Grid& g, const A& a) const {
+  __device__ __forceinline__ float3 gather(const Grid& g, const A& a) {
     int i, j, k;
     cell_ijk(g, cell, i, j, k);
     long long idx[8];
@@ -143,6 +146,7 @@ struct ParticleMx {
       e.x = fmaf(w[c], en.x, e.x);
       e.y = fmaf(w[c], en.y, e.y);
       e.z = fmaf(w[c], en.z, e.z);
+      if (c == 0) nc = en.w;
     }
     return e;
   }
@@ -338,6 +342,7 @@ struct McArgs {
   uint32_t step;
   int bg_mode;  // fixed background density (test mode)
   double bg_density;
+  int count_in_field;  // all channels share one target: its cell count rides in E.w
 };
 
 struct StepBegin {
@@ -462,9 +467,9 @@ void launch_fill64(double* p, long long n, double v, cudaStream_t st);
 void launch_fill32(float* p, long long n, float v, cudaStream_t st);
 void launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t st);
 void launch_rhs(const Grid& g, const double* rho64, const float* rho32, double* b, cudaStream_t st);
-void launch_efield64(const Grid& g, const double* phi, double4_32a* E, cudaStream_t st);
+void launch_efield64(const Grid& g, const double* phi, double4_32a* E, const int32_t* ncount, cudaStream_t st);
 void launch_efield32(const Grid& g, const double* phi, float4* E, cudaStream_t st);
-void launch_efield32f(const Grid& g, const float* phi32, float4* E, cudaStream_t st);
+void launch_efield32f(const Grid& g, const float* phi32, float4* E, const int32_t* ncount, cudaStream_t st);
 void launch_phi_planes(const Grid& g, double* phi, cudaStream_t st);
 void launch_step_begin(DevCounters* cnt, const int* out_buf, int nsp, cudaStream_t st);
 

@@ -6,7 +6,10 @@ Per step from an identical state the bounds are |dx| <= 1e-5 h (FP32 offsets
 carry 2^-24 h; a particle crossing up to ~10 cells per step adds the FP32
 velocity error times v dt), |dv| <= 1e-5 max|v|, |drho| <= 1e-6 of the larger of
 max|rho| and the summed magnitude of the contributions to a node (FP32
-accumulation when charges cancel), |dphi| <= 1e-8 max|phi|. Integer outcomes agree
+accumulation when charges cancel), |dphi| <= 1e-7 of the larger of max|phi| and
+the potential scale of that summed charge (the FP32 density error, ~1e-7
+relative, carries into the space-charge part of phi, which can exceed the
+applied potential). Integer outcomes agree
 except where an FP32-rounded position or velocity sits on a decision boundary
 (absorption, cell index, collision draw); over many steps the trajectories
 decorrelate, so the comparison becomes statistical: ensemble means of particle
@@ -69,7 +72,7 @@ def check_step(sim, ref, wl, allow_count=2):
     scale = max(np.abs(rho_o).max(), npc * qw / wl.h ** 3)
     assert np.abs(rho_g - rho_o).max() <= 1e-6 * scale
     phi_g, phi_o = sim.phi(), ref.phi()
-    assert np.abs(phi_g - phi_o).max() <= 1e-8 * max(np.abs(phi_o).max(), qw / (W.EPS0 * wl.h))
+    assert np.abs(phi_g - phi_o).max() <= 1e-7 * max(np.abs(phi_o).max(), npc * qw / (W.EPS0 * wl.h))
 
 
 def test_mixed_one_step_tiny(pkg):
@@ -98,19 +101,24 @@ def test_mixed_subcase_64x64x128(pkg):
     check_step(sim, ref, wl, allow_count=10)
 
 
-def test_solver_host_loop_matches_graph(pkg):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solver_host_loop_matches_graph(pkg, precision):
+    # the recorded graph and the host-driven loop run the same kernels with
+    # fixed-order reductions: identical input, bit-identical phi
     wl = W.config_tiny(seed=2)
-    sims = []
+    rng = np.random.default_rng(3)
+    rho = rng.standard_normal((wl.nz + 1, wl.ny, wl.nx)) * 1e6
+    out = []
     for mode in ("1", "0"):
         os.environ["PIC_SOLVER_GRAPH"] = mode
         try:
-            sims.append(pkg.Simulation(wl, precision=pkg.PIC_MIXED, cg_rtol=1e-12, cg_maxit=5000))
+            sim = pkg.Simulation(wl, precision=precision, cg_rtol=1e-12, cg_maxit=5000, preload=False)
         finally:
             os.environ.pop("PIC_SOLVER_GRAPH", None)
-    for s in sims:
-        s.step(3)
-    assert np.array_equal(sims[0].phi(), sims[1].phi())
-    assert sims[0].moments()["count"] == sims[1].moments()["count"]
+        out.append(sim.solve(rho))
+        sim.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
 
 
 @pytest.mark.parametrize("steps,seeds", [(150, 8)])
