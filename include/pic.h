@@ -250,6 +250,38 @@ pic_status pic_get_phase_times(pic_handle* h, int32_t inst, double* ms, int64_t*
 /* Kernel launches issued by the library in this process so far. */
 uint64_t pic_launch_count(void);
 
+/* ---- solve without allocating ----------------------------------------------
+ * Not in the paper: an entry point for callers that cannot allocate device
+ * memory while they run (programs that hand out all device memory from their
+ * own pool at start-up, or that must keep a fixed footprint between coupling
+ * steps). It solves the same discrete Poisson problem as pic_solve -- Eq. (1)
+ * on the node grid, 7-point operator, periodic x/y, Dirichlet planes
+ * phi(k=0) = phi_cathode_V and phi(k=nz) = phi_anode_V -- by conjugate gradients,
+ * with every work vector in one fixed array inside the library (file-scope
+ * __device__ storage of PIC_STATIC_MAX_UNKNOWNS-sized vectors, about 8 MiB,
+ * held by every GPU that loads the library until the process exits). It calls
+ * no cudaMalloc, cudaFree or other allocating routine.
+ *  rho_dev: device array of (nz+1)*ny*nx doubles, layout [k][j][i] (read only).
+ *  phi_dev: device array of the same size; its interior (k = 1..nz-1) is the
+ *           initial guess on entry; on return it holds the solution and the
+ *           electrode planes hold their potentials. Caller-owned.
+ *  Stops when the recursive residual reaches rtol ||b|| or after maxit
+ *  iterations; the true relative residual is reported in *resid_rel and the
+ *  iteration count in *iters (either may be NULL).
+ * Returns PIC_EINVAL for bad arguments or nx*ny*(nz-1) > PIC_STATIC_MAX_UNKNOWNS
+ * (pic_last_error(NULL) says which), PIC_ENOCONV if rtol was not reached,
+ * PIC_ECUDA on a CUDA error. The first call on a device looks up the address of
+ * the fixed array on that device (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture. All calls share
+ * the array and it keeps the last call's contents (each call writes every
+ * vector before reading it); calls that overlap on the GPU -- on different
+ * streams or from different host threads on the same device -- race on it.
+ * Work runs on cuda_stream, which the call synchronises. */
+#define PIC_STATIC_MAX_UNKNOWNS (1 << 18)
+pic_status pic_poisson_solve_static(int32_t nx, int32_t ny, int32_t nz, double h, double phi_cathode_V,
+                                    double phi_anode_V, const double* rho_dev, double* phi_dev, double rtol,
+                                    int32_t maxit, void* cuda_stream, int32_t* iters, double* resid_rel);
+
 /* Library version string. */
 const char* pic_version(void);
 

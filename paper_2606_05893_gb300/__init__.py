@@ -83,7 +83,7 @@ EXPORTED = ["pic_create", "pic_inject", "pic_inject_particles", "pic_step", "pic
             "pic_last_error", "pic_get_count", "pic_get_particles", "pic_get_field", "pic_set_phi", "pic_solve",
             "pic_sort_now", "pic_get_cell_start", "pic_get_ionization_log", "pic_philox",
             "pic_set_mcc_background", "pic_version", "pic_set_profiling", "pic_get_phase_times",
-            "pic_launch_count"]
+            "pic_launch_count", "pic_poisson_solve_static"]
 
 _lib = None
 
@@ -130,6 +130,8 @@ def load_library(path: str = LIB_PATH):
         "pic_set_profiling": ([P, C.c_int32], st),
         "pic_get_phase_times": ([P, C.c_int32, d, i64], st),
         "pic_launch_count": ([], C.c_uint64),
+        "pic_poisson_solve_static": ([C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, P, P,
+                                      C.c_double, C.c_int32, P, C.POINTER(C.c_int32), d], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -287,6 +289,23 @@ def pic_get_phase_times(h, inst=0):
 
 def pic_launch_count():
     return int(load_library().pic_launch_count())
+
+
+PIC_STATIC_MAX_UNKNOWNS = 1 << 18
+
+
+def pic_poisson_solve_static(nx, ny, nz, h, phi_cathode_V, phi_anode_V, rho_dev_ptr, phi_dev_ptr, rtol, maxit,
+                             stream=None):
+    """No-allocation Poisson solve on caller-owned device buffers (raw pointers,
+    e.g. torch tensor data_ptr()). Returns (status, iterations, relative residual)."""
+    if stream is None:
+        stream = _torch_stream()
+    it = C.c_int32()
+    rel = C.c_double()
+    st = load_library().pic_poisson_solve_static(nx, ny, nz, h, phi_cathode_V, phi_anode_V, C.c_void_p(rho_dev_ptr),
+                                                 C.c_void_p(phi_dev_ptr), rtol, maxit, C.c_void_p(stream),
+                                                 C.byref(it), C.byref(rel))
+    return st, it.value, rel.value
 
 
 def _torch_stream():

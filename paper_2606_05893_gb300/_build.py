@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpic_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["pic_api.cu", "k_particles.cu", "k_grid.cu", "k_solver.cu", "k_sort.cu"]
+SOURCES = ["pic_api.cu", "k_particles.cu", "k_grid.cu", "k_solver.cu", "k_sort.cu", "pic_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--diag-suppress=177,550", "-I", CSRC, "-I", INCLUDE]

@@ -23,6 +23,7 @@ using namespace pic;
 
 namespace pic {
 unsigned long long g_launches = 0;
+void set_static_error(const char* msg);
 }
 
 namespace {
@@ -186,6 +187,12 @@ pic_status fail(pic_handle* h, pic_status st, const char* fmt, ...) {
   else g_static_err = buf;
   return st;
 }
+
+}  // namespace
+
+void pic::set_static_error(const char* msg) { g_static_err = msg; }
+
+namespace {
 
 #define CK(h, call)                                                                             \
   do {                                                                                          \
