@@ -144,22 +144,53 @@ void launch_deposit<StoreMx>(const DepositArgs<StoreMx>& a, int grid, cudaStream
 // a4 right-hand side of Eq. (1) scaled by h^2 over the unknown nodes k = 1..nz-1:
 //   b = h^2 rho / eps0 (+ phi_c on k = 1) (+ phi_a on k = nz-1)
 // ---------------------------------------------------------------------------
-__global__ void k_rhs(Grid g, const double* __restrict__ rho64, const float* __restrict__ rho32, double* __restrict__ b) {
-  const long long nu = (long long)(g.nz - 1) * g.nplane;
+// 3-D launch helpers: block (32, 8), x over i, y strided over j, z over planes
+// (no integer division in the index math).
+static dim3 grid3(const Grid& g, int planes) {
+  int gy = (g.ny + 7) / 8;
+  gy = gy > 4 ? 4 : gy;
+  return dim3((g.nx + 31) / 32, gy, planes);
+}
+static const dim3 kBlk3(32, 8, 1);
+
+__global__ void __launch_bounds__(256) k_rhs(Grid g, const double* __restrict__ rho64, const float* __restrict__ rho32,
+                                             double* __restrict__ b) {
   const double s = g.h * g.h / kEps0;
   const float s32 = (float)s;
-  for (long long u = gtid(); u < nu; u += gstride()) {
+  const int kn = blockIdx.z + 1;  // node plane of this unknown plane
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  if (i >= g.nx) return;
+  const double fold = (kn == 1 ? g.phi_c : 0.0) + (kn == g.nz - 1 ? g.phi_a : 0.0);
+  for (int j = blockIdx.y * 8 + threadIdx.y; j < g.ny; j += gridDim.y * 8) {
+    const long long u = (long long)blockIdx.z * g.nplane + (long long)j * g.nx + i;
     const long long node = u + g.nplane;
-    const int k = (int)(node / g.nplane);
     // MIXED: the density is FP32 already; scale it in FP32 and widen once
     double v = rho64 ? s * rho64[node] : (double)(s32 * rho32[node]);
-    if (k == 1) v += g.phi_c;
-    if (k == g.nz - 1) v += g.phi_a;
-    b[u] = v;
+    b[u] = v + fold;
   }
 }
 void launch_rhs(const Grid& g, const double* rho64, const float* rho32, double* b, cudaStream_t st) {
-  PIC_LAUNCH(grid_for((long long)(g.nz - 1) * g.nplane), kBlock, 0, st, k_rhs)(g, rho64, rho32, b);
+  PIC_LAUNCH(grid3(g, g.nz - 1), kBlk3, 0, st, k_rhs)(g, rho64, rho32, b);
+}
+
+// MIXED path: the FP32 charge term f = fl32(h^2/eps0 rho) over the unknowns,
+// without the folded Dirichlet terms (the solver keeps phi relative to the
+// vacuum potential). From an FP64 density (a caller's rho) the product is FP64,
+// rounded once.
+__global__ void __launch_bounds__(256) k_rhs_f32(Grid g, const double* __restrict__ rho64,
+                                                 const float* __restrict__ rho32, float* __restrict__ f) {
+  const double s = g.h * g.h / kEps0;
+  const float s32 = (float)s;
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  if (i >= g.nx) return;
+  for (int j = blockIdx.y * 8 + threadIdx.y; j < g.ny; j += gridDim.y * 8) {
+    const long long u = (long long)blockIdx.z * g.nplane + (long long)j * g.nx + i;
+    const long long node = u + g.nplane;
+    f[u] = rho32 ? s32 * rho32[node] : (float)(s * rho64[node]);
+  }
+}
+void launch_rhs_f32(const Grid& g, const double* rho64, const float* rho32, float* f, cudaStream_t st) {
+  PIC_LAUNCH(grid3(g, g.nz - 1), kBlk3, 0, st, k_rhs_f32)(g, rho64, rho32, f);
 }
 
 __global__ void k_phi_planes(Grid g, double* phi) {
@@ -176,15 +207,12 @@ void launch_phi_planes(const Grid& g, double* phi, cudaStream_t st) {
 // a5: node field E = -grad phi. Central differences (periodic in x, y); in z
 // central inside, second-order one-sided on the electrode planes.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double3 node_field(const Grid& g, const double* __restrict__ f, long long n) {
+__device__ __forceinline__ double3 node_field(const Grid& g, const double* __restrict__ f, int i, int j, int k) {
   const long long pl = g.nplane;
-  const int k = (int)(n / pl);
-  const long long r = n - (long long)k * pl;
-  const int j = (int)(r / g.nx);
-  const int i = (int)(r - (long long)j * g.nx);
+  const long long n = (long long)k * pl + (long long)j * g.nx + i;
   const int im = i == 0 ? g.nx - 1 : i - 1, ip = i == g.nx - 1 ? 0 : i + 1;
   const int jm = j == 0 ? g.ny - 1 : j - 1, jp = j == g.ny - 1 ? 0 : j + 1;
-  const long long row = (long long)k * pl + (long long)j * g.nx;
+  const long long row = n - i;
   const double c = 0.5 * g.inv_h;
   double3 e;
   e.x = (f[row + im] - f[row + ip]) * c;
@@ -200,36 +228,38 @@ __device__ __forceinline__ double3 node_field(const Grid& g, const double* __res
 
 // E.w carries the neutral count of the cell whose lower corner is this node
 // (cell and node indices coincide for k < nz), read by the collision filter.
-__global__ void k_efield64(Grid g, const double* __restrict__ phi, double4_32a* __restrict__ E,
-                           const int32_t* __restrict__ ncount) {
-  for (long long n = gtid(); n < g.nnode; n += gstride()) {
-    const double3 e = node_field(g, phi, n);
+__global__ void __launch_bounds__(256) k_efield64(Grid g, const double* __restrict__ phi, double4_32a* __restrict__ E,
+                                                  const int32_t* __restrict__ ncount) {
+  const int k = blockIdx.z;
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  if (i >= g.nx) return;
+  for (int j = blockIdx.y * 8 + threadIdx.y; j < g.ny; j += gridDim.y * 8) {
+    const long long n = (long long)k * g.nplane + (long long)j * g.nx + i;
+    const double3 e = node_field(g, phi, i, j, k);
     double4_32a v;
     v.x = e.x;
     v.y = e.y;
     v.z = e.z;
-    v.w = (ncount && n < g.ncell) ? (double)ncount[n] : 0.0;
+    v.w = (ncount && k < g.nz) ? (double)ncount[n] : 0.0;
     E[n] = v;
   }
 }
-__global__ void k_efield32(Grid g, const double* __restrict__ phi, float4* __restrict__ E) {
-  for (long long n = gtid(); n < g.nnode; n += gstride()) {
-    const double3 e = node_field(g, phi, n);
-    E[n] = make_float4((float)e.x, (float)e.y, (float)e.z, 0.f);
-  }
+void launch_efield64(const Grid& g, const double* phi, double4_32a* E, const int32_t* ncount, cudaStream_t st) {
+  PIC_LAUNCH(grid3(g, g.nz + 1), kBlk3, 0, st, k_efield64)(g, phi, E, ncount);
 }
+
 // MIXED: E from the FP32 deviation from the vacuum potential, plus the vacuum field
-__global__ void k_efield32f(Grid g, const float* __restrict__ f, float4* __restrict__ E, float c, float ez_vac,
-                            const int32_t* __restrict__ ncount) {
-  for (long long n = gtid(); n < g.nnode; n += gstride()) {
-    const long long pl = g.nplane;
-    const int k = (int)(n / pl);
-    const long long r = n - (long long)k * pl;
-    const int j = (int)(r / g.nx);
-    const int i = (int)(r - (long long)j * g.nx);
-    const int im = i == 0 ? g.nx - 1 : i - 1, ip = i == g.nx - 1 ? 0 : i + 1;
+__global__ void __launch_bounds__(256) k_efield32f(Grid g, const float* __restrict__ f, float4* __restrict__ E, float c,
+                                                   float ez_vac, const int32_t* __restrict__ ncount) {
+  const int k = blockIdx.z;
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  if (i >= g.nx) return;
+  const int pl = (int)g.nplane;
+  const int im = i == 0 ? g.nx - 1 : i - 1, ip = i == g.nx - 1 ? 0 : i + 1;
+  for (int j = blockIdx.y * 8 + threadIdx.y; j < g.ny; j += gridDim.y * 8) {
+    const long long n = (long long)k * pl + (long long)j * g.nx + i;
+    const long long row = n - i;
     const int jm = j == 0 ? g.ny - 1 : j - 1, jp = j == g.ny - 1 ? 0 : j + 1;
-    const long long row = (long long)k * pl + (long long)j * g.nx;
     const float ex = (f[row + im] - f[row + ip]) * c;
     const float ey = (f[(long long)k * pl + (long long)jm * g.nx + i] - f[(long long)k * pl + (long long)jp * g.nx + i]) * c;
     float ez;
@@ -239,18 +269,12 @@ __global__ void k_efield32f(Grid g, const float* __restrict__ f, float4* __restr
       ez = (-3.f * f[n] + 4.f * f[n - pl] - f[n - 2 * pl]) * c;
     else
       ez = (f[n - pl] - f[n + pl]) * c;
-    E[n] = make_float4(ex, ey, ez + ez_vac, (ncount && n < g.ncell) ? (float)ncount[n] : 0.f);
+    E[n] = make_float4(ex, ey, ez + ez_vac, (ncount && k < g.nz) ? (float)ncount[n] : 0.f);
   }
 }
 void launch_efield32f(const Grid& g, const float* phi32, float4* E, const int32_t* ncount, cudaStream_t st) {
   const float ez_vac = (float)(-(g.phi_a - g.phi_c) / g.Lz);
-  PIC_LAUNCH(grid_for(g.nnode), kBlock, 0, st, k_efield32f)(g, phi32, E, (float)(0.5 * g.inv_h), ez_vac, ncount);
-}
-void launch_efield64(const Grid& g, const double* phi, double4_32a* E, const int32_t* ncount, cudaStream_t st) {
-  PIC_LAUNCH(grid_for(g.nnode), kBlock, 0, st, k_efield64)(g, phi, E, ncount);
-}
-void launch_efield32(const Grid& g, const double* phi, float4* E, cudaStream_t st) {
-  PIC_LAUNCH(grid_for(g.nnode), kBlock, 0, st, k_efield32)(g, phi, E);
+  PIC_LAUNCH(grid3(g, g.nz + 1), kBlk3, 0, st, k_efield32f)(g, phi32, E, (float)(0.5 * g.inv_h), ez_vac, ncount);
 }
 
 // ---------------------------------------------------------------------------

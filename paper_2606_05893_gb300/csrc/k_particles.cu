@@ -40,10 +40,9 @@ __device__ double xs_sigma64(const XsDev& c, double E) {
 }
 
 // Exact FP64 collision test of Eq. (4); returns -1 (none) or the channel slot.
-__device__ int mcc_exact_dt(const McArgs& m, long long cell, double v2, double U, double dt, double* E_eV_out) {
+__device__ int mcc_exact_dt(const McArgs& m, long long cell, double v2, double U, double dt) {
   const double u = sqrt(v2);
   const double E = m.half_m_over_e * v2;
-  *E_eV_out = E;
   double cum[kMaxXsec];
   double nu = 0.0;
   for (int a = 0; a < m.nch; ++a) {
@@ -59,19 +58,113 @@ __device__ int mcc_exact_dt(const McArgs& m, long long cell, double v2, double U
   return a;
 }
 
-// FP32 filter: true when the electron certainly does not collide. cnt0 >= 0 is
-// the target count of the cell taken from the node field (all channels share
+// FP32 filter, first part: sum_a n_a max sigma_a of the cell (0 when the cell
+// holds no target, and then nu = 0 in FP64 too: no collision, no draw). cnt0 >= 0
+// is the target count of the cell taken from the node field (all channels share
 // that target); otherwise the counts are read per channel.
-__device__ __forceinline__ bool mcc_cannot_collide(const McArgs& m, long long cell, float v2f, float U32, float dt_f,
-                                                   float cnt0) {
+__device__ __forceinline__ float mcc_nu_bound(const McArgs& m, long long cell, float cnt0) {
   float nb = 0.f;
   for (int a = 0; a < m.nch; ++a) {
     const float cnt = m.bg_mode ? 1.f : (cnt0 >= 0.f ? cnt0 : (float)m.ncount[a][cell]);
     nb = fmaf(cnt, m.bound_f[a], nb);
   }
-  // x_upper = u dt sum n_a max sigma_a >= x >= P; 1.001 covers FP32 rounding
+  return nb;
+}
+// Second part: true when the electron certainly does not collide, since
+// x_upper = u dt nb >= x >= P (1.001 covers FP32 rounding) and U32 is within
+// 2^-24 of the FP64 draw.
+__device__ __forceinline__ bool mcc_cannot_collide(float nb, float v2f, float U32, float dt_f) {
   const float xu = sqrtf(v2f) * dt_f * nb * 1.001f;
-  return U32 - 0x1p-25f > xu;
+  return U32 - 0x1p-24f > xu;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 enclosure of the FP64 decision
+// ---------------------------------------------------------------------------
+// The FP32 energy E32 = (m/2e) v^2 is within a relative 8 2^-24 = 2^-21 of the
+// FP64 energy E. When E32 is farther than kBrk = 2^-18 (relative) from every
+// breakpoint of the piecewise-linear table (threshold, first and last point,
+// table points), E lies on the same linear piece as E32 and sigma(E) is inside
+// [lo, hi] below; otherwise the enclosure is not attempted (returns false).
+constexpr float kBrk = 0x1p-18f;
+constexpr float kRel = 0x1p-18f;  // relative margin for FP32 rounding of products and sums
+
+__device__ __forceinline__ bool xs_sigma32(const XsDev& c, float E32, float& lo, float& hi) {
+  const float band = kBrk * E32;
+  if (c.thr_f > 0.f) {
+    if (E32 + band <= c.thr_f) {  // certainly E <= thr
+      lo = hi = 0.f;
+      return true;
+    }
+    if (E32 - band < c.thr_f) return false;
+  } else if (!(E32 > 1e-30f)) {
+    return false;
+  }
+  float s0, sl = 0.f;
+  if (c.n == 1) {
+    s0 = c.sigf[0];
+  } else if (E32 + band <= c.Ef[0]) {
+    s0 = c.sigf[0];
+  } else if (E32 - band >= c.Ef[c.n - 1]) {
+    s0 = c.sigf[c.n - 1];
+  } else {
+    if (E32 - band < c.Ef[0] || E32 + band > c.Ef[c.n - 1]) return false;
+    // bucket of ln E32 (floor without a float->int conversion), then a short scan
+    float v = (__logf(E32) - c.lnE0) * c.inv_dln;
+    v = fminf(fmaxf(v, 0.f), (float)(kXsBuckets - 1));
+    const float t = v + 12582912.f;
+    int b = __float_as_int(t) - 0x4B400000;
+    if (t - 12582912.f > v) --b;
+    int k = c.bucket[b];
+    while (k > 0 && c.Ef[k] > E32) --k;
+    while (k < c.n - 2 && c.Ef[k + 1] <= E32) ++k;
+    const float e0 = c.Ef[k], e1 = c.Ef[k + 1];
+    if (E32 - e0 < band || e1 - E32 < band) return false;
+    sl = c.slopef[k];
+    s0 = fmaf(E32 - e0, sl, c.sigf[k]);
+    const float err = kRel * (fabsf(c.sigf[k]) + fabsf(sl) * E32);
+    lo = s0 - err;
+    hi = s0 + err;
+    return true;
+  }
+  lo = s0 * (1.f - kRel);
+  hi = s0 * (1.f + kRel);
+  return true;
+}
+
+// The channel the FP64 rule of Eq. (4) would pick (mcc_exact_dt), decided in
+// FP32: -1 none, a >= 0 channel, -2 undecided (U within the rounding band of a
+// threshold, or E near a table breakpoint): the caller then runs the FP64 rule.
+// With x = u dt nu, the FP64 rule compares U with T_a = P cum_a / nu
+// = g(x) u dt cum_a, g(x) = (1 - e^-x)/x, and 1 - x/2 <= g(x) <= 1 - x/2 + x^2/6
+// for x >= 0. Each T_a is enclosed from the sigma enclosures, the FP32 draw is
+// within 2^-24 of the FP64 one.
+__device__ int mcc_decide32(const McArgs& m, long long cell, float v2f, float U32, float dt_f, float cnt0) {
+  const float E32 = m.half_m_over_e_f * v2f;
+  const float ud = sqrtf(v2f) * dt_f;
+  float slo[kMaxXsec], shi[kMaxXsec];
+  float clo = 0.f, chi = 0.f;
+  for (int a = 0; a < m.nch; ++a) {
+    const float na = m.bg_mode ? m.bg_density_f
+                               : (cnt0 >= 0.f ? cnt0 : (float)m.ncount[a][cell]) * m.dens_f[a];
+    float lo, hi;
+    if (!xs_sigma32(m.ch[a], E32, lo, hi)) return -2;
+    clo = fmaf(na, fmaxf(lo, 0.f), clo);
+    chi = fmaf(na, hi, chi);
+    slo[a] = clo;
+    shi[a] = chi;
+  }
+  const float xlo = ud * clo * (1.f - kRel), xhi = ud * chi * (1.f + kRel);
+  const float glo = 1.f - 0.5f * xhi;
+  const float ghi = 1.f - 0.5f * xlo + xhi * xhi * (1.f / 6.f) * (1.f + kRel);
+  const float Ulo = U32 - 0x1p-24f, Uhi = U32 + 0x1p-24f;
+  for (int a = 0; a < m.nch; ++a) {
+    const float Tlo = glo * ud * slo[a] * (1.f - kRel);
+    const float Thi = ghi * ud * shi[a] * (1.f + kRel);
+    if (Uhi < Tlo) return a;
+    if (!(Ulo >= Thi)) return -2;
+  }
+  return -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -127,24 +220,22 @@ __global__ void k_inject_commit(DevCounters* cnt, InjectCommit c) {
 // a5-a8 + a10: gather / push / absorb / collide / compact
 // ---------------------------------------------------------------------------
 template <class S, bool CHARGED, bool MCC, bool NEUTRAL>
-__global__ void __launch_bounds__(kPushBlock) k_push(PushArgs<S> a) {
+__global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(PushArgs<S> a) {
   // Each thread advances kIlp particles per round (their loads are issued
   // together, so the memory latency of one hides behind the others). Output
   // slots are reserved once per block and round (one global atomic per
   // kIlp * 256 particles); absorption statistics and elastic counts accumulate
   // in shared memory and reach HBM once per block.
-  __shared__ unsigned long long s_abs[2];
-  __shared__ double s_eabs[2], s_q[2];
-  __shared__ unsigned long long s_el;
   __shared__ unsigned int s_wcnt[kPushWarps];
   __shared__ unsigned long long s_base;
-  if (threadIdx.x == 0) {
-    s_abs[0] = s_abs[1] = 0ull;
-    s_eabs[0] = s_eabs[1] = 0.0;
-    s_q[0] = s_q[1] = 0.0;
-    s_el = 0ull;
-  }
-  __syncthreads();
+  // per-thread tallies, each touched by its own thread only (no atomics, no
+  // registers held): absorbed at cathode / anode, their sum of v^2, elastic
+  // collisions; reduced once per block at the end
+  __shared__ double s_tv2[2][kPushBlock];
+  __shared__ unsigned int s_tn[3][kPushBlock];
+  const int tx = threadIdx.x;
+  s_tv2[0][tx] = s_tv2[1][tx] = 0.0;
+  s_tn[0][tx] = s_tn[1][tx] = s_tn[2][tx] = 0u;
   const long long n = (long long)a.cnt->n[a.cur_in][a.species];
   if (blockIdx.x == 0 && threadIdx.x == 0)
     a.cnt->pushed[a.species] += (unsigned long long)n - (NEUTRAL ? a.cnt->n_tomb[a.species] : 0ull);
@@ -157,16 +248,14 @@ __global__ void __launch_bounds__(kPushBlock) k_push(PushArgs<S> a) {
   for (long long base = (long long)blockIdx.x * round; base < n; base += (long long)gridDim.x * round) {
     Particle p[kIlp];
     bool valid[kIlp], keep[kIlp], ionize[kIlp];
-    long long cell_n[kIlp];
+    int cell_n[kIlp];
     int ch_ion[kIlp];
-    double E_eV[kIlp];
 #pragma unroll
     for (int u = 0; u < kIlp; ++u) {
       const long long i = base + (long long)u * kPushBlock + threadIdx.x;
       valid[u] = i < n;
       keep[u] = ionize[u] = false;
       ch_ion[u] = -1;
-      E_eV[u] = 0.0;
       cell_n[u] = 0;
       if (valid[u]) p[u] = store_read(a.in, g, i);
     }
@@ -174,7 +263,7 @@ __global__ void __launch_bounds__(kPushBlock) k_push(PushArgs<S> a) {
     for (int u = 0; u < kIlp; ++u) {
       if (!valid[u]) continue;
       if (NEUTRAL && p[u].pid == kPidDead) continue;  // converted neutrals of the last step are dropped here
-      cell_n[u] = particle_cell(p[u]);
+      cell_n[u] = (int)particle_cell(p[u]);
       if (CHARGED) {
         const auto e = p[u].gather(g, a);
         p[u].kick(a, e);
@@ -182,29 +271,24 @@ __global__ void __launch_bounds__(kPushBlock) k_push(PushArgs<S> a) {
       const int side = p[u].drift(g);  // -1 cathode, +1 anode, 0 inside
       if (side != 0) {
         const int b = side < 0 ? 0 : 1;
-        const double ke = 0.5 * a.mass * a.weight * p[u].v2();
-        atomicAdd(&s_abs[b], 1ull);
-        atomicAdd(&s_eabs[b], ke);
-        atomicAdd(&s_q[b], a.charge * a.weight);
+        s_tn[b][tx] += 1u;
+        s_tv2[b][tx] += p[u].v2();
         continue;
       }
       keep[u] = true;
       if (MCC) {
-        const uint4 d = draw(a.mc.key, p[u].pid, a.mc.step, TAG_MCC);
+        const float nb = mcc_nu_bound(a.mc, cell_n[u], a.mc.count_in_field ? p[u].nc : -1.f);
+        if (nb <= 0.f) continue;
         const float cnt0 = a.mc.count_in_field ? p[u].nc : -1.f;
-        if (!mcc_cannot_collide(a.mc, cell_n[u], p[u].v2f(), u01_32(d.x), dt_f, cnt0)) {
-          const double U = u01_64(d.x, d.y);
-          const double v2 = p[u].v2();
-          const int ch = mcc_exact_dt(a.mc, cell_n[u], v2, U, g.dt, &E_eV[u]);
+        const uint4 d = draw(a.mc.key, p[u].pid, a.mc.step, TAG_MCC);
+        const float v2f = p[u].v2f(), U32 = u01_32(d.x);
+        if (!mcc_cannot_collide(nb, v2f, U32, dt_f)) {
+          int ch = mcc_decide32(a.mc, cell_n[u], v2f, U32, dt_f, cnt0);
+          if (ch == -2) ch = mcc_exact_dt(a.mc, cell_n[u], p[u].v2(), u01_64(d.x, d.y), g.dt);
           if (ch >= 0) {
             if (a.mc.ch[ch].kind == XS_ELASTIC) {
-              const uint4 sc = draw(a.mc.key, p[u].pid, a.mc.step, TAG_SCATTER);
-              const double ct = 2.0 * u01_64(sc.x, sc.y) - 1.0;
-              const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
-              const double ph = 2.0 * kPi * u01_64(sc.z, sc.w);
-              const double uu = sqrt(v2);
-              p[u].set_v(uu * st * cos(ph), uu * st * sin(ph), uu * ct);
-              atomicAdd(&s_el, 1ull);
+              p[u].scatter_isotropic(draw(a.mc.key, p[u].pid, a.mc.step, TAG_SCATTER));
+              s_tn[2][tx] += 1u;
             } else if (a.mc.bg_mode) {
               // fixed-background test mode: counted, nothing consumed or created
               atomicAdd(&a.cnt->n_ion, 1ull);
@@ -256,7 +340,7 @@ __global__ void __launch_bounds__(kPushBlock) k_push(PushArgs<S> a) {
           ev.cell = (uint32_t)cell_n[u];
           ev.slot = (uint32_t)slot;
           ev.ch = ch_ion[u];
-          ev.E_eV = E_eV[u];
+          ev.E_eV = a.mc.half_m_over_e * p[u].v2();  // velocity unchanged since the decision
           ev.victim = -1;
           ev.next = atomicExch(&a.ev_head[cell_n[u]], (int)e);
           a.ev[e] = ev;
@@ -280,20 +364,46 @@ __global__ void __launch_bounds__(kPushBlock) k_push(PushArgs<S> a) {
       }
     }
   }
+  // block totals of the tallies by warp 0: counts in integers, the FP64 sums of
+  // v^2 only when the block absorbed something (FP64 is a narrow pipe on GB300)
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const int s = a.species;
-    if (s_abs[0]) {
-      atomicAdd(&a.cnt->abs_cathode[s], s_abs[0]);
-      atomicAdd(&a.cnt->abs_energy_cathode[s], s_eabs[0]);
-      atomicAdd(&a.cnt->q_cathode_step, s_q[0]);
+  if (warp == 0) {
+    unsigned int n0 = 0, n1 = 0, nel = 0;
+    for (int t = lane; t < kPushBlock; t += 32) {
+      n0 += s_tn[0][t];
+      n1 += s_tn[1][t];
+      nel += s_tn[2][t];
     }
-    if (s_abs[1]) {
-      atomicAdd(&a.cnt->abs_anode[s], s_abs[1]);
-      atomicAdd(&a.cnt->abs_energy_anode[s], s_eabs[1]);
-      atomicAdd(&a.cnt->q_anode_step, s_q[1]);
+    n0 = __reduce_add_sync(0xffffffffu, n0);
+    n1 = __reduce_add_sync(0xffffffffu, n1);
+    nel = __reduce_add_sync(0xffffffffu, nel);
+    if (n0 + n1 > 0) {
+      double v0 = 0.0, v1 = 0.0;
+      for (int t = lane; t < kPushBlock; t += 32) {
+        v0 += s_tv2[0][t];
+        v1 += s_tv2[1][t];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_down_sync(0xffffffffu, v0, o);
+        v1 += __shfl_down_sync(0xffffffffu, v1, o);
+      }
+      if (lane == 0) {
+        const int s = a.species;
+        const double ke = 0.5 * a.mass * a.weight, qw = a.charge * a.weight;
+        if (n0) {
+          atomicAdd(&a.cnt->abs_cathode[s], (unsigned long long)n0);
+          atomicAdd(&a.cnt->abs_energy_cathode[s], ke * v0);
+          atomicAdd(&a.cnt->q_cathode_step, qw * (double)n0);
+        }
+        if (n1) {
+          atomicAdd(&a.cnt->abs_anode[s], (unsigned long long)n1);
+          atomicAdd(&a.cnt->abs_energy_anode[s], ke * v1);
+          atomicAdd(&a.cnt->q_anode_step, qw * (double)n1);
+        }
+      }
     }
-    if (s_el) atomicAdd(&a.cnt->n_el, s_el);
+    if (lane == 0 && nel) atomicAdd(&a.cnt->n_el, (unsigned long long)nel);
   }
 }
 

@@ -26,7 +26,9 @@
 namespace pic {
 
 constexpr int kSB = 256;
-constexpr int kMaxRedBlocks = 152 * 8;
+constexpr int kMaxRedBlocks = 152 * 8;  // 1-D reductions over whole vectors
+constexpr int kPartsMax = 1 << 16;      // capacity of the block-partials buffer
+constexpr int kPlaneBlocks = 8;         // blocks per plane in plane-major kernels
 
 static int sgrid(long long n) {
   long long b = (n + kSB - 1) / kSB;
@@ -35,103 +37,70 @@ static int sgrid(long long n) {
   return (int)b;
 }
 
+// Level geometry with 32-bit indices (a level holds far fewer than 2^31 unknowns).
 struct Lv {
-  int nx, ny, nz;
-  long long pl, nu;
+  int nx, ny, nz, pl, nu;
 };
-static Lv lv_of(const MgLevel& L) { return Lv{L.nx, L.ny, L.nz, (long long)L.nx * L.ny, L.nu}; }
+static Lv lv_of(const MgLevel& L) { return Lv{L.nx, L.ny, L.nz, L.nx * L.ny, (int)L.nu}; }
+
+// 3-D launches without integer division (on GB300 int division and int<->float
+// conversions run on the narrow FP64/conversion pipe): block (32, 8); x covers
+// the `xe` points of a row, y strides over the rows j, z = unknown plane.
+constexpr int kBX = 32, kBY = 8, kMaxGY = 4;
+static dim3 g3(const Lv& L, int xe) {
+  int gy = (L.ny + kBY - 1) / kBY;
+  gy = gy > kMaxGY ? kMaxGY : gy;
+  return dim3((xe + kBX - 1) / kBX, gy, L.nz - 1 > 0 ? L.nz - 1 : 1);
+}
+static const dim3 kB3(kBX, kBY, 1);
 
 template <class T>
-__device__ __forceinline__ T nb_sum(const Lv& L, const T* __restrict__ x, long long u, int i, int j, int k) {
+__device__ __forceinline__ T nb_sum(const Lv& L, const T* __restrict__ x, int u, int i, int j, int k) {
   // k: unknown plane index 0..nz-2
-  const long long row = u - i;
+  const int row = u - i;
   const int im = i == 0 ? L.nx - 1 : i - 1, ip = i == L.nx - 1 ? 0 : i + 1;
-  const long long rm = (j == 0 ? (long long)(L.ny - 1) * L.nx : -(long long)L.nx);
-  const long long rp = (j == L.ny - 1 ? -(long long)(L.ny - 1) * L.nx : (long long)L.nx);
+  const int rm = j == 0 ? (L.ny - 1) * L.nx : -L.nx;
+  const int rp = j == L.ny - 1 ? -(L.ny - 1) * L.nx : L.nx;
   T s = x[row + im] + x[row + ip] + x[u + rm] + x[u + rp];
   if (k > 0) s += x[u - L.pl];
   if (k < L.nz - 2) s += x[u + L.pl];
   return s;
 }
 
-__device__ __forceinline__ void uijk(const Lv& L, long long u, int& i, int& j, int& k) {
-  k = (int)(u / L.pl);
-  const long long r = u - (long long)k * L.pl;
-  j = (int)(r / L.nx);
-  i = (int)(r - (long long)j * L.nx);
-}
+// loop header of the 3-D kernels: i over [0, xe), j over the rows, k = plane
+#define ROWS3(L, xe)                                                          \
+  const int k = blockIdx.z;                                                  \
+  const int i = blockIdx.x * kBX + threadIdx.x;                              \
+  const bool in_x = i < (xe);                                                \
+  for (int j = blockIdx.y * kBY + threadIdx.y; j < (L).ny; j += gridDim.y * kBY)
 
-template <class T, class Acc>
-__device__ __forceinline__ void block_partial(Acc v, double* part) {
-  __shared__ double sm[kSB / 32];
-  double d = (double)v;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = d;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < kSB / 32; ++w) s += sm[w];
-    part[blockIdx.x] = s;
-  }
-}
-
-// y = A x ; part = x . y
+// r = b - A x (no reduction; multigrid levels)
 template <class T>
-__global__ void __launch_bounds__(kSB) k_apply_dot(Lv L, const T* __restrict__ x, T* __restrict__ y, double* part) {
-  T acc = 0;
-  for (long long u = gtid(); u < L.nu; u += gstride()) {
-    int i, j, k;
-    uijk(L, u, i, j, k);
-    const T xv = x[u];
-    const T yv = (T)6 * xv - nb_sum(L, x, u, i, j, k);
-    y[u] = yv;
-    acc += xv * yv;
+__global__ void __launch_bounds__(256) k_residual(Lv L, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r) {
+  ROWS3(L, L.nx) {
+    if (!in_x) continue;
+    const int u = k * L.pl + j * L.nx + i;
+    r[u] = b[u] - ((T)6 * x[u] - nb_sum(L, x, u, i, j, k));
   }
-  block_partial<T, T>(acc, part);
-}
-
-// r = b - A x ; part = r . r  (Tx/Tb may be FP64 while r is FP32 for the mixed residual)
-template <class Tx, class Tr>
-__global__ void __launch_bounds__(kSB) k_residual(Lv L, const Tx* __restrict__ x, const Tx* __restrict__ b,
-                                                  Tr* __restrict__ r, double* part) {
-  Tx acc = 0;
-  for (long long u = gtid(); u < L.nu; u += gstride()) {
-    int i, j, k;
-    uijk(L, u, i, j, k);
-    const Tx rv = b[u] - ((Tx)6 * x[u] - nb_sum(L, x, u, i, j, k));
-    r[u] = (Tr)rv;
-    acc += rv * rv;
-  }
-  if (part) block_partial<Tx, Tx>(acc, part);
-}
-
-// partial dot a . b
-template <class T>
-__global__ void __launch_bounds__(kSB) k_dot(long long n, const T* __restrict__ a, const T* __restrict__ b, double* part) {
-  T acc = 0;
-  for (long long u = gtid(); u < n; u += gstride()) acc += a[u] * b[u];
-  block_partial<T, T>(acc, part);
 }
 
 // ---------------------------------------------------------------------------
 // multigrid pieces
 // ---------------------------------------------------------------------------
-// One red-black Gauss-Seidel half sweep: points with (i + j + knode) % 2 == color.
+// One red-black Gauss-Seidel half sweep: points with (i + j + knode) % 2 == color
+// (x index m covers the nx/2 points of that colour in a row).
 // zero_init: the level starts from e = 0 (the other colour is written as 0).
 template <class T>
-__global__ void __launch_bounds__(kSB) k_smooth(Lv L, T* __restrict__ e, const T* __restrict__ b, int color, int zero_init) {
-  const int hx = L.nx >> 1;
-  const long long npts = L.nu >> 1;
+__global__ void __launch_bounds__(256) k_smooth(Lv L, T* __restrict__ e, const T* __restrict__ b, int color, int zero_init) {
   const T sixth = (T)(1.0 / 6.0);
-  for (long long t = gtid(); t < npts; t += gstride()) {
-    const long long row = t / hx;
-    const int m = (int)(t - row * hx);
-    const int j = (int)(row % L.ny);
-    const int k = (int)(row / L.ny);  // unknown plane (node k+1)
+  const int hx = L.nx >> 1;
+  const int m = blockIdx.x * kBX + threadIdx.x;
+  const int k = blockIdx.z;
+  if (m >= hx) return;
+  for (int j = blockIdx.y * kBY + threadIdx.y; j < L.ny; j += gridDim.y * kBY) {
     const int par = (j + k + 1 + color) & 1;
     const int i = 2 * m + par;
-    const long long u = (long long)k * L.pl + (long long)j * L.nx + i;
+    const int u = k * L.pl + j * L.nx + i;
     if (zero_init) {
       e[u] = b[u] * sixth;
       e[u - i + (2 * m + (par ^ 1))] = (T)0;
@@ -141,13 +110,17 @@ __global__ void __launch_bounds__(kSB) k_smooth(Lv L, T* __restrict__ e, const T
   }
 }
 
-// b_c = 4 * full-weighting(r_f) on coarse unknowns
+// b_c = 4 * full-weighting(r_f) on coarse unknowns (grid over the coarse level)
 template <class T>
-__global__ void __launch_bounds__(kSB) k_restrict(Lv F, Lv Cc, const T* __restrict__ r, T* __restrict__ bc) {
-  for (long long u = gtid(); u < Cc.nu; u += gstride()) {
-    int I, J, K;
-    uijk(Cc, u, I, J, K);
-    const int Kn = K + 1;  // coarse node index
+__global__ void __launch_bounds__(256) k_restrict(Lv F, Lv Cc, const T* __restrict__ r, T* __restrict__ bc) {
+  const int I = blockIdx.x * kBX + threadIdx.x;
+  const int K = blockIdx.z;
+  if (I >= Cc.nx) return;
+  const int Kn = K + 1;  // coarse node index
+  const int i0 = 2 * I;
+  const int im = i0 == 0 ? F.nx - 1 : i0 - 1;
+  const int ip = i0 + 1 == F.nx ? 0 : i0 + 1;
+  for (int J = blockIdx.y * kBY + threadIdx.y; J < Cc.ny; J += gridDim.y * kBY) {
     T s = 0;
 #pragma unroll
     for (int c = -1; c <= 1; ++c) {
@@ -158,48 +131,52 @@ __global__ void __launch_bounds__(kSB) k_restrict(Lv F, Lv Cc, const T* __restri
         int jf = 2 * J + b2;
         jf = jf < 0 ? jf + F.ny : (jf >= F.ny ? jf - F.ny : jf);
         const T wb = b2 == 0 ? (T)0.5 : (T)0.25;
-        const long long rowf = (long long)kf * F.pl + (long long)jf * F.nx;
-#pragma unroll
-        for (int a2 = -1; a2 <= 1; ++a2) {
-          int iff = 2 * I + a2;
-          iff = iff < 0 ? iff + F.nx : (iff >= F.nx ? iff - F.nx : iff);
-          const T wa = a2 == 0 ? (T)0.5 : (T)0.25;
-          s += wa * wb * wc * r[rowf + iff];
-        }
+        const int rowf = kf * F.pl + jf * F.nx;
+        s += wb * wc * ((T)0.25 * r[rowf + im] + (T)0.5 * r[rowf + i0] + (T)0.25 * r[rowf + ip]);
       }
     }
-    bc[u] = (T)4 * s;
+    bc[K * Cc.pl + J * Cc.nx + I] = (T)4 * s;
   }
 }
 
-// e_f += P e_c (trilinear; coarse Dirichlet planes carry 0)
+// e_f += P e_c (trilinear; coarse Dirichlet planes carry 0); grid over the fine level
 template <class T>
-__global__ void __launch_bounds__(kSB) k_prolong(Lv F, Lv Cc, const T* __restrict__ ec, T* __restrict__ ef) {
-  for (long long u = gtid(); u < F.nu; u += gstride()) {
-    int i, j, k;
-    uijk(F, u, i, j, k);
-    const int kn = k + 1;  // fine node
-    const int I0 = i >> 1, J0 = j >> 1, K0 = kn >> 1;
-    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (kn & 1) ? 2 : 1;
-    const T w = (T)1 / (T)(ni * nj * nk);
-    T s = 0;
-    const int I1 = I0 + 1 == Cc.nx ? 0 : I0 + 1;
+__global__ void __launch_bounds__(256) k_prolong(Lv F, Lv Cc, const T* __restrict__ ec, T* __restrict__ ef) {
+  const int kn = blockIdx.z + 1;  // fine node plane
+  const int K0 = kn >> 1;
+  const bool kodd = kn & 1;
+  const bool use0 = K0 >= 1 && K0 <= Cc.nz - 1;
+  const bool use1 = kodd && (K0 + 1) >= 1 && (K0 + 1) <= Cc.nz - 1;
+  const int off0 = (K0 - 1) * Cc.pl, off1 = K0 * Cc.pl;
+  const T wk = kodd ? (T)0.5 : (T)1;
+  const int i = blockIdx.x * kBX + threadIdx.x;
+  if (i >= F.nx) return;
+  const int I0 = i >> 1;
+  const int I1 = I0 + 1 == Cc.nx ? 0 : I0 + 1;
+  const bool iodd = i & 1;
+  for (int j = blockIdx.y * kBY + threadIdx.y; j < F.ny; j += gridDim.y * kBY) {
+    const int J0 = j >> 1;
     const int J1 = J0 + 1 == Cc.ny ? 0 : J0 + 1;
-    for (int c = 0; c < nk; ++c) {
-      const int K = K0 + c;  // coarse node
-      if (K <= 0 || K >= Cc.nz) continue;
-      const long long pk = (long long)(K - 1) * Cc.pl;
-      for (int b2 = 0; b2 < nj; ++b2) {
-        const long long row = pk + (long long)(b2 ? J1 : J0) * Cc.nx;
-        s += ec[row + I0];
-        if (ni == 2) s += ec[row + I1];
+    const bool jodd = j & 1;
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (c == 0 ? !use0 : !use1) continue;
+      const int off = c == 0 ? off0 : off1;
+      const int r0 = off + J0 * Cc.nx, r1 = off + J1 * Cc.nx;
+      T t = ec[r0 + I0];
+      if (iodd) t = (T)0.5 * (t + ec[r0 + I1]);
+      if (jodd) {
+        T t1 = ec[r1 + I0];
+        if (iodd) t1 = (T)0.5 * (t1 + ec[r1 + I1]);
+        t = (T)0.5 * (t + t1);
       }
+      s += t;
     }
-    ef[u] += w * s;
+    ef[blockIdx.z * F.pl + j * F.nx + i] += wk * s;
   }
 }
 
-// coarsest level: e = Ainv b (dense, row per warp)
 template <class T>
 __global__ void k_coarse(long long n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ e) {
   const int lane = threadIdx.x & 31;
@@ -367,12 +344,11 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
   }
   for (int l = 0; l < nl - 1; ++l) {
     const Lv L = lv_of(levels[l]);
-    const long long half = L.nu >> 1;
-    PIC_LAUNCH(sgrid(half), kSB, 0, s, k_smooth<T>)(L, E[l], B[l], 0, 1);
-    PIC_LAUNCH(sgrid(half), kSB, 0, s, k_smooth<T>)(L, E[l], B[l], 1, 0);
-    PIC_LAUNCH(sgrid(L.nu), kSB, 0, s, k_residual<T, T>)(L, E[l], B[l], r[l], nullptr);
+    PIC_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 0, 1);
+    PIC_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 1, 0);
+    PIC_LAUNCH(g3(L, L.nx), kB3, 0, s, k_residual<T>)(L, E[l], B[l], r[l]);
     const Lv C = lv_of(levels[l + 1]);
-    PIC_LAUNCH(sgrid(C.nu), kSB, 0, s, k_restrict<T>)(L, C, r[l], B[l + 1]);
+    PIC_LAUNCH(g3(C, C.nx), kB3, 0, s, k_restrict<T>)(L, C, r[l], B[l + 1]);
   }
   {
     const Lv C = lv_of(levels[nl - 1]);
@@ -381,26 +357,24 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
       PIC_LAUNCH(cg, kSB, 0, s, k_coarse<T>)(C.nu, Ainv, B[nl - 1],
                                                                                               E[nl - 1]);
     } else {
-      const long long half = C.nu >> 1;
-      PIC_LAUNCH(sgrid(half), kSB, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 1);
-      PIC_LAUNCH(sgrid(half), kSB, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
+      PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 1);
+      PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
       for (int it = 0; it < coarse_sweeps; ++it) {
-        PIC_LAUNCH(sgrid(half), kSB, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
-        PIC_LAUNCH(sgrid(half), kSB, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
-        PIC_LAUNCH(sgrid(half), kSB, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
-        PIC_LAUNCH(sgrid(half), kSB, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
+        PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
+        PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
+        PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
+        PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
       }
-      PIC_LAUNCH(sgrid(half), kSB, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
-      PIC_LAUNCH(sgrid(half), kSB, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
+      PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
+      PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
     }
   }
   for (int l = nl - 2; l >= 0; --l) {
     const Lv L = lv_of(levels[l]);
     const Lv C = lv_of(levels[l + 1]);
-    PIC_LAUNCH(sgrid(L.nu), kSB, 0, s, k_prolong<T>)(L, C, E[l + 1], E[l]);
-    const long long half = L.nu >> 1;
-    PIC_LAUNCH(sgrid(half), kSB, 0, s, k_smooth<T>)(L, E[l], B[l], 1, 0);
-    PIC_LAUNCH(sgrid(half), kSB, 0, s, k_smooth<T>)(L, E[l], B[l], 0, 0);
+    PIC_LAUNCH(g3(L, L.nx), kB3, 0, s, k_prolong<T>)(L, C, E[l + 1], E[l]);
+    PIC_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 1, 0);
+    PIC_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 0, 0);
   }
 }
 
@@ -410,28 +384,64 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
 // CUDA graph (outer: FP64 true residual / refinement; inner: PCG iterations),
 // so a solve is one graph launch with no host round trip.
 // ---------------------------------------------------------------------------
-constexpr int kFinBlock = 512;
-// Sum of the block partials by one block of kFinBlock threads, in a fixed order
-// (strided per-thread sums, then a shared-memory tree); returns the total in
-// every thread.
-__device__ __forceinline__ double sum_parts(const double* part, int n) {
-  __shared__ double sm[kFinBlock];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += kFinBlock) s += part[i];
-  sm[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = kFinBlock / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
-    __syncthreads();
-  }
-  const double t = sm[0];
-  __syncthreads();
-  return t;
+template <class V>
+__device__ __forceinline__ V warp_sum(V d) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+  return d;
 }
 
-__global__ void k_fin_bb(const double* part, int nparts, SolveCtl* c, double rtol, int maxit) {
-  const double bb = sum_parts(part, nparts);
-  if (threadIdx.x != 0) return;
+// Grid-wide sum without a second launch: each block stores its partial in
+// part[block], then the last block to arrive (a ticket counter) adds all
+// partials in a fixed order (fixed thread assignment and tree, so the total is
+// reproducible) and resets the ticket. Returns true in thread 0 of that block
+// only, with the total in *tot. Every thread of every block must call it.
+// Per-thread and warp sums stay in V (FP32 for the FP32 solve: FP64 is a narrow
+// pipe on GB300); warp totals and everything above them are FP64.
+template <class V>
+__device__ __forceinline__ bool grid_total(V v, double* part, unsigned* ticket, double* tot) {
+  __shared__ double sm[32];
+  __shared__ int s_last;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+  const int nw = nthr >> 5;
+  const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+  const V w = warp_sum(v);
+  if ((tid & 31) == 0) sm[tid >> 5] = (double)w;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += sm[k];
+    part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+    __threadfence();
+    s_last = atomicAdd(ticket, 1u) == nb - 1u ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  // four independent partial sums per thread keep several loads in flight
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  unsigned i = tid;
+  for (; i + 3u * nthr < nb; i += 4u * nthr) {
+    s0 += __ldcg(part + i);
+    s1 += __ldcg(part + i + nthr);
+    s2 += __ldcg(part + i + 2u * nthr);
+    s3 += __ldcg(part + i + 3u * nthr);
+  }
+  for (; i < nb; i += nthr) s0 += __ldcg(part + i);
+  double s = warp_sum((s0 + s1) + (s2 + s3));
+  __syncthreads();
+  if ((tid & 31) == 0) sm[tid >> 5] = s;
+  __syncthreads();
+  if (tid != 0) return false;
+  double t = 0.0;
+  for (int k = 0; k < nw; ++k) t += sm[k];
+  *tot = t;
+  *ticket = 0u;
+  return true;
+}
+
+__device__ __forceinline__ void fin_bb(double bb, SolveCtl* c, double rtol, int maxit) {
   c->bb = bb;
   c->tol2 = rtol * rtol * bb;
   c->it_total = 0;
@@ -442,28 +452,20 @@ __global__ void k_fin_bb(const double* part, int nparts, SolveCtl* c, double rto
   c->resid_rel = 0.0;
 }
 
-// r_in = (Tin)(b - A x) with x, b FP64; d = 0; partial sums of r.r (FP64)
-template <class Tin>
-__global__ void __launch_bounds__(kSB) k_residual_prep(Lv L, const double* __restrict__ x, const double* __restrict__ b,
-                                                       Tin* __restrict__ r_in, Tin* __restrict__ d, double* part,
-                                                       const SolveCtl* c) {
+// b.b -> tolerance; start of a solve
+__global__ void __launch_bounds__(kSB) k_dot_bb(int n, const double* __restrict__ b, double* part, SolveCtl* c,
+                                                double rtol, int maxit) {
   double acc = 0.0;
-  const bool zero_x = c->bb == 0.0;
-  for (long long u = gtid(); u < L.nu; u += gstride()) {
-    int i, j, k;
-    uijk(L, u, i, j, k);
-    const double rv = zero_x ? 0.0 : b[u] - (6.0 * x[u] - nb_sum(L, x, u, i, j, k));
-    r_in[u] = (Tin)rv;
-    d[u] = (Tin)0;
-    acc += rv * rv;
-  }
-  block_partial<double, double>(acc, part);
+  for (int u = blockIdx.x * kSB + threadIdx.x; u < n; u += gridDim.x * kSB) acc += b[u] * b[u];
+  double bb;
+  if (grid_total(acc, part, &c->ticket, &bb)) fin_bb(bb, c, rtol, maxit);
 }
 
-__global__ void k_fin_outer(const double* part, int nparts, SolveCtl* c, cudaGraphConditionalHandle h_outer,
-                            cudaGraphConditionalHandle h_inner, double inner_rtol, int mixed, int max_outer, int use_graph) {
-  const double rr = sum_parts(part, nparts);
-  if (threadIdx.x != 0) return;
+// Outer-loop decision from the true residual r.r (last block of a residual kernel)
+__device__ __forceinline__ void fin_outer(double rr, SolveCtl* c, cudaGraphConditionalHandle h_outer,
+                                          cudaGraphConditionalHandle h_inner, double inner_rtol, int mixed,
+                                          int max_outer, int use_graph) {
+  c->ax_valid = 1;
   c->rr_true = rr;
   c->resid_rel = c->bb > 0.0 ? sqrt(rr / c->bb) : 0.0;
   const bool done = c->bb == 0.0 || rr <= c->tol2 || !(rr == rr) || c->it_total >= c->maxit || c->outer >= max_outer;
@@ -473,35 +475,224 @@ __global__ void k_fin_outer(const double* part, int nparts, SolveCtl* c, cudaGra
   c->tol_in2 = mixed ? fmax(inner_rtol * inner_rtol * rr, 0.25 * c->tol2) : c->tol2;
   c->outer += 1;
   c->more = done ? 0 : 1;
+  c->stopped = done ? 1 : 0;
   if (use_graph) {
     cudaGraphSetConditional(h_outer, done ? 0u : 1u);
     cudaGraphSetConditional(h_inner, done ? 0u : 1u);
   }
 }
 
-__global__ void k_fin_rz(const double* part, int nparts, SolveCtl* c) {
-  const double rz = sum_parts(part, nparts);
-  if (threadIdx.x != 0) return;
+// r_in = (Tin)(b - A x) with x, b FP64 (x = 0 when b = 0); d = 0; then, in the last block, the
+// outer-loop decision from r.r (FP64). A x is kept in ax: while c->ax_valid is
+// set, ax holds A x for the current x (x unchanged since it was written), and
+// the residual is b - ax without the stencil.
+template <class Tin>
+__global__ void __launch_bounds__(256) k_residual_prep(Lv L, double* __restrict__ x, const double* __restrict__ b,
+                                                       double* __restrict__ ax, Tin* __restrict__ r_in,
+                                                       Tin* __restrict__ d, double* part, SolveCtl* c,
+                                                       cudaGraphConditionalHandle h_outer,
+                                                       cudaGraphConditionalHandle h_inner, double inner_rtol,
+                                                       int mixed, int max_outer, int use_graph) {
+  Tin acc = 0;
+  const bool zero_x = c->bb == 0.0;
+  const bool cached = c->ax_valid != 0;
+  ROWS3(L, L.nx) {
+    if (!in_x) continue;
+    const int u = k * L.pl + j * L.nx + i;
+    double rv = 0.0;
+    if (zero_x) {  // b = 0: the solution is x = 0
+      x[u] = 0.0;
+      ax[u] = 0.0;
+    } else {
+      double axv;
+      if (cached) {
+        axv = ax[u];
+      } else {
+        axv = 6.0 * x[u] - nb_sum(L, x, u, i, j, k);
+        ax[u] = axv;
+      }
+      rv = b[u] - axv;
+    }
+    const Tin ri = (Tin)rv;
+    r_in[u] = ri;
+    d[u] = (Tin)0;
+    acc += ri * ri;
+  }
+  double rr;
+  if (grid_total(acc, part, &c->ticket, &rr))
+    fin_outer(rr, c, h_outer, h_inner, inner_rtol, mixed, max_outer, use_graph);
+}
+
+// ---------------------------------------------------------------------------
+// MIXED path: the outer loop in float-float arithmetic. Over the unknowns the
+// potential is kept as phi = vac(k) + hi + lo, with hi and lo FP32 and hi the
+// FP32 deviation from the vacuum potential vac(k) = phi_c + k (phi_a - phi_c)/nz
+// that the field kernel reads (phi32). The linear vac satisfies A vac = the
+// folded Dirichlet terms, so b - A phi = f - A (hi + lo), f = fl32(h^2 rho/eps0)
+// the FP32 charge term. A hi is summed with error-free transformations (Knuth's
+// TwoSum; 6 hi exactly as a product and its FMA remainder), A lo in plain FP32:
+// the residual carries about 48 significant bits with no FP64 instruction (FP64
+// is a narrow pipe on GB300). The _rn intrinsics keep the compiler from fusing
+// the products and sums the transformations rely on.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
+// sum of the six neighbours of u as s + e (s rounded, e the accumulated exact errors)
+__device__ __forceinline__ void nb_sum_ff(const Lv& L, const float* __restrict__ x, int u, int i, int j, int k, float& s,
+                                          float& e) {
+  const int row = u - i;
+  const int im = i == 0 ? L.nx - 1 : i - 1, ip = i == L.nx - 1 ? 0 : i + 1;
+  const int rm = j == 0 ? (L.ny - 1) * L.nx : -L.nx;
+  const int rp = j == L.ny - 1 ? -(L.ny - 1) * L.nx : L.nx;
+  float t;
+  s = x[row + im];
+  e = 0.f;
+  two_sum(s, x[row + ip], s, t);
+  e = __fadd_rn(e, t);
+  two_sum(s, x[u + rm], s, t);
+  e = __fadd_rn(e, t);
+  two_sum(s, x[u + rp], s, t);
+  e = __fadd_rn(e, t);
+  if (k > 0) {
+    two_sum(s, x[u - L.pl], s, t);
+    e = __fadd_rn(e, t);
+  }
+  if (k < L.nz - 2) {
+    two_sum(s, x[u + L.pl], s, t);
+    e = __fadd_rn(e, t);
+  }
+}
+
+// sum f.f + folded terms -> tolerance (b = f + fold never materialised)
+__global__ void __launch_bounds__(256) k_dot_bb_ff(Lv L, const float* __restrict__ f, float fold_first, float fold_last,
+                                                   double* part, SolveCtl* c, double rtol, int maxit) {
+  float acc = 0.f;
+  ROWS3(L, L.nx) {
+    if (!in_x) continue;
+    const int u = k * L.pl + j * L.nx + i;
+    float bv = f[u];
+    if (k == 0) bv += fold_first;
+    if (k == L.nz - 2) bv += fold_last;
+    acc += bv * bv;
+  }
+  double bb;
+  if (grid_total(acc, part, &c->ticket, &bb)) fin_bb(bb, c, rtol, maxit);
+}
+
+// r = fl32(f - A (hi + lo)); d = 0; outer decision in the last block.
+// b = 0 (bb = 0): the solution is phi = 0, i.e. hi + lo = -vac.
+__global__ void __launch_bounds__(256) k_residual_ff(Lv L, float* __restrict__ hi, float* __restrict__ lo,
+                                                     const float* __restrict__ f, float* __restrict__ r,
+                                                     float* __restrict__ d, double phi_c, double dphi_dk, double* part,
+                                                     SolveCtl* c, cudaGraphConditionalHandle h_outer,
+                                                     cudaGraphConditionalHandle h_inner, double inner_rtol,
+                                                     int max_outer, int use_graph) {
+  float acc = 0.f;
+  const bool zero_x = c->bb == 0.0;
+  ROWS3(L, L.nx) {
+    if (!in_x) continue;
+    const int u = k * L.pl + j * L.nx + i;
+    float rv = 0.f;
+    if (zero_x) {
+      const double v = -(phi_c + dphi_dk * (double)(k + 1));
+      const float vh = (float)v;
+      hi[u] = vh;
+      lo[u] = (float)(v - (double)vh);
+    } else {
+      float s, e;
+      nb_sum_ff(L, hi, u, i, j, k, s, e);
+      const float hc = hi[u];
+      const float p6 = __fmul_rn(6.f, hc);
+      const float e6 = __fmaf_rn(6.f, hc, -p6);  // 6 hc = p6 + e6 exactly
+      float a1, ea;
+      two_sum(p6, -s, a1, ea);  // A hi = a1 + ea + e6 - e
+      const float alo = __fsub_rn(__fmul_rn(6.f, lo[u]), nb_sum(L, lo, u, i, j, k));
+      float r1, er;
+      two_sum(f[u], -a1, r1, er);
+      const float small = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(er, ea), e6), e), alo);
+      rv = __fadd_rn(r1, small);
+    }
+    r[u] = rv;
+    d[u] = 0.f;
+    acc += rv * rv;
+  }
+  double rr;
+  if (grid_total(acc, part, &c->ticket, &rr))
+    fin_outer(rr, c, h_outer, h_inner, inner_rtol, 1, max_outer, use_graph);
+}
+
+// (hi, lo) += d, renormalised (hi = fl32(hi + lo)); nothing to do once stopped
+__global__ void __launch_bounds__(kSB) k_update_ff(long long n, float* __restrict__ hi, float* __restrict__ lo,
+                                                   const float* __restrict__ d, const SolveCtl* c) {
+  if (c->stopped) return;
+  for (long long u = gtid(); u < n; u += gstride()) {
+    float s, e;
+    two_sum(hi[u], d[u], s, e);
+    e = __fadd_rn(e, lo[u]);
+    const float h2 = __fadd_rn(s, e);
+    hi[u] = h2;
+    lo[u] = __fsub_rn(e, __fsub_rn(h2, s));
+  }
+}
+
+// phi (FP64, unknown view) = vac + hi + lo
+__global__ void __launch_bounds__(256) k_phi_from_ff(Lv L, const float* __restrict__ hi, const float* __restrict__ lo,
+                                                     double* __restrict__ x, double phi_c, double dphi_dk) {
+  const double vac = phi_c + dphi_dk * (double)(blockIdx.z + 1);
+  ROWS3(L, L.nx) {
+    if (!in_x) continue;
+    const int u = k * L.pl + j * L.nx + i;
+    x[u] = vac + ((double)hi[u] + (double)lo[u]);
+  }
+}
+
+// (hi, lo) from phi (FP64, unknown view; nullptr: phi = 0)
+__global__ void __launch_bounds__(256) k_ff_from_phi(Lv L, const double* __restrict__ x, float* __restrict__ hi,
+                                                     float* __restrict__ lo, double phi_c, double dphi_dk) {
+  const double vac = phi_c + dphi_dk * (double)(blockIdx.z + 1);
+  ROWS3(L, L.nx) {
+    if (!in_x) continue;
+    const int u = k * L.pl + j * L.nx + i;
+    const double v = (x ? x[u] : 0.0) - vac;
+    const float vh = (float)v;
+    hi[u] = vh;
+    lo[u] = (float)(v - (double)vh);
+  }
+}
+
+// r.z -> beta
+template <class T>
+__global__ void __launch_bounds__(kSB) k_dot_rz(int n, const T* __restrict__ r, const T* __restrict__ z, double* part,
+                                                SolveCtl* c) {
+  T acc = 0;
+  for (int u = blockIdx.x * kSB + threadIdx.x; u < n; u += gridDim.x * kSB) acc += r[u] * z[u];
+  double rz;
+  if (!grid_total(acc, part, &c->ticket, &rz)) return;
   c->beta = c->it_inner > 0 ? rz / c->rz : 0.0;
   c->rz = rz;
 }
 
-__global__ void k_fin_pq(const double* part, int nparts, SolveCtl* c) {
-  const double pq = sum_parts(part, nparts);
-  if (threadIdx.x != 0) return;
+// q = A p ; p.q -> alpha
+template <class T>
+__global__ void __launch_bounds__(256) k_apply_pq(Lv L, const T* __restrict__ p, T* __restrict__ q, double* part,
+                                                  SolveCtl* c) {
+  T acc = 0;
+  ROWS3(L, L.nx) {
+    if (!in_x) continue;
+    const int u = k * L.pl + j * L.nx + i;
+    const T pv = p[u];
+    const T qv = (T)6 * pv - nb_sum(L, p, u, i, j, k);
+    q[u] = qv;
+    acc += pv * qv;
+  }
+  double pq;
+  if (!grid_total(acc, part, &c->ticket, &pq)) return;
   c->pq = pq;
   c->alpha = pq != 0.0 ? c->rz / pq : 0.0;
-}
-
-__global__ void k_fin_rr(const double* part, int nparts, SolveCtl* c, cudaGraphConditionalHandle h_inner, int use_graph) {
-  const double rr = sum_parts(part, nparts);
-  if (threadIdx.x != 0) return;
-  c->rr = rr;
-  c->it_inner += 1;
-  c->it_total += 1;
-  const bool more = rr > c->tol_in2 && c->it_total < c->maxit && (rr == rr);
-  c->more = more ? 1 : 0;
-  if (use_graph) cudaGraphSetConditional(h_inner, more ? 1u : 0u);
 }
 
 // p = z (first iteration of this inner solve) or z + beta p
@@ -512,10 +703,11 @@ __global__ void __launch_bounds__(kSB) k_pupdate_c(long long n, T* __restrict__ 
   for (long long u = gtid(); u < n; u += gstride()) p[u] = first ? z[u] : z[u] + beta * p[u];
 }
 
-// d += alpha p ; r -= alpha q ; partial r.r
+// d += alpha p ; r -= alpha q ; r.r -> inner-loop decision
 template <class T>
-__global__ void __launch_bounds__(kSB) k_update_c(long long n, T* __restrict__ d, T* __restrict__ r, const T* __restrict__ p,
-                                                  const T* __restrict__ q, const SolveCtl* c, double* part) {
+__global__ void __launch_bounds__(kSB) k_update_rr(long long n, T* __restrict__ d, T* __restrict__ r, const T* __restrict__ p,
+                                                   const T* __restrict__ q, SolveCtl* c, double* part,
+                                                   cudaGraphConditionalHandle h_inner, int use_graph) {
   const T alpha = (T)c->alpha;
   T acc = 0;
   for (long long u = gtid(); u < n; u += gstride()) {
@@ -524,20 +716,31 @@ __global__ void __launch_bounds__(kSB) k_update_c(long long n, T* __restrict__ d
     r[u] = rv;
     acc += rv * rv;
   }
-  block_partial<T, T>(acc, part);
+  double rr;
+  if (!grid_total(acc, part, &c->ticket, &rr)) return;
+  c->rr = rr;
+  c->it_inner += 1;
+  c->it_total += 1;
+  const bool more = rr > c->tol_in2 && c->it_total < c->maxit && (rr == rr);
+  c->more = more ? 1 : 0;
+  if (use_graph) cudaGraphSetConditional(h_inner, more ? 1u : 0u);
 }
 
-// x += d (FP64); optionally phi32 = (float)(x - phi_vac(z)) on the same nodes
+// x += d (FP64); optionally phi32 = (float)(x - phi_vac(z)) on the same nodes.
+// Unless the outer loop has just stopped (then d = 0 and x stays as it is), x
+// changes and the kept A x is no longer valid.
 template <class T>
-__global__ void __launch_bounds__(kSB) k_axpy_out(Lv L, double* __restrict__ x, const T* __restrict__ d, float* __restrict__ phi32,
-                                                  double phi_c, double dphi_dk) {
-  for (long long u = gtid(); u < L.nu; u += gstride()) {
+__global__ void __launch_bounds__(256) k_axpy_out(Lv L, double* __restrict__ x, const T* __restrict__ d, float* __restrict__ phi32,
+                                                  double phi_c, double dphi_dk, SolveCtl* c) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0 && !c->stopped)
+    c->ax_valid = 0;
+  const double vac = phi_c + dphi_dk * (double)(blockIdx.z + 1);  // vacuum potential of this node plane
+  ROWS3(L, L.nx) {
+    if (!in_x) continue;
+    const int u = k * L.pl + j * L.nx + i;
     const double v = x[u] + (double)d[u];
     x[u] = v;
-    if (phi32) {
-      const int k = (int)(u / L.pl) + 1;  // node plane
-      phi32[u] = (float)(v - (phi_c + dphi_dk * (double)k));
-    }
+    if (phi32) phi32[u] = (float)(v - vac);
   }
 }
 
@@ -580,9 +783,18 @@ cudaError_t Solver::init(int nx, int ny, int nz, int precision_) {
   plan = mg_plan(nx, ny, nz);
   n = plan[0].nu;
   cudaError_t err;
-  if ((err = cudaMalloc(&b, sizeof(double) * (size_t)(n > 0 ? n : 1)))) return err;
-  if ((err = cudaMemset(b, 0, sizeof(double) * (size_t)(n > 0 ? n : 1)))) return err;
-  if ((err = cudaMalloc(&part, sizeof(double) * kMaxRedBlocks))) return err;
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  if (precision == 0) {
+    if ((err = cudaMalloc(&b, sizeof(double) * nn))) return err;
+    if ((err = cudaMemset(b, 0, sizeof(double) * nn))) return err;
+    if ((err = cudaMalloc(&ax, sizeof(double) * nn))) return err;
+  } else {
+    if ((err = cudaMalloc(&f32, sizeof(float) * nn))) return err;
+    if ((err = cudaMemset(f32, 0, sizeof(float) * nn))) return err;
+    if ((err = cudaMalloc(&lo32, sizeof(float) * nn))) return err;
+    if ((err = cudaMemset(lo32, 0, sizeof(float) * nn))) return err;
+  }
+  if ((err = cudaMalloc(&part, sizeof(double) * kPartsMax))) return err;
   if ((err = cudaMalloc(&ctl, sizeof(SolveCtl)))) return err;
   if ((err = cudaMemset(ctl, 0, sizeof(SolveCtl)))) return err;
   if ((err = cudaMallocHost(&host_ctl, sizeof(SolveCtl)))) return err;
@@ -597,11 +809,17 @@ void Solver::release() {
   exec = nullptr;
   graph = nullptr;
   cudaFree(b);
+  cudaFree(ax);
+  cudaFree(f32);
+  cudaFree(lo32);
   cudaFree(part);
   cudaFree(ctl);
   if (host_ctl) cudaFreeHost(host_ctl);
   host_ctl = nullptr;
   b = nullptr;
+  ax = nullptr;
+  f32 = nullptr;
+  lo32 = nullptr;
   part = nullptr;
   ctl = nullptr;
   p64.release();
@@ -614,13 +832,11 @@ static void capture_pcg_iteration(Pcg<T>& pc, const Lv& L, double* part, SolveCt
                                   cudaGraphConditionalHandle h_inner, cudaStream_t s, int use_graph = 1) {
   const int G = sgrid(L.nu);
   pc.mg.vcycle(pc.r, pc.z, s);
-  PIC_LAUNCH(G, kSB, 0, s, k_dot<T>)(L.nu, pc.r, pc.z, part);
-  PIC_LAUNCH(1, kFinBlock, 0, s, k_fin_rz)(part, G, ctl);
+  PIC_LAUNCH(G, kSB, 0, s, k_dot_rz<T>)(L.nu, pc.r, pc.z, part, ctl);
+  const dim3 PGd = g3(L, L.nx);
   PIC_LAUNCH(G, kSB, 0, s, k_pupdate_c<T>)(L.nu, pc.p, pc.z, ctl);
-  PIC_LAUNCH(G, kSB, 0, s, k_apply_dot<T>)(L, pc.p, pc.q, part);
-  PIC_LAUNCH(1, kFinBlock, 0, s, k_fin_pq)(part, G, ctl);
-  PIC_LAUNCH(G, kSB, 0, s, k_update_c<T>)(L.nu, pc.d, pc.r, pc.p, pc.q, ctl, part);
-  PIC_LAUNCH(1, kFinBlock, 0, s, k_fin_rr)(part, G, ctl, h_inner, use_graph);
+  PIC_LAUNCH(PGd, kB3, 0, s, k_apply_pq<T>)(L, pc.p, pc.q, part, ctl);
+  PIC_LAUNCH(G, kSB, 0, s, k_update_rr<T>)(L.nu, pc.d, pc.r, pc.p, pc.q, ctl, part, h_inner, use_graph);
 }
 
 // Add a WHILE node at the current capture position of `s`; returns its body graph.
@@ -653,6 +869,7 @@ cudaError_t Solver::build_graph(double* x, float* phi32, double phi_c, double ph
   hx = x;
   hphi32 = phi32;
   h_phi_c = phi_c;
+  h_phi_a = phi_a;
   h_dphi_dk = (phi_a - phi_c) / (double)nz;
   h_rtol = rtol;
   h_maxit = maxit;
@@ -660,6 +877,7 @@ cudaError_t Solver::build_graph(double* x, float* phi32, double phi_c, double ph
   if (env && env[0] == '0') return cudaSuccess;  // host-driven loop (profilers cannot see conditional graphs)
   const Lv L = lv_of(plan[0]);
   const int G = sgrid(L.nu);
+  const dim3 PGd = g3(L, L.nx);
   const int mixed = precision != 0;
   const double dphi_dk = (phi_a - phi_c) / (double)nz;
   cudaStream_t s0 = nullptr, s1 = nullptr, s2 = nullptr;
@@ -671,19 +889,24 @@ cudaError_t Solver::build_graph(double* x, float* phi32, double phi_c, double ph
   cudaGraph_t outer_body = nullptr, inner_body = nullptr;
   e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
-    PIC_LAUNCH(G, kSB, 0, s0, k_dot<double>)(L.nu, b, b, part);
-    PIC_LAUNCH(1, kFinBlock, 0, s0, k_fin_bb)(part, G, ctl, rtol, maxit);
+    if (mixed) {
+      PIC_LAUNCH(PGd, kB3, 0, s0, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, rtol, maxit);
+    } else {
+      PIC_LAUNCH(G, kSB, 0, s0, k_dot_bb)(L.nu, b, part, ctl, rtol, maxit);
+    }
     e = add_while(s0, &h_outer, 1u, &outer_body);
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s1, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-      if (mixed) {
-        PIC_LAUNCH(G, kSB, 0, s1, k_residual_prep<float>)(L, x, b, p32.r, p32.d, part, ctl);
-      } else {
-        PIC_LAUNCH(G, kSB, 0, s1, k_residual_prep<double>)(L, x, b, p64.r, p64.d, part, ctl);
-      }
       e = cudaGraphConditionalHandleCreate(&h_inner, outer_body, 0u, 0);
-      if (e == cudaSuccess)
-        PIC_LAUNCH(1, kFinBlock, 0, s1, k_fin_outer)(part, G, ctl, h_outer, h_inner, inner_rtol, mixed, max_outer, 1);
+      if (e == cudaSuccess) {
+        if (mixed) {
+          PIC_LAUNCH(PGd, kB3, 0, s1, k_residual_ff)(L, phi32, lo32, f32, p32.r, p32.d, phi_c, dphi_dk, part, ctl,
+                                                      h_outer, h_inner, inner_rtol, max_outer, 1);
+        } else {
+          PIC_LAUNCH(PGd, kB3, 0, s1, k_residual_prep<double>)(L, x, b, ax, p64.r, p64.d, part, ctl, h_outer, h_inner,
+                                                                inner_rtol, mixed, max_outer, 1);
+        }
+      }
       if (e == cudaSuccess) {
         // inner WHILE node in the outer body
         cudaStreamCaptureStatus status;
@@ -715,9 +938,9 @@ cudaError_t Solver::build_graph(double* x, float* phi32, double phi_c, double ph
       }
       if (e == cudaSuccess) {
         if (mixed) {
-          PIC_LAUNCH(G, kSB, 0, s1, k_axpy_out<float>)(L, x, p32.d, phi32, phi_c, dphi_dk);
+          PIC_LAUNCH(G, kSB, 0, s1, k_update_ff)(L.nu, phi32, lo32, p32.d, ctl);
         } else {
-          PIC_LAUNCH(G, kSB, 0, s1, k_axpy_out<double>)(L, x, p64.d, nullptr, phi_c, dphi_dk);
+          PIC_LAUNCH(PGd, kB3, 0, s1, k_axpy_out<double>)(L, x, p64.d, nullptr, phi_c, dphi_dk, ctl);
         }
       }
       cudaGraph_t tmp1;
@@ -755,6 +978,7 @@ cudaError_t Solver::launch(cudaStream_t s) {
 cudaError_t Solver::run_host(cudaStream_t s) {
   const Lv L = lv_of(plan[0]);
   const int G = sgrid(L.nu);
+  const dim3 PGd = g3(L, L.nx);
   const int mixed = precision != 0;
   const cudaGraphConditionalHandle none = 0;
   auto read = [&]() -> cudaError_t {
@@ -762,12 +986,15 @@ cudaError_t Solver::run_host(cudaStream_t s) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return e;
   };
-  PIC_LAUNCH(G, kSB, 0, s, k_dot<double>)(L.nu, b, b, part);
-  PIC_LAUNCH(1, kFinBlock, 0, s, k_fin_bb)(part, G, ctl, h_rtol, h_maxit);
+  if (mixed) PIC_LAUNCH(PGd, kB3, 0, s, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, h_rtol, h_maxit);
+  else PIC_LAUNCH(G, kSB, 0, s, k_dot_bb)(L.nu, b, part, ctl, h_rtol, h_maxit);
   for (int outer = 0; outer < max_outer + 1; ++outer) {
-    if (mixed) PIC_LAUNCH(G, kSB, 0, s, k_residual_prep<float>)(L, hx, b, p32.r, p32.d, part, ctl);
-    else PIC_LAUNCH(G, kSB, 0, s, k_residual_prep<double>)(L, hx, b, p64.r, p64.d, part, ctl);
-    PIC_LAUNCH(1, kFinBlock, 0, s, k_fin_outer)(part, G, ctl, none, none, inner_rtol, mixed, max_outer, 0);
+    if (mixed)
+      PIC_LAUNCH(PGd, kB3, 0, s, k_residual_ff)(L, hphi32, lo32, f32, p32.r, p32.d, h_phi_c, h_dphi_dk, part, ctl, none,
+                                                 none, inner_rtol, max_outer, 0);
+    else
+      PIC_LAUNCH(PGd, kB3, 0, s, k_residual_prep<double>)(L, hx, b, ax, p64.r, p64.d, part, ctl, none, none, inner_rtol,
+                                                           mixed, max_outer, 0);
     cudaError_t e = read();
     if (e != cudaSuccess) return e;
     const bool go = host_ctl->more != 0;
@@ -777,11 +1004,28 @@ cudaError_t Solver::run_host(cudaStream_t s) {
       if ((e = read()) != cudaSuccess) return e;
       if (!host_ctl->more) break;
     }
-    if (mixed) PIC_LAUNCH(G, kSB, 0, s, k_axpy_out<float>)(L, hx, p32.d, hphi32, h_phi_c, h_dphi_dk);
-    else PIC_LAUNCH(G, kSB, 0, s, k_axpy_out<double>)(L, hx, p64.d, nullptr, h_phi_c, h_dphi_dk);
+    if (mixed) PIC_LAUNCH(G, kSB, 0, s, k_update_ff)(L.nu, hphi32, lo32, p32.d, ctl);
+    else PIC_LAUNCH(PGd, kB3, 0, s, k_axpy_out<double>)(L, hx, p64.d, nullptr, h_phi_c, h_dphi_dk, ctl);
     if (!go) break;
   }
   return cudaGetLastError();
+}
+
+cudaError_t Solver::phi64_from_ff(cudaStream_t s) {
+  const Lv L = lv_of(plan[0]);
+  PIC_LAUNCH(g3(L, L.nx), kB3, 0, s, k_phi_from_ff)(L, hphi32, lo32, hx, h_phi_c, h_dphi_dk);
+  return cudaGetLastError();
+}
+
+cudaError_t Solver::ff_from_phi64(const double* x, cudaStream_t s) {
+  const Lv L = lv_of(plan[0]);
+  PIC_LAUNCH(g3(L, L.nx), kB3, 0, s, k_ff_from_phi)(L, x, hphi32, lo32, h_phi_c, h_dphi_dk);
+  return cudaGetLastError();
+}
+
+// x was written outside the solver: the next residual takes the stencil.
+cudaError_t Solver::invalidate(cudaStream_t s) {
+  return cudaMemsetAsync(&ctl->ax_valid, 0, sizeof(int), s);
 }
 
 SolveResult Solver::result(cudaStream_t s) {

@@ -103,7 +103,7 @@ struct HostXsec {
   double sig_max = 0.0;
   // device tables
   double *dE = nullptr, *dsig = nullptr;
-  float *dEf = nullptr, *dsigf = nullptr;
+  float *dEf = nullptr, *dsigf = nullptr, *dslopef = nullptr;
   int* dbucket = nullptr;
   XsDev dev{};
 };
@@ -133,7 +133,8 @@ struct Instance {
   double* phi = nullptr;
   double4_32a* E64 = nullptr;
   float4* E32 = nullptr;
-  float* phi32 = nullptr;  // MIXED: (float)(phi - vacuum potential) at nodes
+  float* phi32 = nullptr;  // MIXED: FP32 deviation of phi from the vacuum potential at nodes
+  bool phi64_stale = false;  // MIXED: phi (FP64) not yet rebuilt from the solver's float-float state
   float* acc8 = nullptr;   // MIXED: cell-centric deposit accumulator (8 per cell)
   int32_t* ncount[kMaxSpecies]{};
   // ionization bookkeeping
@@ -236,6 +237,7 @@ void free_instance(Instance* I) {
     cudaFree(x.dsig);
     cudaFree(x.dEf);
     cudaFree(x.dsigf);
+    cudaFree(x.dslopef);
     cudaFree(x.dbucket);
   }
   cudaFree(I->cnt);
@@ -344,7 +346,11 @@ pic_status build_xsec(pic_handle* h, HostXsec& X) {
   CK(h, dalloc(&X.dEf, n));
   CK(h, dalloc(&X.dsigf, n));
   CK(h, dalloc(&X.dbucket, kXsBuckets));
+  CK(h, dalloc(&X.dslopef, std::max(n - 1, 1)));
   std::vector<float> Ef(X.E.begin(), X.E.end()), sf(X.sig.begin(), X.sig.end());
+  std::vector<float> slope(std::max(n - 1, 1), 0.f);
+  for (int i = 0; i + 1 < n; ++i) slope[i] = (float)((X.sig[i + 1] - X.sig[i]) / (X.E[i + 1] - X.E[i]));
+  CK(h, cudaMemcpy(X.dslopef, slope.data(), sizeof(float) * slope.size(), cudaMemcpyHostToDevice));
   CK(h, cudaMemcpy(X.dE, X.E.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
   CK(h, cudaMemcpy(X.dsig, X.sig.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
   CK(h, cudaMemcpy(X.dEf, Ef.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
@@ -374,10 +380,19 @@ pic_status build_xsec(pic_handle* h, HostXsec& X) {
   X.dev.sig = X.dsig;
   X.dev.Ef = X.dEf;
   X.dev.sigf = X.dsigf;
+  X.dev.slopef = X.dslopef;
   X.dev.bucket = X.dbucket;
   X.dev.lnE0 = lnE0;
   X.dev.inv_dln = inv;
   return PIC_OK;
+}
+
+// MIXED path: rebuild the FP64 potential from the solver's float-float state
+// before anything reads it.
+cudaError_t ensure_phi64(Instance* I, cudaStream_t st) {
+  if (!I->mixed || !I->phi64_stale) return cudaSuccess;
+  I->phi64_stale = false;
+  return I->solver.phi64_from_ff(st);
 }
 
 pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** out) {
@@ -409,6 +424,8 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
   g.nplane = (long long)c.nx * c.ny;
   g.ncell = g.nplane * c.nz;
   g.nnode = g.nplane * (c.nz + 1);
+  g.fdx = make_fastdiv(c.nx);
+  g.fdy = make_fastdiv(c.ny);
 
   for (int x = 0; x < c.nxsec; ++x) {
     HostXsec X;
@@ -544,10 +561,13 @@ McArgs mc_args(Instance* I, int proj) {
     m.ch[a] = X.dev;
     m.ncount[a] = I->ncount[X.c.target];
     m.dens[a] = I->species[X.c.target].weight * inv_h3;
+    m.dens_f[a] = (float)m.dens[a];
     const double bd = I->bg_density > 0 ? I->bg_density : m.dens[a];
     m.bound_f[a] = (float)(X.sig_max * bd * 1.0001);
   }
   m.half_m_over_e = 0.5 * I->species[proj].mass_kg / kQe;
+  m.half_m_over_e_f = (float)m.half_m_over_e;
+  m.bg_density_f = (float)I->bg_density;
   m.mass = I->species[proj].mass_kg;
   m.key = make_uint2((uint32_t)I->cfg.seed, (uint32_t)(I->cfg.seed >> 32));
   m.step = I->step;
@@ -681,10 +701,18 @@ pic_status step_instance(pic_handle* h, Instance* I) {
   T.end(st);
   // a4 Poisson solve
   T.begin(PIC_PH_SOLVE, st);
-  launch_rhs(g, I->rho64, I->rho32, I->solver.b, st);
-  double* x = I->phi + g.nplane;
-  if (I->cfg.warm_start == PIC_WARM_ZERO) CK(h, cudaMemsetAsync(x, 0, sizeof(double) * I->solver.n, st));
+  if (I->mixed) {
+    launch_rhs_f32(g, nullptr, I->rho32, I->solver.f32, st);
+    if (I->cfg.warm_start == PIC_WARM_ZERO) CK(h, I->solver.ff_from_phi64(nullptr, st));
+  } else {
+    launch_rhs(g, I->rho64, nullptr, I->solver.b, st);
+    if (I->cfg.warm_start == PIC_WARM_ZERO) {
+      CK(h, cudaMemsetAsync(I->phi + g.nplane, 0, sizeof(double) * I->solver.n, st));
+      CK(h, I->solver.invalidate(st));
+    }
+  }
   CK(h, I->solver.launch(st));
+  if (I->mixed) I->phi64_stale = true;
   T.end(st);
   // a5 node field
   T.begin(PIC_PH_EFIELD, st);
@@ -844,6 +872,7 @@ pic_status pic_create(const pic_instance_cfg* cfgs, int32_t n_instances, void* c
       return st;
     }
     launch_phi_planes(I->g, I->phi, h->stream);
+    if (I->mixed) I->solver.ff_from_phi64(I->phi + I->g.nplane, h->stream);
   }
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
@@ -964,6 +993,11 @@ pic_status pic_step(pic_handle* h, int32_t nsteps) {
         return st;
       }
       const int e = I->host_cnt->error;
+      if (e) {
+        // reported once: clear the device flags so that later steps start clean
+        CK(h, cudaMemsetAsync(&I->cnt->error, 0, sizeof(int), h->stream));
+        I->host_cnt->error = 0;
+      }
       if (e & (ERR_CAPACITY | ERR_EVENTS)) return fail(h, PIC_ECAPACITY, "store or event capacity exceeded (flags %d)", e);
       if (e & ERR_TIMEOUT) return fail(h, PIC_ETIMEOUT, "device wait timed out");
     }
@@ -984,6 +1018,7 @@ pic_status pic_moments(pic_handle* h, int32_t inst, pic_moments_t* out) {
     if (I->mixed) launch_kinetic<StoreMx>(I->smx[sp][c], &I->cnt->n[c][sp], I->cap[sp], I->red + sp, s);
     else launch_kinetic<Store64>(I->s64[sp][c], &I->cnt->n[c][sp], I->cap[sp], I->red + sp, s);
   }
+  CK(h, ensure_phi64(I, s));
   launch_field_energy(I->g, I->phi, I->red + 16, s);
   double red[64];
   CK(h, cudaMemcpyAsync(red, I->red, sizeof(red), cudaMemcpyDeviceToHost, s));
@@ -1080,6 +1115,7 @@ pic_status pic_get_field(pic_handle* h, int32_t inst, int32_t which, int32_t spe
   if (!host_out) return fail(h, PIC_EINVAL, "host_out is NULL");
   const Grid& g = I->g;
   if (which == PIC_FIELD_PHI) {
+    CK(h, ensure_phi64(I, h->stream));
     CK(h, cudaMemcpyAsync(host_out, I->phi, sizeof(double) * g.nnode, cudaMemcpyDeviceToHost, h->stream));
   } else if (which == PIC_FIELD_RHO) {
     if (I->mixed) {
@@ -1107,6 +1143,11 @@ pic_status pic_set_phi(pic_handle* h, int32_t inst, const double* host_phi) {
   if (!host_phi) return fail(h, PIC_EINVAL, "host_phi is NULL");
   CK(h, cudaMemcpyAsync(I->phi, host_phi, sizeof(double) * I->g.nnode, cudaMemcpyHostToDevice, h->stream));
   launch_phi_planes(I->g, I->phi, h->stream);
+  CK(h, I->solver.invalidate(h->stream));
+  if (I->mixed) {
+    CK(h, I->solver.ff_from_phi64(I->phi + I->g.nplane, h->stream));
+    I->phi64_stale = false;
+  }
   CK(h, cudaStreamSynchronize(h->stream));
   return PIC_OK;
 }
@@ -1117,27 +1158,49 @@ pic_status pic_solve(pic_handle* h, int32_t inst, const double* rho, double* phi
   Instance* I = h->inst[inst];
   if (!rho || !phi) return fail(h, PIC_EINVAL, "rho and phi are required");
   const Grid& g = I->g;
-  double *drho = nullptr, *dphi = nullptr;
+  cudaStream_t s = h->stream;
+  const long long nu = I->solver.n;
+  CK(h, ensure_phi64(I, s));
+  double *save_phi = nullptr, *drho = nullptr;
+  float *save32 = nullptr, *save_lo = nullptr;
+  CK(h, dalloc(&save_phi, g.nnode));
   CK(h, dalloc(&drho, g.nnode));
-  CK(h, dalloc(&dphi, g.nnode));
-  CK(h, cudaMemcpyAsync(drho, rho, sizeof(double) * g.nnode, cudaMemcpyHostToDevice, h->stream));
-  CK(h, cudaMemcpyAsync(dphi, phi, sizeof(double) * g.nnode, cudaMemcpyHostToDevice, h->stream));
-  // the recorded solver works on the instance's phi: keep it in dphi meanwhile
-  launch_phi_planes(g, dphi, h->stream);
-  CK(h, cudaMemcpyAsync(drho, I->phi, sizeof(double) * g.nnode, cudaMemcpyDeviceToDevice, h->stream));
-  double* drho_in = nullptr;
-  CK(h, dalloc(&drho_in, g.nnode));
-  CK(h, cudaMemcpyAsync(drho_in, rho, sizeof(double) * g.nnode, cudaMemcpyHostToDevice, h->stream));
-  CK(h, cudaMemcpyAsync(I->phi, dphi, sizeof(double) * g.nnode, cudaMemcpyDeviceToDevice, h->stream));
-  launch_rhs(g, drho_in, nullptr, I->solver.b, h->stream);
-  CK(h, I->solver.launch(h->stream));
-  CK(h, cudaMemcpyAsync(phi, I->phi, sizeof(double) * g.nnode, cudaMemcpyDeviceToHost, h->stream));
-  CK(h, cudaMemcpyAsync(I->phi, drho, sizeof(double) * g.nnode, cudaMemcpyDeviceToDevice, h->stream));
-  SolveResult r = I->solver.result(h->stream);
-  cudaError_t e = cudaStreamSynchronize(h->stream);
-  cudaFree(drho_in);
+  // the recorded solver works on the instance's potential (and, MIXED, on its
+  // float-float state): keep them meanwhile
+  CK(h, cudaMemcpyAsync(save_phi, I->phi, sizeof(double) * g.nnode, cudaMemcpyDeviceToDevice, s));
+  if (I->mixed) {
+    CK(h, dalloc(&save32, g.nnode));
+    CK(h, dalloc(&save_lo, nu));
+    CK(h, cudaMemcpyAsync(save32, I->phi32, sizeof(float) * g.nnode, cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaMemcpyAsync(save_lo, I->solver.lo32, sizeof(float) * nu, cudaMemcpyDeviceToDevice, s));
+  }
+  // initial guess: the caller's phi with the electrode planes
+  CK(h, cudaMemcpyAsync(I->phi, phi, sizeof(double) * g.nnode, cudaMemcpyHostToDevice, s));
+  launch_phi_planes(g, I->phi, s);
+  CK(h, cudaMemcpyAsync(drho, rho, sizeof(double) * g.nnode, cudaMemcpyHostToDevice, s));
+  if (I->mixed) {
+    CK(h, I->solver.ff_from_phi64(I->phi + g.nplane, s));
+    launch_rhs_f32(g, drho, nullptr, I->solver.f32, s);
+  } else {
+    CK(h, I->solver.invalidate(s));
+    launch_rhs(g, drho, nullptr, I->solver.b, s);
+  }
+  CK(h, I->solver.launch(s));
+  if (I->mixed) CK(h, I->solver.phi64_from_ff(s));
+  CK(h, cudaMemcpyAsync(phi, I->phi, sizeof(double) * g.nnode, cudaMemcpyDeviceToHost, s));
+  SolveResult r = I->solver.result(s);
+  CK(h, cudaMemcpyAsync(I->phi, save_phi, sizeof(double) * g.nnode, cudaMemcpyDeviceToDevice, s));
+  if (I->mixed) {
+    CK(h, cudaMemcpyAsync(I->phi32, save32, sizeof(float) * g.nnode, cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaMemcpyAsync(I->solver.lo32, save_lo, sizeof(float) * nu, cudaMemcpyDeviceToDevice, s));
+  } else {
+    CK(h, I->solver.invalidate(s));
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(save_lo);
+  cudaFree(save32);
   cudaFree(drho);
-  cudaFree(dphi);
+  cudaFree(save_phi);
   if (e != cudaSuccess) return fail(h, PIC_ECUDA, "solve failed: %s", cudaGetErrorString(e));
   if (iters) *iters = r.iters;
   if (resid_rel) *resid_rel = r.resid_rel;

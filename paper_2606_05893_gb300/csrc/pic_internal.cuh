@@ -70,8 +70,44 @@ __device__ __forceinline__ double u01_64(uint32_t a, uint32_t b) {
   const double one_m = __hiloint2double(0x3FF00000 | (a >> 12), (a << 20) | (b >> 12));
   return (one_m - 1.0) + 0x1p-53;
 }
-// FP32 companion of u01_64 from the same a: |u01_32(a) - u01_64(a, b)| <= 2^-25.
-__device__ __forceinline__ float u01_32(uint32_t a) { return ((float)(a >> 8) + 0.5f) * 0x1p-24f; }
+// FP32 companion of u01_64 from the same a: the top 23 bits as the float
+// 1 + m 2^-23 in [1,2), shifted to the midpoint of its interval, so that
+// |u01_32(a) - u01_64(a, b)| <= 2^-24 (no int->float conversion).
+__device__ __forceinline__ float u01_32(uint32_t a) {
+  return (__uint_as_float(0x3F800000u | (a >> 9)) - 1.0f) + 0x1p-24f;
+}
+
+// ---------------------------------------------------------------------------
+// Division by a loop-invariant divisor without integer division (whose int <->
+// float conversions run on GB300's narrow FP64/conversion pipe): for 1 < d < 2^31
+// and 0 <= n < 2^31, n / d = umulhi(n, m) >> (s - 1) with s = ceil(log2 d),
+// m = ceil(2^(31+s) / d) (Granlund-Montgomery round-up method).
+// ---------------------------------------------------------------------------
+struct FastDiv {
+  uint32_t m;
+  int s, d;
+};
+inline FastDiv make_fastdiv(int d) {
+  FastDiv f{0u, 0, d};
+  if (d > 1) {
+    int s = 0;
+    while ((1ll << s) < (long long)d) ++s;
+    const unsigned __int128 num = (unsigned __int128)1 << (31 + s);
+    f.m = (uint32_t)((num + (unsigned __int128)(d - 1)) / (unsigned __int128)d);
+    f.s = s;
+  }
+  return f;
+}
+__device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
+  return f.d == 1 ? n : (int)(__umulhi((unsigned)n, f.m) >> (f.s - 1));
+}
+// n mod d for any int n (periodic wrap), d = f.d
+__device__ __forceinline__ int fwrap(int n, const FastDiv& f) {
+  if (n >= 0 && n < f.d) return n;
+  if (n >= f.d) return n - fdiv(n, f) * f.d;
+  const int a = -n - 1;  // n = -(a + 1)
+  return f.d - 1 - (a - fdiv(a, f) * f.d);
+}
 
 // ---------------------------------------------------------------------------
 // Grid description
@@ -83,6 +119,7 @@ struct Grid {
   double phi_c, phi_a;
   float h_f, inv_h_f, dt_over_h_f;
   long long ncell, nnode, nplane;
+  FastDiv fdx, fdy;  // division by nx and ny
 };
 
 __device__ __forceinline__ double wrap_coord(double x, double L, double invL) {
@@ -118,6 +155,7 @@ struct XsDev {
   const double* sig;   // [n]
   const float* Ef;     // [n]
   const float* sigf;   // [n]
+  const float* slopef; // [n - 1] (sig[i+1] - sig[i]) / (E[i+1] - E[i]), rounded from FP64
   const int* bucket;   // [kXsBuckets] lowest candidate interval per log-bucket
   float lnE0, inv_dln; // bucket = (ln E - lnE0) * inv_dln
 };

@@ -62,10 +62,10 @@ __device__ __forceinline__ void cic_weights(T fx, T fy, T fz, T w[8]) {
 }
 
 __device__ __forceinline__ void cell_ijk(const Grid& g, int cell, int& i, int& j, int& k) {
-  i = cell % g.nx;
-  const int t = cell / g.nx;
-  j = t % g.ny;
-  k = t / g.ny;
+  const int t = fdiv(cell, g.fdx);
+  i = cell - t * g.nx;
+  k = fdiv(t, g.fdy);
+  j = t - k * g.ny;
 }
 
 // ---------------------------------------------------------------------------
@@ -113,6 +113,15 @@ struct Particle64 {
   }
   __device__ __forceinline__ double v2() const { return vx * vx + vy * vy + vz * vz; }
   __device__ __forceinline__ float v2f() const { return (float)v2(); }
+  // isotropic elastic scattering at constant speed (FP64, as the oracle):
+  // cos theta = 2 U1 - 1, phi = 2 pi U2 from Philox(pid, step, TAG_SCATTER)
+  __device__ __forceinline__ void scatter_isotropic(const uint4& d) {
+    const double ct = 2.0 * u01_64(d.x, d.y) - 1.0;
+    const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    const double ph = 2.0 * kPi * u01_64(d.z, d.w);
+    const double uu = sqrt(v2());
+    set_v(uu * st * cos(ph), uu * st * sin(ph), uu * ct);
+  }
   __device__ __forceinline__ void set_v(double a, double b, double c) {
     vx = a;
     vy = b;
@@ -156,11 +165,23 @@ struct ParticleMx {
     vy = fmaf(a.qm_dt_f, e.y, vy);
     vz = fmaf(a.qm_dt_f, e.z, vz);
   }
-  // offset += v dt / h; whole cells move the integer index (periodic in x, y)
+  // offset += v dt / h; whole cells move the integer index (periodic in x, y).
+  // floor(o) without conversions: adding 1.5 2^23 rounds o to an integer in the
+  // float's mantissa (|o| < 2^22), read back as an int, then corrected down.
   __device__ __forceinline__ static int split(float& o) {
-    const float f = floorf(o);
+    if (!(fabsf(o) < 4194304.f)) {  // far outside any cell step: conversion path
+      const float f = floorf(o);
+      o -= f;
+      return (int)f;
+    }
+    const float t = o + 12582912.f;
+    float f = t - 12582912.f;
+    int d = __float_as_int(t) - 0x4B400000;
+    if (f > o) {
+      f -= 1.f;
+      d -= 1;
+    }
     o -= f;
-    int d = (int)f;
     if (o >= 1.f) {
       o -= 1.f;
       d += 1;
@@ -177,10 +198,8 @@ struct ParticleMx {
     k += dk;
     if (k < 0) return -1;
     if (k >= g.nz) return 1;
-    i = (i + di) % g.nx;
-    if (i < 0) i += g.nx;
-    j = (j + dj) % g.ny;
-    if (j < 0) j += g.ny;
+    i = fwrap(i + di, g.fdx);
+    j = fwrap(j + dj, g.fdy);
     cell = (k * g.ny + j) * g.nx + i;
     return 0;
   }
@@ -188,6 +207,20 @@ struct ParticleMx {
     return (double)vx * (double)vx + (double)vy * (double)vy + (double)vz * (double)vz;
   }
   __device__ __forceinline__ float v2f() const { return fmaf(vx, vx, fmaf(vy, vy, vz * vz)); }
+  // the same scattering in FP32 from the same draws: cos theta = U1 - (1 - U1)
+  // and sin theta = 2 sqrt(U1 (1 - U1)) with U1 and 1 - U1 each rounded once
+  // from FP64 (no cancellation near the poles), phi = 2 pi U2 via sincospif.
+  __device__ __forceinline__ void scatter_isotropic(const uint4& d) {
+    const double U1 = u01_64(d.x, d.y);
+    const float a = (float)U1, b = (float)(1.0 - U1);
+    const float ct = a - b, st = 2.f * sqrtf(a * b);
+    float sp, cp;
+    sincospif(2.f * (float)u01_64(d.z, d.w), &sp, &cp);
+    const float uu = sqrtf(v2f());
+    vx = uu * st * cp;
+    vy = uu * st * sp;
+    vz = uu * ct;
+  }
   __device__ __forceinline__ void set_v(double a, double b, double c) {
     vx = (float)a;
     vy = (float)b;
@@ -206,10 +239,12 @@ struct PTraits;
 template <>
 struct PTraits<Store64> {
   using P = Particle64;
+  static constexpr int kMinBlocks = 2;  // resident 256-thread push blocks per SM
 };
 template <>
 struct PTraits<StoreMx> {
   using P = ParticleMx;
+  static constexpr int kMinBlocks = 4;
 };
 
 __device__ __forceinline__ Particle64 store_read(const Store64& s, const Grid& g, long long i) {
@@ -336,7 +371,10 @@ struct McArgs {
   const int32_t* ncount[kMaxXsec];  // neutral counts of each channel's target
   double dens[kMaxXsec];            // w_target / h^3
   float bound_f[kMaxXsec];          // (max sigma) w_target / h^3, FP32 filter
+  float dens_f[kMaxXsec];           // dens rounded to FP32 (FP32 enclosure of Eq. 4)
   double half_m_over_e;             // E_eV = v^2 m / (2 e)
+  float half_m_over_e_f;
+  float bg_density_f;
   double mass;
   uint2 key;
   uint32_t step;
@@ -467,8 +505,8 @@ void launch_fill64(double* p, long long n, double v, cudaStream_t st);
 void launch_fill32(float* p, long long n, float v, cudaStream_t st);
 void launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t st);
 void launch_rhs(const Grid& g, const double* rho64, const float* rho32, double* b, cudaStream_t st);
+void launch_rhs_f32(const Grid& g, const double* rho64, const float* rho32, float* f, cudaStream_t st);
 void launch_efield64(const Grid& g, const double* phi, double4_32a* E, const int32_t* ncount, cudaStream_t st);
-void launch_efield32(const Grid& g, const double* phi, float4* E, cudaStream_t st);
 void launch_efield32f(const Grid& g, const float* phi32, float4* E, const int32_t* ncount, cudaStream_t st);
 void launch_phi_planes(const Grid& g, double* phi, cudaStream_t st);
 void launch_step_begin(DevCounters* cnt, const int* out_buf, int nsp, cudaStream_t st);

@@ -18,6 +18,9 @@ struct SolveCtl {
   double bb, tol2, rr_true, resid_rel;
   double rr, rz, pq, alpha, beta, tol_in2;
   int it_total, it_inner, outer, maxit, converged, more;
+  unsigned ticket;  // blocks finished in the current grid-wide sum (0 between launches)
+  int ax_valid;     // Solver::ax holds A x for the current x
+  int stopped;      // the last residual ended the outer loop
 };
 
 struct SolveResult {
@@ -58,11 +61,16 @@ struct Solver {
   int precision = 0;  // 0 FP64, 1 mixed
   long long n = 0;
   std::vector<MgLevel> plan;
-  double* b = nullptr;  // right-hand side over the unknowns
+  // FP64 path
+  double* b = nullptr;   // right-hand side over the unknowns
+  double* ax = nullptr;  // A x of the last FP64 residual (reused while x is unchanged)
+  // MIXED path: phi = vac + hi + lo over the unknowns (hi = the phi32 view)
+  float* f32 = nullptr;  // FP32 charge term h^2 rho / eps0 (no folded boundary terms)
+  float* lo32 = nullptr;
   double* part = nullptr;
   SolveCtl* ctl = nullptr;
   SolveCtl* host_ctl = nullptr;
-  double inner_rtol = 1e-4;
+  double inner_rtol = 1e-6;
   int max_outer = 40;
   Pcg<double> p64;
   Pcg<float> p32;
@@ -73,11 +81,19 @@ struct Solver {
   cudaError_t build_graph(double* x, float* phi32, double phi_c, double phi_a, int nz, double rtol, int maxit);
   cudaError_t launch(cudaStream_t s);
   cudaError_t run_host(cudaStream_t s);
+  cudaError_t invalidate(cudaStream_t s);
+  // MIXED path: FP64 phi (unknown view, hx) from (hi, lo), and back (x = nullptr: phi = 0)
+  cudaError_t phi64_from_ff(cudaStream_t s);
+  cudaError_t ff_from_phi64(const double* x, cudaStream_t s);
   // arguments of the recorded solve (also used by the host-driven loop)
   double* hx = nullptr;
-  float* hphi32 = nullptr;
+  float* hphi32 = nullptr;  // hi of the MIXED path (unknown view of phi32)
+  double h_phi_a = 0.0;
   double h_phi_c = 0.0, h_dphi_dk = 0.0, h_rtol = 1e-8;
   int h_maxit = 1;
+  // Dirichlet values folded into b on the first and last unknown planes
+  float fold_first() const { return (float)(h_phi_c + (plan[0].nz == 2 ? h_phi_a : 0.0)); }
+  float fold_last() const { return plan[0].nz == 2 ? 0.f : (float)h_phi_a; }
   SolveResult result(cudaStream_t s);
 };
 

@@ -165,6 +165,44 @@ def test_background_rates_bit_exact(pkg):
     compare_particles(sim, ref, wl, 0, TOL, TOL)
 
 
+def _breakpoint_electrons(rng, E_tab, n):
+    """Electron energies on the ionization table's points, just around its
+    threshold and spread log-uniformly over the table (isotropic directions)."""
+    k = n // 4
+    E = np.concatenate([
+        E_tab[rng.integers(1, E_tab.size - 1, k)],
+        W.CU_IONIZATION_EV * (1.0 + rng.integers(-40, 41, k) * 1e-7),
+        E_tab[rng.integers(1, E_tab.size - 1, k)] * (1.0 + rng.uniform(-3e-6, 3e-6, k)),
+        np.exp(rng.uniform(0.0, math.log(5000.0), n - 3 * k)),
+    ])
+    speed = np.sqrt(2.0 * E * W.E_CHARGE / W.M_E)
+    v = rng.standard_normal((n, 3))
+    v *= (speed / np.linalg.norm(v, axis=1))[:, None]
+    return v
+
+
+@pytest.mark.parametrize("P_target", [0.02, 0.4])
+def test_background_rates_on_table_breakpoints_bit_exact(pkg, P_target):
+    # Eq. (4) with the tabulated Lotz ionization cross-section: the kernels
+    # decide most collisions in FP32 and fall back to the FP64 rule near table
+    # points, thresholds and the U ~ P boundary; every decision must equal the
+    # oracle's FP64 one. The large-P case makes 1 - exp(-x) far from x.
+    n = 40000
+    rng = np.random.default_rng(31)
+    xs = W.cu_plasma_xsec()
+    wl = bare(nx=8, ny=8, nz=8, h=1e-8, dt=1e-17, weight=1e-30, capacity=1 << 16, xsec=xs)
+    u100 = speed_of_eV(100.0)
+    n0 = P_target / (u100 * (float(xs[0].sigma_m2.max()) + float(xs[1].sigma_m2[0])) * wl.dt)
+    x = (0.3 + 0.4 * rng.random((n, 3))) * np.array(wl.L)
+    wl.preload = [(x, _breakpoint_electrons(rng, xs[0].E_eV, n)), (np.zeros((0, 3)), np.zeros((0, 3))),
+                  (np.zeros((0, 3)), np.zeros((0, 3)))]
+    sim, ref = run_pair(pkg, wl, 2, background_density=n0)
+    mg, mo = sim.moments(), ref.moments()
+    assert mg["n_ionization"] > 20 and mg["n_elastic"] > 100
+    assert mg["n_elastic"] == mo["n_elastic"] and mg["n_ionization"] == mo["n_ionization"]
+    compare_particles(sim, ref, wl, 0, TOL, TOL)
+
+
 def test_sort_permutation_and_offsets_bit_exact(pkg):
     wl = W.config_tiny(seed=9)
     sim = pkg.Simulation(wl)
