@@ -87,11 +87,32 @@ __global__ void __launch_bounds__(kDepBlock) k_deposit_fp64(DepositArgs<Store64>
   }
 }
 
+// Runs of equal keys among consecutive lanes (a cell-sorted store keeps the
+// particles of a cell together): sums each run's values into its first lane
+// (suffix sums bounded by the run's last lane, five shuffle steps) and returns
+// true there. Equal keys that are not adjacent form separate runs.
+template <int N>
+__device__ __forceinline__ bool warp_run_sum(int key, float (&w)[N]) {
+  const int lane = threadIdx.x & 31;
+  const int next = __shfl_down_sync(0xffffffffu, key, 1);
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const unsigned tail = __ballot_sync(0xffffffffu, lane == 31 || next != key);
+  const int run_end = lane + __ffs(tail >> lane) - 1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      const float t = __shfl_down_sync(0xffffffffu, w[c], o);
+      if (lane + o <= run_end) w[c] += t;
+    }
+  }
+  return lane == 0 || prev != key;
+}
+
 __global__ void __launch_bounds__(kDepBlock) k_deposit_mx(DepositArgs<StoreMx> a) {
   const long long n = (long long)a.cnt->n[a.cur][a.species];
   const Grid& g = a.g;
   const float q = (float)a.qw_h3;
-  const int lane = threadIdx.x & 31;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += gstride()) {
     const long long i = base + threadIdx.x;
     const bool valid = i < n;
@@ -103,9 +124,7 @@ __global__ void __launch_bounds__(kDepBlock) k_deposit_mx(DepositArgs<StoreMx> a
 #pragma unroll
       for (int c = 0; c < 8; ++c) w[c] *= q;
     }
-    warp_combine_cell(cell, w);
-    const unsigned peers = __match_any_sync(0xffffffffu, cell);
-    if (valid && lane == __ffs(peers) - 1) {
+    if (warp_run_sum(cell, w) && valid) {
       int ci, cj, ck;
       cell_ijk(g, cell, ci, cj, ck);
       long long idx[8];
@@ -120,9 +139,16 @@ template <class S>
 __global__ void __launch_bounds__(kDepBlock) k_count_neutrals(DepositArgs<S> a) {
   const long long n = (long long)a.cnt->n[a.cur][a.species];
   const Grid& g = a.g;
-  for (long long i = gtid(); i < n; i += gstride()) {
-    const auto p = store_read(a.st, g, i);
-    if (p.pid != kPidDead) atomicAdd(&a.ncount[particle_cell(p)], 1);
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += gstride()) {
+    const long long i = base + threadIdx.x;
+    int cell = -1;
+    float one[1] = {0.f};  // counts are exact in FP32 (a warp holds 32 at most)
+    if (i < n) {
+      const auto p = store_read(a.st, g, i);
+      cell = (int)particle_cell(p);
+      one[0] = p.pid != kPidDead ? 1.f : 0.f;
+    }
+    if (warp_run_sum(cell, one) && i < n && one[0] > 0.f) atomicAdd(&a.ncount[cell], (int)one[0]);
   }
 }
 

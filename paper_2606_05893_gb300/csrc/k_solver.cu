@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "pic_internal.cuh"
@@ -24,6 +25,42 @@
 #include "pic_solver.cuh"
 
 namespace pic {
+
+// Programmatic dependent launch: each solver kernel may be launched while its
+// predecessor drains (it waits here until the predecessor has completed and its
+// writes are visible), and lets its own successor launch as soon as all of its
+// blocks are running. Hides most of the launch gap between the many short
+// multigrid kernels. A no-op for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+bool g_pdl = true;  // cleared when a graph with programmatic edges cannot be built
+
+template <class K>
+struct PdlLaunch {
+  K k;
+  dim3 g, b;
+  size_t smem;
+  cudaStream_t s;
+  template <class... A>
+  void operator()(A&&... a) const {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = g_pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k, std::forward<A>(a)...);
+  }
+};
+#define SOLVER_LAUNCH(grid, block, smem, stream, ...) \
+  (++::pic::g_launches), ::pic::PdlLaunch<decltype(&__VA_ARGS__)>{&__VA_ARGS__, dim3(grid), dim3(block), (size_t)(smem), stream}
 
 constexpr int kSB = 256;
 constexpr int kMaxRedBlocks = 152 * 8;  // 1-D reductions over whole vectors
@@ -77,6 +114,7 @@ __device__ __forceinline__ T nb_sum(const Lv& L, const T* __restrict__ x, int u,
 // r = b - A x (no reduction; multigrid levels)
 template <class T>
 __global__ void __launch_bounds__(256) k_residual(Lv L, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r) {
+  pdl_enter();
   ROWS3(L, L.nx) {
     if (!in_x) continue;
     const int u = k * L.pl + j * L.nx + i;
@@ -92,6 +130,7 @@ __global__ void __launch_bounds__(256) k_residual(Lv L, const T* __restrict__ x,
 // zero_init: the level starts from e = 0 (the other colour is written as 0).
 template <class T>
 __global__ void __launch_bounds__(256) k_smooth(Lv L, T* __restrict__ e, const T* __restrict__ b, int color, int zero_init) {
+  pdl_enter();
   const T sixth = (T)(1.0 / 6.0);
   const int hx = L.nx >> 1;
   const int m = blockIdx.x * kBX + threadIdx.x;
@@ -113,6 +152,7 @@ __global__ void __launch_bounds__(256) k_smooth(Lv L, T* __restrict__ e, const T
 // b_c = 4 * full-weighting(r_f) on coarse unknowns (grid over the coarse level)
 template <class T>
 __global__ void __launch_bounds__(256) k_restrict(Lv F, Lv Cc, const T* __restrict__ r, T* __restrict__ bc) {
+  pdl_enter();
   const int I = blockIdx.x * kBX + threadIdx.x;
   const int K = blockIdx.z;
   if (I >= Cc.nx) return;
@@ -142,6 +182,7 @@ __global__ void __launch_bounds__(256) k_restrict(Lv F, Lv Cc, const T* __restri
 // e_f += P e_c (trilinear; coarse Dirichlet planes carry 0); grid over the fine level
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong(Lv F, Lv Cc, const T* __restrict__ ec, T* __restrict__ ef) {
+  pdl_enter();
   const int kn = blockIdx.z + 1;  // fine node plane
   const int K0 = kn >> 1;
   const bool kodd = kn & 1;
@@ -179,6 +220,7 @@ __global__ void __launch_bounds__(256) k_prolong(Lv F, Lv Cc, const T* __restric
 
 template <class T>
 __global__ void k_coarse(long long n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ e) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -193,22 +235,27 @@ __global__ void k_coarse(long long n, const T* __restrict__ Ainv, const T* __res
 
 template <class T>
 __global__ void k_axpy_cast(long long n, double* __restrict__ x, const T* __restrict__ d) {
+  pdl_enter();
   for (long long u = gtid(); u < n; u += gstride()) x[u] += (double)d[u];
 }
 template <class T>
 __global__ void k_zero(long long n, T* __restrict__ x) {
+  pdl_enter();
   for (long long u = gtid(); u < n; u += gstride()) x[u] = (T)0;
 }
 template <class T>
 __global__ void k_copy(long long n, T* __restrict__ d, const T* __restrict__ s) {
+  pdl_enter();
   for (long long u = gtid(); u < n; u += gstride()) d[u] = s[u];
 }
 
 __global__ void k_copy_cast(long long n, float* __restrict__ d, const double* __restrict__ s) {
+  pdl_enter();
   for (long long u = gtid(); u < n; u += gstride()) d[u] = (float)s[u];
 }
 template <class T>
 __global__ void k_jacobi_scale(long long n, T* z) {
+  pdl_enter();
   for (long long u = gtid(); u < n; u += gstride()) z[u] *= (T)(1.0 / 6.0);
 }
 
@@ -333,8 +380,8 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
   if (!rb_ok) {
     // Jacobi preconditioner: z = rhs / 6
     const Lv L = lv_of(levels[0]);
-    PIC_LAUNCH(sgrid(L.nu), kSB, 0, s, k_copy<T>)(L.nu, z, rhs);
-    PIC_LAUNCH(sgrid(L.nu), kSB, 0, s, k_jacobi_scale<T>)(L.nu, z);
+    SOLVER_LAUNCH(sgrid(L.nu), kSB, 0, s, k_copy<T>)(L.nu, z, rhs);
+    SOLVER_LAUNCH(sgrid(L.nu), kSB, 0, s, k_jacobi_scale<T>)(L.nu, z);
     return;
   }
   std::vector<T*> E(nl), B(nl);
@@ -344,37 +391,37 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
   }
   for (int l = 0; l < nl - 1; ++l) {
     const Lv L = lv_of(levels[l]);
-    PIC_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 0, 1);
-    PIC_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 1, 0);
-    PIC_LAUNCH(g3(L, L.nx), kB3, 0, s, k_residual<T>)(L, E[l], B[l], r[l]);
+    SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 0, 1);
+    SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 1, 0);
+    SOLVER_LAUNCH(g3(L, L.nx), kB3, 0, s, k_residual<T>)(L, E[l], B[l], r[l]);
     const Lv C = lv_of(levels[l + 1]);
-    PIC_LAUNCH(g3(C, C.nx), kB3, 0, s, k_restrict<T>)(L, C, r[l], B[l + 1]);
+    SOLVER_LAUNCH(g3(C, C.nx), kB3, 0, s, k_restrict<T>)(L, C, r[l], B[l + 1]);
   }
   {
     const Lv C = lv_of(levels[nl - 1]);
     if (coarse_dense) {
       const int cg = (int)std::min<long long>((C.nu * 32 + kSB - 1) / kSB, 4096);
-      PIC_LAUNCH(cg, kSB, 0, s, k_coarse<T>)(C.nu, Ainv, B[nl - 1],
+      SOLVER_LAUNCH(cg, kSB, 0, s, k_coarse<T>)(C.nu, Ainv, B[nl - 1],
                                                                                               E[nl - 1]);
     } else {
-      PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 1);
-      PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
+      SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 1);
+      SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
       for (int it = 0; it < coarse_sweeps; ++it) {
-        PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
-        PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
-        PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
-        PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
+        SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
+        SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
+        SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
+        SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
       }
-      PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
-      PIC_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
+      SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
+      SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
     }
   }
   for (int l = nl - 2; l >= 0; --l) {
     const Lv L = lv_of(levels[l]);
     const Lv C = lv_of(levels[l + 1]);
-    PIC_LAUNCH(g3(L, L.nx), kB3, 0, s, k_prolong<T>)(L, C, E[l + 1], E[l]);
-    PIC_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 1, 0);
-    PIC_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 0, 0);
+    SOLVER_LAUNCH(g3(L, L.nx), kB3, 0, s, k_prolong<T>)(L, C, E[l + 1], E[l]);
+    SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 1, 0);
+    SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 0, 0);
   }
 }
 
@@ -455,6 +502,7 @@ __device__ __forceinline__ void fin_bb(double bb, SolveCtl* c, double rtol, int 
 // b.b -> tolerance; start of a solve
 __global__ void __launch_bounds__(kSB) k_dot_bb(int n, const double* __restrict__ b, double* part, SolveCtl* c,
                                                 double rtol, int maxit) {
+  pdl_enter();
   double acc = 0.0;
   for (int u = blockIdx.x * kSB + threadIdx.x; u < n; u += gridDim.x * kSB) acc += b[u] * b[u];
   double bb;
@@ -493,6 +541,7 @@ __global__ void __launch_bounds__(256) k_residual_prep(Lv L, double* __restrict_
                                                        cudaGraphConditionalHandle h_outer,
                                                        cudaGraphConditionalHandle h_inner, double inner_rtol,
                                                        int mixed, int max_outer, int use_graph) {
+  pdl_enter();
   Tin acc = 0;
   const bool zero_x = c->bb == 0.0;
   const bool cached = c->ax_valid != 0;
@@ -570,6 +619,7 @@ __device__ __forceinline__ void nb_sum_ff(const Lv& L, const float* __restrict__
 // sum f.f + folded terms -> tolerance (b = f + fold never materialised)
 __global__ void __launch_bounds__(256) k_dot_bb_ff(Lv L, const float* __restrict__ f, float fold_first, float fold_last,
                                                    double* part, SolveCtl* c, double rtol, int maxit) {
+  pdl_enter();
   float acc = 0.f;
   ROWS3(L, L.nx) {
     if (!in_x) continue;
@@ -591,6 +641,7 @@ __global__ void __launch_bounds__(256) k_residual_ff(Lv L, float* __restrict__ h
                                                      SolveCtl* c, cudaGraphConditionalHandle h_outer,
                                                      cudaGraphConditionalHandle h_inner, double inner_rtol,
                                                      int max_outer, int use_graph) {
+  pdl_enter();
   float acc = 0.f;
   const bool zero_x = c->bb == 0.0;
   ROWS3(L, L.nx) {
@@ -628,6 +679,7 @@ __global__ void __launch_bounds__(256) k_residual_ff(Lv L, float* __restrict__ h
 // (hi, lo) += d, renormalised (hi = fl32(hi + lo)); nothing to do once stopped
 __global__ void __launch_bounds__(kSB) k_update_ff(long long n, float* __restrict__ hi, float* __restrict__ lo,
                                                    const float* __restrict__ d, const SolveCtl* c) {
+  pdl_enter();
   if (c->stopped) return;
   for (long long u = gtid(); u < n; u += gstride()) {
     float s, e;
@@ -642,6 +694,7 @@ __global__ void __launch_bounds__(kSB) k_update_ff(long long n, float* __restric
 // phi (FP64, unknown view) = vac + hi + lo
 __global__ void __launch_bounds__(256) k_phi_from_ff(Lv L, const float* __restrict__ hi, const float* __restrict__ lo,
                                                      double* __restrict__ x, double phi_c, double dphi_dk) {
+  pdl_enter();
   const double vac = phi_c + dphi_dk * (double)(blockIdx.z + 1);
   ROWS3(L, L.nx) {
     if (!in_x) continue;
@@ -653,6 +706,7 @@ __global__ void __launch_bounds__(256) k_phi_from_ff(Lv L, const float* __restri
 // (hi, lo) from phi (FP64, unknown view; nullptr: phi = 0)
 __global__ void __launch_bounds__(256) k_ff_from_phi(Lv L, const double* __restrict__ x, float* __restrict__ hi,
                                                      float* __restrict__ lo, double phi_c, double dphi_dk) {
+  pdl_enter();
   const double vac = phi_c + dphi_dk * (double)(blockIdx.z + 1);
   ROWS3(L, L.nx) {
     if (!in_x) continue;
@@ -665,11 +719,37 @@ __global__ void __launch_bounds__(256) k_ff_from_phi(Lv L, const double* __restr
 }
 
 // r.z -> beta
+// The streaming PCG kernels move FP32 vectors as float4 (16-byte loads keep
+// four times the bytes in flight per load); the FP64 instantiations and the
+// tail after the last full float4 go element by element. The level-0 vectors
+// are separate allocations, hence 16-byte aligned.
+template <class T>
+struct Vec4 {
+  static constexpr bool on = false;
+};
+template <>
+struct Vec4<float> {
+  static constexpr bool on = true;
+};
+
+// r.z -> beta
 template <class T>
 __global__ void __launch_bounds__(kSB) k_dot_rz(int n, const T* __restrict__ r, const T* __restrict__ z, double* part,
                                                 SolveCtl* c) {
+  pdl_enter();
   T acc = 0;
-  for (int u = blockIdx.x * kSB + threadIdx.x; u < n; u += gridDim.x * kSB) acc += r[u] * z[u];
+  int u0 = 0;
+  if constexpr (Vec4<T>::on) {
+    const int n4 = n >> 2;
+    const float4* r4 = reinterpret_cast<const float4*>(r);
+    const float4* z4 = reinterpret_cast<const float4*>(z);
+    for (int q = blockIdx.x * kSB + threadIdx.x; q < n4; q += gridDim.x * kSB) {
+      const float4 a = r4[q], b = z4[q];
+      acc += (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w);
+    }
+    u0 = n4 * 4;
+  }
+  for (int u = u0 + blockIdx.x * kSB + threadIdx.x; u < n; u += gridDim.x * kSB) acc += r[u] * z[u];
   double rz;
   if (!grid_total(acc, part, &c->ticket, &rz)) return;
   c->beta = c->it_inner > 0 ? rz / c->rz : 0.0;
@@ -680,6 +760,7 @@ __global__ void __launch_bounds__(kSB) k_dot_rz(int n, const T* __restrict__ r, 
 template <class T>
 __global__ void __launch_bounds__(256) k_apply_pq(Lv L, const T* __restrict__ p, T* __restrict__ q, double* part,
                                                   SolveCtl* c) {
+  pdl_enter();
   T acc = 0;
   ROWS3(L, L.nx) {
     if (!in_x) continue;
@@ -698,9 +779,26 @@ __global__ void __launch_bounds__(256) k_apply_pq(Lv L, const T* __restrict__ p,
 // p = z (first iteration of this inner solve) or z + beta p
 template <class T>
 __global__ void __launch_bounds__(kSB) k_pupdate_c(long long n, T* __restrict__ p, const T* __restrict__ z, const SolveCtl* c) {
+  pdl_enter();
   const bool first = c->it_inner == 0;
-  const T beta = (T)c->beta;
-  for (long long u = gtid(); u < n; u += gstride()) p[u] = first ? z[u] : z[u] + beta * p[u];
+  const T beta = first ? (T)0 : (T)c->beta;
+  long long u0 = 0;
+  if constexpr (Vec4<T>::on) {
+    const long long n4 = n >> 2;
+    float4* p4 = reinterpret_cast<float4*>(p);
+    const float4* z4 = reinterpret_cast<const float4*>(z);
+    for (long long q = gtid(); q < n4; q += gstride()) {
+      const float4 zv = z4[q];
+      if (first) {
+        p4[q] = zv;
+      } else {
+        const float4 pv = p4[q];
+        p4[q] = make_float4(zv.x + beta * pv.x, zv.y + beta * pv.y, zv.z + beta * pv.z, zv.w + beta * pv.w);
+      }
+    }
+    u0 = n4 * 4;
+  }
+  for (long long u = u0 + gtid(); u < n; u += gstride()) p[u] = first ? z[u] : z[u] + beta * p[u];
 }
 
 // d += alpha p ; r -= alpha q ; r.r -> inner-loop decision
@@ -708,9 +806,34 @@ template <class T>
 __global__ void __launch_bounds__(kSB) k_update_rr(long long n, T* __restrict__ d, T* __restrict__ r, const T* __restrict__ p,
                                                    const T* __restrict__ q, SolveCtl* c, double* part,
                                                    cudaGraphConditionalHandle h_inner, int use_graph) {
+  pdl_enter();
   const T alpha = (T)c->alpha;
   T acc = 0;
-  for (long long u = gtid(); u < n; u += gstride()) {
+  long long u0 = 0;
+  if constexpr (Vec4<T>::on) {
+    const long long n4 = n >> 2;
+    float4* d4 = reinterpret_cast<float4*>(d);
+    float4* r4 = reinterpret_cast<float4*>(r);
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    const float4* q4 = reinterpret_cast<const float4*>(q);
+    for (long long w = gtid(); w < n4; w += gstride()) {
+      const float4 pv = p4[w], qv = q4[w];
+      float4 dv = d4[w], rv = r4[w];
+      dv.x += alpha * pv.x;
+      dv.y += alpha * pv.y;
+      dv.z += alpha * pv.z;
+      dv.w += alpha * pv.w;
+      rv.x -= alpha * qv.x;
+      rv.y -= alpha * qv.y;
+      rv.z -= alpha * qv.z;
+      rv.w -= alpha * qv.w;
+      d4[w] = dv;
+      r4[w] = rv;
+      acc += (rv.x * rv.x + rv.y * rv.y) + (rv.z * rv.z + rv.w * rv.w);
+    }
+    u0 = n4 * 4;
+  }
+  for (long long u = u0 + gtid(); u < n; u += gstride()) {
     d[u] += alpha * p[u];
     const T rv = r[u] - alpha * q[u];
     r[u] = rv;
@@ -732,6 +855,7 @@ __global__ void __launch_bounds__(kSB) k_update_rr(long long n, T* __restrict__ 
 template <class T>
 __global__ void __launch_bounds__(256) k_axpy_out(Lv L, double* __restrict__ x, const T* __restrict__ d, float* __restrict__ phi32,
                                                   double phi_c, double dphi_dk, SolveCtl* c) {
+  pdl_enter();
   if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0 && !c->stopped)
     c->ax_valid = 0;
   const double vac = phi_c + dphi_dk * (double)(blockIdx.z + 1);  // vacuum potential of this node plane
@@ -832,11 +956,11 @@ static void capture_pcg_iteration(Pcg<T>& pc, const Lv& L, double* part, SolveCt
                                   cudaGraphConditionalHandle h_inner, cudaStream_t s, int use_graph = 1) {
   const int G = sgrid(L.nu);
   pc.mg.vcycle(pc.r, pc.z, s);
-  PIC_LAUNCH(G, kSB, 0, s, k_dot_rz<T>)(L.nu, pc.r, pc.z, part, ctl);
+  SOLVER_LAUNCH(G, kSB, 0, s, k_dot_rz<T>)(L.nu, pc.r, pc.z, part, ctl);
   const dim3 PGd = g3(L, L.nx);
-  PIC_LAUNCH(G, kSB, 0, s, k_pupdate_c<T>)(L.nu, pc.p, pc.z, ctl);
-  PIC_LAUNCH(PGd, kB3, 0, s, k_apply_pq<T>)(L, pc.p, pc.q, part, ctl);
-  PIC_LAUNCH(G, kSB, 0, s, k_update_rr<T>)(L.nu, pc.d, pc.r, pc.p, pc.q, ctl, part, h_inner, use_graph);
+  SOLVER_LAUNCH(G, kSB, 0, s, k_pupdate_c<T>)(L.nu, pc.p, pc.z, ctl);
+  SOLVER_LAUNCH(PGd, kB3, 0, s, k_apply_pq<T>)(L, pc.p, pc.q, part, ctl);
+  SOLVER_LAUNCH(G, kSB, 0, s, k_update_rr<T>)(L.nu, pc.d, pc.r, pc.p, pc.q, ctl, part, h_inner, use_graph);
 }
 
 // Add a WHILE node at the current capture position of `s`; returns its body graph.
@@ -863,8 +987,19 @@ static cudaError_t add_while(cudaStream_t s, cudaGraphConditionalHandle* h, unsi
   return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
 }
 
-// Record the solve of A x = b (x = unknown view of phi) for this instance.
+// Record the solve of A x = b (x = unknown view of phi) for this instance;
+// without programmatic launch edges if a graph holding them cannot be built.
 cudaError_t Solver::build_graph(double* x, float* phi32, double phi_c, double phi_a, int nz, double rtol, int maxit) {
+  cudaError_t e = build_graph_once(x, phi32, phi_c, phi_a, nz, rtol, maxit);
+  if (e != cudaSuccess && g_pdl) {
+    g_pdl = false;
+    e = build_graph_once(x, phi32, phi_c, phi_a, nz, rtol, maxit);
+  }
+  return e;
+}
+
+cudaError_t Solver::build_graph_once(double* x, float* phi32, double phi_c, double phi_a, int nz, double rtol,
+                                     int maxit) {
   if (exec) return cudaSuccess;
   hx = x;
   hphi32 = phi32;
@@ -890,9 +1025,9 @@ cudaError_t Solver::build_graph(double* x, float* phi32, double phi_c, double ph
   e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
     if (mixed) {
-      PIC_LAUNCH(PGd, kB3, 0, s0, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, rtol, maxit);
+      SOLVER_LAUNCH(PGd, kB3, 0, s0, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, rtol, maxit);
     } else {
-      PIC_LAUNCH(G, kSB, 0, s0, k_dot_bb)(L.nu, b, part, ctl, rtol, maxit);
+      SOLVER_LAUNCH(G, kSB, 0, s0, k_dot_bb)(L.nu, b, part, ctl, rtol, maxit);
     }
     e = add_while(s0, &h_outer, 1u, &outer_body);
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s1, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
@@ -900,10 +1035,10 @@ cudaError_t Solver::build_graph(double* x, float* phi32, double phi_c, double ph
       e = cudaGraphConditionalHandleCreate(&h_inner, outer_body, 0u, 0);
       if (e == cudaSuccess) {
         if (mixed) {
-          PIC_LAUNCH(PGd, kB3, 0, s1, k_residual_ff)(L, phi32, lo32, f32, p32.r, p32.d, phi_c, dphi_dk, part, ctl,
+          SOLVER_LAUNCH(PGd, kB3, 0, s1, k_residual_ff)(L, phi32, lo32, f32, p32.r, p32.d, phi_c, dphi_dk, part, ctl,
                                                       h_outer, h_inner, inner_rtol, max_outer, 1);
         } else {
-          PIC_LAUNCH(PGd, kB3, 0, s1, k_residual_prep<double>)(L, x, b, ax, p64.r, p64.d, part, ctl, h_outer, h_inner,
+          SOLVER_LAUNCH(PGd, kB3, 0, s1, k_residual_prep<double>)(L, x, b, ax, p64.r, p64.d, part, ctl, h_outer, h_inner,
                                                                 inner_rtol, mixed, max_outer, 1);
         }
       }
@@ -938,9 +1073,9 @@ cudaError_t Solver::build_graph(double* x, float* phi32, double phi_c, double ph
       }
       if (e == cudaSuccess) {
         if (mixed) {
-          PIC_LAUNCH(G, kSB, 0, s1, k_update_ff)(L.nu, phi32, lo32, p32.d, ctl);
+          SOLVER_LAUNCH(G, kSB, 0, s1, k_update_ff)(L.nu, phi32, lo32, p32.d, ctl);
         } else {
-          PIC_LAUNCH(PGd, kB3, 0, s1, k_axpy_out<double>)(L, x, p64.d, nullptr, phi_c, dphi_dk, ctl);
+          SOLVER_LAUNCH(PGd, kB3, 0, s1, k_axpy_out<double>)(L, x, p64.d, nullptr, phi_c, dphi_dk, ctl);
         }
       }
       cudaGraph_t tmp1;
@@ -986,14 +1121,14 @@ cudaError_t Solver::run_host(cudaStream_t s) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return e;
   };
-  if (mixed) PIC_LAUNCH(PGd, kB3, 0, s, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, h_rtol, h_maxit);
-  else PIC_LAUNCH(G, kSB, 0, s, k_dot_bb)(L.nu, b, part, ctl, h_rtol, h_maxit);
+  if (mixed) SOLVER_LAUNCH(PGd, kB3, 0, s, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, h_rtol, h_maxit);
+  else SOLVER_LAUNCH(G, kSB, 0, s, k_dot_bb)(L.nu, b, part, ctl, h_rtol, h_maxit);
   for (int outer = 0; outer < max_outer + 1; ++outer) {
     if (mixed)
-      PIC_LAUNCH(PGd, kB3, 0, s, k_residual_ff)(L, hphi32, lo32, f32, p32.r, p32.d, h_phi_c, h_dphi_dk, part, ctl, none,
+      SOLVER_LAUNCH(PGd, kB3, 0, s, k_residual_ff)(L, hphi32, lo32, f32, p32.r, p32.d, h_phi_c, h_dphi_dk, part, ctl, none,
                                                  none, inner_rtol, max_outer, 0);
     else
-      PIC_LAUNCH(PGd, kB3, 0, s, k_residual_prep<double>)(L, hx, b, ax, p64.r, p64.d, part, ctl, none, none, inner_rtol,
+      SOLVER_LAUNCH(PGd, kB3, 0, s, k_residual_prep<double>)(L, hx, b, ax, p64.r, p64.d, part, ctl, none, none, inner_rtol,
                                                            mixed, max_outer, 0);
     cudaError_t e = read();
     if (e != cudaSuccess) return e;
@@ -1004,8 +1139,8 @@ cudaError_t Solver::run_host(cudaStream_t s) {
       if ((e = read()) != cudaSuccess) return e;
       if (!host_ctl->more) break;
     }
-    if (mixed) PIC_LAUNCH(G, kSB, 0, s, k_update_ff)(L.nu, hphi32, lo32, p32.d, ctl);
-    else PIC_LAUNCH(PGd, kB3, 0, s, k_axpy_out<double>)(L, hx, p64.d, nullptr, h_phi_c, h_dphi_dk, ctl);
+    if (mixed) SOLVER_LAUNCH(G, kSB, 0, s, k_update_ff)(L.nu, hphi32, lo32, p32.d, ctl);
+    else SOLVER_LAUNCH(PGd, kB3, 0, s, k_axpy_out<double>)(L, hx, p64.d, nullptr, h_phi_c, h_dphi_dk, ctl);
     if (!go) break;
   }
   return cudaGetLastError();
@@ -1013,13 +1148,13 @@ cudaError_t Solver::run_host(cudaStream_t s) {
 
 cudaError_t Solver::phi64_from_ff(cudaStream_t s) {
   const Lv L = lv_of(plan[0]);
-  PIC_LAUNCH(g3(L, L.nx), kB3, 0, s, k_phi_from_ff)(L, hphi32, lo32, hx, h_phi_c, h_dphi_dk);
+  SOLVER_LAUNCH(g3(L, L.nx), kB3, 0, s, k_phi_from_ff)(L, hphi32, lo32, hx, h_phi_c, h_dphi_dk);
   return cudaGetLastError();
 }
 
 cudaError_t Solver::ff_from_phi64(const double* x, cudaStream_t s) {
   const Lv L = lv_of(plan[0]);
-  PIC_LAUNCH(g3(L, L.nx), kB3, 0, s, k_ff_from_phi)(L, x, hphi32, lo32, h_phi_c, h_dphi_dk);
+  SOLVER_LAUNCH(g3(L, L.nx), kB3, 0, s, k_ff_from_phi)(L, x, hphi32, lo32, h_phi_c, h_dphi_dk);
   return cudaGetLastError();
 }
 

@@ -79,6 +79,7 @@ struct Solver {
   cudaError_t init(int nx, int ny, int nz, int precision);
   void release();
   cudaError_t build_graph(double* x, float* phi32, double phi_c, double phi_a, int nz, double rtol, int maxit);
+  cudaError_t build_graph_once(double* x, float* phi32, double phi_c, double phi_a, int nz, double rtol, int maxit);
   cudaError_t launch(cudaStream_t s);
   cudaError_t run_host(cudaStream_t s);
   cudaError_t invalidate(cudaStream_t s);
