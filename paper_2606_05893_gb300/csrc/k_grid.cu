@@ -87,28 +87,6 @@ __global__ void __launch_bounds__(kDepBlock) k_deposit_fp64(DepositArgs<Store64>
   }
 }
 
-// Runs of equal keys among consecutive lanes (a cell-sorted store keeps the
-// particles of a cell together): sums each run's values into its first lane
-// (suffix sums bounded by the run's last lane, five shuffle steps) and returns
-// true there. Equal keys that are not adjacent form separate runs.
-template <int N>
-__device__ __forceinline__ bool warp_run_sum(int key, float (&w)[N]) {
-  const int lane = threadIdx.x & 31;
-  const int next = __shfl_down_sync(0xffffffffu, key, 1);
-  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-  const unsigned tail = __ballot_sync(0xffffffffu, lane == 31 || next != key);
-  const int run_end = lane + __ffs(tail >> lane) - 1;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-    for (int c = 0; c < N; ++c) {
-      const float t = __shfl_down_sync(0xffffffffu, w[c], o);
-      if (lane + o <= run_end) w[c] += t;
-    }
-  }
-  return lane == 0 || prev != key;
-}
-
 __global__ void __launch_bounds__(kDepBlock) k_deposit_mx(DepositArgs<StoreMx> a) {
   const long long n = (long long)a.cnt->n[a.cur][a.species];
   const Grid& g = a.g;

@@ -201,6 +201,11 @@ __global__ void k_inject(InjectArgs<S> a) {
     const double vx = s.sig * n1, vy = s.sig * n2, vz = s.sig * fabs(n3);
     const double z = u01_64(d3.x, d3.y) * vz * a.g.dt;
     store_write(a.st[s.species], a.g, slot, x, y, z, vx, vy, vz, pid);
+    if (a.nd.on) {  // the next step's deposit is being accumulated: add this particle
+      const auto p = store_read(a.st[s.species], a.g, slot);
+      if (a.role[s.species] == ROLE_NEUTRAL) atomicAdd(&a.nd.ncount[s.species][cell_now(a.g, p)], 1);
+      else if (a.nd.qw_h3[s.species] != 0.0) deposit_one(a.g, p, a.nd.rho32, a.nd.rho64, a.nd.qw_h3[s.species]);
+    }
   }
 }
 
@@ -219,6 +224,45 @@ __global__ void k_inject_commit(DevCounters* cnt, InjectCommit c) {
 // ---------------------------------------------------------------------------
 // a5-a8 + a10: gather / push / absorb / collide / compact
 // ---------------------------------------------------------------------------
+// Next-step deposit from the push. MIXED store: weights summed over runs of
+// equal cells in the warp (a cell-sorted store keeps them adjacent), one atomic
+// per run and corner; the neutral count likewise. FP64 store: plain FP64
+// atomics (summing doubles across lanes would load the narrow FP64 pipe).
+// Every lane of the warp calls it.
+template <bool CHARGED, bool NEUTRAL>
+__device__ __forceinline__ void next_deposit(const PushArgs<StoreMx>& a, const ParticleMx& p, bool stored) {
+  if (CHARGED) {
+    float w[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int key = -1;
+    if (stored) {
+      key = p.cell;
+      cic_weights(p.ox, p.oy, p.oz, w);
+      const float q = (float)a.nd.qw_h3[a.species];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) w[c] *= q;
+    }
+    if (warp_run_sum(key, w) && key >= 0) {
+      int i, j, k;
+      cell_ijk(a.g, key, i, j, k);
+      long long idx[8];
+      corner_nodes(a.g, i, j, k, idx);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) atomicAdd(&a.nd.rho32[idx[c]], w[c]);
+    }
+  }
+  if (NEUTRAL) {
+    float one[1] = {stored ? 1.f : 0.f};  // counts are exact in FP32
+    const int key = stored ? p.cell : -1;
+    if (warp_run_sum(key, one) && key >= 0) atomicAdd(&a.nd.ncount[a.species][key], (int)one[0]);
+  }
+}
+template <bool CHARGED, bool NEUTRAL>
+__device__ __forceinline__ void next_deposit(const PushArgs<Store64>& a, const Particle64& p, bool stored) {
+  if (!stored) return;
+  if (CHARGED) deposit_one(a.g, p, nullptr, a.nd.rho64, a.nd.qw_h3[a.species]);
+  if (NEUTRAL) atomicAdd(&a.nd.ncount[a.species][cell_now(a.g, p)], 1);
+}
+
 template <class S, bool CHARGED, bool MCC, bool NEUTRAL>
 __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(PushArgs<S> a) {
   // Each thread advances kIlp particles per round (their loads are issued
@@ -322,16 +366,19 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
     __syncthreads();
     unsigned long long wbase = s_base + s_wcnt[warp];
     __syncthreads();  // s_wcnt / s_base are rewritten in the next round
+    bool stored[kIlp];
 #pragma unroll
     for (int u = 0; u < kIlp; ++u) {
       const unsigned long long slot = wbase + __popc(ball[u] & ((1u << lane) - 1u));
       wbase += __popc(ball[u]);
+      stored[u] = false;
       if (!keep[u]) continue;
       if (slot >= (unsigned long long)a.cap) {
         atomicOr(&a.cnt->error, ERR_CAPACITY);
         continue;
       }
       store_write_p(a.out, slot, p[u]);
+      stored[u] = true;
       if (ionize[u]) {
         const unsigned int e = atomicAdd(&a.cnt->n_events, 1u);
         if (e < (unsigned int)a.ev_cap) {
@@ -362,6 +409,12 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
           atomicOr(&a.cnt->error, ERR_EVENTS);
         }
       }
+    }
+    // a3 of the next step while the particles are at hand: charge (or neutral
+    // count) at x^{n+1} of every particle kept
+    if (a.nd.on) {
+#pragma unroll
+      for (int u = 0; u < kIlp; ++u) next_deposit<CHARGED, NEUTRAL>(a, p[u], stored[u]);
     }
   }
   // block totals of the tallies by warp 0: counts in integers, the FP64 sums of
@@ -478,14 +531,23 @@ __global__ void k_resolve_apply(ApplyArgs<S> a) {
     sec.set_v(us * st * cos(ph), us * st * sin(ph), us * ct);
     sec.pid = spid;
     const unsigned long long es = ne_out + r;
-    if (es < (unsigned long long)a.e_cap) store_write_p(a.e_st, es, sec);
-    else atomicOr(&a.cnt->error, ERR_CAPACITY);
+    if (es < (unsigned long long)a.e_cap) {
+      store_write_p(a.e_st, es, sec);
+      if (a.nd.on) deposit_one(a.g, sec, a.nd.rho32, a.nd.rho64, a.nd.qw_h3[a.e_species]);
+    } else {
+      atomicOr(&a.cnt->error, ERR_CAPACITY);
+    }
     // victim neutral -> ion (position x^{n+1}, velocity and pid kept)
     const auto vn = store_read(a.n_st, a.g, cd.slot);
     const unsigned long long is = ni_out + r;
-    if (is < (unsigned long long)a.i_cap) store_write_p(a.i_st, is, vn);
-    else atomicOr(&a.cnt->error, ERR_CAPACITY);
+    if (is < (unsigned long long)a.i_cap) {
+      store_write_p(a.i_st, is, vn);
+      if (a.nd.on) deposit_one(a.g, vn, a.nd.rho32, a.nd.rho64, a.nd.qw_h3[a.i_species]);
+    } else {
+      atomicOr(&a.cnt->error, ERR_CAPACITY);
+    }
     store_kill(a.n_st, cd.slot);
+    if (a.nd.on) atomicSub(&a.nd.ncount[a.n_species][cell_now(a.g, vn)], 1);
     if (a.log) {
       a.log[3 * r] = ev.pid;
       a.log[3 * r + 1] = vn.pid;

@@ -23,7 +23,8 @@ long long sort_hist_entries(long long n_max) { return 256 * sort_blocks(n_max); 
 
 __global__ void __launch_bounds__(kSortBlock) k_radix_hist(const unsigned long long* __restrict__ keys,
                                                            const unsigned long long* n_dev, long long n_max, int shift,
-                                                           uint32_t* __restrict__ hist, int nblocks) {
+                                                           uint32_t* __restrict__ hist, int nblocks, const int* skip) {
+  if (skip && *skip) return;
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
@@ -38,7 +39,8 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_hist(const unsigned long l
 // One block per digit: exclusive scan of that digit's row over the tiles, and
 // the digit total.
 __global__ void __launch_bounds__(kSortBlock) k_radix_scan_rows(uint32_t* __restrict__ hist, int nblocks,
-                                                                uint32_t* __restrict__ digit_tot) {
+                                                                uint32_t* __restrict__ digit_tot, const int* skip) {
+  if (skip && *skip) return;
   __shared__ uint32_t part[kSortBlock];
   uint32_t* row = hist + (long long)blockIdx.x * nblocks;
   const int per = (nblocks + kSortBlock - 1) / kSortBlock;
@@ -68,7 +70,9 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(const unsigned lon
                                                               unsigned long long* __restrict__ kout,
                                                               uint32_t* __restrict__ vout, const unsigned long long* n_dev,
                                                               long long n_max, int shift, const uint32_t* __restrict__ hist,
-                                                              int nblocks, const uint32_t* __restrict__ digit_tot) {
+                                                              int nblocks, const uint32_t* __restrict__ digit_tot,
+                                                              const int* skip) {
+  if (skip && *skip) return;
   __shared__ uint32_t base[256];           // global start of each digit for this tile
   __shared__ uint32_t wc[kWarps][256];     // per-warp digit counts -> offsets
   __shared__ uint32_t tot[256];
@@ -125,18 +129,58 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(const unsigned lon
   }
 }
 
-int radix_sort_pairs(const SortBuffers& b, const unsigned long long* n_dev, int bit0, int bit1, cudaStream_t s) {
+// Small inputs (n <= kSmallSort, the usual ionization event count): one block
+// ranks every pair against all others (ties by input position, so the order is
+// the stable one), writes it at its rank in the buffers the radix passes would
+// end in, and sets *done so that those passes return at once.
+constexpr int kSmallSort = 2048;
+__global__ void __launch_bounds__(1024) k_small_sort(const unsigned long long* __restrict__ kin,
+                                                     const uint32_t* __restrict__ vin,
+                                                     unsigned long long* __restrict__ kout,
+                                                     uint32_t* __restrict__ vout, const unsigned long long* n_dev,
+                                                     long long n_max, int* done) {
+  __shared__ unsigned long long sk[kSmallSort];
+  const long long n = min((long long)*n_dev, n_max);
+  if (n > kSmallSort) {
+    if (threadIdx.x == 0) *done = 0;
+    return;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sk[i] = kin[i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned long long k = sk[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const unsigned long long kj = sk[j];
+      rank += (kj < k || (kj == k && j < i)) ? 1 : 0;
+    }
+    kout[rank] = k;
+    vout[rank] = vin[i];
+  }
+  if (threadIdx.x == 0) *done = 1;
+}
+
+int radix_sort_pairs(const SortBuffers& b, const unsigned long long* n_dev, int bit0, int bit1, cudaStream_t s,
+                     bool small_path) {
   const int nblocks = (int)sort_blocks(b.n_max);
+  const int passes = (bit1 - bit0 + 7) / 8;
+  const int* skip = nullptr;
+  // the small path writes where an odd number of passes ends (kb, vb); an even
+  // number would end in the input buffers, which the ranking still reads
+  if (small_path && (passes & 1)) {
+    PIC_LAUNCH(1, 1024, 0, s, k_small_sort)(b.ka, b.va, b.kb, b.vb, n_dev, b.n_max, b.small_done);
+    skip = b.small_done;
+  }
   int src = 0;
   for (int shift = bit0; shift < bit1; shift += 8) {
     const unsigned long long* kin = src ? b.kb : b.ka;
     const uint32_t* vin = src ? b.vb : b.va;
     unsigned long long* kout = src ? b.ka : b.kb;
     uint32_t* vout = src ? b.va : b.vb;
-    PIC_LAUNCH(nblocks, kSortBlock, 0, s, k_radix_hist)(kin, n_dev, b.n_max, shift, b.hist, nblocks);
-    PIC_LAUNCH(256, kSortBlock, 0, s, k_radix_scan_rows)(b.hist, nblocks, b.digit_tot);
+    PIC_LAUNCH(nblocks, kSortBlock, 0, s, k_radix_hist)(kin, n_dev, b.n_max, shift, b.hist, nblocks, skip);
+    PIC_LAUNCH(256, kSortBlock, 0, s, k_radix_scan_rows)(b.hist, nblocks, b.digit_tot, skip);
     PIC_LAUNCH(nblocks, kSortBlock, 0, s, k_radix_scatter)(kin, vin, kout, vout, n_dev, b.n_max, shift, b.hist, nblocks,
-                                                   b.digit_tot);
+                                                   b.digit_tot, skip);
     src ^= 1;
   }
   return src;

@@ -130,6 +130,12 @@ struct Instance {
   long long cap[kMaxSpecies]{};
   double* rho64 = nullptr;
   float* rho32 = nullptr;
+  // the next step's deposit, accumulated by the push, injection and ionization
+  // kernels of this step (valid once a step has run since the last host upload)
+  double* rho64_next = nullptr;
+  float* rho32_next = nullptr;
+  int32_t* ncount_next[kMaxSpecies]{};
+  bool next_valid = false;
   double* phi = nullptr;
   double4_32a* E64 = nullptr;
   float4* E32 = nullptr;
@@ -230,6 +236,7 @@ void free_instance(Instance* I) {
   for (int s = 0; s < kMaxSpecies; ++s) {
     for (int b = 0; b < 2; ++b) cudaFree(I->mem[s][b]);
     cudaFree(I->ncount[s]);
+    cudaFree(I->ncount_next[s]);
     cudaFree(I->cell_start[s]);
   }
   for (auto& x : I->xs) {
@@ -244,6 +251,8 @@ void free_instance(Instance* I) {
   if (I->host_cnt) cudaFreeHost(I->host_cnt);
   cudaFree(I->rho64);
   cudaFree(I->rho32);
+  cudaFree(I->rho64_next);
+  cudaFree(I->rho32_next);
   cudaFree(I->phi);
   cudaFree(I->E64);
   cudaFree(I->E32);
@@ -260,12 +269,14 @@ void free_instance(Instance* I) {
   cudaFree(I->evsort.vb);
   cudaFree(I->evsort.hist);
   cudaFree(I->evsort.digit_tot);
+  cudaFree(I->evsort.small_done);
   cudaFree(I->csort.ka);
   cudaFree(I->csort.kb);
   cudaFree(I->csort.va);
   cudaFree(I->csort.vb);
   cudaFree(I->csort.hist);
   cudaFree(I->csort.digit_tot);
+  cudaFree(I->csort.small_done);
   cudaFree(I->cell_count);
   cudaFree(I->scan_tmp);
   cudaFree(I->red);
@@ -285,6 +296,7 @@ cudaError_t alloc_sort(SortBuffers& b, long long n_max) {
   if ((e = dalloc(&b.vb, n_max))) return e;
   if ((e = dalloc(&b.hist, sort_hist_entries(n_max)))) return e;
   if ((e = dalloc(&b.digit_tot, 256))) return e;
+  if ((e = dalloc(&b.small_done, 1))) return e;
   return cudaSuccess;
 }
 
@@ -480,15 +492,20 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
         S.pid = (uint32_t*)(S.vz + cap);
       }
     }
-    if (I->species[s].role == PIC_NEUTRAL) CK(h, dalloc(&I->ncount[s], g.ncell));
+    if (I->species[s].role == PIC_NEUTRAL) {
+      CK(h, dalloc(&I->ncount[s], g.ncell));
+      CK(h, dalloc(&I->ncount_next[s], g.ncell));
+    }
     CK(h, dalloc(&I->cell_start[s], g.ncell + 1));
     CK(h, cudaMemset(I->cell_start[s], 0, sizeof(long long) * (g.ncell + 1)));
   }
   if (!I->mixed) {
     CK(h, dalloc(&I->rho64, g.nnode));
+    CK(h, dalloc(&I->rho64_next, g.nnode));
     CK(h, dalloc(&I->E64, g.nnode));
   } else {
     CK(h, dalloc(&I->rho32, g.nnode));
+    CK(h, dalloc(&I->rho32_next, g.nnode));
     CK(h, dalloc(&I->E32, g.nnode));
   }
   CK(h, dalloc(&I->phi, g.nnode));
@@ -609,6 +626,19 @@ pic_status sort_instance(pic_handle* h, Instance* I) {
   return PIC_OK;
 }
 
+NextDeposit next_deposit_of(const Instance* I, bool on) {
+  NextDeposit nd{};
+  nd.on = on ? 1 : 0;
+  nd.rho32 = I->rho32_next;
+  nd.rho64 = I->rho64_next;
+  const double inv_h3 = 1.0 / (I->g.h * I->g.h * I->g.h);
+  for (int s = 0; s < I->nsp; ++s) {
+    nd.ncount[s] = I->ncount_next[s];
+    nd.qw_h3[s] = I->species[s].charge_C * I->species[s].weight * inv_h3;
+  }
+  return nd;
+}
+
 template <class S>
 pic_status step_instance(pic_handle* h, Instance* I) {
   cudaStream_t st = h->stream;
@@ -658,6 +688,8 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     a.nsrc = q;
     a.src_first[q] = total;
     a.total = total;
+    a.nd = next_deposit_of(I, I->next_valid);
+    for (int s = 0; s < I->nsp; ++s) a.role[s] = I->species[s].role == PIC_NEUTRAL ? ROLE_NEUTRAL : ROLE_ELECTRON;
     if (total > 0) {
       for (int s = 0; s < I->nsp; ++s) cm.add[s] = per_species[s];
       cm.total = total;
@@ -675,29 +707,43 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     T.end(st);
   }
 
-  // a3 deposit
+  // a3 deposit: ready from the previous step (push, injection, ionization
+  // accumulated it), else from scratch
   T.begin(PIC_PH_DEPOSIT, st);
-  if (I->mixed)
-    launch_fill32(I->rho32, g.nnode, (float)I->cfg.rho_background, st);
-  else
-    launch_fill64(I->rho64, g.nnode, I->cfg.rho_background, st);
-  for (int s = 0; s < I->nsp; ++s) {
-    DepositArgs<S> d{};
-    d.g = g;
-    d.cnt = I->cnt;
-    d.st = store_of<S>(I, s, I->cur[s]);
-    d.cur = I->cur[s];
-    d.species = s;
-    d.neutral = I->species[s].role == PIC_NEUTRAL;
-    d.qw_h3 = I->species[s].charge_C * I->species[s].weight / (g.h * g.h * g.h);
-    d.rho64 = I->rho64;
-    d.rho32 = I->rho32;
-    d.ncount = I->ncount[s];
-    if (d.neutral) CK(h, cudaMemsetAsync(I->ncount[s], 0, sizeof(int32_t) * g.ncell, st));
-    if (!d.neutral && d.qw_h3 == 0.0) continue;
-    launch_deposit<S>(d, blocks, st);
-  }
+  if (I->next_valid) {
+    std::swap(I->rho32, I->rho32_next);
+    std::swap(I->rho64, I->rho64_next);
+    for (int s = 0; s < I->nsp; ++s) std::swap(I->ncount[s], I->ncount_next[s]);
+  } else {
+    if (I->mixed)
+      launch_fill32(I->rho32, g.nnode, (float)I->cfg.rho_background, st);
+    else
+      launch_fill64(I->rho64, g.nnode, I->cfg.rho_background, st);
+    for (int s = 0; s < I->nsp; ++s) {
+      DepositArgs<S> d{};
+      d.g = g;
+      d.cnt = I->cnt;
+      d.st = store_of<S>(I, s, I->cur[s]);
+      d.cur = I->cur[s];
+      d.species = s;
+      d.neutral = I->species[s].role == PIC_NEUTRAL;
+      d.qw_h3 = I->species[s].charge_C * I->species[s].weight / (g.h * g.h * g.h);
+      d.rho64 = I->rho64;
+      d.rho32 = I->rho32;
+      d.ncount = I->ncount[s];
+      if (d.neutral) CK(h, cudaMemsetAsync(I->ncount[s], 0, sizeof(int32_t) * g.ncell, st));
+      if (!d.neutral && d.qw_h3 == 0.0) continue;
+      launch_deposit<S>(d, blocks, st);
+    }
 
+  }
+  // this step's kernels accumulate the next deposit here
+  if (I->mixed)
+    launch_fill32(I->rho32_next, g.nnode, (float)I->cfg.rho_background, st);
+  else
+    launch_fill64(I->rho64_next, g.nnode, I->cfg.rho_background, st);
+  for (int s = 0; s < I->nsp; ++s)
+    if (I->ncount_next[s]) CK(h, cudaMemsetAsync(I->ncount_next[s], 0, sizeof(int32_t) * g.ncell, st));
   T.end(st);
   // a4 Poisson solve
   T.begin(PIC_PH_SOLVE, st);
@@ -758,6 +804,7 @@ pic_status step_instance(pic_handle* h, Instance* I) {
       a.cand = I->cand;
       a.cand_cap = I->cand_cap;
       a.cand_head = I->cand_head;
+      a.nd = next_deposit_of(I, true);
       const bool mcc = a.mc.nch > 0;
       if (neutral && I->ion_ch < 0) {
         a.ev_head = nullptr;
@@ -784,7 +831,7 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     r.sort_vals = I->evsort.va;
     const int rb = std::min(blocks, (I->ev_cap + 255) / 256);
     launch_resolve_rank(r, rb, st);
-    const int where = radix_sort_pairs(I->evsort, &I->cnt->ev_sort_n, 0, 40, st);
+    const int where = radix_sort_pairs(I->evsort, &I->cnt->ev_sort_n, 0, 40, st, true);
     ApplyArgs<S> ap{};
     ap.g = g;
     ap.cnt = I->cnt;
@@ -808,6 +855,8 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     ap.i_species = i_sp;
     ap.i_cap = I->cap[i_sp];
     ap.log = I->ion_log;
+    ap.nd = next_deposit_of(I, true);
+    ap.n_species = n_sp;
     launch_resolve_apply<S>(ap, rb, st);
     launch_resolve_commit(I->cnt, ap.e_out, e_sp, ap.e_cap, ap.i_out, i_sp, ap.i_cap, n_sp, I->ev_cap, st);
     launch_resolve_cleanup(r, rb, st);
@@ -815,6 +864,7 @@ pic_status step_instance(pic_handle* h, Instance* I) {
   }
   for (int s = 0; s < I->nsp; ++s) I->cur[s] ^= 1;
   I->step += 1;
+  I->next_valid = true;
   T.collect();
   CK(h, cudaGetLastError());
   return PIC_OK;
@@ -954,6 +1004,7 @@ pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, in
   CK(h, cudaMemcpyAsync(dx, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaMemcpyAsync(dv, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
   const int c = I->cur[species];
+  I->next_valid = false;  // uploaded particles are not in the accumulated deposit
   if (I->mixed)
     launch_load<StoreMx>(I->g, I->smx[species][c], I->cnt, c, species, I->cap[species], dx, dv, n, h->stream);
   else

@@ -68,6 +68,29 @@ __device__ __forceinline__ void cell_ijk(const Grid& g, int cell, int& i, int& j
   j = t - k * g.ny;
 }
 
+// Runs of equal keys among consecutive lanes (a cell-sorted store keeps the
+// particles of a cell together): sums each run's values into its first lane
+// (suffix sums bounded by the run's last lane, five shuffle steps) and returns
+// true there. Equal keys that are not adjacent form separate runs. Every lane
+// of the warp must call it.
+template <int N>
+__device__ __forceinline__ bool warp_run_sum(int key, float (&w)[N]) {
+  const int lane = threadIdx.x & 31;
+  const int next = __shfl_down_sync(0xffffffffu, key, 1);
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const unsigned tail = __ballot_sync(0xffffffffu, lane == 31 || next != key);
+  const int run_end = lane + __ffs(tail >> lane) - 1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      const float t = __shfl_down_sync(0xffffffffu, w[c], o);
+      if (lane + o <= run_end) w[c] += t;
+    }
+  }
+  return lane == 0 || prev != key;
+}
+
 // ---------------------------------------------------------------------------
 // particle views
 // ---------------------------------------------------------------------------
@@ -232,6 +255,50 @@ struct ParticleMx {
     vy *= f;
     vz *= f;
   }
+};
+
+// One particle's CIC charge (q = charge * weight / h^3) at its stored position,
+// plain atomics (injection and ionization: few particles), and its cell.
+__device__ __forceinline__ void deposit_one(const Grid& g, const ParticleMx& p, float* rho32, double* rho64, double q) {
+  (void)rho64;
+  float w[8];
+  cic_weights(p.ox, p.oy, p.oz, w);
+  int i, j, k;
+  cell_ijk(g, p.cell, i, j, k);
+  long long idx[8];
+  corner_nodes(g, i, j, k, idx);
+  const float qf = (float)q;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) atomicAdd(&rho32[idx[c]], w[c] * qf);
+}
+__device__ __forceinline__ void deposit_one(const Grid& g, const Particle64& p, float* rho32, double* rho64, double q) {
+  (void)rho32;
+  const Loc l = locate64(g, p.x, p.y, p.z);
+  double w[8];
+  cic_weights(l.fx, l.fy, l.fz, w);
+  long long idx[8];
+  corner_nodes(g, l.i, l.j, l.k, idx);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) atomicAdd(&rho64[idx[c]], w[c] * q);
+}
+__device__ __forceinline__ int cell_now(const Grid& g, const ParticleMx& p) {
+  (void)g;
+  return p.cell;
+}
+__device__ __forceinline__ int cell_now(const Grid& g, const Particle64& p) {
+  const Loc l = locate64(g, p.x, p.y, p.z);
+  return (l.k * g.ny + l.j) * g.nx + l.i;
+}
+
+// Accumulation of the next step's charge density and neutral counts while the
+// particles are at hand (push, injection, ionization): the deposit of step n+1
+// is then ready when it starts.
+struct NextDeposit {
+  int on;                        // accumulate (0: the next step deposits from scratch)
+  float* rho32;                  // MIXED
+  double* rho64;                 // FP64
+  int32_t* ncount[kMaxSpecies];  // neutral species
+  double qw_h3[kMaxSpecies];     // charge * weight / h^3 per species
 };
 
 template <class S>
@@ -407,6 +474,8 @@ struct InjectArgs {
   long long total;
   uint2 key;
   uint32_t step;
+  NextDeposit nd;
+  int role[kMaxSpecies];
 };
 
 struct InjectCommit {
@@ -436,6 +505,7 @@ struct PushArgs {
   Cand* cand;
   int cand_cap;
   int32_t* cand_head;
+  NextDeposit nd;
 };
 
 struct ResolveArgs {
@@ -469,6 +539,8 @@ struct ApplyArgs {
   int i_out, i_species;
   long long i_cap;
   uint32_t* log;
+  NextDeposit nd;
+  int n_species;
 };
 
 template <class S>
@@ -528,10 +600,12 @@ struct SortBuffers {
   uint32_t *va, *vb;
   uint32_t* hist;      // 256 * nblocks(n_max)
   uint32_t* digit_tot; // 256
+  int* small_done;     // set when the single-block path sorted the input
   long long n_max;
 };
 long long sort_hist_entries(long long n_max);
-int radix_sort_pairs(const SortBuffers& b, const unsigned long long* n_dev, int bit0, int bit1, cudaStream_t s);
+int radix_sort_pairs(const SortBuffers& b, const unsigned long long* n_dev, int bit0, int bit1, cudaStream_t s,
+                     bool small_path = false);
 // exclusive scan of int32 counts[n] into int64 out[n+1] (out[n] = total)
 size_t scan_temp_bytes(long long n);
 void exclusive_scan_i32_i64(const int32_t* counts, long long n, long long* out, void* temp, cudaStream_t s);

@@ -31,7 +31,8 @@ def const_xsec(kind, sigma, threshold=0.0, target=1, product=2):
     return W.XSec(kind, 0, target, product, threshold, np.array([1.0]), np.array([sigma]))
 
 
-def ionization_cells_case(seed=3, sigma_ion=1e-17, sigma_el=1e-19, E_eV=100.0, capacity=1 << 14):
+def ionization_cells_case(seed=3, sigma_ion=1e-17, sigma_el=1e-19, E_eV=100.0, capacity=1 << 14, n_dense_e=300,
+                          n_dense_n=400):
     """Electrons co-located with ions (zero net charge at t = 0, so the first push
     sees no field) in a few cells holding neutrals: one dense cell (no
     suppression) and one cell with two neutrals (most ionizations suppressed)."""
@@ -45,9 +46,9 @@ def ionization_cells_case(seed=3, sigma_ion=1e-17, sigma_el=1e-19, E_eV=100.0, c
         return (np.array(c) + 0.05 + 0.9 * rng.random((n, 3))) * h
 
     dense, sparse = (2, 3, 4), (5, 5, 5)
-    xe = np.concatenate([in_cell(300, dense), in_cell(200, sparse)])
+    xe = np.concatenate([in_cell(n_dense_e, dense), in_cell(200, sparse)])
     ve = isotropic(rng, xe.shape[0], speed_of_eV(E_eV))
-    xn = np.concatenate([in_cell(400, dense), in_cell(2, sparse)])
+    xn = np.concatenate([in_cell(n_dense_n, dense), in_cell(2, sparse)])
     vn = rng.standard_normal(xn.shape) * 500.0
     xi = xe.copy()
     vi = np.zeros_like(xi)

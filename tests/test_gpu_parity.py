@@ -134,6 +134,16 @@ def test_ionization_several_steps(pkg):
     assert np.array_equal(sim.ionization_log(), ref.ionization_log())
 
 
+def test_ionization_many_events(pkg):
+    # more events in one step than the single-block event ordering takes
+    # (2048): the radix passes order them
+    wl = ionization_cells_case(seed=5, n_dense_e=3000, n_dense_n=2500)
+    sim, ref = run_pair(pkg, wl, 1)
+    mg, mo = full_compare(sim, ref, wl)
+    assert mg["n_ionization"] + mg["n_suppressed"] > 2048 and mg["n_suppressed"] > 0
+    assert np.array_equal(sim.ionization_log(), ref.ionization_log())
+
+
 def test_small_workload_one_step(pkg):
     wl = W.config_small()
     sim, ref = run_pair(pkg, wl, 1)
