@@ -32,7 +32,13 @@ import numpy as np  # noqa: E402
 
 METRIC = "PIC particle-steps/s (deposit+solve+push+MCC), 1 GB300, vs FP64 plain; HBM %"
 UNIT = "particle-steps/s"
-WORKLOAD = "128x128x256 cells h=2.5nm, 1e7 macroparticles (60% e, 30% Cu, 10% Cu+), J~U[5e11,5e12] A/m2, Cu flux 1e28, sort every 20"
+WORKLOADS = {
+    "c2": ("128x128x256 cells h=2.5nm, 1e7 macroparticles (60% e, 30% Cu, 10% Cu+), J~U[5e11,5e12] A/m2, "
+           "Cu flux 1e28, sort every 20", 10_000_000),
+    "c3": ("256x256x512 cells h=1.25nm (same box), 5e7 macroparticles (60% e, 30% Cu, 10% Cu+), "
+           "J~U[5e11,5e12] A/m2, Cu flux 1e28, sort every 20", 50_000_000),
+}
+WORKLOAD = WORKLOADS["c2"][0]
 FALLBACK_HBM_GBS = 6800.0
 
 # Algorithmic bytes per particle of the fused gather/push/collide/compact kernel:
@@ -115,8 +121,10 @@ class ClockSampler:
         return out
 
 
-def make_workload(seed, n_preload):
+def make_workload(name, seed, n_preload):
     from paper_2606_05893_gb300 import workloads as W
+    if name == "c3":
+        return W.config_mixed_large(seed=seed, n_preload=n_preload)
     return W.config_scale(seed=seed, n_preload=n_preload)
 
 
@@ -135,7 +143,7 @@ def run_gpu(args, rank, ws, local):
             dist.barrier()
         torch.cuda.synchronize()
 
-    wl = make_workload(args.seed + rank, args.n_preload)
+    wl = make_workload(args.workload, args.seed + rank, args.n_preload)
     results = {}
     precisions = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
     stream = torch.cuda.current_stream()
@@ -295,13 +303,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
-    ap.add_argument("--n-preload", type=int, default=10_000_000)
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
+                    help="c2: 128x128x256, 1e7 particles (the headline); c3: 256x256x512, 5e7 particles")
+    ap.add_argument("--n-preload", type=int, default=None, help="macroparticles preloaded (default per workload)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--profile-steps", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-batch", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.n_preload is None:
+        args.n_preload = WORKLOADS[args.workload][1]
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
     ws, rank, local = dist_env()
@@ -340,10 +352,10 @@ def main():
             "warmup": args.warmup, "ms_per_step": a["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": head, "n_preload": args.n_preload,
+            "config": {"workload": WORKLOADS[args.workload][0], "precision": head, "n_preload": args.n_preload,
                        "grid": [wl.nx, wl.ny, wl.nz], "h": wl.h, "dt": wl.dt,
                        "parallelism": f"replicas x{ws}",
-                       "l2": "inputs larger than L2 (particle stores 0.3-0.5 GB per buffer)"},
+                       "l2": "inputs larger than L2 (particle stores of 0.3 GB and more per buffer)"},
             "e2e": e2e, "gpu_launches": r["launches"], "clocks": r["clocks"], "roofline": roofline,
             "phase_ms_per_step": phase_ms, "cg_iters_last_step": r["cg_iters"]}
     if "fp64" in results and head != "fp64":

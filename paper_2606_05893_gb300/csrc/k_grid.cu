@@ -305,7 +305,7 @@ void launch_step_begin(DevCounters* cnt, const int* out_buf, int nsp, cudaStream
 // ---------------------------------------------------------------------------
 template <class S>
 __global__ void k_load(Grid g, S st, DevCounters* cnt, int cur, int species, long long cap, const double* __restrict__ x,
-                       const double* __restrict__ v, long long n) {
+                       const double* __restrict__ v, long long n, NextDeposit nd, int neutral) {
   const unsigned long long base = cnt->n[cur][species];
   const uint32_t pid0 = cnt->next_pid;
   for (long long i = gtid(); i < n; i += gstride()) {
@@ -313,6 +313,11 @@ __global__ void k_load(Grid g, S st, DevCounters* cnt, int cur, int species, lon
     if (slot >= (unsigned long long)cap) continue;
     store_write(st, g, slot, x[3 * i], x[3 * i + 1], x[3 * i + 2], v[3 * i], v[3 * i + 1], v[3 * i + 2],
                 pid0 + (uint32_t)i);
+    if (nd.on) {  // the next step's deposit is being accumulated: add this particle
+      const auto p = store_read(st, g, slot);
+      if (neutral) atomicAdd(&nd.ncount[species][cell_now(g, p)], 1);
+      else if (nd.qw_h3[species] != 0.0) deposit_one(g, p, nd.rho32, nd.rho64, nd.qw_h3[species]);
+    }
   }
 }
 __global__ void k_load_commit(DevCounters* cnt, int cur, int species, long long n) {
@@ -322,9 +327,9 @@ __global__ void k_load_commit(DevCounters* cnt, int cur, int species, long long 
 }
 template <class S>
 void launch_load(const Grid& g, S st, DevCounters* cnt, int cur, int species, long long cap, const double* x,
-                 const double* v, long long n, cudaStream_t s) {
+                 const double* v, long long n, const NextDeposit& nd, int neutral, cudaStream_t s) {
   if (n <= 0) return;
-  PIC_LAUNCH(grid_for(n), kBlock, 0, s, k_load<S>)(g, st, cnt, cur, species, cap, x, v, n);
+  PIC_LAUNCH(grid_for(n), kBlock, 0, s, k_load<S>)(g, st, cnt, cur, species, cap, x, v, n, nd, neutral);
   PIC_LAUNCH(1, 1, 0, s, k_load_commit)(cnt, cur, species, n);
 }
 
@@ -338,9 +343,9 @@ void launch_download(const Grid& g, S st, long long n, double* x, double* v, uin
   PIC_LAUNCH(grid_for(n), kBlock, 0, s, k_download<S>)(g, st, n, x, v, pid);
 }
 template void launch_load<Store64>(const Grid&, Store64, DevCounters*, int, int, long long, const double*,
-                                   const double*, long long, cudaStream_t);
+                                   const double*, long long, const NextDeposit&, int, cudaStream_t);
 template void launch_load<StoreMx>(const Grid&, StoreMx, DevCounters*, int, int, long long, const double*,
-                                   const double*, long long, cudaStream_t);
+                                   const double*, long long, const NextDeposit&, int, cudaStream_t);
 template void launch_download<Store64>(const Grid&, Store64, long long, double*, double*, uint32_t*, cudaStream_t);
 template void launch_download<StoreMx>(const Grid&, StoreMx, long long, double*, double*, uint32_t*, cudaStream_t);
 

@@ -1004,11 +1004,15 @@ pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, in
   CK(h, cudaMemcpyAsync(dx, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaMemcpyAsync(dv, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
   const int c = I->cur[species];
-  I->next_valid = false;  // uploaded particles are not in the accumulated deposit
+  // uploaded particles join the next step's accumulated deposit (if any)
+  const NextDeposit nd = next_deposit_of(I, I->next_valid);
+  const int neutral = I->species[species].role == PIC_NEUTRAL ? 1 : 0;
   if (I->mixed)
-    launch_load<StoreMx>(I->g, I->smx[species][c], I->cnt, c, species, I->cap[species], dx, dv, n, h->stream);
+    launch_load<StoreMx>(I->g, I->smx[species][c], I->cnt, c, species, I->cap[species], dx, dv, n, nd, neutral,
+                         h->stream);
   else
-    launch_load<Store64>(I->g, I->s64[species][c], I->cnt, c, species, I->cap[species], dx, dv, n, h->stream);
+    launch_load<Store64>(I->g, I->s64[species][c], I->cnt, c, species, I->cap[species], dx, dv, n, nd, neutral,
+                         h->stream);
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     h->dead = true;

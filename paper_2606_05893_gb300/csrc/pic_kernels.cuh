@@ -585,7 +585,7 @@ void launch_step_begin(DevCounters* cnt, const int* out_buf, int nsp, cudaStream
 
 template <class S>
 void launch_load(const Grid& g, S st, DevCounters* cnt, int cur, int species, long long cap, const double* x,
-                 const double* v, long long n, cudaStream_t s);
+                 const double* v, long long n, const NextDeposit& nd, int neutral, cudaStream_t s);
 template <class S>
 void launch_download(const Grid& g, S st, long long n, double* x, double* v, uint32_t* pid, cudaStream_t s);
 

@@ -213,6 +213,23 @@ def test_background_rates_on_table_breakpoints_bit_exact(pkg, P_target):
     compare_particles(sim, ref, wl, 0, TOL, TOL)
 
 
+def test_host_upload_between_steps(pkg):
+    # particles handed over by the host between steps (the surface-model transfer)
+    # join the next step's deposit, which the previous step had already started
+    wl = W.config_small(seed=13, n_preload=4000)
+    sim, ref = run_pair(pkg, wl, 2)
+    rng = np.random.default_rng(5)
+    for sp, n in ((0, 300), (1, 200), (2, 100)):
+        x = rng.random((n, 3)) * np.array(wl.L) * np.array([1.0, 1.0, 0.5])
+        v = rng.standard_normal((n, 3)) * (3e5 if sp == 0 else 800.0)
+        pkg.pic_inject_particles(sim.h, 0, sp, x, v)
+        ref.load(sp, x, v)
+    for _ in range(2):
+        sim.step()
+        ref.step()
+    full_compare(sim, ref, wl, tol=1e-9)
+
+
 def test_sort_permutation_and_offsets_bit_exact(pkg):
     wl = W.config_tiny(seed=9)
     sim = pkg.Simulation(wl)
