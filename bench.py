@@ -44,9 +44,10 @@ FALLBACK_HBM_GBS = 6800.0
 # Algorithmic bytes per particle of the fused gather/push/collide/compact kernel:
 # read the particle record and write it once (the node field is gathered from L2).
 BYTES_PER_PARTICLE = {"mixed": 32 + 32, "fp64": 52 + 52}
-# dram bytes per pushed particle of the same kernel from one ncu capture (None until measured
-# on the current kernel version)
-NCU_TRAFFIC_PER_PARTICLE = {"mixed": None, "fp64": None}
+# DRAM bytes (read + write) per pushed electron of the same kernel from one ncu capture of the
+# current kernel (profiles/k_push_mixed_electrons_128x128x256.md: 251.9 MB for 4 090 255
+# electrons); None where no capture of the current kernel exists
+NCU_TRAFFIC_PER_PARTICLE = {"mixed": 61.57, "fp64": None}
 
 
 def dist_env():

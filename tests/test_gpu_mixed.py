@@ -1,6 +1,7 @@
-"""Mixed-precision path (int32 cell + FP32 offsets/velocities, FP32 deposit, gather
-and multigrid smoothing; FP64 residual, refinement, reductions and collision
-decision) against the FP64 oracle.
+"""Mixed-precision path (int32 cell + FP32 offsets/velocities, FP32 deposit, gather,
+multigrid smoothing and scattering angles; the refinement residual and update in
+float-float arithmetic (about 48 bits), FP64 reductions, and collision decisions
+identical to the FP64 rule) against the FP64 oracle.
 
 Per step from an identical state the bounds are |dx| <= 1e-5 h (FP32 offsets
 carry 2^-24 h; a particle crossing up to ~10 cells per step adds the FP32
