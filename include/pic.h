@@ -239,6 +239,14 @@ pic_status pic_philox(pic_handle* h, int64_t n, const uint32_t ctr[4], const uin
  * particles. 0 restores the normal mode. */
 pic_status pic_set_mcc_background(pic_handle* h, int32_t inst, double density_m3);
 
+/* Cell sort interval of one instance from now on (a2: the store is sorted when
+ * the step index is a multiple of it; 0 never sorts). The sort only reorders
+ * particles, so results do not depend on it beyond rounding; it trades the
+ * sort's cost against the locality of the deposit and gather (the
+ * autotuner in the Python package picks it per instance).
+ * PIC_EINVAL for a negative interval or a bad instance. */
+pic_status pic_set_sort_interval(pic_handle* h, int32_t inst, int32_t interval);
+
 /* Phase timing: with on != 0 every later step records CUDA events on the
  * handle's stream around each phase (and waits for them at the end of the step).
  * pic_get_phase_times adds up, per phase, the elapsed milliseconds (ms[PIC_NPHASES])

@@ -83,7 +83,7 @@ EXPORTED = ["pic_create", "pic_inject", "pic_inject_particles", "pic_step", "pic
             "pic_last_error", "pic_get_count", "pic_get_particles", "pic_get_field", "pic_set_phi", "pic_solve",
             "pic_sort_now", "pic_get_cell_start", "pic_get_ionization_log", "pic_philox",
             "pic_set_mcc_background", "pic_version", "pic_set_profiling", "pic_get_phase_times",
-            "pic_launch_count", "pic_poisson_solve_static"]
+            "pic_launch_count", "pic_poisson_solve_static", "pic_set_sort_interval"]
 
 _lib = None
 
@@ -126,6 +126,7 @@ def load_library(path: str = LIB_PATH):
         "pic_get_ionization_log": ([P, C.c_int32, C.c_int64, i64, u32], st),
         "pic_philox": ([P, C.c_int64, u32, u32, u32], st),
         "pic_set_mcc_background": ([P, C.c_int32, C.c_double], st),
+        "pic_set_sort_interval": ([P, C.c_int32, C.c_int32], st),
         "pic_version": ([], C.c_char_p),
         "pic_set_profiling": ([P, C.c_int32], st),
         "pic_get_phase_times": ([P, C.c_int32, d, i64], st),
@@ -274,6 +275,10 @@ def pic_philox(h, n, ctr, key):
 
 def pic_set_mcc_background(h, inst, density):
     return _check(h, load_library().pic_set_mcc_background(h, inst, density))
+
+
+def pic_set_sort_interval(h, inst, interval):
+    return _check(h, load_library().pic_set_sort_interval(h, inst, interval))
 
 
 def pic_set_profiling(h, on=True):

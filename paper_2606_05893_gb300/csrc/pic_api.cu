@@ -165,6 +165,11 @@ struct Instance {
   double bg_density = 0.0;
   bool sorted_once = false;
   PhaseTimer timer;
+  // its own stream when the handle holds several instances (they step
+  // concurrently), else the handle's stream
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t done = nullptr;
   double* stage_x = nullptr;  // device staging of pic_inject_particles
   double* stage_v = nullptr;
   long long stage_cap = 0;
@@ -175,6 +180,7 @@ struct Instance {
 struct pic_handle {
   std::vector<Instance*> inst;
   cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr;  // several instances: their streams start after the caller's work
   std::string err;
   bool dead = false;
   int sticky = 0;  // sticky non-fatal status bits (ENOCONV)
@@ -233,6 +239,8 @@ int bits_for(unsigned long long v) {
 
 void free_instance(Instance* I) {
   if (!I) return;
+  if (I->own_stream && I->stream) cudaStreamDestroy(I->stream);
+  if (I->done) cudaEventDestroy(I->done);
   for (int s = 0; s < kMaxSpecies; ++s) {
     for (int b = 0; b < 2; ++b) cudaFree(I->mem[s][b]);
     cudaFree(I->ncount[s]);
@@ -600,7 +608,7 @@ McArgs mc_args(Instance* I, int proj) {
 // a2: sort every species by (cell, pid)
 template <class S>
 pic_status sort_instance(pic_handle* h, Instance* I) {
-  cudaStream_t st = h->stream;
+  cudaStream_t st = I->stream;
   CK(h, cudaMemcpyAsync(I->host_cnt, I->cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
   CK(h, cudaStreamSynchronize(st));
   const int pid_bits = std::max(1, bits_for(I->host_cnt->next_pid));
@@ -641,7 +649,7 @@ NextDeposit next_deposit_of(const Instance* I, bool on) {
 
 template <class S>
 pic_status step_instance(pic_handle* h, Instance* I) {
-  cudaStream_t st = h->stream;
+  cudaStream_t st = I->stream;
   const Grid& g = I->g;
   const uint2 key = make_uint2((uint32_t)I->cfg.seed, (uint32_t)(I->cfg.seed >> 32));
   const int blocks = sm_count() * kPushBlocksPerSM;
@@ -911,10 +919,24 @@ pic_status pic_create(const pic_instance_cfg* cfgs, int32_t n_instances, void* c
   }
   pic_handle* h = new pic_handle();
   h->stream = (cudaStream_t)cuda_stream;
+  if (n_instances > 1 && cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess) {
+    delete h;
+    return fail(nullptr, PIC_ECUDA, "event creation failed");
+  }
   for (int i = 0; i < n_instances; ++i) {
     Instance* I = nullptr;
     pic_status st = create_instance(h, cfgs[i], &I);
     h->inst.push_back(I);
+    if (st == PIC_OK) {
+      I->stream = h->stream;
+      if (n_instances > 1) {
+        if (cudaStreamCreateWithFlags(&I->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&I->done, cudaEventDisableTiming) != cudaSuccess)
+          st = fail(h, PIC_ECUDA, "stream creation failed");
+        else
+          I->own_stream = true;
+      }
+    }
     if (st != PIC_OK) {
       g_static_err = h->err;
       for (auto* p : h->inst) free_instance(p);
@@ -940,6 +962,7 @@ pic_status pic_destroy(pic_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   for (auto* I : h->inst) free_instance(I);
+  if (h->fork) cudaEventDestroy(h->fork);
   delete h;
   return PIC_OK;
 }
@@ -1026,14 +1049,32 @@ pic_status pic_step(pic_handle* h, int32_t nsteps) {
   if (h->dead) return fail(h, PIC_ESTATE, "handle unusable after an earlier fatal error: %s", h->err.c_str());
   if (nsteps < 0) return fail(h, PIC_EINVAL, "nsteps must be >= 0");
   h->sticky = 0;
-  for (int n = 0; n < nsteps; ++n) {
+  // several instances step concurrently on their own streams, ordered after the
+  // caller's stream and joined back into it
+  const bool fork = h->inst.size() > 1 && nsteps > 0;
+  if (fork) {
+    CK(h, cudaEventRecord(h->fork, h->stream));
+    for (auto* I : h->inst) CK(h, cudaStreamWaitEvent(I->stream, h->fork, 0));
+  }
+  pic_status step_status = PIC_OK;
+  for (int n = 0; n < nsteps && step_status == PIC_OK; ++n) {
     for (auto* I : h->inst) {
       pic_status st = I->mixed ? step_instance<StoreMx>(h, I) : step_instance<Store64>(h, I);
       if (st != PIC_OK) {
-        if (st == PIC_ECUDA) h->dead = true;
-        return st;
+        step_status = st;
+        break;
       }
     }
+  }
+  if (fork) {
+    for (auto* I : h->inst) {
+      CK(h, cudaEventRecord(I->done, I->stream));
+      CK(h, cudaStreamWaitEvent(h->stream, I->done, 0));
+    }
+  }
+  if (step_status != PIC_OK) {
+    if (step_status == PIC_ECUDA) h->dead = true;
+    return step_status;
   }
   // device-side error flags (capacity, event overflow) of the completed steps
   for (auto* I : h->inst) {
@@ -1337,6 +1378,14 @@ pic_status pic_get_phase_times(pic_handle* h, int32_t inst, double* ms, int64_t*
 }
 
 uint64_t pic_launch_count(void) { return (uint64_t)pic::g_launches; }
+
+pic_status pic_set_sort_interval(pic_handle* h, int32_t inst, int32_t interval) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  if (interval < 0) return fail(h, PIC_EINVAL, "sort interval must be >= 0");
+  h->inst[inst]->cfg.sort_interval = interval;
+  return PIC_OK;
+}
 
 pic_status pic_set_mcc_background(pic_handle* h, int32_t inst, double density_m3) {
   pic_status st = check(h, inst);

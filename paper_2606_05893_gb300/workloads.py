@@ -272,3 +272,28 @@ def config_tiny(seed: int = 1, nx=8, ny=8, nz=16, h=5e-9, n_preload=600, anode_V
            Source(1, cx, cy, L[0] / 4, 1e28, 2000.0)]
     return Workload(f"tiny {nx}x{ny}x{nz}", nx, ny, nz, h, 0.5e-15, 0.0, anode_V, sp,
                     cu_plasma_xsec(256), src, seed, sort_interval=4, preload=pre, steps=10)
+
+
+def config_ensemble(seed: int = 0, n_instances: int = 48, sides=(32, 64, 96, 128), h: float = 2.5e-9):
+    """Batched ensemble of independent instances of uneven sizes: grid (n, n, 2n)
+    with n drawn from `sides`, applied field uniform in [5, 15] GV/m, emitter
+    radius uniform in [5, 40] nm, preloaded macroparticles log-uniform in
+    [1e4, 2e6], J per instance as in the at-scale workload."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_instances):
+        n = int(rng.choice(np.asarray(sides)))
+        field = rng.uniform(5e9, 15e9)
+        r_emit = rng.uniform(5e-9, 40e-9)
+        npre = int(round(math.exp(rng.uniform(math.log(1e4), math.log(2e6)))))
+        wl = config_scale(seed=seed * 1000 + i, n_preload=npre, nx=n, ny=n, nz=2 * n, h=h,
+                          anode_V=field * 2 * n * h, r_emit=r_emit)
+        # small populations under a wide, dense emitter are dominated by what is
+        # injected: room for 200 steps of the electron source on top of the preload
+        src = wl.sources[0]
+        inj = src.flux_m2s * math.pi * src.radius ** 2 * wl.dt / wl.species[0].weight
+        extra = int(200 * inj)
+        for sp in wl.species:
+            sp.capacity += extra
+        out.append(wl)
+    return out
