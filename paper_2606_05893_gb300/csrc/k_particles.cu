@@ -244,10 +244,7 @@ __device__ __forceinline__ void next_deposit(const PushArgs<StoreMx>& a, const P
     if (warp_run_sum(key, w) && key >= 0) {
       int i, j, k;
       cell_ijk(a.g, key, i, j, k);
-      long long idx[8];
-      corner_nodes(a.g, i, j, k, idx);
-#pragma unroll
-      for (int c = 0; c < 8; ++c) atomicAdd(&a.nd.rho32[idx[c]], w[c]);
+      cic_add_f32(a.nd.rho32, a.g, i, j, k, w, (a.g.nx & 3) == 0);
     }
   }
   if (NEUTRAL) {
