@@ -48,9 +48,9 @@ FALLBACK_HBM_GBS = 6800.0
 # read the particle record and write it once (the node field is gathered from L2).
 BYTES_PER_PARTICLE = {"mixed": 32 + 32, "fp64": 52 + 52}
 # DRAM bytes (read + write) per pushed electron of the same kernel from one ncu capture of the
-# current kernel (profiles/k_push_mixed_electrons_128x128x256.md: 251.9 MB for 4 090 255
+# current kernel (profiles/k_push_mixed_electrons_128x128x256.md: 253.8 MB for 4 090 255
 # electrons); None where no capture of the current kernel exists
-NCU_TRAFFIC_PER_PARTICLE = {"mixed": 61.57, "fp64": None}
+NCU_TRAFFIC_PER_PARTICLE = {"mixed": 62.05, "fp64": None}
 
 
 def dist_env():
