@@ -17,7 +17,10 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <utility>
+
+#include <cooperative_groups.h>
 #include <vector>
 
 #include "pic_internal.cuh"
@@ -333,6 +336,287 @@ std::vector<MgLevel> mg_plan(int nx, int ny, int nz) {
   return lv;
 }
 
+// ---------------------------------------------------------------------------
+// The deepest multigrid levels in one thread-block cluster (FP32). Launch
+// latency, not bandwidth, bounds the small levels: about 20 dependent kernels
+// of a few microseconds each per V-cycle. Here 8 blocks of one cluster hold the
+// levels in shared memory, split by unknown planes (block c owns planes
+// [c P / 8, (c + 1) P / 8) of every level), read neighbouring planes owned by
+// other blocks through distributed shared memory, and separate the phases
+// with cluster barriers; the operations are those of the per-level kernels.
+// Every thread of every block passes every barrier (no early exit).
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+constexpr int kClusterCTAs = 8;
+constexpr int kClusterThreads = 1024;
+constexpr int kMaxFused = 6;
+constexpr int kMaxPlanes = 128;  // unknown planes of a fused level
+constexpr long long kClusterMaxUnknowns = 16384;
+
+struct KLv {
+  int nx, ny, P, pl, hx;  // cells x, y; unknown planes; plane size; nx / 2
+  FastDiv dnx, dpl, dhx, dhxny;
+  int maxp;               // planes per block at most
+  int oe, ob, orr;        // shared-memory offsets (floats) of e, b, r (maxp planes each)
+};
+struct ClusterArgs {
+  int nlev;  // fused levels, the last the coarsest
+  KLv L[kMaxFused];
+  int dense, nuc, ocb;  // coarsest: dense inverse (nuc x nuc, global), local copy of its b at ocb
+  int coarse_sweeps;
+  const float* Ainv;
+  const float* b_in;  // b of the first fused level (global, all planes)
+  float* e_out;       // e of the first fused level (global)
+};
+
+__device__ __forceinline__ int plane0(int P, int c) { return (c * P) / kClusterCTAs; }
+
+// owner block and local index of every unknown plane of every fused level,
+// built once per launch (no division in the phases)
+struct PlaneMap {
+  unsigned char own[kMaxFused][kMaxPlanes];
+  unsigned char loc[kMaxFused][kMaxPlanes];
+};
+
+// pointer to plane k of an array (offset off) of level l, local or in another block
+__device__ __forceinline__ float* plane_ptr(float* sm, const PlaneMap& pm, int l, const KLv& L, int off, int k,
+                                            int me) {
+  const int o = pm.own[l][k];
+  float* base = sm + off + pm.loc[l][k] * L.pl;
+  return o == me ? base : static_cast<float*>(__cluster_map_shared_rank(base, o));
+}
+
+// sum of the six neighbours of (i, j) in plane k (local pointer c), planes k +- 1 via DSMEM
+__device__ __forceinline__ float k_nb(float* sm, const PlaneMap& pm, int l, const KLv& L, int off, const float* c,
+                                      int k, int i, int j, int me) {
+  const int im = i == 0 ? L.nx - 1 : i - 1, ip = i == L.nx - 1 ? 0 : i + 1;
+  const int jm = j == 0 ? L.ny - 1 : j - 1, jp = j == L.ny - 1 ? 0 : j + 1;
+  const int r = j * L.nx;
+  float s = c[r + im] + c[r + ip] + c[jm * L.nx + i] + c[jp * L.nx + i];
+  if (k > 0) s += plane_ptr(sm, pm, l, L, off, k - 1, me)[r + i];
+  if (k < L.P - 1) s += plane_ptr(sm, pm, l, L, off, k + 1, me)[r + i];
+  return s;
+}
+
+__device__ void kc_smooth(float* sm, const PlaneMap& pm, int l, const KLv& L, int me, int color, int zero_init) {
+  const float sixth = 1.0f / 6.0f;
+  const int p0 = plane0(L.P, me), np = plane0(L.P, me + 1) - p0;
+  const int per = L.hx * L.ny;
+  for (int q = threadIdx.x; q < np * per; q += blockDim.x) {
+    const int kk = fdiv(q, L.dhxny);
+    const int t = q - kk * per;
+    const int j = fdiv(t, L.dhx);
+    const int m = t - j * L.hx;
+    const int k = p0 + kk;
+    const int par = (j + k + 1 + color) & 1;
+    const int i = 2 * m + par;
+    float* e = sm + L.oe + kk * L.pl;
+    const float* b = sm + L.ob + kk * L.pl;
+    const int u = j * L.nx + i;
+    if (zero_init) {
+      e[u] = b[u] * sixth;
+      e[u - i + (2 * m + (par ^ 1))] = 0.f;
+    } else {
+      e[u] = (b[u] + k_nb(sm, pm, l, L, L.oe, e, k, i, j, me)) * sixth;
+    }
+  }
+}
+
+__device__ void kc_residual(float* sm, const PlaneMap& pm, int l, const KLv& L, int me) {
+  const int p0 = plane0(L.P, me), np = plane0(L.P, me + 1) - p0;
+  for (int q = threadIdx.x; q < np * L.pl; q += blockDim.x) {
+    const int kk = fdiv(q, L.dpl);
+    const int u = q - kk * L.pl;
+    const int j = fdiv(u, L.dnx);
+    const int i = u - j * L.nx;
+    const float* e = sm + L.oe + kk * L.pl;
+    sm[L.orr + kk * L.pl + u] =
+        sm[L.ob + kk * L.pl + u] - (6.f * e[u] - k_nb(sm, pm, l, L, L.oe, e, p0 + kk, i, j, me));
+  }
+}
+
+__device__ void kc_restrict(float* sm, const PlaneMap& pm, int l, const KLv& F, const KLv& C, int me) {
+  const int p0 = plane0(C.P, me), np = plane0(C.P, me + 1) - p0;
+  for (int q = threadIdx.x; q < np * C.pl; q += blockDim.x) {
+    const int kk = fdiv(q, C.dpl);
+    const int U = q - kk * C.pl;
+    const int J = fdiv(U, C.dnx);
+    const int I = U - J * C.nx;
+    const int Kn = p0 + kk + 1;  // coarse node plane
+    const int i0 = 2 * I;
+    const int im = i0 == 0 ? F.nx - 1 : i0 - 1;
+    const int ip = i0 + 1 == F.nx ? 0 : i0 + 1;
+    float s = 0.f;
+#pragma unroll
+    for (int cc = -1; cc <= 1; ++cc) {
+      const int kf = 2 * Kn + cc - 1;  // fine unknown plane
+      const float wc = cc == 0 ? 0.5f : 0.25f;
+      const float* rp = plane_ptr(sm, pm, l, F, F.orr, kf, me);
+#pragma unroll
+      for (int b2 = -1; b2 <= 1; ++b2) {
+        int jf = 2 * J + b2;
+        jf = jf < 0 ? jf + F.ny : (jf >= F.ny ? jf - F.ny : jf);
+        const float wb = b2 == 0 ? 0.5f : 0.25f;
+        const float* row = rp + jf * F.nx;
+        s += wb * wc * (0.25f * row[im] + 0.5f * row[i0] + 0.25f * row[ip]);
+      }
+    }
+    sm[C.ob + kk * C.pl + U] = 4.f * s;
+  }
+}
+
+__device__ void kc_prolong(float* sm, const PlaneMap& pm, int l, const KLv& F, const KLv& C, int me) {
+  const int p0 = plane0(F.P, me), np = plane0(F.P, me + 1) - p0;
+  for (int q = threadIdx.x; q < np * F.pl; q += blockDim.x) {
+    const int kk = fdiv(q, F.dpl);
+    const int u = q - kk * F.pl;
+    const int j = fdiv(u, F.dnx);
+    const int i = u - j * F.nx;
+    const int kn = p0 + kk + 1;  // fine node plane
+    const int K0 = kn >> 1;
+    const bool kodd = kn & 1;
+    const int I0 = i >> 1;
+    const int I1 = I0 + 1 == C.nx ? 0 : I0 + 1;
+    const bool iodd = i & 1;
+    const int J0 = j >> 1;
+    const int J1 = J0 + 1 == C.ny ? 0 : J0 + 1;
+    const bool jodd = j & 1;
+    float s = 0.f;
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+      const int Kc = K0 + cc;  // coarse node plane
+      if (cc == 1 && !kodd) continue;
+      if (Kc < 1 || Kc > C.P) continue;
+      const float* ep = plane_ptr(sm, pm, l + 1, C, C.oe, Kc - 1, me);
+      const int r0 = J0 * C.nx, r1 = J1 * C.nx;
+      float t = ep[r0 + I0];
+      if (iodd) t = 0.5f * (t + ep[r0 + I1]);
+      if (jodd) {
+        float t1 = ep[r1 + I0];
+        if (iodd) t1 = 0.5f * (t1 + ep[r1 + I1]);
+        t = 0.5f * (t + t1);
+      }
+      s += t;
+    }
+    sm[F.oe + kk * F.pl + u] += kodd ? 0.5f * s : s;
+  }
+}
+
+__global__ void __launch_bounds__(kClusterThreads) k_coarse_cluster(ClusterArgs a) {
+  pdl_enter();
+  extern __shared__ float sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int me = (int)cl.block_rank();
+  const int nl = a.nlev;
+  __shared__ PlaneMap pm;
+  for (int l = 0; l < nl; ++l) {
+    const int P = a.L[l].P;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+      int c = 0;
+      while (c + 1 < kClusterCTAs && plane0(P, c + 1) <= k) ++c;
+      pm.own[l][k] = (unsigned char)c;
+      pm.loc[l][k] = (unsigned char)(k - plane0(P, c));
+    }
+  }
+  {  // b of the first fused level: this block's planes
+    const KLv& L = a.L[0];
+    const int p0 = plane0(L.P, me), np = plane0(L.P, me + 1) - p0;
+    for (int q = threadIdx.x; q < np * L.pl; q += blockDim.x) sm[L.ob + q] = a.b_in[p0 * L.pl + q];
+  }
+  cl.sync();
+  for (int l = 0; l < nl - 1; ++l) {
+    kc_smooth(sm, pm, l, a.L[l], me, 0, 1);
+    cl.sync();
+    kc_smooth(sm, pm, l, a.L[l], me, 1, 0);
+    cl.sync();
+    kc_residual(sm, pm, l, a.L[l], me);
+    cl.sync();
+    kc_restrict(sm, pm, l, a.L[l], a.L[l + 1], me);
+    cl.sync();
+  }
+  {
+    const KLv& C = a.L[nl - 1];
+    if (a.dense) {
+      // every block copies the whole coarsest b, then forms the rows it owns
+      float* cb = sm + a.ocb;
+      for (int col = threadIdx.x; col < a.nuc; col += blockDim.x) {
+        const int kc = fdiv(col, C.dpl);
+        cb[col] = plane_ptr(sm, pm, nl - 1, C, C.ob, kc, me)[col - kc * C.pl];
+      }
+      __syncthreads();
+      const int p0 = plane0(C.P, me), np = plane0(C.P, me + 1) - p0;
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int rr = warp; rr < np * C.pl; rr += nw) {
+        const int row = p0 * C.pl + rr;
+        float t = 0.f;
+        for (int col = lane; col < a.nuc; col += 32) t += a.Ainv[(long long)row * a.nuc + col] * cb[col];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) sm[C.oe + rr] = t;
+      }
+      cl.sync();
+    } else {
+      kc_smooth(sm, pm, nl - 1, C, me, 0, 1);
+      cl.sync();
+      kc_smooth(sm, pm, nl - 1, C, me, 1, 0);
+      cl.sync();
+      for (int it = 0; it < a.coarse_sweeps; ++it) {
+        kc_smooth(sm, pm, nl - 1, C, me, 1, 0);
+        cl.sync();
+        kc_smooth(sm, pm, nl - 1, C, me, 0, 0);
+        cl.sync();
+        kc_smooth(sm, pm, nl - 1, C, me, 0, 0);
+        cl.sync();
+        kc_smooth(sm, pm, nl - 1, C, me, 1, 0);
+        cl.sync();
+      }
+      kc_smooth(sm, pm, nl - 1, C, me, 1, 0);
+      cl.sync();
+      kc_smooth(sm, pm, nl - 1, C, me, 0, 0);
+      cl.sync();
+    }
+  }
+  for (int l = nl - 2; l >= 0; --l) {
+    kc_prolong(sm, pm, l, a.L[l], a.L[l + 1], me);
+    cl.sync();
+    kc_smooth(sm, pm, l, a.L[l], me, 1, 0);
+    cl.sync();
+    kc_smooth(sm, pm, l, a.L[l], me, 0, 0);
+    cl.sync();
+  }
+  {
+    const KLv& L = a.L[0];
+    const int p0 = plane0(L.P, me), np = plane0(L.P, me + 1) - p0;
+    for (int q = threadIdx.x; q < np * L.pl; q += blockDim.x) a.e_out[p0 * L.pl + q] = sm[L.oe + q];
+  }
+  cl.sync();  // no block leaves while another may still read its shared memory
+}
+
+template <class K>
+struct ClusterLaunch {
+  K k;
+  size_t smem;
+  cudaStream_t s;
+  template <class... A>
+  void operator()(A&&... a) const {
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kClusterCTAs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kClusterCTAs);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = g_pdl ? 2 : 1;
+    cudaLaunchKernelEx(&cfg, k, std::forward<A>(a)...);
+  }
+};
+
 template <class T>
 cudaError_t Mg<T>::init(const std::vector<MgLevel>& plan) {
   levels = plan;
@@ -357,6 +641,56 @@ cudaError_t Mg<T>::init(const std::vector<MgLevel>& plan) {
     std::vector<T> invT(inv.begin(), inv.end());
     if ((err = cudaMalloc(&Ainv, sizeof(T) * invT.size()))) return err;
     if ((err = cudaMemcpy(Ainv, invT.data(), sizeof(T) * invT.size(), cudaMemcpyHostToDevice))) return err;
+  }
+  // FP32: the deepest levels whose e, b, r fit in the shared memory of a
+  // cluster's blocks run in k_coarse_cluster (at least two levels, never level 0)
+  fuse_from = -1;
+  fuse_smem = 0;
+  if constexpr (std::is_same<T, float>::value) {
+    const size_t cap = 200 * 1024;
+    const int nl_ = (int)plan.size();
+    int best = -1;
+    size_t floats = 0, best_floats = 0;
+    for (int l = nl_ - 1; l >= 1; --l) {
+      const long long P = plan[l].nz - 1, pl = (long long)plan[l].nx * plan[l].ny;
+      const long long maxp = (P + kClusterCTAs - 1) / kClusterCTAs;
+      floats += (size_t)(3 * maxp * pl);
+      const size_t extra = coarse_dense ? (size_t)plan[nl_ - 1].nu : 0;  // local copy of the coarsest b
+      // the cluster's 8 SMs issue every phase: levels above ~16 K unknowns are
+      // faster as grid-wide kernels on all SMs
+      if (sizeof(float) * (floats + extra) > cap || nl_ - l > kMaxFused || P > kMaxPlanes ||
+          plan[l].nu > kClusterMaxUnknowns)
+        break;
+      if (nl_ - l >= 2) {
+        best = l;
+        best_floats = floats + extra;
+      }
+    }
+    if (rb_ok && best > 0) {
+      const size_t bytes = sizeof(float) * best_floats;
+      bool ok = cudaFuncSetAttribute(k_coarse_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+                cudaSuccess;
+      if (ok) {  // can a cluster of this size be resident at all?
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = kClusterCTAs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kClusterCTAs);
+        cfg.blockDim = dim3(kClusterThreads);
+        cfg.dynamicSmemBytes = bytes;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        ok = cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_cluster, &cfg) == cudaSuccess && nclusters > 0;
+      }
+      cudaGetLastError();
+      if (ok) {
+        fuse_from = best;
+        fuse_smem = bytes;
+      }
+    }
   }
   return cudaSuccess;
 }
@@ -389,7 +723,8 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
     E[l] = l == 0 ? z : e[l];
     B[l] = l == 0 ? const_cast<T*>(rhs) : b[l];
   }
-  for (int l = 0; l < nl - 1; ++l) {
+  const int ff = fuse_from;  // levels ff..nl-1 run in one cluster (FP32 only), -1: none
+  for (int l = 0; l < (ff > 0 ? ff : nl - 1); ++l) {
     const Lv L = lv_of(levels[l]);
     SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 0, 1);
     SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 1, 0);
@@ -397,7 +732,41 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
     const Lv C = lv_of(levels[l + 1]);
     SOLVER_LAUNCH(g3(C, C.nx), kB3, 0, s, k_restrict<T>)(L, C, r[l], B[l + 1]);
   }
-  {
+  if constexpr (std::is_same<T, float>::value) {
+    if (ff > 0) {
+      ClusterArgs ca{};
+      ca.nlev = nl - ff;
+      int off = 0;
+      for (int q = 0; q < ca.nlev; ++q) {
+        const MgLevel& M = levels[ff + q];
+        KLv& c = ca.L[q];
+        c.nx = M.nx;
+        c.ny = M.ny;
+        c.P = M.nz - 1;
+        c.pl = M.nx * M.ny;
+        c.hx = M.nx / 2;
+        c.dnx = make_fastdiv(c.nx);
+        c.dpl = make_fastdiv(c.pl);
+        c.dhx = make_fastdiv(c.hx);
+        c.dhxny = make_fastdiv(c.hx * c.ny);
+        c.maxp = (c.P + kClusterCTAs - 1) / kClusterCTAs;
+        c.oe = off;
+        c.ob = off + c.maxp * c.pl;
+        c.orr = off + 2 * c.maxp * c.pl;
+        off += 3 * c.maxp * c.pl;
+      }
+      ca.dense = coarse_dense ? 1 : 0;
+      ca.nuc = (int)levels[nl - 1].nu;
+      ca.ocb = off;
+      ca.coarse_sweeps = coarse_sweeps;
+      ca.Ainv = Ainv;
+      ca.b_in = B[ff];
+      ca.e_out = E[ff];
+      ++g_launches;
+      ClusterLaunch<decltype(&k_coarse_cluster)>{&k_coarse_cluster, fuse_smem, s}(ca);
+    }
+  }
+  if (ff <= 0) {
     const Lv C = lv_of(levels[nl - 1]);
     if (coarse_dense) {
       const int cg = (int)std::min<long long>((C.nu * 32 + kSB - 1) / kSB, 4096);
@@ -416,7 +785,7 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
       SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
     }
   }
-  for (int l = nl - 2; l >= 0; --l) {
+  for (int l = (ff > 0 ? ff : nl - 1) - 1; l >= 0; --l) {
     const Lv L = lv_of(levels[l]);
     const Lv C = lv_of(levels[l + 1]);
     SOLVER_LAUNCH(g3(L, L.nx), kB3, 0, s, k_prolong<T>)(L, C, E[l + 1], E[l]);
