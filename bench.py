@@ -157,7 +157,7 @@ def run_gpu(args, rank, ws, local):
         for _ in range(args.warmup):
             sim.step(1)
         m0 = sim.moments()
-        l0 = pkg.pic_launch_count()
+        l0, k0 = pkg.pic_launch_count(), pkg.pic_kernel_count()
         clocks = ClockSampler(local)
         barrier()
         clocks.start()
@@ -172,7 +172,8 @@ def run_gpu(args, rank, ws, local):
         wall = time.perf_counter() - t0
         clk = clocks.stop()
         ms = e0.elapsed_time(e1)
-        launches = pkg.pic_launch_count() - l0
+        launch_ops = pkg.pic_launch_count() - l0
+        launches = pkg.pic_kernel_count() - k0
         m1 = sim.moments()
         pushes = sum(m1["pushed"]) - sum(m0["pushed"])
         push_e = m1["pushed"][0] - m0["pushed"][0]
@@ -213,7 +214,7 @@ def run_gpu(args, rank, ws, local):
         t3 = time.perf_counter()
         me1 = sim.moments()
         e2e_pushes = sum(me1["pushed"]) - sum(me0["pushed"])
-        results[prec] = dict(ms=ms, wall=wall, pushes=pushes, push_e=push_e, launches=launches, clocks=clk,
+        results[prec] = dict(ms=ms, wall=wall, pushes=pushes, push_e=push_e, launches=launches, launch_ops=launch_ops, clocks=clk,
                              phases=phases, prof_push_e=prof_push_e, prof_steps=args.profile_steps,
                              e2e_s=(t3 - t2), e2e_pushes=e2e_pushes, cg_iters=m1["cg_iters"],
                              counts=m1["count"], moments=m1)
@@ -257,7 +258,7 @@ def run_gpu_ensemble(args, rank, ws, local):
         return [sum(sim.moments(i)["pushed"]) for i in range(n_inst)]
 
     p0 = pushed_all()
-    l0 = pkg.pic_launch_count()
+    l0, k0 = pkg.pic_launch_count(), pkg.pic_kernel_count()
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
@@ -270,7 +271,8 @@ def run_gpu_ensemble(args, rank, ws, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    launches = pkg.pic_launch_count() - l0
+    launch_ops = pkg.pic_launch_count() - l0
+    launches = pkg.pic_kernel_count() - k0
     p1 = pushed_all()
     pushes = sum(p1) - sum(p0)
     # per-instance device time (phase events; instances then run one after another)
@@ -310,7 +312,7 @@ def run_gpu_ensemble(args, rank, ws, local):
     agg = reduce_over_ranks(r, dist, "cuda")
     if dist is not None:
         dist.barrier()
-    info = dict(launches=launches, clocks=clk, per_inst=per_inst, chosen=chosen,
+    info = dict(launches=launches, launch_ops=launch_ops, clocks=clk, per_inst=per_inst, chosen=chosen,
                 tune_ms={str(k): float(np.sum(v)) for k, v in measured.items()},
                 push_e_ms=push_e_ms, push_e_n=push_e_n, prof_push_launches=n_inst * args.profile_steps,
                 sizes=[w.nx for w in wls], n_total=sum(w.n_particles() for w in wls))
@@ -456,7 +458,7 @@ def main():
                        "grid": [wl.nx, wl.ny, wl.nz], "h": wl.h, "dt": wl.dt,
                        "parallelism": f"replicas x{ws}",
                        "l2": "inputs larger than L2 (particle stores of 0.3 GB and more per buffer)"},
-            "e2e": e2e, "gpu_launches": r["launches"], "clocks": r["clocks"], "roofline": roofline,
+            "e2e": e2e, "gpu_launches": r["launches"], "launch_ops": r["launch_ops"], "clocks": r["clocks"], "roofline": roofline,
             "phase_ms_per_step": phase_ms, "cg_iters_last_step": r["cg_iters"]}
     if "fp64" in results and head != "fp64":
         f, fa = results["fp64"], agg["fp64"]
@@ -490,7 +492,7 @@ def report_ensemble(args, rank, ws, local):
             "e2e": {"value": a["e2e_pushes"] / a["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": args.e2e_batch * 48,
                     "d2h_bytes_per_step": 1712,
                     "api": "pic_inject_particles(host batch, instance 0) + pic_step(1) of the ensemble + pic_moments"},
-            "gpu_launches": info["launches"], "clocks": info["clocks"],
+            "gpu_launches": info["launches"], "launch_ops": info["launch_ops"], "clocks": info["clocks"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "k_push (electrons, all instances, isolated launches)",
                          "peak_kind": peak_kind, "bytes_per_particle": bpp},

@@ -255,8 +255,15 @@ pic_status pic_set_sort_interval(pic_handle* h, int32_t inst, int32_t interval);
 pic_status pic_set_profiling(pic_handle* h, int32_t on);
 pic_status pic_get_phase_times(pic_handle* h, int32_t inst, double* ms, int64_t* count);
 
-/* Kernel launches issued by the library in this process so far. */
+/* Launch operations the library issued to the GPU in this process so far: a
+ * kernel launch counts one, and so does a graph launch (a recorded solve or a
+ * recorded step), however many kernels the graph runs. */
 uint64_t pic_launch_count(void);
+
+/* Kernels run by those operations: a graph launch adds the kernel nodes it was
+ * recorded with, the body of a device-side loop (the solver's iterations)
+ * counted once, so this is a lower bound when a solve iterates. */
+uint64_t pic_kernel_count(void);
 
 /* ---- solve without allocating ----------------------------------------------
  * Not in the paper: an entry point for callers that cannot allocate device

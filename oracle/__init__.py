@@ -84,6 +84,7 @@ def lib():
         L.or_add_xsec.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, d, d]
         L.or_add_source.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]
         L.or_set_background_density.argtypes = [P, C.c_double]
+        L.or_set_source.argtypes = [P, C.c_int, C.c_double, C.c_double]
         L.or_load.argtypes = [P, C.c_int, C.c_int64, d, d]
         L.or_count.restype = C.c_int64
         L.or_count.argtypes = [P, C.c_int]
@@ -329,6 +330,10 @@ class Oracle:
     @property
     def next_pid(self):
         return int(lib().or_get_next_pid(self._h))
+
+    def set_source(self, q, flux, T_K):
+        if lib().or_set_source(self._h, q, flux, T_K) != 0:
+            raise ValueError("bad source")
 
     def source_acc(self, q):
         return lib().or_get_source_acc(self._h, q)

@@ -255,6 +255,16 @@ int or_add_source(or_state_t* s, int species, double cx, double cy, double R, do
   return 0;
 }
 
+/* Change the flux and temperature of source q from the next step on; its carry
+ * accumulator is kept (a source whose strength changes keeps its fractional
+ * count). */
+int or_set_source(or_state_t* s, int q, double flux, double T) {
+  if (q < 0 || q >= s->nsrc) return -1;
+  s->src[q].flux = flux;
+  s->src[q].T = T;
+  return 0;
+}
+
 void or_set_background_density(or_state_t* s, double n) { s->bg_density = n; }
 
 /* Append particles; pids are assigned from next_pid in array order. */

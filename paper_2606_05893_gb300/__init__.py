@@ -83,7 +83,7 @@ EXPORTED = ["pic_create", "pic_inject", "pic_inject_particles", "pic_step", "pic
             "pic_last_error", "pic_get_count", "pic_get_particles", "pic_get_field", "pic_set_phi", "pic_solve",
             "pic_sort_now", "pic_get_cell_start", "pic_get_ionization_log", "pic_philox",
             "pic_set_mcc_background", "pic_version", "pic_set_profiling", "pic_get_phase_times",
-            "pic_launch_count", "pic_poisson_solve_static", "pic_set_sort_interval"]
+            "pic_launch_count", "pic_kernel_count", "pic_poisson_solve_static", "pic_set_sort_interval"]
 
 _lib = None
 
@@ -131,6 +131,7 @@ def load_library(path: str = LIB_PATH):
         "pic_set_profiling": ([P, C.c_int32], st),
         "pic_get_phase_times": ([P, C.c_int32, d, i64], st),
         "pic_launch_count": ([], C.c_uint64),
+        "pic_kernel_count": ([], C.c_uint64),
         "pic_poisson_solve_static": ([C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, P, P,
                                       C.c_double, C.c_int32, P, C.POINTER(C.c_int32), d], st),
     }
@@ -294,6 +295,10 @@ def pic_get_phase_times(h, inst=0):
 
 def pic_launch_count():
     return int(load_library().pic_launch_count())
+
+
+def pic_kernel_count():
+    return int(load_library().pic_kernel_count())
 
 
 PIC_STATIC_MAX_UNKNOWNS = 1 << 18

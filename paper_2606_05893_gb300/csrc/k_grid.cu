@@ -293,6 +293,11 @@ __global__ void k_step_begin(DevCounters* cnt, StepBegin sb) {
   cnt->q_cathode_step = 0.0;
   cnt->q_anode_step = 0.0;
 }
+__global__ void k_step_end(DevCounters* cnt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cnt->step += 1u;
+}
+void launch_step_end(DevCounters* cnt, cudaStream_t st) { PIC_LAUNCH(1, 32, 0, st, k_step_end)(cnt); }
+
 void launch_step_begin(DevCounters* cnt, const int* out_buf, int nsp, cudaStream_t st) {
   StepBegin sb;
   sb.nsp = nsp;

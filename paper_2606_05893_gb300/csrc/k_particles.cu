@@ -172,24 +172,26 @@ __device__ int mcc_decide32(const McArgs& m, long long cell, float v2f, float U3
 // ---------------------------------------------------------------------------
 template <class S>
 __global__ void k_inject(InjectArgs<S> a) {
-  const long long total = a.total;
+  const InjectPlan& P = *a.plan;
+  const long long total = P.total;
+  const uint32_t step = a.cnt->step;
   for (long long t = gtid(); t < total; t += gstride()) {
     // source of this particle
     int q = 0;
-    while (q + 1 < a.nsrc && t >= a.src_first[q + 1]) ++q;
+    while (q + 1 < a.nsrc && t >= P.src_first[q + 1]) ++q;
     const InjSrc& s = a.src[q];
-    const long long kth = t - a.src_first[q];
+    const long long kth = t - P.src_first[q];
     const uint32_t pid = a.cnt->next_pid + (uint32_t)t;
     const unsigned long long base = a.cnt->n[a.cur[s.species]][s.species];
-    const unsigned long long slot = base + a.species_offset[q] + kth;
+    const unsigned long long slot = base + P.species_offset[q] + kth;
     if (slot >= (unsigned long long)a.cap[s.species]) {
       atomicOr(&a.cnt->error, ERR_CAPACITY);
       continue;
     }
-    const uint4 dp = draw(a.key, pid, a.step, TAG_INJ_POS);
-    const uint4 d1 = draw(a.key, pid, a.step, TAG_INJ_VXY);
-    const uint4 d2 = draw(a.key, pid, a.step, TAG_INJ_VZ);
-    const uint4 d3 = draw(a.key, pid, a.step, TAG_INJ_Z);
+    const uint4 dp = draw(a.key, pid, step, TAG_INJ_POS);
+    const uint4 d1 = draw(a.key, pid, step, TAG_INJ_VXY);
+    const uint4 d2 = draw(a.key, pid, step, TAG_INJ_VZ);
+    const uint4 d3 = draw(a.key, pid, step, TAG_INJ_Z);
     const double r = s.R * sqrt(u01_64(dp.x, dp.y));
     const double th = 2.0 * kPi * u01_64(dp.z, dp.w);
     const double x = wrap_coord(s.cx + r * cos(th), a.g.Lx, a.g.inv_Lx);
@@ -209,16 +211,39 @@ __global__ void k_inject(InjectArgs<S> a) {
   }
 }
 
+// a1 counts of this step from the carry accumulators (FP64, the host formula)
+__global__ void k_inject_plan(InjectPlan* P, int nsp) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  long long total = 0;
+  long long per_species[kMaxSpecies] = {0};
+  for (int q = 0; q < P->nsrc; ++q) {
+    double acc = P->acc[q] + P->mu[q];
+    const double nf = floor(acc);
+    acc -= nf;
+    P->acc[q] = acc;
+    const long long n = (long long)nf;
+    P->src_first[q] = total;
+    P->species_offset[q] = per_species[P->species[q]];
+    per_species[P->species[q]] += n;
+    total += n;
+  }
+  P->src_first[P->nsrc] = total;
+  P->total = total;
+  for (int s = 0; s < nsp && s < kMaxSpecies; ++s) P->add[s] = per_species[s];
+}
+
 __global__ void k_inject_commit(DevCounters* cnt, InjectCommit c) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const InjectPlan& P = *c.plan;
+  if (P.total == 0) return;
   for (int s = 0; s < c.nsp; ++s) {
-    if (c.add[s] == 0) continue;
-    unsigned long long nn = cnt->n[c.cur[s]][s] + c.add[s];
+    if (P.add[s] == 0) continue;
+    unsigned long long nn = cnt->n[c.cur[s]][s] + P.add[s];
     if (nn > (unsigned long long)c.cap[s]) nn = c.cap[s];
     cnt->injected[s] += nn - cnt->n[c.cur[s]][s];
     cnt->n[c.cur[s]][s] = nn;
   }
-  cnt->next_pid += (unsigned int)c.total;
+  cnt->next_pid += (unsigned int)P.total;
 }
 
 // ---------------------------------------------------------------------------
@@ -278,6 +303,7 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
   s_tv2[0][tx] = s_tv2[1][tx] = 0.0;
   s_tn[0][tx] = s_tn[1][tx] = s_tn[2][tx] = 0u;
   const long long n = (long long)a.cnt->n[a.cur_in][a.species];
+  const uint32_t step = a.cnt->step;
   if (blockIdx.x == 0 && threadIdx.x == 0)
     a.cnt->pushed[a.species] += (unsigned long long)n - (NEUTRAL ? a.cnt->n_tomb[a.species] : 0ull);
   const Grid& g = a.g;
@@ -321,14 +347,14 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
         const float nb = mcc_nu_bound(a.mc, cell_n[u], a.mc.count_in_field ? p[u].nc : -1.f);
         if (nb <= 0.f) continue;
         const float cnt0 = a.mc.count_in_field ? p[u].nc : -1.f;
-        const uint4 d = draw(a.mc.key, p[u].pid, a.mc.step, TAG_MCC);
+        const uint4 d = draw(a.mc.key, p[u].pid, step, TAG_MCC);
         const float v2f = p[u].v2f(), U32 = u01_32(d.x);
         if (!mcc_cannot_collide(nb, v2f, U32, dt_f)) {
           int ch = mcc_decide32(a.mc, cell_n[u], v2f, U32, dt_f, cnt0);
           if (ch == -2) ch = mcc_exact_dt(a.mc, cell_n[u], p[u].v2(), u01_64(d.x, d.y), g.dt);
           if (ch >= 0) {
             if (a.mc.ch[ch].kind == XS_ELASTIC) {
-              p[u].scatter_isotropic(draw(a.mc.key, p[u].pid, a.mc.step, TAG_SCATTER));
+              p[u].scatter_isotropic(draw(a.mc.key, p[u].pid, step, TAG_SCATTER));
               s_tn[2][tx] += 1u;
             } else if (a.mc.bg_mode) {
               // fixed-background test mode: counted, nothing consumed or created
@@ -396,7 +422,7 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
         // candidate victim of an ionization in its cell at x^n
         const unsigned int c = atomicAdd(&a.cnt->n_cands, 1u);
         if (c < (unsigned int)a.cand_cap) {
-          const uint4 k = draw(a.mc.key, p[u].pid, a.mc.step, TAG_VICTIM);
+          const uint4 k = draw(a.mc.key, p[u].pid, step, TAG_VICTIM);
           Cand cd;
           cd.key = ((unsigned long long)k.x << 32) | (unsigned long long)p[u].pid;
           cd.slot = (uint32_t)slot;
@@ -507,8 +533,8 @@ __global__ void k_resolve_apply(ApplyArgs<S> a) {
     const Event ev = a.ev[a.sorted_vals[r]];
     const Cand cd = a.cand[ev.victim];
     const XsDev& X = a.ch[ev.ch];
-    const uint4 g0 = draw(a.key, ev.pid, a.step, TAG_IONIZE, 0);
-    const uint4 g1 = draw(a.key, ev.pid, a.step, TAG_IONIZE, 1);
+    const uint4 g0 = draw(a.key, ev.pid, a.cnt->step, TAG_IONIZE, 0);
+    const uint4 g1 = draw(a.key, ev.pid, a.cnt->step, TAG_IONIZE, 1);
     const double Eex = ev.E_eV - X.thr;
     const double Us = u01_64(g0.x, g0.y);
     const double E2 = Us * Eex;
@@ -598,6 +624,9 @@ void launch_push(const PushArgs<S>& a, int role, bool mcc, int grid, cudaStream_
 
 void launch_inject_commit(DevCounters* cnt, const InjectCommit& c, cudaStream_t st) {
   PIC_LAUNCH(1, 1, 0, st, k_inject_commit)(cnt, c);
+}
+void launch_inject_plan(InjectPlan* plan, int nsp, cudaStream_t st) {
+  PIC_LAUNCH(1, 32, 0, st, k_inject_plan)(plan, nsp);
 }
 
 void launch_resolve_rank(const ResolveArgs& a, int grid, cudaStream_t st) { PIC_LAUNCH(grid, 256, 0, st, k_resolve_rank)(a); }

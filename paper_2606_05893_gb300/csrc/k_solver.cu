@@ -63,7 +63,7 @@ struct PdlLaunch {
   }
 };
 #define SOLVER_LAUNCH(grid, block, smem, stream, ...) \
-  (++::pic::g_launches), ::pic::PdlLaunch<decltype(&__VA_ARGS__)>{&__VA_ARGS__, dim3(grid), dim3(block), (size_t)(smem), stream}
+  (::pic::count_kernel()), ::pic::PdlLaunch<decltype(&__VA_ARGS__)>{&__VA_ARGS__, dim3(grid), dim3(block), (size_t)(smem), stream}
 
 constexpr int kSB = 256;
 constexpr int kMaxRedBlocks = 152 * 8;  // 1-D reductions over whole vectors
@@ -762,7 +762,7 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
       ca.Ainv = Ainv;
       ca.b_in = B[ff];
       ca.e_out = E[ff];
-      ++g_launches;
+      count_kernel();
       ClusterLaunch<decltype(&k_coarse_cluster)>{&k_coarse_cluster, fuse_smem, s}(ca);
     }
   }
@@ -1292,6 +1292,8 @@ cudaError_t Solver::init(int nx, int ny, int nz, int precision_) {
   if ((err = cudaMemset(ctl, 0, sizeof(SolveCtl)))) return err;
   if ((err = cudaMallocHost(&host_ctl, sizeof(SolveCtl)))) return err;
   memset(host_ctl, 0, sizeof(SolveCtl));
+  for (auto& a : aux)
+    if ((err = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking))) return err;
   if (precision == 0) return p64.init(plan);
   return p32.init(plan);
 }
@@ -1309,6 +1311,10 @@ void Solver::release() {
   cudaFree(ctl);
   if (host_ctl) cudaFreeHost(host_ctl);
   host_ctl = nullptr;
+  for (auto& a : aux) {
+    if (a) cudaStreamDestroy(a);
+    a = nullptr;
+  }
   b = nullptr;
   ax = nullptr;
   f32 = nullptr;
@@ -1379,78 +1385,16 @@ cudaError_t Solver::build_graph_once(double* x, float* phi32, double phi_c, doub
   h_maxit = maxit;
   const char* env = getenv("PIC_SOLVER_GRAPH");
   if (env && env[0] == '0') return cudaSuccess;  // host-driven loop (profilers cannot see conditional graphs)
-  const Lv L = lv_of(plan[0]);
-  const int G = sgrid(L.nu);
-  const dim3 PGd = g3(L, L.nx);
-  const int mixed = precision != 0;
-  const double dphi_dk = (phi_a - phi_c) / (double)nz;
-  cudaStream_t s0 = nullptr, s1 = nullptr, s2 = nullptr;
+  cudaStream_t s0 = nullptr;
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking))) return e;
-  if ((e = cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking))) return e;
-  if ((e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking))) return e;
-  cudaGraphConditionalHandle h_outer, h_inner;
-  cudaGraph_t outer_body = nullptr, inner_body = nullptr;
+  const unsigned long long l0 = g_launches, k0 = g_kernels;
   e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
-    if (mixed) {
-      SOLVER_LAUNCH(PGd, kB3, 0, s0, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, rtol, maxit);
-    } else {
-      SOLVER_LAUNCH(G, kSB, 0, s0, k_dot_bb)(L.nu, b, part, ctl, rtol, maxit);
-    }
-    e = add_while(s0, &h_outer, 1u, &outer_body);
-    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s1, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-    if (e == cudaSuccess) {
-      e = cudaGraphConditionalHandleCreate(&h_inner, outer_body, 0u, 0);
-      if (e == cudaSuccess) {
-        if (mixed) {
-          SOLVER_LAUNCH(PGd, kB3, 0, s1, k_residual_ff)(L, phi32, lo32, f32, p32.r, p32.d, phi_c, dphi_dk, part, ctl,
-                                                      h_outer, h_inner, inner_rtol, max_outer, 1);
-        } else {
-          SOLVER_LAUNCH(PGd, kB3, 0, s1, k_residual_prep<double>)(L, x, b, ax, p64.r, p64.d, part, ctl, h_outer, h_inner,
-                                                                inner_rtol, mixed, max_outer, 1);
-        }
-      }
-      if (e == cudaSuccess) {
-        // inner WHILE node in the outer body
-        cudaStreamCaptureStatus status;
-        cudaGraph_t g;
-        const cudaGraphNode_t* deps = nullptr;
-        const cudaGraphEdgeData* edges = nullptr;
-        size_t ndeps = 0;
-        e = cudaStreamGetCaptureInfo(s1, &status, nullptr, &g, &deps, &edges, &ndeps);
-        if (e == cudaSuccess) {
-          cudaGraphNodeParams np = {};
-          np.type = cudaGraphNodeTypeConditional;
-          np.conditional.handle = h_inner;
-          np.conditional.type = cudaGraphCondTypeWhile;
-          np.conditional.size = 1;
-          cudaGraphNode_t node;
-          e = cudaGraphAddNode(&node, g, deps, edges, ndeps, &np);
-          if (e == cudaSuccess) {
-            inner_body = np.conditional.phGraph_out[0];
-            e = cudaStreamUpdateCaptureDependencies(s1, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
-          }
-        }
-      }
-      if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s2, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-      if (e == cudaSuccess) {
-        if (mixed) capture_pcg_iteration(p32, L, part, ctl, h_inner, s2);
-        else capture_pcg_iteration(p64, L, part, ctl, h_inner, s2);
-        cudaGraph_t tmp;
-        e = cudaStreamEndCapture(s2, &tmp);
-      }
-      if (e == cudaSuccess) {
-        if (mixed) {
-          SOLVER_LAUNCH(G, kSB, 0, s1, k_update_ff)(L.nu, phi32, lo32, p32.d, ctl);
-        } else {
-          SOLVER_LAUNCH(PGd, kB3, 0, s1, k_axpy_out<double>)(L, x, p64.d, nullptr, phi_c, dphi_dk, ctl);
-        }
-      }
-      cudaGraph_t tmp1;
-      cudaError_t e1 = cudaStreamEndCapture(s1, &tmp1);
-      if (e == cudaSuccess) e = e1;
-    }
+    e = record(s0);
+    graph_kernels = g_kernels - k0;
+    g_launches = l0;  // recorded, not run
+    g_kernels = k0;
     cudaGraph_t whole = nullptr;
     cudaError_t e0 = cudaStreamEndCapture(s0, &whole);
     if (e == cudaSuccess) e = e0;
@@ -1458,8 +1402,6 @@ cudaError_t Solver::build_graph_once(double* x, float* phi32, double phi_c, doub
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
   cudaStreamDestroy(s0);
-  cudaStreamDestroy(s1);
-  cudaStreamDestroy(s2);
   if (e != cudaSuccess) {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -1470,9 +1412,93 @@ cudaError_t Solver::build_graph_once(double* x, float* phi32, double phi_c, doub
   return e;
 }
 
+// Add the whole solve (initial norm, outer WHILE node holding the residual, the
+// inner WHILE node of PCG iterations and the update) at the capture position of
+// s0, in whatever graph s0 is capturing into.
+cudaError_t Solver::record(cudaStream_t s0) {
+  const Lv L = lv_of(plan[0]);
+  const int G = sgrid(L.nu);
+  const dim3 PGd = g3(L, L.nx);
+  const int mixed = precision != 0;
+  const double phi_c = h_phi_c, dphi_dk = h_dphi_dk, rtol = h_rtol;
+  const int maxit = h_maxit;
+  double* x = hx;
+  float* phi32 = hphi32;
+  cudaStream_t s1 = aux[0], s2 = aux[1];
+  cudaError_t e;
+  cudaGraphConditionalHandle h_outer, h_inner;
+  cudaGraph_t outer_body = nullptr, inner_body = nullptr;
+  if (mixed) {
+    SOLVER_LAUNCH(PGd, kB3, 0, s0, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, rtol, maxit);
+  } else {
+    SOLVER_LAUNCH(G, kSB, 0, s0, k_dot_bb)(L.nu, b, part, ctl, rtol, maxit);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = add_while(s0, &h_outer, 1u, &outer_body);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s1, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    e = cudaGraphConditionalHandleCreate(&h_inner, outer_body, 0u, 0);
+    if (e == cudaSuccess) {
+      if (mixed) {
+        SOLVER_LAUNCH(PGd, kB3, 0, s1, k_residual_ff)(L, phi32, lo32, f32, p32.r, p32.d, phi_c, dphi_dk, part, ctl,
+                                                    h_outer, h_inner, inner_rtol, max_outer, 1);
+      } else {
+        SOLVER_LAUNCH(PGd, kB3, 0, s1, k_residual_prep<double>)(L, x, b, ax, p64.r, p64.d, part, ctl, h_outer, h_inner,
+                                                              inner_rtol, mixed, max_outer, 1);
+      }
+    }
+    if (e == cudaSuccess) {
+      // inner WHILE node in the outer body
+      cudaStreamCaptureStatus status;
+      cudaGraph_t g;
+      const cudaGraphNode_t* deps = nullptr;
+      const cudaGraphEdgeData* edges = nullptr;
+      size_t ndeps = 0;
+      e = cudaStreamGetCaptureInfo(s1, &status, nullptr, &g, &deps, &edges, &ndeps);
+      if (e == cudaSuccess) {
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h_inner;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        e = cudaGraphAddNode(&node, g, deps, edges, ndeps, &np);
+        if (e == cudaSuccess) {
+          inner_body = np.conditional.phGraph_out[0];
+          e = cudaStreamUpdateCaptureDependencies(s1, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        }
+      }
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s2, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      if (mixed) capture_pcg_iteration(p32, L, part, ctl, h_inner, s2);
+      else capture_pcg_iteration(p64, L, part, ctl, h_inner, s2);
+      cudaGraph_t tmp;
+      e = cudaStreamEndCapture(s2, &tmp);
+    }
+    if (e == cudaSuccess) {
+      if (mixed) {
+        SOLVER_LAUNCH(G, kSB, 0, s1, k_update_ff)(L.nu, phi32, lo32, p32.d, ctl);
+      } else {
+        SOLVER_LAUNCH(PGd, kB3, 0, s1, k_axpy_out<double>)(L, x, p64.d, nullptr, phi_c, dphi_dk, ctl);
+      }
+    }
+    cudaGraph_t tmp1;
+    cudaError_t e1 = cudaStreamEndCapture(s1, &tmp1);
+    if (e == cudaSuccess) e = e1;
+  }
+  return e;
+}
+
 cudaError_t Solver::launch(cudaStream_t s) {
   if (exec) {
-    ++g_launches;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    // a step being recorded takes the solver's nodes directly (a child graph
+    // cannot hold conditional nodes)
+    if (cs == cudaStreamCaptureStatusActive) return record(s);
+    count_graph(graph_kernels);
     return cudaGraphLaunch(exec, s);
   }
   return run_host(s);

@@ -23,6 +23,7 @@ using namespace pic;
 
 namespace pic {
 unsigned long long g_launches = 0;
+unsigned long long g_kernels = 0;
 void set_static_error(const char* msg);
 }
 
@@ -136,6 +137,17 @@ struct Instance {
   float* rho32_next = nullptr;
   int32_t* ncount_next[kMaxSpecies]{};
   bool next_valid = false;
+  const void* rho_first = nullptr;  // the first-allocated rho buffer (identifies the swap parity)
+  // a1 counts on the device (InjectPlan); the host list is uploaded when it changed
+  InjectPlan* plan = nullptr;
+  bool plan_dirty = true;
+  bool plan_used = false;
+  // recorded steps: one graph per (store parity, rho parity), replayed for every
+  // step that neither sorts, nor times phases, nor deposits from scratch
+  cudaGraphExec_t step_exec[4]{};
+  unsigned long long step_kernels[4]{};  // kernel nodes recorded in each
+  bool graphs_ok = true;
+  cudaStream_t cap_stream = nullptr;  // private stream for recording
   double* phi = nullptr;
   double4_32a* E64 = nullptr;
   float4* E32 = nullptr;
@@ -261,6 +273,10 @@ void free_instance(Instance* I) {
   cudaFree(I->rho32);
   cudaFree(I->rho64_next);
   cudaFree(I->rho32_next);
+  cudaFree(I->plan);
+  for (auto& e : I->step_exec)
+    if (e) cudaGraphExecDestroy(e);
+  if (I->cap_stream) cudaStreamDestroy(I->cap_stream);
   cudaFree(I->phi);
   cudaFree(I->E64);
   cudaFree(I->E32);
@@ -463,6 +479,8 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
   }
 
   CK(h, dalloc(&I->cnt, 1));
+  CK(h, dalloc(&I->plan, 1));
+  CK(h, cudaMemset(I->plan, 0, sizeof(InjectPlan)));
   CK(h, cudaMemset(I->cnt, 0, sizeof(DevCounters)));
   CK(h, cudaMallocHost((void**)&I->host_cnt, sizeof(DevCounters)));
   memset(I->host_cnt, 0, sizeof(DevCounters));
@@ -510,10 +528,12 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
   if (!I->mixed) {
     CK(h, dalloc(&I->rho64, g.nnode));
     CK(h, dalloc(&I->rho64_next, g.nnode));
+    I->rho_first = I->rho64;
     CK(h, dalloc(&I->E64, g.nnode));
   } else {
     CK(h, dalloc(&I->rho32, g.nnode));
     CK(h, dalloc(&I->rho32_next, g.nnode));
+    I->rho_first = I->rho32;
     CK(h, dalloc(&I->E32, g.nnode));
   }
   CK(h, dalloc(&I->phi, g.nnode));
@@ -595,7 +615,6 @@ McArgs mc_args(Instance* I, int proj) {
   m.bg_density_f = (float)I->bg_density;
   m.mass = I->species[proj].mass_kg;
   m.key = make_uint2((uint32_t)I->cfg.seed, (uint32_t)(I->cfg.seed >> 32));
-  m.step = I->step;
   m.bg_mode = I->bg_density > 0 ? 1 : 0;
   m.bg_density = I->bg_density;
   const int ft = field_count_target(I);
@@ -655,16 +674,17 @@ pic_status step_instance(pic_handle* h, Instance* I) {
   const int blocks = sm_count() * kPushBlocksPerSM;
 
   PhaseTimer& T = I->timer;
-  // a1 injection: integer counts from the carry accumulators (host)
+  // a1 injection: counts from the carry accumulators (device plan)
   T.begin(PIC_PH_INJECT, st);
-  {
+  if (!I->sources.empty()) {
     InjectArgs<S> a{};
     InjectCommit cm{};
     a.g = g;
     a.cnt = I->cnt;
     a.key = key;
-    a.step = I->step;
+    a.plan = I->plan;
     cm.nsp = I->nsp;
+    cm.plan = I->plan;
     for (int s = 0; s < I->nsp; ++s) {
       a.st[s] = store_of<S>(I, s, I->cur[s]);
       a.cur[s] = I->cur[s];
@@ -672,38 +692,23 @@ pic_status step_instance(pic_handle* h, Instance* I) {
       cm.cur[s] = I->cur[s];
       cm.cap[s] = I->cap[s];
     }
-    long long total = 0;
-    long long per_species[kMaxSpecies] = {0};
     int q = 0;
     for (auto& src : I->sources) {
       const pic_species& sp = I->species[src.species];
-      const double mu = src.flux * kPi * src.R * src.R * g.dt / sp.weight;
-      src.acc += mu;
-      const double nf = std::floor(src.acc);
-      src.acc -= nf;
-      const long long n = (long long)nf;
       a.src[q].species = src.species;
       a.src[q].cx = src.cx;
       a.src[q].cy = src.cy;
       a.src[q].R = src.R;
       a.src[q].sig = std::sqrt(kKB * src.T / sp.mass_kg);
-      a.src_first[q] = total;
-      a.species_offset[q] = per_species[src.species];
-      per_species[src.species] += n;
-      total += n;
       ++q;
     }
     a.nsrc = q;
-    a.src_first[q] = total;
-    a.total = total;
     a.nd = next_deposit_of(I, I->next_valid);
     for (int s = 0; s < I->nsp; ++s) a.role[s] = I->species[s].role == PIC_NEUTRAL ? ROLE_NEUTRAL : ROLE_ELECTRON;
-    if (total > 0) {
-      for (int s = 0; s < I->nsp; ++s) cm.add[s] = per_species[s];
-      cm.total = total;
-      launch_inject<S>(a, (int)std::min<long long>((total + 255) / 256, blocks), st);
-      launch_inject_commit(I->cnt, cm, st);
-    }
+    launch_inject_plan(I->plan, I->nsp, st);
+    launch_inject<S>(a, 2 * sm_count(), st);
+    launch_inject_commit(I->cnt, cm, st);
+    I->plan_used = true;
   }
   T.end(st);
 
@@ -805,7 +810,6 @@ pic_status step_instance(pic_handle* h, Instance* I) {
       a.E64 = I->E64;
       a.E32 = I->E32;
       a.mc = mc_args(I, s);
-      a.mc.step = I->step;
       a.ev = I->ev;
       a.ev_cap = I->ev_cap;
       a.ev_head = I->ev_head;
@@ -850,7 +854,6 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     McArgs m = mc_args(I, X.c.projectile);
     for (int a2 = 0; a2 < kMaxXsec; ++a2) ap.ch[a2] = m.ch[a2];
     ap.key = key;
-    ap.step = I->step;
     const int e_sp = X.c.projectile, n_sp = X.c.target, i_sp = X.c.product;
     ap.e_st = store_of<S>(I, e_sp, I->cur[e_sp] ^ 1);
     ap.e_out = I->cur[e_sp] ^ 1;
@@ -870,11 +873,139 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     launch_resolve_cleanup(r, rb, st);
     T.end(st);
   }
+  launch_step_end(I->cnt, st);
   for (int s = 0; s < I->nsp; ++s) I->cur[s] ^= 1;
   I->step += 1;
   I->next_valid = true;
   T.collect();
   CK(h, cudaGetLastError());
+  return PIC_OK;
+}
+
+// Upload the host source list (with the carries) to the device plan.
+pic_status upload_plan(pic_handle* h, Instance* I) {
+  InjectPlan P{};
+  P.nsrc = (int)I->sources.size();
+  for (int q = 0; q < P.nsrc; ++q) {
+    const Source& src = I->sources[q];
+    P.species[q] = src.species;
+    P.mu[q] = src.flux * kPi * src.R * src.R * I->g.dt / I->species[src.species].weight;
+    P.acc[q] = src.acc;
+  }
+  CK(h, cudaStreamSynchronize(I->stream));
+  CK(h, cudaMemcpy(I->plan, &P, sizeof(InjectPlan), cudaMemcpyHostToDevice));
+  I->plan_dirty = false;
+  return PIC_OK;
+}
+
+// Read the device carries back into the host list (before the list changes).
+pic_status download_carries(pic_handle* h, Instance* I) {
+  if (!I->plan_used) return PIC_OK;
+  InjectPlan P{};
+  CK(h, cudaStreamSynchronize(I->stream));
+  CK(h, cudaMemcpy(&P, I->plan, sizeof(InjectPlan), cudaMemcpyDeviceToHost));
+  for (int q = 0; q < P.nsrc && q < (int)I->sources.size(); ++q) I->sources[q].acc = P.acc[q];
+  return PIC_OK;
+}
+
+void drop_step_graphs(Instance* I) {
+  for (auto& e : I->step_exec) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
+}
+
+// One step of one instance: replayed from a recorded graph when the step neither
+// sorts nor times phases nor deposits from scratch, else enqueued directly (and
+// recorded first when it qualifies). Recording runs the same enqueue code with a
+// private stream in capture mode, so the host-side state advances exactly as in
+// a direct step; a replay advances it the same way.
+template <class S>
+pic_status run_step(pic_handle* h, Instance* I) {
+  if (I->plan_dirty) {
+    pic_status ps = upload_plan(h, I);
+    if (ps != PIC_OK) return ps;
+    drop_step_graphs(I);
+  }
+  const bool sort_now = I->cfg.sort_interval > 0 && I->step % (uint32_t)I->cfg.sort_interval == 0;
+  const bool graphable =
+      I->graphs_ok && I->next_valid && !sort_now && !I->timer.on && I->solver.exec != nullptr;
+  if (!graphable) return step_instance<S>(h, I);
+  const void* rho_now = I->mixed ? (const void*)I->rho32 : (const void*)I->rho64;
+  const int key = (I->cur[0] & 1) | (rho_now == I->rho_first ? 2 : 0);
+  if (I->step_exec[key]) {
+    count_graph(I->step_kernels[key]);
+    CK(h, cudaGraphLaunch(I->step_exec[key], I->stream));
+    std::swap(I->rho32, I->rho32_next);
+    std::swap(I->rho64, I->rho64_next);
+    for (int s = 0; s < I->nsp; ++s) std::swap(I->ncount[s], I->ncount_next[s]);
+    if (I->mixed) I->phi64_stale = true;
+    for (int s = 0; s < I->nsp; ++s) I->cur[s] ^= 1;
+    I->step += 1;
+    return PIC_OK;
+  }
+  if (!I->cap_stream && cudaStreamCreateWithFlags(&I->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    I->graphs_ok = false;
+    return step_instance<S>(h, I);
+  }
+  // host-side state the recording advances (restored if recording fails)
+  double* r64 = I->rho64;
+  double* r64n = I->rho64_next;
+  float* r32 = I->rho32;
+  float* r32n = I->rho32_next;
+  int32_t* nc[kMaxSpecies];
+  int32_t* ncn[kMaxSpecies];
+  int cur[kMaxSpecies];
+  for (int s = 0; s < kMaxSpecies; ++s) {
+    nc[s] = I->ncount[s];
+    ncn[s] = I->ncount_next[s];
+    cur[s] = I->cur[s];
+  }
+  const uint32_t step0 = I->step;
+  const bool stale0 = I->phi64_stale;
+  const cudaStream_t run = I->stream;
+  const unsigned long long l0 = g_launches, k0 = g_kernels;
+  I->stream = I->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(I->cap_stream, cudaStreamCaptureModeThreadLocal);
+  pic_status ps = e == cudaSuccess ? step_instance<S>(h, I) : PIC_ECUDA;
+  cudaGraph_t g = nullptr;
+  cudaError_t e1 = e == cudaSuccess ? cudaStreamEndCapture(I->cap_stream, &g) : e;
+  I->stream = run;
+  const unsigned long long kernels = g_kernels - k0;
+  g_launches = l0;  // recorded, not run
+  g_kernels = k0;
+  cudaGraphExec_t exec = nullptr;
+  if (ps == PIC_OK && e1 == cudaSuccess && g) {
+    e1 = cudaGraphInstantiate(&exec, g, 0);
+    if (e1 != cudaSuccess) exec = nullptr;
+  }
+  if (g) cudaGraphDestroy(g);
+  if (!exec) {
+    // steps of this instance cannot be recorded here: restore, step directly from now on
+    if (getenv("PIC_VERBOSE"))
+      fprintf(stderr, "pic: step recording unavailable (%s%s%s), stepping directly\n",
+              cudaGetErrorString(e1 != cudaSuccess ? e1 : e), ps == PIC_OK ? "" : "; ", ps == PIC_OK ? "" : h->err.c_str());
+    cudaGetLastError();
+    h->err.clear();
+    I->rho64 = r64;
+    I->rho64_next = r64n;
+    I->rho32 = r32;
+    I->rho32_next = r32n;
+    for (int s = 0; s < kMaxSpecies; ++s) {
+      I->ncount[s] = nc[s];
+      I->ncount_next[s] = ncn[s];
+      I->cur[s] = cur[s];
+    }
+    I->step = step0;
+    I->phi64_stale = stale0;
+    I->graphs_ok = false;
+    return step_instance<S>(h, I);
+  }
+  I->step_exec[key] = exec;
+  I->step_kernels[key] = kernels;
+  count_graph(kernels);
+  CK(h, cudaGraphLaunch(exec, I->stream));
   return PIC_OK;
 }
 
@@ -975,6 +1106,9 @@ pic_status pic_inject(pic_handle* h, int32_t inst, int32_t species, double cx, d
   if (species < 0 || species >= I->nsp) return fail(h, PIC_EINVAL, "species %d out of range", species);
   if (!(radius_m > 0) || !(flux_m2s >= 0) || !(T_K >= 0) || !std::isfinite(cx) || !std::isfinite(cy))
     return fail(h, PIC_EINVAL, "source needs radius > 0, flux >= 0, T >= 0");
+  st = download_carries(h, I);
+  if (st != PIC_OK) return st;
+  I->plan_dirty = true;
   for (size_t q = 0; q < I->sources.size(); ++q) {
     Source& s = I->sources[q];
     if (s.species == species && s.cx == cx && s.cy == cy && s.R == radius_m) {
@@ -1059,7 +1193,7 @@ pic_status pic_step(pic_handle* h, int32_t nsteps) {
   pic_status step_status = PIC_OK;
   for (int n = 0; n < nsteps && step_status == PIC_OK; ++n) {
     for (auto* I : h->inst) {
-      pic_status st = I->mixed ? step_instance<StoreMx>(h, I) : step_instance<Store64>(h, I);
+      pic_status st = I->mixed ? run_step<StoreMx>(h, I) : run_step<Store64>(h, I);
       if (st != PIC_OK) {
         step_status = st;
         break;
@@ -1378,6 +1512,7 @@ pic_status pic_get_phase_times(pic_handle* h, int32_t inst, double* ms, int64_t*
 }
 
 uint64_t pic_launch_count(void) { return (uint64_t)pic::g_launches; }
+uint64_t pic_kernel_count(void) { return (uint64_t)pic::g_kernels; }
 
 pic_status pic_set_sort_interval(pic_handle* h, int32_t inst, int32_t interval) {
   pic_status st = check(h, inst);
@@ -1392,6 +1527,7 @@ pic_status pic_set_mcc_background(pic_handle* h, int32_t inst, double density_m3
   if (st != PIC_OK) return st;
   if (!(density_m3 >= 0)) return fail(h, PIC_EINVAL, "density must be >= 0");
   h->inst[inst]->bg_density = density_m3;
+  drop_step_graphs(h->inst[inst]);
   return PIC_OK;
 }
 

@@ -180,11 +180,39 @@ struct DevCounters {
   double cg_resid;
   unsigned long long ev_sort_n;  // events to order this step (min(n_events, capacity))
   unsigned long long pushed[kMaxSpecies];  // cumulative particle pushes (metric units)
+  unsigned int step;                       // index of the step being taken (Philox counter word 1)
+};
+
+// Injection counts of the current step (a1), kept on the device so that a step
+// can be recorded once and replayed: the carry accumulator of every source
+// advances here exactly as the host formula does (acc += mu; n = floor(acc);
+// acc -= n, all FP64).
+struct InjectPlan {
+  int nsrc;
+  int species[kMaxSources];
+  double mu[kMaxSources];   // expected macroparticles per step
+  double acc[kMaxSources];  // carry
+  long long total;
+  long long src_first[kMaxSources + 1];
+  long long species_offset[kMaxSources];
+  long long add[kMaxSpecies];
 };
 
 // Host-side count of kernel launches issued by the library (all handles).
+// g_launches: launch operations issued to the GPU (a kernel, or a whole graph);
+// g_kernels: kernels those operations run (a graph adds the kernel nodes it was
+// recorded with, each conditional body once).
 extern unsigned long long g_launches;
-#define PIC_LAUNCH(grid, block, smem, stream, ...) (++::pic::g_launches), __VA_ARGS__<<<grid, block, smem, stream>>>
+extern unsigned long long g_kernels;
+inline void count_kernel() {
+  ++g_launches;
+  ++g_kernels;
+}
+inline void count_graph(unsigned long long kernels) {
+  ++g_launches;
+  g_kernels += kernels;
+}
+#define PIC_LAUNCH(grid, block, smem, stream, ...) (::pic::count_kernel()), __VA_ARGS__<<<grid, block, smem, stream>>>
 
 // Ionization event (one per ionizing collision, before victim choice)
 struct Event {

@@ -477,7 +477,6 @@ struct McArgs {
   float bg_density_f;
   double mass;
   uint2 key;
-  uint32_t step;
   int bg_mode;  // fixed background density (test mode)
   double bg_density;
   int count_in_field;  // all channels share one target: its cell count rides in E.w
@@ -502,11 +501,8 @@ struct InjectArgs {
   long long cap[kMaxSpecies];
   int nsrc;
   InjSrc src[kMaxSources];
-  long long src_first[kMaxSources + 1];
-  long long species_offset[kMaxSources];
-  long long total;
+  const InjectPlan* plan;  // this step's counts (device)
   uint2 key;
-  uint32_t step;
   NextDeposit nd;
   int role[kMaxSpecies];
 };
@@ -514,9 +510,8 @@ struct InjectArgs {
 struct InjectCommit {
   int nsp;
   int cur[kMaxSpecies];
-  long long add[kMaxSpecies];
   long long cap[kMaxSpecies];
-  long long total;
+  const InjectPlan* plan;
 };
 
 template <class S>
@@ -562,7 +557,6 @@ struct ApplyArgs {
   const uint32_t* sorted_vals;
   XsDev ch[kMaxXsec];
   uint2 key;
-  uint32_t step;
   S e_st;
   int e_out, e_species;
   long long e_cap;
@@ -595,6 +589,8 @@ struct DepositArgs {
 template <class S>
 void launch_inject(const InjectArgs<S>& a, int grid, cudaStream_t st);
 void launch_inject_commit(DevCounters* cnt, const InjectCommit& c, cudaStream_t st);
+void launch_inject_plan(InjectPlan* plan, int nsp, cudaStream_t st);
+void launch_step_end(DevCounters* cnt, cudaStream_t st);
 template <class S>
 void launch_push(const PushArgs<S>& a, int role, bool mcc, int grid, cudaStream_t st);
 void launch_resolve_rank(const ResolveArgs& a, int grid, cudaStream_t st);

@@ -78,11 +78,14 @@ struct Solver {
   Pcg<float> p32;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  unsigned long long graph_kernels = 0;  // kernel nodes in graph (loop bodies once)
+  cudaStream_t aux[2] = {nullptr, nullptr};  // capture streams of the two loop bodies
   cudaError_t init(int nx, int ny, int nz, int precision);
   void release();
   cudaError_t build_graph(double* x, float* phi32, double phi_c, double phi_a, int nz, double rtol, int maxit);
   cudaError_t build_graph_once(double* x, float* phi32, double phi_c, double phi_a, int nz, double rtol, int maxit);
   cudaError_t launch(cudaStream_t s);
+  cudaError_t record(cudaStream_t s0);
   cudaError_t run_host(cudaStream_t s);
   cudaError_t invalidate(cudaStream_t s);
   // MIXED path: FP64 phi (unknown view, hx) from (hi, lo), and back (x = nullptr: phi = 0)
