@@ -368,9 +368,49 @@ __global__ void k_cell_keys(Grid g, S st, long long n_max, const unsigned long l
     const unsigned long long cell = p.pid == kPidDead ? (unsigned long long)g.ncell : (unsigned long long)particle_cell(p);
     keys[i] = (cell << pid_bits) | ((unsigned long long)p.pid & pmask);
     vals[i] = (uint32_t)i;
-    if (p.pid != kPidDead) atomicAdd(&cell_count[cell], 1);
+    if (cell_count && p.pid != kPidDead) atomicAdd(&cell_count[cell], 1);
   }
 }
+
+// Bucket slots of the cell sort: lanes of a warp with the same cell (the store
+// is close to cell order between sorts) take consecutive slots with one atomic.
+// The loop runs over whole warps, so every lane reaches the match.
+template <class S>
+__global__ void k_cell_slots(Grid g, S st, long long n_max, const unsigned long long* n_dev, int32_t* cell_count,
+                             unsigned long long* __restrict__ words, uint32_t* __restrict__ pids, SegCtl* ctl) {
+  const long long n = min((long long)*n_dev, n_max);
+  const int lane = threadIdx.x & 31;
+  for (long long w0 = gtid() - lane; w0 < n; w0 += gstride()) {
+    const long long i = w0 + lane;
+    const bool valid = i < n;
+    int cell = -1;
+    uint32_t pid = 0;
+    if (valid) {
+      const auto p = store_read(st, g, i);
+      pid = p.pid;
+      cell = pid == kPidDead ? (int)g.ncell : (int)particle_cell(p);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, cell);
+    const int leader = __ffs(peers) - 1;
+    int slot0 = 0;
+    if (valid && lane == leader)
+      slot0 = atomicAdd(cell == (int)g.ncell ? &ctl->dead : &cell_count[cell], __popc(peers));
+    slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+    if (valid) {
+      words[i] = ((unsigned long long)(unsigned)cell << 32) | (unsigned)(slot0 + __popc(peers & ((1u << lane) - 1u)));
+      pids[i] = pid;
+    }
+  }
+}
+template <class S>
+void launch_cell_slots(const Grid& g, S st, long long n_max, const unsigned long long* n_dev, int32_t* cell_count,
+                       unsigned long long* words, uint32_t* pids, SegCtl* ctl, cudaStream_t s) {
+  PIC_LAUNCH(grid_for(n_max), kBlock, 0, s, k_cell_slots<S>)(g, st, n_max, n_dev, cell_count, words, pids, ctl);
+}
+template void launch_cell_slots<Store64>(const Grid&, Store64, long long, const unsigned long long*, int32_t*,
+                                         unsigned long long*, uint32_t*, SegCtl*, cudaStream_t);
+template void launch_cell_slots<StoreMx>(const Grid&, StoreMx, long long, const unsigned long long*, int32_t*,
+                                         unsigned long long*, uint32_t*, SegCtl*, cudaStream_t);
 template <class S>
 void launch_cell_keys(const Grid& g, S st, long long n_max, const unsigned long long* n_dev, int pid_bits,
                       unsigned long long* keys, uint32_t* vals, int32_t* cell_count, cudaStream_t s) {

@@ -187,6 +187,134 @@ int radix_sort_pairs(const SortBuffers& b, const unsigned long long* n_dev, int 
 }
 
 // ---------------------------------------------------------------------------
+// cell sort by buckets: scatter into the buckets, then sort each bucket
+// ---------------------------------------------------------------------------
+// words[i] = cell << 32 | slot (the bucket and the slot taken in it); the pair
+// (pid << 32 | i) goes to cell_start[cell] + slot. The dead bucket is cell =
+// ncell, and cell_start[ncell] is the live total.
+__global__ void k_seg_scatter(long long n_max, const unsigned long long* n_dev,
+                              const unsigned long long* __restrict__ words, const uint32_t* __restrict__ pids,
+                              const long long* __restrict__ cs, unsigned long long* __restrict__ out) {
+  const long long n = min((long long)*n_dev, n_max);
+  for (long long i = gtid(); i < n; i += gstride()) {
+    const unsigned long long w = words[i];
+    out[cs[w >> 32] + (long long)(w & 0xFFFFFFFFull)] = ((unsigned long long)pids[i] << 32) | (unsigned long long)i;
+  }
+}
+
+// One thread per bucket (cells 0..ncell-1, then the dead bucket): the rank of
+// an entry among the bucket's (pid, index) values is its place. Larger buckets
+// are listed for the warp-wide kernel (from the front of `big`) or the
+// block-wide one (from the back; ncell + 1 entries hold both lists).
+__global__ void k_seg_sort(long long ncell, const long long* __restrict__ cs, const unsigned long long* n_dev,
+                           const unsigned long long* __restrict__ v, uint32_t* __restrict__ perm,
+                           int32_t* __restrict__ big, SegCtl* ctl) {
+  const long long n = (long long)*n_dev;
+  for (long long c = gtid(); c <= ncell; c += gstride()) {
+    const long long a = cs[c];
+    const long long b = c < ncell ? cs[c + 1] : n;
+    const long long m = b - a;
+    if (m <= 0) continue;
+    if (m == 1) {
+      perm[a] = (uint32_t)v[a];
+      continue;
+    }
+    if (m > kSegMid) {
+      big[ncell - atomicAdd(&ctl->nbig, 1)] = (int32_t)c;
+      continue;
+    }
+    if (m > kSegSmall) {
+      big[atomicAdd(&ctl->nmid, 1)] = (int32_t)c;
+      continue;
+    }
+    for (long long j = a; j < b; ++j) {
+      const unsigned long long x = v[j];
+      int r = 0;
+      for (long long k = a; k < b; ++k) r += v[k] < x ? 1 : 0;
+      perm[a + r] = (uint32_t)x;
+    }
+  }
+}
+
+// One warp per bucket of the front list (up to kSegMid entries, staged in the
+// warp's slice of shared memory).
+constexpr int kMidWarps = kSortBlock / 32;
+__global__ void __launch_bounds__(kSortBlock) k_seg_sort_mid(long long ncell, const long long* __restrict__ cs,
+                                                             const unsigned long long* n_dev,
+                                                             const unsigned long long* __restrict__ v,
+                                                             uint32_t* __restrict__ perm,
+                                                             const int32_t* __restrict__ big, const SegCtl* ctl) {
+  __shared__ unsigned long long sv[kMidWarps][kSegMid];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long n = (long long)*n_dev;
+  const int nmid = ctl->nmid;
+  for (int q = blockIdx.x * kMidWarps + w; q < nmid; q += gridDim.x * kMidWarps) {
+    const long long c = big[q];
+    const long long a = cs[c];
+    const long long b = c < ncell ? cs[c + 1] : n;
+    const int m = (int)(b - a);  // kSegSmall < m <= kSegMid
+    __syncwarp();  // the previous bucket's readers are done with this slice
+    for (int j = lane; j < m; j += 32) sv[w][j] = v[a + j];
+    __syncwarp();
+    for (int j = lane; j < m; j += 32) {
+      const unsigned long long x = sv[w][j];
+      int r = 0;
+      for (int k = 0; k < m; ++k) r += sv[w][k] < x ? 1 : 0;
+      perm[a + r] = (uint32_t)x;
+    }
+  }
+}
+
+// One block per bucket of the back list (up to kSegBig entries staged in
+// shared memory; a larger one sets overflow and is left to the radix path).
+__global__ void __launch_bounds__(kSortBlock) k_seg_sort_big(long long ncell, const long long* __restrict__ cs,
+                                                             const unsigned long long* n_dev,
+                                                             const unsigned long long* __restrict__ v,
+                                                             uint32_t* __restrict__ perm,
+                                                             const int32_t* __restrict__ big, SegCtl* ctl) {
+  __shared__ unsigned long long sv[kSegBig];
+  const long long n = (long long)*n_dev;
+  const int nbig = ctl->nbig;
+  for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
+    const long long c = big[ncell - q];
+    const long long a = cs[c];
+    const long long b = c < ncell ? cs[c + 1] : n;
+    const int m = (int)(b - a);
+    if (m > kSegBig) {  // the same m in every thread: the block skips together
+      if (threadIdx.x == 0) ctl->overflow = 1;
+      continue;
+    }
+    __syncthreads();  // the previous bucket's readers are done with sv
+    for (int j = threadIdx.x; j < m; j += blockDim.x) sv[j] = v[a + j];
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      const unsigned long long x = sv[j];
+      int r = 0;
+      for (int k = 0; k < m; ++k) r += sv[k] < x ? 1 : 0;
+      perm[a + r] = (uint32_t)x;
+    }
+  }
+}
+
+static int seg_grid(long long n) {
+  const long long b = (n + kSortBlock - 1) / kSortBlock;
+  const long long cap = 16LL * sm_count();
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+void launch_seg_scatter(long long n_max, const unsigned long long* n_dev, const unsigned long long* words,
+                        const uint32_t* pids, const long long* cell_start, unsigned long long* out, cudaStream_t s) {
+  PIC_LAUNCH(seg_grid(n_max), kSortBlock, 0, s, k_seg_scatter)(n_max, n_dev, words, pids, cell_start, out);
+}
+
+void launch_seg_sort(long long ncell, const long long* cell_start, const unsigned long long* n_dev,
+                     const unsigned long long* vals, uint32_t* perm, int32_t* big, SegCtl* ctl, cudaStream_t s) {
+  PIC_LAUNCH(seg_grid(ncell + 1), kSortBlock, 0, s, k_seg_sort)(ncell, cell_start, n_dev, vals, perm, big, ctl);
+  PIC_LAUNCH(8 * sm_count(), kSortBlock, 0, s, k_seg_sort_mid)(ncell, cell_start, n_dev, vals, perm, big, ctl);
+  PIC_LAUNCH(2 * sm_count(), kSortBlock, 0, s, k_seg_sort_big)(ncell, cell_start, n_dev, vals, perm, big, ctl);
+}
+
+// ---------------------------------------------------------------------------
 // exclusive scan int32 -> int64 (three kernels: tile sums, scan of sums, tiles)
 // ---------------------------------------------------------------------------
 constexpr int kScanBlock = 256;

@@ -25,6 +25,16 @@ namespace pic {
 unsigned long long g_launches = 0;
 unsigned long long g_kernels = 0;
 void set_static_error(const char* msg);
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
 }
 
 namespace {
@@ -168,6 +178,9 @@ struct Instance {
   SortBuffers csort{};
   int32_t* cell_count = nullptr;
   long long* cell_start[kMaxSpecies]{};
+  SegCtl* seg_ctl = nullptr;    // bucket path state (device)
+  SegCtl* seg_host = nullptr;   // pinned mirror
+  int32_t* seg_big = nullptr;   // buckets for the block-wide sort (ncell + 1)
   void* scan_tmp = nullptr;
   double* red = nullptr;  // reduction scratch (moments)
   Solver solver;
@@ -232,16 +245,6 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * count);
 }
 
-int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 152;
-  }
-  return n;
-}
 
 int bits_for(unsigned long long v) {
   int b = 0;
@@ -302,6 +305,9 @@ void free_instance(Instance* I) {
   cudaFree(I->csort.digit_tot);
   cudaFree(I->csort.small_done);
   cudaFree(I->cell_count);
+  cudaFree(I->seg_ctl);
+  cudaFree(I->seg_big);
+  if (I->seg_host) cudaFreeHost(I->seg_host);
   cudaFree(I->scan_tmp);
   cudaFree(I->red);
   cudaFree(I->stage_x);
@@ -559,6 +565,9 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
   }
   if (alloc_sort(I->csort, maxcap)) return fail(h, PIC_ENOMEM, "sort buffers");
   CK(h, dalloc(&I->cell_count, g.ncell));
+  CK(h, dalloc(&I->seg_ctl, 1));
+  CK(h, dalloc(&I->seg_big, g.ncell + 1));
+  CK(h, cudaMallocHost((void**)&I->seg_host, sizeof(SegCtl)));
   CK(h, cudaMalloc(&I->scan_tmp, scan_temp_bytes(g.ncell)));
   CK(h, dalloc(&I->red, 64));
 
@@ -636,15 +645,33 @@ pic_status sort_instance(pic_handle* h, Instance* I) {
   for (int s = 0; s < I->nsp; ++s) {
     const int c = I->cur[s];
     unsigned long long* ndev = &I->cnt->n[c][s];
+    if (I->host_cnt->n[c][s] == 0) {  // nothing to move: offsets all zero; buffers flip as for every species
+      CK(h, cudaMemsetAsync(I->cell_start[s], 0, sizeof(long long) * (I->g.ncell + 1), st));
+      launch_sort_commit(I->cnt, c, s, st);
+      I->cur[s] = c ^ 1;
+      continue;
+    }
+    // bucket path: slots, offsets, scatter, per-bucket sort by (pid, index)
     CK(h, cudaMemsetAsync(I->cell_count, 0, sizeof(int32_t) * I->g.ncell, st));
-    launch_cell_keys<S>(I->g, store_of<S>(I, s, c), I->cap[s], ndev, pid_bits, I->csort.ka, I->csort.va,
-                        I->cell_count, st);
-    SortBuffers b = I->csort;
-    b.n_max = I->cap[s];
-    const int where = radix_sort_pairs(b, ndev, 0, ((key_bits + 7) / 8) * 8, st);
-    const uint32_t* perm = where ? b.vb : b.va;
-    launch_gather<S>(store_of<S>(I, s, c), store_of<S>(I, s, c ^ 1), perm, ndev, I->cap[s], st);
+    CK(h, cudaMemsetAsync(I->seg_ctl, 0, sizeof(SegCtl), st));
+    launch_cell_slots<S>(I->g, store_of<S>(I, s, c), I->cap[s], ndev, I->cell_count, I->csort.ka, I->csort.va,
+                         I->seg_ctl, st);
     exclusive_scan_i32_i64(I->cell_count, I->g.ncell, I->cell_start[s], I->scan_tmp, st);
+    launch_seg_scatter(I->cap[s], ndev, I->csort.ka, I->csort.va, I->cell_start[s], I->csort.kb, st);
+    launch_seg_sort(I->g.ncell, I->cell_start[s], ndev, I->csort.kb, I->csort.vb, I->seg_big, I->seg_ctl, st);
+    CK(h, cudaMemcpyAsync(I->seg_host, I->seg_ctl, sizeof(SegCtl), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    const uint32_t* perm = I->csort.vb;
+    if (I->seg_host->overflow) {
+      // a bucket too large for one block: LSD radix sort of the key (cell, pid)
+      launch_cell_keys<S>(I->g, store_of<S>(I, s, c), I->cap[s], ndev, pid_bits, I->csort.ka, I->csort.va, nullptr,
+                          st);
+      SortBuffers b = I->csort;
+      b.n_max = I->cap[s];
+      const int where = radix_sort_pairs(b, ndev, 0, ((key_bits + 7) / 8) * 8, st);
+      perm = where ? b.vb : b.va;
+    }
+    launch_gather<S>(store_of<S>(I, s, c), store_of<S>(I, s, c ^ 1), perm, ndev, I->cap[s], st);
     launch_sort_commit(I->cnt, c, s, st);
     I->cur[s] = c ^ 1;
   }

@@ -202,6 +202,7 @@ struct InjectPlan {
 // g_launches: launch operations issued to the GPU (a kernel, or a whole graph);
 // g_kernels: kernels those operations run (a graph adds the kernel nodes it was
 // recorded with, each conditional body once).
+int sm_count();  // multiprocessors of the current device
 extern unsigned long long g_launches;
 extern unsigned long long g_kernels;
 inline void count_kernel() {

@@ -624,6 +624,30 @@ void launch_cell_keys(const Grid& g, S st, long long n_max, const unsigned long 
 
 // radix sort of (u64 key, u32 value) pairs over bits [bit0, bit1); n read from
 // the device (at most n_max). Returns 0 if the result is in (ka, va), 1 if in (kb, vb).
+// a2 cell sort by buckets (k_sort.cu, k_grid.cu): every particle takes a slot in
+// its cell's bucket (warp-aggregated atomics on the cell counts, so the order
+// inside a bucket is arbitrary), the buckets are laid out by a scan of the
+// counts, and each bucket is then sorted by (pid, input index), which makes the
+// permutation the unique one of the key (cell, pid). Dead slots form a last
+// bucket after every cell, in input order. A bucket larger than kSegBig sets
+// `overflow`, and the caller sorts that species by the radix path instead.
+struct SegCtl {
+  int dead;      // slots taken in the dead bucket
+  int nmid;      // buckets of kSegSmall < m <= kSegMid entries, listed from the front of `big`
+  int nbig;      // buckets of kSegMid < m entries, listed from the back of `big`
+  int overflow;  // a bucket of more than kSegBig entries
+};
+constexpr int kSegSmall = 16;   // sorted by one thread
+constexpr int kSegMid = 256;    // by one warp
+constexpr int kSegBig = 4096;   // by one block
+template <class S>
+void launch_cell_slots(const Grid& g, S st, long long n_max, const unsigned long long* n_dev, int32_t* cell_count,
+                       unsigned long long* words, uint32_t* pids, SegCtl* ctl, cudaStream_t s);
+void launch_seg_scatter(long long n_max, const unsigned long long* n_dev, const unsigned long long* words,
+                        const uint32_t* pids, const long long* cell_start, unsigned long long* out, cudaStream_t s);
+void launch_seg_sort(long long ncell, const long long* cell_start, const unsigned long long* n_dev,
+                     const unsigned long long* vals, uint32_t* perm, int32_t* big, SegCtl* ctl, cudaStream_t s);
+
 struct SortBuffers {
   unsigned long long *ka, *kb;
   uint32_t *va, *vb;

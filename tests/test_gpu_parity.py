@@ -244,6 +244,50 @@ def test_sort_permutation_and_offsets_bit_exact(pkg):
     sim.close()
 
 
+@pytest.mark.parametrize("n_dense", [300, 5000])
+def test_sort_crowded_cells_and_dead_slots(pkg, n_dense):
+    # one dense cell (n_dense electrons and as many ions: above 4096 the radix
+    # path takes over), 400 neutrals and 200 sparse electrons in buckets sorted
+    # block-wide, and, right after a step, the dead slots of converted neutrals
+    wl = ionization_cells_case(seed=7, n_dense_e=n_dense, capacity=1 << 17)
+    sim = pkg.Simulation(wl)
+    ref = O.Oracle(wl)
+    for _ in range(2):
+        sim.step()
+        ref.step()
+        assert sim.moments()["n_ionization"] > 0
+        sim.sort_now()
+        ref.sort()
+        for sp in range(3):
+            _, _, pg = sim.particles(sp)
+            _, _, po = ref.particles(sp)
+            assert np.array_equal(pg, po), sp
+            assert np.array_equal(sim.cell_start(sp), ref.cell_start(sp)), sp
+    sim.close()
+
+
+def test_sort_order_mixed_store(pkg):
+    # the mixed store's cells come from FP32 offsets, so cell boundaries may
+    # differ from the oracle's by rounding: check the order itself (pids rising
+    # inside every cell range, ranges covering the store) and the pid sets
+    wl = ionization_cells_case(seed=8, n_dense_e=600, capacity=1 << 15)
+    sim = pkg.Simulation(wl, precision=pkg.PIC_MIXED)
+    ref = O.Oracle(wl)
+    sim.step(2)
+    ref.step(2)
+    sim.sort_now()
+    for sp in range(3):
+        _, _, pg = sim.particles(sp)
+        _, _, po = ref.particles(sp)
+        cs = sim.cell_start(sp)
+        assert cs[0] == 0 and cs[-1] == pg.size and np.all(np.diff(cs) >= 0)
+        for a, b in zip(cs[:-1], cs[1:]):
+            if b - a > 1:
+                assert np.all(np.diff(pg[a:b].astype(np.int64)) > 0)
+        assert np.array_equal(np.sort(pg), np.sort(po))
+    sim.close()
+
+
 def test_vacuum_uniform_field_push_exact(pkg):
     wl = bare(nx=4, ny=4, nz=16, h=5e-9, dt=1e-16, phi_c=0.0, phi_a=100.0, weight=1e-30)
     rng = np.random.default_rng(1)
