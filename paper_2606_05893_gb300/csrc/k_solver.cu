@@ -130,9 +130,8 @@ __global__ void __launch_bounds__(256) k_residual(Lv L, const T* __restrict__ x,
 // ---------------------------------------------------------------------------
 // One red-black Gauss-Seidel half sweep: points with (i + j + knode) % 2 == color
 // (x index m covers the nx/2 points of that colour in a row).
-// zero_init: the level starts from e = 0 (the other colour is written as 0).
 template <class T>
-__global__ void __launch_bounds__(256) k_smooth(Lv L, T* __restrict__ e, const T* __restrict__ b, int color, int zero_init) {
+__global__ void __launch_bounds__(256) k_smooth(Lv L, T* __restrict__ e, const T* __restrict__ b, int color) {
   pdl_enter();
   const T sixth = (T)(1.0 / 6.0);
   const int hx = L.nx >> 1;
@@ -140,15 +139,47 @@ __global__ void __launch_bounds__(256) k_smooth(Lv L, T* __restrict__ e, const T
   const int k = blockIdx.z;
   if (m >= hx) return;
   for (int j = blockIdx.y * kBY + threadIdx.y; j < L.ny; j += gridDim.y * kBY) {
-    const int par = (j + k + 1 + color) & 1;
-    const int i = 2 * m + par;
+    const int i = 2 * m + ((j + k + 1 + color) & 1);
     const int u = k * L.pl + j * L.nx + i;
-    if (zero_init) {
-      e[u] = b[u] * sixth;
-      e[u - i + (2 * m + (par ^ 1))] = (T)0;
-    } else {
-      e[u] = (b[u] + nb_sum(L, e, u, i, j, k)) * sixth;
-    }
+    e[u] = (b[u] + nb_sum(L, e, u, i, j, k)) * sixth;
+  }
+}
+
+// products rounded on their own (no contraction into a neighbouring add), so a
+// value recomputed in a register equals the one a separate kernel stored
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// nb_sum of the values x / 6 (each product rounded as a stored x / 6 would be)
+template <class T>
+__device__ __forceinline__ T nb_sum_sixth(const Lv& L, const T* __restrict__ x, int u, int i, int j, int k, T sixth) {
+  const int row = u - i;
+  const int im = i == 0 ? L.nx - 1 : i - 1, ip = i == L.nx - 1 ? 0 : i + 1;
+  const int rm = j == 0 ? (L.ny - 1) * L.nx : -L.nx;
+  const int rp = j == L.ny - 1 ? -(L.ny - 1) * L.nx : L.nx;
+  T s = mul_rn(x[row + im], sixth) + mul_rn(x[row + ip], sixth) + mul_rn(x[u + rm], sixth) + mul_rn(x[u + rp], sixth);
+  if (k > 0) s += mul_rn(x[u - L.pl], sixth);
+  if (k < L.nz - 2) s += mul_rn(x[u + L.pl], sixth);
+  return s;
+}
+
+// The two pre-smoothing half sweeps from e = 0 in one pass: colour 0 takes
+// b / 6, colour 1 then takes (b + the sum of its colour-0 neighbours) / 6, the
+// neighbours' b / 6 recomputed here. Same values as the two sweeps.
+template <class T>
+__global__ void __launch_bounds__(256) k_smooth_pre(Lv L, T* __restrict__ e, const T* __restrict__ b) {
+  pdl_enter();
+  const T sixth = (T)(1.0 / 6.0);
+  const int hx = L.nx >> 1;
+  const int m = blockIdx.x * kBX + threadIdx.x;
+  const int k = blockIdx.z;
+  if (m >= hx) return;
+  for (int j = blockIdx.y * kBY + threadIdx.y; j < L.ny; j += gridDim.y * kBY) {
+    const int par = (j + k + 1) & 1;  // colour 0 at i = 2m + par
+    const int i0 = 2 * m + par, i1 = 2 * m + (par ^ 1);
+    const int row = k * L.pl + j * L.nx;
+    e[row + i0] = mul_rn(b[row + i0], sixth);
+    e[row + i1] = (b[row + i1] + nb_sum_sixth(L, b, row + i1, i1, j, k, sixth)) * sixth;
   }
 }
 
@@ -182,7 +213,10 @@ __global__ void __launch_bounds__(256) k_restrict(Lv F, Lv Cc, const T* __restri
   }
 }
 
-// e_f += P e_c (trilinear; coarse Dirichlet planes carry 0); grid over the fine level
+// e_f += P e_c (trilinear; coarse Dirichlet planes carry 0) on the colour-0
+// points only: the colour-1 half sweep that follows reads colour-0 neighbours
+// alone and overwrites colour 1, so prolonged colour-1 values would never be
+// read. Grid as for the half sweeps (x covers the nx / 2 points of a colour).
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong(Lv F, Lv Cc, const T* __restrict__ ec, T* __restrict__ ef) {
   pdl_enter();
@@ -193,12 +227,13 @@ __global__ void __launch_bounds__(256) k_prolong(Lv F, Lv Cc, const T* __restric
   const bool use1 = kodd && (K0 + 1) >= 1 && (K0 + 1) <= Cc.nz - 1;
   const int off0 = (K0 - 1) * Cc.pl, off1 = K0 * Cc.pl;
   const T wk = kodd ? (T)0.5 : (T)1;
-  const int i = blockIdx.x * kBX + threadIdx.x;
-  if (i >= F.nx) return;
-  const int I0 = i >> 1;
-  const int I1 = I0 + 1 == Cc.nx ? 0 : I0 + 1;
-  const bool iodd = i & 1;
+  const int m = blockIdx.x * kBX + threadIdx.x;
+  if (m >= (F.nx >> 1)) return;
   for (int j = blockIdx.y * kBY + threadIdx.y; j < F.ny; j += gridDim.y * kBY) {
+    const int i = 2 * m + ((j + (int)blockIdx.z + 1) & 1);  // colour 0
+    const int I0 = i >> 1;
+    const int I1 = I0 + 1 == Cc.nx ? 0 : I0 + 1;
+    const bool iodd = i & 1;
     const int J0 = j >> 1;
     const int J1 = J0 + 1 == Cc.ny ? 0 : J0 + 1;
     const bool jodd = j & 1;
@@ -398,7 +433,7 @@ __device__ __forceinline__ float k_nb(float* sm, const PlaneMap& pm, int l, cons
   return s;
 }
 
-__device__ void kc_smooth(float* sm, const PlaneMap& pm, int l, const KLv& L, int me, int color, int zero_init) {
+__device__ void kc_smooth(float* sm, const PlaneMap& pm, int l, const KLv& L, int me, int color) {
   const float sixth = 1.0f / 6.0f;
   const int p0 = plane0(L.P, me), np = plane0(L.P, me + 1) - p0;
   const int per = L.hx * L.ny;
@@ -408,17 +443,39 @@ __device__ void kc_smooth(float* sm, const PlaneMap& pm, int l, const KLv& L, in
     const int j = fdiv(t, L.dhx);
     const int m = t - j * L.hx;
     const int k = p0 + kk;
-    const int par = (j + k + 1 + color) & 1;
-    const int i = 2 * m + par;
+    const int i = 2 * m + ((j + k + 1 + color) & 1);
     float* e = sm + L.oe + kk * L.pl;
     const float* b = sm + L.ob + kk * L.pl;
     const int u = j * L.nx + i;
-    if (zero_init) {
-      e[u] = b[u] * sixth;
-      e[u - i + (2 * m + (par ^ 1))] = 0.f;
-    } else {
-      e[u] = (b[u] + k_nb(sm, pm, l, L, L.oe, e, k, i, j, me)) * sixth;
-    }
+    e[u] = (b[u] + k_nb(sm, pm, l, L, L.oe, e, k, i, j, me)) * sixth;
+  }
+}
+
+// the two pre-smoothing half sweeps from e = 0 in one phase (as k_smooth_pre)
+__device__ void kc_smooth_pre(float* sm, const PlaneMap& pm, int l, const KLv& L, int me) {
+  const float sixth = 1.0f / 6.0f;
+  const int p0 = plane0(L.P, me), np = plane0(L.P, me + 1) - p0;
+  const int per = L.hx * L.ny;
+  for (int q = threadIdx.x; q < np * per; q += blockDim.x) {
+    const int kk = fdiv(q, L.dhxny);
+    const int t = q - kk * per;
+    const int j = fdiv(t, L.dhx);
+    const int m = t - j * L.hx;
+    const int k = p0 + kk;
+    const int par = (j + k + 1) & 1;
+    const int i0 = 2 * m + par, i1 = 2 * m + (par ^ 1);
+    float* e = sm + L.oe + kk * L.pl;
+    const float* bp = sm + L.ob + kk * L.pl;
+    const int r = j * L.nx;
+    e[r + i0] = __fmul_rn(bp[r + i0], sixth);
+    // colour-0 neighbours of (i1, j, k), each b / 6, summed in k_nb's order
+    const int im = i1 == 0 ? L.nx - 1 : i1 - 1, ip = i1 == L.nx - 1 ? 0 : i1 + 1;
+    const int jm = j == 0 ? L.ny - 1 : j - 1, jp = j == L.ny - 1 ? 0 : j + 1;
+    float sn = __fmul_rn(bp[r + im], sixth) + __fmul_rn(bp[r + ip], sixth) + __fmul_rn(bp[jm * L.nx + i1], sixth) +
+               __fmul_rn(bp[jp * L.nx + i1], sixth);
+    if (k > 0) sn += __fmul_rn(plane_ptr(sm, pm, l, L, L.ob, k - 1, me)[r + i1], sixth);
+    if (k < L.P - 1) sn += __fmul_rn(plane_ptr(sm, pm, l, L, L.ob, k + 1, me)[r + i1], sixth);
+    e[r + i1] = (bp[r + i1] + sn) * sixth;
   }
 }
 
@@ -466,12 +523,15 @@ __device__ void kc_restrict(float* sm, const PlaneMap& pm, int l, const KLv& F, 
 }
 
 __device__ void kc_prolong(float* sm, const PlaneMap& pm, int l, const KLv& F, const KLv& C, int me) {
+  // colour-0 points only (the colour-1 half sweep that follows reads colour 0 alone)
   const int p0 = plane0(F.P, me), np = plane0(F.P, me + 1) - p0;
-  for (int q = threadIdx.x; q < np * F.pl; q += blockDim.x) {
-    const int kk = fdiv(q, F.dpl);
-    const int u = q - kk * F.pl;
-    const int j = fdiv(u, F.dnx);
-    const int i = u - j * F.nx;
+  const int per = F.hx * F.ny;
+  for (int q = threadIdx.x; q < np * per; q += blockDim.x) {
+    const int kk = fdiv(q, F.dhxny);
+    const int t = q - kk * per;
+    const int j = fdiv(t, F.dhx);
+    const int i = 2 * (t - j * F.hx) + ((j + p0 + kk + 1) & 1);
+    const int u = j * F.nx + i;
     const int kn = p0 + kk + 1;  // fine node plane
     const int K0 = kn >> 1;
     const bool kodd = kn & 1;
@@ -525,9 +585,7 @@ __global__ void __launch_bounds__(kClusterThreads) k_coarse_cluster(ClusterArgs 
   }
   cl.sync();
   for (int l = 0; l < nl - 1; ++l) {
-    kc_smooth(sm, pm, l, a.L[l], me, 0, 1);
-    cl.sync();
-    kc_smooth(sm, pm, l, a.L[l], me, 1, 0);
+    kc_smooth_pre(sm, pm, l, a.L[l], me);
     cl.sync();
     kc_residual(sm, pm, l, a.L[l], me);
     cl.sync();
@@ -556,32 +614,30 @@ __global__ void __launch_bounds__(kClusterThreads) k_coarse_cluster(ClusterArgs 
       }
       cl.sync();
     } else {
-      kc_smooth(sm, pm, nl - 1, C, me, 0, 1);
-      cl.sync();
-      kc_smooth(sm, pm, nl - 1, C, me, 1, 0);
+      kc_smooth_pre(sm, pm, nl - 1, C, me);
       cl.sync();
       for (int it = 0; it < a.coarse_sweeps; ++it) {
-        kc_smooth(sm, pm, nl - 1, C, me, 1, 0);
+        kc_smooth(sm, pm, nl - 1, C, me, 1);
         cl.sync();
-        kc_smooth(sm, pm, nl - 1, C, me, 0, 0);
+        kc_smooth(sm, pm, nl - 1, C, me, 0);
         cl.sync();
-        kc_smooth(sm, pm, nl - 1, C, me, 0, 0);
+        kc_smooth(sm, pm, nl - 1, C, me, 0);
         cl.sync();
-        kc_smooth(sm, pm, nl - 1, C, me, 1, 0);
+        kc_smooth(sm, pm, nl - 1, C, me, 1);
         cl.sync();
       }
-      kc_smooth(sm, pm, nl - 1, C, me, 1, 0);
+      kc_smooth(sm, pm, nl - 1, C, me, 1);
       cl.sync();
-      kc_smooth(sm, pm, nl - 1, C, me, 0, 0);
+      kc_smooth(sm, pm, nl - 1, C, me, 0);
       cl.sync();
     }
   }
   for (int l = nl - 2; l >= 0; --l) {
     kc_prolong(sm, pm, l, a.L[l], a.L[l + 1], me);
     cl.sync();
-    kc_smooth(sm, pm, l, a.L[l], me, 1, 0);
+    kc_smooth(sm, pm, l, a.L[l], me, 1);
     cl.sync();
-    kc_smooth(sm, pm, l, a.L[l], me, 0, 0);
+    kc_smooth(sm, pm, l, a.L[l], me, 0);
     cl.sync();
   }
   {
@@ -726,8 +782,7 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
   const int ff = fuse_from;  // levels ff..nl-1 run in one cluster (FP32 only), -1: none
   for (int l = 0; l < (ff > 0 ? ff : nl - 1); ++l) {
     const Lv L = lv_of(levels[l]);
-    SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 0, 1);
-    SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 1, 0);
+    SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth_pre<T>)(L, E[l], B[l]);
     SOLVER_LAUNCH(g3(L, L.nx), kB3, 0, s, k_residual<T>)(L, E[l], B[l], r[l]);
     const Lv C = lv_of(levels[l + 1]);
     SOLVER_LAUNCH(g3(C, C.nx), kB3, 0, s, k_restrict<T>)(L, C, r[l], B[l + 1]);
@@ -773,24 +828,23 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
       SOLVER_LAUNCH(cg, kSB, 0, s, k_coarse<T>)(C.nu, Ainv, B[nl - 1],
                                                                                               E[nl - 1]);
     } else {
-      SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 1);
-      SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
+      SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth_pre<T>)(C, E[nl - 1], B[nl - 1]);
       for (int it = 0; it < coarse_sweeps; ++it) {
-        SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
-        SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
-        SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
-        SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
+        SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1);
+        SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0);
+        SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0);
+        SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1);
       }
-      SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1, 0);
-      SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0, 0);
+      SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 1);
+      SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0);
     }
   }
   for (int l = (ff > 0 ? ff : nl - 1) - 1; l >= 0; --l) {
     const Lv L = lv_of(levels[l]);
     const Lv C = lv_of(levels[l + 1]);
-    SOLVER_LAUNCH(g3(L, L.nx), kB3, 0, s, k_prolong<T>)(L, C, E[l + 1], E[l]);
-    SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 1, 0);
-    SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 0, 0);
+    SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_prolong<T>)(L, C, E[l + 1], E[l]);
+    SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 1);
+    SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 0);
   }
 }
 
