@@ -114,6 +114,24 @@ __device__ __forceinline__ T nb_sum(const Lv& L, const T* __restrict__ x, int u,
   const bool in_x = i < (xe);                                                \
   for (int j = blockIdx.y * kBY + threadIdx.y; j < (L).ny; j += gridDim.y * kBY)
 
+// The same with k striding over the planes too, for the kernels that end in a
+// grid-wide sum: launched on g3r (at most one wave of blocks), so each block
+// pays the partial's fence and ticket once for several planes.
+#define ROWS3K(L, xe)                                                         \
+  const int i = blockIdx.x * kBX + threadIdx.x;                              \
+  const bool in_x = i < (xe);                                                \
+  for (int k = blockIdx.z; k < (L).nz - 1; k += gridDim.z)                   \
+    for (int j = blockIdx.y * kBY + threadIdx.y; j < (L).ny; j += gridDim.y * kBY)
+constexpr int kWaveBlocks = 152 * 8;  // resident 256-thread blocks on 152 SMs
+static dim3 g3r(const Lv& L) {
+  dim3 g = g3(L, L.nx);
+  const int per_plane = (int)(g.x * g.y);
+  int gz = kWaveBlocks / per_plane;
+  gz = gz < 1 ? 1 : (gz > (int)g.z ? (int)g.z : gz);
+  g.z = gz;
+  return g;
+}
+
 // r = b - A x (no reduction; multigrid levels)
 template <class T>
 __global__ void __launch_bounds__(256) k_residual(Lv L, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r) {
@@ -968,7 +986,7 @@ __global__ void __launch_bounds__(256) k_residual_prep(Lv L, double* __restrict_
   Tin acc = 0;
   const bool zero_x = c->bb == 0.0;
   const bool cached = c->ax_valid != 0;
-  ROWS3(L, L.nx) {
+  ROWS3K(L, L.nx) {
     if (!in_x) continue;
     const int u = k * L.pl + j * L.nx + i;
     double rv = 0.0;
@@ -1044,7 +1062,7 @@ __global__ void __launch_bounds__(256) k_dot_bb_ff(Lv L, const float* __restrict
                                                    double* part, SolveCtl* c, double rtol, int maxit) {
   pdl_enter();
   float acc = 0.f;
-  ROWS3(L, L.nx) {
+  ROWS3K(L, L.nx) {
     if (!in_x) continue;
     const int u = k * L.pl + j * L.nx + i;
     float bv = f[u];
@@ -1067,7 +1085,7 @@ __global__ void __launch_bounds__(256) k_residual_ff(Lv L, float* __restrict__ h
   pdl_enter();
   float acc = 0.f;
   const bool zero_x = c->bb == 0.0;
-  ROWS3(L, L.nx) {
+  ROWS3K(L, L.nx) {
     if (!in_x) continue;
     const int u = k * L.pl + j * L.nx + i;
     float rv = 0.f;
@@ -1185,7 +1203,7 @@ __global__ void __launch_bounds__(256) k_apply_pq(Lv L, const T* __restrict__ p,
                                                   SolveCtl* c) {
   pdl_enter();
   T acc = 0;
-  ROWS3(L, L.nx) {
+  ROWS3K(L, L.nx) {
     if (!in_x) continue;
     const int u = k * L.pl + j * L.nx + i;
     const T pv = p[u];
@@ -1388,7 +1406,7 @@ static void capture_pcg_iteration(Pcg<T>& pc, const Lv& L, double* part, SolveCt
   SOLVER_LAUNCH(G, kSB, 0, s, k_dot_rz<T>)(L.nu, pc.r, pc.z, part, ctl);
   const dim3 PGd = g3(L, L.nx);
   SOLVER_LAUNCH(G, kSB, 0, s, k_pupdate_c<T>)(L.nu, pc.p, pc.z, ctl);
-  SOLVER_LAUNCH(PGd, kB3, 0, s, k_apply_pq<T>)(L, pc.p, pc.q, part, ctl);
+  SOLVER_LAUNCH(g3r(L), kB3, 0, s, k_apply_pq<T>)(L, pc.p, pc.q, part, ctl);
   SOLVER_LAUNCH(G, kSB, 0, s, k_update_rr<T>)(L.nu, pc.d, pc.r, pc.p, pc.q, ctl, part, h_inner, use_graph);
 }
 
@@ -1483,7 +1501,7 @@ cudaError_t Solver::record(cudaStream_t s0) {
   cudaGraphConditionalHandle h_outer, h_inner;
   cudaGraph_t outer_body = nullptr, inner_body = nullptr;
   if (mixed) {
-    SOLVER_LAUNCH(PGd, kB3, 0, s0, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, rtol, maxit);
+    SOLVER_LAUNCH(g3r(L), kB3, 0, s0, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, rtol, maxit);
   } else {
     SOLVER_LAUNCH(G, kSB, 0, s0, k_dot_bb)(L.nu, b, part, ctl, rtol, maxit);
   }
@@ -1494,10 +1512,10 @@ cudaError_t Solver::record(cudaStream_t s0) {
     e = cudaGraphConditionalHandleCreate(&h_inner, outer_body, 0u, 0);
     if (e == cudaSuccess) {
       if (mixed) {
-        SOLVER_LAUNCH(PGd, kB3, 0, s1, k_residual_ff)(L, phi32, lo32, f32, p32.r, p32.d, phi_c, dphi_dk, part, ctl,
+        SOLVER_LAUNCH(g3r(L), kB3, 0, s1, k_residual_ff)(L, phi32, lo32, f32, p32.r, p32.d, phi_c, dphi_dk, part, ctl,
                                                     h_outer, h_inner, inner_rtol, max_outer, 1);
       } else {
-        SOLVER_LAUNCH(PGd, kB3, 0, s1, k_residual_prep<double>)(L, x, b, ax, p64.r, p64.d, part, ctl, h_outer, h_inner,
+        SOLVER_LAUNCH(g3r(L), kB3, 0, s1, k_residual_prep<double>)(L, x, b, ax, p64.r, p64.d, part, ctl, h_outer, h_inner,
                                                               inner_rtol, mixed, max_outer, 1);
       }
     }
@@ -1570,14 +1588,14 @@ cudaError_t Solver::run_host(cudaStream_t s) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return e;
   };
-  if (mixed) SOLVER_LAUNCH(PGd, kB3, 0, s, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, h_rtol, h_maxit);
+  if (mixed) SOLVER_LAUNCH(g3r(L), kB3, 0, s, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, h_rtol, h_maxit);
   else SOLVER_LAUNCH(G, kSB, 0, s, k_dot_bb)(L.nu, b, part, ctl, h_rtol, h_maxit);
   for (int outer = 0; outer < max_outer + 1; ++outer) {
     if (mixed)
-      SOLVER_LAUNCH(PGd, kB3, 0, s, k_residual_ff)(L, hphi32, lo32, f32, p32.r, p32.d, h_phi_c, h_dphi_dk, part, ctl, none,
+      SOLVER_LAUNCH(g3r(L), kB3, 0, s, k_residual_ff)(L, hphi32, lo32, f32, p32.r, p32.d, h_phi_c, h_dphi_dk, part, ctl, none,
                                                  none, inner_rtol, max_outer, 0);
     else
-      SOLVER_LAUNCH(PGd, kB3, 0, s, k_residual_prep<double>)(L, hx, b, ax, p64.r, p64.d, part, ctl, none, none, inner_rtol,
+      SOLVER_LAUNCH(g3r(L), kB3, 0, s, k_residual_prep<double>)(L, hx, b, ax, p64.r, p64.d, part, ctl, none, none, inner_rtol,
                                                            mixed, max_outer, 0);
     cudaError_t e = read();
     if (e != cudaSuccess) return e;
