@@ -97,6 +97,8 @@ def lib():
         L.or_get_cell_start.argtypes = [P, C.c_int, C.POINTER(C.c_int64)]
         L.or_get_log.restype = C.c_int64
         L.or_get_log.argtypes = [P, u32]
+        L.or_get_hits.restype = C.c_int64
+        L.or_get_hits.argtypes = [P, u32, C.POINTER(C.c_int32), u32, d, d]
         L.or_inject.restype = C.c_int64
         L.or_inject.argtypes = [P]
         L.or_sort.argtypes = [P]
@@ -309,6 +311,22 @@ class Oracle:
         out = np.zeros((max(n, 1), 3), dtype=np.uint32)
         lib().or_get_log(self._h, out.ctypes.data_as(C.POINTER(C.c_uint32)))
         return out[:n]
+
+    def hits(self):
+        """Ions absorbed at the cathode since the last call (the log is emptied),
+        ordered by (step, pid): pid, species, step, xy (n x 2: where the path
+        crossed z = 0), v (n x 3: v^{n+1/2})."""
+        n = lib().or_get_hits(self._h, None, None, None, None, None)
+        m = max(n, 1)
+        pid = np.zeros(m, dtype=np.uint32)
+        sp = np.zeros(m, dtype=np.int32)
+        step = np.zeros(m, dtype=np.uint32)
+        xy = np.zeros((m, 2))
+        v = np.zeros((m, 3))
+        lib().or_get_hits(self._h, pid.ctypes.data_as(C.POINTER(C.c_uint32)), sp.ctypes.data_as(C.POINTER(C.c_int32)),
+                          step.ctypes.data_as(C.POINTER(C.c_uint32)), _dp(xy), _dp(v))
+        o = np.lexsort((pid[:n], step[:n]))
+        return {"pid": pid[:n][o], "species": sp[:n][o], "step": step[:n][o], "xy": xy[:n][o], "v": v[:n][o]}
 
     def gather(self, xyz):
         xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)

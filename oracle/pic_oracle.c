@@ -155,6 +155,14 @@ typedef struct {
 } or_moments_t;
 
 typedef struct {
+  uint32_t pid;
+  int32_t sp;
+  uint32_t step;      /* the step in which the ion crossed z = 0 */
+  double x, y;        /* where the straight path x^n -> x^{n+1} crosses z = 0, wrapped */
+  double vx, vy, vz;  /* v^{n+1/2} */
+} or_hit_t;
+
+typedef struct {
   or_cfg_t c;
   or_species_t sp[OR_MAXSP];
   or_xsec_t xs[OR_MAXXS];
@@ -175,6 +183,11 @@ typedef struct {
   /* last ionization-event log: (primary pid, victim pid, secondary pid) */
   int64_t nlog;
   uint32_t* log;
+  /* ions absorbed at the cathode since the last or_get_hits: the surface
+   * coupling output (ions that bombard the cathode are handed to the surface
+   * model, Sec. 2 and Appendix A) */
+  int64_t nhit, hitcap;
+  or_hit_t* hit;
 } or_state_t;
 
 static void store_reserve(or_store_t* s, int64_t need) {
@@ -233,7 +246,7 @@ void or_destroy(or_state_t* s) {
   if (!s) return;
   for (int i = 0; i < OR_MAXSP; ++i) { store_free(&s->st[i]); free(s->ncount[i]); free(s->cell_start[i]); }
   for (int i = 0; i < s->nxs; ++i) { free(s->xs[i].E); free(s->xs[i].sig); }
-  free(s->rho); free(s->phi); free(s->log);
+  free(s->rho); free(s->phi); free(s->log); free(s->hit);
   free(s);
 }
 
@@ -302,6 +315,32 @@ void or_get_cell_start(const or_state_t* s, int sp, int64_t* out) { memcpy(out, 
 int64_t or_get_log(const or_state_t* s, uint32_t* out) {
   if (out) memcpy(out, s->log, (size_t)s->nlog * 3 * sizeof(uint32_t));
   return s->nlog;
+}
+
+/* Cathode hits of ions since the last call, in the order they were found.
+ * With pid == NULL only the count is returned; otherwise every field is copied
+ * (xy: 2 per hit, v: 3 per hit) and the log is emptied. */
+int64_t or_get_hits(or_state_t* s, uint32_t* pid, int32_t* sp, uint32_t* step, double* xy, double* v) {
+  const int64_t n = s->nhit;
+  if (!pid) return n;
+  for (int64_t i = 0; i < n; ++i) {
+    const or_hit_t* h = &s->hit[i];
+    pid[i] = h->pid; sp[i] = h->sp; step[i] = h->step;
+    xy[2 * i] = h->x; xy[2 * i + 1] = h->y;
+    v[3 * i] = h->vx; v[3 * i + 1] = h->vy; v[3 * i + 2] = h->vz;
+  }
+  s->nhit = 0;
+  return n;
+}
+
+static void log_hit(or_state_t* s, uint32_t pid, int sp, double x, double y, double vx, double vy, double vz) {
+  if (s->nhit == s->hitcap) {
+    s->hitcap = s->hitcap ? 2 * s->hitcap : 1024;
+    s->hit = realloc(s->hit, (size_t)s->hitcap * sizeof(or_hit_t));
+  }
+  or_hit_t* h = &s->hit[s->nhit++];
+  h->pid = pid; h->sp = sp; h->step = s->step;
+  h->x = x; h->y = y; h->vx = vx; h->vy = vy; h->vz = vz;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -746,7 +785,15 @@ void or_push_collide_resolve(or_state_t* s) {
       if (zn < 0.0 || zn >= Lz) {
         dead[sp][p] = 1;
         double ke = 0.5 * S->m * S->w * v2;
-        if (zn < 0.0) { s->mom.abs_cathode[sp] += 1; s->mom.abs_energy_cathode[sp] += ke; q_cath += S->q * S->w; }
+        if (zn < 0.0) {
+          s->mom.abs_cathode[sp] += 1; s->mom.abs_energy_cathode[sp] += ke; q_cath += S->q * S->w;
+          if (S->role == OR_ION) {
+            /* z^n >= 0 > z^{n+1}, so vz < 0: the path meets z = 0 at x^n - v z^n / vz */
+            const double f = t->z[p] / t->vz[p];
+            log_hit(s, t->pid[p], sp, wrap(t->x[p] - t->vx[p] * f, Lx), wrap(t->y[p] - t->vy[p] * f, Ly),
+                    t->vx[p], t->vy[p], t->vz[p]);
+          }
+        }
         else { s->mom.abs_anode[sp] += 1; s->mom.abs_energy_anode[sp] += ke; q_anode += S->q * S->w; }
         continue;
       }

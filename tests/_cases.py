@@ -54,3 +54,28 @@ def ionization_cells_case(seed=3, sigma_ion=1e-17, sigma_el=1e-19, E_eV=100.0, c
     vi = np.zeros_like(xi)
     wl.preload = [(xe, ve), (xn, vn), (xi, vi)]
     return wl
+
+
+def cathode_hits_case(n_ions=40, n_other=20, kmax=12, seed=11):
+    """Field-free box (both electrodes at 0 V, weight 1e-30) with ions heading
+    for the cathode: ion i starts at z0 = (k_i + 1/2) |vz| dt, k_i in [0, kmax),
+    with a large transverse speed, some of them next to the x = Lx face so that
+    the crossing point wraps. Electrons and neutrals head for the cathode too.
+    Returns the workload and the per-ion k_i."""
+    wl = bare(nx=4, ny=4, nz=16, h=5e-9, dt=1e-16)
+    rng = np.random.default_rng(seed)
+    Lx, Ly, _ = wl.L
+    k = rng.integers(0, kmax, n_ions)
+    vz = -rng.uniform(2e4, 2e5, n_ions)
+    vxy = rng.uniform(-2e6, 2e6, (n_ions, 2))
+    x0 = rng.random((n_ions, 2)) * np.array([Lx, Ly])
+    x0[: n_ions // 4, 0] = Lx - 1e-10
+    vxy[: n_ions // 4, 0] = 2e6
+    z0 = (k + 0.5) * (-vz) * wl.dt
+    xi = np.column_stack([x0, z0])
+    vi = np.column_stack([vxy, vz])
+    xo = np.column_stack([rng.random((n_other, 2)) * np.array([Lx, Ly]), rng.uniform(1e-12, 2e-11, n_other)])
+    ve = np.column_stack([np.zeros((n_other, 2)), -rng.uniform(1e5, 1e6, n_other)])
+    vn = np.column_stack([np.zeros((n_other, 2)), -rng.uniform(2e5, 1e6, n_other)])
+    wl.preload = [(xo, ve), (xo.copy(), vn), (xi, vi)]
+    return wl, k
