@@ -239,6 +239,34 @@ pic_status pic_philox(pic_handle* h, int64_t n, const uint32_t ctr[4], const uin
  * particles. 0 restores the normal mode. */
 pic_status pic_set_mcc_background(pic_handle* h, int32_t inst, double density_m3);
 
+/* ---- surface coupling: ions that bombard the cathode ----------------------
+ * In the paper's coupled model ions that reach the cathode are handed to the
+ * atomistic surface model, where they heat or sputter it (Sec. 2, and the
+ * particle transfer of Appendix A). These two calls export them for such a
+ * model: every superparticle of an ion species (PIC_ION) absorbed at the
+ * cathode (z^{n+1} < 0, step a7) is logged with its pid, species, the step in
+ * which it crossed, the point where its straight path from x^n to x^{n+1}
+ * meets the plane z = 0 (x and y wrapped into the box), and v^{n+1/2}.
+ *
+ * pic_set_hit_log: log from the next step on, keeping at most `capacity` hits
+ * between two reads (device memory allocated here; 0 switches the log off and
+ * frees it). Synchronises the instance. PIC_EINVAL for capacity < 0,
+ * PIC_ENOMEM if the log cannot be allocated (the log is then off). */
+pic_status pic_set_hit_log(pic_handle* h, int32_t inst, int64_t capacity);
+
+/* pic_get_hits: the hits logged since the previous call (or since the log was
+ * switched on), ordered by (step, pid), after which the log is empty.
+ * Synchronises the instance. Caller-owned outputs with room for `cap` hits:
+ * pid[cap], species[cap], step[cap], x[3 cap] (crossing point, z = 0),
+ * v[3 cap] (m/s), ke_eV[cap] (1/2 m |v|^2 of one physical ion, in eV).
+ * *n receives the number of hits returned, *lost the number beyond the log's
+ * capacity since the previous read (those are not kept; which hits are kept
+ * when the capacity overflows is not specified). PIC_EINVAL if no log is on,
+ * if an output pointer is null, or if more than `cap` hits are waiting (then
+ * nothing is copied and the log is kept). */
+pic_status pic_get_hits(pic_handle* h, int32_t inst, int64_t cap, int64_t* n, int64_t* lost, uint32_t* pid,
+                        int32_t* species, int64_t* step, double* x, double* v, double* ke_eV);
+
 /* Cell sort interval of one instance from now on (a2: the store is sorted when
  * the step index is a multiple of it; 0 never sorts). The sort only reorders
  * particles, so results do not depend on it beyond rounding; it trades the

@@ -83,7 +83,8 @@ EXPORTED = ["pic_create", "pic_inject", "pic_inject_particles", "pic_step", "pic
             "pic_last_error", "pic_get_count", "pic_get_particles", "pic_get_field", "pic_set_phi", "pic_solve",
             "pic_sort_now", "pic_get_cell_start", "pic_get_ionization_log", "pic_philox",
             "pic_set_mcc_background", "pic_version", "pic_set_profiling", "pic_get_phase_times",
-            "pic_launch_count", "pic_kernel_count", "pic_poisson_solve_static", "pic_set_sort_interval"]
+            "pic_launch_count", "pic_kernel_count", "pic_poisson_solve_static", "pic_set_sort_interval",
+            "pic_set_hit_log", "pic_get_hits"]
 
 _lib = None
 
@@ -127,6 +128,9 @@ def load_library(path: str = LIB_PATH):
         "pic_philox": ([P, C.c_int64, u32, u32, u32], st),
         "pic_set_mcc_background": ([P, C.c_int32, C.c_double], st),
         "pic_set_sort_interval": ([P, C.c_int32, C.c_int32], st),
+        "pic_set_hit_log": ([P, C.c_int32, C.c_int64], st),
+        "pic_get_hits": ([P, C.c_int32, C.c_int64, i64, i64, C.POINTER(C.c_uint32), C.POINTER(C.c_int32), i64,
+                          d, d, d], st),
         "pic_version": ([], C.c_char_p),
         "pic_set_profiling": ([P, C.c_int32], st),
         "pic_get_phase_times": ([P, C.c_int32, d, i64], st),
@@ -141,6 +145,10 @@ def load_library(path: str = LIB_PATH):
         f.restype = res
     _lib = L
     return L
+
+
+def _i64p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int64))
 
 
 def _dp(a):
@@ -276,6 +284,29 @@ def pic_philox(h, n, ctr, key):
 
 def pic_set_mcc_background(h, inst, density):
     return _check(h, load_library().pic_set_mcc_background(h, inst, density))
+
+
+def pic_set_hit_log(h, inst, capacity):
+    return _check(h, load_library().pic_set_hit_log(h, inst, capacity))
+
+
+def pic_get_hits(h, inst=0, cap=1 << 16):
+    """Ions absorbed at the cathode since the last read, ordered by (step, pid):
+    a dict of pid, species, step, x (n x 3, z = 0), v (n x 3), ke_eV, and lost."""
+    n, lost = C.c_int64(), C.c_int64()
+    pid = np.zeros(max(cap, 1), dtype=np.uint32)
+    sp = np.zeros(max(cap, 1), dtype=np.int32)
+    step = np.zeros(max(cap, 1), dtype=np.int64)
+    x = np.zeros((max(cap, 1), 3))
+    v = np.zeros((max(cap, 1), 3))
+    ke = np.zeros(max(cap, 1))
+    _check(h, load_library().pic_get_hits(h, inst, cap, C.byref(n), C.byref(lost),
+                                          pid.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                          sp.ctypes.data_as(C.POINTER(C.c_int32)), _i64p(step), _dp(x), _dp(v),
+                                          _dp(ke)))
+    k = n.value
+    return {"pid": pid[:k].copy(), "species": sp[:k].copy(), "step": step[:k].copy(), "x": x[:k].copy(),
+            "v": v[:k].copy(), "ke_eV": ke[:k].copy(), "lost": lost.value}
 
 
 def pic_set_sort_interval(h, inst, interval):

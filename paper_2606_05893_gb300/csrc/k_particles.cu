@@ -285,6 +285,22 @@ __device__ __forceinline__ void next_deposit(const PushArgs<Store64>& a, const P
   if (NEUTRAL) atomicAdd(&a.nd.ncount[a.species][cell_now(a.g, p)], 1);
 }
 
+// One ion absorbed at the cathode into the hit log (rare: out of the push's
+// main path; scalar arguments, so the particle stays in registers).
+__device__ __noinline__ void log_cathode_hit(const HitLog& h, uint32_t pid, int species, uint32_t step, double xc,
+                                             double yc, double vx, double vy, double vz) {
+  const unsigned long long k = atomicAdd(h.n, 1ull);
+  if (k >= (unsigned long long)h.cap) return;
+  h.pid[k] = pid;
+  h.species[k] = species;
+  h.step[k] = step;
+  h.xy[2 * k] = xc;
+  h.xy[2 * k + 1] = yc;
+  h.v[3 * k] = vx;
+  h.v[3 * k + 1] = vy;
+  h.v[3 * k + 2] = vz;
+}
+
 template <class S, bool CHARGED, bool MCC, bool NEUTRAL>
 __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(PushArgs<S> a) {
   // Each thread advances kIlp particles per round (their loads are issued
@@ -340,6 +356,12 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
         const int b = side < 0 ? 0 : 1;
         s_tn[b][tx] += 1u;
         s_tv2[b][tx] += p[u].v2();
+        if (side < 0 && a.hits.n) {
+          double xc, yc;
+          p[u].cathode_point(g, xc, yc);
+          const double3 v = p[u].vel();
+          log_cathode_hit(a.hits, p[u].pid, a.species, step, xc, yc, v.x, v.y, v.z);
+        }
         continue;
       }
       keep[u] = true;

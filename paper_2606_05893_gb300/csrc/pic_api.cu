@@ -178,6 +178,8 @@ struct Instance {
   SortBuffers csort{};
   int32_t* cell_count = nullptr;
   long long* cell_start[kMaxSpecies]{};
+  // surface-coupling output: ions absorbed at the cathode (cap 0: off)
+  HitLog hits{};
   SegCtl* seg_ctl = nullptr;    // bucket path state (device)
   SegCtl* seg_host = nullptr;   // pinned mirror
   int32_t* seg_big = nullptr;   // buckets for the block-wide sort (ncell + 1)
@@ -252,6 +254,8 @@ int bits_for(unsigned long long v) {
   return b;
 }
 
+void free_hit_log(Instance* I);
+
 void free_instance(Instance* I) {
   if (!I) return;
   if (I->own_stream && I->stream) cudaStreamDestroy(I->stream);
@@ -304,6 +308,7 @@ void free_instance(Instance* I) {
   cudaFree(I->csort.hist);
   cudaFree(I->csort.digit_tot);
   cudaFree(I->csort.small_done);
+  free_hit_log(I);
   cudaFree(I->cell_count);
   cudaFree(I->seg_ctl);
   cudaFree(I->seg_big);
@@ -844,6 +849,7 @@ pic_status step_instance(pic_handle* h, Instance* I) {
       a.cand_cap = I->cand_cap;
       a.cand_head = I->cand_head;
       a.nd = next_deposit_of(I, true);
+      if (I->species[s].role == PIC_ION) a.hits = I->hits;
       const bool mcc = a.mc.nch > 0;
       if (neutral && I->ion_ch < 0) {
         a.ev_head = nullptr;
@@ -933,6 +939,17 @@ pic_status download_carries(pic_handle* h, Instance* I) {
   CK(h, cudaMemcpy(&P, I->plan, sizeof(InjectPlan), cudaMemcpyDeviceToHost));
   for (int q = 0; q < P.nsrc && q < (int)I->sources.size(); ++q) I->sources[q].acc = P.acc[q];
   return PIC_OK;
+}
+
+void free_hit_log(Instance* I) {
+  HitLog& L = I->hits;
+  cudaFree(L.n);
+  cudaFree(L.pid);
+  cudaFree(L.species);
+  cudaFree(L.step);
+  cudaFree(L.xy);
+  cudaFree(L.v);
+  L = HitLog{};
 }
 
 void drop_step_graphs(Instance* I) {
@@ -1546,6 +1563,77 @@ pic_status pic_set_sort_interval(pic_handle* h, int32_t inst, int32_t interval) 
   if (st != PIC_OK) return st;
   if (interval < 0) return fail(h, PIC_EINVAL, "sort interval must be >= 0");
   h->inst[inst]->cfg.sort_interval = interval;
+  return PIC_OK;
+}
+
+pic_status pic_set_hit_log(pic_handle* h, int32_t inst, int64_t capacity) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  if (capacity < 0) return fail(h, PIC_EINVAL, "hit log capacity must be >= 0");
+  Instance* I = h->inst[inst];
+  CK(h, cudaStreamSynchronize(I->stream));
+  free_hit_log(I);
+  drop_step_graphs(I);  // the push arguments the recorded steps hold change
+  if (capacity == 0) return PIC_OK;
+  HitLog& L = I->hits;
+  L.cap = capacity;
+  if (dalloc(&L.n, 1) != cudaSuccess || dalloc(&L.pid, capacity) != cudaSuccess ||
+      dalloc(&L.species, capacity) != cudaSuccess || dalloc(&L.step, capacity) != cudaSuccess ||
+      dalloc(&L.xy, 2 * capacity) != cudaSuccess || dalloc(&L.v, 3 * capacity) != cudaSuccess) {
+    cudaGetLastError();
+    free_hit_log(I);
+    return fail(h, PIC_ENOMEM, "hit log of %lld entries", (long long)capacity);
+  }
+  CK(h, cudaMemset(L.n, 0, sizeof(unsigned long long)));
+  return PIC_OK;
+}
+
+pic_status pic_get_hits(pic_handle* h, int32_t inst, int64_t cap, int64_t* n, int64_t* lost, uint32_t* pid,
+                        int32_t* species, int64_t* step, double* x, double* v, double* ke_eV) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  Instance* I = h->inst[inst];
+  if (!I->hits.n) return fail(h, PIC_EINVAL, "instance %d: no hit log (pic_set_hit_log)", inst);
+  if (!n || !lost || cap < 0 || (cap > 0 && (!pid || !species || !step || !x || !v || !ke_eV)))
+    return fail(h, PIC_EINVAL, "pic_get_hits: null output or negative cap");
+  HitLog& L = I->hits;
+  unsigned long long total = 0;
+  CK(h, cudaStreamSynchronize(I->stream));
+  CK(h, cudaMemcpy(&total, L.n, sizeof(total), cudaMemcpyDeviceToHost));
+  const long long k = (long long)std::min<unsigned long long>(total, (unsigned long long)L.cap);
+  if (k > cap) return fail(h, PIC_EINVAL, "%lld hits logged, room for %lld (nothing copied)", k, (long long)cap);
+  std::vector<uint32_t> hp(k), hstep(k);
+  std::vector<int32_t> hs(k);
+  std::vector<double> hxy(2 * k), hv(3 * k);
+  if (k > 0) {
+    CK(h, cudaMemcpy(hp.data(), L.pid, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(hs.data(), L.species, sizeof(int32_t) * k, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(hstep.data(), L.step, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(hxy.data(), L.xy, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(hv.data(), L.v, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost));
+  }
+  std::vector<long long> o(k);
+  for (long long i = 0; i < k; ++i) o[i] = i;
+  std::sort(o.begin(), o.end(), [&](long long a, long long b) {
+    return hstep[a] != hstep[b] ? hstep[a] < hstep[b] : hp[a] < hp[b];
+  });
+  for (long long q = 0; q < k; ++q) {
+    const long long i = o[q];
+    pid[q] = hp[i];
+    species[q] = hs[i];
+    step[q] = hstep[i];
+    x[3 * q] = hxy[2 * i];
+    x[3 * q + 1] = hxy[2 * i + 1];
+    x[3 * q + 2] = 0.0;
+    const double vx = hv[3 * i], vy = hv[3 * i + 1], vz = hv[3 * i + 2];
+    v[3 * q] = vx;
+    v[3 * q + 1] = vy;
+    v[3 * q + 2] = vz;
+    ke_eV[q] = 0.5 * I->species[hs[i]].mass_kg * (vx * vx + vy * vy + vz * vz) / kQe;
+  }
+  *n = k;
+  *lost = (long long)(total - (unsigned long long)k);
+  CK(h, cudaMemset(L.n, 0, sizeof(unsigned long long)));
   return PIC_OK;
 }
 

@@ -134,6 +134,14 @@ struct Particle64 {
     z = zn;
     return 0;
   }
+  // where the straight path x^n -> x^{n+1} crosses z = 0 (after drift returned
+  // -1, which leaves x^n in place): x^n - v z^n / vz
+  __device__ __forceinline__ void cathode_point(const Grid& g, double& xc, double& yc) const {
+    const double f = z / vz;
+    xc = wrap_coord(x - vx * f, g.Lx, g.inv_Lx);
+    yc = wrap_coord(y - vy * f, g.Ly, g.inv_Ly);
+  }
+  __device__ __forceinline__ double3 vel() const { return make_double3(vx, vy, vz); }
   __device__ __forceinline__ double v2() const { return vx * vx + vy * vy + vz * vz; }
   __device__ __forceinline__ float v2f() const { return (float)v2(); }
   // isotropic elastic scattering at constant speed (FP64, as the oracle):
@@ -219,13 +227,30 @@ struct ParticleMx {
     int i, j, k;
     cell_ijk(g, cell, i, j, k);
     k += dk;
-    if (k < 0) return -1;
+    if (k < 0) {
+      // absorbed at the cathode: keep x^{n+1} for the hit log (cell of the
+      // wrapped column in plane 0, oz = z^{n+1} / h < 0)
+      i = fwrap(i + di, g.fdx);
+      j = fwrap(j + dj, g.fdy);
+      cell = j * g.nx + i;
+      oz += (float)k;
+      return -1;
+    }
     if (k >= g.nz) return 1;
     i = fwrap(i + di, g.fdx);
     j = fwrap(j + dj, g.fdy);
     cell = (k * g.ny + j) * g.nx + i;
     return 0;
   }
+  // where the straight path x^n -> x^{n+1} crosses z = 0 (after drift returned -1)
+  __device__ __forceinline__ void cathode_point(const Grid& g, double& xc, double& yc) const {
+    int i, j, k;
+    cell_ijk(g, cell, i, j, k);
+    const double f = (double)oz * g.h / (double)vz;  // z^{n+1} / vz, z^{n+1} < 0 and vz < 0
+    xc = wrap_coord(((double)i + (double)ox) * g.h - (double)vx * f, g.Lx, g.inv_Lx);
+    yc = wrap_coord(((double)j + (double)oy) * g.h - (double)vy * f, g.Ly, g.inv_Ly);
+  }
+  __device__ __forceinline__ double3 vel() const { return make_double3(vx, vy, vz); }
   __device__ __forceinline__ double v2() const {
     return (double)vx * (double)vx + (double)vy * (double)vy + (double)vz * (double)vz;
   }
@@ -514,6 +539,18 @@ struct InjectCommit {
   const InjectPlan* plan;
 };
 
+// Surface-coupling output: ions absorbed at the cathode (n == nullptr: not
+// logged for this species). n counts every hit; the first cap are stored.
+struct HitLog {
+  unsigned long long* n;
+  long long cap;
+  uint32_t* pid;
+  int32_t* species;
+  uint32_t* step;
+  double* xy;  // 2 per hit: crossing point of z = 0
+  double* v;   // 3 per hit: v^{n+1/2}
+};
+
 template <class S>
 struct PushArgs {
   Grid g;
@@ -534,6 +571,7 @@ struct PushArgs {
   int cand_cap;
   int32_t* cand_head;
   NextDeposit nd;
+  HitLog hits;
 };
 
 struct ResolveArgs {
