@@ -181,20 +181,31 @@ void launch_rhs(const Grid& g, const double* rho64, const float* rho32, double* 
 // without the folded Dirichlet terms (the solver keeps phi relative to the
 // vacuum potential). From an FP64 density (a caller's rho) the product is FP64,
 // rounded once.
+// The unknowns are the nodes of planes 1..nz-1, one contiguous range of the
+// node array, so this is a flat pass: four values per thread (16-byte loads)
+// where the plane size keeps the range 16-byte aligned.
 __global__ void __launch_bounds__(256) k_rhs_f32(Grid g, const double* __restrict__ rho64,
                                                  const float* __restrict__ rho32, float* __restrict__ f) {
   const double s = g.h * g.h / kEps0;
   const float s32 = (float)s;
-  const int i = blockIdx.x * 32 + threadIdx.x;
-  if (i >= g.nx) return;
-  for (int j = blockIdx.y * 8 + threadIdx.y; j < g.ny; j += gridDim.y * 8) {
-    const long long u = (long long)blockIdx.z * g.nplane + (long long)j * g.nx + i;
-    const long long node = u + g.nplane;
-    f[u] = rho32 ? s32 * rho32[node] : (float)(s * rho64[node]);
+  const long long nu = (long long)(g.nz - 1) * g.nplane;
+  const float* r32 = rho32 ? rho32 + g.nplane : nullptr;
+  const double* r64 = rho64 ? rho64 + g.nplane : nullptr;
+  long long u0 = 0;
+  if (r32 && (g.nplane & 3) == 0) {
+    const long long n4 = nu >> 2;
+    const float4* s4 = reinterpret_cast<const float4*>(r32);
+    float4* f4 = reinterpret_cast<float4*>(f);
+    for (long long q = gtid(); q < n4; q += gstride()) {
+      const float4 v = s4[q];
+      f4[q] = make_float4(s32 * v.x, s32 * v.y, s32 * v.z, s32 * v.w);
+    }
+    u0 = n4 << 2;
   }
+  for (long long u = u0 + gtid(); u < nu; u += gstride()) f[u] = r32 ? s32 * r32[u] : (float)(s * r64[u]);
 }
 void launch_rhs_f32(const Grid& g, const double* rho64, const float* rho32, float* f, cudaStream_t st) {
-  PIC_LAUNCH(grid3(g, g.nz - 1), kBlk3, 0, st, k_rhs_f32)(g, rho64, rho32, f);
+  PIC_LAUNCH(grid_for((long long)(g.nz - 1) * g.nplane / 4 + 1), kBlock, 0, st, k_rhs_f32)(g, rho64, rho32, f);
 }
 
 __global__ void k_phi_planes(Grid g, double* phi) {

@@ -170,6 +170,14 @@ __device__ int mcc_decide32(const McArgs& m, long long cell, float v2f, float U3
 // ---------------------------------------------------------------------------
 // a1: injection
 // ---------------------------------------------------------------------------
+// -2 log U in FP32 for the Box-Muller radius, accurate to about 1e-7 relative
+// over all of (0, 1): U from the 53-bit draw, and near 1 through log1p of the
+// exactly formed 1 - U (log of a rounded U would lose 1 - U there)
+__device__ __forceinline__ float m2log_u(uint32_t a, uint32_t b) {
+  const double u = u01_64(a, b);
+  return u < 0.5 ? -2.f * logf((float)u) : -2.f * log1pf(-(float)(1.0 - u));
+}
+
 template <class S>
 __global__ void k_inject(InjectArgs<S> a) {
   const InjectPlan& P = *a.plan;
@@ -192,16 +200,41 @@ __global__ void k_inject(InjectArgs<S> a) {
     const uint4 d1 = draw(a.key, pid, step, TAG_INJ_VXY);
     const uint4 d2 = draw(a.key, pid, step, TAG_INJ_VZ);
     const uint4 d3 = draw(a.key, pid, step, TAG_INJ_Z);
-    const double r = s.R * sqrt(u01_64(dp.x, dp.y));
-    const double th = 2.0 * kPi * u01_64(dp.z, dp.w);
-    const double x = wrap_coord(s.cx + r * cos(th), a.g.Lx, a.g.inv_Lx);
-    const double y = wrap_coord(s.cy + r * sin(th), a.g.Ly, a.g.inv_Ly);
-    const double rad1 = sqrt(-2.0 * log(u01_64(d1.x, d1.y)));
-    const double ph1 = 2.0 * kPi * u01_64(d1.z, d1.w);
-    const double n1 = rad1 * cos(ph1), n2 = rad1 * sin(ph1);
-    const double n3 = sqrt(-2.0 * log(u01_64(d2.x, d2.y))) * cos(2.0 * kPi * u01_64(d2.z, d2.w));
-    const double vx = s.sig * n1, vy = s.sig * n2, vz = s.sig * fabs(n3);
-    const double z = u01_64(d3.x, d3.y) * vz * a.g.dt;
+    double x, y, z, vx, vy, vz;
+    if constexpr (std::is_same<S, StoreMx>::value) {
+      // the FP32 store takes FP32 velocity samples (FP64 transcendentals run on
+      // the narrow FP64 pipe): the same 53-bit uniforms rounded to FP32
+      // (relative error 2^-24), the same formulas in FP32. The position stays
+      // FP64: the source radius spans many cells, and an FP32 r cos(theta)
+      // would be far coarser than the store's FP32 offset within a cell.
+      double sr, cr;
+      float s1, c1;
+      sincospi(2.0 * u01_64(dp.z, dp.w), &sr, &cr);
+      const double r = s.R * sqrt(u01_64(dp.x, dp.y));
+      x = wrap_coord(s.cx + r * cr, a.g.Lx, a.g.inv_Lx);
+      y = wrap_coord(s.cy + r * sr, a.g.Ly, a.g.inv_Ly);
+      sincospif(2.f * (float)u01_64(d1.z, d1.w), &s1, &c1);
+      const float rad1 = sqrtf(m2log_u(d1.x, d1.y));
+      const float n3 = sqrtf(m2log_u(d2.x, d2.y)) * cospif(2.f * (float)u01_64(d2.z, d2.w));
+      const float sig = (float)s.sig;
+      vx = (double)(sig * (rad1 * c1));
+      vy = (double)(sig * (rad1 * s1));
+      vz = (double)(sig * fabsf(n3));
+      z = (double)((float)u01_64(d3.x, d3.y) * (float)vz * (float)a.g.dt);
+    } else {
+      const double r = s.R * sqrt(u01_64(dp.x, dp.y));
+      const double th = 2.0 * kPi * u01_64(dp.z, dp.w);
+      x = wrap_coord(s.cx + r * cos(th), a.g.Lx, a.g.inv_Lx);
+      y = wrap_coord(s.cy + r * sin(th), a.g.Ly, a.g.inv_Ly);
+      const double rad1 = sqrt(-2.0 * log(u01_64(d1.x, d1.y)));
+      const double ph1 = 2.0 * kPi * u01_64(d1.z, d1.w);
+      const double n1 = rad1 * cos(ph1), n2 = rad1 * sin(ph1);
+      const double n3 = sqrt(-2.0 * log(u01_64(d2.x, d2.y))) * cos(2.0 * kPi * u01_64(d2.z, d2.w));
+      vx = s.sig * n1;
+      vy = s.sig * n2;
+      vz = s.sig * fabs(n3);
+      z = u01_64(d3.x, d3.y) * vz * a.g.dt;
+    }
     store_write(a.st[s.species], a.g, slot, x, y, z, vx, vy, vz, pid);
     if (a.nd.on) {  // the next step's deposit is being accumulated: add this particle
       const auto p = store_read(a.st[s.species], a.g, slot);
