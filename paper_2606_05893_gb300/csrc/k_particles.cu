@@ -483,6 +483,7 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
           cd.slot = (uint32_t)slot;
           cd.next = atomicExch(&a.cand_head[cell_n[u]], (int)c);
           a.cand[c] = cd;
+          a.cand_cell[c] = (uint32_t)cell_n[u];
         } else {
           atomicOr(&a.cnt->error, ERR_EVENTS);
         }
@@ -542,38 +543,93 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
 // a9: ionization resolve
 // ---------------------------------------------------------------------------
 // Rank of each event among the events of its cell by primary pid, then its
-// victim: the rank-th smallest (key, pid) candidate of that cell.
-__global__ void k_resolve_rank(ResolveArgs a) {
+// victim: the rank-th smallest (key, pid) candidate of that cell. One warp per
+// event: it scans the flat candidate array (coalesced, no chain of dependent
+// loads) and gathers its cell's keys into shared memory, where each key's rank
+// is counted; a cell with more than kRankCand candidates is searched along its
+// linked list by repeated minimum selection instead. Keys are unique (they
+// carry the pid), so both give the same victim.
+constexpr int kRankCand = 256;
+constexpr int kRankWarps = 8;
+__global__ void __launch_bounds__(kRankWarps * 32) k_resolve_rank(ResolveArgs a) {
+  __shared__ unsigned long long sk[kRankWarps][kRankCand];
+  __shared__ int si[kRankWarps][kRankCand];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned int ne = min(a.cnt->n_events, (unsigned int)a.ev_cap);
+  const unsigned int nc = min(a.cnt->n_cands, (unsigned int)a.cand_cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) a.cnt->ev_sort_n = ne;
-  for (long long e = gtid(); e < ne; e += gstride()) {
-    Event& ev = a.ev[e];
+  const unsigned lt = (1u << lane) - 1u;
+  for (long long e = (long long)blockIdx.x * kRankWarps + w; e < ne; e += (long long)gridDim.x * kRankWarps) {
+    const uint32_t cell = a.ev[e].cell, pid = a.ev[e].pid;
     int r = 0;
     int guard = 0;
-    for (int j = a.ev_head[ev.cell]; j >= 0 && guard < (1 << 22); j = a.ev[j].next, ++guard)
-      if (a.ev[j].pid < ev.pid) ++r;
-    // r-th smallest candidate key (0-based) by repeated minimum selection
-    unsigned long long prev = 0;
-    bool have_prev = false;
-    int victim = -1;
-    for (int s = 0; s <= r; ++s) {
-      unsigned long long best = ~0ull;
-      int bi = -1;
-      int g2 = 0;
-      for (int c = a.cand_head[ev.cell]; c >= 0 && g2 < (1 << 22); c = a.cand[c].next, ++g2) {
-        const unsigned long long k = a.cand[c].key;
-        if ((!have_prev || k > prev) && k < best) { best = k; bi = c; }
+    for (int j = a.ev_head[cell]; j >= 0 && guard < (1 << 22); j = a.ev[j].next, ++guard)
+      if (a.ev[j].pid < pid) ++r;
+    // this cell's candidates, four chunks of 32 per round (their loads overlap)
+    int m = 0;
+    for (unsigned base = 0; base < nc; base += 128) {
+      bool match[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const unsigned c = base + 32u * q + lane;
+        match[q] = c < nc && a.cand_cell[c] == cell;
       }
-      if (bi < 0) { victim = -1; break; }
-      prev = best;
-      have_prev = true;
-      victim = bi;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const unsigned bal = __ballot_sync(0xffffffffu, match[q]);
+        const int pos = m + __popc(bal & lt);
+        if (match[q] && pos < kRankCand) {
+          const unsigned c = base + 32u * q + lane;
+          sk[w][pos] = a.cand[c].key;
+          si[w][pos] = (int)c;
+        }
+        m += __popc(bal);
+      }
     }
-    ev.victim = victim;
-    // sort key for the apply order: successful events first, by primary pid
-    a.sort_keys[e] = ((unsigned long long)(victim < 0 ? 1 : 0) << 32) | ev.pid;
-    a.sort_vals[e] = (uint32_t)e;
-    if (victim >= 0) atomicAdd(&a.cnt->n_success, 1u);
+    __syncwarp();
+    int victim = -1;
+    if (m <= kRankCand) {
+      for (int q = lane; q < m; q += 32) {
+        const unsigned long long kq = sk[w][q];
+        int below = 0;
+        for (int t = 0; t < m; ++t) below += sk[w][t] < kq ? 1 : 0;
+        if (below == r) victim = si[w][q];
+      }
+      victim = __reduce_max_sync(0xffffffffu, victim);  // one lane at most found it
+    } else {
+      if (lane == 0) {
+        unsigned long long prev = 0;
+        bool have_prev = false;
+        for (int s = 0; s <= r; ++s) {
+          unsigned long long best = ~0ull;
+          int bi = -1;
+          int g2 = 0;
+          for (int c = a.cand_head[cell]; c >= 0 && g2 < (1 << 22); c = a.cand[c].next, ++g2) {
+            const unsigned long long k = a.cand[c].key;
+            if ((!have_prev || k > prev) && k < best) {
+              best = k;
+              bi = c;
+            }
+          }
+          if (bi < 0) {
+            victim = -1;
+            break;
+          }
+          prev = best;
+          have_prev = true;
+          victim = bi;
+        }
+      }
+      victim = __shfl_sync(0xffffffffu, victim, 0);
+    }
+    if (lane == 0) {
+      a.ev[e].victim = victim;
+      // sort key for the apply order: successful events first, by primary pid
+      a.sort_keys[e] = ((unsigned long long)(victim < 0 ? 1 : 0) << 32) | pid;
+      a.sort_vals[e] = (uint32_t)e;
+      if (victim >= 0) atomicAdd(&a.cnt->n_success, 1u);
+    }
+    __syncwarp();  // the slice of sk / si is reused by the next event
   }
 }
 
@@ -684,7 +740,9 @@ void launch_inject_plan(InjectPlan* plan, int nsp, cudaStream_t st) {
   PIC_LAUNCH(1, 32, 0, st, k_inject_plan)(plan, nsp);
 }
 
-void launch_resolve_rank(const ResolveArgs& a, int grid, cudaStream_t st) { PIC_LAUNCH(grid, 256, 0, st, k_resolve_rank)(a); }
+void launch_resolve_rank(const ResolveArgs& a, int grid, cudaStream_t st) {
+  PIC_LAUNCH(grid, kRankWarps * 32, 0, st, k_resolve_rank)(a);
+}
 void launch_resolve_cleanup(const ResolveArgs& a, int grid, cudaStream_t st) {
   PIC_LAUNCH(grid, 256, 0, st, k_resolve_cleanup)(a);
 }

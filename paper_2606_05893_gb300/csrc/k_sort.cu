@@ -134,13 +134,17 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(const unsigned lon
 // the stable one), writes it at its rank in the buffers the radix passes would
 // end in, and sets *done so that those passes return at once.
 constexpr int kSmallSort = 2048;
+// In a recorded graph the radix passes sit in a conditional IF node whose
+// condition this kernel sets (use_graph): they are launched only when needed.
 __global__ void __launch_bounds__(1024) k_small_sort(const unsigned long long* __restrict__ kin,
                                                      const uint32_t* __restrict__ vin,
                                                      unsigned long long* __restrict__ kout,
                                                      uint32_t* __restrict__ vout, const unsigned long long* n_dev,
-                                                     long long n_max, int* done) {
+                                                     long long n_max, int* done, cudaGraphConditionalHandle h_radix,
+                                                     int use_graph) {
   __shared__ unsigned long long sk[kSmallSort];
   const long long n = min((long long)*n_dev, n_max);
+  if (use_graph && threadIdx.x == 0) cudaGraphSetConditional(h_radix, n > kSmallSort ? 1u : 0u);
   if (n > kSmallSort) {
     if (threadIdx.x == 0) *done = 0;
     return;
@@ -160,17 +164,69 @@ __global__ void __launch_bounds__(1024) k_small_sort(const unsigned long long* _
   if (threadIdx.x == 0) *done = 1;
 }
 
+static int radix_passes(const SortBuffers& b, const unsigned long long* n_dev, int bit0, int bit1, cudaStream_t s,
+                        const int* skip);
+
+// When s is capturing (a step being recorded), the small path's kernel decides
+// through a conditional IF node whether the radix passes run at all.
+static cudaError_t radix_if_node(const SortBuffers& b, const unsigned long long* n_dev, int bit0, int bit1,
+                                 cudaStream_t s) {
+  cudaStreamCaptureStatus status;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &status, nullptr, &g, &deps, &edges, &ndeps);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  if ((e = cudaGraphConditionalHandleCreate(&h, g, 0u, cudaGraphCondAssignDefault))) return e;
+  PIC_LAUNCH(1, 1024, 0, s, k_small_sort)(b.ka, b.va, b.kb, b.vb, n_dev, b.n_max, b.small_done, h, 1);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = cudaStreamGetCaptureInfo(s, &status, nullptr, &g, &deps, &edges, &ndeps))) return e;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeIf;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, edges, ndeps, &np))) return e;
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(b.aux, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed))) return e;
+  radix_passes(b, n_dev, bit0, bit1, b.aux, nullptr);
+  cudaGraph_t tmp;
+  const cudaError_t e1 = cudaStreamEndCapture(b.aux, &tmp);
+  if ((e = cudaGetLastError()) || (e = e1)) return e;
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
 int radix_sort_pairs(const SortBuffers& b, const unsigned long long* n_dev, int bit0, int bit1, cudaStream_t s,
                      bool small_path) {
-  const int nblocks = (int)sort_blocks(b.n_max);
   const int passes = (bit1 - bit0 + 7) / 8;
   const int* skip = nullptr;
   // the small path writes where an odd number of passes ends (kb, vb); an even
   // number would end in the input buffers, which the ranking still reads
   if (small_path && (passes & 1)) {
-    PIC_LAUNCH(1, 1024, 0, s, k_small_sort)(b.ka, b.va, b.kb, b.vb, n_dev, b.n_max, b.small_done);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (b.aux && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive) {
+      if (radix_if_node(b, n_dev, bit0, bit1, s) != cudaSuccess) {
+        // a half-built node must not be replayed: synchronising a capturing
+        // stream is illegal and invalidates the capture, so the recording
+        // fails and the instance steps directly from then on
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+      }
+      return 1;
+    }
+    const cudaGraphConditionalHandle none = 0;
+    PIC_LAUNCH(1, 1024, 0, s, k_small_sort)(b.ka, b.va, b.kb, b.vb, n_dev, b.n_max, b.small_done, none, 0);
     skip = b.small_done;
   }
+  return radix_passes(b, n_dev, bit0, bit1, s, skip);
+}
+
+static int radix_passes(const SortBuffers& b, const unsigned long long* n_dev, int bit0, int bit1, cudaStream_t s,
+                        const int* skip) {
+  const int nblocks = (int)sort_blocks(b.n_max);
   int src = 0;
   for (int shift = bit0; shift < bit1; shift += 8) {
     const unsigned long long* kin = src ? b.kb : b.ka;

@@ -170,6 +170,7 @@ struct Instance {
   int ev_cap = 0, cand_cap = 0;
   Event* ev = nullptr;
   Cand* cand = nullptr;
+  uint32_t* cand_cell = nullptr;
   int32_t* ev_head = nullptr;
   int32_t* cand_head = nullptr;
   uint32_t* ion_log = nullptr;
@@ -291,6 +292,7 @@ void free_instance(Instance* I) {
   cudaFree(I->acc8);
   cudaFree(I->ev);
   cudaFree(I->cand);
+  cudaFree(I->cand_cell);
   cudaFree(I->ev_head);
   cudaFree(I->cand_head);
   cudaFree(I->ion_log);
@@ -301,6 +303,7 @@ void free_instance(Instance* I) {
   cudaFree(I->evsort.hist);
   cudaFree(I->evsort.digit_tot);
   cudaFree(I->evsort.small_done);
+  if (I->evsort.aux) cudaStreamDestroy(I->evsort.aux);
   cudaFree(I->csort.ka);
   cudaFree(I->csort.kb);
   cudaFree(I->csort.va);
@@ -308,6 +311,7 @@ void free_instance(Instance* I) {
   cudaFree(I->csort.hist);
   cudaFree(I->csort.digit_tot);
   cudaFree(I->csort.small_done);
+  if (I->csort.aux) cudaStreamDestroy(I->csort.aux);
   free_hit_log(I);
   cudaFree(I->cell_count);
   cudaFree(I->seg_ctl);
@@ -332,6 +336,7 @@ cudaError_t alloc_sort(SortBuffers& b, long long n_max) {
   if ((e = dalloc(&b.hist, sort_hist_entries(n_max)))) return e;
   if ((e = dalloc(&b.digit_tot, 256))) return e;
   if ((e = dalloc(&b.small_done, 1))) return e;
+  if ((e = cudaStreamCreateWithFlags(&b.aux, cudaStreamNonBlocking))) return e;
   return cudaSuccess;
 }
 
@@ -561,6 +566,7 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
     I->cand_cap = (int)std::min<long long>(std::max<long long>(ncap / 4, 16384), 1 << 26);
     CK(h, dalloc(&I->ev, I->ev_cap));
     CK(h, dalloc(&I->cand, I->cand_cap));
+    CK(h, dalloc(&I->cand_cell, I->cand_cap));
     CK(h, dalloc(&I->ev_head, g.ncell));
     CK(h, dalloc(&I->cand_head, g.ncell));
     CK(h, cudaMemset(I->ev_head, 0xFF, sizeof(int32_t) * g.ncell));
@@ -846,6 +852,7 @@ pic_status step_instance(pic_handle* h, Instance* I) {
       a.ev_cap = I->ev_cap;
       a.ev_head = I->ev_head;
       a.cand = I->cand;
+      a.cand_cell = I->cand_cell;
       a.cand_cap = I->cand_cap;
       a.cand_head = I->cand_head;
       a.nd = next_deposit_of(I, true);
@@ -871,6 +878,8 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     r.ev_cap = I->ev_cap;
     r.ev_head = I->ev_head;
     r.cand = I->cand;
+    r.cand_cell = I->cand_cell;
+    r.cand_cap = I->cand_cap;
     r.cand_head = I->cand_head;
     r.sort_keys = I->evsort.ka;
     r.sort_vals = I->evsort.va;

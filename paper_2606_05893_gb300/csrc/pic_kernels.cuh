@@ -568,6 +568,7 @@ struct PushArgs {
   int ev_cap;
   int32_t* ev_head;
   Cand* cand;
+  uint32_t* cand_cell;
   int cand_cap;
   int32_t* cand_head;
   NextDeposit nd;
@@ -580,6 +581,8 @@ struct ResolveArgs {
   int ev_cap;
   int32_t* ev_head;
   Cand* cand;
+  uint32_t* cand_cell;  // cell of each candidate (a flat array the rank kernel scans)
+  int cand_cap;
   int32_t* cand_head;
   unsigned long long* sort_keys;
   uint32_t* sort_vals;
@@ -693,6 +696,7 @@ struct SortBuffers {
   uint32_t* digit_tot; // 256
   int* small_done;     // set when the single-block path sorted the input
   long long n_max;
+  cudaStream_t aux;    // capture stream of the radix passes inside a recorded step (small path)
 };
 long long sort_hist_entries(long long n_max);
 int radix_sort_pairs(const SortBuffers& b, const unsigned long long* n_dev, int bit0, int bit1, cudaStream_t s,
