@@ -543,14 +543,58 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
 // a9: ionization resolve
 // ---------------------------------------------------------------------------
 // Rank of each event among the events of its cell by primary pid, then its
-// victim: the rank-th smallest (key, pid) candidate of that cell. One warp per
-// event: it scans the flat candidate array (coalesced, no chain of dependent
-// loads) and gathers its cell's keys into shared memory, where each key's rank
-// is counted; a cell with more than kRankCand candidates is searched along its
-// linked list by repeated minimum selection instead. Keys are unique (they
-// carry the pid), so both give the same victim.
+// victim: the rank-th smallest (key, pid) candidate of that cell, i.e. the
+// candidate with exactly that many smaller keys. Keys are unique (they carry
+// the pid), so the two searches below give the same victim.
+// Few events and candidates (events x candidates <= kScanWork, the usual step):
+// one warp per event scans the flat candidate array (coalesced, no chain of
+// dependent loads), gathers its cell's keys into shared memory and counts
+// ranks there; a cell with more than kRankCand candidates falls back to the
+// list walk. Otherwise one thread per event walks its cell's candidate list by
+// repeated minimum selection (the flat scan would cost events x candidates).
 constexpr int kRankCand = 256;
 constexpr int kRankWarps = 8;
+constexpr unsigned long long kScanWork = 1ull << 22;
+
+__device__ int victim_by_list(const ResolveArgs& a, uint32_t cell, int r) {
+  unsigned long long prev = 0;
+  bool have_prev = false;
+  int victim = -1;
+  for (int s = 0; s <= r; ++s) {
+    unsigned long long best = ~0ull;
+    int bi = -1;
+    int g2 = 0;
+    for (int c = a.cand_head[cell]; c >= 0 && g2 < (1 << 22); c = a.cand[c].next, ++g2) {
+      const unsigned long long k = a.cand[c].key;
+      if ((!have_prev || k > prev) && k < best) {
+        best = k;
+        bi = c;
+      }
+    }
+    if (bi < 0) return -1;
+    prev = best;
+    have_prev = true;
+    victim = bi;
+  }
+  return victim;
+}
+
+__device__ __forceinline__ int event_rank(const ResolveArgs& a, uint32_t cell, uint32_t pid) {
+  int r = 0;
+  int guard = 0;
+  for (int j = a.ev_head[cell]; j >= 0 && guard < (1 << 22); j = a.ev[j].next, ++guard)
+    if (a.ev[j].pid < pid) ++r;
+  return r;
+}
+
+__device__ __forceinline__ void finish_event(const ResolveArgs& a, long long e, uint32_t pid, int victim) {
+  a.ev[e].victim = victim;
+  // sort key for the apply order: successful events first, by primary pid
+  a.sort_keys[e] = ((unsigned long long)(victim < 0 ? 1 : 0) << 32) | pid;
+  a.sort_vals[e] = (uint32_t)e;
+  if (victim >= 0) atomicAdd(&a.cnt->n_success, 1u);
+}
+
 __global__ void __launch_bounds__(kRankWarps * 32) k_resolve_rank(ResolveArgs a) {
   __shared__ unsigned long long sk[kRankWarps][kRankCand];
   __shared__ int si[kRankWarps][kRankCand];
@@ -558,13 +602,17 @@ __global__ void __launch_bounds__(kRankWarps * 32) k_resolve_rank(ResolveArgs a)
   const unsigned int ne = min(a.cnt->n_events, (unsigned int)a.ev_cap);
   const unsigned int nc = min(a.cnt->n_cands, (unsigned int)a.cand_cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) a.cnt->ev_sort_n = ne;
+  if ((unsigned long long)ne * nc > kScanWork) {
+    for (long long e = gtid(); e < ne; e += gstride()) {
+      const uint32_t cell = a.ev[e].cell, pid = a.ev[e].pid;
+      finish_event(a, e, pid, victim_by_list(a, cell, event_rank(a, cell, pid)));
+    }
+    return;
+  }
   const unsigned lt = (1u << lane) - 1u;
   for (long long e = (long long)blockIdx.x * kRankWarps + w; e < ne; e += (long long)gridDim.x * kRankWarps) {
     const uint32_t cell = a.ev[e].cell, pid = a.ev[e].pid;
-    int r = 0;
-    int guard = 0;
-    for (int j = a.ev_head[cell]; j >= 0 && guard < (1 << 22); j = a.ev[j].next, ++guard)
-      if (a.ev[j].pid < pid) ++r;
+    const int r = event_rank(a, cell, pid);
     // this cell's candidates, four chunks of 32 per round (their loads overlap)
     int m = 0;
     for (unsigned base = 0; base < nc; base += 128) {
@@ -597,38 +645,10 @@ __global__ void __launch_bounds__(kRankWarps * 32) k_resolve_rank(ResolveArgs a)
       }
       victim = __reduce_max_sync(0xffffffffu, victim);  // one lane at most found it
     } else {
-      if (lane == 0) {
-        unsigned long long prev = 0;
-        bool have_prev = false;
-        for (int s = 0; s <= r; ++s) {
-          unsigned long long best = ~0ull;
-          int bi = -1;
-          int g2 = 0;
-          for (int c = a.cand_head[cell]; c >= 0 && g2 < (1 << 22); c = a.cand[c].next, ++g2) {
-            const unsigned long long k = a.cand[c].key;
-            if ((!have_prev || k > prev) && k < best) {
-              best = k;
-              bi = c;
-            }
-          }
-          if (bi < 0) {
-            victim = -1;
-            break;
-          }
-          prev = best;
-          have_prev = true;
-          victim = bi;
-        }
-      }
+      if (lane == 0) victim = victim_by_list(a, cell, r);
       victim = __shfl_sync(0xffffffffu, victim, 0);
     }
-    if (lane == 0) {
-      a.ev[e].victim = victim;
-      // sort key for the apply order: successful events first, by primary pid
-      a.sort_keys[e] = ((unsigned long long)(victim < 0 ? 1 : 0) << 32) | pid;
-      a.sort_vals[e] = (uint32_t)e;
-      if (victim >= 0) atomicAdd(&a.cnt->n_success, 1u);
-    }
+    if (lane == 0) finish_event(a, e, pid, victim);
     __syncwarp();  // the slice of sk / si is reused by the next event
   }
 }
