@@ -33,6 +33,8 @@ import numpy as np  # noqa: E402
 METRIC = "PIC particle-steps/s (deposit+solve+push+MCC), 1 GB300, vs FP64 plain; HBM %"
 UNIT = "particle-steps/s"
 WORKLOADS = {
+    "c1": ("32x32x64 cells h=5nm, 1e4 macroparticles at weight 100 (60% e, 30% Cu, 10% Cu+), J=1e12 A/m2 "
+           "from a 10 nm disk, Cu flux 1e27, 3 kV, sort every 20", 10_000),
     "c2": ("128x128x256 cells h=2.5nm, 1e7 macroparticles (60% e, 30% Cu, 10% Cu+), J~U[5e11,5e12] A/m2, "
            "Cu flux 1e28, sort every 20", 10_000_000),
     "c3": ("256x256x512 cells h=1.25nm (same box), 5e7 macroparticles (60% e, 30% Cu, 10% Cu+), "
@@ -127,6 +129,8 @@ class ClockSampler:
 
 def make_workload(name, seed, n_preload):
     from paper_2606_05893_gb300 import workloads as W
+    if name == "c1":
+        return W.config_small(seed=42 + seed, n_preload=n_preload)
     if name == "c3":
         return W.config_mixed_large(seed=seed, n_preload=n_preload)
     return W.config_scale(seed=seed, n_preload=n_preload)
@@ -343,12 +347,19 @@ def reduce_over_ranks(r, dist, device):
                 e2e_s=red(r["e2e_s"], dist.ReduceOp.MAX), e2e_pushes=red(r["e2e_pushes"], dist.ReduceOp.SUM))
 
 
-def cpu_baseline(seconds_target=15.0, steps_max=6):
+def cpu_baseline(seconds_target=15.0, steps_max=6, workload="c2"):
     """The FP64 oracle as it stands, single thread, on a bounded sample of the workload:
-    the 64x64x128-cell sub-box (1/8 of the volume, same h and particle density)."""
+    the 64x64x128-cell sub-box (1/8 of the volume, same h and particle density), or
+    for the small 32x32x64 workload the workload itself."""
     import oracle
     from paper_2606_05893_gb300 import workloads as W
-    wl = W.config_scale(seed=0, n_preload=1_250_000, nx=64, ny=64, nz=128, h=2.5e-9)
+    if workload == "c1":
+        wl = make_workload("c1", 0, WORKLOADS["c1"][1])
+        steps_max = 1000
+        what = "the 32x32x64 workload itself (1e4 macroparticles)"
+    else:
+        wl = W.config_scale(seed=0, n_preload=1_250_000, nx=64, ny=64, nz=128, h=2.5e-9)
+        what = "the 64x64x128-cell sub-box (same h = 2.5 nm and particle density, 1.25e6 macroparticles)"
     o = oracle.Oracle(wl)
     t0 = time.perf_counter()
     pushes = 0
@@ -365,8 +376,7 @@ def cpu_baseline(seconds_target=15.0, steps_max=6):
     pushes += sum(m["injected"])
     o.close()
     return {"value": pushes / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} oracle steps of the 64x64x128-cell sub-box (same h = 2.5 nm and particle "
-                      f"density, 1.25e6 macroparticles), FP64, single thread, {dt:.1f} s"}
+            "sample": f"{steps} oracle steps of {what}, FP64, single thread, {dt:.1f} s"}
 
 
 def run_reference(args, rank, ws):
@@ -374,7 +384,11 @@ def run_reference(args, rank, ws):
         return 0
     import oracle
     from paper_2606_05893_gb300 import workloads as W
-    wl = W.config_scale(seed=args.seed, n_preload=1_250_000, nx=64, ny=64, nz=128, h=2.5e-9)
+    if args.workload == "c1":
+        wl, sample = make_workload("c1", args.seed, WORKLOADS["c1"][1]), "the whole workload"
+    else:
+        wl = W.config_scale(seed=args.seed, n_preload=1_250_000, nx=64, ny=64, nz=128, h=2.5e-9)
+        sample = "64x64x128-cell sub-box, 1.25e6 macroparticles"
     o = oracle.Oracle(wl)
     for _ in range(args.warmup):
         o.step()
@@ -393,7 +407,7 @@ def run_reference(args, rank, ws):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "64x64x128-cell sub-box, 1.25e6 macroparticles"},
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][0], "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} timed oracle steps of the 64x64x128-cell sub-box "
                                        f"(same h and particle density), started with {n_start} particles"},
@@ -410,7 +424,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
-                    help="c2: 128x128x256, 1e7 particles (the headline); c3: 256x256x512, 5e7 particles")
+                    help="c1: 32x32x64, 1e4 particles; c2: 128x128x256, 1e7 particles (the headline); "
+                         "c3: 256x256x512, 5e7 particles; c4: 48-instance ensemble")
     ap.add_argument("--n-preload", type=int, default=None, help="macroparticles preloaded (default per workload)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--profile-steps", type=int, default=20)
@@ -479,7 +494,7 @@ def main():
                               "phase_ms_per_step": {k: round(v[0] / max(f["prof_steps"], 1), 4) for k, v in fph.items()},
                               "push_kernel_ms": fpush_ms / max(fpush_n, 1), "clocks": f["clocks"]}
     if not args.no_cpu_baseline and ws >= 1:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(workload=args.workload)
     print(json.dumps(line), flush=True)
     return 0
 
