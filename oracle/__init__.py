@@ -55,6 +55,7 @@ class OrMoments(C.Structure):
         ("field_energy", C.c_double),
         ("charge_to_cathode_last", C.c_double), ("charge_to_anode_last", C.c_double),
         ("next_pid", C.c_uint32),
+        ("anode_V", C.c_double),
     ]
 
 
@@ -85,6 +86,7 @@ def lib():
         L.or_add_source.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]
         L.or_set_background_density.argtypes = [P, C.c_double]
         L.or_set_source.argtypes = [P, C.c_int, C.c_double, C.c_double]
+        L.or_set_circuit.argtypes = [P, C.c_double, C.c_double, C.c_double]
         L.or_load.argtypes = [P, C.c_int, C.c_int64, d, d]
         L.or_count.restype = C.c_int64
         L.or_count.argtypes = [P, C.c_int]
@@ -349,6 +351,10 @@ class Oracle:
     def next_pid(self):
         return int(lib().or_get_next_pid(self._h))
 
+    def set_circuit(self, R_ohm, C_farad, V0):
+        """External RC circuit on the anode (off unless R > 0 and C > 0)."""
+        lib().or_set_circuit(self._h, float(R_ohm), float(C_farad), float(V0))
+
     def set_source(self, q, flux, T_K):
         if lib().or_set_source(self._h, q, flux, T_K) != 0:
             raise ValueError("bad source")
@@ -379,4 +385,5 @@ class Oracle:
             "charge_to_cathode_last": m.charge_to_cathode_last,
             "charge_to_anode_last": m.charge_to_anode_last,
             "next_pid": m.next_pid,
+            "anode_V": m.anode_V,
         }

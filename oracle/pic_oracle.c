@@ -152,6 +152,7 @@ typedef struct {
   double field_energy;
   double charge_to_cathode_last, charge_to_anode_last; /* C absorbed in the last step */
   uint32_t next_pid;
+  double anode_V;  /* anode potential the next solve uses */
 } or_moments_t;
 
 typedef struct {
@@ -188,6 +189,14 @@ typedef struct {
    * model, Sec. 2 and Appendix A) */
   int64_t nhit, hitcap;
   or_hit_t* hit;
+  /* external circuit (the serial RC circuit between the electrodes, Sec. 2):
+   * a source V0 charges the anode through R, the gap holds capacitance C, and
+   * the charge the anode collects in a step flows onto it:
+   * V <- V + (dt (V0 - V) / R + Q_anode) / C once per step, after the push.
+   * Off (constant anode potential) unless R > 0 and C > 0. */
+  int circuit_on;
+  double circ_R, circ_C, circ_V0;
+  double anode_V;  /* anode potential of the next solve */
 } or_state_t;
 
 static void store_reserve(or_store_t* s, int64_t need) {
@@ -221,6 +230,7 @@ static void store_free(or_store_t* s) {
 or_state_t* or_create(const or_cfg_t* cfg) {
   if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 2 || cfg->nsp < 1 || cfg->nsp > OR_MAXSP) return NULL;
   or_state_t* s = calloc(1, sizeof(or_state_t));
+  s->anode_V = cfg->phi_a;
   s->c = *cfg;
   for (int i = 0; i < cfg->nsp; ++i) {
     s->sp[i].q = cfg->q[i]; s->sp[i].m = cfg->m[i]; s->sp[i].w = cfg->w[i]; s->sp[i].role = cfg->role[i];
@@ -640,7 +650,7 @@ int or_solve(or_state_t* s) {
     for (int64_t p = plane; p < (int64_t)s->c.nz * plane; ++p) s->phi[p] = 0.0;
   }
   double rel = 0.0;
-  int it = or_poisson(s->c.nx, s->c.ny, s->c.nz, s->c.h, s->c.phi_c, s->c.phi_a, s->rho, s->phi, s->c.cg_rtol,
+  int it = or_poisson(s->c.nx, s->c.ny, s->c.nz, s->c.h, s->c.phi_c, s->anode_V, s->rho, s->phi, s->c.cg_rtol,
                       s->c.cg_maxit, &rel);
   s->mom.cg_iters = it;
   s->mom.cg_resid_rel = rel;
@@ -964,18 +974,31 @@ void or_compute_moments(or_state_t* s) {
 
 void or_get_moments(or_state_t* s, or_moments_t* out) {
   or_compute_moments(s);
+  s->mom.anode_V = s->anode_V;
   *out = s->mom;
 }
 
 /* One full step n -> n+1 in the order
  *   inject, [sort every sort_interval steps], deposit, solve, push/absorb/MCC,
  *   ionization resolve, compaction. */
+static void circuit_step(or_state_t* s) {
+  if (!s->circuit_on) return;
+  const double dv = (s->c.dt * (s->circ_V0 - s->anode_V) / s->circ_R + s->mom.charge_to_anode_last) / s->circ_C;
+  s->anode_V += dv;
+}
+
+void or_set_circuit(or_state_t* s, double R, double C, double V0) {
+  s->circuit_on = R > 0.0 && C > 0.0;
+  s->circ_R = R; s->circ_C = C; s->circ_V0 = V0;
+}
+
 int or_step(or_state_t* s) {
   or_inject(s);
   if (s->c.sort_interval > 0 && s->step % (uint32_t)s->c.sort_interval == 0) or_sort(s);
   or_deposit(s);
   or_solve(s);
   or_push_collide_resolve(s);
+  circuit_step(s);
   s->step += 1;
   return 0;
 }
@@ -990,6 +1013,7 @@ int or_step_until_solve(or_state_t* s) {
 
 void or_step_finish(or_state_t* s) {
   or_push_collide_resolve(s);
+  circuit_step(s);
   s->step += 1;
 }
 
