@@ -135,6 +135,8 @@ typedef struct {
   int32_t error_flags;                            /* device-side error bits seen */
   int64_t pushed[PIC_MAX_SPECIES];                /* cumulative particle pushes (one per
                                                      live particle per step) */
+  double anode_V;                                 /* anode potential of the next solve (moves
+                                                     only with an external circuit) */
 } pic_moments_t;
 
 /* Phases of a step, for pic_get_phase_times. */
@@ -238,6 +240,20 @@ pic_status pic_philox(pic_handle* h, int64_t n, const uint32_t ctr[4], const uin
  * counts, and ionizations are counted without consuming neutrals or creating
  * particles. 0 restores the normal mode. */
 pic_status pic_set_mcc_background(pic_handle* h, int32_t inst, double density_m3);
+
+/* ---- external circuit -------------------------------------------------------
+ * The paper puts a serial RC circuit (R = 1 kOhm, C = 1 pF) between the
+ * electrodes and treats the voltage as constant on its time scale (Sec. 2).
+ * This call makes it dynamic: a source V0 charges the anode through R, the gap
+ * holds capacitance C, and the charge the anode collects in a step (electrons
+ * and ions absorbed there, pic_moments_t.charge_to_anode_C) flows onto it, once
+ * per step after the push:
+ *   V <- V + (dt (V0 - V) / R + Q_anode) / C.
+ * The next step's Poisson solve uses V at the anode plane (pic_moments_t.anode_V
+ * reports it); the cathode stays at phi_cathode_V. R <= 0 or C <= 0 switches the
+ * circuit off, and the anode then keeps its current potential. PIC_EINVAL for a
+ * NaN argument. */
+pic_status pic_set_circuit(pic_handle* h, int32_t inst, double R_ohm, double C_farad, double V0);
 
 /* ---- surface coupling: ions that bombard the cathode ----------------------
  * In the paper's coupled model ions that reach the cathode are handed to the

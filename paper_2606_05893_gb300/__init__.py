@@ -72,7 +72,8 @@ class pic_moments_t(C.Structure):
                 ("field_energy_J", C.c_double),
                 ("charge_to_cathode_C", C.c_double), ("charge_to_anode_C", C.c_double),
                 ("next_pid", C.c_uint32), ("error_flags", C.c_int32),
-                ("pushed", C.c_int64 * PIC_MAX_SPECIES)]
+                ("pushed", C.c_int64 * PIC_MAX_SPECIES),
+                ("anode_V", C.c_double)]
 
 
 PHASES = ["inject", "sort", "deposit", "solve", "efield", "push_electron", "push_ion", "push_neutral", "resolve"]
@@ -84,7 +85,7 @@ EXPORTED = ["pic_create", "pic_inject", "pic_inject_particles", "pic_step", "pic
             "pic_sort_now", "pic_get_cell_start", "pic_get_ionization_log", "pic_philox",
             "pic_set_mcc_background", "pic_version", "pic_set_profiling", "pic_get_phase_times",
             "pic_launch_count", "pic_kernel_count", "pic_poisson_solve_static", "pic_set_sort_interval",
-            "pic_set_hit_log", "pic_get_hits"]
+            "pic_set_hit_log", "pic_get_hits", "pic_set_circuit"]
 
 _lib = None
 
@@ -129,6 +130,7 @@ def load_library(path: str = LIB_PATH):
         "pic_set_mcc_background": ([P, C.c_int32, C.c_double], st),
         "pic_set_sort_interval": ([P, C.c_int32, C.c_int32], st),
         "pic_set_hit_log": ([P, C.c_int32, C.c_int64], st),
+        "pic_set_circuit": ([P, C.c_int32, C.c_double, C.c_double, C.c_double], st),
         "pic_get_hits": ([P, C.c_int32, C.c_int64, i64, i64, C.POINTER(C.c_uint32), C.POINTER(C.c_int32), i64,
                           d, d, d], st),
         "pic_version": ([], C.c_char_p),
@@ -286,6 +288,10 @@ def pic_set_mcc_background(h, inst, density):
     return _check(h, load_library().pic_set_mcc_background(h, inst, density))
 
 
+def pic_set_circuit(h, inst, R_ohm, C_farad, V0):
+    return _check(h, load_library().pic_set_circuit(h, inst, float(R_ohm), float(C_farad), float(V0)))
+
+
 def pic_set_hit_log(h, inst, capacity):
     return _check(h, load_library().pic_set_hit_log(h, inst, capacity))
 
@@ -440,7 +446,7 @@ class Simulation:
             "cg_iters": m.cg_iters, "cg_resid_rel": m.cg_resid_rel, "total_charge": m.total_charge_C,
             "kinetic": list(m.kinetic_J[:ns]), "field_energy": m.field_energy_J,
             "charge_to_cathode_last": m.charge_to_cathode_C, "charge_to_anode_last": m.charge_to_anode_C,
-            "next_pid": m.next_pid, "error_flags": m.error_flags, "pushed": list(m.pushed[:ns]),
+            "next_pid": m.next_pid, "error_flags": m.error_flags, "pushed": list(m.pushed[:ns]), "anode_V": m.anode_V,
         }
 
     def particles(self, sp, inst=0):

@@ -157,14 +157,14 @@ static dim3 grid3(const Grid& g, int planes) {
 }
 static const dim3 kBlk3(32, 8, 1);
 
-__global__ void __launch_bounds__(256) k_rhs(Grid g, const double* __restrict__ rho64, const float* __restrict__ rho32,
-                                             double* __restrict__ b) {
+__global__ void __launch_bounds__(256) k_rhs(Grid g, const DevCounters* cnt, const double* __restrict__ rho64,
+                                             const float* __restrict__ rho32, double* __restrict__ b) {
   const double s = g.h * g.h / kEps0;
   const float s32 = (float)s;
   const int kn = blockIdx.z + 1;  // node plane of this unknown plane
   const int i = blockIdx.x * 32 + threadIdx.x;
   if (i >= g.nx) return;
-  const double fold = (kn == 1 ? g.phi_c : 0.0) + (kn == g.nz - 1 ? g.phi_a : 0.0);
+  const double fold = (kn == 1 ? g.phi_c : 0.0) + (kn == g.nz - 1 ? cnt->anode_V : 0.0);
   for (int j = blockIdx.y * 8 + threadIdx.y; j < g.ny; j += gridDim.y * 8) {
     const long long u = (long long)blockIdx.z * g.nplane + (long long)j * g.nx + i;
     const long long node = u + g.nplane;
@@ -173,8 +173,9 @@ __global__ void __launch_bounds__(256) k_rhs(Grid g, const double* __restrict__ 
     b[u] = v + fold;
   }
 }
-void launch_rhs(const Grid& g, const double* rho64, const float* rho32, double* b, cudaStream_t st) {
-  PIC_LAUNCH(grid3(g, g.nz - 1), kBlk3, 0, st, k_rhs)(g, rho64, rho32, b);
+void launch_rhs(const Grid& g, const DevCounters* cnt, const double* rho64, const float* rho32, double* b,
+                cudaStream_t st) {
+  PIC_LAUNCH(grid3(g, g.nz - 1), kBlk3, 0, st, k_rhs)(g, cnt, rho64, rho32, b);
 }
 
 // MIXED path: the FP32 charge term f = fl32(h^2/eps0 rho) over the unknowns,
@@ -184,11 +185,18 @@ void launch_rhs(const Grid& g, const double* rho64, const float* rho32, double* 
 // The unknowns are the nodes of planes 1..nz-1, one contiguous range of the
 // node array, so this is a flat pass: four values per thread (16-byte loads)
 // where the plane size keeps the range 16-byte aligned.
-__global__ void __launch_bounds__(256) k_rhs_f32(Grid g, const double* __restrict__ rho64,
-                                                 const float* __restrict__ rho32, float* __restrict__ f) {
+// The solver keeps phi relative to the vacuum potential of the configured
+// electrode voltages; when an external circuit has moved the anode by dV since,
+// dV enters as one more folded Dirichlet term on the last unknown plane, and
+// the FP32 potential carries dV on the anode plane (the field kernel reads it).
+__global__ void __launch_bounds__(256) k_rhs_f32(Grid g, const DevCounters* cnt, const double* __restrict__ rho64,
+                                                 const float* __restrict__ rho32, float* __restrict__ f,
+                                                 float* __restrict__ phi32) {
   const double s = g.h * g.h / kEps0;
   const float s32 = (float)s;
   const long long nu = (long long)(g.nz - 1) * g.nplane;
+  const long long last = nu - g.nplane;  // first unknown of the plane next to the anode
+  const double dV = cnt->anode_V - g.phi_a;
   const float* r32 = rho32 ? rho32 + g.nplane : nullptr;
   const double* r64 = rho64 ? rho64 + g.nplane : nullptr;
   long long u0 = 0;
@@ -196,26 +204,56 @@ __global__ void __launch_bounds__(256) k_rhs_f32(Grid g, const double* __restric
     const long long n4 = nu >> 2;
     const float4* s4 = reinterpret_cast<const float4*>(r32);
     float4* f4 = reinterpret_cast<float4*>(f);
+    const float d4 = (float)dV;
     for (long long q = gtid(); q < n4; q += gstride()) {
       const float4 v = s4[q];
-      f4[q] = make_float4(s32 * v.x, s32 * v.y, s32 * v.z, s32 * v.w);
+      float4 o = make_float4(s32 * v.x, s32 * v.y, s32 * v.z, s32 * v.w);
+      if (dV != 0.0 && (q << 2) >= last) {  // a plane holds whole float4s here
+        o.x += d4;
+        o.y += d4;
+        o.z += d4;
+        o.w += d4;
+      }
+      f4[q] = o;
     }
     u0 = n4 << 2;
   }
-  for (long long u = u0 + gtid(); u < nu; u += gstride()) f[u] = r32 ? s32 * r32[u] : (float)(s * r64[u]);
+  for (long long u = u0 + gtid(); u < nu; u += gstride()) {
+    float v = r32 ? s32 * r32[u] : (float)(s * r64[u]);
+    if (dV != 0.0 && u >= last) v += (float)dV;
+    f[u] = v;
+  }
+  if (phi32)
+    for (long long p = gtid(); p < g.nplane; p += gstride()) phi32[(long long)g.nz * g.nplane + p] = (float)dV;
 }
-void launch_rhs_f32(const Grid& g, const double* rho64, const float* rho32, float* f, cudaStream_t st) {
-  PIC_LAUNCH(grid_for((long long)(g.nz - 1) * g.nplane / 4 + 1), kBlock, 0, st, k_rhs_f32)(g, rho64, rho32, f);
+void launch_rhs_f32(const Grid& g, const DevCounters* cnt, const double* rho64, const float* rho32, float* f,
+                    float* phi32, cudaStream_t st) {
+  PIC_LAUNCH(grid_for((long long)(g.nz - 1) * g.nplane / 4 + 1), kBlock, 0, st, k_rhs_f32)(g, cnt, rho64, rho32, f,
+                                                                                          phi32);
 }
 
-__global__ void k_phi_planes(Grid g, double* phi) {
+__global__ void k_phi_planes(Grid g, const DevCounters* cnt, double* phi) {
+  const double va = cnt->anode_V;
   for (long long p = gtid(); p < g.nplane; p += gstride()) {
     phi[p] = g.phi_c;
-    phi[(long long)g.nz * g.nplane + p] = g.phi_a;
+    phi[(long long)g.nz * g.nplane + p] = va;
   }
 }
-void launch_phi_planes(const Grid& g, double* phi, cudaStream_t st) {
-  PIC_LAUNCH(grid_for(g.nplane), kBlock, 0, st, k_phi_planes)(g, phi);
+void launch_phi_planes(const Grid& g, const DevCounters* cnt, double* phi, cudaStream_t st) {
+  PIC_LAUNCH(grid_for(g.nplane), kBlock, 0, st, k_phi_planes)(g, cnt, phi);
+}
+
+// MIXED: the electrode planes of the FP64 potential as the last solve used them
+// (the anode plane of the FP32 deviation holds the circuit's offset dV)
+__global__ void k_planes_from_ff(Grid g, const float* __restrict__ phi32, double* __restrict__ phi) {
+  const long long top = (long long)g.nz * g.nplane;
+  for (long long p = gtid(); p < g.nplane; p += gstride()) {
+    phi[p] = g.phi_c;
+    phi[top + p] = g.phi_a + (double)phi32[top + p];
+  }
+}
+void launch_planes_from_ff(const Grid& g, const float* phi32, double* phi, cudaStream_t st) {
+  PIC_LAUNCH(grid_for(g.nplane), kBlock, 0, st, k_planes_from_ff)(g, phi32, phi);
 }
 
 // ---------------------------------------------------------------------------
@@ -304,10 +342,17 @@ __global__ void k_step_begin(DevCounters* cnt, StepBegin sb) {
   cnt->q_cathode_step = 0.0;
   cnt->q_anode_step = 0.0;
 }
-__global__ void k_step_end(DevCounters* cnt) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) cnt->step += 1u;
+__global__ void k_step_end(DevCounters* cnt, Circuit c) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (c.on) {
+    const double dv = (c.dt * (c.V0 - cnt->anode_V) / c.R + cnt->q_anode_step) / c.C;
+    cnt->anode_V += dv;
+  }
+  cnt->step += 1u;
 }
-void launch_step_end(DevCounters* cnt, cudaStream_t st) { PIC_LAUNCH(1, 32, 0, st, k_step_end)(cnt); }
+void launch_step_end(DevCounters* cnt, const Circuit& c, cudaStream_t st) {
+  PIC_LAUNCH(1, 32, 0, st, k_step_end)(cnt, c);
+}
 
 void launch_step_begin(DevCounters* cnt, const int* out_buf, int nsp, cudaStream_t st) {
   StepBegin sb;

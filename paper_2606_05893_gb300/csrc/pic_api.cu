@@ -181,6 +181,7 @@ struct Instance {
   long long* cell_start[kMaxSpecies]{};
   // surface-coupling output: ions absorbed at the cathode (cap 0: off)
   HitLog hits{};
+  Circuit circ{};  // external circuit on the anode (off by default)
   SegCtl* seg_ctl = nullptr;    // bucket path state (device)
   SegCtl* seg_host = nullptr;   // pinned mirror
   int32_t* seg_big = nullptr;   // buckets for the block-wide sort (ncell + 1)
@@ -444,6 +445,7 @@ pic_status build_xsec(pic_handle* h, HostXsec& X) {
 cudaError_t ensure_phi64(Instance* I, cudaStream_t st) {
   if (!I->mixed || !I->phi64_stale) return cudaSuccess;
   I->phi64_stale = false;
+  launch_planes_from_ff(I->g, I->phi32, I->phi, st);  // the anode the last solve used (external circuit)
   return I->solver.phi64_from_ff(st);
 }
 
@@ -498,6 +500,7 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
   CK(h, dalloc(&I->plan, 1));
   CK(h, cudaMemset(I->plan, 0, sizeof(InjectPlan)));
   CK(h, cudaMemset(I->cnt, 0, sizeof(DevCounters)));
+  CK(h, cudaMemcpy(&I->cnt->anode_V, &c.phi_anode_V, sizeof(double), cudaMemcpyHostToDevice));
   CK(h, cudaMallocHost((void**)&I->host_cnt, sizeof(DevCounters)));
   memset(I->host_cnt, 0, sizeof(DevCounters));
 
@@ -799,10 +802,11 @@ pic_status step_instance(pic_handle* h, Instance* I) {
   // a4 Poisson solve
   T.begin(PIC_PH_SOLVE, st);
   if (I->mixed) {
-    launch_rhs_f32(g, nullptr, I->rho32, I->solver.f32, st);
+    launch_rhs_f32(g, I->cnt, nullptr, I->rho32, I->solver.f32, I->phi32, st);
     if (I->cfg.warm_start == PIC_WARM_ZERO) CK(h, I->solver.ff_from_phi64(nullptr, st));
   } else {
-    launch_rhs(g, I->rho64, nullptr, I->solver.b, st);
+    if (I->circ.on) launch_phi_planes(g, I->cnt, I->phi, st);  // the anode has moved
+    launch_rhs(g, I->cnt, I->rho64, nullptr, I->solver.b, st);
     if (I->cfg.warm_start == PIC_WARM_ZERO) {
       CK(h, cudaMemsetAsync(I->phi + g.nplane, 0, sizeof(double) * I->solver.n, st));
       CK(h, I->solver.invalidate(st));
@@ -915,7 +919,7 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     launch_resolve_cleanup(r, rb, st);
     T.end(st);
   }
-  launch_step_end(I->cnt, st);
+  launch_step_end(I->cnt, I->circ, st);
   for (int s = 0; s < I->nsp; ++s) I->cur[s] ^= 1;
   I->step += 1;
   I->next_valid = true;
@@ -1127,7 +1131,7 @@ pic_status pic_create(const pic_instance_cfg* cfgs, int32_t n_instances, void* c
       delete h;
       return st;
     }
-    launch_phi_planes(I->g, I->phi, h->stream);
+    launch_phi_planes(I->g, I->cnt, I->phi, h->stream);
     if (I->mixed) I->solver.ff_from_phi64(I->phi + I->g.nplane, h->stream);
   }
   cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -1331,6 +1335,7 @@ pic_status pic_moments(pic_handle* h, int32_t inst, pic_moments_t* out) {
   out->field_energy_J = 0.5 * kEps0 * I->g.h * red[16];
   out->charge_to_cathode_C = c.q_cathode_step;
   out->charge_to_anode_C = c.q_anode_step;
+  out->anode_V = c.anode_V;
   out->next_pid = c.next_pid;
   out->error_flags = c.error;
   for (int sp = 0; sp < I->nsp; ++sp) out->pushed[sp] = (int64_t)c.pushed[sp];
@@ -1425,7 +1430,7 @@ pic_status pic_set_phi(pic_handle* h, int32_t inst, const double* host_phi) {
   Instance* I = h->inst[inst];
   if (!host_phi) return fail(h, PIC_EINVAL, "host_phi is NULL");
   CK(h, cudaMemcpyAsync(I->phi, host_phi, sizeof(double) * I->g.nnode, cudaMemcpyHostToDevice, h->stream));
-  launch_phi_planes(I->g, I->phi, h->stream);
+  launch_phi_planes(I->g, I->cnt, I->phi, h->stream);
   CK(h, I->solver.invalidate(h->stream));
   if (I->mixed) {
     CK(h, I->solver.ff_from_phi64(I->phi + I->g.nplane, h->stream));
@@ -1459,14 +1464,14 @@ pic_status pic_solve(pic_handle* h, int32_t inst, const double* rho, double* phi
   }
   // initial guess: the caller's phi with the electrode planes
   CK(h, cudaMemcpyAsync(I->phi, phi, sizeof(double) * g.nnode, cudaMemcpyHostToDevice, s));
-  launch_phi_planes(g, I->phi, s);
+  launch_phi_planes(g, I->cnt, I->phi, s);
   CK(h, cudaMemcpyAsync(drho, rho, sizeof(double) * g.nnode, cudaMemcpyHostToDevice, s));
   if (I->mixed) {
     CK(h, I->solver.ff_from_phi64(I->phi + g.nplane, s));
-    launch_rhs_f32(g, drho, nullptr, I->solver.f32, s);
+    launch_rhs_f32(g, I->cnt, drho, nullptr, I->solver.f32, I->phi32, s);
   } else {
     CK(h, I->solver.invalidate(s));
-    launch_rhs(g, drho, nullptr, I->solver.b, s);
+    launch_rhs(g, I->cnt, drho, nullptr, I->solver.b, s);
   }
   CK(h, I->solver.launch(s));
   if (I->mixed) CK(h, I->solver.phi64_from_ff(s));
@@ -1643,6 +1648,21 @@ pic_status pic_get_hits(pic_handle* h, int32_t inst, int64_t cap, int64_t* n, in
   *n = k;
   *lost = (long long)(total - (unsigned long long)k);
   CK(h, cudaMemset(L.n, 0, sizeof(unsigned long long)));
+  return PIC_OK;
+}
+
+pic_status pic_set_circuit(pic_handle* h, int32_t inst, double R_ohm, double C_farad, double V0) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  if (!(R_ohm == R_ohm) || !(C_farad == C_farad) || !(V0 == V0)) return fail(h, PIC_EINVAL, "NaN circuit value");
+  Instance* I = h->inst[inst];
+  Circuit& c = I->circ;
+  c.on = R_ohm > 0.0 && C_farad > 0.0 ? 1 : 0;
+  c.R = R_ohm;
+  c.C = C_farad;
+  c.V0 = V0;
+  c.dt = I->g.dt;
+  drop_step_graphs(I);  // the recorded steps hold the circuit's values
   return PIC_OK;
 }
 

@@ -181,6 +181,15 @@ struct DevCounters {
   unsigned long long ev_sort_n;  // events to order this step (min(n_events, capacity))
   unsigned long long pushed[kMaxSpecies];  // cumulative particle pushes (metric units)
   unsigned int step;                       // index of the step being taken (Philox counter word 1)
+  double anode_V;                          // anode potential of the next solve (external circuit)
+};
+
+// External circuit (the serial RC circuit between the electrodes): a source V0
+// charges the anode through R, the gap holds capacitance C, and the charge the
+// anode collects in a step flows onto it. Applied once per step, after the push.
+struct Circuit {
+  int on;
+  double R, C, V0, dt;
 };
 
 // Injection counts of the current step (a1), kept on the device so that a step

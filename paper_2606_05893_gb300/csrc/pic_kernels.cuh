@@ -631,7 +631,7 @@ template <class S>
 void launch_inject(const InjectArgs<S>& a, int grid, cudaStream_t st);
 void launch_inject_commit(DevCounters* cnt, const InjectCommit& c, cudaStream_t st);
 void launch_inject_plan(InjectPlan* plan, int nsp, cudaStream_t st);
-void launch_step_end(DevCounters* cnt, cudaStream_t st);
+void launch_step_end(DevCounters* cnt, const Circuit& c, cudaStream_t st);
 template <class S>
 void launch_push(const PushArgs<S>& a, int role, bool mcc, int grid, cudaStream_t st);
 void launch_resolve_rank(const ResolveArgs& a, int grid, cudaStream_t st);
@@ -646,11 +646,14 @@ void launch_deposit(const DepositArgs<S>& a, int grid, cudaStream_t st);
 void launch_fill64(double* p, long long n, double v, cudaStream_t st);
 void launch_fill32(float* p, long long n, float v, cudaStream_t st);
 void launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t st);
-void launch_rhs(const Grid& g, const double* rho64, const float* rho32, double* b, cudaStream_t st);
-void launch_rhs_f32(const Grid& g, const double* rho64, const float* rho32, float* f, cudaStream_t st);
+void launch_rhs(const Grid& g, const DevCounters* cnt, const double* rho64, const float* rho32, double* b,
+                cudaStream_t st);
+void launch_rhs_f32(const Grid& g, const DevCounters* cnt, const double* rho64, const float* rho32, float* f,
+                    float* phi32, cudaStream_t st);
 void launch_efield64(const Grid& g, const double* phi, double4_32a* E, const int32_t* ncount, cudaStream_t st);
 void launch_efield32f(const Grid& g, const float* phi32, float4* E, const int32_t* ncount, cudaStream_t st);
-void launch_phi_planes(const Grid& g, double* phi, cudaStream_t st);
+void launch_phi_planes(const Grid& g, const DevCounters* cnt, double* phi, cudaStream_t st);
+void launch_planes_from_ff(const Grid& g, const float* phi32, double* phi, cudaStream_t st);
 void launch_step_begin(DevCounters* cnt, const int* out_buf, int nsp, cudaStream_t st);
 
 template <class S>
