@@ -132,12 +132,19 @@ static dim3 g3r(const Lv& L) {
   return g;
 }
 
-// r = b - A x (no reduction; multigrid levels)
+// r = b - A x at the colour-0 points only (x index m over the nx/2 points of
+// that colour, as the half sweeps). After the pre-smoothing half sweeps the
+// colour-1 residual is zero in exact arithmetic (the colour-1 sweep solved
+// those equations with their colour-0 neighbours fixed), so it is neither
+// formed nor restricted; the V-cycle is the same operator.
 template <class T>
 __global__ void __launch_bounds__(256) k_residual(Lv L, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r) {
   pdl_enter();
-  ROWS3(L, L.nx) {
-    if (!in_x) continue;
+  const int m = blockIdx.x * kBX + threadIdx.x;
+  const int k = blockIdx.z;
+  if (m >= (L.nx >> 1)) return;
+  for (int j = blockIdx.y * kBY + threadIdx.y; j < L.ny; j += gridDim.y * kBY) {
+    const int i = 2 * m + ((j + k + 1) & 1);
     const int u = k * L.pl + j * L.nx + i;
     r[u] = b[u] - ((T)6 * x[u] - nb_sum(L, x, u, i, j, k));
   }
@@ -224,7 +231,9 @@ __global__ void __launch_bounds__(256) k_restrict(Lv F, Lv Cc, const T* __restri
         jf = jf < 0 ? jf + F.ny : (jf >= F.ny ? jf - F.ny : jf);
         const T wb = b2 == 0 ? (T)0.5 : (T)0.25;
         const int rowf = kf * F.pl + jf * F.nx;
-        s += wb * wc * ((T)0.25 * r[rowf + im] + (T)0.5 * r[rowf + i0] + (T)0.25 * r[rowf + ip]);
+        // colour-0 fine points only (even offset sum; the colour-1 residual is zero)
+        if (((b2 + c) & 1) == 0) s += wb * wc * ((T)0.5 * r[rowf + i0]);
+        else s += wb * wc * ((T)0.25 * (r[rowf + im] + r[rowf + ip]));
       }
     }
     bc[K * Cc.pl + J * Cc.nx + I] = (T)4 * s;
@@ -497,13 +506,16 @@ __device__ void kc_smooth_pre(float* sm, const PlaneMap& pm, int l, const KLv& L
   }
 }
 
+// colour-0 points only, as k_residual
 __device__ void kc_residual(float* sm, const PlaneMap& pm, int l, const KLv& L, int me) {
   const int p0 = plane0(L.P, me), np = plane0(L.P, me + 1) - p0;
-  for (int q = threadIdx.x; q < np * L.pl; q += blockDim.x) {
-    const int kk = fdiv(q, L.dpl);
-    const int u = q - kk * L.pl;
-    const int j = fdiv(u, L.dnx);
-    const int i = u - j * L.nx;
+  const int per = L.hx * L.ny;
+  for (int q = threadIdx.x; q < np * per; q += blockDim.x) {
+    const int kk = fdiv(q, L.dhxny);
+    const int t = q - kk * per;
+    const int j = fdiv(t, L.dhx);
+    const int i = 2 * (t - j * L.hx) + ((j + p0 + kk + 1) & 1);
+    const int u = j * L.nx + i;
     const float* e = sm + L.oe + kk * L.pl;
     sm[L.orr + kk * L.pl + u] =
         sm[L.ob + kk * L.pl + u] - (6.f * e[u] - k_nb(sm, pm, l, L, L.oe, e, p0 + kk, i, j, me));
@@ -533,7 +545,8 @@ __device__ void kc_restrict(float* sm, const PlaneMap& pm, int l, const KLv& F, 
         jf = jf < 0 ? jf + F.ny : (jf >= F.ny ? jf - F.ny : jf);
         const float wb = b2 == 0 ? 0.5f : 0.25f;
         const float* row = rp + jf * F.nx;
-        s += wb * wc * (0.25f * row[im] + 0.5f * row[i0] + 0.25f * row[ip]);
+        if (((b2 + cc) & 1) == 0) s += wb * wc * (0.5f * row[i0]);
+        else s += wb * wc * (0.25f * (row[im] + row[ip]));
       }
     }
     sm[C.ob + kk * C.pl + U] = 4.f * s;
@@ -801,7 +814,7 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
   for (int l = 0; l < (ff > 0 ? ff : nl - 1); ++l) {
     const Lv L = lv_of(levels[l]);
     SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth_pre<T>)(L, E[l], B[l]);
-    SOLVER_LAUNCH(g3(L, L.nx), kB3, 0, s, k_residual<T>)(L, E[l], B[l], r[l]);
+    SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_residual<T>)(L, E[l], B[l], r[l]);
     const Lv C = lv_of(levels[l + 1]);
     SOLVER_LAUNCH(g3(C, C.nx), kB3, 0, s, k_restrict<T>)(L, C, r[l], B[l + 1]);
   }
