@@ -123,6 +123,14 @@ __device__ __forceinline__ T nb_sum(const Lv& L, const T* __restrict__ x, int u,
   for (int k = blockIdx.z; k < (L).nz - 1; k += gridDim.z)                   \
     for (int j = blockIdx.y * kBY + threadIdx.y; j < (L).ny; j += gridDim.y * kBY)
 constexpr int kWaveBlocks = 152 * 8;  // resident 256-thread blocks on 152 SMs
+static dim3 g3rs(const Lv& L) {  // as g3r, x over the nx / 2 points of a colour
+  dim3 g = g3(L, L.nx / 2);
+  const int per_plane = (int)(g.x * g.y);
+  int gz = kWaveBlocks / per_plane;
+  gz = gz < 1 ? 1 : (gz > (int)g.z ? (int)g.z : gz);
+  g.z = gz;
+  return g;
+}
 static dim3 g3r(const Lv& L) {
   dim3 g = g3(L, L.nx);
   const int per_plane = (int)(g.x * g.y);
@@ -280,6 +288,175 @@ __global__ void __launch_bounds__(256) k_prolong(Lv F, Lv Cc, const T* __restric
       s += t;
     }
     ef[blockIdx.z * F.pl + j * F.nx + i] += wk * s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Colour-split layout of the finest level (MIXED path): every colour-0 point,
+// then every colour-1 point, each half in (plane, row, m) order with m = i / 2.
+// A half sweep in the natural order reads one colour with stride 2 (a warp's
+// load spans twice the bytes it uses); here every neighbour a point needs is a
+// contiguous run of the other colour: its y and z neighbours sit at the same m,
+// its x neighbours at m - 1 + p and m + p (p = the parity of i, (j + k + 1 + c)
+// & 1 for colour c; nx, ny even). The sums keep the natural kernels' order, so
+// the values are theirs.
+// ---------------------------------------------------------------------------
+struct SpNb {
+  int xm, xp, ym, yp, zm, zp;  // offsets into the other colour's half (zm / zp: -1 when absent)
+};
+// neighbours of point (m, j, k) of parity p in the other colour's half
+__device__ __forceinline__ SpNb sp_nb(const Lv& L, int m, int j, int k, int p) {
+  const int hx = L.nx >> 1;
+  const int row = (k * L.ny + j) * hx;
+  SpNb n;
+  int a = m - 1 + p, b = m + p;
+  a = a < 0 ? hx - 1 : a;
+  b = b == hx ? 0 : b;
+  n.xm = row + a;
+  n.xp = row + b;
+  n.ym = (j == 0 ? row + (L.ny - 1) * hx : row - hx) + m;
+  n.yp = (j == L.ny - 1 ? row - (L.ny - 1) * hx : row + hx) + m;
+  n.zm = k > 0 ? row - L.ny * hx + m : -1;
+  n.zp = k < L.nz - 2 ? row + L.ny * hx + m : -1;
+  return n;
+}
+template <class T>
+__device__ __forceinline__ T sp_sum(const T* __restrict__ o, const SpNb& n) {
+  T s = o[n.xm] + o[n.xp] + o[n.ym] + o[n.yp];
+  if (n.zm >= 0) s += o[n.zm];
+  if (n.zp >= 0) s += o[n.zp];
+  return s;
+}
+template <class T>
+__device__ __forceinline__ T sp_sum_sixth(const T* __restrict__ o, const SpNb& n, T sixth) {
+  T s = mul_rn(o[n.xm], sixth) + mul_rn(o[n.xp], sixth) + mul_rn(o[n.ym], sixth) + mul_rn(o[n.yp], sixth);
+  if (n.zm >= 0) s += mul_rn(o[n.zm], sixth);
+  if (n.zp >= 0) s += mul_rn(o[n.zp], sixth);
+  return s;
+}
+// split index of natural point (i, j, k)
+__device__ __forceinline__ int sp_index(const Lv& L, int i, int j, int k) {
+  const int hx = L.nx >> 1;
+  return ((i + j + k + 1) & 1) * (L.nu >> 1) + (k * L.ny + j) * hx + (i >> 1);
+}
+
+// the loop header of the split kernels: m over the nx / 2 points of a colour in
+// a row, j over the rows, k = plane (grid g3(L, nx / 2))
+#define SPLIT_ROWS(L)                                                        \
+  const int m = blockIdx.x * kBX + threadIdx.x;                              \
+  const int k = blockIdx.z;                                                  \
+  const int hx_ = (L).nx >> 1;                                               \
+  const int half_ = (L).nu >> 1;                                             \
+  if (m >= hx_) return;                                                      \
+  for (int j = blockIdx.y * kBY + threadIdx.y; j < (L).ny; j += gridDim.y * kBY)
+
+template <class T>
+__global__ void __launch_bounds__(256) k_smooth_s(Lv L, T* __restrict__ e, const T* __restrict__ b, int color) {
+  pdl_enter();
+  const T sixth = (T)(1.0 / 6.0);
+  SPLIT_ROWS(L) {
+    const int p = (j + k + 1 + color) & 1;
+    const int u = color * half_ + (k * L.ny + j) * hx_ + m;
+    const SpNb n = sp_nb(L, m, j, k, p);
+    e[u] = (b[u] + sp_sum(e + (color ^ 1) * half_, n)) * sixth;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_smooth_pre_s(Lv L, T* __restrict__ e, const T* __restrict__ b) {
+  pdl_enter();
+  const T sixth = (T)(1.0 / 6.0);
+  SPLIT_ROWS(L) {
+    const int u = (k * L.ny + j) * hx_ + m;
+    e[u] = mul_rn(b[u], sixth);  // colour 0 from e = 0
+    const SpNb n = sp_nb(L, m, j, k, (j + k) & 1);  // colour 1, its neighbours colour 0
+    e[half_ + u] = (b[half_ + u] + sp_sum_sixth(b, n, sixth)) * sixth;
+  }
+}
+
+// residual at the colour-0 points (written into the colour-0 half)
+template <class T>
+__global__ void __launch_bounds__(256) k_residual_s(Lv L, const T* __restrict__ x, const T* __restrict__ b,
+                                                    T* __restrict__ r) {
+  pdl_enter();
+  SPLIT_ROWS(L) {
+    const int u = (k * L.ny + j) * hx_ + m;
+    const SpNb n = sp_nb(L, m, j, k, (j + k + 1) & 1);
+    r[u] = b[u] - ((T)6 * x[u] - sp_sum(x + half_, n));
+  }
+}
+
+// b_c = 4 * full-weighting of the colour-0 residual of the split finest level
+// (natural coarse output; grid over the coarse level). The colour-0 points of
+// the 27-point stencil have an even offset sum: the centre column (i = 2I) when
+// the row and plane offsets sum to an even number, else its two x-neighbours
+// (i = 2I +- 1, both of m = I and I - 1).
+template <class T>
+__global__ void __launch_bounds__(256) k_restrict_s0(Lv F, Lv Cc, const T* __restrict__ r, T* __restrict__ bc) {
+  pdl_enter();
+  const int I = blockIdx.x * kBX + threadIdx.x;
+  const int K = blockIdx.z;
+  if (I >= Cc.nx) return;
+  const int Kn = K + 1;
+  const int hx = F.nx >> 1;
+  const int Im = I == 0 ? hx - 1 : I - 1;
+  for (int J = blockIdx.y * kBY + threadIdx.y; J < Cc.ny; J += gridDim.y * kBY) {
+    T s = 0;
+#pragma unroll
+    for (int c = -1; c <= 1; ++c) {
+      const int kf = 2 * Kn + c - 1;
+      const T wc = c == 0 ? (T)0.5 : (T)0.25;
+#pragma unroll
+      for (int b2 = -1; b2 <= 1; ++b2) {
+        int jf = 2 * J + b2;
+        jf = jf < 0 ? jf + F.ny : (jf >= F.ny ? jf - F.ny : jf);
+        const T wb = b2 == 0 ? (T)0.5 : (T)0.25;
+        const int rowf = (kf * F.ny + jf) * hx;
+        if (((b2 + c) & 1) == 0) s += wb * wc * ((T)0.5 * r[rowf + I]);
+        else s += wb * wc * ((T)0.25 * (r[rowf + Im] + r[rowf + I]));
+      }
+    }
+    bc[K * Cc.pl + J * Cc.nx + I] = (T)4 * s;
+  }
+}
+
+// e_f += P e_c at the colour-0 points of the split finest level (natural coarse input)
+template <class T>
+__global__ void __launch_bounds__(256) k_prolong_s0(Lv F, Lv Cc, const T* __restrict__ ec, T* __restrict__ ef) {
+  pdl_enter();
+  const int kn = blockIdx.z + 1;
+  const int K0 = kn >> 1;
+  const bool kodd = kn & 1;
+  const bool use0 = K0 >= 1 && K0 <= Cc.nz - 1;
+  const bool use1 = kodd && (K0 + 1) >= 1 && (K0 + 1) <= Cc.nz - 1;
+  const int off0 = (K0 - 1) * Cc.pl, off1 = K0 * Cc.pl;
+  const T wk = kodd ? (T)0.5 : (T)1;
+  const int m = blockIdx.x * kBX + threadIdx.x;
+  const int hx = F.nx >> 1;
+  if (m >= hx) return;
+  const int I0 = m;  // i >> 1 for both parities
+  const int I1 = I0 + 1 == Cc.nx ? 0 : I0 + 1;
+  for (int j = blockIdx.y * kBY + threadIdx.y; j < F.ny; j += gridDim.y * kBY) {
+    const bool iodd = ((j + (int)blockIdx.z + 1) & 1) != 0;  // parity of i at colour 0
+    const int J0 = j >> 1;
+    const int J1 = J0 + 1 == Cc.ny ? 0 : J0 + 1;
+    const bool jodd = j & 1;
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (c == 0 ? !use0 : !use1) continue;
+      const int off = c == 0 ? off0 : off1;
+      const int r0 = off + J0 * Cc.nx, r1 = off + J1 * Cc.nx;
+      T t = ec[r0 + I0];
+      if (iodd) t = (T)0.5 * (t + ec[r0 + I1]);
+      if (jodd) {
+        T t1 = ec[r1 + I0];
+        if (iodd) t1 = (T)0.5 * (t1 + ec[r1 + I1]);
+        t = (T)0.5 * (t + t1);
+      }
+      s += t;
+    }
+    ef[(blockIdx.z * F.ny + j) * hx + m] += wk * s;
   }
 }
 
@@ -708,6 +885,7 @@ template <class T>
 cudaError_t Mg<T>::init(const std::vector<MgLevel>& plan) {
   levels = plan;
   rb_ok = (plan[0].nx % 2 == 0) && (plan[0].ny % 2 == 0);
+  split0 = std::is_same<T, float>::value && rb_ok && plan.size() >= 2;
   const size_t nl = plan.size();
   e.assign(nl, nullptr);
   b.assign(nl, nullptr);
@@ -813,9 +991,15 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
   const int ff = fuse_from;  // levels ff..nl-1 run in one cluster (FP32 only), -1: none
   for (int l = 0; l < (ff > 0 ? ff : nl - 1); ++l) {
     const Lv L = lv_of(levels[l]);
+    const Lv C = lv_of(levels[l + 1]);
+    if (l == 0 && split0) {
+      SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth_pre_s<T>)(L, E[l], B[l]);
+      SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_residual_s<T>)(L, E[l], B[l], r[l]);
+      SOLVER_LAUNCH(g3(C, C.nx), kB3, 0, s, k_restrict_s0<T>)(L, C, r[l], B[l + 1]);
+      continue;
+    }
     SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth_pre<T>)(L, E[l], B[l]);
     SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_residual<T>)(L, E[l], B[l], r[l]);
-    const Lv C = lv_of(levels[l + 1]);
     SOLVER_LAUNCH(g3(C, C.nx), kB3, 0, s, k_restrict<T>)(L, C, r[l], B[l + 1]);
   }
   if constexpr (std::is_same<T, float>::value) {
@@ -873,6 +1057,12 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
   for (int l = (ff > 0 ? ff : nl - 1) - 1; l >= 0; --l) {
     const Lv L = lv_of(levels[l]);
     const Lv C = lv_of(levels[l + 1]);
+    if (l == 0 && split0) {
+      SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_prolong_s0<T>)(L, C, E[l + 1], E[l]);
+      SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth_s<T>)(L, E[l], B[l], 1);
+      SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth_s<T>)(L, E[l], B[l], 0);
+      continue;
+    }
     SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_prolong<T>)(L, C, E[l + 1], E[l]);
     SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 1);
     SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 0);
@@ -1089,12 +1279,13 @@ __global__ void __launch_bounds__(256) k_dot_bb_ff(Lv L, const float* __restrict
 
 // r = fl32(f - A (hi + lo)); d = 0; outer decision in the last block.
 // b = 0 (bb = 0): the solution is phi = 0, i.e. hi + lo = -vac.
+// split: r and d are in the colour-split layout of the finest level (hi, lo, f natural)
 __global__ void __launch_bounds__(256) k_residual_ff(Lv L, float* __restrict__ hi, float* __restrict__ lo,
                                                      const float* __restrict__ f, float* __restrict__ r,
                                                      float* __restrict__ d, double phi_c, double dphi_dk, double* part,
                                                      SolveCtl* c, cudaGraphConditionalHandle h_outer,
                                                      cudaGraphConditionalHandle h_inner, double inner_rtol,
-                                                     int max_outer, int use_graph) {
+                                                     int max_outer, int use_graph, int split) {
   pdl_enter();
   float acc = 0.f;
   const bool zero_x = c->bb == 0.0;
@@ -1121,8 +1312,9 @@ __global__ void __launch_bounds__(256) k_residual_ff(Lv L, float* __restrict__ h
       const float small = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(er, ea), e6), e), alo);
       rv = __fadd_rn(r1, small);
     }
-    r[u] = rv;
-    d[u] = 0.f;
+    const int w = split ? sp_index(L, i, j, k) : u;
+    r[w] = rv;
+    d[w] = 0.f;
     acc += rv * rv;
   }
   double rr;
@@ -1130,14 +1322,18 @@ __global__ void __launch_bounds__(256) k_residual_ff(Lv L, float* __restrict__ h
     fin_outer(rr, c, h_outer, h_inner, inner_rtol, 1, max_outer, use_graph);
 }
 
-// (hi, lo) += d, renormalised (hi = fl32(hi + lo)); nothing to do once stopped
-__global__ void __launch_bounds__(kSB) k_update_ff(long long n, float* __restrict__ hi, float* __restrict__ lo,
-                                                   const float* __restrict__ d, const SolveCtl* c) {
+// (hi, lo) += d, renormalised (hi = fl32(hi + lo)); nothing to do once stopped.
+// split: d in the colour-split layout of the finest level.
+__global__ void __launch_bounds__(256) k_update_ff(Lv L, float* __restrict__ hi, float* __restrict__ lo,
+                                                   const float* __restrict__ d, const SolveCtl* c, int split) {
   pdl_enter();
   if (c->stopped) return;
-  for (long long u = gtid(); u < n; u += gstride()) {
+  ROWS3(L, L.nx) {
+    if (!in_x) continue;
+    const int u = k * L.pl + j * L.nx + i;
+    const float dv = d[split ? sp_index(L, i, j, k) : u];
     float s, e;
-    two_sum(hi[u], d[u], s, e);
+    two_sum(hi[u], dv, s, e);
     e = __fadd_rn(e, lo[u]);
     const float h2 = __fadd_rn(s, e);
     hi[u] = h2;
@@ -1223,6 +1419,35 @@ __global__ void __launch_bounds__(256) k_apply_pq(Lv L, const T* __restrict__ p,
     const T qv = (T)6 * pv - nb_sum(L, p, u, i, j, k);
     q[u] = qv;
     acc += pv * qv;
+  }
+  double pq;
+  if (!grid_total(acc, part, &c->ticket, &pq)) return;
+  c->pq = pq;
+  c->alpha = pq != 0.0 ? c->rz / pq : 0.0;
+}
+
+// q = A p ; p.q -> alpha, on the split finest level (both colours per thread;
+// planes strided as in the natural kernel, at most one wave of blocks)
+template <class T>
+__global__ void __launch_bounds__(256) k_apply_pq_s(Lv L, const T* __restrict__ p, T* __restrict__ q, double* part,
+                                                    SolveCtl* c) {
+  pdl_enter();
+  T acc = 0;
+  const int m = blockIdx.x * kBX + threadIdx.x;
+  const int hx = L.nx >> 1, half = L.nu >> 1;
+  if (m < hx) {
+    for (int k = blockIdx.z; k < L.nz - 1; k += gridDim.z)
+      for (int j = blockIdx.y * kBY + threadIdx.y; j < L.ny; j += gridDim.y * kBY) {
+        const int row = (k * L.ny + j) * hx + m;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const SpNb n = sp_nb(L, m, j, k, (j + k + 1 + cc) & 1);
+          const T pv = p[cc * half + row];
+          const T qv = (T)6 * pv - sp_sum(p + (cc ^ 1) * half, n);
+          q[cc * half + row] = qv;
+          acc += pv * qv;
+        }
+      }
   }
   double pq;
   if (!grid_total(acc, part, &c->ticket, &pq)) return;
@@ -1419,7 +1644,8 @@ static void capture_pcg_iteration(Pcg<T>& pc, const Lv& L, double* part, SolveCt
   SOLVER_LAUNCH(G, kSB, 0, s, k_dot_rz<T>)(L.nu, pc.r, pc.z, part, ctl);
   const dim3 PGd = g3(L, L.nx);
   SOLVER_LAUNCH(G, kSB, 0, s, k_pupdate_c<T>)(L.nu, pc.p, pc.z, ctl);
-  SOLVER_LAUNCH(g3r(L), kB3, 0, s, k_apply_pq<T>)(L, pc.p, pc.q, part, ctl);
+  if (pc.mg.split0) SOLVER_LAUNCH(g3rs(L), kB3, 0, s, k_apply_pq_s<T>)(L, pc.p, pc.q, part, ctl);
+  else SOLVER_LAUNCH(g3r(L), kB3, 0, s, k_apply_pq<T>)(L, pc.p, pc.q, part, ctl);
   SOLVER_LAUNCH(G, kSB, 0, s, k_update_rr<T>)(L.nu, pc.d, pc.r, pc.p, pc.q, ctl, part, h_inner, use_graph);
 }
 
@@ -1526,7 +1752,7 @@ cudaError_t Solver::record(cudaStream_t s0) {
     if (e == cudaSuccess) {
       if (mixed) {
         SOLVER_LAUNCH(g3r(L), kB3, 0, s1, k_residual_ff)(L, phi32, lo32, f32, p32.r, p32.d, phi_c, dphi_dk, part, ctl,
-                                                    h_outer, h_inner, inner_rtol, max_outer, 1);
+                                                    h_outer, h_inner, inner_rtol, max_outer, 1, (int)p32.mg.split0);
       } else {
         SOLVER_LAUNCH(g3r(L), kB3, 0, s1, k_residual_prep<double>)(L, x, b, ax, p64.r, p64.d, part, ctl, h_outer, h_inner,
                                                               inner_rtol, mixed, max_outer, 1);
@@ -1563,7 +1789,7 @@ cudaError_t Solver::record(cudaStream_t s0) {
     }
     if (e == cudaSuccess) {
       if (mixed) {
-        SOLVER_LAUNCH(G, kSB, 0, s1, k_update_ff)(L.nu, phi32, lo32, p32.d, ctl);
+        SOLVER_LAUNCH(g3(L, L.nx), kB3, 0, s1, k_update_ff)(L, phi32, lo32, p32.d, ctl, (int)p32.mg.split0);
       } else {
         SOLVER_LAUNCH(PGd, kB3, 0, s1, k_axpy_out<double>)(L, x, p64.d, nullptr, phi_c, dphi_dk, ctl);
       }
@@ -1606,7 +1832,7 @@ cudaError_t Solver::run_host(cudaStream_t s) {
   for (int outer = 0; outer < max_outer + 1; ++outer) {
     if (mixed)
       SOLVER_LAUNCH(g3r(L), kB3, 0, s, k_residual_ff)(L, hphi32, lo32, f32, p32.r, p32.d, h_phi_c, h_dphi_dk, part, ctl, none,
-                                                 none, inner_rtol, max_outer, 0);
+                                                 none, inner_rtol, max_outer, 0, (int)p32.mg.split0);
     else
       SOLVER_LAUNCH(g3r(L), kB3, 0, s, k_residual_prep<double>)(L, hx, b, ax, p64.r, p64.d, part, ctl, none, none, inner_rtol,
                                                            mixed, max_outer, 0);
@@ -1619,7 +1845,7 @@ cudaError_t Solver::run_host(cudaStream_t s) {
       if ((e = read()) != cudaSuccess) return e;
       if (!host_ctl->more) break;
     }
-    if (mixed) SOLVER_LAUNCH(G, kSB, 0, s, k_update_ff)(L.nu, hphi32, lo32, p32.d, ctl);
+    if (mixed) SOLVER_LAUNCH(g3(L, L.nx), kB3, 0, s, k_update_ff)(L, hphi32, lo32, p32.d, ctl, (int)p32.mg.split0);
     else SOLVER_LAUNCH(PGd, kB3, 0, s, k_axpy_out<double>)(L, hx, p64.d, nullptr, h_phi_c, h_dphi_dk, ctl);
     if (!go) break;
   }

@@ -41,6 +41,7 @@ struct Mg {
   int coarse_sweeps = 16;
   int fuse_from = -1;    // levels fuse_from..end run in one thread-block cluster (FP32), -1: none
   size_t fuse_smem = 0;  // its dynamic shared memory per block
+  bool split0 = false;   // finest level in the colour-split layout (FP32, red-black, two levels or more)
   cudaError_t init(const std::vector<MgLevel>& plan);
   void release();
   void vcycle(const T* rhs, T* z, cudaStream_t s);
