@@ -301,6 +301,10 @@ __global__ void __launch_bounds__(256) k_prolong(Lv F, Lv Cc, const T* __restric
 // & 1 for colour c; nx, ny even). The sums keep the natural kernels' order, so
 // the values are theirs.
 // ---------------------------------------------------------------------------
+template <class V>
+__device__ __forceinline__ bool grid_total(V v, double* part, unsigned* ticket, double* tot);
+__device__ __forceinline__ void set_beta(SolveCtl* c, double rz);
+
 struct SpNb {
   int xm, xp, ym, yp, zm, zp;  // offsets into the other colour's half (zm / zp: -1 when absent)
 };
@@ -360,6 +364,34 @@ __global__ void __launch_bounds__(256) k_smooth_s(Lv L, T* __restrict__ e, const
     const SpNb n = sp_nb(L, m, j, k, p);
     e[u] = (b[u] + sp_sum(e + (color ^ 1) * half_, n)) * sixth;
   }
+}
+
+// The V-cycle's last half sweep (colour 0 of the split finest level) with the
+// PCG product r.z: each thread adds its colour-0 point, just written, and the
+// colour-1 point at the same index of the other half, final since the sweep
+// before; the last block turns r.z into beta. Planes strided on at most one
+// wave of blocks (every thread reaches the grid-wide sum).
+template <class T>
+__global__ void __launch_bounds__(256) k_smooth_s_dot(Lv L, T* __restrict__ e, const T* __restrict__ b, double* part,
+                                                      SolveCtl* c) {
+  pdl_enter();
+  const T sixth = (T)(1.0 / 6.0);
+  const int m = blockIdx.x * kBX + threadIdx.x;
+  const int hx = L.nx >> 1, half = L.nu >> 1;
+  T acc = 0;
+  if (m < hx) {
+    for (int k = blockIdx.z; k < L.nz - 1; k += gridDim.z)
+      for (int j = blockIdx.y * kBY + threadIdx.y; j < L.ny; j += gridDim.y * kBY) {
+        const int u = (k * L.ny + j) * hx + m;
+        const SpNb n = sp_nb(L, m, j, k, (j + k + 1) & 1);
+        const T b0 = b[u];
+        const T e0 = (b0 + sp_sum(e + half, n)) * sixth;
+        e[u] = e0;
+        acc += b0 * e0 + b[half + u] * e[half + u];
+      }
+  }
+  double rz;
+  if (grid_total(acc, part, &c->ticket, &rz)) set_beta(c, rz);
 }
 
 template <class T>
@@ -974,14 +1006,15 @@ void Mg<T>::release() {
 
 // z = M^-1 rhs (one V(1,1) cycle from zero); rhs and z live at level 0 outside
 template <class T>
-void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
+bool Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s, double* part, SolveCtl* ctl) {
   const int nl = (int)levels.size();
+  bool dot_done = false;
   if (!rb_ok) {
     // Jacobi preconditioner: z = rhs / 6
     const Lv L = lv_of(levels[0]);
     SOLVER_LAUNCH(sgrid(L.nu), kSB, 0, s, k_copy<T>)(L.nu, z, rhs);
     SOLVER_LAUNCH(sgrid(L.nu), kSB, 0, s, k_jacobi_scale<T>)(L.nu, z);
-    return;
+    return false;
   }
   std::vector<T*> E(nl), B(nl);
   for (int l = 0; l < nl; ++l) {
@@ -1060,13 +1093,19 @@ void Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s) {
     if (l == 0 && split0) {
       SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_prolong_s0<T>)(L, C, E[l + 1], E[l]);
       SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth_s<T>)(L, E[l], B[l], 1);
-      SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth_s<T>)(L, E[l], B[l], 0);
+      if (ctl) {
+        SOLVER_LAUNCH(g3rs(L), kB3, 0, s, k_smooth_s_dot<T>)(L, E[l], B[l], part, ctl);
+        dot_done = true;
+      } else {
+        SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth_s<T>)(L, E[l], B[l], 0);
+      }
       continue;
     }
     SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_prolong<T>)(L, C, E[l + 1], E[l]);
     SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 1);
     SOLVER_LAUNCH(g3(L, L.nx / 2), kB3, 0, s, k_smooth<T>)(L, E[l], B[l], 0);
   }
+  return dot_done;
 }
 
 // ---------------------------------------------------------------------------
@@ -1373,6 +1412,12 @@ __global__ void __launch_bounds__(256) k_ff_from_phi(Lv L, const double* __restr
 // four times the bytes in flight per load); the FP64 instantiations and the
 // tail after the last full float4 go element by element. The level-0 vectors
 // are separate allocations, hence 16-byte aligned.
+// r.z of this iteration -> beta (0 on the first iteration of an inner solve)
+__device__ __forceinline__ void set_beta(SolveCtl* c, double rz) {
+  c->beta = c->it_inner > 0 ? rz / c->rz : 0.0;
+  c->rz = rz;
+}
+
 template <class T>
 struct Vec4 {
   static constexpr bool on = false;
@@ -1401,9 +1446,7 @@ __global__ void __launch_bounds__(kSB) k_dot_rz(int n, const T* __restrict__ r, 
   }
   for (int u = u0 + blockIdx.x * kSB + threadIdx.x; u < n; u += gridDim.x * kSB) acc += r[u] * z[u];
   double rz;
-  if (!grid_total(acc, part, &c->ticket, &rz)) return;
-  c->beta = c->it_inner > 0 ? rz / c->rz : 0.0;
-  c->rz = rz;
+  if (grid_total(acc, part, &c->ticket, &rz)) set_beta(c, rz);
 }
 
 // q = A p ; p.q -> alpha
@@ -1640,8 +1683,7 @@ template <class T>
 static void capture_pcg_iteration(Pcg<T>& pc, const Lv& L, double* part, SolveCtl* ctl,
                                   cudaGraphConditionalHandle h_inner, cudaStream_t s, int use_graph = 1) {
   const int G = sgrid(L.nu);
-  pc.mg.vcycle(pc.r, pc.z, s);
-  SOLVER_LAUNCH(G, kSB, 0, s, k_dot_rz<T>)(L.nu, pc.r, pc.z, part, ctl);
+  if (!pc.mg.vcycle(pc.r, pc.z, s, part, ctl)) SOLVER_LAUNCH(G, kSB, 0, s, k_dot_rz<T>)(L.nu, pc.r, pc.z, part, ctl);
   const dim3 PGd = g3(L, L.nx);
   SOLVER_LAUNCH(G, kSB, 0, s, k_pupdate_c<T>)(L.nu, pc.p, pc.z, ctl);
   if (pc.mg.split0) SOLVER_LAUNCH(g3rs(L), kB3, 0, s, k_apply_pq_s<T>)(L, pc.p, pc.q, part, ctl);

@@ -44,7 +44,8 @@ struct Mg {
   bool split0 = false;   // finest level in the colour-split layout (FP32, red-black, two levels or more)
   cudaError_t init(const std::vector<MgLevel>& plan);
   void release();
-  void vcycle(const T* rhs, T* z, cudaStream_t s);
+  // part, ctl given: the last half sweep also forms the PCG product r.z (returns true then)
+  bool vcycle(const T* rhs, T* z, cudaStream_t s, double* part = nullptr, SolveCtl* ctl = nullptr);
 };
 
 template <class T>
