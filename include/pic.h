@@ -243,7 +243,8 @@ pic_status pic_set_mcc_background(pic_handle* h, int32_t inst, double density_m3
 
 /* ---- external circuit -------------------------------------------------------
  * The paper puts a serial RC circuit (R = 1 kOhm, C = 1 pF) between the
- * electrodes and treats the voltage as constant on its time scale (Sec. 2).
+ * electrodes and treats the voltage as constant on its time scale (the
+ * paragraph describing the simulated system).
  * This call makes it dynamic: a source V0 charges the anode through R, the gap
  * holds capacitance C, and the charge the anode collects in a step (electrons
  * and ions absorbed there, pic_moments_t.charge_to_anode_C) flows onto it, once
@@ -257,8 +258,9 @@ pic_status pic_set_circuit(pic_handle* h, int32_t inst, double R_ohm, double C_f
 
 /* ---- surface coupling: ions that bombard the cathode ----------------------
  * In the paper's coupled model ions that reach the cathode are handed to the
- * atomistic surface model, where they heat or sputter it (Sec. 2, and the
- * particle transfer of Appendix A). These two calls export them for such a
+ * atomistic surface model, where they heat or sputter it (the PIC/MCC
+ * paragraph after Eq. 4, and the particle transfer of Appendix A). These two
+ * calls export them for such a
  * model: every superparticle of an ion species (PIC_ION) absorbed at the
  * cathode (z^{n+1} < 0, step a7) is logged with its pid, species, the step in
  * which it crossed, the point where its straight path from x^n to x^{n+1}

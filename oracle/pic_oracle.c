@@ -186,10 +186,11 @@ typedef struct {
   uint32_t* log;
   /* ions absorbed at the cathode since the last or_get_hits: the surface
    * coupling output (ions that bombard the cathode are handed to the surface
-   * model, Sec. 2 and Appendix A) */
+   * model: the PIC/MCC paragraph after Eq. 4 and Appendix A) */
   int64_t nhit, hitcap;
   or_hit_t* hit;
-  /* external circuit (the serial RC circuit between the electrodes, Sec. 2):
+  /* external circuit (the serial RC circuit between the electrodes, in the
+   * paragraph describing the simulated system):
    * a source V0 charges the anode through R, the gap holds capacitance C, and
    * the charge the anode collects in a step flows onto it:
    * V <- V + (dt (V0 - V) / R + Q_anode) / C once per step, after the push.

@@ -1,7 +1,7 @@
 """Pins of the oracle's external circuit: the serial RC circuit between the
-electrodes (Sec. 2), read as a source V0 charging the anode through R with the
-gap capacitance C, the charge the anode collects in a step flowing onto it
-once per step after the push. An empty box relaxes towards V0 along the closed
+electrodes (the paragraph describing the simulated system), read as a source
+V0 charging the anode through R with the gap capacitance C, the charge the
+anode collects in a step flowing onto it once per step after the push. An empty box relaxes towards V0 along the closed
 form of that recurrence, and a step whose only event is a known charge landing
 on the anode moves the potential by exactly that charge over C."""
 import numpy as np

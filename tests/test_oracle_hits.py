@@ -1,6 +1,6 @@
 """Pins of the oracle's surface-coupling output: the ions absorbed at the
 cathode, for an MD or heat model of the surface (ions that bombard the cathode
-are handed over to it, Sec. 2 and Appendix A). In a field-free box an ion
+are handed over to it: the PIC/MCC paragraph after Eq. 4 and Appendix A). In a field-free box an ion
 moves in a straight line, so the step of its crossing, the point where its
 path meets z = 0 and its velocity have closed forms; electrons and neutrals
 crossing the same plane are not ions and stay out of the log."""
