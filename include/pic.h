@@ -260,11 +260,11 @@ pic_status pic_set_circuit(pic_handle* h, int32_t inst, double R_ohm, double C_f
  * In the paper's coupled model ions that reach the cathode are handed to the
  * atomistic surface model, where they heat or sputter it (the PIC/MCC
  * paragraph after Eq. 4, and the particle transfer of Appendix A). These two
- * calls export them for such a
- * model: every superparticle of an ion species (PIC_ION) absorbed at the
- * cathode (z^{n+1} < 0, step a7) is logged with its pid, species, the step in
- * which it crossed, the point where its straight path from x^n to x^{n+1}
- * meets the plane z = 0 (x and y wrapped into the box), and v^{n+1/2}.
+ * calls export them for such a model: every superparticle of an ion species
+ * (PIC_ION) absorbed at the cathode (z^{n+1} < 0, step a7) is logged with its
+ * pid, species, the step in which it crossed, the point where its straight
+ * path from x^n to x^{n+1} meets the plane z = 0 (x and y wrapped into the
+ * box), and v^{n+1/2}.
  *
  * pic_set_hit_log: log from the next step on, keeping at most `capacity` hits
  * between two reads (device memory allocated here; 0 switches the log off and
