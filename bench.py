@@ -127,6 +127,81 @@ class ClockSampler:
         return out
 
 
+class NvmlClockSampler:
+    """SM clock and clock-event reasons read through NVML (the driver's library,
+    read-only queries) every millisecond from a thread during the timed region;
+    the device is found by its UUID, so it is the one being timed."""
+
+    # clock-event reason bits of the public NVML API
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown", 0x4: "sw_power_cap"}
+
+    def __init__(self, local):
+        import ctypes
+        import threading
+        self.ct, self.threading = ctypes, threading
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.dev = ctypes.c_void_p()
+        import torch
+        uuid = getattr(torch.cuda.get_device_properties(local), "uuid", None)
+        ok = False
+        if uuid is not None:
+            ok = self.lib.nvmlDeviceGetHandleByUUID(f"GPU-{uuid}".encode(), ctypes.byref(self.dev)) == 0
+        if not ok and self.lib.nvmlDeviceGetHandleByIndex_v2(local, ctypes.byref(self.dev)) != 0:
+            raise RuntimeError("no NVML device")
+        self.samples, self.stop_flag, self.thread = [], False, None
+
+    def _read(self):
+        ct = self.ct
+        sm, smax, r = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        try:
+            if self.lib.nvmlDeviceGetClockInfo(self.dev, 1, ct.byref(sm)) != 0:  # NVML_CLOCK_SM
+                return None
+            self.lib.nvmlDeviceGetMaxClockInfo(self.dev, 1, ct.byref(smax))
+            self.lib.nvmlDeviceGetCurrentClocksEventReasons(self.dev, ct.byref(r))
+        except Exception:
+            return None
+        return sm.value, smax.value, r.value
+
+    def _loop(self):
+        while not self.stop_flag:
+            v = self._read()
+            if v is not None:
+                self.samples.append(v)
+            time.sleep(0.001)
+
+    def start(self):
+        self.samples, self.stop_flag = [], False
+        v = self._read()  # one sample before the region starts
+        if v is not None:
+            self.samples.append(v)
+        self.thread = self.threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        self.stop_flag = True
+        self.thread.join(timeout=5)
+        v = self._read()
+        if v is not None:
+            self.samples.append(v)
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "source": "nvml, 1 ms"}
+        if self.samples:
+            out["sm_mhz"] = statistics.median(x[0] for x in self.samples)
+            out["sm_max_mhz"] = max(x[1] for x in self.samples)
+            out["samples"] = len(self.samples)
+            out["reasons"] = sorted({n for x in self.samples for b, n in self.REASONS.items() if x[2] & b})
+        return out
+
+
+def clock_sampler(local):
+    """NVML sampling where the driver's library loads, else nvidia-smi."""
+    try:
+        return NvmlClockSampler(local)
+    except Exception:
+        return ClockSampler(local)
+
+
 def make_workload(name, seed, n_preload):
     from paper_2606_05893_gb300 import workloads as W
     if name == "c1":
@@ -169,7 +244,7 @@ def run_gpu(args, rank, ws, local):
                     sim.step(1)
         m0 = sim.moments()
         l0, k0 = pkg.pic_launch_count(), pkg.pic_kernel_count()
-        clocks = ClockSampler(local)
+        clocks = clock_sampler(local)
         barrier()
         clocks.start()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -270,7 +345,7 @@ def run_gpu_ensemble(args, rank, ws, local):
 
     p0 = pushed_all()
     l0, k0 = pkg.pic_launch_count(), pkg.pic_kernel_count()
-    clocks = ClockSampler(local)
+    clocks = clock_sampler(local)
     barrier()
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
