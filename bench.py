@@ -460,10 +460,10 @@ def run_reference(args, rank, ws):
     import oracle
     from paper_2606_05893_gb300 import workloads as W
     if args.workload == "c1":
-        wl, sample = make_workload("c1", args.seed, WORKLOADS["c1"][1]), "the whole workload"
+        wl, sample = make_workload("c1", args.seed, WORKLOADS["c1"][1]), "the whole 32x32x64 workload"
     else:
         wl = W.config_scale(seed=args.seed, n_preload=1_250_000, nx=64, ny=64, nz=128, h=2.5e-9)
-        sample = "64x64x128-cell sub-box, 1.25e6 macroparticles"
+        sample = "the 64x64x128-cell sub-box (same h and particle density, 1.25e6 macroparticles)"
     o = oracle.Oracle(wl)
     for _ in range(args.warmup):
         o.step()
@@ -484,8 +484,8 @@ def run_reference(args, rank, ws):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][0], "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} timed oracle steps of the 64x64x128-cell sub-box "
-                                       f"(same h and particle density), started with {n_start} particles"},
+                             "sample": f"{args.steps} timed oracle steps of {sample}, started with "
+                                       f"{n_start} particles"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
