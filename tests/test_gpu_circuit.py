@@ -87,3 +87,32 @@ def test_circuit_switched_on_between_recorded_steps(pkg):
     sim.step(2)
     assert sim.moments()["anode_V"] == v
     sim.close()
+
+
+def test_two_instances_keep_their_own_circuit_and_hit_log(pkg):
+    # one handle, two instances stepping concurrently on their own streams:
+    # instance 0 with a circuit and a hit log, instance 1 with neither
+    from tests._cases import cathode_hits_case
+    wa = W.config_small(seed=43, n_preload=3000)
+    wb, _ = cathode_hits_case(seed=16)
+    wb.phi_anode = 500.0
+    sim = pkg.Simulation([wa, wb], cg_rtol=1e-13, cg_maxit=5000)
+    ra, rb = O.Oracle(wa, cg_rtol=1e-13), O.Oracle(wb, cg_rtol=1e-13)
+    R, Cg, V0 = 1.0e3, 1.0e-15, wa.phi_anode + 20.0
+    pkg.pic_set_circuit(sim.h, 0, R, Cg, V0)
+    ra.set_circuit(R, Cg, V0)
+    pkg.pic_set_hit_log(sim.h, 1, 1024)
+    for _ in range(6):
+        sim.step(1)
+        ra.step(1)
+        rb.step(1)
+    ma, mb = sim.moments(0), sim.moments(1)
+    assert abs(ma["anode_V"] - ra.moments()["anode_V"]) <= 1e-12 * abs(ra.moments()["anode_V"])
+    assert mb["anode_V"] == wb.phi_anode
+    compare_integer_moments(ma, ra.moments())
+    compare_integer_moments(mb, rb.moments())
+    g, o = pkg.pic_get_hits(sim.h, 1), rb.hits()
+    assert g["pid"].size > 0 and np.array_equal(g["pid"], o["pid"])
+    with pytest.raises(pkg.PicError):
+        pkg.pic_get_hits(sim.h, 0)  # instance 0 has no log
+    sim.close()
