@@ -194,9 +194,9 @@ const char* pic_last_error(pic_handle* h);
 /* ---- inspection, test and tuning hooks (synchronous) -----------------------
  * These have no counterpart in the paper: they read or set the state that the
  * steps above work on, so that tests can compare it with the oracle and
- * callers can tune or observe a run. Each returns PIC_EINVAL for a NULL
- * handle, an instance or species index out of range, or a NULL output where
- * one is required, and PIC_ECUDA if a CUDA call fails. */
+ * callers can tune or observe a run. Each that returns a pic_status gives
+ * PIC_EINVAL for a NULL handle, an instance or species index out of range, or
+ * a NULL output where one is required, and PIC_ECUDA if a CUDA call fails. */
 
 /* Number of live superparticles of a species. */
 pic_status pic_get_count(pic_handle* h, int32_t inst, int32_t species, int64_t* n);
