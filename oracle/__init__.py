@@ -56,6 +56,7 @@ class OrMoments(C.Structure):
         ("charge_to_cathode_last", C.c_double), ("charge_to_anode_last", C.c_double),
         ("next_pid", C.c_uint32),
         ("anode_V", C.c_double),
+        ("n_cx", C.c_int64),
     ]
 
 
@@ -386,4 +387,5 @@ class Oracle:
             "charge_to_anode_last": m.charge_to_anode_last,
             "next_pid": m.next_pid,
             "anode_V": m.anode_V,
+            "n_cx": m.n_cx,
         }

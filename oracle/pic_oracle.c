@@ -38,7 +38,11 @@
 #define OR_MAXSRC 16
 
 enum { OR_ELECTRON = 0, OR_NEUTRAL = 1, OR_ION = 2 };
-enum { OR_XS_IONIZATION = 0, OR_XS_ELASTIC = 1 };
+/* Collision channels. Charge exchange is the resonant ion-atom kind named
+ * among the paper's MCC collisions (the PIC/MCC paragraph with Eq. 4): the ion
+ * takes an electron from a neutral of its own element and both keep their
+ * velocities, so a fast neutral and a slow ion come out. */
+enum { OR_XS_IONIZATION = 0, OR_XS_ELASTIC = 1, OR_XS_CX = 2 };
 
 /* Philox counter layout: (pid, step, tag, j). Tags name the purpose of a draw. */
 enum {
@@ -153,6 +157,7 @@ typedef struct {
   double charge_to_cathode_last, charge_to_anode_last; /* C absorbed in the last step */
   uint32_t next_pid;
   double anode_V;  /* anode potential the next solve uses */
+  int64_t n_cx;    /* charge exchanges */
 } or_moments_t;
 
 typedef struct {
@@ -263,7 +268,7 @@ void or_destroy(or_state_t* s) {
 
 int or_add_xsec(or_state_t* s, int kind, int proj, int target, int product, double thr, int n,
                 const double* E, const double* sig) {
-  if (s->nxs >= OR_MAXXS || n < 1) return -1;
+  if (s->nxs >= OR_MAXXS || n < 1 || kind < OR_XS_IONIZATION || kind > OR_XS_CX) return -1;
   or_xsec_t* x = &s->xs[s->nxs++];
   x->kind = kind; x->projectile = proj; x->target = target; x->product = product;
   x->thr = thr; x->n = n;
@@ -728,10 +733,10 @@ double or_sigma(const or_state_t* s, int ch, double E) { return xs_sigma(&s->xs[
 /* a6-a9: push, absorb, MCC, ionization resolve, compaction.                  */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-  int64_t e_idx;    /* electron index in the projectile store */
+  int64_t e_idx;    /* primary's index in the projectile store (electron or ion) */
   int proj;         /* projectile species */
   int ch;           /* channel */
-  int64_t cell;     /* cell of the electron at x^n */
+  int64_t cell;     /* cell of the primary at x^n */
   uint32_t pid;
   double E_eV;      /* pre-collision energy */
   int64_t victim;   /* neutral index in the target store, -1 = suppressed */
@@ -853,13 +858,17 @@ void or_push_collide_resolve(or_state_t* s) {
     }
   }
 
-  /* a9: ionization resolve. Per (target species, cell): events in order of
-   * electron pid take the surviving neutrals whose cell at x^n is that cell,
-   * in increasing order of (Philox victim key, pid). Events left without a
-   * neutral are suppressed. */
+  /* a9: resolve of the events that need a victim neutral (ionization, charge
+   * exchange). Per (target species, cell): events of every channel together,
+   * in order of primary pid, take the surviving neutrals whose cell at x^n is
+   * that cell, in increasing order of (Philox victim key, pid). Events left
+   * without a neutral are suppressed. */
   if (s->bg_density > 0.0) {
-    /* fixed background: ionizations are counted but consume nothing */
-    s->mom.n_ionization += nev;
+    /* fixed background: events are counted but consume or convert nothing */
+    for (int64_t a = 0; a < nev; ++a) {
+      if (s->xs[ev[a].ch].kind == OR_XS_CX) s->mom.n_cx += 1;
+      else s->mom.n_ionization += 1;
+    }
     nev = 0;
   }
   qsort(ev, nev, sizeof(or_event_t), cmp_event_cell_pid);
@@ -894,6 +903,18 @@ void or_push_collide_resolve(or_state_t* s) {
     const or_xsec_t* X = &s->xs[e->ch];
     or_store_t* Ep = &s->st[e->proj];
     or_store_t* T = &s->st[X->target];
+    if (X->kind == OR_XS_CX) {
+      /* the ion becomes a neutral of the product species and the victim
+       * neutral becomes an ion of the projectile species; both keep x^{n+1},
+       * v^{n+1/2} and their pids */
+      int64_t p = e->e_idx, vi = e->victim;
+      store_push(&s->st[X->product], Ep->x[p], Ep->y[p], Ep->z[p], Ep->vx[p], Ep->vy[p], Ep->vz[p], Ep->pid[p]);
+      store_push(Ep, T->x[vi], T->y[vi], T->z[vi], T->vx[vi], T->vy[vi], T->vz[vi], T->pid[vi]);
+      dead[e->proj][p] = 1;
+      dead[X->target][vi] = 1;
+      s->mom.n_cx += 1;
+      continue;
+    }
     const double me = s->sp[e->proj].m;
     int64_t p = e->e_idx;
     draw2 g0 = draw(s->c.seed, e->pid, s->step, TAG_IONIZE, 0);

@@ -31,7 +31,7 @@ AMU = 1.66053906660e-27
 M_CU = 63.546 * AMU
 
 ELECTRON, NEUTRAL, ION = 0, 1, 2
-XS_IONIZATION, XS_ELASTIC = 0, 1
+XS_IONIZATION, XS_ELASTIC, XS_CHARGE_EXCHANGE = 0, 1, 2
 
 # Lotz single-shell ionization constants for Cu (a: generic Lotz constant,
 # q: electrons in the outer shell, P: first ionization energy of Cu).

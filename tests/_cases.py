@@ -79,3 +79,42 @@ def cathode_hits_case(n_ions=40, n_other=20, kmax=12, seed=11):
     vn = np.column_stack([np.zeros((n_other, 2)), -rng.uniform(2e5, 1e6, n_other)])
     wl.preload = [(xo, ve), (xo.copy(), vn), (xi, vi)]
     return wl, k
+
+
+def cx_xsec(sigma, ion=2, neutral=1, E=None):
+    """Resonant charge exchange of species `ion` on `neutral` (the ion leaves as a
+    neutral of the same element); constant sigma, or a table over E (eV)."""
+    if E is None:
+        return W.XSec(W.XS_CHARGE_EXCHANGE, ion, neutral, neutral, 0.0, np.array([1.0]), np.array([sigma]))
+    return W.XSec(W.XS_CHARGE_EXCHANGE, ion, neutral, neutral, 0.0, np.asarray(E, float), np.asarray(sigma, float))
+
+
+def cx_cells_case(seed=21, sigma_cx=1e-10, sigma_ion=None, capacity=1 << 14, with_electrons=False):
+    """Ions and neutrals (weight 1, both electrodes at 0 V) in a few cells: a cell
+    with more neutrals than ions, one with more ions than neutrals, one with
+    ions only, one with neutrals only. sigma_cx = 1e-10 m^2 makes
+    u dt n sigma >= 1e2 for every ion (P = 1 in FP64). With electrons, each ion
+    cell also holds 100 eV electrons (ionization with the same huge sigma when
+    sigma_ion is given), which compete for the same victims."""
+    xs = [cx_xsec(sigma_cx)]
+    if sigma_ion is not None:
+        xs.append(const_xsec(W.XS_IONIZATION, sigma_ion, threshold=W.CU_IONIZATION_EV))
+    wl = bare(nx=8, ny=8, nz=8, h=5e-9, dt=1e-16, weight=1.0, capacity=capacity, seed=seed, xsec=xs)
+    rng = np.random.default_rng(seed)
+    h = wl.h
+
+    def in_cell(n, c):
+        return (np.array(c) + 0.05 + 0.9 * rng.random((n, 3))) * h
+
+    cells = [((2, 3, 4), 60, 90), ((5, 5, 5), 70, 7), ((1, 6, 2), 30, 0), ((6, 1, 3), 0, 40)]
+    xi = np.concatenate([in_cell(ni, c) for c, ni, _ in cells if ni])
+    xn = np.concatenate([in_cell(nn, c) for c, _, nn in cells if nn])
+    vi = isotropic(rng, xi.shape[0], 1.0e4) * rng.uniform(0.5, 1.5, (xi.shape[0], 1))
+    vn = rng.standard_normal(xn.shape) * 500.0
+    if with_electrons:
+        xe = np.concatenate([in_cell(25, c) for c, ni, _ in cells if ni])
+        ve = isotropic(rng, xe.shape[0], speed_of_eV(100.0))
+    else:
+        xe, ve = np.zeros((0, 3)), np.zeros((0, 3))
+    wl.preload = [(xe, ve), (xn, vn), (xi, vi)]
+    return wl
