@@ -64,7 +64,7 @@ typedef enum {
 } pic_status;
 
 enum { PIC_ELECTRON = 0, PIC_NEUTRAL = 1, PIC_ION = 2 };
-enum { PIC_XS_IONIZATION = 0, PIC_XS_ELASTIC = 1 };
+enum { PIC_XS_IONIZATION = 0, PIC_XS_ELASTIC = 1, PIC_XS_CHARGE_EXCHANGE = 2 };
 enum { PIC_FP64 = 0, PIC_MIXED = 1 };
 enum { PIC_WARM_PREV = 0, PIC_WARM_ZERO = 1 };
 enum { PIC_FIELD_RHO = 0, PIC_FIELD_PHI = 1, PIC_FIELD_NCOUNT = 2 };
@@ -84,7 +84,20 @@ typedef struct {
  * clamped to the end values outside [E_0, E_{n-1}].
  * IONIZATION: projectile (electron) + target (neutral) -> 2 projectiles + product
  *   (ion); the weights of projectile, target and product must be equal.
- * ELASTIC: projectile scattered isotropically by target, speed kept. */
+ * ELASTIC: projectile (electron) scattered isotropically by target, speed kept.
+ * CHARGE_EXCHANGE: resonant charge exchange, one of the MCC collisions of the
+ *   PIC/MCC paragraph with Eq. (4): projectile (ion) + target (neutral of the
+ *   same element) -> the ion continues as a neutral of species `product` (which
+ *   must be the target species), the neutral continues as an ion of the
+ *   projectile species; both keep position and velocity. u in Eq. (4) is the
+ *   ion speed (neutral at rest), E = m_ion u^2 / 2. Weights of projectile and
+ *   target must be equal; threshold_eV >= 0. Ionization and charge exchange
+ *   draw their victims from one pool: they must share the target species, and
+ *   the exchange's projectile must be the ionization's product.
+ * The victim of an event (ionization or charge exchange) is a target
+ * superparticle in the primary's cell at x^n: per cell, events in increasing
+ * primary pid take the targets in increasing Philox key; an event left without
+ * one is suppressed. */
 typedef struct {
   int32_t kind;
   int32_t projectile, target, product; /* species indices */
@@ -137,6 +150,7 @@ typedef struct {
                                                      live particle per step) */
   double anode_V;                                 /* anode potential of the next solve (moves
                                                      only with an external circuit) */
+  int64_t charge_exchanges;                       /* cumulative (PIC_XS_CHARGE_EXCHANGE) */
 } pic_moments_t;
 
 /* Phases of a step, for pic_get_phase_times. */

@@ -27,7 +27,7 @@ PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECAPACITY, PIC_ENOCONV, PIC_ECUDA, PIC_ETIME
 STATUS_NAMES = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECAPACITY", -4: "PIC_ENOCONV",
                 -5: "PIC_ECUDA", -6: "PIC_ETIMEOUT", -7: "PIC_ESTATE"}
 PIC_ELECTRON, PIC_NEUTRAL, PIC_ION = 0, 1, 2
-PIC_XS_IONIZATION, PIC_XS_ELASTIC = 0, 1
+PIC_XS_IONIZATION, PIC_XS_ELASTIC, PIC_XS_CHARGE_EXCHANGE = 0, 1, 2
 PIC_FP64, PIC_MIXED = 0, 1
 PIC_WARM_PREV, PIC_WARM_ZERO = 0, 1
 PIC_FIELD_RHO, PIC_FIELD_PHI, PIC_FIELD_NCOUNT = 0, 1, 2
@@ -73,7 +73,7 @@ class pic_moments_t(C.Structure):
                 ("charge_to_cathode_C", C.c_double), ("charge_to_anode_C", C.c_double),
                 ("next_pid", C.c_uint32), ("error_flags", C.c_int32),
                 ("pushed", C.c_int64 * PIC_MAX_SPECIES),
-                ("anode_V", C.c_double)]
+                ("anode_V", C.c_double), ("charge_exchanges", C.c_int64)]
 
 
 PHASES = ["inject", "sort", "deposit", "solve", "efield", "push_electron", "push_ion", "push_neutral", "resolve"]
@@ -447,6 +447,7 @@ class Simulation:
             "kinetic": list(m.kinetic_J[:ns]), "field_energy": m.field_energy_J,
             "charge_to_cathode_last": m.charge_to_cathode_C, "charge_to_anode_last": m.charge_to_anode_C,
             "next_pid": m.next_pid, "error_flags": m.error_flags, "pushed": list(m.pushed[:ns]), "anode_V": m.anode_V,
+            "n_cx": m.charge_exchanges,
         }
 
     def particles(self, sp, inst=0):

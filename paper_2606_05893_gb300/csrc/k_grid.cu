@@ -75,8 +75,9 @@ __global__ void __launch_bounds__(kDepBlock) k_deposit_fp64(DepositArgs<Store64>
       cell = (int)p.cell;
       corner_nodes(g, p.l.i, p.l.j, p.l.k, idx);
       cic_weights(p.l.fx, p.l.fy, p.l.fz, w);
+      const double q = p.pid != kPidDead ? a.qw_h3 : 0.0;  // tombstones carry no charge
 #pragma unroll
-      for (int c = 0; c < 8; ++c) w[c] *= a.qw_h3;
+      for (int c = 0; c < 8; ++c) w[c] *= q;
     }
     warp_combine_cell(cell, w);
     const unsigned peers = __match_any_sync(0xffffffffu, cell);
@@ -99,8 +100,9 @@ __global__ void __launch_bounds__(kDepBlock) k_deposit_mx(DepositArgs<StoreMx> a
     if (valid) {
       cell = a.st.cell[i];
       cic_weights(a.st.ox[i], a.st.oy[i], a.st.oz[i], w);
+      const float qi = a.st.pid[i] != kPidDead ? q : 0.f;  // tombstones carry no charge
 #pragma unroll
-      for (int c = 0; c < 8; ++c) w[c] *= q;
+      for (int c = 0; c < 8; ++c) w[c] *= qi;
     }
     if (warp_run_sum(cell, w) && valid) {
       int ci, cj, ck;
@@ -338,6 +340,7 @@ __global__ void k_step_begin(DevCounters* cnt, StepBegin sb) {
   for (int s = 0; s < sb.nsp; ++s) cnt->n[sb.out[s]][s] = 0;
   cnt->n_events = 0;
   cnt->n_success = 0;
+  cnt->n_success_cx = 0;
   cnt->n_cands = 0;
   cnt->q_cathode_step = 0.0;
   cnt->q_anode_step = 0.0;

@@ -4,7 +4,8 @@
 //   a5+a6+a7+a8 (+a10)   k_push<Store>: field gather at x^n, leapfrog kick/drift,
 //                        absorption at the electrodes, Monte Carlo collisions
 //                        (Eq. 4), warp-aggregated compaction into the other buffer
-//   a9 ionization        k_resolve_rank / k_resolve_apply / k_resolve_cleanup
+//   a9 ionization and    k_resolve_rank / k_resolve_apply / k_resolve_cleanup
+//      charge exchange
 //
 // Collision test (Eq. 4): P = 1 - exp(-u dt sum_c n_c sigma_c(E)), decided with the
 // FP64 uniform U1 of Philox(pid, step, TAG_MCC). Because 1 - exp(-x) <= x and
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
   const long long n = (long long)a.cnt->n[a.cur_in][a.species];
   const uint32_t step = a.cnt->step;
   if (blockIdx.x == 0 && threadIdx.x == 0)
-    a.cnt->pushed[a.species] += (unsigned long long)n - (NEUTRAL ? a.cnt->n_tomb[a.species] : 0ull);
+    a.cnt->pushed[a.species] += (unsigned long long)n - a.cnt->n_tomb[a.species];
   const Grid& g = a.g;
   const float dt_f = (float)g.dt;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
 #pragma unroll
     for (int u = 0; u < kIlp; ++u) {
       if (!valid[u]) continue;
-      if (NEUTRAL && p[u].pid == kPidDead) continue;  // converted neutrals of the last step are dropped here
+      if (p[u].pid == kPidDead) continue;  // neutrals and ions converted in the last step are dropped here
       cell_n[u] = (int)particle_cell(p[u]);
       if (CHARGED) {
         const auto e = p[u].gather(g, a);
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
               s_tn[2][tx] += 1u;
             } else if (a.mc.bg_mode) {
               // fixed-background test mode: counted, nothing consumed or created
-              atomicAdd(&a.cnt->n_ion, 1ull);
+              atomicAdd(a.mc.ch[ch].kind == XS_CHARGE_EXCHANGE ? &a.cnt->n_cx : &a.cnt->n_ion, 1ull);
             } else {
               ionize[u] = true;
               ch_ion[u] = ch;
@@ -464,7 +465,8 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
           ev.pid = p[u].pid;
           ev.cell = (uint32_t)cell_n[u];
           ev.slot = (uint32_t)slot;
-          ev.ch = ch_ion[u];
+          ev.ch = (int16_t)ch_ion[u];
+          ev.kind = (int16_t)a.mc.ch[ch_ion[u]].kind;
           ev.E_eV = a.mc.half_m_over_e * p[u].v2();  // velocity unchanged since the decision
           ev.victim = -1;
           ev.next = atomicExch(&a.ev_head[cell_n[u]], (int)e);
@@ -474,7 +476,7 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
         }
       }
       if (NEUTRAL && a.ev_head != nullptr && a.ev_head[cell_n[u]] >= 0) {
-        // candidate victim of an ionization in its cell at x^n
+        // candidate victim of an ionization or charge exchange in its cell at x^n
         const unsigned int c = atomicAdd(&a.cnt->n_cands, 1u);
         if (c < (unsigned int)a.cand_cap) {
           const uint4 k = draw(a.mc.key, p[u].pid, step, TAG_VICTIM);
@@ -540,7 +542,7 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
 }
 
 // ---------------------------------------------------------------------------
-// a9: ionization resolve
+// a9: resolve of the events that need a victim (ionization, charge exchange)
 // ---------------------------------------------------------------------------
 // Rank of each event among the events of its cell by primary pid, then its
 // victim: the rank-th smallest (key, pid) candidate of that cell, i.e. the
@@ -589,10 +591,15 @@ __device__ __forceinline__ int event_rank(const ResolveArgs& a, uint32_t cell, u
 
 __device__ __forceinline__ void finish_event(const ResolveArgs& a, long long e, uint32_t pid, int victim) {
   a.ev[e].victim = victim;
-  // sort key for the apply order: successful events first, by primary pid
-  a.sort_keys[e] = ((unsigned long long)(victim < 0 ? 1 : 0) << 32) | pid;
+  // sort key for the apply order: successful ionizations by primary pid, then
+  // successful charge exchanges by primary pid, then the suppressed events
+  const bool cx = a.ev[e].kind == XS_CHARGE_EXCHANGE;
+  a.sort_keys[e] = ((unsigned long long)(victim < 0 ? 1 : 0) << 33) | ((unsigned long long)(cx ? 1 : 0) << 32) | pid;
   a.sort_vals[e] = (uint32_t)e;
-  if (victim >= 0) atomicAdd(&a.cnt->n_success, 1u);
+  if (victim >= 0) {
+    atomicAdd(&a.cnt->n_success, 1u);
+    if (cx) atomicAdd(&a.cnt->n_success_cx, 1u);
+  }
 }
 
 __global__ void __launch_bounds__(kRankWarps * 32) k_resolve_rank(ResolveArgs a) {
@@ -653,16 +660,50 @@ __global__ void __launch_bounds__(kRankWarps * 32) k_resolve_rank(ResolveArgs a)
   }
 }
 
+// Successful events in apply order: ionizations (rank r < nion) then charge
+// exchanges. Every victim neutral becomes an ion (slot ni_out + r). An
+// ionization scales its primary electron and appends a secondary (pid and
+// slot from r, so secondaries take pids in increasing primary pid); an exchange
+// turns its primary ion into a neutral (slot nn_out + r - nion) and takes back
+// the charge the push deposited for it at x^{n+1}.
 template <class S>
 __global__ void k_resolve_apply(ApplyArgs<S> a) {
   const unsigned int ns = a.cnt->n_success;
-  const unsigned int ne = min(a.cnt->n_events, (unsigned int)a.ev_cap);
-  const unsigned long long ne_out = a.cnt->n[a.e_out][a.e_species];
+  const unsigned int nion = ns - a.cnt->n_success_cx;
+  const unsigned long long ne_out = a.e_species >= 0 ? a.cnt->n[a.e_out][a.e_species] : 0ull;
   const unsigned long long ni_out = a.cnt->n[a.i_out][a.i_species];
+  const unsigned long long nn_out = a.cnt->n[a.n_out][a.n_species];
   const uint32_t pid0 = a.cnt->next_pid;
   for (long long r = gtid(); r < ns; r += gstride()) {
     const Event ev = a.ev[a.sorted_vals[r]];
     const Cand cd = a.cand[ev.victim];
+    // victim neutral -> ion (position x^{n+1}, velocity and pid kept)
+    const auto vn = store_read(a.n_st, a.g, cd.slot);
+    const unsigned long long is = ni_out + r;
+    if (is < (unsigned long long)a.i_cap) {
+      store_write_p(a.i_st, is, vn);
+      if (a.nd.on) deposit_one(a.g, vn, a.nd.rho32, a.nd.rho64, a.nd.qw_h3[a.i_species]);
+    } else {
+      atomicOr(&a.cnt->error, ERR_CAPACITY);
+    }
+    store_kill(a.n_st, cd.slot);
+    if (a.nd.on) atomicSub(&a.nd.ncount[a.n_species][cell_now(a.g, vn)], 1);
+    if (r >= nion) {
+      // charge exchange: the primary ion continues as a neutral
+      const auto pi = store_read(a.i_st, a.g, ev.slot);
+      store_kill(a.i_st, ev.slot);
+      const unsigned long long os = nn_out + (r - nion);
+      if (os < (unsigned long long)a.n_cap) {
+        store_write_p(a.n_st, os, pi);
+        if (a.nd.on) {
+          deposit_one(a.g, pi, a.nd.rho32, a.nd.rho64, -a.nd.qw_h3[a.i_species]);
+          atomicAdd(&a.nd.ncount[a.n_species][cell_now(a.g, pi)], 1);
+        }
+      } else {
+        atomicOr(&a.cnt->error, ERR_CAPACITY);
+      }
+      continue;
+    }
     const XsDev& X = a.ch[ev.ch];
     const uint4 g0 = draw(a.key, ev.pid, a.cnt->step, TAG_IONIZE, 0);
     const uint4 g1 = draw(a.key, ev.pid, a.cnt->step, TAG_IONIZE, 1);
@@ -691,39 +732,34 @@ __global__ void k_resolve_apply(ApplyArgs<S> a) {
     } else {
       atomicOr(&a.cnt->error, ERR_CAPACITY);
     }
-    // victim neutral -> ion (position x^{n+1}, velocity and pid kept)
-    const auto vn = store_read(a.n_st, a.g, cd.slot);
-    const unsigned long long is = ni_out + r;
-    if (is < (unsigned long long)a.i_cap) {
-      store_write_p(a.i_st, is, vn);
-      if (a.nd.on) deposit_one(a.g, vn, a.nd.rho32, a.nd.rho64, a.nd.qw_h3[a.i_species]);
-    } else {
-      atomicOr(&a.cnt->error, ERR_CAPACITY);
-    }
-    store_kill(a.n_st, cd.slot);
-    if (a.nd.on) atomicSub(&a.nd.ncount[a.n_species][cell_now(a.g, vn)], 1);
     if (a.log) {
       a.log[3 * r] = ev.pid;
       a.log[3 * r + 1] = vn.pid;
       a.log[3 * r + 2] = spid;
     }
   }
-  (void)ne;
 }
 
-__global__ void k_resolve_commit(DevCounters* cnt, int e_out, int e_sp, long long e_cap, int i_out, int i_sp,
-                                 long long i_cap, int n_sp, int ev_cap) {
+__global__ void k_resolve_commit(DevCounters* cnt, ResolveCommit c) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const unsigned int ne = min(cnt->n_events, (unsigned int)ev_cap);
+  const unsigned int ne = min(cnt->n_events, (unsigned int)c.ev_cap);
   const unsigned int ns = cnt->n_success;
-  cnt->n_ion += ns;
+  const unsigned int ncx = cnt->n_success_cx;
+  const unsigned int nion = ns - ncx;
+  cnt->n_ion += nion;
+  cnt->n_cx += ncx;
   cnt->n_supp += ne - ns;
-  unsigned long long a = cnt->n[e_out][e_sp] + ns;
-  cnt->n[e_out][e_sp] = a > (unsigned long long)e_cap ? e_cap : a;
-  unsigned long long b = cnt->n[i_out][i_sp] + ns;
-  cnt->n[i_out][i_sp] = b > (unsigned long long)i_cap ? i_cap : b;
-  cnt->n_tomb[n_sp] = ns;
-  cnt->next_pid += ns;
+  if (c.e_sp >= 0) {
+    const unsigned long long a = cnt->n[c.e_out][c.e_sp] + nion;
+    cnt->n[c.e_out][c.e_sp] = a > (unsigned long long)c.e_cap ? c.e_cap : a;
+  }
+  const unsigned long long b = cnt->n[c.i_out][c.i_sp] + ns;
+  cnt->n[c.i_out][c.i_sp] = b > (unsigned long long)c.i_cap ? c.i_cap : b;
+  const unsigned long long d = cnt->n[c.n_out][c.n_sp] + ncx;
+  cnt->n[c.n_out][c.n_sp] = d > (unsigned long long)c.n_cap ? c.n_cap : d;
+  cnt->n_tomb[c.n_sp] = ns;
+  cnt->n_tomb[c.i_sp] = ncx;
+  cnt->next_pid += nion;
 }
 
 __global__ void k_resolve_cleanup(ResolveArgs a) {
@@ -770,9 +806,8 @@ template <class S>
 void launch_resolve_apply(const ApplyArgs<S>& a, int grid, cudaStream_t st) {
   PIC_LAUNCH(grid, 256, 0, st, k_resolve_apply<S>)(a);
 }
-void launch_resolve_commit(DevCounters* cnt, int e_out, int e_sp, long long e_cap, int i_out, int i_sp,
-                           long long i_cap, int n_sp, int ev_cap, cudaStream_t st) {
-  PIC_LAUNCH(1, 1, 0, st, k_resolve_commit)(cnt, e_out, e_sp, e_cap, i_out, i_sp, i_cap, n_sp, ev_cap);
+void launch_resolve_commit(DevCounters* cnt, const ResolveCommit& c, cudaStream_t st) {
+  PIC_LAUNCH(1, 1, 0, st, k_resolve_commit)(cnt, c);
 }
 
 template void launch_inject<Store64>(const InjectArgs<Store64>&, int, cudaStream_t);

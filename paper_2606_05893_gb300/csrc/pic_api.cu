@@ -165,8 +165,11 @@ struct Instance {
   bool phi64_stale = false;  // MIXED: phi (FP64) not yet rebuilt from the solver's float-float state
   float* acc8 = nullptr;   // MIXED: cell-centric deposit accumulator (8 per cell)
   int32_t* ncount[kMaxSpecies]{};
-  // ionization bookkeeping
+  // bookkeeping of the events that need a victim
   int ion_ch = -1;  // index into xs of the ionization channel
+  int cx_ch = -1;   // index into xs of the charge-exchange channel
+  bool events() const { return ion_ch >= 0 || cx_ch >= 0; }
+  int event_target() const { return ion_ch >= 0 ? xs[ion_ch].c.target : (cx_ch >= 0 ? xs[cx_ch].c.target : -1); }
   int ev_cap = 0, cand_cap = 0;
   Event* ev = nullptr;
   Cand* cand = nullptr;
@@ -363,14 +366,20 @@ pic_status validate(pic_handle* h, const pic_instance_cfg& c, int idx) {
     if (p.role == PIC_NEUTRAL && p.charge_C != 0.0)
       return fail(h, PIC_EINVAL, "instance %d species %d: neutral species must have zero charge", idx, s);
   }
-  int nion = 0;
+  int nion = 0, ncx = 0, ion_k = -1, cx_k = -1;
   for (int x = 0; x < c.nxsec; ++x) {
     const pic_xsec& X = c.xsec[x];
-    if (X.kind != PIC_XS_IONIZATION && X.kind != PIC_XS_ELASTIC) return fail(h, PIC_EINVAL, "xsec %d: bad kind", x);
+    if (X.kind != PIC_XS_IONIZATION && X.kind != PIC_XS_ELASTIC && X.kind != PIC_XS_CHARGE_EXCHANGE)
+      return fail(h, PIC_EINVAL, "xsec %d: bad kind", x);
     if (X.projectile < 0 || X.projectile >= c.nspecies || X.target < 0 || X.target >= c.nspecies)
       return fail(h, PIC_EINVAL, "xsec %d: bad species index", x);
-    if (c.species[X.projectile].role != PIC_ELECTRON || c.species[X.target].role != PIC_NEUTRAL)
-      return fail(h, PIC_EINVAL, "xsec %d: projectile must be an electron species, target a neutral species", x);
+    if (c.species[X.target].role != PIC_NEUTRAL) return fail(h, PIC_EINVAL, "xsec %d: target must be a neutral species", x);
+    if (X.kind == PIC_XS_CHARGE_EXCHANGE) {
+      if (c.species[X.projectile].role != PIC_ION)
+        return fail(h, PIC_EINVAL, "xsec %d: charge-exchange projectile must be an ion species", x);
+    } else if (c.species[X.projectile].role != PIC_ELECTRON) {
+      return fail(h, PIC_EINVAL, "xsec %d: projectile must be an electron species", x);
+    }
     if (X.n < 1 || !X.E_eV || !X.sigma_m2) return fail(h, PIC_EINVAL, "xsec %d: empty table", x);
     for (int i = 0; i < X.n; ++i) {
       if (!(X.sigma_m2[i] >= 0) || !std::isfinite(X.sigma_m2[i])) return fail(h, PIC_EINVAL, "xsec %d: sigma must be >= 0", x);
@@ -384,9 +393,24 @@ pic_status validate(pic_handle* h, const pic_instance_cfg& c, int idx) {
       if (c.species[X.target].weight != w || c.species[X.product].weight != w)
         return fail(h, PIC_EINVAL, "xsec %d: ionization needs equal weights of projectile, target, product", x);
       if (!(X.threshold_eV > 0)) return fail(h, PIC_EINVAL, "xsec %d: ionization threshold must be > 0", x);
+      ion_k = x;
+    }
+    if (X.kind == PIC_XS_CHARGE_EXCHANGE) {
+      ++ncx;
+      if (X.product != X.target)
+        return fail(h, PIC_EINVAL, "xsec %d: charge-exchange product must be the target species (resonant)", x);
+      if (c.species[X.target].weight != c.species[X.projectile].weight)
+        return fail(h, PIC_EINVAL, "xsec %d: charge exchange needs equal weights of projectile and target", x);
+      if (!(X.threshold_eV >= 0)) return fail(h, PIC_EINVAL, "xsec %d: threshold must be >= 0", x);
+      cx_k = x;
     }
   }
   if (nion > 1) return fail(h, PIC_EINVAL, "instance %d: at most one ionization channel is supported", idx);
+  if (ncx > 1) return fail(h, PIC_EINVAL, "instance %d: at most one charge-exchange channel is supported", idx);
+  if (ion_k >= 0 && cx_k >= 0 &&
+      (c.xsec[cx_k].target != c.xsec[ion_k].target || c.xsec[cx_k].projectile != c.xsec[ion_k].product))
+    return fail(h, PIC_EINVAL,
+                "instance %d: charge exchange must act on the ionization's target with its product ion", idx);
   return PIC_OK;
 }
 
@@ -490,6 +514,7 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
     X.c.sigma_m2 = nullptr;
     I->xs.push_back(X);
     if (X.c.kind == PIC_XS_IONIZATION) I->ion_ch = x;
+    if (X.c.kind == PIC_XS_CHARGE_EXCHANGE) I->cx_ch = x;
   }
   for (auto& X : I->xs) {
     pic_status st = build_xsec(h, X);
@@ -558,13 +583,14 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
   CK(h, dalloc(&I->phi, g.nnode));
   CK(h, cudaMemset(I->phi, 0, sizeof(double) * g.nnode));
 
-  // events: bounded by the electron population; candidates by the neutral population
+  // events: bounded by the projectile populations; candidates by the neutral population
   long long ecap = 1, ncap = 1;
   for (int s = 0; s < I->nsp; ++s) {
     if (I->species[s].role == PIC_ELECTRON) ecap = std::max(ecap, I->cap[s]);
+    if (I->species[s].role == PIC_ION && I->cx_ch >= 0) ecap = std::max(ecap, I->cap[s]);
     if (I->species[s].role == PIC_NEUTRAL) ncap = std::max(ncap, I->cap[s]);
   }
-  if (I->ion_ch >= 0) {
+  if (I->events()) {
     I->ev_cap = (int)std::min<long long>(std::max<long long>(ecap / 16, 4096), 1 << 24);
     I->cand_cap = (int)std::min<long long>(std::max<long long>(ncap / 4, 16384), 1 << 26);
     CK(h, dalloc(&I->ev, I->ev_cap));
@@ -862,8 +888,8 @@ pic_status step_instance(pic_handle* h, Instance* I) {
       a.nd = next_deposit_of(I, true);
       if (I->species[s].role == PIC_ION) a.hits = I->hits;
       const bool mcc = a.mc.nch > 0;
-      if (neutral && I->ion_ch < 0) {
-        a.ev_head = nullptr;
+      if (neutral && s != I->event_target()) {
+        a.ev_head = nullptr;  // no victims in this species
       }
       const int role = I->species[s].role;
       T.begin(role == PIC_ELECTRON ? PIC_PH_PUSH_ELECTRON : (role == PIC_ION ? PIC_PH_PUSH_ION : PIC_PH_PUSH_NEUTRAL), st);
@@ -872,10 +898,9 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     }
   }
 
-  // a9 ionization resolve
-  if (I->ion_ch >= 0) {
+  // a9 resolve of ionizations and charge exchanges
+  if (I->events()) {
     T.begin(PIC_PH_RESOLVE, st);
-    const HostXsec& X = I->xs[I->ion_ch];
     ResolveArgs r{};
     r.cnt = I->cnt;
     r.ev = I->ev;
@@ -897,16 +922,26 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     ap.ev_cap = I->ev_cap;
     ap.cand = I->cand;
     ap.sorted_vals = where ? I->evsort.vb : I->evsort.va;
-    McArgs m = mc_args(I, X.c.projectile);
-    for (int a2 = 0; a2 < kMaxXsec; ++a2) ap.ch[a2] = m.ch[a2];
     ap.key = key;
-    const int e_sp = X.c.projectile, n_sp = X.c.target, i_sp = X.c.product;
-    ap.e_st = store_of<S>(I, e_sp, I->cur[e_sp] ^ 1);
-    ap.e_out = I->cur[e_sp] ^ 1;
+    // the ionization fixes electrons, victims and ions; without it the exchange
+    // fixes victims and ions (validation makes the two agree when both exist)
+    const HostXsec* XI = I->ion_ch >= 0 ? &I->xs[I->ion_ch] : nullptr;
+    const HostXsec& XV = XI ? *XI : I->xs[I->cx_ch];
+    const int e_sp = XI ? XI->c.projectile : -1;
+    const int n_sp = XV.c.target;
+    const int i_sp = XI ? XI->c.product : XV.c.projectile;
     ap.e_species = e_sp;
-    ap.e_cap = I->cap[e_sp];
-    ap.e_mass = I->species[e_sp].mass_kg;
+    if (XI) {
+      McArgs m = mc_args(I, e_sp);
+      for (int a2 = 0; a2 < kMaxXsec; ++a2) ap.ch[a2] = m.ch[a2];
+      ap.e_st = store_of<S>(I, e_sp, I->cur[e_sp] ^ 1);
+      ap.e_out = I->cur[e_sp] ^ 1;
+      ap.e_cap = I->cap[e_sp];
+      ap.e_mass = I->species[e_sp].mass_kg;
+    }
     ap.n_st = store_of<S>(I, n_sp, I->cur[n_sp] ^ 1);
+    ap.n_out = I->cur[n_sp] ^ 1;
+    ap.n_cap = I->cap[n_sp];
     ap.i_st = store_of<S>(I, i_sp, I->cur[i_sp] ^ 1);
     ap.i_out = I->cur[i_sp] ^ 1;
     ap.i_species = i_sp;
@@ -915,7 +950,18 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     ap.nd = next_deposit_of(I, true);
     ap.n_species = n_sp;
     launch_resolve_apply<S>(ap, rb, st);
-    launch_resolve_commit(I->cnt, ap.e_out, e_sp, ap.e_cap, ap.i_out, i_sp, ap.i_cap, n_sp, I->ev_cap, st);
+    ResolveCommit rc{};
+    rc.e_out = ap.e_out;
+    rc.e_sp = e_sp;
+    rc.e_cap = ap.e_cap;
+    rc.i_out = ap.i_out;
+    rc.i_sp = i_sp;
+    rc.i_cap = ap.i_cap;
+    rc.n_out = ap.n_out;
+    rc.n_sp = n_sp;
+    rc.n_cap = ap.n_cap;
+    rc.ev_cap = I->ev_cap;
+    launch_resolve_commit(I->cnt, rc, st);
     launch_resolve_cleanup(r, rb, st);
     T.end(st);
   }
@@ -1329,6 +1375,7 @@ pic_status pic_moments(pic_handle* h, int32_t inst, pic_moments_t* out) {
   out->ionizations = (int64_t)c.n_ion;
   out->elastic = (int64_t)c.n_el;
   out->suppressed = (int64_t)c.n_supp;
+  out->charge_exchanges = (int64_t)c.n_cx;
   out->cg_iters = I->last.iters;
   out->cg_resid_rel = I->last.resid_rel;
   out->total_charge_C = q;
@@ -1524,7 +1571,7 @@ pic_status pic_get_ionization_log(pic_handle* h, int32_t inst, int64_t cap, int6
   if (!n) return fail(h, PIC_EINVAL, "n is NULL");
   st = sync_counters(h, I);
   if (st != PIC_OK) return st;
-  const long long ns = I->ion_ch >= 0 ? I->host_cnt->n_success : 0;
+  const long long ns = I->ion_ch >= 0 ? (long long)I->host_cnt->n_success - I->host_cnt->n_success_cx : 0;
   *n = ns;
   if (ns == 0) return PIC_OK;
   if (!rows || cap < ns) return fail(h, PIC_EINVAL, "cap %lld below %lld rows", (long long)cap, ns);

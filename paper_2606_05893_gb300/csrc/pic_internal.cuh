@@ -25,7 +25,7 @@ constexpr double kEps0 = 8.8541878128e-12;
 constexpr double kKB = 1.380649e-23;
 constexpr double kPi = 3.14159265358979323846;
 
-constexpr uint32_t kPidDead = 0xFFFFFFFFu;  // tombstone of a converted neutral
+constexpr uint32_t kPidDead = 0xFFFFFFFFu;  // tombstone of a converted neutral or exchanged ion
 
 // Philox counter layout (pid, step, tag, j); tags give each draw a purpose.
 enum : uint32_t {
@@ -40,7 +40,7 @@ enum : uint32_t {
 };
 
 enum : int { ROLE_ELECTRON = 0, ROLE_NEUTRAL = 1, ROLE_ION = 2 };
-enum : int { XS_IONIZATION = 0, XS_ELASTIC = 1 };
+enum : int { XS_IONIZATION = 0, XS_ELASTIC = 1, XS_CHARGE_EXCHANGE = 2 };
 
 // device error bits (DevCounters::error)
 enum : int { ERR_CAPACITY = 1, ERR_EVENTS = 2, ERR_TIMEOUT = 4, ERR_NOCONV = 8, ERR_BOUNDS = 16 };
@@ -169,10 +169,11 @@ struct DevCounters {
   unsigned long long abs_cathode[kMaxSpecies], abs_anode[kMaxSpecies];
   double abs_energy_cathode[kMaxSpecies], abs_energy_anode[kMaxSpecies];
   double q_cathode_step, q_anode_step;
-  unsigned long long n_ion, n_el, n_supp;
+  unsigned long long n_ion, n_el, n_supp, n_cx;
   unsigned long long n_tomb[kMaxSpecies];
-  unsigned int n_events;   // ionization events this step
-  unsigned int n_success;  // successful ionizations this step
+  unsigned int n_events;      // events needing a victim this step (ionization, charge exchange)
+  unsigned int n_success;     // of which found a victim
+  unsigned int n_success_cx;  // of which charge exchanges
   unsigned int n_cands;    // victim candidates this step
   unsigned int next_pid;
   int error;
@@ -226,10 +227,11 @@ inline void count_graph(unsigned long long kernels) {
 
 // Ionization event (one per ionizing collision, before victim choice)
 struct Event {
-  uint32_t pid;      // primary electron pid
+  uint32_t pid;      // primary pid (electron or ion)
   uint32_t cell;     // primary's cell at x^n
-  uint32_t slot;     // primary's slot in the new electron buffer
-  int32_t ch;        // channel
+  uint32_t slot;     // primary's slot in its species' new buffer
+  int16_t ch;        // channel slot among the primary species' channels
+  int16_t kind;      // XS_IONIZATION | XS_CHARGE_EXCHANGE
   double E_eV;       // pre-collision energy
   int32_t next;      // next event in the same cell (linked list), -1 = end
   int32_t victim;    // victim candidate index, -1 = suppressed

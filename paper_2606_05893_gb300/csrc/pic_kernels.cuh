@@ -598,17 +598,30 @@ struct ApplyArgs {
   const uint32_t* sorted_vals;
   XsDev ch[kMaxXsec];
   uint2 key;
-  S e_st;
+  S e_st;                  // ionization: electrons (e_species < 0 without an ionization channel)
   int e_out, e_species;
   long long e_cap;
   double e_mass;
-  S n_st;
-  S i_st;
+  S n_st;                  // the target neutrals (victims; exchanged ions land here)
+  int n_out;
+  long long n_cap;
+  S i_st;                  // the ions (victims land here; exchanging ions leave)
   int i_out, i_species;
   long long i_cap;
   uint32_t* log;
   NextDeposit nd;
   int n_species;
+};
+
+// Buffers and capacities the resolve commit updates (species < 0: absent).
+struct ResolveCommit {
+  int e_out, e_sp;
+  long long e_cap;
+  int i_out, i_sp;
+  long long i_cap;
+  int n_out, n_sp;
+  long long n_cap;
+  int ev_cap;
 };
 
 template <class S>
@@ -638,8 +651,7 @@ void launch_resolve_rank(const ResolveArgs& a, int grid, cudaStream_t st);
 void launch_resolve_cleanup(const ResolveArgs& a, int grid, cudaStream_t st);
 template <class S>
 void launch_resolve_apply(const ApplyArgs<S>& a, int grid, cudaStream_t st);
-void launch_resolve_commit(DevCounters* cnt, int e_out, int e_sp, long long e_cap, int i_out, int i_sp,
-                           long long i_cap, int n_sp, int ev_cap, cudaStream_t st);
+void launch_resolve_commit(DevCounters* cnt, const ResolveCommit& c, cudaStream_t st);
 
 template <class S>
 void launch_deposit(const DepositArgs<S>& a, int grid, cudaStream_t st);

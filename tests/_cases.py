@@ -89,7 +89,8 @@ def cx_xsec(sigma, ion=2, neutral=1, E=None):
     return W.XSec(W.XS_CHARGE_EXCHANGE, ion, neutral, neutral, 0.0, np.asarray(E, float), np.asarray(sigma, float))
 
 
-def cx_cells_case(seed=21, sigma_cx=1e-10, sigma_ion=None, capacity=1 << 14, with_electrons=False):
+def cx_cells_case(seed=21, sigma_cx=1e-10, sigma_ion=None, capacity=1 << 14, with_electrons=False, n_dense_i=60,
+                  n_dense_n=90):
     """Ions and neutrals (weight 1, both electrodes at 0 V) in a few cells: a cell
     with more neutrals than ions, one with more ions than neutrals, one with
     ions only, one with neutrals only. sigma_cx = 1e-10 m^2 makes
@@ -106,7 +107,7 @@ def cx_cells_case(seed=21, sigma_cx=1e-10, sigma_ion=None, capacity=1 << 14, wit
     def in_cell(n, c):
         return (np.array(c) + 0.05 + 0.9 * rng.random((n, 3))) * h
 
-    cells = [((2, 3, 4), 60, 90), ((5, 5, 5), 70, 7), ((1, 6, 2), 30, 0), ((6, 1, 3), 0, 40)]
+    cells = [((2, 3, 4), n_dense_i, n_dense_n), ((5, 5, 5), 70, 7), ((1, 6, 2), 30, 0), ((6, 1, 3), 0, 40)]
     xi = np.concatenate([in_cell(ni, c) for c, ni, _ in cells if ni])
     xn = np.concatenate([in_cell(nn, c) for c, _, nn in cells if nn])
     vi = isotropic(rng, xi.shape[0], 1.0e4) * rng.uniform(0.5, 1.5, (xi.shape[0], 1))

@@ -37,7 +37,7 @@ def rel_inf(a, b):
 
 
 INT_KEYS = ("count", "injected", "abs_cathode", "abs_anode", "n_ionization", "n_elastic", "n_suppressed",
-            "next_pid")
+            "n_cx", "next_pid")
 
 
 def compare_integer_moments(mg, mo):
