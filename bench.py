@@ -202,13 +202,28 @@ def clock_sampler(local):
         return ClockSampler(local)
 
 
-def make_workload(name, seed, n_preload):
+def with_cx(wl, cx_sigma):
+    """The workload with resonant charge exchange Cu+ + Cu added at a constant
+    cross-section (m^2); unchanged for cx_sigma = 0."""
+    if not cx_sigma:
+        return wl
+    import numpy as np
+    from paper_2606_05893_gb300 import workloads as W
+    wl.xsec = list(wl.xsec) + [W.XSec(W.XS_CHARGE_EXCHANGE, 2, 1, 1, 0.0, np.array([1.0]), np.array([cx_sigma]))]
+    return wl
+
+
+def cx_label(cx_sigma):
+    return f" + charge exchange Cu+ + Cu at a constant {cx_sigma:g} m2" if cx_sigma else ""
+
+
+def make_workload(name, seed, n_preload, cx_sigma=0.0):
     from paper_2606_05893_gb300 import workloads as W
     if name == "c1":
-        return W.config_small(seed=42 + seed, n_preload=n_preload)
+        return with_cx(W.config_small(seed=42 + seed, n_preload=n_preload), cx_sigma)
     if name == "c3":
-        return W.config_mixed_large(seed=seed, n_preload=n_preload)
-    return W.config_scale(seed=seed, n_preload=n_preload)
+        return with_cx(W.config_mixed_large(seed=seed, n_preload=n_preload), cx_sigma)
+    return with_cx(W.config_scale(seed=seed, n_preload=n_preload), cx_sigma)
 
 
 def run_gpu(args, rank, ws, local):
@@ -226,7 +241,7 @@ def run_gpu(args, rank, ws, local):
             dist.barrier()
         torch.cuda.synchronize()
 
-    wl = make_workload(args.workload, args.seed + rank, args.n_preload)
+    wl = make_workload(args.workload, args.seed + rank, args.n_preload, args.cx_sigma)
     results = {}
     precisions = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
     stream = torch.cuda.current_stream()
@@ -422,18 +437,18 @@ def reduce_over_ranks(r, dist, device):
                 e2e_s=red(r["e2e_s"], dist.ReduceOp.MAX), e2e_pushes=red(r["e2e_pushes"], dist.ReduceOp.SUM))
 
 
-def cpu_baseline(seconds_target=15.0, steps_max=6, workload="c2"):
+def cpu_baseline(seconds_target=15.0, steps_max=6, workload="c2", cx_sigma=0.0):
     """The FP64 oracle as it stands, single thread, on a bounded sample of the workload:
     the 64x64x128-cell sub-box (1/8 of the volume, same h and particle density), or
     for the small 32x32x64 workload the workload itself."""
     import oracle
     from paper_2606_05893_gb300 import workloads as W
     if workload == "c1":
-        wl = make_workload("c1", 0, WORKLOADS["c1"][1])
+        wl = make_workload("c1", 0, WORKLOADS["c1"][1], cx_sigma)
         steps_max = 1000
         what = "the 32x32x64 workload itself (1e4 macroparticles)"
     else:
-        wl = W.config_scale(seed=0, n_preload=1_250_000, nx=64, ny=64, nz=128, h=2.5e-9)
+        wl = with_cx(W.config_scale(seed=0, n_preload=1_250_000, nx=64, ny=64, nz=128, h=2.5e-9), cx_sigma)
         what = "the 64x64x128-cell sub-box (same h = 2.5 nm and particle density, 1.25e6 macroparticles)"
     o = oracle.Oracle(wl)
     t0 = time.perf_counter()
@@ -460,9 +475,10 @@ def run_reference(args, rank, ws):
     import oracle
     from paper_2606_05893_gb300 import workloads as W
     if args.workload == "c1":
-        wl, sample = make_workload("c1", args.seed, WORKLOADS["c1"][1]), "the whole 32x32x64 workload"
+        wl, sample = make_workload("c1", args.seed, WORKLOADS["c1"][1], args.cx_sigma), "the whole 32x32x64 workload"
     else:
-        wl = W.config_scale(seed=args.seed, n_preload=1_250_000, nx=64, ny=64, nz=128, h=2.5e-9)
+        wl = with_cx(W.config_scale(seed=args.seed, n_preload=1_250_000, nx=64, ny=64, nz=128, h=2.5e-9),
+                     args.cx_sigma)
         sample = "the 64x64x128-cell sub-box (same h and particle density, 1.25e6 macroparticles)"
     o = oracle.Oracle(wl)
     for _ in range(args.warmup):
@@ -482,7 +498,8 @@ def run_reference(args, rank, ws):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][0], "sample": sample},
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][0] + cx_label(args.cx_sigma),
+                                            "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} timed oracle steps of {sample}, started with "
                                        f"{n_start} particles"},
@@ -508,6 +525,9 @@ def main():
     ap.add_argument("--e2e-batch", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune-window", type=int, default=50, help="steps per sort-interval candidate (c4)")
+    ap.add_argument("--cx-sigma", type=float, default=0.0,
+                    help="add resonant charge exchange Cu+ + Cu at this constant cross-section (m^2) "
+                         "to c1-c3; 0 (default): off, the headline workload")
     args = ap.parse_args()
     if args.n_preload is None:
         args.n_preload = WORKLOADS[args.workload][1]
@@ -515,6 +535,10 @@ def main():
         args.precision = "mixed"
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
+    if args.cx_sigma and args.workload == "c4":
+        ap.error("--cx-sigma applies to c1-c3")
+    if args.cx_sigma < 0:
+        ap.error("--cx-sigma must be >= 0")
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, ws)
@@ -553,7 +577,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": a["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload][0], "precision": head, "n_preload": args.n_preload,
+            "config": {"workload": WORKLOADS[args.workload][0] + cx_label(args.cx_sigma), "precision": head,
+                       "n_preload": args.n_preload,
                        "grid": [wl.nx, wl.ny, wl.nz], "h": wl.h, "dt": wl.dt,
                        "parallelism": f"replicas x{ws}",
                        "l2": "inputs larger than L2 (particle stores of 0.3 GB and more per buffer)",
@@ -569,7 +594,7 @@ def main():
                               "phase_ms_per_step": {k: round(v[0] / max(f["prof_steps"], 1), 4) for k, v in fph.items()},
                               "push_kernel_ms": fpush_ms / max(fpush_n, 1), "clocks": f["clocks"]}
     if not args.no_cpu_baseline and ws >= 1:
-        line["cpu_baseline"] = cpu_baseline(workload=args.workload)
+        line["cpu_baseline"] = cpu_baseline(workload=args.workload, cx_sigma=args.cx_sigma)
     print(json.dumps(line), flush=True)
     return 0
 
