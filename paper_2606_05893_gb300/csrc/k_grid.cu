@@ -541,52 +541,80 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;
 }
 
-__device__ __forceinline__ double v2_of(const Store64& s, long long i) {
-  return s.vx[i] * s.vx[i] + s.vy[i] * s.vy[i] + s.vz[i] * s.vz[i];
-}
-__device__ __forceinline__ double v2_of(const StoreMx& s, long long i) {
-  const double a = s.vx[i], b = s.vy[i], c = s.vz[i];
-  return a * a + b * b + c * c;
-}
-template <class S>
-__global__ void k_kinetic(S st, const unsigned long long* n_dev, long long n_max, double* out) {
+// Sum of |v|^2 over the live particles of one store. FP64 store: in FP64. Mixed
+// store (FP32 velocities): |v|^2 in FP32 (relative rounding ~1e-7, the
+// velocities' own precision), summed in FP32 over runs of 8 particles of a
+// thread and those partial sums in FP64, so the FP64 pipe (narrow on GB300)
+// sees one add per 8 particles instead of seven operations per particle.
+__global__ void k_kinetic64(Store64 st, const unsigned long long* n_dev, long long n_max, double* out) {
   const long long n = (long long)*n_dev;
   double acc = 0.0;
   for (long long i = gtid(); i < n && i < n_max; i += gstride())
-    if (st.pid[i] != kPidDead) acc += v2_of(st, i);
+    if (st.pid[i] != kPidDead) acc += st.vx[i] * st.vx[i] + st.vy[i] * st.vy[i] + st.vz[i] * st.vz[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+__global__ void k_kinetic_mx(StoreMx st, const unsigned long long* n_dev, long long n_max, double* out) {
+  const long long n = min((long long)*n_dev, n_max);
+  double acc = 0.0;
+  float part = 0.f;
+  int run = 0;
+  for (long long i = gtid(); i < n; i += gstride()) {
+    const float a = st.vx[i], b = st.vy[i], c = st.vz[i];
+    if (st.pid[i] != kPidDead) part += fmaf(a, a, fmaf(b, b, c * c));
+    if (++run == 8) {
+      acc += (double)part;
+      part = 0.f;
+      run = 0;
+    }
+  }
+  acc += (double)part;
   acc = block_sum(acc);
   if (threadIdx.x == 0) atomicAdd(out, acc);
 }
 template <class S>
-void launch_kinetic(S st, const unsigned long long* n_dev, long long n_max, double* out, cudaStream_t s) {
-  PIC_LAUNCH(grid_for(n_max), kBlock, 0, s, k_kinetic<S>)(st, n_dev, n_max, out);
+void launch_kinetic(S st, const unsigned long long* n_dev, long long n_max, double* out, cudaStream_t s);
+template <>
+void launch_kinetic<Store64>(Store64 st, const unsigned long long* n_dev, long long n_max, double* out, cudaStream_t s) {
+  PIC_LAUNCH(grid_for(n_max), kBlock, 0, s, k_kinetic64)(st, n_dev, n_max, out);
 }
-template void launch_kinetic<Store64>(Store64, const unsigned long long*, long long, double*, cudaStream_t);
-template void launch_kinetic<StoreMx>(StoreMx, const unsigned long long*, long long, double*, cudaStream_t);
+template <>
+void launch_kinetic<StoreMx>(StoreMx st, const unsigned long long* n_dev, long long n_max, double* out, cudaStream_t s) {
+  PIC_LAUNCH(grid_for(n_max), kBlock, 0, s, k_kinetic_mx)(st, n_dev, n_max, out);
+}
 
-// sum over edges of (delta phi)^2
+// Sum over edges of (delta phi)^2. A block takes whole node rows (k, j) and its
+// threads the nodes i of a row, so the row's indices cost one division per row
+// rather than two 64-bit divisions per node.
 __global__ void k_field_energy(Grid g, const double* __restrict__ f, double* out) {
+  const long long pl = g.nplane;
+  const long long rows = (long long)g.ny * (g.nz + 1);
   double acc = 0.0;
-  for (long long n = gtid(); n < g.nnode; n += gstride()) {
-    const long long pl = g.nplane;
-    const int k = (int)(n / pl);
-    const long long r = n - (long long)k * pl;
-    const int j = (int)(r / g.nx);
-    const int i = (int)(r - (long long)j * g.nx);
-    const double c = f[n];
-    const double dx = f[(long long)k * pl + (long long)j * g.nx + (i + 1 == g.nx ? 0 : i + 1)] - c;
-    const double dy = f[(long long)k * pl + (long long)(j + 1 == g.ny ? 0 : j + 1) * g.nx + i] - c;
-    acc += dx * dx + dy * dy;
-    if (k < g.nz) {
-      const double dz = f[n + pl] - c;
-      acc += dz * dz;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int k = (int)(r / g.ny);
+    const int j = (int)(r - (long long)k * g.ny);
+    const double* row = f + (long long)k * pl + (long long)j * g.nx;
+    const double* north = f + (long long)k * pl + (long long)(j + 1 == g.ny ? 0 : j + 1) * g.nx;
+    const bool up = k < g.nz;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      const double c = row[i];
+      const double dx = row[i + 1 == g.nx ? 0 : i + 1] - c;
+      const double dy = north[i] - c;
+      acc += dx * dx + dy * dy;
+      if (up) {
+        const double dz = row[pl + i] - c;
+        acc += dz * dz;
+      }
     }
   }
   acc = block_sum(acc);
   if (threadIdx.x == 0) atomicAdd(out, acc);
 }
 void launch_field_energy(const Grid& g, const double* phi, double* out, cudaStream_t s) {
-  PIC_LAUNCH(grid_for(g.nnode), kBlock, 0, s, k_field_energy)(g, phi, out);
+  const long long rows = (long long)g.ny * (g.nz + 1);
+  const int threads = g.nx >= 256 ? 256 : (g.nx >= 128 ? 128 : 64);
+  const int grid = (int)std::min<long long>(rows, 152 * 16);
+  PIC_LAUNCH(grid, threads, 0, s, k_field_energy)(g, phi, out);
 }
 
 // Philox on the device (test hook)
