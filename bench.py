@@ -50,9 +50,9 @@ FALLBACK_HBM_GBS = 6800.0
 # read the particle record and write it once (the node field is gathered from L2).
 BYTES_PER_PARTICLE = {"mixed": 32 + 32, "fp64": 52 + 52}
 # DRAM bytes (read + write) per pushed electron of the same kernel from one ncu capture of the
-# current kernel (profiles/k_push_mixed_electrons_128x128x256.md: 146.0 MB for 2 593 379
+# current kernel (profiles/k_push_mixed_electrons_128x128x256.md: 145.18 MB for 2 593 379
 # electrons); None where no capture of the current kernel exists
-NCU_TRAFFIC_PER_PARTICLE = {"mixed": 56.30, "fp64": None}
+NCU_TRAFFIC_PER_PARTICLE = {"mixed": 55.98, "fp64": None}
 
 
 def dist_env():
