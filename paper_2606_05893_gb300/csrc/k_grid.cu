@@ -617,6 +617,74 @@ void launch_field_energy(const Grid& g, const double* phi, double* out, cudaStre
   PIC_LAUNCH(grid, threads, 0, s, k_field_energy)(g, phi, out);
 }
 
+// MIXED: the same sum from the solver's own state, without rebuilding phi in
+// FP64: phi = phi_c on the cathode plane, phi_a + d on the anode plane (d: the
+// external circuit's offset in the FP32 deviation's anode plane) and
+// vac(k) + hi + lo in between (vac linear in k, hi the FP32 deviation, lo its
+// FP32 remainder). The vacuum part cancels in x and y and is one constant per
+// z edge (dz_in inside, dz_top for the last edge). A difference of two exact
+// FP32 values is rounded relative to the difference itself, so every edge
+// difference comes out within ~1e-7 of its size; the squares are summed in
+// FP32 over runs of 8 nodes and those sums in FP64.
+__global__ void k_field_energy_ff(Grid g, const float* __restrict__ hi, const float* __restrict__ lo, float dz_in,
+                                  float dz_top, double* out) {
+  const long long pl = g.nplane;
+  const long long rows = (long long)g.ny * (g.nz + 1);
+  double acc = 0.0;
+  float part = 0.f;
+  int run = 0;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int k = (int)(r / g.ny);
+    const int j = (int)(r - (long long)k * g.ny);
+    const long long c0 = (long long)j * g.nx;                               // row j in a plane
+    const long long cn = (long long)(j + 1 == g.ny ? 0 : j + 1) * g.nx;     // row j + 1
+    const float* H = hi + (long long)k * pl;                                 // plane k (node view)
+    const float* L = lo + (long long)(k - 1) * pl;                           // plane k (unknown view)
+    const bool interior = k > 0 && k < g.nz;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      const int ip = i + 1 == g.nx ? 0 : i + 1;
+      float h0 = 0.f, hx = 0.f, hy = 0.f, l0 = 0.f, lx = 0.f, ly = 0.f;
+      if (k > 0) {
+        h0 = H[c0 + i];
+        hx = H[c0 + ip];
+        hy = H[cn + i];
+      }
+      if (interior) {
+        l0 = L[c0 + i];
+        lx = L[c0 + ip];
+        ly = L[cn + i];
+      }
+      const float dx = (hx - h0) + (lx - l0);
+      const float dy = (hy - h0) + (ly - l0);
+      float sq = fmaf(dx, dx, dy * dy);
+      if (k < g.nz) {
+        const float h1 = H[pl + c0 + i];
+        const float l1 = k + 1 < g.nz ? L[pl + c0 + i] : 0.f;
+        const float dz = (k + 1 == g.nz ? dz_top : dz_in) + ((h1 - h0) + (l1 - l0));
+        sq = fmaf(dz, dz, sq);
+      }
+      part += sq;
+      if (++run == 8) {
+        acc += (double)part;
+        part = 0.f;
+        run = 0;
+      }
+    }
+  }
+  acc += (double)part;
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+void launch_field_energy_ff(const Grid& g, const float* phi32, const float* lo32, double* out, cudaStream_t s) {
+  const double dphi_dk = (g.phi_a - g.phi_c) / (double)g.nz;
+  const float dz_in = (float)dphi_dk;
+  const float dz_top = (float)(g.phi_a - (g.phi_c + dphi_dk * (double)(g.nz - 1)));
+  const long long rows = (long long)g.ny * (g.nz + 1);
+  const int threads = g.nx >= 256 ? 256 : (g.nx >= 128 ? 128 : 64);
+  const int grid = (int)std::min<long long>(rows, 152 * 16);
+  PIC_LAUNCH(grid, threads, 0, s, k_field_energy_ff)(g, phi32, lo32, dz_in, dz_top, out);
+}
+
 // Philox on the device (test hook)
 __global__ void k_philox(long long n, uint4 ctr, uint2 key, uint32_t* out) {
   for (long long i = gtid(); i < n; i += gstride()) {

@@ -1351,8 +1351,12 @@ pic_status pic_moments(pic_handle* h, int32_t inst, pic_moments_t* out) {
     if (I->mixed) launch_kinetic<StoreMx>(I->smx[sp][c], &I->cnt->n[c][sp], I->cap[sp], I->red + sp, s);
     else launch_kinetic<Store64>(I->s64[sp][c], &I->cnt->n[c][sp], I->cap[sp], I->red + sp, s);
   }
-  CK(h, ensure_phi64(I, s));
-  launch_field_energy(I->g, I->phi, I->red + 16, s);
+  if (I->mixed) {
+    // from the solver's float-float state (the potential the last solve left)
+    launch_field_energy_ff(I->g, I->phi32, I->solver.lo32, I->red + 16, s);
+  } else {
+    launch_field_energy(I->g, I->phi, I->red + 16, s);
+  }
   double red[64];
   CK(h, cudaMemcpyAsync(red, I->red, sizeof(red), cudaMemcpyDeviceToHost, s));
   st = sync_counters(h, I);

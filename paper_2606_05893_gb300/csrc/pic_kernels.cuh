@@ -729,6 +729,7 @@ void launch_sort_commit(DevCounters* cnt, int c, int s, cudaStream_t st);
 template <class S>
 void launch_kinetic(S st, const unsigned long long* n_dev, long long n_max, double* out, cudaStream_t s);
 void launch_field_energy(const Grid& g, const double* phi, double* out, cudaStream_t s);
+void launch_field_energy_ff(const Grid& g, const float* phi32, const float* lo32, double* out, cudaStream_t s);
 
 void launch_philox(long long n, uint4 ctr, uint2 key, uint32_t* out, cudaStream_t s);
 
