@@ -245,8 +245,9 @@ pic_status pic_sort_now(pic_handle* h, int32_t inst);
 /* Per-cell offsets of the last cell sort of a species: ncells + 1 int64. */
 pic_status pic_get_cell_start(pic_handle* h, int32_t inst, int32_t species, int64_t* host_out);
 
-/* Ionization events of the last step: rows (primary pid, victim pid, secondary
- * pid) in increasing primary pid; cap rows at most, *n receives the number. */
+/* Successful ionizations of the last step: rows (primary pid, victim pid,
+ * secondary pid) in increasing primary pid; cap rows at most, *n receives the
+ * number. Charge exchanges are not listed (their count is a moment). */
 pic_status pic_get_ionization_log(pic_handle* h, int32_t inst, int64_t cap, int64_t* n, uint32_t* rows);
 
 /* Philox4x32-10 on the device for n consecutive counters
@@ -256,8 +257,8 @@ pic_status pic_philox(pic_handle* h, int64_t n, const uint32_t ctr[4], const uin
 
 /* Test mode for the collision rates of Eq. (4): with density_m3 > 0 every
  * collision channel sees this fixed target density instead of the neutral
- * counts, and ionizations are counted without consuming neutrals or creating
- * particles. 0 restores the normal mode. */
+ * counts, and ionizations and charge exchanges are counted without consuming
+ * neutrals, creating or converting particles. 0 restores the normal mode. */
 pic_status pic_set_mcc_background(pic_handle* h, int32_t inst, double density_m3);
 
 /* ---- external circuit -------------------------------------------------------
