@@ -18,6 +18,8 @@ neutral are suppressed.
    untouched, counts per species and the total momentum are unchanged.
 3. With electrons ionizing in the same cells, both channels share one victim
    pool in primary-pid order (electron pids come first in the preload).
+4. In a plasma run with field, sources and sorting, the per-species counts move
+   only by injection, absorption and ionization, and pids stay unique.
 """
 import math
 
@@ -141,3 +143,29 @@ def test_ionization_and_exchange_share_the_victims():
     assert m["count"] == [c0[0] + n_ion, c0[1] - n_ion, c0[2] + n_ion]
     neut = _by_pid(o, 1)
     assert {p for p, _ in pairs if p >= ne} <= set(neut)
+
+
+def test_bookkeeping_in_a_plasma_run_with_exchange():
+    # counts per species move only by injection, absorption and ionization
+    # (an exchange turns one ion into a neutral and one neutral into an ion);
+    # pids stay unique across species
+    wl = W.config_small(seed=47, n_preload=4000)
+    wl.xsec = list(wl.xsec) + [cx_xsec(1e-16)]
+    o = O.Oracle(wl, cg_rtol=1e-10)
+    m = o.moments()
+    cx_seen = 0
+    for _ in range(12):
+        o.step()
+        m1 = o.moments()
+        d_inj = [a - b for a, b in zip(m1["injected"], m["injected"])]
+        d_abs = [a + c - b - d for a, b, c, d in zip(m1["abs_cathode"], m["abs_cathode"], m1["abs_anode"], m["abs_anode"])]
+        d_ion = m1["n_ionization"] - m["n_ionization"]
+        expect = [m["count"][0] + d_inj[0] - d_abs[0] + d_ion,
+                  m["count"][1] + d_inj[1] - d_abs[1] - d_ion,
+                  m["count"][2] + d_inj[2] - d_abs[2] + d_ion]
+        assert m1["count"] == expect
+        cx_seen += m1["n_cx"] - m["n_cx"]
+        pids = np.concatenate([o.particles(sp)[2] for sp in range(3)])
+        assert np.unique(pids).size == pids.size
+        m = m1
+    assert cx_seen > 0
