@@ -305,6 +305,25 @@ pic_status pic_set_hit_log(pic_handle* h, int32_t inst, int64_t capacity);
 pic_status pic_get_hits(pic_handle* h, int32_t inst, int64_t cap, int64_t* n, int64_t* lost, uint32_t* pid,
                         int32_t* species, int64_t* step, double* x, double* v, double* ke_eV);
 
+/* Checkpoint and resume of one instance (no counterpart in the paper: the
+ * state of a long run, kept so that it can stop and continue). pic_save writes
+ * to `path` the live particles of every species in increasing pid (the store's
+ * own representation: FP64 x, v; or cell, FP32 offsets and velocities of the
+ * mixed store), the potential (and the mixed solver's FP32 state), the
+ * cumulative counters, step and next pid, the surface sources with their carry
+ * accumulators, the sort interval, the external circuit and the background
+ * test mode. The hit log and the ionization log are outputs, not state, and
+ * are not saved. pic_load reads such a file into an instance created with the
+ * same grid, precision, electrode potentials, time step, seed and species; it
+ * checks the whole file first and leaves the instance unchanged on any error
+ * (PIC_EINVAL: unreadable, not a checkpoint, a different configuration, or
+ * truncated; PIC_ECAPACITY: more particles than a species holds). Draws are
+ * counter-based, so a resumed run takes the same decisions as an
+ * uninterrupted one; its first step deposits from scratch, so floating-point
+ * sums may differ in the last bits. Both synchronise the caller's stream. */
+pic_status pic_save(pic_handle* h, int32_t inst, const char* path);
+pic_status pic_load(pic_handle* h, int32_t inst, const char* path);
+
 /* Cell sort interval of one instance from now on (a2: the store is sorted when
  * the step index is a multiple of it; 0 never sorts). The sort only reorders
  * particles, so results do not depend on it beyond rounding; it trades the

@@ -85,7 +85,7 @@ EXPORTED = ["pic_create", "pic_inject", "pic_inject_particles", "pic_step", "pic
             "pic_sort_now", "pic_get_cell_start", "pic_get_ionization_log", "pic_philox",
             "pic_set_mcc_background", "pic_version", "pic_set_profiling", "pic_get_phase_times",
             "pic_launch_count", "pic_kernel_count", "pic_poisson_solve_static", "pic_set_sort_interval",
-            "pic_set_hit_log", "pic_get_hits", "pic_set_circuit"]
+            "pic_set_hit_log", "pic_get_hits", "pic_set_circuit", "pic_save", "pic_load"]
 
 _lib = None
 
@@ -131,6 +131,8 @@ def load_library(path: str = LIB_PATH):
         "pic_set_sort_interval": ([P, C.c_int32, C.c_int32], st),
         "pic_set_hit_log": ([P, C.c_int32, C.c_int64], st),
         "pic_set_circuit": ([P, C.c_int32, C.c_double, C.c_double, C.c_double], st),
+        "pic_save": ([P, C.c_int32, C.c_char_p], st),
+        "pic_load": ([P, C.c_int32, C.c_char_p], st),
         "pic_get_hits": ([P, C.c_int32, C.c_int64, i64, i64, C.POINTER(C.c_uint32), C.POINTER(C.c_int32), i64,
                           d, d, d], st),
         "pic_version": ([], C.c_char_p),
@@ -292,6 +294,14 @@ def pic_set_circuit(h, inst, R_ohm, C_farad, V0):
     return _check(h, load_library().pic_set_circuit(h, inst, float(R_ohm), float(C_farad), float(V0)))
 
 
+def pic_save(h, inst, path):
+    return _check(h, load_library().pic_save(h, inst, os.fsencode(path)))
+
+
+def pic_load(h, inst, path):
+    return _check(h, load_library().pic_load(h, inst, os.fsencode(path)))
+
+
 def pic_set_hit_log(h, inst, capacity):
     return _check(h, load_library().pic_set_hit_log(h, inst, capacity))
 
@@ -419,6 +429,14 @@ class Simulation:
                 for sp, (x, v) in enumerate(w.preload):
                     if len(x):
                         pic_inject_particles(self.h, i, sp, x, v)
+
+    def save(self, path, inst=0):
+        """Checkpoint of one instance (pic_save)."""
+        pic_save(self.h, inst, path)
+
+    def load(self, path, inst=0):
+        """Resume one instance from a checkpoint (pic_load)."""
+        pic_load(self.h, inst, path)
 
     def close(self):
         if self.h:

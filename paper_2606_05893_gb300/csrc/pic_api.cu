@@ -1727,3 +1727,300 @@ pic_status pic_set_mcc_background(pic_handle* h, int32_t inst, double density_m3
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char kCkptMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, counters_bytes;
+  int32_t precision, nx, ny, nz, nspecies, sort_interval;
+  double h, dt, phi_c, phi_a;
+  uint64_t seed;
+  uint32_t step, reserved;
+  double bg_density;
+  int32_t circ_on, last_iters;
+  double circ_R, circ_C, circ_V0, last_resid;
+  int32_t nsources, reserved2;
+};
+
+struct CkptSpecies {
+  double charge_C, mass_kg, weight;
+  int32_t role, reserved;
+  int64_t n;
+};
+
+struct CkptSource {
+  int32_t species, reserved;
+  double cx, cy, R, flux, T, acc;
+};
+
+// Host copy of `count` elements of a device array.
+template <class T>
+cudaError_t pull(std::vector<T>& out, const T* dev, long long count) {
+  out.resize((size_t)count);
+  if (count == 0) return cudaSuccess;
+  return cudaMemcpy(out.data(), dev, sizeof(T) * (size_t)count, cudaMemcpyDeviceToHost);
+}
+
+template <class T>
+bool put(std::FILE* f, const std::vector<T>& a, const std::vector<long long>& order) {
+  std::vector<T> tmp(order.size());
+  for (size_t k = 0; k < order.size(); ++k) tmp[k] = a[(size_t)order[k]];
+  return tmp.empty() || std::fwrite(tmp.data(), sizeof(T), tmp.size(), f) == tmp.size();
+}
+
+// Bounded reader over the file image.
+struct Cursor {
+  const std::vector<char>& b;
+  size_t at = 0;
+  bool take(void* dst, size_t bytes) {
+    if (bytes > b.size() - at) return false;
+    if (bytes) memcpy(dst, b.data() + at, bytes);
+    at += bytes;
+    return true;
+  }
+  const char* skip(size_t bytes) {
+    if (bytes > b.size() - at) return nullptr;
+    const char* p = b.data() + at;
+    at += bytes;
+    return p;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_save(pic_handle* h, int32_t inst, const char* path) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  if (!path) return fail(h, PIC_EINVAL, "path is NULL");
+  Instance* I = h->inst[inst];
+  st = download_carries(h, I);
+  if (st != PIC_OK) return st;
+  CK(h, cudaStreamSynchronize(I->stream));
+  CK(h, ensure_phi64(I, h->stream));
+  st = sync_counters(h, I);
+  if (st != PIC_OK) return st;
+  const DevCounters c = *I->host_cnt;
+
+  CkptHeader hd{};
+  memcpy(hd.magic, kCkptMagic, sizeof hd.magic);
+  hd.version = kCkptVersion;
+  hd.counters_bytes = (uint32_t)sizeof(DevCounters);
+  hd.precision = I->cfg.precision;
+  hd.nx = I->g.nx;
+  hd.ny = I->g.ny;
+  hd.nz = I->g.nz;
+  hd.nspecies = I->nsp;
+  hd.sort_interval = I->cfg.sort_interval;
+  hd.h = I->g.h;
+  hd.dt = I->g.dt;
+  hd.phi_c = I->cfg.phi_cathode_V;
+  hd.phi_a = I->cfg.phi_anode_V;
+  hd.seed = I->cfg.seed;
+  hd.step = I->step;
+  hd.bg_density = I->bg_density;
+  hd.circ_on = I->circ.on;
+  hd.circ_R = I->circ.R;
+  hd.circ_C = I->circ.C;
+  hd.circ_V0 = I->circ.V0;
+  hd.last_iters = I->last.iters;
+  hd.last_resid = I->last.resid_rel;
+  hd.nsources = (int32_t)I->sources.size();
+
+  std::FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(h, PIC_EINVAL, "cannot open %s for writing", path);
+  bool ok = std::fwrite(&hd, sizeof hd, 1, f) == 1 && std::fwrite(&c, sizeof c, 1, f) == 1;
+  for (const Source& q : I->sources) {
+    CkptSource r{};
+    r.species = q.species;
+    r.cx = q.cx;
+    r.cy = q.cy;
+    r.R = q.R;
+    r.flux = q.flux;
+    r.T = q.T;
+    r.acc = q.acc;
+    ok = ok && std::fwrite(&r, sizeof r, 1, f) == 1;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int sp = 0; ok && sp < I->nsp; ++sp) {
+    const int b = I->cur[sp];
+    const long long slots = (long long)c.n[b][sp];
+    std::vector<uint32_t> pid;
+    std::vector<long long> order;
+    std::vector<double> d[6];
+    std::vector<float> fl[6];
+    std::vector<int32_t> cell;
+    if (I->mixed) {
+      const StoreMx& S = I->smx[sp][b];
+      float* src[6] = {S.ox, S.oy, S.oz, S.vx, S.vy, S.vz};
+      if (!e) e = pull(pid, S.pid, slots);
+      if (!e) e = pull(cell, S.cell, slots);
+      for (int a = 0; a < 6 && !e; ++a) e = pull(fl[a], src[a], slots);
+    } else {
+      const Store64& S = I->s64[sp][b];
+      double* src[6] = {S.x, S.y, S.z, S.vx, S.vy, S.vz};
+      if (!e) e = pull(pid, S.pid, slots);
+      for (int a = 0; a < 6 && !e; ++a) e = pull(d[a], src[a], slots);
+    }
+    if (e) break;
+    for (long long i = 0; i < slots; ++i)
+      if (pid[(size_t)i] != kPidDead) order.push_back(i);
+    std::sort(order.begin(), order.end(), [&](long long a, long long b2) { return pid[(size_t)a] < pid[(size_t)b2]; });
+    CkptSpecies r{};
+    const pic_species& S = I->species[sp];
+    r.charge_C = S.charge_C;
+    r.mass_kg = S.mass_kg;
+    r.weight = S.weight;
+    r.role = S.role;
+    r.n = (int64_t)order.size();
+    ok = ok && std::fwrite(&r, sizeof r, 1, f) == 1 && put(f, pid, order);
+    if (I->mixed) {
+      ok = ok && put(f, cell, order);
+      for (int a = 0; a < 6; ++a) ok = ok && put(f, fl[a], order);
+    } else {
+      for (int a = 0; a < 6; ++a) ok = ok && put(f, d[a], order);
+    }
+  }
+  if (ok && !e) {
+    std::vector<double> phi;
+    e = pull(phi, (const double*)I->phi, I->g.nnode);
+    ok = !e && std::fwrite(phi.data(), sizeof(double), phi.size(), f) == phi.size();
+  }
+  if (ok && !e && I->mixed) {
+    std::vector<float> hi, lo;
+    e = pull(hi, (const float*)I->phi32, I->g.nnode);
+    if (!e) e = pull(lo, (const float*)I->solver.lo32, I->solver.n);
+    ok = !e && std::fwrite(hi.data(), sizeof(float), hi.size(), f) == hi.size() &&
+         (lo.empty() || std::fwrite(lo.data(), sizeof(float), lo.size(), f) == lo.size());
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (e) return fail(h, PIC_ECUDA, "checkpoint download failed: %s", cudaGetErrorString(e));
+  if (!ok) return fail(h, PIC_EINVAL, "cannot write %s", path);
+  return PIC_OK;
+}
+
+pic_status pic_load(pic_handle* h, int32_t inst, const char* path) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  if (!path) return fail(h, PIC_EINVAL, "path is NULL");
+  Instance* I = h->inst[inst];
+  std::vector<char> buf;
+  {
+    std::FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(h, PIC_EINVAL, "cannot open %s", path);
+    char chunk[1 << 16];
+    size_t got;
+    while ((got = std::fread(chunk, 1, sizeof chunk, f)) > 0) buf.insert(buf.end(), chunk, chunk + got);
+    std::fclose(f);
+  }
+  // parse and check everything before any state changes
+  Cursor cur{buf};
+  CkptHeader hd{};
+  DevCounters c{};
+  if (!cur.take(&hd, sizeof hd) || memcmp(hd.magic, kCkptMagic, sizeof hd.magic) != 0 || hd.version != kCkptVersion)
+    return fail(h, PIC_EINVAL, "%s is not a checkpoint of this library", path);
+  if (hd.counters_bytes != sizeof(DevCounters) || !cur.take(&c, sizeof c))
+    return fail(h, PIC_EINVAL, "%s: counter block of another build", path);
+  if (hd.precision != I->cfg.precision || hd.nx != I->g.nx || hd.ny != I->g.ny || hd.nz != I->g.nz ||
+      hd.nspecies != I->nsp || hd.h != I->g.h || hd.dt != I->g.dt || hd.phi_c != I->cfg.phi_cathode_V ||
+      hd.phi_a != I->cfg.phi_anode_V || hd.seed != I->cfg.seed)
+    return fail(h, PIC_EINVAL, "%s: grid, precision, electrodes, time step or seed differ from instance %d", path, inst);
+  if (hd.nsources < 0 || hd.nsources > kMaxSources || hd.sort_interval < 0)
+    return fail(h, PIC_EINVAL, "%s: bad source count or sort interval", path);
+  std::vector<Source> sources;
+  for (int q = 0; q < hd.nsources; ++q) {
+    CkptSource r{};
+    if (!cur.take(&r, sizeof r) || r.species < 0 || r.species >= I->nsp)
+      return fail(h, PIC_EINVAL, "%s: bad source record", path);
+    sources.push_back(Source{r.species, r.cx, r.cy, r.R, r.flux, r.T, r.acc});
+  }
+  const size_t per64 = sizeof(uint32_t) + 6 * sizeof(double);
+  const size_t permx = sizeof(uint32_t) + sizeof(int32_t) + 6 * sizeof(float);
+  std::vector<const char*> parts(I->nsp);
+  std::vector<long long> counts(I->nsp);
+  for (int sp = 0; sp < I->nsp; ++sp) {
+    CkptSpecies r{};
+    if (!cur.take(&r, sizeof r)) return fail(h, PIC_EINVAL, "%s: truncated", path);
+    const pic_species& S = I->species[sp];
+    if (r.charge_C != S.charge_C || r.mass_kg != S.mass_kg || r.weight != S.weight || r.role != S.role)
+      return fail(h, PIC_EINVAL, "%s: species %d differs from instance %d", path, sp, inst);
+    if (r.n < 0 || r.n > I->cap[sp])
+      return fail(h, PIC_ECAPACITY, "%s: species %d holds %lld, capacity %lld", path, sp, (long long)r.n, I->cap[sp]);
+    counts[sp] = r.n;
+    parts[sp] = cur.skip((size_t)r.n * (I->mixed ? permx : per64));
+    if (!parts[sp]) return fail(h, PIC_EINVAL, "%s: truncated", path);
+  }
+  const char* phi = cur.skip(sizeof(double) * (size_t)I->g.nnode);
+  const char* hi = I->mixed ? cur.skip(sizeof(float) * (size_t)I->g.nnode) : nullptr;
+  const char* lo = I->mixed ? cur.skip(sizeof(float) * (size_t)I->solver.n) : nullptr;
+  if (!phi || (I->mixed && (!hi || !lo)) || cur.at != buf.size())
+    return fail(h, PIC_EINVAL, "%s: truncated or trailing bytes", path);
+
+  // apply: particles into buffer 0 of every species, counters, potential, host state
+  CK(h, cudaStreamSynchronize(I->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  for (int sp = 0; sp < I->nsp; ++sp) {
+    const long long n = counts[sp];
+    const char* p = parts[sp];
+    I->cur[sp] = 0;
+    if (I->mixed) {
+      const StoreMx& S = I->smx[sp][0];
+      CK(h, cudaMemcpy(S.pid, p, sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
+      p += sizeof(uint32_t) * n;
+      CK(h, cudaMemcpy(S.cell, p, sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+      p += sizeof(int32_t) * n;
+      float* dst[6] = {S.ox, S.oy, S.oz, S.vx, S.vy, S.vz};
+      for (int a = 0; a < 6; ++a, p += sizeof(float) * n)
+        CK(h, cudaMemcpy(dst[a], p, sizeof(float) * n, cudaMemcpyHostToDevice));
+    } else {
+      const Store64& S = I->s64[sp][0];
+      CK(h, cudaMemcpy(S.pid, p, sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
+      p += sizeof(uint32_t) * n;
+      double* dst[6] = {S.x, S.y, S.z, S.vx, S.vy, S.vz};
+      for (int a = 0; a < 6; ++a, p += sizeof(double) * n)
+        CK(h, cudaMemcpy(dst[a], p, sizeof(double) * n, cudaMemcpyHostToDevice));
+    }
+    c.n[0][sp] = (unsigned long long)n;
+    c.n[1][sp] = 0;
+    c.n_tomb[sp] = 0;
+  }
+  c.n_events = c.n_success = c.n_success_cx = c.n_cands = 0;
+  c.ev_sort_n = 0;
+  c.error = 0;
+  CK(h, cudaMemcpy(I->cnt, &c, sizeof c, cudaMemcpyHostToDevice));
+  *I->host_cnt = c;
+  CK(h, cudaMemcpy(I->phi, phi, sizeof(double) * I->g.nnode, cudaMemcpyHostToDevice));
+  if (I->mixed) {
+    CK(h, cudaMemcpy(I->phi32, hi, sizeof(float) * I->g.nnode, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(I->solver.lo32, lo, sizeof(float) * I->solver.n, cudaMemcpyHostToDevice));
+  }
+  I->phi64_stale = false;
+  CK(h, I->solver.invalidate(h->stream));
+  I->step = hd.step;
+  I->cfg.sort_interval = hd.sort_interval;
+  I->bg_density = hd.bg_density;
+  I->circ.on = hd.circ_on;
+  I->circ.R = hd.circ_R;
+  I->circ.C = hd.circ_C;
+  I->circ.V0 = hd.circ_V0;
+  I->circ.dt = I->g.dt;
+  I->last = SolveResult{hd.last_iters, hd.last_resid, true};
+  I->sources = sources;
+  I->plan_dirty = true;
+  I->plan_used = false;
+  I->next_valid = false;  // the next step deposits from scratch
+  I->sorted_once = false;
+  drop_step_graphs(I);
+  CK(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+}  // extern "C"
