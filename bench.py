@@ -128,7 +128,7 @@ class ClockSampler:
 
 
 class NvmlClockSampler:
-    """SM clock and clock-event reasons read through NVML (the driver's library,
+    """SM clock and clock-event reasons read through NVML (the NVIDIA driver's management library,
     read-only queries) every millisecond from a thread during the timed region;
     the device is found by its UUID, so it is the one being timed."""
 
@@ -195,7 +195,7 @@ class NvmlClockSampler:
 
 
 def clock_sampler(local):
-    """NVML sampling where the driver's library loads, else nvidia-smi."""
+    """NVML sampling where NVIDIA's management library loads, else nvidia-smi."""
     try:
         return NvmlClockSampler(local)
     except Exception:
