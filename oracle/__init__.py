@@ -1,7 +1,7 @@
 """ctypes wrapper of the plain FP64 CPU oracle (pic_oracle.c).
 
 TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
-CPU-baseline leg are the only users. The oracle is independent of the CUDA
+CPU-baseline and reference legs are the only users. The oracle is independent of the CUDA
 library (no shared source, header or helper); both sides consume the seeded
 inputs of ``paper_2606_05893_gb300.workloads`` and nothing else.
 """

@@ -2,7 +2,7 @@
  * pic_oracle.c -- plain, slow FP64 CPU oracle of the electrostatic PIC/MCC step.
  *
  * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the
- * CPU-baseline leg of the benchmark load this library. It shares no code,
+ * CPU-baseline and reference legs of the benchmark load this library. It shares no code,
  * header, table or helper with the CUDA library; the two meet only through
  * seeded input arrays.
  *
@@ -13,7 +13,10 @@
  *   - PIC/MCC paragraph: superparticles injected from the cathode (emitted
  *     electrons, evaporated Cu neutrals), moved by electric forces, colliding by
  *     Monte Carlo collisions with probability Eq. (4)
- *         P = 1 - exp(-u n sigma(E) dt_PIC).
+ *         P = 1 - exp(-u n sigma(E) dt_PIC)
+ *     (electron-impact ionization and elastic scattering; resonant charge
+ *     exchange of an ion on a neutral of its own element, one of the MCC
+ *     collisions the paragraph lists).
  *   - Ions leave the plasma domain when they hit the cathode (Appendix A).
  * The paper fixes neither discretisation nor step order; the readings used here
  * (structured node grid, 7-point Laplacian, cloud-in-cell shape, leapfrog push,
