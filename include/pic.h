@@ -167,39 +167,57 @@ enum {
   PIC_NPHASES = 9
 };
 
-/* Create n_instances independent instances on the current CUDA device.
+/* Create n_instances independent instances on the current CUDA device: the
+ * plasma domain of the PIC/MCC paragraph (superparticles of the species in
+ * cfgs[i].species, the collision channels of Eq. (4) in cfgs[i].xsec) between a
+ * cathode and an anode held at the Dirichlet potentials of Eq. (1) (the setup
+ * paragraph after Eq. (4): grounded cathode, anode at V0).
  * cfgs: array of n_instances configurations (copied). cuda_stream: the stream
  * all work is enqueued on. Errors: PIC_EINVAL (bad geometry, species, tables,
  * weights), PIC_ENOMEM, PIC_ECUDA. */
 pic_status pic_create(const pic_instance_cfg* cfgs, int32_t n_instances, void* cuda_stream,
                       pic_handle** out);
 
-/* Add (flux > 0) or remove (flux == 0) a persistent surface source of species
+/* Superparticle injection of the PIC/MCC paragraph (emitted electrons,
+ * evaporated or sputtered neutrals entering the plasma at the surface).
+ * Add (flux > 0) or remove (flux == 0) a persistent surface source of species
  * `species` on the cathode: a disk of radius radius_m centred at (cx, cy).
  * Every step it injects floor(acc) superparticles, acc += flux pi R^2 dt / w,
  * uniform on the disk with a half-Maxwellian velocity at temperature T_K
  * (vx, vy ~ N(0, kT/m), vz = |N(0, kT/m)|) and z = U vz dt. The carry
- * accumulator acc is kept on the host. Up to PIC_MAX_SOURCES sources per
- * instance; a source with the same (species, cx, cy, radius) is replaced. */
+ * accumulator acc lives on the device, where each step updates it (in FP64,
+ * the formula above); it is read back when the source list changes and by
+ * pic_save. Up to
+ * PIC_MAX_SOURCES sources per instance; a source with the same (species, cx,
+ * cy, radius) is replaced and keeps its carry. */
 pic_status pic_inject(pic_handle* h, int32_t inst, int32_t species, double cx, double cy,
                       double radius_m, double flux_m2s, double T_K);
 
-/* Append n superparticles of `species` (host arrays x[n][3], v[n][3], copied;
- * v is taken as v^{n-1/2}). Positions must lie in [0,Lx) x [0,Ly) x [0,Lz).
+/* Particle transfer into the plasma (Appendix A: atoms or clusters leaving the
+ * surface model become superparticles of the PIC system); also the preload of
+ * a population. Append n superparticles of `species` (host arrays x[n][3],
+ * v[n][3], copied; v is taken as v^{n-1/2}). Positions must lie in [0,Lx) x [0,Ly) x [0,Lz).
  * pids continue from next_pid in array order. PIC_ECAPACITY if the store
  * would overflow (nothing is appended then). */
 pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
                                 const double* x, const double* v);
 
-/* Advance every instance by nsteps steps (asynchronous on the stream). The
+/* Advance every instance by nsteps PIC steps of length dt (the PIC/MCC
+ * paragraph: the field of Eq. (1) from the deposited charge, the push by
+ * electric forces, collisions with the probability of Eq. (4), absorption at
+ * the electrodes; the order is listed at the top of this file). Asynchronous on
+ * the stream. The
  * returned status covers argument checks, launch errors and the device error
  * flags of earlier completed steps (PIC_ECAPACITY, PIC_ENOCONV, PIC_ETIMEOUT). */
 pic_status pic_step(pic_handle* h, int32_t nsteps);
 
-/* Fill *out (caller-owned) with the moments of instance inst. Synchronises. */
+/* Fill *out (caller-owned) with the moments of instance inst: the counts,
+ * collision events (Eq. 4), absorbed particles and energies, charge and energies
+ * that the PIC/MCC paragraph's quantities are summed from. Synchronises. */
 pic_status pic_moments(pic_handle* h, int32_t inst, pic_moments_t* out);
 
-/* Release all device and host memory of the handle (NULL is accepted). */
+/* Release all device and host memory of the handle (NULL is accepted). Pure
+ * resource management: the paper has no counterpart. */
 pic_status pic_destroy(pic_handle* h);
 
 /* Text of the last error on this handle (static storage, never NULL). */
@@ -354,9 +372,9 @@ uint64_t pic_kernel_count(void);
  * Not in the paper: an entry point for callers that cannot allocate device
  * memory while they run (programs that hand out all device memory from their
  * own pool at start-up, or that must keep a fixed footprint between coupling
- * steps). It solves the same discrete Poisson problem as pic_solve -- Eq. (1)
- * on the node grid, 7-point operator, periodic x/y, Dirichlet planes
- * phi(k=0) = phi_cathode_V and phi(k=nz) = phi_anode_V -- by conjugate gradients,
+ * steps). It solves the node-grid Poisson problem that pic_solve solves --
+ * 7-point operator, periodic x/y, Dirichlet planes phi(k=0) = phi_cathode_V and
+ * phi(k=nz) = phi_anode_V -- by unpreconditioned conjugate gradients,
  * with every work vector in one fixed array inside the library (file-scope
  * __device__ storage of PIC_STATIC_MAX_UNKNOWNS-sized vectors, about 8 MiB,
  * held by every GPU that loads the library until the process exits). It calls
@@ -365,18 +383,22 @@ uint64_t pic_kernel_count(void);
  *  phi_dev: device array of the same size; its interior (k = 1..nz-1) is the
  *           initial guess on entry; on return it holds the solution and the
  *           electrode planes hold their potentials. Caller-owned.
- *  Stops when the recursive residual reaches rtol ||b|| or after maxit
- *  iterations; the true relative residual is reported in *resid_rel and the
- *  iteration count in *iters (either may be NULL).
- * Returns PIC_EINVAL for bad arguments or nx*ny*(nz-1) > PIC_STATIC_MAX_UNKNOWNS
- * (pic_last_error(NULL) says which), PIC_ENOCONV if rtol was not reached,
- * PIC_ECUDA on a CUDA error. The first call on a device looks up the address of
+ *  Iterates until the recursive residual reaches rtol ||b|| or maxit
+ *  iterations have run, then recomputes the true residual b - A phi; the status
+ *  follows that true residual, which at very tight rtol can sit just above the
+ *  recursive one. The true relative residual is reported in *resid_rel and the
+ *  iteration count in *iters (either may be NULL). rho = 0 with both electrodes
+ *  at 0 V gives the zero solution after 0 iterations.
+ * Returns PIC_EINVAL for bad arguments or nx*ny*(nz-1) > PIC_STATIC_MAX_UNKNOWNS,
+ * PIC_ENOCONV if the true residual is above rtol, PIC_ECUDA if a launch or copy
+ * fails; pic_last_error(NULL) then says which. The first call on a device looks up the address of
  * the fixed array on that device (cudaGetSymbolAddress, with that device
  * current); make that first call before any stream capture. All calls share
  * the array and it keeps the last call's contents (each call writes every
  * vector before reading it); calls that overlap on the GPU -- on different
  * streams or from different host threads on the same device -- race on it.
- * Work runs on cuda_stream, which the call synchronises. */
+ * Work runs on cuda_stream; the call reads the residual back and synchronises
+ * that stream once per iteration. */
 #define PIC_STATIC_MAX_UNKNOWNS (1 << 18)
 pic_status pic_poisson_solve_static(int32_t nx, int32_t ny, int32_t nz, double h, double phi_cathode_V,
                                     double phi_anode_V, const double* rho_dev, double* phi_dev, double rtol,

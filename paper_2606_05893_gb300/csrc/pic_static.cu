@@ -16,6 +16,7 @@
 // nothing needs clearing between calls. Calls whose work overlaps on the GPU
 // (different streams, or different host threads on one device) race on it.
 #include <cmath>
+#include <cstdio>
 #include <mutex>
 
 #include "../../include/pic.h"
@@ -207,16 +208,31 @@ extern "C" pic_status pic_poisson_solve_static(int32_t nx, int32_t ny, int32_t n
   const int G = (int)(gb < 1 ? 1 : (gb > kStaticParts ? kStaticParts : gb));
   double* x = phi_dev + L.pl;  // unknown nodes k = 1..nz-1 are contiguous
 
-  auto read = [&](int idx, double* out) -> bool {
-    if (cudaMemcpyAsync(out, sc + idx, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
-    return cudaStreamSynchronize(s) == cudaSuccess;
+  // A failed launch leaves no sticky error and the scalars keep the previous
+  // call's values, so every read of a decision scalar is preceded by a check of
+  // the launches before it.
+  auto fail = [&](const char* what, cudaError_t e) -> pic_status {
+    char msg[256];
+    snprintf(msg, sizeof msg, "pic_poisson_solve_static: %s: %s", what, cudaGetErrorString(e));
+    set_static_error(msg);
+    return PIC_ECUDA;
   };
+  auto read = [&](int idx, double* out) -> cudaError_t {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(out, sc + idx, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+  };
+  // a launch error left by earlier, unrelated work is cleared, not reported as this call's
+  cudaError_t e = cudaGetLastError();
   PIC_LAUNCH(G, kStaticBlock, 0, s, k_static_rhs)(L, h, phi_cathode_V, phi_anode_V, rho_dev, phi_dev, b, part);
   PIC_LAUNCH(1, 1, 0, s, k_static_scalars)(part, G, sc, 0);
   PIC_LAUNCH(G, kStaticBlock, 0, s, k_static_residual)(L, x, b, r, p, part);
   PIC_LAUNCH(1, 1, 0, s, k_static_scalars)(part, G, sc, 1);
   double bb = 0.0, rr = 0.0;
-  if (!read(4, &bb) || !read(0, &rr)) return PIC_ECUDA;
+  if ((e = read(4, &bb)) != cudaSuccess) return fail("right-hand side", e);
+  if ((e = read(0, &rr)) != cudaSuccess) return fail("initial residual", e);
   const double tol = rtol * std::sqrt(bb);
   int it = 0;
   if (bb > 0.0) {
@@ -227,20 +243,28 @@ extern "C" pic_status pic_poisson_solve_static(int32_t nx, int32_t ny, int32_t n
       PIC_LAUNCH(1, 1, 0, s, k_static_scalars)(part, G, sc, 3);
       PIC_LAUNCH(G, kStaticBlock, 0, s, k_static_direction)(L, p, r, sc);
       ++it;
-      if (!read(0, &rr)) return PIC_ECUDA;
+      if ((e = read(0, &rr)) != cudaSuccess) return fail("CG iteration", e);
       if (!std::isfinite(rr)) break;
     }
-    // confirm with the true residual
+    // the status follows the true residual b - A x, recomputed here
     PIC_LAUNCH(G, kStaticBlock, 0, s, k_static_residual)(L, x, b, r, p, part);
     PIC_LAUNCH(1, 1, 0, s, k_static_scalars)(part, G, sc, 1);
-    if (!read(0, &rr)) return PIC_ECUDA;
+    if ((e = read(0, &rr)) != cudaSuccess) return fail("true residual", e);
   } else {
-    if (cudaMemsetAsync(x, 0, sizeof(double) * nu, s) != cudaSuccess) return PIC_ECUDA;
+    if ((e = cudaMemsetAsync(x, 0, sizeof(double) * nu, s)) != cudaSuccess) return fail("zero solution", e);
     rr = 0.0;
   }
-  if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail("stream synchronise", e);
   const double rel = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
   if (iters) *iters = it;
   if (resid_rel) *resid_rel = rel;
-  return rel <= rtol ? PIC_OK : PIC_ENOCONV;
+  if (!(rel <= rtol)) {
+    char msg[256];
+    snprintf(msg, sizeof msg,
+             "pic_poisson_solve_static: true relative residual %.3e above rtol %.3e after %d iterations", rel, rtol,
+             it);
+    set_static_error(msg);
+    return PIC_ENOCONV;
+  }
+  return PIC_OK;
 }

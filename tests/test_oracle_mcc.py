@@ -154,3 +154,38 @@ def test_lotz_table_lookup():
         assert o.sigma(0, e) == pytest.approx(exact, rel=2e-3)
     assert o.sigma(0, 2e5) == s[-1]
     assert o.sigma(1, 1e-3) == W.ELASTIC_SIGMA_M2
+
+
+def test_ionization_secondary_direction_isotropic():
+    """The secondary electron of an ionization leaves isotropically (reading of
+    the ionization kinematics under Eq. 4): cos(theta) uniform on [-1, 1] and the
+    azimuth uniform on (-pi, pi], whatever the primary's direction. Checked on
+    about two thousand events of one step by the first two moments of cos(theta)
+    against 1/3 and 0 (3 standard errors), Kolmogorov-Smirnov tests of cos(theta)
+    and of the azimuth, and no correlation with the primary's direction."""
+    from scipy import stats
+    wl = ionization_cells_case(seed=9, n_dense_e=6000, n_dense_n=8000)
+    o = O.Oracle(wl, cg_rtol=1e-13)
+    o.step()
+    log = o.ionization_log()
+    n = log.shape[0]
+    assert n > 1500
+    xe, ve, pe = o.particles(0)
+    be = {int(p): k for k, p in enumerate(pe)}
+    sec = np.array([ve[be[int(s)]] for s in log[:, 2]])
+    prim = np.array([ve[be[int(p)]] for p in log[:, 0]])
+    speed = np.linalg.norm(sec, axis=1)
+    keep = speed > 0
+    u = sec[keep] / speed[keep, None]
+    ct = u[:, 2]
+    m = ct.size
+    assert abs(ct.mean()) <= 3.0 * math.sqrt(1.0 / 3.0 / m)
+    assert abs((ct ** 2).mean() - 1.0 / 3.0) <= 3.0 * math.sqrt(4.0 / 45.0 / m)
+    assert stats.kstest(ct, "uniform", args=(-1.0, 2.0)).pvalue > 1e-3
+    az = np.arctan2(u[:, 1], u[:, 0])
+    assert stats.kstest(az, "uniform", args=(-math.pi, 2.0 * math.pi)).pvalue > 1e-3
+    for c in range(3):
+        assert abs(u[:, c].mean()) <= 3.0 * math.sqrt(1.0 / 3.0 / m)
+    pu = prim[keep] / np.linalg.norm(prim[keep], axis=1)[:, None]
+    cos_between = np.einsum("ij,ij->i", u, pu)
+    assert abs(cos_between.mean()) <= 3.0 * math.sqrt(1.0 / 3.0 / m)
