@@ -111,24 +111,34 @@ def upsample2_backward(dy):
 # ----------------------------------------------------------------------------
 # the network
 # ----------------------------------------------------------------------------
-def forward(params, x):
+def _keep(a):
+    return a
+
+
+def forward(params, x, rnd=None):
     """params: dict name -> weight (LAYERS and OUT); x: (IN_CHANNELS, D, H, W) with
-    D, H, W multiples of 8. Returns (y of shape (1, D, H, W), cache)."""
+    D, H, W multiples of 8. Returns (y of shape (1, D, H, W), cache).
+
+    rnd (default: none) is applied to every stored activation (each ReLU output
+    and each pooled tensor): a caller that stores activations in a narrower
+    format passes its rounding here, so that both sides take the ReLU decisions
+    on the same values. The arithmetic between those points stays FP64."""
+    rnd = rnd or _keep
     cache = {"x": x}
 
     def block(name_a, name_b, inp):
         za = conv3x3(inp, params[name_a])
-        ya = relu(za)
+        ya = rnd(relu(za))
         zb = conv3x3(ya, params[name_b])
-        yb = relu(zb)
+        yb = rnd(relu(zb))
         cache[name_a] = (inp, ya)
         cache[name_b] = (ya, yb)
         return yb
 
     e0 = block("e0a", "e0b", x)
-    e1 = block("e1a", "e1b", avgpool2(e0))
-    e2 = block("e2a", "e2b", avgpool2(e1))
-    e3 = block("e3a", "e3b", avgpool2(e2))
+    e1 = block("e1a", "e1b", rnd(avgpool2(e0)))
+    e2 = block("e2a", "e2b", rnd(avgpool2(e1)))
+    e3 = block("e3a", "e3b", rnd(avgpool2(e2)))
     d2 = block("d2a", "d2b", np.concatenate([upsample2(e3), e2]))
     d1 = block("d1a", "d1b", np.concatenate([upsample2(d2), e1]))
     d0 = block("d0a", "d0b", np.concatenate([upsample2(d1), e0]))
@@ -136,27 +146,33 @@ def forward(params, x):
     return conv1x1(d0, params["out"]), cache
 
 
-def backward(params, cache, dy):
-    """Gradients of sum(dy * forward(params, x)) for every weight, and for x."""
+def backward(params, cache, dy, rnd=None):
+    """Gradients of sum(dy * forward(params, x)) for every weight, and for x.
+
+    rnd (default: none) is applied to every stored activation gradient (the
+    gradient at each convolution's output after its ReLU mask, at each
+    convolution's input, and after each adjoint upsampling); weight gradients
+    are never rounded."""
+    rnd = rnd or _keep
     g = {}
     dd0, g["out"] = conv1x1_backward(cache["out"], params["out"], dy)
 
     def block_back(name_a, name_b, dout):
         ya, yb = cache[name_b]
-        dzb = dout * (yb > 0)
+        dzb = rnd(dout * (yb > 0))
         dya, g[name_b] = conv3x3_backward(ya, params[name_b], dzb)
         inp, ya2 = cache[name_a]
-        dza = dya * (ya2 > 0)
+        dza = rnd(dya * (ya2 > 0))
         dinp, g[name_a] = conv3x3_backward(inp, params[name_a], dza)
-        return dinp
+        return rnd(dinp)
 
     c3, c2, c1 = CH[3], CH[2], CH[1]
     dcat0 = block_back("d0a", "d0b", dd0)
-    dd1, de0 = upsample2_backward(dcat0[:c1]), dcat0[c1:]
+    dd1, de0 = rnd(upsample2_backward(dcat0[:c1])), dcat0[c1:]
     dcat1 = block_back("d1a", "d1b", dd1)
-    dd2, de1 = upsample2_backward(dcat1[:c2]), dcat1[c2:]
+    dd2, de1 = rnd(upsample2_backward(dcat1[:c2])), dcat1[c2:]
     dcat2 = block_back("d2a", "d2b", dd2)
-    de3, de2 = upsample2_backward(dcat2[:c3]), dcat2[c3:]
+    de3, de2 = rnd(upsample2_backward(dcat2[:c3])), dcat2[c3:]
     dp3 = block_back("e3a", "e3b", de3)
     de2 = de2 + avgpool2_backward(dp3)
     dp2 = block_back("e2a", "e2b", de2)

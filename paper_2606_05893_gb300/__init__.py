@@ -85,7 +85,11 @@ EXPORTED = ["pic_create", "pic_inject", "pic_inject_particles", "pic_step", "pic
             "pic_sort_now", "pic_get_cell_start", "pic_get_ionization_log", "pic_philox",
             "pic_set_mcc_background", "pic_version", "pic_set_profiling", "pic_get_phase_times",
             "pic_launch_count", "pic_kernel_count", "pic_poisson_solve_static", "pic_set_sort_interval",
-            "pic_set_hit_log", "pic_get_hits", "pic_set_circuit", "pic_save", "pic_load"]
+            "pic_set_hit_log", "pic_get_hits", "pic_set_circuit", "pic_save", "pic_load",
+            "pic_set_warm_unet", "pic_get_phi_device",
+            "unet_num_weights", "unet_create", "unet_destroy", "unet_set_weights", "unet_get_weights",
+            "unet_forward", "unet_backward", "unet_get_grads", "unet_train_step", "unet_last_error",
+            "unet_launch_count", "unet_make_sample", "unet_layer_forward", "unet_layer_backward"]
 
 _lib = None
 
@@ -142,6 +146,22 @@ def load_library(path: str = LIB_PATH):
         "pic_kernel_count": ([], C.c_uint64),
         "pic_poisson_solve_static": ([C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, P, P,
                                       C.c_double, C.c_int32, P, C.POINTER(C.c_int32), d], st),
+        "pic_set_warm_unet": ([P, C.c_int32, P], st),
+        "pic_get_phi_device": ([P, C.c_int32, P], st),
+        "unet_num_weights": ([], C.c_int64),
+        "unet_create": ([C.c_int32, C.c_int32, C.c_int32, P, C.POINTER(P)], st),
+        "unet_destroy": ([P], st),
+        "unet_set_weights": ([P, C.POINTER(C.c_float), C.c_int64], st),
+        "unet_get_weights": ([P, C.POINTER(C.c_float), C.c_int64], st),
+        "unet_forward": ([P, P, P], st),
+        "unet_backward": ([P, P], st),
+        "unet_get_grads": ([P, C.POINTER(C.c_float), C.c_int64], st),
+        "unet_train_step": ([P, P, P, C.c_int32, C.c_float, d], st),
+        "unet_last_error": ([P], C.c_char_p),
+        "unet_launch_count": ([], C.c_uint64),
+        "unet_make_sample": ([P, P, P, P, P, d], st),
+        "unet_layer_forward": ([P, C.c_int32, P, P, C.c_int32], st),
+        "unet_layer_backward": ([P, C.c_int32, P, P, P, C.POINTER(C.c_float), C.c_int64], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -363,6 +383,154 @@ def pic_poisson_solve_static(nx, ny, nz, h, phi_cathode_V, phi_anode_V, rho_dev_
                                                  C.c_void_p(phi_dev_ptr), rtol, maxit, C.c_void_p(stream),
                                                  C.byref(it), C.byref(rel))
     return st, it.value, rel.value
+
+
+# ----------------------------------------------------------------------------
+# learned warm start (include/unet.h): device buffers are passed as raw device
+# pointers (e.g. torch tensor data_ptr()); weights as flat FP32 host arrays
+# ----------------------------------------------------------------------------
+def _ucheck(net, status):
+    if status != PIC_OK:
+        msg = load_library().unet_last_error(net)
+        raise PicError(status, msg.decode() if msg else "")
+    return status
+
+
+def unet_num_weights():
+    return int(load_library().unet_num_weights())
+
+
+def unet_create(D, H, W, stream=None):
+    if stream is None:
+        stream = _torch_stream()
+    net = C.c_void_p()
+    st = load_library().unet_create(D, H, W, C.c_void_p(stream), C.byref(net))
+    if st != PIC_OK:
+        raise PicError(st, f"unet_create({D}, {H}, {W})")
+    return net
+
+
+def unet_destroy(net):
+    if net:
+        load_library().unet_destroy(net)
+
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def unet_set_weights(net, w):
+    w = np.ascontiguousarray(w, dtype=np.float32).reshape(-1)
+    return _ucheck(net, load_library().unet_set_weights(net, _fp(w), w.size))
+
+
+def unet_get_weights(net):
+    w = np.zeros(unet_num_weights(), dtype=np.float32)
+    _ucheck(net, load_library().unet_get_weights(net, _fp(w), w.size))
+    return w
+
+
+def unet_get_grads(net):
+    g = np.zeros(unet_num_weights(), dtype=np.float32)
+    _ucheck(net, load_library().unet_get_grads(net, _fp(g), g.size))
+    return g
+
+
+def unet_forward(net, x_ptr, y_ptr):
+    return _ucheck(net, load_library().unet_forward(net, C.c_void_p(x_ptr), C.c_void_p(y_ptr)))
+
+
+def unet_backward(net, dy_ptr):
+    return _ucheck(net, load_library().unet_backward(net, C.c_void_p(dy_ptr)))
+
+
+def unet_train_step(net, x_ptr, t_ptr, loss_planes, lr):
+    loss = C.c_double()
+    _ucheck(net, load_library().unet_train_step(net, C.c_void_p(x_ptr), C.c_void_p(t_ptr), loss_planes, lr,
+                                                C.byref(loss)))
+    return loss.value
+
+
+def unet_make_sample(net, phi_new_ptr, phi_old_ptr, x_ptr, t_ptr):
+    s = C.c_double()
+    _ucheck(net, load_library().unet_make_sample(net, C.c_void_p(phi_new_ptr), C.c_void_p(phi_old_ptr),
+                                                 C.c_void_p(x_ptr), C.c_void_p(t_ptr), C.byref(s)))
+    return s.value
+
+
+def unet_layer_forward(net, layer, x_ptr, y_ptr, relu=False):
+    return _ucheck(net, load_library().unet_layer_forward(net, layer, C.c_void_p(x_ptr), C.c_void_p(y_ptr),
+                                                          1 if relu else 0))
+
+
+def unet_layer_backward(net, layer, x_ptr, dz_ptr, dx_ptr, n_dw):
+    dw = np.zeros(n_dw, dtype=np.float32)
+    _ucheck(net, load_library().unet_layer_backward(net, layer, C.c_void_p(x_ptr), C.c_void_p(dz_ptr),
+                                                    C.c_void_p(dx_ptr) if dx_ptr else None, _fp(dw), n_dw))
+    return dw
+
+
+def unet_launch_count():
+    return int(load_library().unet_launch_count())
+
+
+def pic_set_warm_unet(h, inst, net):
+    return _check(h, load_library().pic_set_warm_unet(h, inst, net if net else None))
+
+
+def pic_get_phi_device(h, inst, dev_ptr):
+    return _check(h, load_library().pic_get_phi_device(h, inst, C.c_void_p(dev_ptr)))
+
+
+class UNet:
+    """One network (include/unet.h) for D x H x W volumes; torch CUDA tensors as
+    device buffers."""
+
+    def __init__(self, D, H, W, weights=None, stream=None):
+        import torch
+        self.D, self.H, self.W = D, H, W
+        self.net = unet_create(D, H, W, stream)
+        self.y = torch.zeros((D, H, W), dtype=torch.float32, device="cuda")
+        if weights is not None:
+            self.set_weights(weights)
+
+    def close(self):
+        if self.net:
+            unet_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_weights(self, w):
+        unet_set_weights(self.net, w)
+
+    def weights(self):
+        return unet_get_weights(self.net)
+
+    def grads(self):
+        return unet_get_grads(self.net)
+
+    def forward(self, x):
+        """x: torch CUDA float32 tensor (2, D, H, W); returns a (D, H, W) tensor (the network's own buffer)."""
+        assert x.is_cuda and x.dtype.is_floating_point and x.is_contiguous()
+        unet_forward(self.net, x.data_ptr(), self.y.data_ptr())
+        return self.y
+
+    def backward(self, dy):
+        assert dy.is_cuda and dy.is_contiguous()
+        unet_backward(self.net, dy.data_ptr())
+        return self.grads()
+
+    def train_step(self, x, t, lr, loss_planes=None):
+        return unet_train_step(self.net, x.data_ptr(), t.data_ptr(), self.D - 1 if loss_planes is None else loss_planes,
+                               lr)
+
+    def make_sample(self, phi_new, phi_old, x, t):
+        return unet_make_sample(self.net, phi_new.data_ptr(), phi_old.data_ptr(), x.data_ptr(), t.data_ptr())
 
 
 def _torch_stream():

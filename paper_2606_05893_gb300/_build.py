@@ -17,7 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpic_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["pic_api.cu", "k_particles.cu", "k_grid.cu", "k_solver.cu", "k_sort.cu", "pic_static.cu"]
+SOURCES = ["pic_api.cu", "k_particles.cu", "k_grid.cu", "k_solver.cu", "k_sort.cu", "pic_static.cu", "unet_conv.cu",
+           "unet_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--diag-suppress=177,550", "-I", CSRC, "-I", INCLUDE]
@@ -31,7 +32,7 @@ def nvcc() -> str:
 
 
 def _deps():
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "pic.h")]
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     return max(os.path.getmtime(f) for f in files)
 
 

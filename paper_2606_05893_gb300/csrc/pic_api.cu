@@ -15,9 +15,11 @@
 #include <vector>
 
 #include "../../include/pic.h"
+#include "../../include/unet.h"
 #include "pic_internal.cuh"
 #include "pic_kernels.cuh"
 #include "pic_solver.cuh"
+#include "unet_warm.cuh"
 
 using namespace pic;
 
@@ -185,6 +187,7 @@ struct Instance {
   // surface-coupling output: ions absorbed at the cathode (cap 0: off)
   HitLog hits{};
   Circuit circ{};  // external circuit on the anode (off by default)
+  unet_handle* net = nullptr;  // learned warm start of the solve (not owned), nullptr: cfg.warm_start
   SegCtl* seg_ctl = nullptr;    // bucket path state (device)
   SegCtl* seg_host = nullptr;   // pinned mirror
   int32_t* seg_big = nullptr;   // buckets for the block-wide sort (ncell + 1)
@@ -837,6 +840,22 @@ pic_status step_instance(pic_handle* h, Instance* I) {
       CK(h, cudaMemsetAsync(I->phi + g.nplane, 0, sizeof(double) * I->solver.n, st));
       CK(h, I->solver.invalidate(st));
     }
+  }
+  if (I->net) {
+    // learned warm start: phi0 = phi_prev + s f(r / s, ramp), r the residual of phi_prev
+    unet::WarmTarget w;
+    if (I->mixed) {
+      w.hi = I->phi32 + g.nplane;
+      w.lo = I->solver.lo32;
+      w.f32 = I->solver.f32;
+      w.fold_first = I->solver.fold_first();
+      w.fold_last = I->solver.fold_last();
+    } else {
+      w.x64 = I->phi + g.nplane;
+      w.b64 = I->solver.b;
+    }
+    CK(h, unet::warm_start(I->net, w, st));
+    if (!I->mixed) CK(h, I->solver.invalidate(st));
   }
   CK(h, I->solver.launch(st));
   if (I->mixed) I->phi64_stale = true;
@@ -1723,6 +1742,30 @@ pic_status pic_set_mcc_background(pic_handle* h, int32_t inst, double density_m3
   if (!(density_m3 >= 0)) return fail(h, PIC_EINVAL, "density must be >= 0");
   h->inst[inst]->bg_density = density_m3;
   drop_step_graphs(h->inst[inst]);
+  return PIC_OK;
+}
+
+pic_status pic_set_warm_unet(pic_handle* h, int32_t inst, unet_handle* net) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  Instance* I = h->inst[inst];
+  if (net && !unet::warm_matches(net, I->g.nx, I->g.ny, I->g.nz))
+    return fail(h, PIC_EINVAL, "the network's volume must be nz x ny x nx = %d x %d x %d", I->g.nz, I->g.ny,
+                I->g.nx);
+  CK(h, cudaStreamSynchronize(I->stream));
+  I->net = net;
+  drop_step_graphs(I);
+  return PIC_OK;
+}
+
+pic_status pic_get_phi_device(pic_handle* h, int32_t inst, double* dev_out) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  if (!dev_out) return fail(h, PIC_EINVAL, "dev_out is NULL");
+  Instance* I = h->inst[inst];
+  CK(h, ensure_phi64(I, I->stream));
+  CK(h, cudaMemcpyAsync(dev_out, I->phi, sizeof(double) * I->g.nnode, cudaMemcpyDeviceToDevice, I->stream));
+  CK(h, cudaStreamSynchronize(I->stream));
   return PIC_OK;
 }
 

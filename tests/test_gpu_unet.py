@@ -1,0 +1,246 @@
+"""GPU parity of the U-Net warm start's network against the FP64 oracle
+(oracle/unet.py), through the C ABI (include/unet.h).
+
+Single layers. Each of the 14 3x3x3 convolutions runs alone on random
+BF16-representable inputs with every input channel in use (several 16-channel
+chunks, both halves of the concatenated layers) at its own resolution of a
+64 x 48 x 40 volume (5 to 10 voxels per side at the coarsest level, so every
+launch spans several 128-row tiles and ends in a ragged one). The forward
+output and the data gradient are stored in BF16 after FP32 accumulation: they
+differ from the oracle's FP64 value rounded to BF16 by at most one BF16 unit
+(2^-8 relative, only near rounding ties), so elements are held to 2^-7 of their
+size and the relative L2 norm to 2e-3. Weight gradients are FP32 sums over all
+voxels: relative L2 1e-3.
+
+The whole network. The GPU stores every activation and activation gradient in
+BF16 and takes its ReLU decisions on those values, so it is compared with the
+oracle run with the same rounding at the same points (the oracle's `rnd`
+hook). That BF16-stored network is itself chaotic at rounding ties: nudging
+each value by 1e-7 relative before its rounding (far below the FP32 against FP64
+accumulation difference) changes about 30 % of the stored values in the deep
+layers by one unit and moves the output by about 5e-3 and deep weight
+gradients by up to about 15 %. So the whole-network bound is self-calibrated:
+the GPU must lie within 3 times the distance between the staged oracle and that
+nudged copy (plus 1e-4). The plain FP64 oracle (no rounding) bounds the BF16
+network's own output error at 3e-2. Layer-level mistakes (a tap, a channel, a
+transposition, a mask) move results by order one and fail the layer tests.
+"""
+import numpy as np
+import pytest
+
+from oracle import unet as U
+from paper_2606_05893_gb300 import unet_inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FWD_TOL = 3e-2
+
+
+def bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as FP64."""
+    a32 = np.ascontiguousarray(a, dtype=np.float32)
+    u = a32.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def flat(ws):
+    return np.concatenate([w.reshape(-1) for w in ws])
+
+
+def unflat(v):
+    out, off = [], 0
+    for s in U.weight_shapes():
+        n = int(np.prod(s))
+        out.append(v[off:off + n].reshape(s).astype(np.float64))
+        off += n
+    return out
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def setup(D, H, W, seed):
+    import torch
+    import paper_2606_05893_gb300 as pkg
+    ws = [bf16(w) for w in I.init_weights(U.weight_shapes(), seed=seed)]
+    ws[-1] = bf16(ws[-1])  # output weights stay FP32 on the GPU; BF16 values are exact there too
+    x = bf16(I.random_volume(U.IN_CHANNELS, D, H, W, seed=seed + 1, smooth=1))
+    net = pkg.UNet(D, H, W, weights=flat(ws).astype(np.float32))
+    xt = torch.from_numpy(x.astype(np.float32)).cuda().contiguous()
+    return net, ws, x, xt
+
+
+VOL = (64, 48, 40)
+LEVEL_OF = {n: int(n[1]) for n in U.names()[:-1]}
+
+
+def bf16_nudged(rel, seed):
+    rng = np.random.default_rng(seed)
+
+    def f(a):
+        return bf16(a * (1.0 + rel * rng.standard_normal(a.shape)))
+    return f
+
+
+@pytest.mark.parametrize("layer", list(range(14)))
+def test_single_layer_forward_and_backward(layer):
+    import torch
+    import paper_2606_05893_gb300 as pkg
+    name, cin, cout = U.LAYERS[layer]
+    lev = LEVEL_OF[name]
+    D, H, W = (v >> lev for v in VOL)
+    ws = [bf16(w) for w in I.init_weights(U.weight_shapes(), seed=60 + layer)]
+    net = pkg.UNet(*VOL, weights=flat(ws).astype(np.float32))
+    w = ws[layer]
+    x = bf16(I.random_volume(cin, D, H, W, seed=70 + layer))
+    dz = bf16(I.random_volume(cout, D, H, W, seed=80 + layer))
+    xt = torch.from_numpy(x.astype(np.float32)).cuda().contiguous()
+    dzt = torch.from_numpy(dz.astype(np.float32)).cuda().contiguous()
+    yt = torch.zeros((cout, D, H, W), dtype=torch.float32, device="cuda")
+    dxt = torch.zeros((cin, D, H, W), dtype=torch.float32, device="cuda")
+    pkg.unet_layer_forward(net.net, layer, xt.data_ptr(), yt.data_ptr(), relu=True)
+    dw = pkg.unet_layer_backward(net.net, layer, xt.data_ptr(), dzt.data_ptr(), dxt.data_ptr(),
+                                 27 * cin * cout).reshape(cout, cin, 3, 3, 3)
+    net.close()
+    y, dx = yt.cpu().numpy().astype(np.float64), dxt.cpu().numpy().astype(np.float64)
+    yo = bf16(U.relu(U.conv3x3(x, w)))
+    dxo, dwo = U.conv3x3_backward(x, w, dz)
+    dxo_r = bf16(dxo)
+    # FP32 accumulation leaves an absolute error of order u32 sqrt(K) sum |w x| before the
+    # BF16 rounding; 2^-18 sum |w x| covers it, 2^-7 of the value covers one BF16 unit
+    s_fwd = U.conv3x3(np.abs(x), np.abs(w))
+    s_dx = U.conv3x3_backward(np.abs(x), np.abs(w), np.abs(dz))[0]
+    for got, ref, sabs, what in ((y, yo, s_fwd, "forward"), (dx, dxo_r, s_dx, "data gradient")):
+        d = np.abs(got - ref)
+        bound = 2.0 ** -7 * np.maximum(np.abs(ref), np.abs(got)) + 2.0 ** -18 * sabs
+        assert np.all(d <= bound), (name, what, int((d > bound).sum()), float((d - bound).max()))
+        assert rel_l2(got, ref) <= 1e-3, (name, what, rel_l2(got, ref))
+    assert rel_l2(dw, dwo) <= 1e-3, (name, "weight gradient", rel_l2(dw, dwo))
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (32, 16, 24), (24, 40, 8)])
+def test_network_forward_matches_oracle(shape):
+    D, H, W = shape
+    net, ws, x, xt = setup(D, H, W, seed=21)
+    y = net.forward(xt).cpu().numpy().astype(np.float64)
+    net.close()
+    p = dict(zip(U.names(), ws))
+    ys = U.forward(p, x, rnd=bf16)[0][0]
+    yn = U.forward(p, x, rnd=bf16_nudged(1e-7, 3))[0][0]
+    yo = U.forward(p, x)[0][0]
+    sens = rel_l2(yn, ys)
+    e_staged, e = rel_l2(y, ys), rel_l2(y, yo)
+    print(f"forward: staged {e_staged:.2e} (nudged oracle {sens:.2e}), plain FP64 {e:.2e}")
+    assert np.isfinite(y).all()
+    assert e_staged <= 3 * sens + 1e-4, (e_staged, sens)
+    assert e <= FWD_TOL, e
+
+
+def test_weights_round_trip_and_zero_network():
+    import torch
+    import paper_2606_05893_gb300 as pkg
+    net = pkg.UNet(8, 8, 16)
+    w = np.random.default_rng(4).standard_normal(pkg.unet_num_weights()).astype(np.float32)
+    net.set_weights(w)
+    assert np.array_equal(net.weights(), w)
+    net.set_weights(np.zeros_like(w))
+    x = torch.randn((2, 8, 8, 16), device="cuda")
+    assert not net.forward(x).cpu().numpy().any()
+    net.close()
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (32, 16, 24)])
+def test_network_weight_gradients_match_oracle(shape):
+    import torch
+    D, H, W = shape
+    net, ws, x, xt = setup(D, H, W, seed=33)
+    dy = bf16(I.random_volume(1, D, H, W, seed=34))
+    dyt = torch.from_numpy(dy[0].astype(np.float32)).cuda().contiguous()
+    net.forward(xt)
+    g = unflat(net.backward(dyt))
+    net.close()
+    p = dict(zip(U.names(), ws))
+    _, cs = U.forward(p, x, rnd=bf16)
+    gs, _ = U.backward(p, cs, dy, rnd=bf16)
+    nud = bf16_nudged(1e-7, 4)
+    _, cn = U.forward(p, x, rnd=nud)
+    gn, _ = U.backward(p, cn, dy, rnd=nud)
+    staged = {n: rel_l2(gg, gs[n]) for n, gg in zip(U.names(), g)}
+    sens = {n: rel_l2(gn[n], gs[n]) for n in U.names()}
+    print("gradient relative L2 errors (GPU / nudged oracle):",
+          {n: f"{staged[n]:.1e}/{sens[n]:.1e}" for n in U.names()})
+    bad = {n: (staged[n], sens[n]) for n in U.names() if not staged[n] <= 3 * sens[n] + 1e-3}
+    assert not bad, bad
+
+
+def test_make_sample_matches_host():
+    import torch
+    import paper_2606_05893_gb300 as pkg
+    nz, ny, nx = 16, 8, 24
+    rng = np.random.default_rng(8)
+    po = rng.standard_normal((nz + 1, ny, nx))
+    pn = po + 1e-3 * rng.standard_normal(po.shape)
+    pn[0] = po[0]
+    pn[-1] = po[-1]
+    net = pkg.UNet(nz, ny, nx)
+    x = torch.zeros((2, nz, ny, nx), dtype=torch.float32, device="cuda")
+    t = torch.zeros((nz, ny, nx), dtype=torch.float32, device="cuda")
+    s = net.make_sample(torch.from_numpy(pn).cuda(), torch.from_numpy(po).cuda(), x, t)
+    # host: delta on the unknown planes, zero Dirichlet planes, periodic x/y
+    dl = np.zeros((nz + 1, ny, nx))
+    dl[1:nz] = (pn - po)[1:nz]
+    A = 6 * dl - np.roll(dl, 1, 2) - np.roll(dl, -1, 2) - np.roll(dl, 1, 1) - np.roll(dl, -1, 1)
+    A[1:nz] -= dl[0:nz - 1] + dl[2:nz + 1]
+    r = A[1:nz]
+    s_ref = np.sqrt((r ** 2).mean())
+    assert s == pytest.approx(s_ref, rel=1e-12)
+    xr = np.zeros((2, nz, ny, nx))
+    xr[0, :nz - 1] = r / s_ref
+    xr[1] = ((np.arange(nz) + 1) / nz)[:, None, None]
+    tr = np.zeros((nz, ny, nx))
+    tr[:nz - 1] = dl[1:nz] / s_ref
+    assert np.abs(x.cpu().numpy() - xr).max() <= 1e-6 * np.abs(xr).max()
+    assert np.abs(t.cpu().numpy() - tr).max() <= 1e-6 * np.abs(tr).max()
+    net.close()
+
+
+def test_training_reduces_the_loss():
+    """Adam on the masked MSE loss: the first step moves every weight by
+    -lr g / (|g| + eps) with g the gradient of unet_backward for dL/dy (Kingma
+    and Ba: m_hat = g, v_hat = g^2 at t = 1); later steps move a weight by at
+    most lr (1 - beta1) / sqrt(1 - beta2); 30 steps on one sample cut the loss;
+    the reported loss is the staged oracle's loss of the pass before the update."""
+    import torch
+    D, H, W = 16, 16, 16
+    lr = 1e-3
+    net, ws, x, xt = setup(D, H, W, seed=44)
+    tgt = torch.from_numpy(I.random_volume(1, D, H, W, seed=45, smooth=3)[0].astype(np.float32)).cuda()
+    mask = torch.ones((D, H, W), device="cuda")
+    mask[D - 1] = 0
+    y = net.forward(xt).clone()
+    dy = (2.0 / float(mask.sum())) * (y - tgt) * mask
+    g = net.backward(dy.contiguous())
+    w0 = net.weights()
+    losses = [net.train_step(xt, tgt, lr)]
+    w1 = net.weights()
+    big = np.abs(g) > 1e-6
+    assert big.sum() > 0.5 * g.size
+    step = (w1 - w0)[big]
+    assert np.abs(step + lr * g[big] / (np.abs(g[big]) + 1e-8)).max() <= 1e-3 * lr
+    losses += [net.train_step(xt, tgt, lr) for _ in range(29)]
+    w30 = net.weights()
+    assert np.isfinite(losses).all()
+    assert losses[-1] < 0.7 * losses[0], losses
+    assert np.abs(w30 - w0).max() <= 30 * lr * 0.1 / np.sqrt(1e-3) * 1.001
+    # the loss is the oracle's masked MSE of the forward pass before the update
+    w30r = unflat(w30)
+    p = dict(zip(U.names(), [bf16(w) for w in w30r[:-1]] + [w30r[-1]]))
+    loss_gpu = net.train_step(xt, tgt, 0.0)
+    y, _ = U.forward(p, bf16(x), rnd=bf16)
+    m = np.ones((1, D, H, W), dtype=bool)
+    m[:, D - 1] = False
+    lo, _ = U.mse_loss(y, tgt.cpu().numpy()[None].astype(np.float64), m)
+    assert loss_gpu == pytest.approx(lo, rel=3e-2)
+    net.close()
