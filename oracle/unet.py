@@ -205,3 +205,31 @@ def adam_step(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 def names():
     return [n for n, _, _ in LAYERS] + [OUT[0]]
+
+
+# ----------------------------------------------------------------------------
+# the loss the warm start is trained on: the residual it leaves
+# ----------------------------------------------------------------------------
+def apply_A(y):
+    """The scaled 7-point operator of Eq. (1) on a (1, D, H, W) network volume whose
+    planes d = 0..D-2 are the unknown node planes k = d + 1 and whose last plane
+    lies on the anode: periodic in x (W) and y (H), zero Dirichlet values on the
+    cathode plane (d = -1) and the anode plane (d = D - 1). The last plane of the
+    result is 0."""
+    z = np.array(y, dtype=np.float64, copy=True)
+    z[:, -1] = 0.0
+    a = 6.0 * z - np.roll(z, 1, 3) - np.roll(z, -1, 3) - np.roll(z, 1, 2) - np.roll(z, -1, 2)
+    a[:, 1:] -= z[:, :-1]
+    a[:, :-1] -= z[:, 1:]
+    a[:, -1] = 0.0
+    return a
+
+
+def residual_loss(y, r):
+    """L = mean over the unknown planes of (r - A y)^2, the squared residual that
+    the initial guess y leaves for the right-hand side r (both scaled by the same
+    s), and dL/dy = -(2 / n) A (r - A y) (A is symmetric)."""
+    e = np.array(r, dtype=np.float64, copy=True) - apply_A(y)
+    e[:, -1] = 0.0
+    n = e[:, :-1].size
+    return float((e * e).sum() / n), -2.0 / n * apply_A(e)

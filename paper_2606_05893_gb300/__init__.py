@@ -389,6 +389,15 @@ def pic_poisson_solve_static(nx, ny, nz, h, phi_cathode_V, phi_anode_V, rho_dev_
 # learned warm start (include/unet.h): device buffers are passed as raw device
 # pointers (e.g. torch tensor data_ptr()); weights as flat FP32 host arrays
 # ----------------------------------------------------------------------------
+# The library's network (layer table of csrc/unet_api.cu): the 3x3x3 convolutions
+# in the order e0a e0b e1a e1b e2a e2b e3a e3b d2a d2b d1a d1b d0a d0b as
+# (name, input channels, output channels), then the 1x1x1 output layer.
+UNET_LAYERS = (("e0a", 2, 16), ("e0b", 16, 16), ("e1a", 16, 32), ("e1b", 32, 32), ("e2a", 32, 64),
+               ("e2b", 64, 64), ("e3a", 64, 128), ("e3b", 128, 128), ("d2a", 192, 64), ("d2b", 64, 64),
+               ("d1a", 96, 32), ("d1b", 32, 32), ("d0a", 48, 16), ("d0b", 16, 16))
+UNET_WEIGHT_SHAPES = [(co, ci, 3, 3, 3) for _, ci, co in UNET_LAYERS] + [(1, 16)]
+
+
 def _ucheck(net, status):
     if status != PIC_OK:
         msg = load_library().unet_last_error(net)

@@ -189,3 +189,40 @@ def test_mse_loss_gradient():
         ym[idx] -= eps
         fd = (U.mse_loss(yp, t, mask)[0] - U.mse_loss(ym, t, mask)[0]) / (2 * eps)
         assert abs(fd - dy[idx]) <= 1e-7
+
+
+def test_library_architecture_table_matches_the_oracle():
+    """The library's layer table is written separately from the oracle's: same
+    layers, same shapes, same flat weight count."""
+    import paper_2606_05893_gb300 as pkg
+    assert [n for n, _, _ in pkg.UNET_LAYERS] == [n for n, _, _ in U.LAYERS]
+    assert [tuple(s) for s in pkg.UNET_WEIGHT_SHAPES] == [tuple(s) for s in U.weight_shapes()]
+
+
+def test_operator_eigenfunction_and_residual_loss_gradient():
+    """A sin(pi m (d+1) / D) cos(2 pi k x / W) cos(2 pi l y / H) = (6 - 2 cos(pi m / D)
+    - 2 cos(2 pi k / W) - 2 cos(2 pi l / H)) times the same on the unknown planes
+    (the discrete Dirichlet-periodic eigenfunctions); the residual loss's gradient
+    by central differences."""
+    D, H, W = 8, 6, 10
+    d = np.arange(D)[:, None, None]
+    yy = np.arange(H)[None, :, None]
+    xx = np.arange(W)[None, None, :]
+    for m, k, l in [(1, 0, 0), (3, 2, 1), (7, 5, 3)]:
+        f = np.sin(np.pi * m * (d + 1) / D) * np.cos(2 * np.pi * k * xx / W) * np.cos(2 * np.pi * l * yy / H)
+        lam = 6 - 2 * np.cos(np.pi * m / D) - 2 * np.cos(2 * np.pi * k / W) - 2 * np.cos(2 * np.pi * l / H)
+        Af = U.apply_A(f[None])[0]
+        assert np.abs(Af[:-1] - lam * f[:-1]).max() <= 1e-13 and not Af[-1].any()
+    rng = np.random.default_rng(14)
+    y, r = rng.standard_normal((1, D, H, W)), rng.standard_normal((1, D, H, W))
+    L, dy = U.residual_loss(y, r)
+    e = r - U.apply_A(y)
+    assert L == pytest.approx((e[:, :-1] ** 2).mean(), rel=1e-14)
+    assert not dy[:, -1].any()
+    eps = 1e-6
+    for idx in [(0, 0, 0, 0), (0, 3, 2, 7), (0, 6, 5, 9), (0, 7, 1, 1)]:
+        yp, ym = y.copy(), y.copy()
+        yp[idx] += eps
+        ym[idx] -= eps
+        fd = (U.residual_loss(yp, r)[0] - U.residual_loss(ym, r)[0]) / (2 * eps)
+        assert abs(fd - dy[idx]) <= 1e-7 * max(1.0, abs(fd)), (idx, fd, dy[idx])
