@@ -88,6 +88,16 @@ pic_status unet_layer_forward(unet_handle* net, int32_t layer, const float* x_de
 pic_status unet_layer_backward(unet_handle* net, int32_t layer, const float* x_dev, const float* dz_dev, float* dx_dev,
                                float* dw_host, int64_t n_dw);
 
+/* One training step on the warm start's own objective: forward on x_dev
+ * (2 x D x H x W, channel 0 the scaled residual r / s of the previous
+ * potential), loss L = mean over the unknown planes (all but the last) of
+ * (r / s - A y)^2 -- the scaled residual the warm start phi_prev + s y leaves,
+ * A the 7-point operator of Eq. (1) with zero values on the cathode plane below
+ * the volume and on its last (anode) plane, periodic x/y -- then backward with
+ * dL/dy = -(2 / n) A (r / s - A y) and one Adam update as unet_train_step.
+ * *loss (host, may be NULL) receives L before the update. */
+pic_status unet_train_step_residual(unet_handle* net, const float* x_dev, float lr, double* loss);
+
 /* Text of the last error on this network (static storage, never NULL). */
 const char* unet_last_error(unet_handle* net);
 

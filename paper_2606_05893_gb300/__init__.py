@@ -89,7 +89,8 @@ EXPORTED = ["pic_create", "pic_inject", "pic_inject_particles", "pic_step", "pic
             "pic_set_warm_unet", "pic_get_phi_device",
             "unet_num_weights", "unet_create", "unet_destroy", "unet_set_weights", "unet_get_weights",
             "unet_forward", "unet_backward", "unet_get_grads", "unet_train_step", "unet_last_error",
-            "unet_launch_count", "unet_make_sample", "unet_layer_forward", "unet_layer_backward"]
+            "unet_launch_count", "unet_make_sample", "unet_layer_forward", "unet_layer_backward",
+            "unet_train_step_residual"]
 
 _lib = None
 
@@ -161,6 +162,7 @@ def load_library(path: str = LIB_PATH):
         "unet_launch_count": ([], C.c_uint64),
         "unet_make_sample": ([P, P, P, P, P, d], st),
         "unet_layer_forward": ([P, C.c_int32, P, P, C.c_int32], st),
+        "unet_train_step_residual": ([P, P, C.c_float, d], st),
         "unet_layer_backward": ([P, C.c_int32, P, P, P, C.POINTER(C.c_float), C.c_int64], st),
     }
     for name, (args, res) in sig.items():
@@ -460,6 +462,12 @@ def unet_train_step(net, x_ptr, t_ptr, loss_planes, lr):
     return loss.value
 
 
+def unet_train_step_residual(net, x_ptr, lr):
+    loss = C.c_double()
+    _ucheck(net, load_library().unet_train_step_residual(net, C.c_void_p(x_ptr), lr, C.byref(loss)))
+    return loss.value
+
+
 def unet_make_sample(net, phi_new_ptr, phi_old_ptr, x_ptr, t_ptr):
     s = C.c_double()
     _ucheck(net, load_library().unet_make_sample(net, C.c_void_p(phi_new_ptr), C.c_void_p(phi_old_ptr),
@@ -537,6 +545,10 @@ class UNet:
     def train_step(self, x, t, lr, loss_planes=None):
         return unet_train_step(self.net, x.data_ptr(), t.data_ptr(), self.D - 1 if loss_planes is None else loss_planes,
                                lr)
+
+    def train_step_residual(self, x, lr):
+        """Adam step on the residual the warm start leaves (unet_train_step_residual)."""
+        return unet_train_step_residual(self.net, x.data_ptr(), lr)
 
     def make_sample(self, phi_new, phi_old, x, t):
         return unet_make_sample(self.net, phi_new.data_ptr(), phi_old.data_ptr(), x.data_ptr(), t.data_ptr())

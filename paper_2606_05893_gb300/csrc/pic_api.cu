@@ -848,8 +848,6 @@ pic_status step_instance(pic_handle* h, Instance* I) {
       w.hi = I->phi32 + g.nplane;
       w.lo = I->solver.lo32;
       w.f32 = I->solver.f32;
-      w.fold_first = I->solver.fold_first();
-      w.fold_last = I->solver.fold_last();
     } else {
       w.x64 = I->phi + g.nplane;
       w.b64 = I->solver.b;

@@ -407,6 +407,47 @@ __global__ void k_unpack_dense(Vol v, int C, const __nv_bfloat16* t, float* x) {
   }
 }
 
+// residual loss, pass 1: e = x0 - A y on the unknown planes (the last plane is
+// the anode: y there counts as 0, e = 0); sum e^2
+__device__ __forceinline__ float stencil_A(const Vol& v, const float* __restrict__ f, long long n, int d, int j, int i) {
+  const long long hw = (long long)v.H * v.W;
+  const int im = i == 0 ? v.W - 1 : i - 1, ip = i == v.W - 1 ? 0 : i + 1;
+  const int jm = j == 0 ? v.H - 1 : j - 1, jp = j == v.H - 1 ? 0 : j + 1;
+  const long long row = n - i;
+  float a = 6.f * f[n] - f[row + im] - f[row + ip] - f[n + (long long)(jm - j) * v.W] - f[n + (long long)(jp - j) * v.W];
+  if (d > 0) a -= f[n - hw];
+  if (d < v.D - 2) a -= f[n + hw];
+  return a;
+}
+
+__global__ void k_resid_e(Vol v, const float* __restrict__ x0, const float* __restrict__ y, float* e, double* loss) {
+  double acc = 0.0;
+  VOXELS(v, n) {
+    int d, j, i;
+    decode(v, n, d, j, i);
+    if (d >= v.D - 1) {
+      e[n] = 0.f;
+      continue;
+    }
+    const float r = x0[n] - stencil_A(v, y, n, d, j, i);
+    e[n] = r;
+    acc += (double)r * r;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+}
+
+// pass 2: dy = -(2 / n) A e (0 on the anode plane); loss /= n once
+__global__ void k_resid_dy(Vol v, const float* __restrict__ e, double inv_n, float* dy, double* loss) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) loss[0] *= inv_n;
+  const float c = (float)(-2.0 * inv_n);
+  VOXELS(v, n) {
+    int d, j, i;
+    decode(v, n, d, j, i);
+    dy[n] = d >= v.D - 1 ? 0.f : c * stencil_A(v, e, n, d, j, i);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host helpers
 // ---------------------------------------------------------------------------
@@ -688,11 +729,14 @@ __global__ void k_warm_apply64(Vol v, const double* s_dev, const float* __restri
   }
 }
 
-// mixed store: r = f + folded electrode terms - A (hi + lo) in FP32 (hi over the
-// unknown view of phi32, lo over the unknowns); dense into r_out; sum r^2
+// mixed store: phi = vacuum ramp + hi + lo, and A (vacuum ramp) equals the folded
+// electrode terms, so r = f - A (hi + lo) with zero values on the electrode
+// planes, in FP32 (hi over the unknown view of phi32, lo over the unknowns);
+// dense into r_out; sum r^2. (With an external circuit the anode's offset from
+// the configured voltage is a further folded term, left out here: it only
+// makes this starting residual, not the solve, approximate.)
 __global__ void k_warm_resid32(Vol v, const float* __restrict__ hi, const float* __restrict__ lo,
-                               const float* __restrict__ f, float fold_first, float fold_last, float* r_out,
-                               double* ss) {
+                               const float* __restrict__ f, float* r_out, double* ss) {
   const int nx = v.W, ny = v.H, nz = v.D;
   const long long pl = (long long)nx * ny;
   double acc = 0.0;
@@ -711,10 +755,7 @@ __global__ void k_warm_resid32(Vol v, const float* __restrict__ hi, const float*
     float s = X(row + im) + X(row + ip) + X(u + (long long)(jm - j) * nx) + X(u + (long long)(jp - j) * nx);
     if (d > 0) s += X(u - pl);
     if (d < nz - 2) s += X(u + pl);
-    float bb = f[u];
-    if (d == 0) bb += fold_first;
-    if (d == nz - 2) bb += fold_last;
-    const float r = bb - (6.f * X(u) - s);
+    const float r = f[u] - (6.f * X(u) - s);
     r_out[n] = r;
     acc += (double)r * r;
   }
@@ -745,7 +786,7 @@ cudaError_t warm_start(unet_handle* n, const WarmTarget& w, cudaStream_t st) {
   if (w.x64)
     ULAUNCH(grid_for(nv), 256, 0, st, k_warm_resid64)(v, w.x64, w.b64, r, n->red + 1);
   else
-    ULAUNCH(grid_for(nv), 256, 0, st, k_warm_resid32)(v, w.hi, w.lo, w.f32, w.fold_first, w.fold_last, r, n->red + 1);
+    ULAUNCH(grid_for(nv), 256, 0, st, k_warm_resid32)(v, w.hi, w.lo, w.f32, r, n->red + 1);
   // scale the residual by its root mean square over the unknowns, ramp in channel 1
   ULAUNCH(grid_for(nv), 256, 0, st, k_sample_scale)(v, n->red + 1, (double)(v.D - 1) * v.H * v.W, r, ramp, nullptr,
                                                     n->red + 2);
@@ -1005,6 +1046,31 @@ extern "C" pic_status unet_layer_backward(unet_handle* n, int32_t layer, const f
   if (ps != PIC_OK) return ps;
   store_to_host(L.def, L.cin, g.data(), dw_host);
   return PIC_OK;
+}
+
+extern "C" pic_status unet_train_step_residual(unet_handle* n, const float* x, float lr, double* loss) {
+  if (!n || !x || !(lr >= 0.f)) return fail(n, PIC_EINVAL, "unet_train_step_residual: bad argument");
+  cudaStream_t st = n->stream;
+  const Vol& v = n->vol[0];
+  const long long nv = (long long)v.D * v.H * v.W;
+  cudaError_t e = forward(n, x, n->y, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->red + 3, 0, sizeof(double), st);
+  if (e != cudaSuccess) return fail(n, PIC_ECUDA, "unet_train_step_residual: %s", cudaGetErrorString(e));
+  float* ebuf = n->xin;  // scratch (the warm start's input buffer)
+  ULAUNCH(grid_for(nv), 256, 0, st, k_resid_e)(v, x, n->y, ebuf, n->red + 3);
+  ULAUNCH(grid_for(nv), 256, 0, st, k_resid_dy)(v, ebuf, 1.0 / ((double)(v.D - 1) * v.H * v.W), n->dy, n->red + 3);
+  e = backward(n, n->dy, nullptr, v.D, st);
+  if (e != cudaSuccess) return fail(n, PIC_ECUDA, "unet_train_step_residual: %s", cudaGetErrorString(e));
+  n->adam_t += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)n->adam_t), c2 = 1.f - powf(b2, (float)n->adam_t);
+  ULAUNCH(grid_for(n->n_store), 256, 0, st, k_adam)(n->wbuf, n->wbuf + n->n_store, n->wbuf + 2 * n->n_store,
+                                                    n->wbuf + 3 * n->n_store, n->n_store, lr, b1, b2, 1e-8f, c1, c2);
+  rebuild_images(n, st);
+  n->have_forward = false;
+  if (loss && cudaMemcpyAsync(loss, n->red + 3, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return fail(n, PIC_ECUDA, "unet_train_step_residual: loss read failed");
+  return check_err(n);
 }
 
 extern "C" pic_status unet_make_sample(unet_handle* n, const double* pn, const double* po, float* x, float* t,

@@ -9,15 +9,13 @@ namespace unet {
 
 // Where the initial guess lives: the FP64 store's unknown view of phi and the
 // right-hand side b over the unknowns; or the mixed store's FP32 hi (unknown
-// view of phi32), lo, charge term f and the Dirichlet values folded into the
-// first and last unknown planes.
+// view of phi32), lo and charge term f.
 struct WarmTarget {
   double* x64 = nullptr;
   const double* b64 = nullptr;
   float* hi = nullptr;
   const float* lo = nullptr;
   const float* f32 = nullptr;
-  float fold_first = 0.f, fold_last = 0.f;
 };
 
 bool warm_matches(const unet_handle* n, int nx, int ny, int nz);

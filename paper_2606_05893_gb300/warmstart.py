@@ -12,8 +12,12 @@ residual the previous potential leaves in this step's problem, target delta / s,
 delta = phi_n - phi_{n-1} (unet_make_sample). That is what the warm start meets:
 it starts the solve of step n from phi_{n-1} + s f(r / s, ramp).
 
-Training. Adam on the masked MSE over the unknown planes, one sample per step,
-samples drawn in a seeded random order.
+Training. Adam, one sample per step, samples drawn in a seeded random order, on
+the residual the warm start leaves, mean (r / s - A y)^2 over the unknown
+planes (unet_train_step_residual): the solve's iteration count depends on that
+residual. (The squared error against delta / s is the other choice; it weights
+smooth components, which A shrinks, and leaves high-frequency errors, which A
+amplifies up to twelvefold, so it does not lower the starting residual.)
 
 Evaluation. Two instances of the same held-out workload, one with the plain warm
 start (the previous step's potential) and one with the network, both solved to
@@ -78,9 +82,12 @@ def collect(wls, steps_per_run, skip, net, precision=None, samples=None, log=Non
     return samples
 
 
-def train(net, samples, iters, lr=1e-3, lr_end=None, seed=0, log=None, every=100):
+def train(net, samples, iters, lr=1e-3, lr_end=None, seed=0, log=None, every=100, objective="residual"):
     """Adam over the samples in a seeded random order; the learning rate decays
-    geometrically from lr to lr_end (default lr / 10). Returns the losses."""
+    geometrically from lr to lr_end (default lr / 10). objective "residual"
+    minimises the scaled residual the warm start leaves (the quantity the solve
+    then reduces), "target" the squared error against delta / s. Returns the
+    losses."""
     rng = np.random.default_rng(seed)
     lr_end = lr / 10 if lr_end is None else lr_end
     losses = []
@@ -93,7 +100,10 @@ def train(net, samples, iters, lr=1e-3, lr_end=None, seed=0, log=None, every=100
         i = int(order[k])
         k += 1
         a = lr * (lr_end / lr) ** (it / max(iters - 1, 1))
-        losses.append(net.train_step(samples.X[i], samples.T[i], a))
+        if objective == "residual":
+            losses.append(net.train_step_residual(samples.X[i], a))
+        else:
+            losses.append(net.train_step(samples.X[i], samples.T[i], a))
         if log and (it + 1) % every == 0:
             log(f"iter {it + 1}: loss {np.mean(losses[-every:]):.4e} lr {a:.2e} ({time.perf_counter() - t0:.1f} s)")
     return losses

@@ -300,13 +300,15 @@ def config_ensemble(seed: int = 0, n_instances: int = 48, sides=(32, 64, 96, 128
 
 
 def config_warm_start(seed: int = 0, n_preload: int = 10_000_000, nx: int = 128, ny: int = 128, nz: int = 256,
-                      h: float = 2.5e-9):
+                      h: float = 2.5e-9, capacity_factor: float = 1.25, r_emit: float = 40e-9):
     """A run for the learned warm start's samples: the at-scale physics on the
     128x128x256 grid with the applied field uniform in [5, 15] GV/m, J uniform
     in [5e11, 5e12] A/m^2 (as the at-scale workload) and the Cu flux log-uniform
-    in [1e26, 1e28] m^-2 s^-1, all drawn from the seed."""
+    in [1e26, 1e28] m^-2 s^-1, all drawn from the seed (emitter radius 40 nm as at
+    scale; smaller boxes take a smaller one so injection stays a small fraction
+    of the population per step)."""
     rng = np.random.default_rng(10_000 + seed)
     field = rng.uniform(5e9, 15e9)
     flux = math.exp(rng.uniform(math.log(1e26), math.log(1e28)))
     return config_scale(seed=seed, n_preload=n_preload, nx=nx, ny=ny, nz=nz, h=h, anode_V=field * nz * h,
-                        neutral_flux=flux)
+                        neutral_flux=flux, capacity_factor=capacity_factor, r_emit=r_emit)
