@@ -49,6 +49,9 @@ FALLBACK_HBM_GBS = 6800.0
 # Algorithmic bytes per particle of the fused gather/push/collide/compact kernel:
 # read the particle record and write it once (the node field is gathered from L2).
 BYTES_PER_PARTICLE = {"mixed": 32 + 32, "fp64": 52 + 52}
+# DRAM bytes (read + write) per launch of the forward convolutions captured with ncu
+# (profiles/unet_conv_forward_128x128x256.md); layers without a capture are absent
+UNET_NCU_TRAFFIC = {"d0a": 541.8e6}
 # DRAM bytes (read + write) per pushed electron of the same kernel from one ncu capture of the
 # current kernel (profiles/k_push_mixed_electrons_128x128x256.md: 145.18 MB for 2 593 379
 # electrons); None where no capture of the current kernel exists
@@ -60,6 +63,17 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def peak_tflops():
+    """Sustained BF16 tensor throughput (the network runs inside a long step)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained"]), "measured, sustained"
+    except Exception:
+        return 1700.0, "fallback, sustained"
 
 
 def peaks():
@@ -422,6 +436,102 @@ def run_gpu_ensemble(args, rank, ws, local):
     return info, agg
 
 
+def run_warm_start_leg(args, peak_tflops, peak_kind):
+    """Learned warm start on the 128x128x256 grid: samples from runs at random field,
+    J and Cu flux, training on the GPU with the library's kernels (residual
+    objective), then on a held-out run the solve's iterations, the network's
+    inference time and the step throughput with and without it, both solved to the
+    workload's 1e-8 relative residual."""
+    import torch
+    import paper_2606_05893_gb300 as pkg
+    from paper_2606_05893_gb300 import unet_inputs
+    from paper_2606_05893_gb300 import warmstart as WS
+    from paper_2606_05893_gb300 import workloads as W
+    t_all = time.perf_counter()
+    n_pre = args.c5_n_preload
+    runs = [W.config_warm_start(seed=100 + k, n_preload=n_pre) for k in range(args.c5_runs)]
+    held = W.config_warm_start(seed=1000, n_preload=n_pre)
+    D, H, Wd = held.nz, held.ny, held.nx
+    net = pkg.UNet(D, H, Wd)
+    w0 = np.concatenate([w.reshape(-1) for w in unet_inputs.init_weights(pkg.UNET_WEIGHT_SHAPES, seed=0)])
+    net.set_weights(w0.astype(np.float32))
+    t0 = time.perf_counter()
+    samples = WS.collect(runs, args.c5_samples, 5, net, precision=pkg.PIC_MIXED)
+    collect_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = WS.train(net, samples, args.c5_iters, lr=args.c5_lr, seed=0)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    ratio = WS.residual_ratio(net, samples, range(0, samples.n, max(1, samples.n // 6)))
+    # inference: CUDA events around whole forward passes and around each convolution
+    x = samples.X[0]
+    for _ in range(3):
+        net.forward(x)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.c5_infer):
+        net.forward(x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    infer_ms = e0.elapsed_time(e1) / args.c5_infer
+    pkg.unet_set_profiling(net.net, True)
+    for _ in range(args.c5_infer):
+        net.forward(x)
+    lt = pkg.unet_get_layer_times(net.net)
+    pkg.unet_set_profiling(net.net, False)
+    flops = {}
+    for name, ci, co in pkg.UNET_LAYERS:
+        lev = int(name[1])
+        flops[name] = 2.0 * (D >> lev) * (H >> lev) * (Wd >> lev) * 27 * ci * co
+    top = max(lt, key=lambda k: lt[k][0])
+    top_ms = lt[top][0] / max(lt[top][1], 1)
+    achieved = flops[top] / (top_ms * 1e-3) / 1e12
+    net_flops = sum(flops.values())
+    out = {"workload": "128x128x256 cells h=2.5nm, 1e7 macroparticles per run, field U[5,15] GV/m, J U[5e11,5e12], "
+                       "Cu flux logU[1e26,1e28]; network 4 levels 16/32/64/128 channels, 3x3x3, BF16/FP32",
+           "samples": samples.n, "runs": len(runs), "collect_s": round(collect_s, 1),
+           "train_iters": len(losses), "train_s": round(train_s, 1),
+           "train_ms_per_iter": round(1e3 * train_s / max(len(losses), 1), 2),
+           "loss_first_last": [float(np.mean(losses[:50])), float(np.mean(losses[-50:]))],
+           "train_residual_ratio": float(np.mean(ratio)),
+           "inference_ms": infer_ms, "network_gflop": net_flops / 1e9,
+           "network_tflops": net_flops / (infer_ms * 1e-3) / 1e12,
+           "roofline": {"bound": "tensor", "kernel": f"k_conv3 forward, layer {top}", "achieved": achieved,
+                        "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                        "peak_kind": peak_kind, "flop_per_launch": flops[top], "launch_ms": top_ms,
+                        "traffic": UNET_NCU_TRAFFIC.get(top)},
+           "layer_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in lt.items()}}
+    for prec_name, prec in (("mixed", pkg.PIC_MIXED), ("fp64", pkg.PIC_FP64)):
+        ev = WS.evaluate(held, net, args.c5_eval_steps, warmup=5, precision=prec)
+        res = {}
+        for mode in ("plain", "unet"):
+            sim = pkg.Simulation(held, precision=prec)
+            if mode == "unet":
+                pkg.pic_set_warm_unet(sim.h, 0, net.net)
+            sim.step(5)
+            m0 = sim.moments()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.step(args.c5_eval_steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            m1 = sim.moments()
+            pushes = sum(m1["pushed"]) - sum(m0["pushed"])
+            res[mode] = {"ms_per_step": ms / args.c5_eval_steps, "particle_steps_s": pushes / (ms * 1e-3),
+                         "cg_iters_mean": float(np.mean(ev[mode]["iters"])),
+                         "solve_ms": ev[mode]["solve_ms"], "max_resid": float(np.max(ev[mode]["resid"]))}
+            sim.close()
+        res["iterations_saved_per_step"] = res["plain"]["cg_iters_mean"] - res["unet"]["cg_iters_mean"]
+        res["speedup_unet_over_plain"] = res["unet"]["particle_steps_s"] / res["plain"]["particle_steps_s"]
+        out[prec_name] = res
+    net.close()
+    out["leg_s"] = round(time.perf_counter() - t_all, 1)
+    return out
+
+
 def reduce_over_ranks(r, dist, device):
     """Whole-job numbers of independent replicas: the slowest rank's time and the
     sum of every rank's particle pushes (no collective touches the data path)."""
@@ -525,6 +635,15 @@ def main():
     ap.add_argument("--e2e-batch", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune-window", type=int, default=50, help="steps per sort-interval candidate (c4)")
+    ap.add_argument("--no-c5", dest="c5", action="store_false",
+                    help="skip the learned warm start leg (on by default with the c2 workload)")
+    ap.add_argument("--c5-runs", type=int, default=4, help="warm start: sample runs")
+    ap.add_argument("--c5-samples", type=int, default=40, help="warm start: samples per run")
+    ap.add_argument("--c5-iters", type=int, default=800, help="warm start: training iterations")
+    ap.add_argument("--c5-lr", type=float, default=5e-4)
+    ap.add_argument("--c5-infer", type=int, default=20, help="warm start: timed forward passes")
+    ap.add_argument("--c5-eval-steps", type=int, default=20)
+    ap.add_argument("--c5-n-preload", type=int, default=10_000_000)
     ap.add_argument("--cx-sigma", type=float, default=0.0,
                     help="add resonant charge exchange Cu+ + Cu at this constant cross-section (m^2) "
                          "to c1-c3; 0 (default): off, the headline workload")
@@ -593,6 +712,9 @@ def main():
                               "speedup_mixed_over_fp64": value / (fa["pushes"] / (fa["ms"] * 1e-3)),
                               "phase_ms_per_step": {k: round(v[0] / max(f["prof_steps"], 1), 4) for k, v in fph.items()},
                               "push_kernel_ms": fpush_ms / max(fpush_n, 1), "clocks": f["clocks"]}
+    if args.c5 and args.workload == "c2":
+        ptf, pkind = peak_tflops()
+        line["learned_warm_start"] = run_warm_start_leg(args, ptf, pkind)
     if not args.no_cpu_baseline and ws >= 1:
         line["cpu_baseline"] = cpu_baseline(workload=args.workload, cx_sigma=args.cx_sigma)
     print(json.dumps(line), flush=True)

@@ -98,6 +98,16 @@ pic_status unet_layer_backward(unet_handle* net, int32_t layer, const float* x_d
  * *loss (host, may be NULL) receives L before the update. */
 pic_status unet_train_step_residual(unet_handle* net, const float* x_dev, float lr, double* loss);
 
+/* Timing of the forward convolutions: with on != 0 every later forward pass
+ * records CUDA events on the network's stream around each of the 14
+ * convolutions (layer order above; not inside a stream capture, such as a
+ * recorded PIC step); unet_get_layer_times adds up, per layer,
+ * the elapsed milliseconds (ms[14]) and the number of timed launches
+ * (count[14]) since profiling was switched on (either pointer may be NULL;
+ * synchronises). Switching on or off resets the sums. */
+pic_status unet_set_profiling(unet_handle* net, int32_t on);
+pic_status unet_get_layer_times(unet_handle* net, double* ms, int64_t* count);
+
 /* Text of the last error on this network (static storage, never NULL). */
 const char* unet_last_error(unet_handle* net);
 

@@ -90,7 +90,7 @@ EXPORTED = ["pic_create", "pic_inject", "pic_inject_particles", "pic_step", "pic
             "unet_num_weights", "unet_create", "unet_destroy", "unet_set_weights", "unet_get_weights",
             "unet_forward", "unet_backward", "unet_get_grads", "unet_train_step", "unet_last_error",
             "unet_launch_count", "unet_make_sample", "unet_layer_forward", "unet_layer_backward",
-            "unet_train_step_residual"]
+            "unet_train_step_residual", "unet_set_profiling", "unet_get_layer_times"]
 
 _lib = None
 
@@ -163,6 +163,8 @@ def load_library(path: str = LIB_PATH):
         "unet_make_sample": ([P, P, P, P, P, d], st),
         "unet_layer_forward": ([P, C.c_int32, P, P, C.c_int32], st),
         "unet_train_step_residual": ([P, P, C.c_float, d], st),
+        "unet_set_profiling": ([P, C.c_int32], st),
+        "unet_get_layer_times": ([P, d, i64], st),
         "unet_layer_backward": ([P, C.c_int32, P, P, P, C.POINTER(C.c_float), C.c_int64], st),
     }
     for name, (args, res) in sig.items():
@@ -485,6 +487,18 @@ def unet_layer_backward(net, layer, x_ptr, dz_ptr, dx_ptr, n_dw):
     _ucheck(net, load_library().unet_layer_backward(net, layer, C.c_void_p(x_ptr), C.c_void_p(dz_ptr),
                                                     C.c_void_p(dx_ptr) if dx_ptr else None, _fp(dw), n_dw))
     return dw
+
+
+def unet_set_profiling(net, on=True):
+    return _ucheck(net, load_library().unet_set_profiling(net, 1 if on else 0))
+
+
+def unet_get_layer_times(net):
+    """Per convolution (UNET_LAYERS order): (summed forward ms, timed launches)."""
+    ms = np.zeros(len(UNET_LAYERS))
+    cnt = np.zeros(len(UNET_LAYERS), dtype=np.int64)
+    _ucheck(net, load_library().unet_get_layer_times(net, _dp(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64))))
+    return {name: (float(ms[i]), int(cnt[i])) for i, (name, _, _) in enumerate(UNET_LAYERS)}
 
 
 def unet_launch_count():

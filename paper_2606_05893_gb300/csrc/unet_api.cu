@@ -79,6 +79,12 @@ struct unet_handle {
   int* err = nullptr;
   long long adam_t = 0;
   bool have_forward = false;
+  // per-layer forward timing (unet_set_profiling): events around each convolution
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  double layer_ms[14] = {0};
+  long long layer_n[14] = {0};
   char msg[256] = {0};
 };
 
@@ -466,8 +472,51 @@ static int pow2_cols(int c) {
 }
 
 // convolution (forward, or data gradient when `dgrad`) of layer l
+static cudaEvent_t take_event(unet_handle* n) {
+  if (!n->ev_pool.empty()) {
+    cudaEvent_t e = n->ev_pool.back();
+    n->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// sums the timed forward convolutions whose events have completed
+static void collect_times(unet_handle* n) {
+  for (auto& p : n->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
+      n->layer_ms[p.first] += ms;
+      n->layer_n[p.first] += 1;
+    }
+    n->ev_pool.push_back(p.second.first);
+    n->ev_pool.push_back(p.second.second);
+  }
+  n->ev_pending.clear();
+}
+
+static void conv_impl(unet_handle* n, int l, bool dgrad, const Tensor& s0, const Tensor* s1, const Tensor& d0,
+                      const Tensor* d1, const Tensor* m0, const Tensor* m1, bool relu, cudaStream_t st);
+
 static void conv(unet_handle* n, int l, bool dgrad, const Tensor& s0, const Tensor* s1, const Tensor& d0,
                  const Tensor* d1, const Tensor* m0, const Tensor* m1, bool relu, cudaStream_t st) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (n->prof && !dgrad) cudaStreamIsCapturing(st, &cap);
+  if (!n->prof || dgrad || cap != cudaStreamCaptureStatusNone) {  // never timed inside a recorded graph
+    conv_impl(n, l, dgrad, s0, s1, d0, d1, m0, m1, relu, st);
+    return;
+  }
+  cudaEvent_t a = take_event(n), b = take_event(n);
+  cudaEventRecord(a, st);
+  conv_impl(n, l, dgrad, s0, s1, d0, d1, m0, m1, relu, st);
+  cudaEventRecord(b, st);
+  n->ev_pending.push_back({l, {a, b}});
+}
+
+static void conv_impl(unet_handle* n, int l, bool dgrad, const Tensor& s0, const Tensor* s1, const Tensor& d0,
+                      const Tensor* d1, const Tensor* m0, const Tensor* m1, bool relu, cudaStream_t st) {
   const Layer& L = n->L[l];
   ConvArgs a{};
   const int cin = dgrad ? L.def.cout : L.cin;
@@ -898,9 +947,34 @@ extern "C" pic_status unet_create(int32_t D, int32_t H, int32_t W, void* cuda_st
   return PIC_OK;
 }
 
+extern "C" pic_status unet_set_profiling(unet_handle* n, int32_t on) {
+  if (!n) return PIC_EINVAL;
+  if (cudaStreamSynchronize(n->stream) != cudaSuccess) return fail(n, PIC_ECUDA, "unet_set_profiling: sync failed");
+  collect_times(n);
+  n->prof = on != 0;
+  for (int l = 0; l < kNL; ++l) {
+    n->layer_ms[l] = 0.0;
+    n->layer_n[l] = 0;
+  }
+  return PIC_OK;
+}
+
+extern "C" pic_status unet_get_layer_times(unet_handle* n, double* ms, int64_t* count) {
+  if (!n) return PIC_EINVAL;
+  if (cudaStreamSynchronize(n->stream) != cudaSuccess) return fail(n, PIC_ECUDA, "unet_get_layer_times: sync failed");
+  collect_times(n);
+  for (int l = 0; l < kNL; ++l) {
+    if (ms) ms[l] = n->layer_ms[l];
+    if (count) count[l] = n->layer_n[l];
+  }
+  return PIC_OK;
+}
+
 extern "C" pic_status unet_destroy(unet_handle* n) {
   if (!n) return PIC_OK;
   if (n->stream) cudaStreamSynchronize(n->stream);
+  collect_times(n);
+  for (cudaEvent_t e : n->ev_pool) cudaEventDestroy(e);
   for (void* p : n->allocs) cudaFree(p);
   delete n;
   return PIC_OK;
