@@ -53,6 +53,8 @@ struct Layer {
   float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // [27][cout][cin]
   __nv_bfloat16* wf = nullptr;  // forward image [3][cin/16][9][2][cout][8]
   __nv_bfloat16* wd = nullptr;  // data-gradient image [3][cout/16][9][2][cin][8]
+  __nv_bfloat16* zf = nullptr;  // the forward image with dz next to the output channel: [cin/16][9][2][3][cout][8]
+  __nv_bfloat16* zd = nullptr;  // the same for the data-gradient image: [cout/16][9][2][3][cin][8]
   long long nw() const { return 27ll * def.cout * cin; }
 };
 
@@ -321,6 +323,22 @@ __global__ void k_wimage_dgrad(const float* __restrict__ w, int cin, int cout, _
   }
 }
 
+// image for the plane-streaming convolution: dz moved next to the output channel,
+// zimg[c][t9][kg][dz][n][e] = img[dz][c][t9][kg][n][e] (N output channels, nch chunks)
+__global__ void k_zimage(const __nv_bfloat16* __restrict__ img, int nch, int N, __nv_bfloat16* zimg) {
+  const long long total = 27ll * 16 * nch * N;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+    long long r = q;
+    const int e = (int)(r % 8); r /= 8;
+    const int n = (int)(r % N); r /= N;
+    const int dz = (int)(r % 3); r /= 3;
+    const int kg = (int)(r % 2); r /= 2;
+    const int t9 = (int)(r % 9); r /= 9;
+    const int c = (int)r;
+    zimg[q] = img[((((long long)(dz * nch + c) * 9 + t9) * 2 + kg) * N + n) * 8 + e];
+  }
+}
+
 // Adam (Kingma and Ba, Algorithm 1) over the flat FP32 master weights
 __global__ void k_adam(float* w, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
                        float c1, float c2) {
@@ -515,9 +533,53 @@ static void conv(unet_handle* n, int l, bool dgrad, const Tensor& s0, const Tens
   n->ev_pending.push_back({l, {a, b}});
 }
 
+// Plane streaming for 16 output channels (the finest level): there it reads each
+// input tile once for three dz taps; at 32 and 64 channels (coarser levels, one
+// 128-row tile per CTA) the per-plane kernel measured faster.
+constexpr int kZMaxCout = 16;
+
 static void conv_impl(unet_handle* n, int l, bool dgrad, const Tensor& s0, const Tensor* s1, const Tensor& d0,
                       const Tensor* d1, const Tensor* m0, const Tensor* m1, bool relu, cudaStream_t st) {
   const Layer& L = n->L[l];
+  if ((dgrad ? L.cin : L.def.cout) <= kZMaxCout) {
+    const int cin = dgrad ? L.def.cout : L.cin;
+    const int cout = dgrad ? L.cin : L.def.cout;
+    const Vol& v = n->vol[s0.level];
+    ConvZArgs z{};
+    ConvArgs& a = z.c;
+    a.src0 = s0.p;
+    a.src1 = s1 ? s1->p : nullptr;
+    a.nchunk = cin / 16;
+    a.nchunk0 = s1 ? s0.C / 16 : a.nchunk;
+    a.cout = cout;
+    a.dst0 = d0.p;
+    a.dst1 = d1 ? d1->p : nullptr;
+    a.dgroups0 = d1 ? d0.C / 8 : cout / 8;
+    a.mask0 = m0 ? m0->p : nullptr;
+    a.mask1 = m1 ? m1->p : nullptr;
+    a.relu = relu ? 1 : 0;
+    a.v = v;
+    a.err = n->err;
+    z.zimg = dgrad ? L.zd : L.zf;
+    // TMEM T x Zc x cout <= 256 columns (two CTAs per SM): the deepest plane column
+    // that leaves at least one tile, then two tiles where that still keeps 8 planes
+    a.T = cout <= 16 ? 2 : 1;
+    z.Zc = 256 / (a.T * cout);
+    if (z.Zc > 8) z.Zc = 8;
+    if (z.Zc > v.D) z.Zc = v.D;
+    a.R = 128 * a.T + 2 * v.Wp + 2;
+    a.a_bytes = (uint32_t)a.R * 32u;
+    z.bz_bytes = 9u * 2u * 3u * (uint32_t)cout * 16u;
+    int ns = (int)((110u * 1024u - 2u * z.bz_bytes) / a.a_bytes);
+    a.nstage = ns > 4 ? 4 : (ns < 2 ? 2 : ns);
+    z.a_region = (uint32_t)a.nstage * a.a_bytes;
+    a.stage_bytes = a.a_bytes;
+    a.tmem_cols = (uint32_t)pow2_cols(a.T * z.Zc * cout);
+    z.u_begin = v.Wp + 1;
+    z.u_end = (long long)v.H * v.Wp + v.W + 1;
+    launch_conv3z(z, st);
+    return;
+  }
   ConvArgs a{};
   const int cin = dgrad ? L.def.cout : L.cin;
   const int cout = dgrad ? L.cin : L.def.cout;
@@ -598,6 +660,8 @@ static void rebuild_images(unet_handle* n, cudaStream_t st) {
     const long long tot = L.nw();
     ULAUNCH(grid_for(tot), 256, 0, st, k_wimage_fwd)(L.w, L.cin, L.def.cout, L.wf);
     ULAUNCH(grid_for(tot), 256, 0, st, k_wimage_dgrad)(L.w, L.cin, L.def.cout, L.wd);
+    if (L.def.cout <= kZMaxCout) ULAUNCH(grid_for(tot), 256, 0, st, k_zimage)(L.wf, L.cin / 16, L.def.cout, L.zf);
+    if (L.cin <= kZMaxCout) ULAUNCH(grid_for(tot), 256, 0, st, k_zimage)(L.wd, L.def.cout / 16, L.cin, L.zd);
   }
 }
 
@@ -904,7 +968,9 @@ extern "C" pic_status unet_create(int32_t D, int32_t H, int32_t W, void* cuda_st
       off += L.nw();
       L.wf = (__nv_bfloat16*)dev_alloc(sizeof(__nv_bfloat16) * L.nw());
       L.wd = (__nv_bfloat16*)dev_alloc(sizeof(__nv_bfloat16) * L.nw());
-      ok = ok && L.wf && L.wd;
+      L.zf = (__nv_bfloat16*)dev_alloc(sizeof(__nv_bfloat16) * L.nw());
+      L.zd = (__nv_bfloat16*)dev_alloc(sizeof(__nv_bfloat16) * L.nw());
+      ok = ok && L.wf && L.wd && L.zf && L.zd;
     }
     n->wout = n->wbuf + off;
     n->gout = n->wbuf + ns + off;

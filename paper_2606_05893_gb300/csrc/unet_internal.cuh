@@ -69,6 +69,20 @@ struct ConvArgs {
   int* err;
 };
 
+// The same convolution with the input planes streamed through a CTA that owns
+// T in-plane tiles of Zc output planes (cout <= 64): for input plane p, in-plane
+// tap (dy, dx) and a 16-channel chunk one MMA with N = (number of valid dz) x
+// cout adds in[p] w[dz][dy][dx] to output planes p + 1 - dz at once (adjacent
+// TMEM column blocks), so each input tile is read once for up to three taps.
+struct ConvZArgs {
+  ConvArgs c;             // sources, outputs, masks, geometry, T, R, stage sizes (a_bytes), tmem_cols, err
+  const __nv_bfloat16* zimg;  // [nchunk][9 (dy, dx)][2][3 cout (dz, co)][8]
+  int Zc;                 // output planes per CTA
+  long long u_begin, u_end;  // in-plane rows of the interior: Wp + 1 .. H Wp + W + 1
+  uint32_t bz_bytes;      // one chunk's image: 9 x 2 x 3 cout x 16
+  uint32_t a_region;      // nstage x a_bytes (B buffers follow)
+};
+
 // weight gradient of a 3x3x3 convolution:
 // dw[tap][co][ci] += sum_r in[r + off(tap)][ci] dz[r][co]
 struct WgradArgs {
@@ -94,6 +108,7 @@ struct WgradArgs {
 enum { kErrWaitProducer = 1, kErrWaitMma = 2, kErrWaitDone = 4 };
 
 void launch_conv3(const ConvArgs& a, cudaStream_t s);
+void launch_conv3z(const ConvZArgs& a, cudaStream_t s);
 void launch_wgrad(const WgradArgs& a, cudaStream_t s);
 uint64_t launch_count();
 
