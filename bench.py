@@ -329,10 +329,35 @@ def run_gpu(args, rank, ws, local):
         t3 = time.perf_counter()
         me1 = sim.moments()
         e2e_pushes = sum(me1["pushed"]) - sum(me0["pushed"])
+        # a longer window of the same instance further into the run (the population
+        # drains through the anode, so the first window is a transient)
+        steady = None
+        if prec == precisions[0] and args.steady_steps > 0:
+            sim.step(1)
+            ms0 = sim.moments()
+            sim.step(1)
+            ms1 = sim.moments()
+            torch.cuda.synchronize()
+            e4 = torch.cuda.Event(enable_timing=True)
+            e5 = torch.cuda.Event(enable_timing=True)
+            e4.record(stream)
+            sim.step(args.steady_steps)
+            e5.record(stream)
+            torch.cuda.synchronize()
+            ms2 = sim.moments()
+            sim.step(1)
+            ms3 = sim.moments()
+            st_ms = e4.elapsed_time(e5)
+            st_push = sum(ms2["pushed"]) - sum(ms1["pushed"])
+            steady = {"first_step": ms1["step"], "steps": args.steady_steps, "value": st_push / (st_ms * 1e-3),
+                      "ms_per_step": st_ms / args.steady_steps,
+                      "pushes_per_step_at_start": sum(ms1["pushed"]) - sum(ms0["pushed"]),
+                      "pushes_per_step_at_end": sum(ms3["pushed"]) - sum(ms2["pushed"]),
+                      "particles_at_end": sum(ms3["count"])}
         results[prec] = dict(ms=ms, wall=wall, pushes=pushes, push_e=push_e, launches=launches, launch_ops=launch_ops, clocks=clk,
                              phases=phases, prof_push_e=prof_push_e, prof_steps=args.profile_steps,
                              e2e_s=(t3 - t2), e2e_pushes=e2e_pushes, cg_iters=m1["cg_iters"],
-                             counts=m1["count"], moments=m1)
+                             counts=m1["count"], moments=m1, steady=steady)
         sim.close()
         torch.cuda.synchronize()
 
@@ -348,7 +373,7 @@ def run_gpu_ensemble(args, rank, ws, local):
     import torch
     import paper_2606_05893_gb300 as pkg
     from paper_2606_05893_gb300 import workloads as W
-    from paper_2606_05893_gb300.autotune import tune_sort_interval
+    from paper_2606_05893_gb300.autotune import tune
 
     torch.cuda.set_device(local)
     dist = None
@@ -367,7 +392,9 @@ def run_gpu_ensemble(args, rank, ws, local):
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         sim.step(1)
-    chosen, measured = tune_sort_interval(sim, window=args.tune_window)
+    t_tune = time.perf_counter()
+    chosen, measured = tune(sim, window=args.tune_window)
+    tune_s = time.perf_counter() - t_tune
 
     def pushed_all():
         return [sum(sim.moments(i)["pushed"]) for i in range(n_inst)]
@@ -430,10 +457,55 @@ def run_gpu_ensemble(args, rank, ws, local):
     if dist is not None:
         dist.barrier()
     info = dict(launches=launches, launch_ops=launch_ops, clocks=clk, per_inst=per_inst, chosen=chosen,
-                tune_ms={str(k): float(np.sum(v)) for k, v in measured.items()},
+                tune_ms={f"interval {k[0]}, {k[1]} blocks/SM": float(np.sum([x for x in v if x is not None]))
+                         for k, v in measured.items()}, tune_s=tune_s,
                 push_e_ms=push_e_ms, push_e_n=push_e_n, prof_push_launches=n_inst * args.profile_steps,
                 sizes=[w.nx for w in wls], n_total=sum(w.n_particles() for w in wls))
     return info, agg
+
+
+def run_c3_leg(args, peak, peak_kind):
+    """The largest single-GPU workload: 256x256x512 cells of 1.25 nm (the same box),
+    5e7 macroparticles, mixed precision; device-timed steps and the electron push's
+    roofline, as for the headline."""
+    import torch
+    import paper_2606_05893_gb300 as pkg
+    from paper_2606_05893_gb300 import workloads as W
+    t0 = time.perf_counter()
+    wl = W.config_mixed_large(seed=0, n_preload=args.c3_n_preload)
+    sim = pkg.Simulation(wl, precision=pkg.PIC_MIXED)
+    setup_s = time.perf_counter() - t0
+    sim.step(3)
+    stream = torch.cuda.current_stream()
+    m0 = sim.moments()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.c3_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    m1 = sim.moments()
+    pushes = sum(m1["pushed"]) - sum(m0["pushed"])
+    pkg.pic_set_profiling(sim.h, True)
+    mp0 = sim.moments()
+    sim.step(3)
+    ph = pkg.pic_get_phase_times(sim.h, 0)
+    mp1 = sim.moments()
+    pkg.pic_set_profiling(sim.h, False)
+    sim.close()
+    push_ms, push_n = ph["push_electron"]
+    e_per = (mp1["pushed"][0] - mp0["pushed"][0]) / max(push_n, 1)
+    per_ms = push_ms / max(push_n, 1)
+    achieved = BYTES_PER_PARTICLE["mixed"] * e_per / (per_ms * 1e-3) / 1e9
+    return {"workload": WORKLOADS["c3"][0], "n_preload": args.c3_n_preload, "steps": args.c3_steps, "warmup": 3,
+            "value": pushes / (ms * 1e-3), "ms_per_step": ms / args.c3_steps, "setup_s": round(setup_s, 1),
+            "cg_iters_last_step": m1["cg_iters"],
+            "phase_ms_per_step": {k: round(v[0] / 3, 4) for k, v in ph.items()},
+            "roofline": {"bound": "hbm", "kernel": "k_push (electrons)", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                         "bytes_per_particle": BYTES_PER_PARTICLE["mixed"], "particles_per_launch": e_per,
+                         "launch_ms": per_ms, "traffic": None}}
 
 
 def run_warm_start_leg(args, peak_tflops, peak_kind):
@@ -575,8 +647,8 @@ def cpu_baseline(seconds_target=15.0, steps_max=6, workload="c2", cx_sigma=0.0):
     m = o.moments()
     pushes += sum(m["injected"])
     o.close()
-    return {"value": pushes / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} oracle steps of {what}, FP64, single thread, {dt:.1f} s"}
+    return {"value": pushes / dt, "unit": UNIT, "cores": 1, "cores_available": len(os.sched_getaffinity(0)),
+            "kind": "oracle", "sample": f"{steps} oracle steps of {what}, FP64, single thread, {dt:.1f} s"}
 
 
 def run_reference(args, rank, ws):
@@ -634,7 +706,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-batch", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tune-window", type=int, default=50, help="steps per sort-interval candidate (c4)")
+    ap.add_argument("--tune-window", type=int, default=None,
+                    help="steps per autotuner candidate (c4; default: one common period of the candidate intervals)")
+    ap.add_argument("--steady-steps", type=int, default=100,
+                    help="a second, longer timed window of the headline instance (0: off)")
+    ap.add_argument("--no-c3", dest="c3", action="store_false",
+                    help="skip the 256x256x512 / 5e7 leg (on by default with the c2 workload)")
+    ap.add_argument("--c3-steps", type=int, default=10)
+    ap.add_argument("--c3-n-preload", type=int, default=50_000_000)
     ap.add_argument("--no-c5", dest="c5", action="store_false",
                     help="skip the learned warm start leg (on by default with the c2 workload)")
     ap.add_argument("--c5-runs", type=int, default=4, help="warm start: sample runs")
@@ -712,6 +791,10 @@ def main():
                               "speedup_mixed_over_fp64": value / (fa["pushes"] / (fa["ms"] * 1e-3)),
                               "phase_ms_per_step": {k: round(v[0] / max(f["prof_steps"], 1), 4) for k, v in fph.items()},
                               "push_kernel_ms": fpush_ms / max(fpush_n, 1), "clocks": f["clocks"]}
+    if r.get("steady"):
+        line["steady_state"] = r["steady"]
+    if args.c3 and args.workload == "c2":
+        line["c3_mixed"] = run_c3_leg(args, peak, peak_kind)
     if args.c5 and args.workload == "c2":
         ptf, pkind = peak_tflops()
         line["learned_warm_start"] = run_warm_start_leg(args, ptf, pkind)
@@ -744,7 +827,9 @@ def report_ensemble(args, rank, ws, local):
                          "traffic": None, "kernel": "k_push (electrons, all instances, isolated launches)",
                          "peak_kind": peak_kind, "bytes_per_particle": bpp},
             "per_instance_particle_steps_s": {"min": pi[0], "median": pi[len(pi) // 2], "max": pi[-1]},
-            "sort_interval_chosen": info["chosen"], "autotune_ms_per_step_sum": info["tune_ms"]}
+            "autotune": {"chosen_interval_blocks_per_sm": info["chosen"], "ms_per_step_summed": info["tune_ms"],
+                         "seconds": round(info["tune_s"], 1),
+                         "method": "every candidate timed from the same checkpointed state of every instance"}}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

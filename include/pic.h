@@ -350,6 +350,14 @@ pic_status pic_load(pic_handle* h, int32_t inst, const char* path);
  * PIC_EINVAL for a negative interval or a bad instance. */
 pic_status pic_set_sort_interval(pic_handle* h, int32_t inst, int32_t interval);
 
+/* Launch shape of one instance's particle kernels (push, scratch deposit,
+ * injection, resolve) from now on: blocks_per_sm thread blocks per SM (1..32,
+ * default 8), each striding over the store. Like the sort interval it changes
+ * no result beyond rounding (the order of compacted particles and of deposit
+ * sums), only how the work is spread (the autotuner picks it with the sort
+ * interval). PIC_EINVAL outside 1..32 or for a bad instance. */
+pic_status pic_set_launch_shape(pic_handle* h, int32_t inst, int32_t blocks_per_sm);
+
 /* Phase timing: with on != 0 every later step records CUDA events on the
  * handle's stream around each phase (and waits for them at the end of the step).
  * pic_get_phase_times adds up, per phase, the elapsed milliseconds (ms[PIC_NPHASES])

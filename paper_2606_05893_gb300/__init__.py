@@ -86,7 +86,7 @@ EXPORTED = ["pic_create", "pic_inject", "pic_inject_particles", "pic_step", "pic
             "pic_set_mcc_background", "pic_version", "pic_set_profiling", "pic_get_phase_times",
             "pic_launch_count", "pic_kernel_count", "pic_poisson_solve_static", "pic_set_sort_interval",
             "pic_set_hit_log", "pic_get_hits", "pic_set_circuit", "pic_save", "pic_load",
-            "pic_set_warm_unet", "pic_get_phi_device",
+            "pic_set_warm_unet", "pic_get_phi_device", "pic_set_launch_shape",
             "unet_num_weights", "unet_create", "unet_destroy", "unet_set_weights", "unet_get_weights",
             "unet_forward", "unet_backward", "unet_get_grads", "unet_train_step", "unet_last_error",
             "unet_launch_count", "unet_make_sample", "unet_layer_forward", "unet_layer_backward",
@@ -134,6 +134,7 @@ def load_library(path: str = LIB_PATH):
         "pic_philox": ([P, C.c_int64, u32, u32, u32], st),
         "pic_set_mcc_background": ([P, C.c_int32, C.c_double], st),
         "pic_set_sort_interval": ([P, C.c_int32, C.c_int32], st),
+        "pic_set_launch_shape": ([P, C.c_int32, C.c_int32], st),
         "pic_set_hit_log": ([P, C.c_int32, C.c_int64], st),
         "pic_set_circuit": ([P, C.c_int32, C.c_double, C.c_double, C.c_double], st),
         "pic_save": ([P, C.c_int32, C.c_char_p], st),
@@ -353,6 +354,10 @@ def pic_set_sort_interval(h, inst, interval):
     return _check(h, load_library().pic_set_sort_interval(h, inst, interval))
 
 
+def pic_set_launch_shape(h, inst, blocks_per_sm):
+    return _check(h, load_library().pic_set_launch_shape(h, inst, blocks_per_sm))
+
+
 def pic_set_profiling(h, on=True):
     return _check(h, load_library().pic_set_profiling(h, 1 if on else 0))
 
@@ -545,27 +550,46 @@ class UNet:
     def grads(self):
         return unet_get_grads(self.net)
 
+    @staticmethod
+    def _dev(t, dtype, shape, what):
+        """The device pointer of a contiguous CUDA tensor of the given dtype and shape (the
+        library reads raw memory: a wrong dtype or shape is refused, not reinterpreted)."""
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+            raise TypeError(f"{what}: a contiguous CUDA tensor is required")
+        if t.dtype != dtype or tuple(t.shape) != tuple(shape):
+            raise TypeError(f"{what}: expected {dtype} of shape {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+        return t.data_ptr()
+
     def forward(self, x):
-        """x: torch CUDA float32 tensor (2, D, H, W); returns a (D, H, W) tensor (the network's own buffer)."""
-        assert x.is_cuda and x.dtype.is_floating_point and x.is_contiguous()
-        unet_forward(self.net, x.data_ptr(), self.y.data_ptr())
+        """x: CUDA float32 tensor (2, D, H, W); returns a (D, H, W) tensor (the network's own buffer)."""
+        import torch
+        unet_forward(self.net, self._dev(x, torch.float32, (2, self.D, self.H, self.W), "x"), self.y.data_ptr())
         return self.y
 
     def backward(self, dy):
-        assert dy.is_cuda and dy.is_contiguous()
-        unet_backward(self.net, dy.data_ptr())
+        import torch
+        unet_backward(self.net, self._dev(dy, torch.float32, (self.D, self.H, self.W), "dy"))
         return self.grads()
 
     def train_step(self, x, t, lr, loss_planes=None):
-        return unet_train_step(self.net, x.data_ptr(), t.data_ptr(), self.D - 1 if loss_planes is None else loss_planes,
-                               lr)
+        import torch
+        return unet_train_step(self.net, self._dev(x, torch.float32, (2, self.D, self.H, self.W), "x"),
+                               self._dev(t, torch.float32, (self.D, self.H, self.W), "t"),
+                               self.D - 1 if loss_planes is None else loss_planes, lr)
 
     def train_step_residual(self, x, lr):
         """Adam step on the residual the warm start leaves (unet_train_step_residual)."""
-        return unet_train_step_residual(self.net, x.data_ptr(), lr)
+        import torch
+        return unet_train_step_residual(self.net, self._dev(x, torch.float32, (2, self.D, self.H, self.W), "x"), lr)
 
     def make_sample(self, phi_new, phi_old, x, t):
-        return unet_make_sample(self.net, phi_new.data_ptr(), phi_old.data_ptr(), x.data_ptr(), t.data_ptr())
+        import torch
+        nodes = (self.D + 1) * self.H * self.W
+        pn = self._dev(phi_new.reshape(-1), torch.float64, (nodes,), "phi_new")
+        po = self._dev(phi_old.reshape(-1), torch.float64, (nodes,), "phi_old")
+        return unet_make_sample(self.net, pn, po, self._dev(x, torch.float32, (2, self.D, self.H, self.W), "x"),
+                                self._dev(t, torch.float32, (self.D, self.H, self.W), "t"))
 
 
 def _torch_stream():

@@ -188,6 +188,7 @@ struct Instance {
   HitLog hits{};
   Circuit circ{};  // external circuit on the anode (off by default)
   unet_handle* net = nullptr;  // learned warm start of the solve (not owned), nullptr: cfg.warm_start
+  int push_blocks_per_sm = kPushBlocksPerSM;  // grid of the particle kernels (pic_set_launch_shape)
   SegCtl* seg_ctl = nullptr;    // bucket path state (device)
   SegCtl* seg_host = nullptr;   // pinned mirror
   int32_t* seg_big = nullptr;   // buckets for the block-wide sort (ncell + 1)
@@ -741,7 +742,7 @@ pic_status step_instance(pic_handle* h, Instance* I) {
   cudaStream_t st = I->stream;
   const Grid& g = I->g;
   const uint2 key = make_uint2((uint32_t)I->cfg.seed, (uint32_t)(I->cfg.seed >> 32));
-  const int blocks = sm_count() * kPushBlocksPerSM;
+  const int blocks = sm_count() * I->push_blocks_per_sm;
 
   PhaseTimer& T = I->timer;
   // a1 injection: counts from the carry accumulators (device plan)
@@ -1645,6 +1646,17 @@ pic_status pic_set_sort_interval(pic_handle* h, int32_t inst, int32_t interval) 
   if (st != PIC_OK) return st;
   if (interval < 0) return fail(h, PIC_EINVAL, "sort interval must be >= 0");
   h->inst[inst]->cfg.sort_interval = interval;
+  return PIC_OK;
+}
+
+pic_status pic_set_launch_shape(pic_handle* h, int32_t inst, int32_t blocks_per_sm) {
+  pic_status st = check(h, inst);
+  if (st != PIC_OK) return st;
+  if (blocks_per_sm < 1 || blocks_per_sm > 32) return fail(h, PIC_EINVAL, "blocks per SM must be in 1..32");
+  Instance* I = h->inst[inst];
+  CK(h, cudaStreamSynchronize(I->stream));
+  I->push_blocks_per_sm = blocks_per_sm;
+  drop_step_graphs(I);  // the recorded steps hold the old grid
   return PIC_OK;
 }
 

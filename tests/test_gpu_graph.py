@@ -77,3 +77,34 @@ def test_mixed_replays_keep_counts(pkg):
         assert a[k] == b[k], k
     sim.close()
     direct.close()
+
+
+def test_autotuner_times_every_candidate_from_the_same_state():
+    """The autotuner restores every instance before each candidate and once at the
+    end: the run continues from where it was (exact checkpoint round trip), and a
+    second call finds every bucket cached and runs no step."""
+    import paper_2606_05893_gb300 as pkg
+    from paper_2606_05893_gb300 import autotune
+    from paper_2606_05893_gb300 import workloads as W
+    wls = [W.config_tiny(seed=11), W.config_tiny(seed=12, nx=8, ny=8, nz=24)]
+    sim = pkg.Simulation(wls, precision=pkg.PIC_MIXED)
+    sim.step(3)
+    before = [sim.moments(i) for i in range(2)]
+    parts = [[sim.particles(sp, i) for sp in range(3)] for i in range(2)]
+    cache = {}
+    chosen, measured = autotune.tune(sim, intervals=(5, 20), shapes=(4, 8), window=6, cache=cache)
+    assert len(measured) == 4 and all(c in measured for c in chosen)
+    for i in range(2):
+        m = sim.moments(i)
+        assert m["step"] == before[i]["step"] and m["count"] == before[i]["count"]
+        assert m["pushed"] == before[i]["pushed"]
+        for sp in range(3):
+            x, v, p = sim.particles(sp, i)
+            x0, v0, p0 = parts[i][sp]
+            o, o0 = np.argsort(p), np.argsort(p0)
+            assert np.array_equal(p[o], p0[o0]) and np.array_equal(x[o], x0[o0]) and np.array_equal(v[o], v0[o0])
+    chosen2, measured2 = autotune.tune(sim, intervals=(5, 20), shapes=(4, 8), window=6, cache=cache)
+    assert measured2 == {} and chosen2 == chosen
+    assert sim.moments(0)["step"] == before[0]["step"]
+    sim.step(2)
+    sim.close()

@@ -146,7 +146,7 @@ def test_weights_round_trip_and_zero_network():
     net.set_weights(w)
     assert np.array_equal(net.weights(), w)
     net.set_weights(np.zeros_like(w))
-    x = torch.randn((2, 8, 8, 16), device="cuda")
+    x = torch.randn((2, 8, 8, 16), dtype=torch.float32, device="cuda")
     assert not net.forward(x).cpu().numpy().any()
     net.close()
 
@@ -217,11 +217,13 @@ def test_training_reduces_the_loss():
     lr = 1e-3
     net, ws, x, xt = setup(D, H, W, seed=44)
     tgt = torch.from_numpy(I.random_volume(1, D, H, W, seed=45, smooth=3)[0].astype(np.float32)).cuda()
-    mask = torch.ones((D, H, W), device="cuda")
+    mask = torch.ones((D, H, W), dtype=torch.float32, device="cuda")
     mask[D - 1] = 0
     y = net.forward(xt).clone()
     dy = (2.0 / float(mask.sum())) * (y - tgt) * mask
     g = net.backward(dy.contiguous())
+    ymax, dymax, gmax = float(y.abs().max()), float(dy.abs().max()), float(np.abs(g).max())
+    assert np.isfinite(ymax) and ymax < 1e3 and dymax < 1e3 and gmax < 1e3, (ymax, dymax, gmax)
     w0 = net.weights()
     losses = [net.train_step(xt, tgt, lr)]
     w1 = net.weights()

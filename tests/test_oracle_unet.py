@@ -11,7 +11,6 @@ import torch.nn.functional as F
 from oracle import unet as U
 from paper_2606_05893_gb300 import unet_inputs as I
 
-torch.set_default_dtype(torch.float64)
 
 
 def T(a):
