@@ -50,8 +50,8 @@ FALLBACK_HBM_GBS = 6800.0
 # read the particle record and write it once (the node field is gathered from L2).
 BYTES_PER_PARTICLE = {"mixed": 32 + 32, "fp64": 52 + 52}
 # DRAM bytes (read + write) per launch of the forward convolutions captured with ncu
-# (profiles/unet_conv_forward_128x128x256.md); layers without a capture are absent
-UNET_NCU_TRAFFIC = {"d0a": 541.8e6}
+# (profiles/unet_conv_d0a_forward_128x128x256.md); layers without a capture are absent
+UNET_NCU_TRAFFIC = {"d0a": 536.2e6}
 # DRAM bytes (read + write) per pushed electron of the same kernel from one ncu capture of the
 # current kernel (profiles/k_push_mixed_electrons_128x128x256.md: 145.18 MB for 2 593 379
 # electrons); None where no capture of the current kernel exists
@@ -569,7 +569,9 @@ def run_warm_start_leg(args, peak_tflops, peak_kind):
            "train_residual_ratio": float(np.mean(ratio)),
            "inference_ms": infer_ms, "network_gflop": net_flops / 1e9,
            "network_tflops": net_flops / (infer_ms * 1e-3) / 1e12,
-           "roofline": {"bound": "tensor", "kernel": f"k_conv3 forward, layer {top}", "achieved": achieved,
+           "roofline": {"bound": "tensor",
+                        "kernel": f"{'k_conv3z' if dict((n, co) for n, _, co in pkg.UNET_LAYERS)[top] <= 16 else 'k_conv3'}"
+                                  f" forward, layer {top}", "achieved": achieved,
                         "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                         "peak_kind": peak_kind, "flop_per_launch": flops[top], "launch_ms": top_ms,
                         "traffic": UNET_NCU_TRAFFIC.get(top)},

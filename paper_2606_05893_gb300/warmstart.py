@@ -173,11 +173,25 @@ def main(argv=None):
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--out", default=None, help="write the trained weights here (.npy, FP32)")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--forward-only", type=int, default=0, metavar="N",
+                    help="only run N forward passes of a He-initialised network on a random 128x128x256 "
+                         "input (for profilers) and exit")
     a = ap.parse_args(argv)
     torch.cuda.set_device(0)
     prec = pkg.PIC_MIXED if a.precision == "mixed" else pkg.PIC_FP64
     log = lambda s: print(s, flush=True)  # noqa: E731
     from . import unet_inputs
+    if a.forward_only:
+        net = pkg.UNet(256, 128, 128)
+        w = np.concatenate([w.reshape(-1) for w in unet_inputs.init_weights(pkg.UNET_WEIGHT_SHAPES, seed=a.seed)])
+        net.set_weights(w.astype(np.float32))
+        x = torch.from_numpy(unet_inputs.random_volume(2, 256, 128, 128, seed=a.seed).astype(np.float32)).cuda()
+        for _ in range(a.forward_only):
+            net.forward(x)
+        torch.cuda.synchronize()
+        net.close()
+        log(f"{a.forward_only} forward passes")
+        return 0
     wls = [W.config_warm_start(seed=a.seed + k, n_preload=a.n_preload) for k in range(a.runs)]
     wl0 = wls[0]
     net = pkg.UNet(wl0.nz, wl0.ny, wl0.nx)
