@@ -145,13 +145,19 @@ typedef struct {
   double charge_to_cathode_C;                     /* absorbed in the last step */
   double charge_to_anode_C;
   uint32_t next_pid;
-  int32_t error_flags;                            /* device-side error bits seen */
+  int32_t error_flags;                            /* device-side error bits seen, and
+                                                     PIC_FLAG_NONFINITE */
   int64_t pushed[PIC_MAX_SPECIES];                /* cumulative particle pushes (one per
                                                      live particle per step) */
   double anode_V;                                 /* anode potential of the next solve (moves
                                                      only with an external circuit) */
   int64_t charge_exchanges;                       /* cumulative (PIC_XS_CHARGE_EXCHANGE) */
 } pic_moments_t;
+
+/* error_flags bit set by pic_moments when a reduced moment (a species' kinetic
+ * energy, the field energy, the anode potential or the last residual) is NaN
+ * or Inf: some particle velocity or the potential is not finite. */
+#define PIC_FLAG_NONFINITE 32
 
 /* Phases of a step, for pic_get_phase_times. */
 enum {
@@ -359,7 +365,8 @@ pic_status pic_set_sort_interval(pic_handle* h, int32_t inst, int32_t interval);
 pic_status pic_set_launch_shape(pic_handle* h, int32_t inst, int32_t blocks_per_sm);
 
 /* Phase timing: with on != 0 every later step records CUDA events on the
- * handle's stream around each phase (and waits for them at the end of the step).
+ * handle's stream around each phase (and waits for them at the end of the step),
+ * and marks each phase as an NVTX range for timeline profilers.
  * pic_get_phase_times adds up, per phase, the elapsed milliseconds (ms[PIC_NPHASES])
  * and the number of timed phase executions (count[PIC_NPHASES]) since profiling
  * was switched on; either pointer may be NULL. Switching on resets the sums. */

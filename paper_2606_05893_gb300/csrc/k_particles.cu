@@ -184,7 +184,11 @@ __global__ void k_inject(InjectArgs<S> a) {
   const InjectPlan& P = *a.plan;
   const long long total = P.total;
   const uint32_t step = a.cnt->step;
-  for (long long t = gtid(); t < total; t += gstride()) {
+  // particle t on block t mod G (thread t / G): a step injects tens to hundreds of
+  // particles, each with FP64 transcendentals, and one SM's narrow FP64 pipe
+  // would take them all one after another; spread this way each SM gets one or two
+  for (long long t = blockIdx.x + (long long)gridDim.x * threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
     // source of this particle
     int q = 0;
     while (q + 1 < a.nsrc && t >= P.src_first[q + 1]) ++q;
@@ -617,7 +621,9 @@ __global__ void __launch_bounds__(kRankWarps * 32) k_resolve_rank(ResolveArgs a)
     return;
   }
   const unsigned lt = (1u << lane) - 1u;
-  for (long long e = (long long)blockIdx.x * kRankWarps + w; e < ne; e += (long long)gridDim.x * kRankWarps) {
+  // event e on block e mod G, warp e / G: tens of events each scan the candidate
+  // array, and spread one per block they do so on as many SMs
+  for (long long e = blockIdx.x + (long long)gridDim.x * w; e < ne; e += (long long)gridDim.x * kRankWarps) {
     const uint32_t cell = a.ev[e].cell, pid = a.ev[e].pid;
     const int r = event_rank(a, cell, pid);
     // this cell's candidates, four chunks of 32 per round (their loads overlap)
@@ -674,7 +680,10 @@ __global__ void k_resolve_apply(ApplyArgs<S> a) {
   const unsigned long long ni_out = a.cnt->n[a.i_out][a.i_species];
   const unsigned long long nn_out = a.cnt->n[a.n_out][a.n_species];
   const uint32_t pid0 = a.cnt->next_pid;
-  for (long long r = gtid(); r < ns; r += gstride()) {
+  // event r on block r mod G (as for injection: each event's FP64 kinematics
+  // then run on their own SM's FP64 pipe instead of queueing on one)
+  for (long long r = blockIdx.x + (long long)gridDim.x * threadIdx.x; r < ns;
+       r += (long long)gridDim.x * blockDim.x) {
     const Event ev = a.ev[a.sorted_vals[r]];
     const Cand cd = a.cand[ev.victim];
     // victim neutral -> ion (position x^{n+1}, velocity and pid kept)

@@ -21,6 +21,8 @@
 #include "pic_solver.cuh"
 #include "unet_warm.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace pic;
 
 namespace pic {
@@ -67,14 +69,22 @@ struct PhaseTimer {
     }
     return pool[used++];
   }
+  // NVTX range names of the phases (shown by Nsight Systems / Compute while profiling is on)
+  static const char* name(int phase) {
+    static const char* n[] = {"pic inject", "pic sort", "pic deposit", "pic solve", "pic field",
+                              "pic push electrons", "pic push ions", "pic push neutrals", "pic resolve"};
+    return phase >= 0 && phase < 9 ? n[phase] : "pic phase";
+  }
   void begin(int phase, cudaStream_t s) {
     if (!on) return;
     open_phase = phase;
     open_ev = next();
     cudaEventRecord(open_ev, s);
+    nvtxRangePushA(name(phase));
   }
   void end(cudaStream_t s) {
     if (!on || open_phase < 0) return;
+    nvtxRangePop();
     cudaEvent_t b = next();
     cudaEventRecord(b, s);
     marks.push_back(Mark{open_phase, open_ev, b});
@@ -1408,6 +1418,11 @@ pic_status pic_moments(pic_handle* h, int32_t inst, pic_moments_t* out) {
   out->next_pid = c.next_pid;
   out->error_flags = c.error;
   for (int sp = 0; sp < I->nsp; ++sp) out->pushed[sp] = (int64_t)c.pushed[sp];
+  // a NaN or Inf anywhere in a species' velocities or in the potential reaches these sums
+  bool finite = std::isfinite(out->field_energy_J) && std::isfinite(out->anode_V) &&
+                !(out->cg_resid_rel != out->cg_resid_rel);
+  for (int sp = 0; sp < I->nsp; ++sp) finite = finite && std::isfinite(out->kinetic_J[sp]);
+  if (!finite) out->error_flags |= PIC_FLAG_NONFINITE;
   return PIC_OK;
 }
 

@@ -143,3 +143,26 @@ def test_warm_start_zero_matches_previous_phi(pkg):
     assert b.moments()["cg_iters"] >= a.moments()["cg_iters"]
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nonfinite_potential_flags_the_moments(pkg, precision):
+    """A potential holding NaN (set through pic_set_phi) makes the field energy
+    NaN, and pic_moments flags it (PIC_FLAG_NONFINITE) rather than returning a
+    NaN moment silently; a finite potential clears the flag. No step runs on the
+    NaN potential: the push derives cell indices from positions and is never fed
+    non-finite values (uploads refuse them)."""
+    import paper_2606_05893_gb300 as p
+    wl = W.config_tiny(seed=21)
+    sim = p.Simulation(wl, precision=precision)
+    sim.step(1)
+    assert not sim.moments()["error_flags"] & 32
+    phi = sim.phi()
+    bad = phi.copy()
+    bad[wl.nz // 2, wl.ny // 2, wl.nx // 2] = np.nan
+    sim.set_phi(bad)
+    m = sim.moments()
+    assert m["error_flags"] & 32 and not np.isfinite(m["field_energy"])
+    sim.set_phi(phi)
+    assert not sim.moments()["error_flags"] & 32
+    sim.close()
