@@ -621,50 +621,68 @@ def reduce_over_ranks(r, dist, device):
                 e2e_s=red(r["e2e_s"], dist.ReduceOp.MAX), e2e_pushes=red(r["e2e_pushes"], dist.ReduceOp.SUM))
 
 
-def cpu_baseline(seconds_target=15.0, steps_max=6, workload="c2", cx_sigma=0.0):
-    """The FP64 oracle as it stands, single thread, on a bounded sample of the workload:
-    the 64x64x128-cell sub-box (1/8 of the volume, same h and particle density), or
-    for the small 32x32x64 workload the workload itself."""
-    import oracle
+def _oracle_sample(workload, cx_sigma, seed=0):
+    """The bounded CPU sample of a workload: the 64x64x128-cell sub-box (1/8 of the
+    volume, same h and particle density), or for the small 32x32x64 workload the
+    workload itself."""
     from paper_2606_05893_gb300 import workloads as W
     if workload == "c1":
-        wl = make_workload("c1", 0, WORKLOADS["c1"][1], cx_sigma)
-        steps_max = 1000
-        what = "the 32x32x64 workload itself (1e4 macroparticles)"
-    else:
-        wl = with_cx(W.config_scale(seed=0, n_preload=1_250_000, nx=64, ny=64, nz=128, h=2.5e-9), cx_sigma)
-        what = "the 64x64x128-cell sub-box (same h = 2.5 nm and particle density, 1.25e6 macroparticles)"
-    o = oracle.Oracle(wl)
+        return (make_workload("c1", seed, WORKLOADS["c1"][1], cx_sigma),
+                "the 32x32x64 workload itself (1e4 macroparticles)")
+    return (with_cx(W.config_scale(seed=seed, n_preload=1_250_000, nx=64, ny=64, nz=128, h=2.5e-9), cx_sigma),
+            "the 64x64x128-cell sub-box (same h = 2.5 nm and particle density, 1.25e6 macroparticles)")
+
+
+def _time_oracle(wl, omp, seconds_target, steps_max):
+    """Steps of the oracle until steps_max or seconds_target; (pushes/s, steps, s)."""
+    import oracle
+    o = oracle.Oracle(wl, omp=omp)
     t0 = time.perf_counter()
     pushes = 0
     steps = 0
     while steps < steps_max:
         n = sum(o.count(s) for s in range(3))
         o.step()
-        pushes += n + 0  # particles present at the start of the step (injected ones added below)
+        pushes += n  # particles present at the start of the step (injected ones added below)
         steps += 1
         if time.perf_counter() - t0 > seconds_target:
             break
     dt = time.perf_counter() - t0
-    m = o.moments()
-    pushes += sum(m["injected"])
+    pushes += sum(o.moments()["injected"])
     o.close()
-    return {"value": pushes / dt, "unit": UNIT, "cores": 1, "cores_available": len(os.sched_getaffinity(0)),
-            "kind": "oracle", "sample": f"{steps} oracle steps of {what}, FP64, single thread, {dt:.1f} s"}
+    return pushes / dt, steps, dt
+
+
+def cpu_baseline(seconds_target=10.0, steps_max=10, workload="c2", cx_sigma=0.0):
+    """The FP64 oracle as it stands on a bounded sample of the workload, timed twice:
+    its OpenMP build on every core this process may use (the line's value), and
+    the single-threaded build beside it over the same steps. The two builds give
+    bit-identical results (every sum keeps one fixed order)."""
+    import oracle
+    wl, what = _oracle_sample(workload, cx_sigma)
+    if workload == "c1":
+        steps_max = 1000
+    v1, steps, dt1 = _time_oracle(wl, False, seconds_target, steps_max)
+    avail = len(os.sched_getaffinity(0))
+    threads = oracle.set_threads(avail)
+    wl, _ = _oracle_sample(workload, cx_sigma)
+    vp, steps_p, dtp = _time_oracle(wl, True, 1e30, steps)
+    return {"value": vp, "unit": UNIT, "cores": threads, "cores_available": avail, "kind": "oracle",
+            "build": "OpenMP build of the oracle source (bit-identical to the serial build)",
+            "sample": f"{steps_p} oracle steps of {what}, FP64, {threads} threads, {dtp:.1f} s",
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": f"{steps} oracle steps of the same sample, serial build, {dt1:.1f} s"}}
 
 
 def run_reference(args, rank, ws):
+    """The oracle as the reference arm: its OpenMP build on every core this process
+    may use, on the bounded sample of the workload (rank 0 only)."""
     if rank != 0:
         return 0
     import oracle
-    from paper_2606_05893_gb300 import workloads as W
-    if args.workload == "c1":
-        wl, sample = make_workload("c1", args.seed, WORKLOADS["c1"][1], args.cx_sigma), "the whole 32x32x64 workload"
-    else:
-        wl = with_cx(W.config_scale(seed=args.seed, n_preload=1_250_000, nx=64, ny=64, nz=128, h=2.5e-9),
-                     args.cx_sigma)
-        sample = "the 64x64x128-cell sub-box (same h and particle density, 1.25e6 macroparticles)"
-    o = oracle.Oracle(wl)
+    wl, sample = _oracle_sample(args.workload, args.cx_sigma, args.seed)
+    threads = oracle.set_threads(len(os.sched_getaffinity(0)))
+    o = oracle.Oracle(wl, omp=True)
     for _ in range(args.warmup):
         o.step()
     m0 = o.moments()
@@ -684,9 +702,11 @@ def run_reference(args, rank, ws):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][0] + cx_label(args.cx_sigma),
                                             "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads,
+                             "cores_available": len(os.sched_getaffinity(0)), "kind": "oracle",
+                             "build": "OpenMP build of the oracle source (bit-identical to the serial build)",
                              "sample": f"{args.steps} timed oracle steps of {sample}, started with "
-                                       f"{n_start} particles"},
+                                       f"{n_start} particles, {threads} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

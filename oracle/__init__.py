@@ -18,8 +18,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pic_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+# the same source built with -fopenmp (bit-identical results, all host cores)
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 MAXSP = 8
 
@@ -60,23 +63,31 @@ class OrMoments(C.Structure):
     ]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (single-threaded, -ffp-contract=off)."""
+def _compile(out: str, extra, force: bool) -> str:
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", *extra, "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with gcc (-ffp-contract=off): single-threaded, or with
+    -fopenmp (omp=True). Both builds are made by default; returns the asked one."""
     with _lock:
-        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-            return _LIB
-        os.makedirs(_BUILD, exist_ok=True)
-        tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-        return _LIB
+        _compile(_LIB, [], force)
+        _compile(_LIB_OMP, ["-fopenmp"], force)
+        return _LIB_OMP if omp else _LIB
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
+def lib(omp: bool = False):
+    """The serial oracle library, or its OpenMP build (omp=True)."""
+    global _lib, _lib_omp
+    if (_lib_omp if omp else _lib) is None:
+        L = C.CDLL(build(omp=omp))
         P = C.c_void_p
         d = C.POINTER(C.c_double)
         u32 = C.POINTER(C.c_uint32)
@@ -135,10 +146,20 @@ def lib():
         L.or_uniform_fill.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint32, d]
         L.or_sizeof_cfg.restype = C.c_size_t
         L.or_sizeof_moments.restype = C.c_size_t
+        L.or_set_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
         assert L.or_sizeof_cfg() == C.sizeof(OrCfg), "oracle cfg layout mismatch"
         assert L.or_sizeof_moments() == C.sizeof(OrMoments), "oracle moments layout mismatch"
-        _lib = L
-    return _lib
+        if omp:
+            _lib_omp = L
+        else:
+            _lib = L
+    return _lib_omp if omp else _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the OpenMP build (0: all it may use); returns the count in use."""
+    return int(lib(omp=True).or_set_threads(int(n)))
 
 
 def _dp(a):
@@ -195,8 +216,10 @@ class Oracle:
     """One PIC/MCC instance on the CPU, driven step by step."""
 
     def __init__(self, wl, cg_rtol=None, cg_maxit=None, warm_zero=False, preload=True,
-                 background_density=0.0):
-        L = lib()
+                 background_density=0.0, omp=False):
+        """omp=True runs the OpenMP build of the same source (bit-identical results)."""
+        L = lib(omp)
+        self._L = L
         c = OrCfg()
         c.nx, c.ny, c.nz = wl.nx, wl.ny, wl.nz
         c.h, c.dt, c.phi_c, c.phi_a, c.rho_bg = wl.h, wl.dt, wl.phi_cathode, wl.phi_anode, wl.rho_background
@@ -228,7 +251,7 @@ class Oracle:
 
     def close(self):
         if self._h:
-            lib().or_destroy(self._h)
+            self._L.or_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -241,92 +264,92 @@ class Oracle:
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
         v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
         assert x.shape == v.shape
-        r = lib().or_load(self._h, sp, x.shape[0], _dp(x), _dp(v))
+        r = self._L.or_load(self._h, sp, x.shape[0], _dp(x), _dp(v))
         if r != 0:
             raise ValueError("bad species")
 
     def step(self, n=1):
         for _ in range(n):
-            lib().or_step(self._h)
+            self._L.or_step(self._h)
 
     def step_until_solve(self):
-        return lib().or_step_until_solve(self._h)
+        return self._L.or_step_until_solve(self._h)
 
     def step_finish(self):
-        lib().or_step_finish(self._h)
+        self._L.or_step_finish(self._h)
 
     def inject(self):
-        return lib().or_inject(self._h)
+        return self._L.or_inject(self._h)
 
     def sort(self):
-        lib().or_sort(self._h)
+        self._L.or_sort(self._h)
 
     def deposit(self):
-        lib().or_deposit(self._h)
+        self._L.or_deposit(self._h)
 
     def solve(self):
-        return lib().or_solve(self._h)
+        return self._L.or_solve(self._h)
 
     def count(self, sp):
-        return int(lib().or_count(self._h, sp))
+        return int(self._L.or_count(self._h, sp))
 
     def particles(self, sp):
         n = self.count(sp)
         x = np.zeros((n, 3)); v = np.zeros((n, 3)); pid = np.zeros(n, dtype=np.uint32)
-        lib().or_get_particles(self._h, sp, _dp(x), _dp(v), pid.ctypes.data_as(C.POINTER(C.c_uint32)))
+        self._L.or_get_particles(self._h, sp, _dp(x), _dp(v), pid.ctypes.data_as(C.POINTER(C.c_uint32)))
         return x, v, pid
 
     def set_velocities(self, sp, v):
         v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
         assert v.shape[0] == self.count(sp)
-        lib().or_set_velocities(self._h, sp, _dp(v))
+        self._L.or_set_velocities(self._h, sp, _dp(v))
 
     def rho(self):
         wl = self.wl
         out = np.zeros(wl.nx * wl.ny * (wl.nz + 1))
-        lib().or_get_rho(self._h, _dp(out))
+        self._L.or_get_rho(self._h, _dp(out))
         return out.reshape(wl.nz + 1, wl.ny, wl.nx)
 
     def phi(self):
         wl = self.wl
         out = np.zeros(wl.nx * wl.ny * (wl.nz + 1))
-        lib().or_get_phi(self._h, _dp(out))
+        self._L.or_get_phi(self._h, _dp(out))
         return out.reshape(wl.nz + 1, wl.ny, wl.nx)
 
     def set_phi(self, phi):
         phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
-        lib().or_set_phi(self._h, _dp(phi))
+        self._L.or_set_phi(self._h, _dp(phi))
 
     def ncount(self, sp):
         wl = self.wl
         out = np.zeros(wl.nx * wl.ny * wl.nz, dtype=np.int32)
-        lib().or_get_ncount(self._h, sp, out.ctypes.data_as(C.POINTER(C.c_int32)))
+        self._L.or_get_ncount(self._h, sp, out.ctypes.data_as(C.POINTER(C.c_int32)))
         return out.reshape(wl.nz, wl.ny, wl.nx)
 
     def cell_start(self, sp):
         wl = self.wl
         out = np.zeros(wl.nx * wl.ny * wl.nz + 1, dtype=np.int64)
-        lib().or_get_cell_start(self._h, sp, out.ctypes.data_as(C.POINTER(C.c_int64)))
+        self._L.or_get_cell_start(self._h, sp, out.ctypes.data_as(C.POINTER(C.c_int64)))
         return out
 
     def ionization_log(self):
-        n = lib().or_get_log(self._h, None)
+        n = self._L.or_get_log(self._h, None)
         out = np.zeros((max(n, 1), 3), dtype=np.uint32)
-        lib().or_get_log(self._h, out.ctypes.data_as(C.POINTER(C.c_uint32)))
+        self._L.or_get_log(self._h, out.ctypes.data_as(C.POINTER(C.c_uint32)))
         return out[:n]
 
     def hits(self):
         """Ions absorbed at the cathode since the last call (the log is emptied),
         ordered by (step, pid): pid, species, step, xy (n x 2: where the path
         crossed z = 0), v (n x 3: v^{n+1/2})."""
-        n = lib().or_get_hits(self._h, None, None, None, None, None)
+        n = self._L.or_get_hits(self._h, None, None, None, None, None)
         m = max(n, 1)
         pid = np.zeros(m, dtype=np.uint32)
         sp = np.zeros(m, dtype=np.int32)
         step = np.zeros(m, dtype=np.uint32)
         xy = np.zeros((m, 2))
         v = np.zeros((m, 3))
-        lib().or_get_hits(self._h, pid.ctypes.data_as(C.POINTER(C.c_uint32)), sp.ctypes.data_as(C.POINTER(C.c_int32)),
+        self._L.or_get_hits(self._h, pid.ctypes.data_as(C.POINTER(C.c_uint32)), sp.ctypes.data_as(C.POINTER(C.c_int32)),
                           step.ctypes.data_as(C.POINTER(C.c_uint32)), _dp(xy), _dp(v))
         o = np.lexsort((pid[:n], step[:n]))
         return {"pid": pid[:n][o], "species": sp[:n][o], "step": step[:n][o], "xy": xy[:n][o], "v": v[:n][o]}
@@ -334,38 +357,38 @@ class Oracle:
     def gather(self, xyz):
         xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
         E = np.zeros_like(xyz)
-        lib().or_gather_points(self._h, xyz.shape[0], _dp(xyz), _dp(E))
+        self._L.or_gather_points(self._h, xyz.shape[0], _dp(xyz), _dp(E))
         return E
 
     def sigma(self, ch, E):
-        return lib().or_sigma(self._h, ch, float(E))
+        return self._L.or_sigma(self._h, ch, float(E))
 
     @property
     def step_index(self):
-        return int(lib().or_get_step(self._h))
+        return int(self._L.or_get_step(self._h))
 
     @step_index.setter
     def step_index(self, v):
-        lib().or_set_step(self._h, int(v))
+        self._L.or_set_step(self._h, int(v))
 
     @property
     def next_pid(self):
-        return int(lib().or_get_next_pid(self._h))
+        return int(self._L.or_get_next_pid(self._h))
 
     def set_circuit(self, R_ohm, C_farad, V0):
         """External RC circuit on the anode (off unless R > 0 and C > 0)."""
-        lib().or_set_circuit(self._h, float(R_ohm), float(C_farad), float(V0))
+        self._L.or_set_circuit(self._h, float(R_ohm), float(C_farad), float(V0))
 
     def set_source(self, q, flux, T_K):
-        if lib().or_set_source(self._h, q, flux, T_K) != 0:
+        if self._L.or_set_source(self._h, q, flux, T_K) != 0:
             raise ValueError("bad source")
 
     def source_acc(self, q):
-        return lib().or_get_source_acc(self._h, q)
+        return self._L.or_get_source_acc(self._h, q)
 
     def moments(self):
         m = OrMoments()
-        lib().or_get_moments(self._h, C.byref(m))
+        self._L.or_get_moments(self._h, C.byref(m))
         ns = self.nsp
         return {
             "step": m.step,

@@ -26,11 +26,33 @@
  * Everything is FP64. Loops are plain and unblocked. Sorting uses qsort,
  * the Poisson solve is unpreconditioned conjugate gradients.
  * Build with -ffp-contract=off so the rounding does not depend on the host.
+ *
+ * The same source also builds with -fopenmp (a timing baseline on all host
+ * cores). Only loops whose iterations are independent run in parallel, and
+ * every sum has one fixed order in both builds (dot products add fixed chunks
+ * of OR_CHUNK terms, then the chunk sums in order; the push advances particles
+ * in parallel and does its counts, energy sums, logs and event lists in a
+ * serial pass in particle order), so both builds give bit-identical results
+ * with any number of threads.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the OpenMP build (n <= 0: all it may use); 1 in the serial build. */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 #define OR_QE 1.602176634e-19
 #define OR_EPS0 8.8541878128e-12
@@ -551,6 +573,7 @@ typedef struct { int nx, ny, nu; } lap_t; /* nu = nz - 1 unknown planes */
 
 static void lap_apply(const lap_t* L, const double* x, double* y) {
   int nx = L->nx, ny = L->ny, nu = L->nu;
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < nu; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -565,9 +588,21 @@ static void lap_apply(const lap_t* L, const double* x, double* y) {
       }
 }
 
-static double dot(int64_t n, const double* a, const double* b) {
+/* Sum of a[i] b[i] in a fixed order: chunks of OR_CHUNK consecutive terms
+ * summed in index order, then the chunk sums in chunk order. part holds
+ * ceil(n / OR_CHUNK) doubles. */
+#define OR_CHUNK 4096
+static double dot(int64_t n, const double* a, const double* b, double* part) {
+  const int64_t nc = (n + OR_CHUNK - 1) / OR_CHUNK;
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nc; ++c) {
+    const int64_t i1 = (c + 1) * OR_CHUNK < n ? (c + 1) * OR_CHUNK : n;
+    double s = 0.0;
+    for (int64_t i = c * OR_CHUNK; i < i1; ++i) s += a[i] * b[i];
+    part[c] = s;
+  }
   double s = 0.0;
-  for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+  for (int64_t c = 0; c < nc; ++c) s += part[c];
   return s;
 }
 
@@ -578,41 +613,45 @@ static int cg_solve(const lap_t* L, const double* b, double* x, double rtol, int
   double* r = malloc(n * sizeof(double));
   double* p = malloc(n * sizeof(double));
   double* q = malloc(n * sizeof(double));
-  double bn = sqrt(dot(n, b, b));
+  double* part = malloc(((n + OR_CHUNK - 1) / OR_CHUNK + 1) * sizeof(double));
+  double bn = sqrt(dot(n, b, b, part));
   int it = 0;
   double rel = 0.0;
   if (bn == 0.0) {
     for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
     *rel_out = 0.0;
-    free(r); free(p); free(q);
+    free(r); free(p); free(q); free(part);
     return 0;
   }
   double tol = rtol * bn;
   for (int restart = 0; restart < 8; ++restart) {
     lap_apply(L, x, q);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) { r[i] = b[i] - q[i]; p[i] = r[i]; }
-    double rr = dot(n, r, r);
+    double rr = dot(n, r, r, part);
     rel = sqrt(rr) / bn;
     if (sqrt(rr) <= tol || it >= maxit) break;
     while (it < maxit) {
       lap_apply(L, p, q);
-      double alpha = rr / dot(n, p, q);
+      double alpha = rr / dot(n, p, q, part);
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
-      double rr_new = dot(n, r, r);
+      double rr_new = dot(n, r, r, part);
       ++it;
       if (sqrt(rr_new) <= tol) { rr = rr_new; break; }
       double beta = rr_new / rr;
       rr = rr_new;
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
     }
   }
   /* final true residual */
   lap_apply(L, x, q);
-  double tr = 0.0;
-  for (int64_t i = 0; i < n; ++i) { double d = b[i] - q[i]; tr += d * d; }
-  rel = sqrt(tr) / bn;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) q[i] = b[i] - q[i];
+  rel = sqrt(dot(n, q, q, part)) / bn;
   *rel_out = rel;
-  free(r); free(p); free(q);
+  free(r); free(p); free(q); free(part);
   return it;
 }
 
@@ -621,6 +660,7 @@ static void poisson_rhs(int nx, int ny, int nz, double h, double phi_c, double p
                         double* b) {
   int64_t plane = (int64_t)nx * ny;
   double s = h * h / OR_EPS0;
+#pragma omp parallel for schedule(static)
   for (int k = 1; k < nz; ++k)
     for (int64_t p = 0; p < plane; ++p) {
       double v = s * rho[(int64_t)k * plane + p];
@@ -780,14 +820,27 @@ void or_push_collide_resolve(or_state_t* s) {
     npre[sp] = t->n;
     dead[sp] = calloc(t->n ? t->n : 1, 1);
     cell_n[sp] = malloc((t->n ? t->n : 1) * sizeof(int64_t));
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < t->n; ++p) cell_n[sp][p] = cell_of(s, t->x[p], t->y[p], t->z[p]);
   }
 
+  /* Per particle: 0 moves on, 1 absorbed at the cathode, 2 at the anode, 3
+   * scattered elastically, 4 an event needing a victim (channel ev_ch, energy
+   * ev_E). The particles advance independently (in parallel in the OpenMP
+   * build); counts, energy sums, hit logs and events follow in particle order. */
   for (int sp = 0; sp < nsp; ++sp) {
     or_store_t* t = &s->st[sp];
     const or_species_t* S = &s->sp[sp];
-    double qm_dt = S->q / S->m * dt;
-    for (int64_t p = 0; p < t->n; ++p) {
+    const double qm_dt = S->q / S->m * dt;
+    int chs[OR_MAXXS], nch = 0;
+    for (int c = 0; c < s->nxs; ++c) if (s->xs[c].projectile == sp) chs[nch++] = c;
+    const int64_t n = t->n;
+    uint8_t* status = malloc(n ? n : 1);
+    int* ev_ch = malloc((n ? n : 1) * sizeof(int));
+    double* ev_E = malloc((n ? n : 1) * sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < n; ++p) {
+      status[p] = 0;
       /* a5 + a6: gather at x^n, leapfrog kick and drift */
       if (S->q != 0.0) {
         double E[3];
@@ -799,21 +852,11 @@ void or_push_collide_resolve(or_state_t* s) {
       double xn = t->x[p] + t->vx[p] * dt;
       double yn = t->y[p] + t->vy[p] * dt;
       double zn = t->z[p] + t->vz[p] * dt;
-      /* a7: absorption at the electrodes */
+      /* a7: absorption at the electrodes (x^n and v^{n+1/2} are kept for the
+       * energy sums and the hit log) */
       double v2 = t->vx[p] * t->vx[p] + t->vy[p] * t->vy[p] + t->vz[p] * t->vz[p];
       if (zn < 0.0 || zn >= Lz) {
-        dead[sp][p] = 1;
-        double ke = 0.5 * S->m * S->w * v2;
-        if (zn < 0.0) {
-          s->mom.abs_cathode[sp] += 1; s->mom.abs_energy_cathode[sp] += ke; q_cath += S->q * S->w;
-          if (S->role == OR_ION) {
-            /* z^n >= 0 > z^{n+1}, so vz < 0: the path meets z = 0 at x^n - v z^n / vz */
-            const double f = t->z[p] / t->vz[p];
-            log_hit(s, t->pid[p], sp, wrap(t->x[p] - t->vx[p] * f, Lx), wrap(t->y[p] - t->vy[p] * f, Ly),
-                    t->vx[p], t->vy[p], t->vz[p]);
-          }
-        }
-        else { s->mom.abs_anode[sp] += 1; s->mom.abs_energy_anode[sp] += ke; q_anode += S->q * S->w; }
+        status[p] = zn < 0.0 ? 1 : 2;
         continue;
       }
       t->x[p] = wrap(xn, Lx);
@@ -822,8 +865,6 @@ void or_push_collide_resolve(or_state_t* s) {
       /* a8: Monte Carlo collisions, Eq. (4): P = 1 - exp(-u n sigma(E) dt) summed
        * over the channels of this projectile; target density from the NGP
        * neutral count of the projectile's cell at x^n. */
-      int chs[OR_MAXXS], nch = 0;
-      for (int c = 0; c < s->nxs; ++c) if (s->xs[c].projectile == sp) chs[nch++] = c;
       if (nch == 0) continue;
       double u = sqrt(v2);
       double E_eV = 0.5 * S->m * v2 / OR_QE;
@@ -851,14 +892,41 @@ void or_push_collide_resolve(or_state_t* s) {
         t->vx[p] = u * st * cos(ph);
         t->vy[p] = u * st * sin(ph);
         t->vz[p] = u * ct;
-        s->mom.n_elastic += 1;
+        status[p] = 3;
       } else {
-        if (nev == evcap) { evcap = evcap ? 2 * evcap : 256; ev = realloc(ev, evcap * sizeof(or_event_t)); }
-        or_event_t* e = &ev[nev++];
-        e->e_idx = p; e->proj = sp; e->ch = chs[a]; e->cell = cell_n[sp][p]; e->pid = t->pid[p];
-        e->E_eV = E_eV; e->victim = -1;
+        status[p] = 4;
+        ev_ch[p] = chs[a];
+        ev_E[p] = E_eV;
       }
     }
+    for (int64_t p = 0; p < n; ++p) {
+      const int st = status[p];
+      if (st == 1 || st == 2) {
+        dead[sp][p] = 1;
+        const double v2 = t->vx[p] * t->vx[p] + t->vy[p] * t->vy[p] + t->vz[p] * t->vz[p];
+        double ke = 0.5 * S->m * S->w * v2;
+        if (st == 1) {
+          s->mom.abs_cathode[sp] += 1; s->mom.abs_energy_cathode[sp] += ke; q_cath += S->q * S->w;
+          if (S->role == OR_ION) {
+            /* z^n >= 0 > z^{n+1}, so vz < 0: the path meets z = 0 at x^n - v z^n / vz */
+            const double f = t->z[p] / t->vz[p];
+            log_hit(s, t->pid[p], sp, wrap(t->x[p] - t->vx[p] * f, Lx), wrap(t->y[p] - t->vy[p] * f, Ly),
+                    t->vx[p], t->vy[p], t->vz[p]);
+          }
+        }
+        else { s->mom.abs_anode[sp] += 1; s->mom.abs_energy_anode[sp] += ke; q_anode += S->q * S->w; }
+      } else if (st == 3) {
+        s->mom.n_elastic += 1;
+      } else if (st == 4) {
+        if (nev == evcap) { evcap = evcap ? 2 * evcap : 256; ev = realloc(ev, evcap * sizeof(or_event_t)); }
+        or_event_t* e = &ev[nev++];
+        e->e_idx = p; e->proj = sp; e->ch = ev_ch[p]; e->cell = cell_n[sp][p]; e->pid = t->pid[p];
+        e->E_eV = ev_E[p]; e->victim = -1;
+      }
+    }
+    free(status);
+    free(ev_ch);
+    free(ev_E);
   }
 
   /* a9: resolve of the events that need a victim neutral (ionization, charge

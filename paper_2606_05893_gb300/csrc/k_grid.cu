@@ -384,9 +384,11 @@ __global__ void k_load(Grid g, S st, DevCounters* cnt, int cur, int species, lon
     }
   }
 }
-__global__ void k_load_commit(DevCounters* cnt, int cur, int species, long long n) {
+__global__ void k_load_commit(DevCounters* cnt, int cur, int species, long long n, long long cap) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  cnt->n[cur][species] += n;
+  const unsigned long long m = cnt->n[cur][species] + (unsigned long long)n;
+  if (m > (unsigned long long)cap) atomicOr(&cnt->error, ERR_CAPACITY);
+  cnt->n[cur][species] = m > (unsigned long long)cap ? (unsigned long long)cap : m;
   cnt->next_pid += (unsigned int)n;
 }
 template <class S>
@@ -394,7 +396,7 @@ void launch_load(const Grid& g, S st, DevCounters* cnt, int cur, int species, lo
                  const double* v, long long n, const NextDeposit& nd, int neutral, cudaStream_t s) {
   if (n <= 0) return;
   PIC_LAUNCH(grid_for(n), kBlock, 0, s, k_load<S>)(g, st, cnt, cur, species, cap, x, v, n, nd, neutral);
-  PIC_LAUNCH(1, 1, 0, s, k_load_commit)(cnt, cur, species, n);
+  PIC_LAUNCH(1, 1, 0, s, k_load_commit)(cnt, cur, species, n, cap);
 }
 
 template <class S>

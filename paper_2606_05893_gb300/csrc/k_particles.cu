@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
   const int tx = threadIdx.x;
   s_tv2[0][tx] = s_tv2[1][tx] = 0.0;
   s_tn[0][tx] = s_tn[1][tx] = s_tn[2][tx] = 0u;
-  const long long n = (long long)a.cnt->n[a.cur_in][a.species];
+  const long long n = min((long long)a.cnt->n[a.cur_in][a.species], a.cap);
   const uint32_t step = a.cnt->step;
   if (blockIdx.x == 0 && threadIdx.x == 0)
     a.cnt->pushed[a.species] += (unsigned long long)n - a.cnt->n_tomb[a.species];
@@ -445,6 +445,10 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
         tot += c;
       }
       s_base = tot ? atomicAdd(out_count, (unsigned long long)tot) : 0ull;
+      // an overflowing round (ERR_CAPACITY below) caps the count again after its
+      // own add, so the count ends at min(kept, capacity) and no later kernel
+      // indexes past the store
+      if (s_base + tot > (unsigned long long)a.cap) atomicMin(out_count, (unsigned long long)a.cap);
     }
     __syncthreads();
     unsigned long long wbase = s_base + s_wcnt[warp];

@@ -247,28 +247,35 @@ static int radix_passes(const SortBuffers& b, const unsigned long long* n_dev, i
 // ---------------------------------------------------------------------------
 // words[i] = cell << 32 | slot (the bucket and the slot taken in it); the pair
 // (pid << 32 | i) goes to cell_start[cell] + slot. The dead bucket is cell =
-// ncell, and cell_start[ncell] is the live total.
-__global__ void k_seg_scatter(long long n_max, const unsigned long long* n_dev,
+// ncell, and cell_start[ncell] is the live total. Tombstones are dropped after
+// the sort, so their order is free: they take their permutation entries here,
+// in slot order, and their bucket is never sorted.
+__global__ void k_seg_scatter(long long ncell, long long n_max, const unsigned long long* n_dev,
                               const unsigned long long* __restrict__ words, const uint32_t* __restrict__ pids,
-                              const long long* __restrict__ cs, unsigned long long* __restrict__ out) {
+                              const long long* __restrict__ cs, unsigned long long* __restrict__ out,
+                              uint32_t* __restrict__ perm) {
   const long long n = min((long long)*n_dev, n_max);
   for (long long i = gtid(); i < n; i += gstride()) {
     const unsigned long long w = words[i];
-    out[cs[w >> 32] + (long long)(w & 0xFFFFFFFFull)] = ((unsigned long long)pids[i] << 32) | (unsigned long long)i;
+    const long long pos = cs[w >> 32] + (long long)(w & 0xFFFFFFFFull);
+    if ((long long)(w >> 32) == ncell)
+      perm[pos] = (uint32_t)i;
+    else
+      out[pos] = ((unsigned long long)pids[i] << 32) | (unsigned long long)i;
   }
 }
 
-// One thread per bucket (cells 0..ncell-1, then the dead bucket): the rank of
-// an entry among the bucket's (pid, index) values is its place. Larger buckets
+// One thread per cell bucket: the rank of an entry among the bucket's
+// (pid, index) values is its place. Larger buckets
 // are listed for the warp-wide kernel (from the front of `big`) or the
 // block-wide one (from the back; ncell + 1 entries hold both lists).
 __global__ void k_seg_sort(long long ncell, const long long* __restrict__ cs, const unsigned long long* n_dev,
                            const unsigned long long* __restrict__ v, uint32_t* __restrict__ perm,
                            int32_t* __restrict__ big, SegCtl* ctl) {
-  const long long n = (long long)*n_dev;
-  for (long long c = gtid(); c <= ncell; c += gstride()) {
+  (void)n_dev;
+  for (long long c = gtid(); c < ncell; c += gstride()) {
     const long long a = cs[c];
-    const long long b = c < ncell ? cs[c + 1] : n;
+    const long long b = cs[c + 1];
     const long long m = b - a;
     if (m <= 0) continue;
     if (m == 1) {
@@ -358,14 +365,16 @@ static int seg_grid(long long n) {
   return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
-void launch_seg_scatter(long long n_max, const unsigned long long* n_dev, const unsigned long long* words,
-                        const uint32_t* pids, const long long* cell_start, unsigned long long* out, cudaStream_t s) {
-  PIC_LAUNCH(seg_grid(n_max), kSortBlock, 0, s, k_seg_scatter)(n_max, n_dev, words, pids, cell_start, out);
+void launch_seg_scatter(long long ncell, long long n_max, const unsigned long long* n_dev,
+                        const unsigned long long* words, const uint32_t* pids, const long long* cell_start,
+                        unsigned long long* out, uint32_t* perm, cudaStream_t s) {
+  PIC_LAUNCH(seg_grid(n_max), kSortBlock, 0, s, k_seg_scatter)(ncell, n_max, n_dev, words, pids, cell_start, out,
+                                                               perm);
 }
 
 void launch_seg_sort(long long ncell, const long long* cell_start, const unsigned long long* n_dev,
                      const unsigned long long* vals, uint32_t* perm, int32_t* big, SegCtl* ctl, cudaStream_t s) {
-  PIC_LAUNCH(seg_grid(ncell + 1), kSortBlock, 0, s, k_seg_sort)(ncell, cell_start, n_dev, vals, perm, big, ctl);
+  PIC_LAUNCH(seg_grid(ncell), kSortBlock, 0, s, k_seg_sort)(ncell, cell_start, n_dev, vals, perm, big, ctl);
   PIC_LAUNCH(8 * sm_count(), kSortBlock, 0, s, k_seg_sort_mid)(ncell, cell_start, n_dev, vals, perm, big, ctl);
   PIC_LAUNCH(2 * sm_count(), kSortBlock, 0, s, k_seg_sort_big)(ncell, cell_start, n_dev, vals, perm, big, ctl);
 }

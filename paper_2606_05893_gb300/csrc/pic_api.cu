@@ -711,7 +711,8 @@ pic_status sort_instance(pic_handle* h, Instance* I) {
     launch_cell_slots<S>(I->g, store_of<S>(I, s, c), I->cap[s], ndev, I->cell_count, I->csort.ka, I->csort.va,
                          I->seg_ctl, st);
     exclusive_scan_i32_i64(I->cell_count, I->g.ncell, I->cell_start[s], I->scan_tmp, st);
-    launch_seg_scatter(I->cap[s], ndev, I->csort.ka, I->csort.va, I->cell_start[s], I->csort.kb, st);
+    launch_seg_scatter(I->g.ncell, I->cap[s], ndev, I->csort.ka, I->csort.va, I->cell_start[s], I->csort.kb,
+                       I->csort.vb, st);
     launch_seg_sort(I->g.ncell, I->cell_start[s], ndev, I->csort.kb, I->csort.vb, I->seg_big, I->seg_ctl, st);
     CK(h, cudaMemcpyAsync(I->seg_host, I->seg_ctl, sizeof(SegCtl), cudaMemcpyDeviceToHost, st));
     CK(h, cudaStreamSynchronize(st));

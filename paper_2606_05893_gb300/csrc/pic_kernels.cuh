@@ -699,8 +699,9 @@ constexpr int kSegBig = 4096;   // by one block
 template <class S>
 void launch_cell_slots(const Grid& g, S st, long long n_max, const unsigned long long* n_dev, int32_t* cell_count,
                        unsigned long long* words, uint32_t* pids, SegCtl* ctl, cudaStream_t s);
-void launch_seg_scatter(long long n_max, const unsigned long long* n_dev, const unsigned long long* words,
-                        const uint32_t* pids, const long long* cell_start, unsigned long long* out, cudaStream_t s);
+void launch_seg_scatter(long long ncell, long long n_max, const unsigned long long* n_dev,
+                        const unsigned long long* words, const uint32_t* pids, const long long* cell_start,
+                        unsigned long long* out, uint32_t* perm, cudaStream_t s);
 void launch_seg_sort(long long ncell, const long long* cell_start, const unsigned long long* n_dev,
                      const unsigned long long* vals, uint32_t* perm, int32_t* big, SegCtl* ctl, cudaStream_t s);
 
