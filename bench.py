@@ -55,7 +55,13 @@ UNET_NCU_TRAFFIC = {"d0a": 536.2e6}
 # DRAM bytes (read + write) per pushed electron of the same kernel from one ncu capture of the
 # current kernel (profiles/k_push_mixed_electrons_128x128x256.md: 145.18 MB for 2 593 379
 # electrons); None where no capture of the current kernel exists
-NCU_TRAFFIC_PER_PARTICLE = {"mixed": 55.98, "fp64": None}
+NCU_TRAFFIC_PER_PARTICLE = {"mixed": 56.07, "fp64": 102.68}
+# The FP64 electron push is bound by GB300's FP64 pipe (2 FP64 operations per cycle
+# and SM), not by HBM: FP64 warp instructions x 32 per pushed electron from one ncu
+# capture of the current kernel (profiles/k_push_fp64_electrons_128x128x256.md:
+# 9 081 415 instructions for 2 593 379 electrons, the pipe active 84 % of cycles)
+FP64_PIPE_SLOTS_PER_ELECTRON = 112.06
+FP64_OPS_PER_SM_CYCLE = 2
 
 
 def dist_env():
@@ -813,6 +819,22 @@ def main():
                               "speedup_mixed_over_fp64": value / (fa["pushes"] / (fa["ms"] * 1e-3)),
                               "phase_ms_per_step": {k: round(v[0] / max(f["prof_steps"], 1), 4) for k, v in fph.items()},
                               "push_kernel_ms": fpush_ms / max(fpush_n, 1), "clocks": f["clocks"]}
+        # its push against the FP64 pipe (the bound) and against HBM
+        import torch
+        f_e = f["prof_push_e"] / max(fpush_n, 1)
+        f_s = fpush_ms / max(fpush_n, 1) * 1e-3
+        sm_mhz = (f["clocks"] or {}).get("sm_mhz") or 2070.0
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+        f_peak = nsm * FP64_OPS_PER_SM_CYCLE * sm_mhz * 1e6 / 1e12
+        f_ach = FP64_PIPE_SLOTS_PER_ELECTRON * f_e / f_s / 1e12
+        f_hbm = BYTES_PER_PARTICLE["fp64"] * f_e / f_s / 1e9
+        line["fp64_plain"]["push_roofline"] = {
+            "bound": "fp64", "achieved": f_ach, "peak": f_peak, "unit": "T FP64 ops/s", "frac": f_ach / f_peak,
+            "peak_kind": f"{nsm} SMs x {FP64_OPS_PER_SM_CYCLE} FP64 ops per cycle at the sampled {sm_mhz:.0f} MHz",
+            "ops_per_particle": FP64_PIPE_SLOTS_PER_ELECTRON, "particles_per_launch": f_e,
+            "hbm": {"achieved": f_hbm, "peak": peak, "unit": "GB/s", "frac": f_hbm / peak,
+                    "bytes_per_particle": BYTES_PER_PARTICLE["fp64"],
+                    "traffic": NCU_TRAFFIC_PER_PARTICLE["fp64"] * f_e}}
     if r.get("steady"):
         line["steady_state"] = r["steady"]
     if args.c3 and args.workload == "c2":

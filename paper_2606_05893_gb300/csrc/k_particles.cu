@@ -287,34 +287,52 @@ __global__ void k_inject_commit(DevCounters* cnt, InjectCommit c) {
 // ---------------------------------------------------------------------------
 // a5-a8 + a10: gather / push / absorb / collide / compact
 // ---------------------------------------------------------------------------
-// Next-step deposit from the push. MIXED store: weights summed over runs of
-// equal cells in the warp (a cell-sorted store keeps them adjacent), one atomic
-// per run and corner; the neutral count likewise. FP64 store: plain FP64
+// Next-step deposit from the push. MIXED store: the lanes of a warp whose
+// particles landed in the same cell are grouped with __match_any_sync (adjacent
+// or not: the particles of one cell are interleaved with those of the next
+// plane after a drift), the group's lowest lane adds the others' CIC weights
+// from shared memory and issues the group's reductions: one per row and group.
+// The neutral count likewise (the group's size). FP64 store: plain FP64
 // atomics (summing doubles across lanes would load the narrow FP64 pipe).
 // Every lane of the warp calls it.
 template <bool CHARGED, bool NEUTRAL>
 __device__ __forceinline__ void next_deposit(const PushArgs<StoreMx>& a, const ParticleMx& p, bool stored) {
+  const int lane = threadIdx.x & 31;
+  // a lane without a particle gets a key of its own (negative: never a cell)
+  const int key = stored ? p.cell : -1 - lane;
+  const unsigned grp = __match_any_sync(0xffffffffu, key);
+  const bool lead = stored && (__ffs(grp) - 1) == lane;
   if (CHARGED) {
+    // this warp's weights, [corner][lane] (conflict-free rows of 32 words)
+    __shared__ float s_w[kPushWarps][8 * 32];
+    float* sw = s_w[threadIdx.x >> 5];
     float w[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int key = -1;
     if (stored) {
-      key = p.cell;
       cic_weights(p.ox, p.oy, p.oz, w);
       const float q = (float)a.nd.qw_h3[a.species];
 #pragma unroll
       for (int c = 0; c < 8; ++c) w[c] *= q;
     }
-    if (warp_run_sum(key, w) && key >= 0) {
+    if (__ballot_sync(0xffffffffu, grp != (1u << lane))) {  // some lanes share a cell
+#pragma unroll
+      for (int c = 0; c < 8; ++c) sw[c * 32 + lane] = w[c];
+      __syncwarp();
+      if (lead) {
+        for (unsigned m = grp & ~(1u << lane); m; m &= m - 1) {
+          const int l = __ffs(m) - 1;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) w[c] += sw[c * 32 + l];
+        }
+      }
+      __syncwarp();  // the buffer is refilled by the next call
+    }
+    if (lead) {
       int i, j, k;
       cell_ijk(a.g, key, i, j, k);
       cic_add_f32(a.nd.rho32, a.g, i, j, k, w, (a.g.nx & 3) == 0);
     }
   }
-  if (NEUTRAL) {
-    float one[1] = {stored ? 1.f : 0.f};  // counts are exact in FP32
-    const int key = stored ? p.cell : -1;
-    if (warp_run_sum(key, one) && key >= 0) atomicAdd(&a.nd.ncount[a.species][key], (int)one[0]);
-  }
+  if (NEUTRAL && lead) atomicAdd(&a.nd.ncount[a.species][key], __popc(grp));
 }
 template <bool CHARGED, bool NEUTRAL>
 __device__ __forceinline__ void next_deposit(const PushArgs<Store64>& a, const Particle64& p, bool stored) {
