@@ -1914,6 +1914,14 @@ cudaError_t Solver::invalidate(cudaStream_t s) {
 SolveResult Solver::result(cudaStream_t s) {
   cudaMemcpyAsync(host_ctl, ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
+  return result_read();
+}
+
+cudaError_t Solver::result_async(cudaStream_t s) {
+  return cudaMemcpyAsync(host_ctl, ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s);
+}
+
+SolveResult Solver::result_read() const {
   SolveResult r;
   r.iters = host_ctl->it_total;
   r.resid_rel = host_ctl->resid_rel;

@@ -170,6 +170,8 @@ struct Instance {
   unsigned long long step_kernels[4]{};  // kernel nodes recorded in each
   bool graphs_ok = true;
   cudaStream_t cap_stream = nullptr;  // private stream for recording
+  cudaEvent_t cap_done = nullptr;     // end of this instance's branch in a recorded ensemble step
+  unsigned int graph_epoch = 0;       // advanced whenever the recorded steps are dropped
   double* phi = nullptr;
   double4_32a* E64 = nullptr;
   float4* E32 = nullptr;
@@ -223,6 +225,15 @@ struct Instance {
 
 }  // namespace
 
+// One step of every instance of a handle recorded as one graph (each instance a
+// branch from a common fork to a common join), keyed by each instance's store
+// and deposit parities and graph epoch.
+struct EnsembleGraph {
+  std::vector<uint32_t> key;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long kernels = 0;
+};
+
 struct pic_handle {
   std::vector<Instance*> inst;
   cudaStream_t stream = nullptr;
@@ -230,6 +241,10 @@ struct pic_handle {
   std::string err;
   bool dead = false;
   int sticky = 0;  // sticky non-fatal status bits (ENOCONV)
+  std::vector<EnsembleGraph> ens;  // recorded ensemble steps (a few parity patterns)
+  bool ens_ok = true;              // false once recording an ensemble step failed
+  cudaStream_t ens_cap = nullptr;  // origin stream of the ensemble recording
+  cudaEvent_t ens_fork = nullptr;  // the recording's fork into the instance streams
 };
 
 namespace {
@@ -303,6 +318,7 @@ void free_instance(Instance* I) {
   for (auto& e : I->step_exec)
     if (e) cudaGraphExecDestroy(e);
   if (I->cap_stream) cudaStreamDestroy(I->cap_stream);
+  if (I->cap_done) cudaEventDestroy(I->cap_done);
   cudaFree(I->phi);
   cudaFree(I->E64);
   cudaFree(I->E32);
@@ -1045,6 +1061,68 @@ void drop_step_graphs(Instance* I) {
     if (e) cudaGraphExecDestroy(e);
     e = nullptr;
   }
+  ++I->graph_epoch;  // recorded ensemble steps holding this instance no longer match
+}
+
+// Host-side state a step advances (restored when recording a step fails).
+struct HostStepState {
+  double *r64, *r64n;
+  float *r32, *r32n;
+  int32_t *nc[kMaxSpecies], *ncn[kMaxSpecies];
+  int cur[kMaxSpecies];
+  uint32_t step;
+  bool stale;
+  void save(const Instance* I) {
+    r64 = I->rho64;
+    r64n = I->rho64_next;
+    r32 = I->rho32;
+    r32n = I->rho32_next;
+    for (int s = 0; s < kMaxSpecies; ++s) {
+      nc[s] = I->ncount[s];
+      ncn[s] = I->ncount_next[s];
+      cur[s] = I->cur[s];
+    }
+    step = I->step;
+    stale = I->phi64_stale;
+  }
+  void restore(Instance* I) const {
+    I->rho64 = r64;
+    I->rho64_next = r64n;
+    I->rho32 = r32;
+    I->rho32_next = r32n;
+    for (int s = 0; s < kMaxSpecies; ++s) {
+      I->ncount[s] = nc[s];
+      I->ncount_next[s] = ncn[s];
+      I->cur[s] = cur[s];
+    }
+    I->step = step;
+    I->phi64_stale = stale;
+  }
+};
+
+// The host-side effect of replaying a recorded step (what step_instance does
+// to the host state of a step that neither sorts nor deposits from scratch).
+void advance_replayed(Instance* I) {
+  std::swap(I->rho32, I->rho32_next);
+  std::swap(I->rho64, I->rho64_next);
+  for (int s = 0; s < I->nsp; ++s) std::swap(I->ncount[s], I->ncount_next[s]);
+  if (I->mixed) I->phi64_stale = true;
+  for (int s = 0; s < I->nsp; ++s) I->cur[s] ^= 1;
+  I->step += 1;
+}
+
+bool sort_due(const Instance* I) {
+  return I->cfg.sort_interval > 0 && I->step % (uint32_t)I->cfg.sort_interval == 0;
+}
+
+// a step of this instance qualifies for a recorded graph (its own or the ensemble's)
+bool step_recordable(const Instance* I) {
+  return I->graphs_ok && I->next_valid && !sort_due(I) && !I->timer.on && I->solver.exec != nullptr;
+}
+
+uint32_t graph_key(const Instance* I) {
+  const void* rho_now = I->mixed ? (const void*)I->rho32 : (const void*)I->rho64;
+  return (uint32_t)((I->cur[0] & 1) | (rho_now == I->rho_first ? 2 : 0));
 }
 
 // One step of one instance: replayed from a recorded graph when the step neither
@@ -1059,21 +1137,12 @@ pic_status run_step(pic_handle* h, Instance* I) {
     if (ps != PIC_OK) return ps;
     drop_step_graphs(I);
   }
-  const bool sort_now = I->cfg.sort_interval > 0 && I->step % (uint32_t)I->cfg.sort_interval == 0;
-  const bool graphable =
-      I->graphs_ok && I->next_valid && !sort_now && !I->timer.on && I->solver.exec != nullptr;
-  if (!graphable) return step_instance<S>(h, I);
-  const void* rho_now = I->mixed ? (const void*)I->rho32 : (const void*)I->rho64;
-  const int key = (I->cur[0] & 1) | (rho_now == I->rho_first ? 2 : 0);
+  if (!step_recordable(I)) return step_instance<S>(h, I);
+  const int key = (int)graph_key(I);
   if (I->step_exec[key]) {
     count_graph(I->step_kernels[key]);
     CK(h, cudaGraphLaunch(I->step_exec[key], I->stream));
-    std::swap(I->rho32, I->rho32_next);
-    std::swap(I->rho64, I->rho64_next);
-    for (int s = 0; s < I->nsp; ++s) std::swap(I->ncount[s], I->ncount_next[s]);
-    if (I->mixed) I->phi64_stale = true;
-    for (int s = 0; s < I->nsp; ++s) I->cur[s] ^= 1;
-    I->step += 1;
+    advance_replayed(I);
     return PIC_OK;
   }
   if (!I->cap_stream && cudaStreamCreateWithFlags(&I->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1082,20 +1151,8 @@ pic_status run_step(pic_handle* h, Instance* I) {
     return step_instance<S>(h, I);
   }
   // host-side state the recording advances (restored if recording fails)
-  double* r64 = I->rho64;
-  double* r64n = I->rho64_next;
-  float* r32 = I->rho32;
-  float* r32n = I->rho32_next;
-  int32_t* nc[kMaxSpecies];
-  int32_t* ncn[kMaxSpecies];
-  int cur[kMaxSpecies];
-  for (int s = 0; s < kMaxSpecies; ++s) {
-    nc[s] = I->ncount[s];
-    ncn[s] = I->ncount_next[s];
-    cur[s] = I->cur[s];
-  }
-  const uint32_t step0 = I->step;
-  const bool stale0 = I->phi64_stale;
+  HostStepState saved;
+  saved.save(I);
   const cudaStream_t run = I->stream;
   const unsigned long long l0 = g_launches, k0 = g_kernels;
   I->stream = I->cap_stream;
@@ -1120,17 +1177,7 @@ pic_status run_step(pic_handle* h, Instance* I) {
               cudaGetErrorString(e1 != cudaSuccess ? e1 : e), ps == PIC_OK ? "" : "; ", ps == PIC_OK ? "" : h->err.c_str());
     cudaGetLastError();
     h->err.clear();
-    I->rho64 = r64;
-    I->rho64_next = r64n;
-    I->rho32 = r32;
-    I->rho32_next = r32n;
-    for (int s = 0; s < kMaxSpecies; ++s) {
-      I->ncount[s] = nc[s];
-      I->ncount_next[s] = ncn[s];
-      I->cur[s] = cur[s];
-    }
-    I->step = step0;
-    I->phi64_stale = stale0;
+    saved.restore(I);
     I->graphs_ok = false;
     return step_instance<S>(h, I);
   }
@@ -1139,6 +1186,112 @@ pic_status run_step(pic_handle* h, Instance* I) {
   count_graph(kernels);
   CK(h, cudaGraphLaunch(exec, I->stream));
   return PIC_OK;
+}
+
+// One step of every instance of the handle as one recorded graph launched on
+// the handle's stream: each instance's step is a branch between a common fork
+// and join, so the instances run concurrently as they do on their own streams,
+// with one launch per ensemble step instead of one per instance. Used when
+// every instance's step qualifies for recording (no sort, no phase timing, no
+// deposit from scratch); the graph is recorded the first time a pattern of
+// parities appears (a handful of patterns: each step flips every parity).
+// Returns false, with nothing enqueued and every host state unchanged, when the
+// step cannot be recorded; the caller then steps the instances one by one.
+bool ensemble_recordable(const pic_handle* h) {
+  if (h->inst.size() < 2 || !h->ens_ok) return false;
+  for (const auto* I : h->inst)
+    if (I->plan_dirty || !step_recordable(I)) return false;
+  return true;
+}
+
+bool run_ensemble_step(pic_handle* h) {
+  std::vector<uint32_t> key;
+  key.reserve(h->inst.size());
+  for (const auto* I : h->inst) key.push_back(graph_key(I) | (I->graph_epoch << 2));
+  for (auto& g : h->ens) {
+    if (g.key != key) continue;
+    count_graph(g.kernels);
+    if (cudaGraphLaunch(g.exec, h->stream) != cudaSuccess) {
+      cudaGetLastError();
+      h->ens_ok = false;
+      return false;
+    }
+    for (auto* I : h->inst) advance_replayed(I);
+    return true;
+  }
+  // record: the origin stream forks into every instance's private stream
+  bool ok = h->ens_cap != nullptr || cudaStreamCreateWithFlags(&h->ens_cap, cudaStreamNonBlocking) == cudaSuccess;
+  if (ok && !h->ens_fork) ok = cudaEventCreateWithFlags(&h->ens_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (auto* I : h->inst) {
+    if (!ok) break;
+    if (!I->cap_stream) ok = cudaStreamCreateWithFlags(&I->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok && !I->cap_done) ok = cudaEventCreateWithFlags(&I->cap_done, cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    h->ens_ok = false;
+    return false;
+  }
+  std::vector<HostStepState> saved(h->inst.size());
+  std::vector<cudaStream_t> run(h->inst.size());
+  for (size_t i = 0; i < h->inst.size(); ++i) {
+    saved[i].save(h->inst[i]);
+    run[i] = h->inst[i]->stream;
+  }
+  const unsigned long long l0 = g_launches, k0 = g_kernels;
+  cudaError_t e = cudaStreamBeginCapture(h->ens_cap, cudaStreamCaptureModeThreadLocal);
+  pic_status ps = e == cudaSuccess ? PIC_OK : PIC_ECUDA;
+  if (e == cudaSuccess) e = cudaEventRecord(h->ens_fork, h->ens_cap);
+  for (size_t i = 0; i < h->inst.size() && e == cudaSuccess && ps == PIC_OK; ++i) {
+    Instance* I = h->inst[i];
+    I->stream = I->cap_stream;
+    e = cudaStreamWaitEvent(I->cap_stream, h->ens_fork, 0);
+    if (e == cudaSuccess) ps = I->mixed ? step_instance<StoreMx>(h, I) : step_instance<Store64>(h, I);
+    if (e == cudaSuccess && ps == PIC_OK) e = cudaEventRecord(I->cap_done, I->cap_stream);
+    if (e == cudaSuccess && ps == PIC_OK) e = cudaStreamWaitEvent(h->ens_cap, I->cap_done, 0);
+    I->stream = run[i];
+  }
+  cudaGraph_t g = nullptr;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(h->ens_cap, &cs);
+  cudaError_t e1 = cs != cudaStreamCaptureStatusNone ? cudaStreamEndCapture(h->ens_cap, &g) : cudaErrorStreamCaptureInvalidated;
+  for (size_t i = 0; i < h->inst.size(); ++i) h->inst[i]->stream = run[i];
+  const unsigned long long kernels = g_kernels - k0;
+  g_launches = l0;  // recorded, not run
+  g_kernels = k0;
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess && ps == PIC_OK && e1 == cudaSuccess && g) {
+    if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
+  }
+  if (g) cudaGraphDestroy(g);
+  if (!exec) {
+    if (getenv("PIC_VERBOSE"))
+      fprintf(stderr, "pic: ensemble step recording unavailable (%s%s%s), stepping instances one by one\n",
+              cudaGetErrorString(e != cudaSuccess ? e : e1), ps == PIC_OK ? "" : "; ", ps == PIC_OK ? "" : h->err.c_str());
+    cudaGetLastError();
+    h->err.clear();
+    for (size_t i = 0; i < h->inst.size(); ++i) saved[i].restore(h->inst[i]);
+    h->ens_ok = false;
+    return false;
+  }
+  if (h->ens.size() >= 8) {  // a few patterns recur; drop the oldest beyond that
+    cudaGraphExecDestroy(h->ens.front().exec);
+    h->ens.erase(h->ens.begin());
+  }
+  EnsembleGraph eg;
+  eg.key = key;
+  eg.exec = exec;
+  eg.kernels = kernels;
+  h->ens.push_back(eg);
+  count_graph(kernels);
+  if (cudaGraphLaunch(exec, h->stream) != cudaSuccess) {
+    // recorded but not launched: the host states advanced by the recording go back
+    cudaGetLastError();
+    for (size_t i = 0; i < h->inst.size(); ++i) saved[i].restore(h->inst[i]);
+    h->ens_ok = false;
+    return false;
+  }
+  return true;
 }
 
 pic_status check(pic_handle* h, int inst) {
@@ -1224,6 +1377,10 @@ pic_status pic_destroy(pic_handle* h) {
   if (!h) return PIC_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  for (auto& g : h->ens)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (h->ens_cap) cudaStreamDestroy(h->ens_cap);
+  if (h->ens_fork) cudaEventDestroy(h->ens_fork);
   for (auto* I : h->inst) free_instance(I);
   if (h->fork) cudaEventDestroy(h->fork);
   delete h;
@@ -1315,15 +1472,36 @@ pic_status pic_step(pic_handle* h, int32_t nsteps) {
   if (h->dead) return fail(h, PIC_ESTATE, "handle unusable after an earlier fatal error: %s", h->err.c_str());
   if (nsteps < 0) return fail(h, PIC_EINVAL, "nsteps must be >= 0");
   h->sticky = 0;
-  // several instances step concurrently on their own streams, ordered after the
-  // caller's stream and joined back into it
-  const bool fork = h->inst.size() > 1 && nsteps > 0;
-  if (fork) {
+  // several instances step concurrently: as one recorded ensemble step on the
+  // caller's stream when every instance's step qualifies, else each on its own
+  // stream, ordered after the caller's stream and joined back into it
+  const bool multi = h->inst.size() > 1 && nsteps > 0;
+  bool forked = false;   // the instance streams are ordered after the caller's stream
+  bool pending = false;  // the instance streams hold work not yet joined into it
+  auto fork_instances = [&]() -> pic_status {
     CK(h, cudaEventRecord(h->fork, h->stream));
     for (auto* I : h->inst) CK(h, cudaStreamWaitEvent(I->stream, h->fork, 0));
-  }
+    forked = true;
+    return PIC_OK;
+  };
+  auto join_instances = [&]() -> pic_status {
+    for (auto* I : h->inst) {
+      CK(h, cudaEventRecord(I->done, I->stream));
+      CK(h, cudaStreamWaitEvent(h->stream, I->done, 0));
+    }
+    pending = false;
+    return PIC_OK;
+  };
   pic_status step_status = PIC_OK;
   for (int n = 0; n < nsteps && step_status == PIC_OK; ++n) {
+    if (multi && ensemble_recordable(h)) {
+      if (pending && (step_status = join_instances()) != PIC_OK) break;
+      if (run_ensemble_step(h)) {
+        forked = false;
+        continue;
+      }
+    }
+    if (multi && !forked && (step_status = fork_instances()) != PIC_OK) break;
     for (auto* I : h->inst) {
       pic_status st = I->mixed ? run_step<StoreMx>(h, I) : run_step<Store64>(h, I);
       if (st != PIC_OK) {
@@ -1331,11 +1509,15 @@ pic_status pic_step(pic_handle* h, int32_t nsteps) {
         break;
       }
     }
+    pending = multi;
   }
-  if (fork) {
-    for (auto* I : h->inst) {
-      CK(h, cudaEventRecord(I->done, I->stream));
-      CK(h, cudaStreamWaitEvent(h->stream, I->done, 0));
+  if (multi) {
+    // joined into the caller's stream, and left ordered after it
+    pic_status js = pending ? join_instances() : PIC_OK;
+    if (js == PIC_OK && !forked) js = fork_instances();
+    if (js != PIC_OK) {
+      h->dead = true;
+      return js;
     }
   }
   if (step_status != PIC_OK) {
@@ -1343,17 +1525,21 @@ pic_status pic_step(pic_handle* h, int32_t nsteps) {
     return step_status;
   }
   // device-side error flags (capacity, event overflow) of the completed steps
+  // and the last solve of every instance: all copies queued, one wait
+  for (auto* I : h->inst) {
+    if (nsteps > 0) CK(h, I->solver.result_async(h->stream));
+    if (I->host_cnt) CK(h, cudaMemcpyAsync(I->host_cnt, I->cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, h->stream));
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    h->dead = true;
+    return fail(h, PIC_ECUDA, "step: %s", cudaGetErrorString(cudaGetLastError()));
+  }
   for (auto* I : h->inst) {
     if (nsteps > 0) {
-      I->last = I->solver.result(h->stream);
+      I->last = I->solver.result_read();
       if (!I->last.converged) h->sticky |= 1;
     }
     if (I->host_cnt) {
-      pic_status st = sync_counters(h, I);
-      if (st != PIC_OK) {
-        h->dead = true;
-        return st;
-      }
       const int e = I->host_cnt->error;
       if (e) {
         // reported once: clear the device flags so that later steps start clean

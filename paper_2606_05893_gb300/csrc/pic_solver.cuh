@@ -103,6 +103,10 @@ struct Solver {
   float fold_first() const { return (float)(h_phi_c + (plan[0].nz == 2 ? h_phi_a : 0.0)); }
   float fold_last() const { return plan[0].nz == 2 ? 0.f : (float)h_phi_a; }
   SolveResult result(cudaStream_t s);
+  // the same in two parts: enqueue the copy of the decision block, then (after
+  // the caller synchronized the stream) read it
+  cudaError_t result_async(cudaStream_t s);
+  SolveResult result_read() const;
 };
 
 }  // namespace pic

@@ -66,3 +66,42 @@ def test_sort_interval_changes_order_only(pkg):
         pkg.pic_set_sort_interval(s1.h, 0, -1)
     s1.close()
     s2.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ensemble_steps_are_one_recorded_launch(pkg, precision):
+    """Steps in which every instance qualifies for recording run as one graph
+    launch for the whole handle (each instance a branch) and give what the
+    instances give alone; a sort step of one instance falls back to stepping
+    the instances one by one."""
+    prec = pkg.PIC_FP64 if precision == "fp64" else pkg.PIC_MIXED
+    wls = [W.config_small(seed=31, n_preload=2500), W.config_tiny(seed=32, n_preload=700),
+           W.config_small(seed=33, n_preload=1500)]
+    for w in wls:
+        w.sort_interval = 6
+    both = pkg.Simulation(wls, precision=prec, cg_rtol=1e-13, cg_maxit=5000)
+    alone = [pkg.Simulation(w, precision=prec, cg_rtol=1e-13, cg_maxit=5000) for w in wls]
+    both.step(2)  # step 0 deposits from scratch and sorts; step 1 is recorded
+    for s in alone:
+        s.step(2)
+    l0 = pkg.pic_launch_count()
+    both.step(3)  # steps 2-4: replays of two parity patterns, one launch each
+    assert pkg.pic_launch_count() - l0 == 3
+    both.step(5)  # steps 5-9: step 6 sorts every instance (stepped one by one)
+    for s in alone:
+        s.step(8)
+    for i, w in enumerate(wls):
+        compare_integer_moments(both.moments(i), alone[i].moments())
+        if precision == "fp64":
+            same_particles(both, i, alone[i], 0, w.L)
+        else:
+            for sp in range(3):
+                xa, va, pa = by_pid(*both.particles(sp, i))
+                xb, vb, pb = by_pid(*alone[i].particles(sp, 0))
+                assert np.array_equal(pa, pb)
+                if pa.size:
+                    d = np.abs(xa - xb)
+                    d[:, :2] = np.minimum(d[:, :2], np.array(w.L[:2]) - d[:, :2])
+                    assert d.max() <= 1e-5 * max(w.L)
+    for s in [both] + alone:
+        s.close()
