@@ -25,6 +25,7 @@
 
 #include "pic_internal.cuh"
 #include "pic_kernels.cuh"
+#include "tc_ptx.cuh"
 #include "pic_solver.cuh"
 
 namespace pic {
@@ -913,6 +914,197 @@ struct ClusterLaunch {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Exact coarse-grid solve by fast diagonalization (FP32). The level operator
+// 6 e - (sum of the six neighbours) with periodic x, y and zero Dirichlet
+// planes beyond the first and last unknown planes is the Kronecker sum
+// C_x + C_y + T_z of two periodic second-difference matrices and one Dirichlet
+// one, each diagonalized by a real orthonormal basis: Fourier cosines and sines
+// in x and y, sines in z. So A^-1 b = Q (Q^T b / (lx_p + ly_q + lz_r)), Q the
+// tensor product of the three bases, applied as small dense products along one
+// axis at a time: per unknown plane along x and y (k_spec_plane), per column
+// along z with the eigenvalue division between the two z products (k_spec_z).
+// ---------------------------------------------------------------------------
+struct SpecLv {
+  int nx, ny, P, Pp, pl;    // cells x, y; unknown planes (Pp: padded to a multiple of 4); plane size
+  // bases as columns, rows padded to 4 more floats than they hold (the shared-memory layout):
+  const float* qx;          // [nx][nx + 4]: qx[i][m], basis vector m at point i
+  const float* qxT;         // its transpose
+  const float* qy;          // [ny][ny + 4]
+  const float* qyT;
+  const float* qz;          // [Pp][Pp + 4] (zero beyond P)
+  const float* qzT;
+  const float* lx;          // [nx] eigenvalues
+  const float* ly;          // [ny]
+  const float* lz;          // [Pp] (1 beyond P)
+  int* timeout;             // set when a copy did not arrive in time (the solve then stops converging)
+};
+constexpr unsigned long long kSpecWaitNs = 1000000000ull;  // bound of every copy wait
+constexpr long long kSpecMaxUnknowns = 70000;  // largest level solved this way (32 x 32 x 63 unknowns and below)
+
+// Every thread waits for the phase; the block decides together (a wait that ran
+// out anywhere marks the timeout, lets the copies in flight land, and every
+// thread then leaves).
+__device__ __forceinline__ bool spec_wait(uint64_t* bar, uint32_t parity, int* timeout) {
+  const int late = tc::mbar_wait(bar, parity, kSpecWaitNs) ? 0 : 1;
+  if (__syncthreads_or(late)) {
+    if (threadIdx.x == 0 && timeout) atomicExch(timeout, 1);
+    tc::mbar_wait(bar, parity, kSpecWaitNs);
+    return false;
+  }
+  return true;
+}
+
+// C[M][N] = A[M][K] B[K][N] in shared memory, M and N multiples of 4, each
+// thread a 4x4 register tile (one float4 of B and four scalars of A per step).
+// Every leading dimension is a multiple of 4 and 4 more than the row it holds,
+// so the four A scalars of a step (rows 4 apart) fall in different banks.
+__device__ __forceinline__ void smem_gemm4(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M,
+                                           int N, int K) {
+  const int tn = N >> 2, tiles = (M >> 2) * tn;
+  for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+    const int m0 = (t / tn) << 2, n0 = (t % tn) << 2;
+    float acc[4][4] = {};
+    for (int k = 0; k < K; ++k) {
+      const float4 b = *reinterpret_cast<const float4*>(B + k * ldb + n0);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float a = A[(m0 + r) * lda + k];
+        acc[r][0] = fmaf(a, b.x, acc[r][0]);
+        acc[r][1] = fmaf(a, b.y, acc[r][1]);
+        acc[r][2] = fmaf(a, b.z, acc[r][2]);
+        acc[r][3] = fmaf(a, b.w, acc[r][3]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      *reinterpret_cast<float4*>(C + (m0 + r) * ldc + n0) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+  }
+}
+
+// one unknown plane per block: FWD out = Qy^T (in Qx), INV out = Qy (in Qx^T);
+// in and out may be the same array (a block reads its whole plane first). The
+// bases and the plane's rows arrive by bulk copies on one mbarrier.
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_spec_plane(SpecLv S, const float* in, float* out) {
+  pdl_enter();
+  extern __shared__ __align__(16) float sms[];
+  __shared__ __align__(8) uint64_t bar;
+  const int lx = S.nx + 4, ly = S.ny + 4;
+  float* qx = sms;                // [nx][nx + 4]
+  float* qy = qx + S.nx * lx;     // [ny][ny + 4]
+  float* a = qy + S.ny * ly;      // the plane, [ny][nx + 4]
+  float* t = a + S.ny * lx;       // after the x products
+  const long long base = (long long)blockIdx.x * S.pl;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::mbar_fence_init();
+    const uint32_t bx = (uint32_t)(sizeof(float) * S.nx * lx), by = (uint32_t)(sizeof(float) * S.ny * ly);
+    const uint32_t row = (uint32_t)(sizeof(float) * S.nx);
+    tc::mbar_arrive_expect_tx(&bar, bx + by + row * S.ny);
+    tc::bulk_g2s(qx, FWD ? S.qx : S.qxT, bx, &bar);
+    tc::bulk_g2s(qy, FWD ? S.qyT : S.qy, by, &bar);
+    for (int j = 0; j < S.ny; ++j) tc::bulk_g2s(a + j * lx, in + base + (long long)j * S.nx, row, &bar);
+  }
+  __syncthreads();
+  if (!spec_wait(&bar, 0, S.timeout)) return;
+  smem_gemm4(a, lx, qx, lx, t, lx, S.ny, S.nx, S.nx);  // along x
+  __syncthreads();
+  smem_gemm4(qy, ly, t, lx, a, lx, S.ny, S.nx, S.ny);  // along y
+  __syncthreads();
+  const int c4 = S.nx >> 2, l4 = lx >> 2;
+  for (int u = threadIdx.x; u < (S.pl >> 2); u += blockDim.x) {
+    const int r = u / c4;
+    reinterpret_cast<float4*>(out + base)[u] = reinterpret_cast<const float4*>(a)[r * l4 + (u - r * c4)];
+  }
+}
+
+// 32 columns (x, y points) per block along z: hat = Qz^T c, hat /= eigenvalue
+// sum, c = Qz hat (in place). Both bases and the columns' rows arrive by bulk
+// copies on one mbarrier.
+__global__ void __launch_bounds__(256) k_spec_z(SpecLv S, float* __restrict__ c) {
+  pdl_enter();
+  extern __shared__ __align__(16) float sms[];
+  __shared__ __align__(8) uint64_t bar;
+  const int Pp = S.Pp, lq = Pp + 4, lc = 36;
+  float* qT = sms;            // [Pp][Pp + 4]
+  float* q = qT + Pp * lq;    // [Pp][Pp + 4]
+  float* a = q + Pp * lq;     // [Pp][36]
+  float* h = a + Pp * lc;     // [Pp][36]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int col0 = blockIdx.x * 32, col = col0 + lane;
+  const uint32_t bq = (uint32_t)(sizeof(float) * Pp * lq);
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::mbar_fence_init();
+    tc::mbar_arrive_expect_tx(&bar, 2 * bq + (uint32_t)(128 * S.P));
+    tc::bulk_g2s(qT, S.qzT, bq, &bar);
+    tc::bulk_g2s(q, S.qz, bq, &bar);
+    for (int k = 0; k < S.P; ++k) tc::bulk_g2s(a + k * lc, c + (long long)k * S.pl + col0, 128, &bar);
+  }
+  for (int k = S.P + w; k < Pp; k += nw) a[k * lc + lane] = 0.f;  // padding rows (no copy writes them)
+  __syncthreads();
+  if (!spec_wait(&bar, 0, S.timeout)) return;
+  smem_gemm4(qT, lq, a, lc, h, lc, Pp, 32, Pp);
+  __syncthreads();
+  {
+    const int jj = col / S.nx;
+    const float lxy = S.lx[col - jj * S.nx] + S.ly[jj];
+    for (int r = w; r < Pp; r += nw) h[r * lc + lane] /= lxy + S.lz[r];
+  }
+  __syncthreads();
+  smem_gemm4(q, lq, h, lc, a, lc, Pp, 32, Pp);
+  __syncthreads();
+  for (int k = w; k < S.P; k += nw) c[(long long)k * S.pl + col] = a[k * lc + lane];
+}
+
+// Orthonormal eigenbasis of the periodic second difference on n points
+// (columns of q, row-major [i][m]) and its eigenvalues: the constant, cosine
+// and sine pairs, and for even n the alternating vector.
+static void periodic_basis(int n, std::vector<double>& q, std::vector<double>& lam) {
+  q.assign((size_t)n * n, 0.0);
+  lam.assign(n, 0.0);
+  int m = 0;
+  for (int i = 0; i < n; ++i) q[(size_t)i * n + m] = 1.0 / std::sqrt((double)n);
+  lam[m++] = 0.0;
+  for (int f = 1; 2 * f < n; ++f) {
+    const double th = 2.0 * kPi * f / n, l = 2.0 - 2.0 * std::cos(th);
+    for (int i = 0; i < n; ++i) {
+      q[(size_t)i * n + m] = std::sqrt(2.0 / n) * std::cos(th * i);
+      q[(size_t)i * n + m + 1] = std::sqrt(2.0 / n) * std::sin(th * i);
+    }
+    lam[m] = lam[m + 1] = l;
+    m += 2;
+  }
+  if (n % 2 == 0) {
+    for (int i = 0; i < n; ++i) q[(size_t)i * n + m] = (i % 2 ? -1.0 : 1.0) / std::sqrt((double)n);
+    lam[m++] = 4.0;
+  }
+}
+
+// Dirichlet second difference on P points (zero beyond both ends): sines
+static void dirichlet_basis(int P, std::vector<double>& q, std::vector<double>& lam) {
+  q.assign((size_t)P * P, 0.0);
+  lam.assign(P, 0.0);
+  for (int r = 0; r < P; ++r) {
+    const double th = kPi * (r + 1) / (P + 1);
+    lam[r] = 2.0 - 2.0 * std::cos(th);
+    for (int k = 0; k < P; ++k) q[(size_t)k * P + r] = std::sqrt(2.0 / (P + 1)) * std::sin(th * (k + 1));
+  }
+}
+
+// largest |Q^T Q - I| entry (the bases are orthonormal to rounding)
+static double ortho_err(const std::vector<double>& q, int n) {
+  double e = 0.0;
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      double d = 0.0;
+      for (int i = 0; i < n; ++i) d += q[(size_t)i * n + a] * q[(size_t)i * n + b];
+      e = std::max(e, std::fabs(d - (a == b ? 1.0 : 0.0)));
+    }
+  return e;
+}
+
 template <class T>
 cudaError_t Mg<T>::init(const std::vector<MgLevel>& plan) {
   levels = plan;
@@ -939,11 +1131,80 @@ cudaError_t Mg<T>::init(const std::vector<MgLevel>& plan) {
     if ((err = cudaMalloc(&Ainv, sizeof(T) * invT.size()))) return err;
     if ((err = cudaMemcpy(Ainv, invT.data(), sizeof(T) * invT.size(), cudaMemcpyHostToDevice))) return err;
   }
-  // FP32: the deepest levels whose e, b, r fit in the shared memory of a
-  // cluster's blocks run in k_coarse_cluster (at least two levels, never level 0)
+  // FP32: the coarse-grid correction is an exact fast-diagonalization solve at
+  // the first level below the finest that allows it
   fuse_from = -1;
   fuse_smem = 0;
+  spectral_at = -1;
   if constexpr (std::is_same<T, float>::value) {
+    for (int l = 1; l < (int)plan.size() && rb_ok; ++l) {
+      const MgLevel& M = plan[l];
+      const int P = M.nz - 1;
+      // the transforms cost nu (nx + ny + P) products: deep enough that this
+      // stays below the per-level kernels it replaces
+      if (M.nu > kSpecMaxUnknowns || M.nx > 64 || M.ny > 64 || M.nx % 4 || M.ny % 4 || (M.nx * M.ny) % 32 || P < 1 ||
+          P > 128)
+        continue;
+      std::vector<double> qx, lx, qy, ly, qz, lz;
+      periodic_basis(M.nx, qx, lx);
+      periodic_basis(M.ny, qy, ly);
+      dirichlet_basis(P, qz, lz);
+      if (ortho_err(qx, M.nx) > 1e-10 || ortho_err(qy, M.ny) > 1e-10 || ortho_err(qz, P) > 1e-10) break;
+      const int Pp = (P + 3) & ~3;
+      // rows padded to 4 more floats (the kernels' shared-memory layout, one bulk copy each)
+      const int lxp = M.nx + 4, lyp = M.ny + 4, lzp = Pp + 4;
+      const size_t nxx = (size_t)M.nx * lxp, nyy = (size_t)M.ny * lyp, npp = (size_t)Pp * lzp;
+      std::vector<float> h(2 * nxx + 2 * nyy + 2 * npp + M.nx + M.ny + Pp + 4, 0.f);
+      float* hx = h.data();
+      float* hxT = hx + nxx;
+      float* hy = hxT + nxx;
+      float* hyT = hy + nyy;
+      float* hz = hyT + nyy;
+      float* hzT = hz + npp;
+      float* hlx = hzT + npp;
+      float* hly = hlx + M.nx;
+      float* hlz = hly + M.ny;
+      for (int i = 0; i < M.nx; ++i)
+        for (int m = 0; m < M.nx; ++m) {
+          hx[(size_t)i * lxp + m] = (float)qx[(size_t)i * M.nx + m];
+          hxT[(size_t)m * lxp + i] = (float)qx[(size_t)i * M.nx + m];
+        }
+      for (int j = 0; j < M.ny; ++j)
+        for (int m = 0; m < M.ny; ++m) {
+          hy[(size_t)j * lyp + m] = (float)qy[(size_t)j * M.ny + m];
+          hyT[(size_t)m * lyp + j] = (float)qy[(size_t)j * M.ny + m];
+        }
+      for (int k = 0; k < P; ++k)
+        for (int r = 0; r < P; ++r) {
+          hz[(size_t)k * lzp + r] = (float)qz[(size_t)k * P + r];
+          hzT[(size_t)r * lzp + k] = (float)qz[(size_t)k * P + r];
+        }
+      for (int i = 0; i < M.nx; ++i) hlx[i] = (float)lx[i];
+      for (int j = 0; j < M.ny; ++j) hly[j] = (float)ly[j];
+      for (int r = 0; r < Pp; ++r) hlz[r] = r < P ? (float)lz[r] : 1.f;
+      if ((err = cudaMalloc(&spec_mem, sizeof(float) * h.size()))) return err;
+      if ((err = cudaMemcpy(spec_mem, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice))) return err;
+      spec_smem_plane = sizeof(float) * (nxx + nyy + 2 * (size_t)M.ny * lxp);
+      spec_smem_z = sizeof(float) * (2 * npp + 72 * (size_t)Pp);
+      // the attribute is the kernel's, shared by every solver of the process:
+      // set to what the largest admitted level needs (64 x 64, 128 planes)
+      const int plane_max = (int)sizeof(float) * (4 * 64 * 68);
+      const int z_max = (int)sizeof(float) * (2 * 128 * 132 + 72 * 128);
+      bool ok = cudaFuncSetAttribute(k_spec_plane<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, plane_max) ==
+                    cudaSuccess &&
+                cudaFuncSetAttribute(k_spec_plane<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, plane_max) ==
+                    cudaSuccess &&
+                cudaFuncSetAttribute(k_spec_z, cudaFuncAttributeMaxDynamicSharedMemorySize, z_max) == cudaSuccess;
+      cudaGetLastError();
+      if (ok) spectral_at = l;
+      break;
+    }
+  }
+  // FP32 without that solve: the deepest levels whose e, b, r fit in the shared
+  // memory of a cluster's blocks run in k_coarse_cluster (at least two levels,
+  // never level 0)
+  if constexpr (std::is_same<T, float>::value) {
+    if (spectral_at > 0) return cudaSuccess;
     const size_t cap = 200 * 1024;
     const int nl_ = (int)plan.size();
     int best = -1;
@@ -965,7 +1226,9 @@ cudaError_t Mg<T>::init(const std::vector<MgLevel>& plan) {
     }
     if (rb_ok && best > 0) {
       const size_t bytes = sizeof(float) * best_floats;
-      bool ok = cudaFuncSetAttribute(k_coarse_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+      // the attribute is the kernel's, shared by every solver of the process: the
+      // cap of the selection above, so that every instance's launch fits
+      bool ok = cudaFuncSetAttribute(k_coarse_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap) ==
                 cudaSuccess;
       if (ok) {  // can a cluster of this size be resident at all?
         cudaLaunchAttribute at[1];
@@ -1002,6 +1265,9 @@ void Mg<T>::release() {
   r.clear();
   if (Ainv) cudaFree(Ainv);
   Ainv = nullptr;
+  if (spec_mem) cudaFree(spec_mem);
+  spec_mem = nullptr;
+  spectral_at = -1;
 }
 
 // z = M^-1 rhs (one V(1,1) cycle from zero); rhs and z live at level 0 outside
@@ -1022,7 +1288,9 @@ bool Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s, double* part, SolveCtl* c
     B[l] = l == 0 ? const_cast<T*>(rhs) : b[l];
   }
   const int ff = fuse_from;  // levels ff..nl-1 run in one cluster (FP32 only), -1: none
-  for (int l = 0; l < (ff > 0 ? ff : nl - 1); ++l) {
+  const int sp = spectral_at;  // level solved exactly (FP32 only), -1: none
+  const int bottom = sp > 0 ? sp : (ff > 0 ? ff : nl - 1);
+  for (int l = 0; l < bottom; ++l) {
     const Lv L = lv_of(levels[l]);
     const Lv C = lv_of(levels[l + 1]);
     if (l == 0 && split0) {
@@ -1036,7 +1304,31 @@ bool Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s, double* part, SolveCtl* c
     SOLVER_LAUNCH(g3(C, C.nx), kB3, 0, s, k_restrict<T>)(L, C, r[l], B[l + 1]);
   }
   if constexpr (std::is_same<T, float>::value) {
-    if (ff > 0) {
+    if (sp > 0) {
+      const MgLevel& M = levels[sp];
+      SpecLv S;
+      S.nx = M.nx;
+      S.ny = M.ny;
+      S.P = M.nz - 1;
+      S.Pp = (S.P + 3) & ~3;
+      S.pl = M.nx * M.ny;
+      const size_t nxx = (size_t)M.nx * (M.nx + 4), nyy = (size_t)M.ny * (M.ny + 4), npp = (size_t)S.Pp * (S.Pp + 4);
+      S.timeout = ctl ? &ctl->spec_timeout : nullptr;
+      S.qx = spec_mem;
+      S.qxT = S.qx + nxx;
+      S.qy = S.qxT + nxx;
+      S.qyT = S.qy + nyy;
+      S.qz = S.qyT + nyy;
+      S.qzT = S.qz + npp;
+      S.lx = S.qzT + npp;
+      S.ly = S.lx + M.nx;
+      S.lz = S.ly + M.ny;
+      // e = A^-1 b at this level: forward transforms into e, per-column solve, inverse transforms
+      SOLVER_LAUNCH(S.P, 256, spec_smem_plane, s, k_spec_plane<true>)(S, B[sp], E[sp]);
+      SOLVER_LAUNCH((S.pl + 31) / 32, 256, spec_smem_z, s, k_spec_z)(S, E[sp]);
+      SOLVER_LAUNCH(S.P, 256, spec_smem_plane, s, k_spec_plane<false>)(S, E[sp], E[sp]);
+    }
+    if (sp <= 0 && ff > 0) {
       ClusterArgs ca{};
       ca.nlev = nl - ff;
       int off = 0;
@@ -1069,7 +1361,7 @@ bool Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s, double* part, SolveCtl* c
       ClusterLaunch<decltype(&k_coarse_cluster)>{&k_coarse_cluster, fuse_smem, s}(ca);
     }
   }
-  if (ff <= 0) {
+  if (sp <= 0 && ff <= 0) {
     const Lv C = lv_of(levels[nl - 1]);
     if (coarse_dense) {
       const int cg = (int)std::min<long long>((C.nu * 32 + kSB - 1) / kSB, 4096);
@@ -1087,7 +1379,7 @@ bool Mg<T>::vcycle(const T* rhs, T* z, cudaStream_t s, double* part, SolveCtl* c
       SOLVER_LAUNCH(g3(C, C.nx / 2), kB3, 0, s, k_smooth<T>)(C, E[nl - 1], B[nl - 1], 0);
     }
   }
-  for (int l = (ff > 0 ? ff : nl - 1) - 1; l >= 0; --l) {
+  for (int l = bottom - 1; l >= 0; --l) {
     const Lv L = lv_of(levels[l]);
     const Lv C = lv_of(levels[l + 1]);
     if (l == 0 && split0) {
@@ -1926,6 +2218,7 @@ SolveResult Solver::result_read() const {
   r.iters = host_ctl->it_total;
   r.resid_rel = host_ctl->resid_rel;
   r.converged = host_ctl->converged != 0;
+  r.timeout = host_ctl->spec_timeout != 0;
   return r;
 }
 

@@ -1538,6 +1538,11 @@ pic_status pic_step(pic_handle* h, int32_t nsteps) {
     if (nsteps > 0) {
       I->last = I->solver.result_read();
       if (!I->last.converged) h->sticky |= 1;
+      if (I->last.timeout) {
+        // reported once (the flag is cleared), as for the device error flags
+        CK(h, cudaMemsetAsync(&I->solver.ctl->spec_timeout, 0, sizeof(int), h->stream));
+        return fail(h, PIC_ETIMEOUT, "instance solve: a copy of the coarse-grid solve timed out");
+      }
     }
     if (I->host_cnt) {
       const int e = I->host_cnt->error;
@@ -1763,6 +1768,10 @@ pic_status pic_solve(pic_handle* h, int32_t inst, const double* rho, double* phi
   if (e != cudaSuccess) return fail(h, PIC_ECUDA, "solve failed: %s", cudaGetErrorString(e));
   if (iters) *iters = r.iters;
   if (resid_rel) *resid_rel = r.resid_rel;
+  if (r.timeout) {
+    CK(h, cudaMemset(&I->solver.ctl->spec_timeout, 0, sizeof(int)));
+    return fail(h, PIC_ETIMEOUT, "solve: a copy of the coarse-grid solve timed out");
+  }
   if (!r.converged) return fail(h, PIC_ENOCONV, "solve did not reach cg_rtol (%g after %d iterations)", r.resid_rel, r.iters);
   return PIC_OK;
 }

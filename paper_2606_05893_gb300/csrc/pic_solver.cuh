@@ -21,12 +21,14 @@ struct SolveCtl {
   unsigned ticket;  // blocks finished in the current grid-wide sum (0 between launches)
   int ax_valid;     // Solver::ax holds A x for the current x
   int stopped;      // the last residual ended the outer loop
+  int spec_timeout; // a copy of the exact coarse solve did not arrive in time (sticky until reported)
 };
 
 struct SolveResult {
   int iters;
   double resid_rel;
   bool converged;
+  bool timeout;  // SolveCtl::spec_timeout
 };
 
 std::vector<MgLevel> mg_plan(int nx, int ny, int nz);
@@ -42,6 +44,12 @@ struct Mg {
   int fuse_from = -1;    // levels fuse_from..end run in one thread-block cluster (FP32), -1: none
   size_t fuse_smem = 0;  // its dynamic shared memory per block
   bool split0 = false;   // finest level in the colour-split layout (FP32, red-black, two levels or more)
+  // FP32: the first level below the finest that fast diagonalization solves
+  // exactly (x, y at most 64 and multiples of 4, at most 128 unknown planes);
+  // the V-cycle stops there. -1: none (the deeper levels as above)
+  int spectral_at = -1;
+  float* spec_mem = nullptr;  // its bases and eigenvalues
+  size_t spec_smem_plane = 0, spec_smem_z = 0;
   cudaError_t init(const std::vector<MgLevel>& plan);
   void release();
   // part, ctl given: the last half sweep also forms the PCG product r.z (returns true then)

@@ -92,10 +92,15 @@ def test_poisson_solve_matches_oracle(pkg, shape):
     sim.close()
 
 
-def test_poisson_solve_mixed_precision(pkg):
-    nx, ny, nz = 32, 32, 64
+# The mixed solver's multigrid stops at the first coarse level of at most 70 000
+# unknowns whose sides allow the exact fast-diagonalization solve: 16x16x31
+# (32x32x64), 32x16x63 (unequal sides), 24x24x47; 10x10x19 (sides not multiples
+# of 4) keeps the deeper levels and the cluster kernel.
+@pytest.mark.parametrize("shape", [(32, 32, 64), (64, 32, 128), (48, 48, 96), (20, 20, 40)])
+def test_poisson_solve_mixed_precision(pkg, shape):
+    nx, ny, nz = shape
     wl = bare(nx=nx, ny=ny, nz=nz, h=2.5e-9, phi_c=0.0, phi_a=600.0)
-    rng = np.random.default_rng(4)
+    rng = np.random.default_rng(4 + nx)
     rho = rng.standard_normal((nz + 1, ny, nx)) * 3e6
     sim = pkg.Simulation(wl, precision=pkg.PIC_MIXED, cg_rtol=1e-12, cg_maxit=20000, preload=False)
     phi_g, it, rel = sim.solve(rho)
