@@ -470,6 +470,33 @@ def run_gpu_ensemble(args, rank, ws, local):
     return info, agg
 
 
+def run_c4_leg(args, local, peak, peak_kind):
+    """The batched ensemble (48 instances of uneven grids and populations in one
+    handle, autotuned, each ensemble step one recorded graph launch) as an extra
+    leg of the default run: a shorter tuning window and timed window than
+    `--workload c4` (one replica, this rank's GPU)."""
+    import copy
+    a2 = copy.copy(args)
+    a2.steps, a2.warmup, a2.profile_steps, a2.e2e_steps = args.c4_steps, 3, 2, 2
+    a2.tune_window = 20
+    t0 = time.perf_counter()
+    info, a = run_gpu_ensemble(a2, 0, 1, local)
+    pi = sorted(info["per_inst"])
+    achieved = BYTES_PER_PARTICLE["mixed"] * info["push_e_n"] / (info["push_e_ms"] * 1e-3) / 1e9
+    return {"workload": WORKLOADS["c4"][0], "instances": len(info["sizes"]), "macroparticles": info["n_total"],
+            "steps": a2.steps, "warmup": a2.warmup, "value": a["pushes"] / (a["ms"] * 1e-3), "unit": UNIT,
+            "ms_per_step": a["ms"] / a2.steps,
+            "e2e": {"value": a["e2e_pushes"] / a["e2e_s"], "unit": UNIT},
+            "per_instance_particle_steps_s": {"min": pi[0], "median": pi[len(pi) // 2], "max": pi[-1]},
+            "launch_ops_per_step": info["launch_ops"] / a2.steps, "kernels_per_step": info["launches"] / a2.steps,
+            "roofline": {"bound": "hbm", "kernel": "k_push (electrons, all instances, isolated launches)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "bytes_per_particle": BYTES_PER_PARTICLE["mixed"], "traffic": None},
+            "autotune": {"chosen_interval_blocks_per_sm": info["chosen"], "window": a2.tune_window,
+                         "seconds": round(info["tune_s"], 1)},
+            "leg_s": round(time.perf_counter() - t0, 1)}
+
+
 def run_c3_leg(args, peak, peak_kind):
     """The largest single-GPU workload: 256x256x512 cells of 1.25 nm (the same box),
     5e7 macroparticles, mixed precision; device-timed steps and the electron push's
@@ -741,6 +768,9 @@ def main():
     ap.add_argument("--no-c3", dest="c3", action="store_false",
                     help="skip the 256x256x512 / 5e7 leg (on by default with the c2 workload)")
     ap.add_argument("--c3-steps", type=int, default=10)
+    ap.add_argument("--no-c4", dest="c4", action="store_false",
+                    help="skip the batched-ensemble leg of the default run")
+    ap.add_argument("--c4-steps", type=int, default=10)
     ap.add_argument("--c3-n-preload", type=int, default=50_000_000)
     ap.add_argument("--no-c5", dest="c5", action="store_false",
                     help="skip the learned warm start leg (on by default with the c2 workload)")
@@ -839,6 +869,8 @@ def main():
         line["steady_state"] = r["steady"]
     if args.c3 and args.workload == "c2":
         line["c3_mixed"] = run_c3_leg(args, peak, peak_kind)
+    if args.c4 and args.workload == "c2":
+        line["c4_ensemble"] = run_c4_leg(args, dist_env()[2], peak, peak_kind)
     if args.c5 and args.workload == "c2":
         ptf, pkind = peak_tflops()
         line["learned_warm_start"] = run_warm_start_leg(args, ptf, pkind)
