@@ -179,10 +179,43 @@ __device__ __forceinline__ float m2log_u(uint32_t a, uint32_t b) {
   return u < 0.5 ? -2.f * logf((float)u) : -2.f * log1pf(-(float)(1.0 - u));
 }
 
+// This step's counts from the carry accumulators (FP64, the host formula:
+// acc += mu; n = floor(acc); acc -= n): first particle of each source, its
+// offset among its species' new particles, and the total.
+struct InjCounts {
+  long long first[kMaxSources + 1];
+  long long offset[kMaxSources];
+  long long add[kMaxSpecies];
+  double acc[kMaxSources];
+};
+__device__ __forceinline__ void inject_counts(const InjectPlan& P, InjCounts& c) {
+  long long total = 0;
+  for (int s = 0; s < kMaxSpecies; ++s) c.add[s] = 0;
+  for (int q = 0; q < P.nsrc; ++q) {
+    double acc = P.acc[q] + P.mu[q];
+    const double nf = floor(acc);
+    acc -= nf;
+    c.acc[q] = acc;
+    const long long n = (long long)nf;
+    c.first[q] = total;
+    c.offset[q] = c.add[P.species[q]];
+    c.add[P.species[q]] += n;
+    total += n;
+  }
+  c.first[P.nsrc] = total;
+}
+
+// a1 in one launch: every block forms the step's counts from the carries (the
+// same FP64 arithmetic in each), places its share of the new particles, and the
+// last block to finish commits the step (carries, store counts, next pid).
 template <class S>
 __global__ void k_inject(InjectArgs<S> a) {
+  __shared__ InjCounts sc;
+  __shared__ bool s_last;
   const InjectPlan& P = *a.plan;
-  const long long total = P.total;
+  if (threadIdx.x == 0) inject_counts(P, sc);
+  __syncthreads();
+  const long long total = sc.first[P.nsrc];
   const uint32_t step = a.cnt->step;
   // particle t on block t mod G (thread t / G): a step injects tens to hundreds of
   // particles, each with FP64 transcendentals, and one SM's narrow FP64 pipe
@@ -191,12 +224,12 @@ __global__ void k_inject(InjectArgs<S> a) {
        t += (long long)gridDim.x * blockDim.x) {
     // source of this particle
     int q = 0;
-    while (q + 1 < a.nsrc && t >= P.src_first[q + 1]) ++q;
+    while (q + 1 < a.nsrc && t >= sc.first[q + 1]) ++q;
     const InjSrc& s = a.src[q];
-    const long long kth = t - P.src_first[q];
+    const long long kth = t - sc.first[q];
     const uint32_t pid = a.cnt->next_pid + (uint32_t)t;
     const unsigned long long base = a.cnt->n[a.cur[s.species]][s.species];
-    const unsigned long long slot = base + P.species_offset[q] + kth;
+    const unsigned long long slot = base + sc.offset[q] + kth;
     if (slot >= (unsigned long long)a.cap[s.species]) {
       atomicOr(&a.cnt->error, ERR_CAPACITY);
       continue;
@@ -247,41 +280,25 @@ __global__ void k_inject(InjectArgs<S> a) {
       else if (a.nd.qw_h3[s.species] != 0.0) deposit_one(a.g, p, a.nd.rho32, a.nd.rho64, a.nd.qw_h3[s.species]);
     }
   }
-}
-
-// a1 counts of this step from the carry accumulators (FP64, the host formula)
-__global__ void k_inject_plan(InjectPlan* P, int nsp) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  long long total = 0;
-  long long per_species[kMaxSpecies] = {0};
-  for (int q = 0; q < P->nsrc; ++q) {
-    double acc = P->acc[q] + P->mu[q];
-    const double nf = floor(acc);
-    acc -= nf;
-    P->acc[q] = acc;
-    const long long n = (long long)nf;
-    P->src_first[q] = total;
-    P->species_offset[q] = per_species[P->species[q]];
-    per_species[P->species[q]] += n;
-    total += n;
+  // the last block: every block's reads of the counters and carries are done
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&a.plan->ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  InjectPlan& W = *a.plan;
+  for (int q = 0; q < W.nsrc; ++q) W.acc[q] = sc.acc[q];
+  W.ticket = 0u;
+  if (total == 0) return;
+  for (int sp = 0; sp < a.nsp; ++sp) {
+    if (sc.add[sp] == 0) continue;
+    unsigned long long nn = a.cnt->n[a.cur[sp]][sp] + sc.add[sp];
+    if (nn > (unsigned long long)a.cap[sp]) nn = a.cap[sp];
+    a.cnt->injected[sp] += nn - a.cnt->n[a.cur[sp]][sp];
+    a.cnt->n[a.cur[sp]][sp] = nn;
   }
-  P->src_first[P->nsrc] = total;
-  P->total = total;
-  for (int s = 0; s < nsp && s < kMaxSpecies; ++s) P->add[s] = per_species[s];
-}
-
-__global__ void k_inject_commit(DevCounters* cnt, InjectCommit c) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const InjectPlan& P = *c.plan;
-  if (P.total == 0) return;
-  for (int s = 0; s < c.nsp; ++s) {
-    if (P.add[s] == 0) continue;
-    unsigned long long nn = cnt->n[c.cur[s]][s] + P.add[s];
-    if (nn > (unsigned long long)c.cap[s]) nn = c.cap[s];
-    cnt->injected[s] += nn - cnt->n[c.cur[s]][s];
-    cnt->n[c.cur[s]][s] = nn;
-  }
-  cnt->next_pid += (unsigned int)P.total;
+  a.cnt->next_pid += (unsigned int)total;
 }
 
 // ---------------------------------------------------------------------------
@@ -575,11 +592,12 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
 // candidate with exactly that many smaller keys. Keys are unique (they carry
 // the pid), so the two searches below give the same victim.
 // Few events and candidates (events x candidates <= kScanWork, the usual step):
-// one warp per event scans the flat candidate array (coalesced, no chain of
-// dependent loads), gathers its cell's keys into shared memory and counts
-// ranks there; a cell with more than kRankCand candidates falls back to the
-// list walk. Otherwise one thread per event walks its cell's candidate list by
-// repeated minimum selection (the flat scan would cost events x candidates).
+// one block per event scans the flat candidate array (its eight warps take
+// interleaved chunks, so the scan is a few rounds of coalesced loads, not a
+// chain of dependent ones), gathers its cell's keys into shared memory and
+// counts ranks there; a cell with more than kRankCand candidates falls back to
+// the list walk. Otherwise one thread per event walks its cell's candidate list
+// by repeated minimum selection (the flat scan would cost events x candidates).
 constexpr int kRankCand = 256;
 constexpr int kRankWarps = 8;
 constexpr unsigned long long kScanWork = 1ull << 22;
@@ -629,8 +647,9 @@ __device__ __forceinline__ void finish_event(const ResolveArgs& a, long long e, 
 }
 
 __global__ void __launch_bounds__(kRankWarps * 32) k_resolve_rank(ResolveArgs a) {
-  __shared__ unsigned long long sk[kRankWarps][kRankCand];
-  __shared__ int si[kRankWarps][kRankCand];
+  __shared__ unsigned long long sk[kRankCand];
+  __shared__ int si[kRankCand];
+  __shared__ int s_m, s_victim;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned int ne = min(a.cnt->n_events, (unsigned int)a.ev_cap);
   const unsigned int nc = min(a.cnt->n_cands, (unsigned int)a.cand_cap);
@@ -643,48 +662,53 @@ __global__ void __launch_bounds__(kRankWarps * 32) k_resolve_rank(ResolveArgs a)
     return;
   }
   const unsigned lt = (1u << lane) - 1u;
-  // event e on block e mod G, warp e / G: tens of events each scan the candidate
-  // array, and spread one per block they do so on as many SMs
-  for (long long e = blockIdx.x + (long long)gridDim.x * w; e < ne; e += (long long)gridDim.x * kRankWarps) {
+  // event e on block e mod G: tens of events, each scanned by a whole block
+  for (long long e = blockIdx.x; e < ne; e += gridDim.x) {
     const uint32_t cell = a.ev[e].cell, pid = a.ev[e].pid;
-    const int r = event_rank(a, cell, pid);
-    // this cell's candidates, four chunks of 32 per round (their loads overlap)
-    int m = 0;
-    for (unsigned base = 0; base < nc; base += 128) {
-      bool match[4];
+    if (threadIdx.x == 0) {
+      s_m = 0;
+      s_victim = -1;
+    }
+    __syncthreads();
+    // this cell's candidates: warp w takes chunks w, w + 8, ... of 256 (eight loads per lane in flight)
+    for (unsigned base = (unsigned)w * 256u; base < nc; base += 256u * kRankWarps) {
+      bool match[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < 8; ++q) {
         const unsigned c = base + 32u * q + lane;
         match[q] = c < nc && a.cand_cell[c] == cell;
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < 8; ++q) {
         const unsigned bal = __ballot_sync(0xffffffffu, match[q]);
-        const int pos = m + __popc(bal & lt);
+        if (!bal) continue;
+        int at = 0;
+        if (lane == 0) at = atomicAdd(&s_m, __popc(bal));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        const int pos = at + __popc(bal & lt);
         if (match[q] && pos < kRankCand) {
           const unsigned c = base + 32u * q + lane;
-          sk[w][pos] = a.cand[c].key;
-          si[w][pos] = (int)c;
+          sk[pos] = a.cand[c].key;
+          si[pos] = (int)c;
         }
-        m += __popc(bal);
       }
     }
-    __syncwarp();
-    int victim = -1;
+    __syncthreads();
+    const int m = s_m;
     if (m <= kRankCand) {
-      for (int q = lane; q < m; q += 32) {
-        const unsigned long long kq = sk[w][q];
+      const int r = event_rank(a, cell, pid);  // every thread the same
+      for (int q = threadIdx.x; q < m; q += blockDim.x) {
+        const unsigned long long kq = sk[q];
         int below = 0;
-        for (int t = 0; t < m; ++t) below += sk[w][t] < kq ? 1 : 0;
-        if (below == r) victim = si[w][q];
+        for (int t = 0; t < m; ++t) below += sk[t] < kq ? 1 : 0;
+        if (below == r) s_victim = si[q];  // keys are unique: one thread at most
       }
-      victim = __reduce_max_sync(0xffffffffu, victim);  // one lane at most found it
-    } else {
-      if (lane == 0) victim = victim_by_list(a, cell, r);
-      victim = __shfl_sync(0xffffffffu, victim, 0);
+    } else if (threadIdx.x == 0) {
+      s_victim = victim_by_list(a, cell, event_rank(a, cell, pid));
     }
-    if (lane == 0) finish_event(a, e, pid, victim);
-    __syncwarp();  // the slice of sk / si is reused by the next event
+    __syncthreads();
+    if (threadIdx.x == 0) finish_event(a, e, pid, s_victim);
+    __syncthreads();  // s_m, s_victim, sk, si are reused by the next event
   }
 }
 
@@ -820,12 +844,6 @@ void launch_push(const PushArgs<S>& a, int role, bool mcc, int grid, cudaStream_
     PIC_LAUNCH(grid, 256, 0, st, k_push<S, true, false, false>)(a);
 }
 
-void launch_inject_commit(DevCounters* cnt, const InjectCommit& c, cudaStream_t st) {
-  PIC_LAUNCH(1, 1, 0, st, k_inject_commit)(cnt, c);
-}
-void launch_inject_plan(InjectPlan* plan, int nsp, cudaStream_t st) {
-  PIC_LAUNCH(1, 32, 0, st, k_inject_plan)(plan, nsp);
-}
 
 void launch_resolve_rank(const ResolveArgs& a, int grid, cudaStream_t st) {
   PIC_LAUNCH(grid, kRankWarps * 32, 0, st, k_resolve_rank)(a);

@@ -776,19 +776,15 @@ pic_status step_instance(pic_handle* h, Instance* I) {
   T.begin(PIC_PH_INJECT, st);
   if (!I->sources.empty()) {
     InjectArgs<S> a{};
-    InjectCommit cm{};
     a.g = g;
     a.cnt = I->cnt;
     a.key = key;
     a.plan = I->plan;
-    cm.nsp = I->nsp;
-    cm.plan = I->plan;
+    a.nsp = I->nsp;
     for (int s = 0; s < I->nsp; ++s) {
       a.st[s] = store_of<S>(I, s, I->cur[s]);
       a.cur[s] = I->cur[s];
       a.cap[s] = I->cap[s];
-      cm.cur[s] = I->cur[s];
-      cm.cap[s] = I->cap[s];
     }
     int q = 0;
     for (auto& src : I->sources) {
@@ -803,9 +799,7 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     a.nsrc = q;
     a.nd = next_deposit_of(I, I->next_valid);
     for (int s = 0; s < I->nsp; ++s) a.role[s] = I->species[s].role == PIC_NEUTRAL ? ROLE_NEUTRAL : ROLE_ELECTRON;
-    launch_inject_plan(I->plan, I->nsp, st);
     launch_inject<S>(a, 2 * sm_count(), st);
-    launch_inject_commit(I->cnt, cm, st);
     I->plan_used = true;
   }
   T.end(st);

@@ -202,10 +202,7 @@ struct InjectPlan {
   int species[kMaxSources];
   double mu[kMaxSources];   // expected macroparticles per step
   double acc[kMaxSources];  // carry
-  long long total;
-  long long src_first[kMaxSources + 1];
-  long long species_offset[kMaxSources];
-  long long add[kMaxSpecies];
+  unsigned int ticket;       // blocks of the injection launch finished (0 between launches)
 };
 
 // Host-side count of kernel launches issued by the library (all handles).

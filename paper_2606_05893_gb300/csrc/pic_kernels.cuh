@@ -526,17 +526,11 @@ struct InjectArgs {
   long long cap[kMaxSpecies];
   int nsrc;
   InjSrc src[kMaxSources];
-  const InjectPlan* plan;  // this step's counts (device)
+  InjectPlan* plan;  // sources and carries (device); the launch's last block advances the carries
   uint2 key;
   NextDeposit nd;
   int role[kMaxSpecies];
-};
-
-struct InjectCommit {
   int nsp;
-  int cur[kMaxSpecies];
-  long long cap[kMaxSpecies];
-  const InjectPlan* plan;
 };
 
 // Surface-coupling output: ions absorbed at the cathode (n == nullptr: not
@@ -642,8 +636,6 @@ struct DepositArgs {
 // ---------------------------------------------------------------------------
 template <class S>
 void launch_inject(const InjectArgs<S>& a, int grid, cudaStream_t st);
-void launch_inject_commit(DevCounters* cnt, const InjectCommit& c, cudaStream_t st);
-void launch_inject_plan(InjectPlan* plan, int nsp, cudaStream_t st);
 void launch_step_end(DevCounters* cnt, const Circuit& c, cudaStream_t st);
 template <class S>
 void launch_push(const PushArgs<S>& a, int role, bool mcc, int grid, cudaStream_t st);
