@@ -4,7 +4,7 @@
 //   a5+a6+a7+a8 (+a10)   k_push<Store>: field gather at x^n, leapfrog kick/drift,
 //                        absorption at the electrodes, Monte Carlo collisions
 //                        (Eq. 4), warp-aggregated compaction into the other buffer
-//   a9 ionization and    k_resolve_rank / k_resolve_apply / k_resolve_cleanup
+//   a9 ionization and    k_resolve_rank / k_resolve_apply (with the commit and the list-head reset)
 //      charge exchange
 //
 // Collision test (Eq. 4): P = 1 - exp(-u dt sum_c n_c sigma_c(E)), decided with the
@@ -712,6 +712,28 @@ __global__ void __launch_bounds__(kRankWarps * 32) k_resolve_rank(ResolveArgs a)
   }
 }
 
+// Counters of the resolved step: outcomes, the stores' new lengths, pids.
+__device__ void resolve_commit(DevCounters* cnt, const ResolveCommit& c) {
+  const unsigned int ne = min(cnt->n_events, (unsigned int)c.ev_cap);
+  const unsigned int ns = cnt->n_success;
+  const unsigned int ncx = cnt->n_success_cx;
+  const unsigned int nion = ns - ncx;
+  cnt->n_ion += nion;
+  cnt->n_cx += ncx;
+  cnt->n_supp += ne - ns;
+  if (c.e_sp >= 0) {
+    const unsigned long long a = cnt->n[c.e_out][c.e_sp] + nion;
+    cnt->n[c.e_out][c.e_sp] = a > (unsigned long long)c.e_cap ? c.e_cap : a;
+  }
+  const unsigned long long b = cnt->n[c.i_out][c.i_sp] + ns;
+  cnt->n[c.i_out][c.i_sp] = b > (unsigned long long)c.i_cap ? c.i_cap : b;
+  const unsigned long long d = cnt->n[c.n_out][c.n_sp] + ncx;
+  cnt->n[c.n_out][c.n_sp] = d > (unsigned long long)c.n_cap ? c.n_cap : d;
+  cnt->n_tomb[c.n_sp] = ns;
+  cnt->n_tomb[c.i_sp] = ncx;
+  cnt->next_pid += nion;
+}
+
 // Successful events in apply order: ionizations (rank r < nion) then charge
 // exchanges. Every victim neutral becomes an ion (slot ni_out + r). An
 // ionization scales its primary electron and appends a secondary (pid and
@@ -793,38 +815,27 @@ __global__ void k_resolve_apply(ApplyArgs<S> a) {
       a.log[3 * r + 2] = spid;
     }
   }
-}
-
-__global__ void k_resolve_commit(DevCounters* cnt, ResolveCommit c) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const unsigned int ne = min(cnt->n_events, (unsigned int)c.ev_cap);
-  const unsigned int ns = cnt->n_success;
-  const unsigned int ncx = cnt->n_success_cx;
-  const unsigned int nion = ns - ncx;
-  cnt->n_ion += nion;
-  cnt->n_cx += ncx;
-  cnt->n_supp += ne - ns;
-  if (c.e_sp >= 0) {
-    const unsigned long long a = cnt->n[c.e_out][c.e_sp] + nion;
-    cnt->n[c.e_out][c.e_sp] = a > (unsigned long long)c.e_cap ? c.e_cap : a;
-  }
-  const unsigned long long b = cnt->n[c.i_out][c.i_sp] + ns;
-  cnt->n[c.i_out][c.i_sp] = b > (unsigned long long)c.i_cap ? c.i_cap : b;
-  const unsigned long long d = cnt->n[c.n_out][c.n_sp] + ncx;
-  cnt->n[c.n_out][c.n_sp] = d > (unsigned long long)c.n_cap ? c.n_cap : d;
-  cnt->n_tomb[c.n_sp] = ns;
-  cnt->n_tomb[c.i_sp] = ncx;
-  cnt->next_pid += nion;
-}
-
-__global__ void k_resolve_cleanup(ResolveArgs a) {
-  const unsigned int ne = min(a.cnt->n_events, (unsigned int)a.ev_cap);
+  // the per-cell list heads of this step's events (and so of its candidates) go
+  // back to empty; nothing in this kernel reads them
+  const unsigned int ne = min(a.cnt->n_events, (unsigned int)a.commit.ev_cap);
   for (long long e = gtid(); e < ne; e += gstride()) {
     const uint32_t c = a.ev[e].cell;
     a.ev_head[c] = -1;
     a.cand_head[c] = -1;
   }
+  // the last block to finish commits the step's counts (every block has read them)
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&a.cnt->resolve_ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    resolve_commit(a.cnt, a.commit);
+    a.cnt->resolve_ticket = 0u;
+  }
 }
+
 
 // ---------------------------------------------------------------------------
 // explicit instantiations through launchers
@@ -848,15 +859,9 @@ void launch_push(const PushArgs<S>& a, int role, bool mcc, int grid, cudaStream_
 void launch_resolve_rank(const ResolveArgs& a, int grid, cudaStream_t st) {
   PIC_LAUNCH(grid, kRankWarps * 32, 0, st, k_resolve_rank)(a);
 }
-void launch_resolve_cleanup(const ResolveArgs& a, int grid, cudaStream_t st) {
-  PIC_LAUNCH(grid, 256, 0, st, k_resolve_cleanup)(a);
-}
 template <class S>
 void launch_resolve_apply(const ApplyArgs<S>& a, int grid, cudaStream_t st) {
   PIC_LAUNCH(grid, 256, 0, st, k_resolve_apply<S>)(a);
-}
-void launch_resolve_commit(DevCounters* cnt, const ResolveCommit& c, cudaStream_t st) {
-  PIC_LAUNCH(1, 1, 0, st, k_resolve_commit)(cnt, c);
 }
 
 template void launch_inject<Store64>(const InjectArgs<Store64>&, int, cudaStream_t);

@@ -988,8 +988,9 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     ap.log = I->ion_log;
     ap.nd = next_deposit_of(I, true);
     ap.n_species = n_sp;
-    launch_resolve_apply<S>(ap, rb, st);
-    ResolveCommit rc{};
+    ap.ev_head = I->ev_head;
+    ap.cand_head = I->cand_head;
+    ResolveCommit& rc = ap.commit;
     rc.e_out = ap.e_out;
     rc.e_sp = e_sp;
     rc.e_cap = ap.e_cap;
@@ -1000,8 +1001,7 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     rc.n_sp = n_sp;
     rc.n_cap = ap.n_cap;
     rc.ev_cap = I->ev_cap;
-    launch_resolve_commit(I->cnt, rc, st);
-    launch_resolve_cleanup(r, rb, st);
+    launch_resolve_apply<S>(ap, rb, st);  // with the commit and the list-head reset
     T.end(st);
   }
   launch_step_end(I->cnt, I->circ, st);

@@ -183,6 +183,7 @@ struct DevCounters {
   unsigned long long pushed[kMaxSpecies];  // cumulative particle pushes (metric units)
   unsigned int step;                       // index of the step being taken (Philox counter word 1)
   double anode_V;                          // anode potential of the next solve (external circuit)
+  unsigned int resolve_ticket;             // blocks of the resolve launch finished (0 between launches)
 };
 
 // External circuit (the serial RC circuit between the electrodes): a source V0

@@ -582,6 +582,17 @@ struct ResolveArgs {
   uint32_t* sort_vals;
 };
 
+// Buffers and capacities the resolve commit updates (species < 0: absent).
+struct ResolveCommit {
+  int e_out, e_sp;
+  long long e_cap;
+  int i_out, i_sp;
+  long long i_cap;
+  int n_out, n_sp;
+  long long n_cap;
+  int ev_cap;
+};
+
 template <class S>
 struct ApplyArgs {
   Grid g;
@@ -605,18 +616,11 @@ struct ApplyArgs {
   uint32_t* log;
   NextDeposit nd;
   int n_species;
+  int32_t* ev_head;      // per-cell list heads, emptied for the next step
+  int32_t* cand_head;
+  ResolveCommit commit;  // applied by the launch's last block
 };
 
-// Buffers and capacities the resolve commit updates (species < 0: absent).
-struct ResolveCommit {
-  int e_out, e_sp;
-  long long e_cap;
-  int i_out, i_sp;
-  long long i_cap;
-  int n_out, n_sp;
-  long long n_cap;
-  int ev_cap;
-};
 
 template <class S>
 struct DepositArgs {
@@ -640,10 +644,8 @@ void launch_step_end(DevCounters* cnt, const Circuit& c, cudaStream_t st);
 template <class S>
 void launch_push(const PushArgs<S>& a, int role, bool mcc, int grid, cudaStream_t st);
 void launch_resolve_rank(const ResolveArgs& a, int grid, cudaStream_t st);
-void launch_resolve_cleanup(const ResolveArgs& a, int grid, cudaStream_t st);
 template <class S>
 void launch_resolve_apply(const ApplyArgs<S>& a, int grid, cudaStream_t st);
-void launch_resolve_commit(DevCounters* cnt, const ResolveCommit& c, cudaStream_t st);
 
 template <class S>
 void launch_deposit(const DepositArgs<S>& a, int grid, cudaStream_t st);
