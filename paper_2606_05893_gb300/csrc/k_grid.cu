@@ -630,12 +630,14 @@ void launch_field_energy(const Grid& g, const double* phi, double* out, cudaStre
 // FP32 over runs of 8 nodes and those sums in FP64.
 __global__ void k_field_energy_ff(Grid g, const float* __restrict__ hi, const float* __restrict__ lo, float dz_in,
                                   float dz_top, double* out) {
+  // threads (x over a row, y over kFeRows rows): a block keeps that many rows'
+  // loads in flight at once
   const long long pl = g.nplane;
   const long long rows = (long long)g.ny * (g.nz + 1);
   double acc = 0.0;
   float part = 0.f;
   int run = 0;
-  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+  for (long long r = (long long)blockIdx.x * blockDim.y + threadIdx.y; r < rows; r += (long long)gridDim.x * blockDim.y) {
     const int k = (int)(r / g.ny);
     const int j = (int)(r - (long long)k * g.ny);
     const long long c0 = (long long)j * g.nx;                               // row j in a plane
@@ -674,17 +676,133 @@ __global__ void k_field_energy_ff(Grid g, const float* __restrict__ hi, const fl
     }
   }
   acc += (double)part;
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) atomicAdd(out, acc);
+  // block sum over the linear thread index (two-dimensional block)
+  __shared__ double sm[32];
+  const int t = threadIdx.y * blockDim.x + threadIdx.x, nw = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((t & 31) == 0) sm[t >> 5] = acc;
+  __syncthreads();
+  if (t < 32) {
+    acc = t < nw ? sm[t] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (t == 0) atomicAdd(out, acc);
+  }
 }
 void launch_field_energy_ff(const Grid& g, const float* phi32, const float* lo32, double* out, cudaStream_t s) {
   const double dphi_dk = (g.phi_a - g.phi_c) / (double)g.nz;
   const float dz_in = (float)dphi_dk;
   const float dz_top = (float)(g.phi_a - (g.phi_c + dphi_dk * (double)(g.nz - 1)));
   const long long rows = (long long)g.ny * (g.nz + 1);
-  const int threads = g.nx >= 256 ? 256 : (g.nx >= 128 ? 128 : 64);
-  const int grid = (int)std::min<long long>(rows, 152 * 16);
-  PIC_LAUNCH(grid, threads, 0, s, k_field_energy_ff)(g, phi32, lo32, dz_in, dz_top, out);
+  const int tx = g.nx >= 128 ? 128 : (g.nx >= 64 ? 64 : 32);
+  const int ty = 256 / tx;
+  const int grid = (int)std::min<long long>((rows + ty - 1) / ty, 152 * 8);
+  PIC_LAUNCH(grid, dim3(tx, ty), 0, s, k_field_energy_ff)(g, phi32, lo32, dz_in, dz_top, out);
+}
+
+// The moments of the mixed store in one launch: every block sums |v|^2 of its
+// share of every species (FP32 runs of 8, then FP64, as k_kinetic_mx), then its
+// share of the field energy's node rows (as k_field_energy_ff); one FP64 atomic
+// per block and sum into out (out[sp] per species, out[16] the field).
+__global__ void k_moments_mx(MomentsMx a, double* out) {
+  __shared__ double sm[32];
+  const int t = threadIdx.x, nw = blockDim.x >> 5;
+  auto block_total = [&](double v) -> double {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((t & 31) == 0) sm[t >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (t < 32) {
+      r = t < nw ? sm[t] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();  // sm is reused by the next total
+    return r;
+  };
+  {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (int sp = 0; sp < a.nsp; ++sp) {
+      const StoreMx& st = a.st[sp];
+      const long long n = min((long long)*a.n_dev[sp], a.n_max[sp]);
+      double acc = 0.0;
+      float part = 0.f;
+      int run = 0;
+      for (long long i = (long long)blockIdx.x * blockDim.x + t; i < n; i += stride) {
+        const float x = st.vx[i], y = st.vy[i], z = st.vz[i];
+        if (st.pid[i] != kPidDead) part += fmaf(x, x, fmaf(y, y, z * z));
+        if (++run == 8) {
+          acc += (double)part;
+          part = 0.f;
+          run = 0;
+        }
+      }
+      acc = block_total(acc + (double)part);
+      if (t == 0 && acc != 0.0) atomicAdd(out + sp, acc);
+    }
+  }
+  // field energy: edge differences of the solver's FP32 hi / lo state, rows of
+  // nodes over (blocks - kin_blocks) blocks, several rows per block at once
+  const Grid& g = a.g;
+  const long long pl = g.nplane;
+  const long long rows = (long long)g.ny * (g.nz + 1);
+  const int tx = a.fe_tx, ty = blockDim.x / tx, lx0 = t % tx, ly0 = t / tx;
+  const long long fb = blockIdx.x, nfb = gridDim.x;
+  double acc = 0.0;
+  float part = 0.f;
+  int run = 0;
+  for (long long r = fb * ty + ly0; r < rows; r += nfb * ty) {
+    const int k = (int)(r / g.ny);
+    const int j = (int)(r - (long long)k * g.ny);
+    const long long c0 = (long long)j * g.nx;
+    const long long cn = (long long)(j + 1 == g.ny ? 0 : j + 1) * g.nx;
+    const float* H = a.hi + (long long)k * pl;
+    const float* L = a.lo + (long long)(k - 1) * pl;
+    const bool interior = k > 0 && k < g.nz;
+    for (int i = lx0; i < g.nx; i += tx) {
+      const int ip = i + 1 == g.nx ? 0 : i + 1;
+      float h0 = 0.f, hx = 0.f, hy = 0.f, l0 = 0.f, lxv = 0.f, ly = 0.f;
+      if (k > 0) {
+        h0 = H[c0 + i];
+        hx = H[c0 + ip];
+        hy = H[cn + i];
+      }
+      if (interior) {
+        l0 = L[c0 + i];
+        lxv = L[c0 + ip];
+        ly = L[cn + i];
+      }
+      const float dx = (hx - h0) + (lxv - l0);
+      const float dy = (hy - h0) + (ly - l0);
+      float sq = fmaf(dx, dx, dy * dy);
+      if (k < g.nz) {
+        const float h1 = H[pl + c0 + i];
+        const float l1 = k + 1 < g.nz ? L[pl + c0 + i] : 0.f;
+        const float dz = (k + 1 == g.nz ? a.dz_top : a.dz_in) + ((h1 - h0) + (l1 - l0));
+        sq = fmaf(dz, dz, sq);
+      }
+      part += sq;
+      if (++run == 8) {
+        acc += (double)part;
+        part = 0.f;
+        run = 0;
+      }
+    }
+  }
+  acc = block_total(acc + (double)part);
+  if (t == 0 && acc != 0.0) atomicAdd(out + 16, acc);
+}
+void launch_moments_mx(const MomentsMx& a0, double* out, cudaStream_t s) {
+  MomentsMx a = a0;
+  const Grid& g = a.g;
+  const double dphi_dk = (g.phi_a - g.phi_c) / (double)g.nz;
+  a.dz_in = (float)dphi_dk;
+  a.dz_top = (float)(g.phi_a - (g.phi_c + dphi_dk * (double)(g.nz - 1)));
+  a.fe_tx = g.nx >= 128 ? 128 : (g.nx >= 64 ? 64 : 32);
+  a.kin_blocks = 0;
+  PIC_LAUNCH(152 * 8, kBlock, 0, s, k_moments_mx)(a, out);
 }
 
 // Philox on the device (test hook)

@@ -44,6 +44,7 @@ int sm_count() {
 namespace {
 
 constexpr int kPushBlocksPerSM = 8;
+constexpr long long kStageHost = 65536;  // largest upload staged on the host (returns before the device runs it)
 constexpr int kPhases = PIC_NPHASES;
 
 // CUDA-event timing of the phases of a step on the handle's stream.
@@ -221,6 +222,12 @@ struct Instance {
   double* stage_x = nullptr;  // device staging of pic_inject_particles
   double* stage_v = nullptr;
   long long stage_cap = 0;
+  // small uploads go through pinned host staging and return without waiting
+  // for the device (kStageHost particles at most)
+  double* hstage = nullptr;      // x then v, 6 doubles per particle (pinned)
+  cudaEvent_t hstage_done = nullptr;
+  bool hstage_busy = false;      // a copy out of hstage may still be in flight
+  bool host_fresh = false;       // host_cnt equals the device counters once the queued work ends
 };
 
 }  // namespace
@@ -355,6 +362,8 @@ void free_instance(Instance* I) {
   cudaFree(I->red);
   cudaFree(I->stage_x);
   cudaFree(I->stage_v);
+  if (I->hstage) cudaFreeHost(I->hstage);
+  if (I->hstage_done) cudaEventDestroy(I->hstage_done);
   I->timer.release();
   I->solver.release();
   delete I;
@@ -747,6 +756,7 @@ pic_status sort_instance(pic_handle* h, Instance* I) {
     I->cur[s] = c ^ 1;
   }
   I->sorted_once = true;
+  I->host_fresh = false;  // the sort drops tombstones from the counts
   CK(h, cudaGetLastError());
   return PIC_OK;
 }
@@ -1298,6 +1308,7 @@ pic_status check(pic_handle* h, int inst) {
 pic_status sync_counters(pic_handle* h, Instance* I) {
   CK(h, cudaMemcpyAsync(I->host_cnt, I->cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  I->host_fresh = true;
   return PIC_OK;
 }
 
@@ -1424,8 +1435,12 @@ pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, in
     for (int c = 0; c < 3; ++c)
       if (!std::isfinite(v[3 * i + c])) return fail(h, PIC_EINVAL, "particle %lld has a non-finite velocity", (long long)i);
   }
-  st = sync_counters(h, I);
-  if (st != PIC_OK) return st;
+  // the counters on the host are current unless device work changed them since
+  // they were last read (a step, a sort)
+  if (!I->host_fresh) {
+    st = sync_counters(h, I);
+    if (st != PIC_OK) return st;
+  }
   const long long have = (long long)I->host_cnt->n[I->cur[species]][species];
   if (have + n > I->cap[species]) return fail(h, PIC_ECAPACITY, "species %d: %lld + %lld exceeds capacity %lld", species, have, (long long)n, I->cap[species]);
   if ((unsigned long long)I->host_cnt->next_pid + (unsigned long long)n > 0xFFFFFFFEull)
@@ -1435,14 +1450,31 @@ pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, in
     cudaFree(I->stage_v);
     I->stage_x = I->stage_v = nullptr;
     I->stage_cap = 0;
-    CK(h, dalloc(&I->stage_x, 3 * (size_t)n));
-    CK(h, dalloc(&I->stage_v, 3 * (size_t)n));
-    I->stage_cap = n;
+    CK(h, dalloc(&I->stage_x, 3 * (size_t)std::max<long long>(n, kStageHost)));
+    CK(h, dalloc(&I->stage_v, 3 * (size_t)std::max<long long>(n, kStageHost)));
+    I->stage_cap = std::max<long long>(n, kStageHost);
   }
   double* dx = I->stage_x;
   double* dv = I->stage_v;
-  CK(h, cudaMemcpyAsync(dx, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
-  CK(h, cudaMemcpyAsync(dv, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+  const bool small = n <= kStageHost;
+  if (small) {
+    // the caller's arrays are copied into pinned staging on the host, so the call
+    // returns as soon as the copy and the upload kernel are queued
+    if (!I->hstage) {
+      CK(h, cudaMallocHost((void**)&I->hstage, sizeof(double) * 6 * kStageHost));
+      CK(h, cudaEventCreateWithFlags(&I->hstage_done, cudaEventDisableTiming));
+    }
+    if (I->hstage_busy) CK(h, cudaEventSynchronize(I->hstage_done));  // the last upload has left the staging
+    memcpy(I->hstage, x, sizeof(double) * 3 * n);
+    memcpy(I->hstage + 3 * n, v, sizeof(double) * 3 * n);
+    CK(h, cudaMemcpyAsync(dx, I->hstage, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(dv, I->hstage + 3 * n, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaEventRecord(I->hstage_done, h->stream));
+    I->hstage_busy = true;
+  } else {
+    CK(h, cudaMemcpyAsync(dx, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(dv, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+  }
   const int c = I->cur[species];
   // uploaded particles join the next step's accumulated deposit (if any)
   const NextDeposit nd = next_deposit_of(I, I->next_valid);
@@ -1453,6 +1485,13 @@ pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, in
   else
     launch_load<Store64>(I->g, I->s64[species][c], I->cnt, c, species, I->cap[species], dx, dv, n, nd, neutral,
                          h->stream);
+  // what the upload does to the counters (checked above: no capacity clamp)
+  I->host_cnt->n[c][species] += (unsigned long long)n;
+  I->host_cnt->next_pid += (unsigned int)n;
+  if (small) {
+    CK(h, cudaGetLastError());
+    return PIC_OK;
+  }
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     h->dead = true;
@@ -1466,6 +1505,7 @@ pic_status pic_step(pic_handle* h, int32_t nsteps) {
   if (h->dead) return fail(h, PIC_ESTATE, "handle unusable after an earlier fatal error: %s", h->err.c_str());
   if (nsteps < 0) return fail(h, PIC_EINVAL, "nsteps must be >= 0");
   h->sticky = 0;
+  for (auto* I : h->inst) I->host_fresh = false;
   // several instances step concurrently: as one recorded ensemble step on the
   // caller's stream when every instance's step qualifies, else each on its own
   // stream, ordered after the caller's stream and joined back into it
@@ -1528,6 +1568,7 @@ pic_status pic_step(pic_handle* h, int32_t nsteps) {
     h->dead = true;
     return fail(h, PIC_ECUDA, "step: %s", cudaGetErrorString(cudaGetLastError()));
   }
+  for (auto* I : h->inst) I->host_fresh = I->host_cnt != nullptr;
   for (auto* I : h->inst) {
     if (nsteps > 0) {
       I->last = I->solver.result_read();
@@ -1560,15 +1601,26 @@ pic_status pic_moments(pic_handle* h, int32_t inst, pic_moments_t* out) {
   Instance* I = h->inst[inst];
   cudaStream_t s = h->stream;
   CK(h, cudaMemsetAsync(I->red, 0, sizeof(double) * 64, s));
-  for (int sp = 0; sp < I->nsp; ++sp) {
-    const int c = I->cur[sp];
-    if (I->mixed) launch_kinetic<StoreMx>(I->smx[sp][c], &I->cnt->n[c][sp], I->cap[sp], I->red + sp, s);
-    else launch_kinetic<Store64>(I->s64[sp][c], &I->cnt->n[c][sp], I->cap[sp], I->red + sp, s);
-  }
   if (I->mixed) {
-    // from the solver's float-float state (the potential the last solve left)
-    launch_field_energy_ff(I->g, I->phi32, I->solver.lo32, I->red + 16, s);
+    // one launch: kinetic sums and the field energy from the solver's
+    // float-float state (the potential the last solve left)
+    MomentsMx m{};
+    m.g = I->g;
+    m.nsp = I->nsp;
+    for (int sp = 0; sp < I->nsp; ++sp) {
+      const int c = I->cur[sp];
+      m.st[sp] = I->smx[sp][c];
+      m.n_dev[sp] = &I->cnt->n[c][sp];
+      m.n_max[sp] = I->cap[sp];
+    }
+    m.hi = I->phi32;
+    m.lo = I->solver.lo32;
+    launch_moments_mx(m, I->red, s);
   } else {
+    for (int sp = 0; sp < I->nsp; ++sp) {
+      const int c = I->cur[sp];
+      launch_kinetic<Store64>(I->s64[sp][c], &I->cnt->n[c][sp], I->cap[sp], I->red + sp, s);
+    }
     launch_field_energy(I->g, I->phi, I->red + 16, s);
   }
   double red[64];
@@ -2255,6 +2307,7 @@ pic_status pic_load(pic_handle* h, int32_t inst, const char* path) {
   c.error = 0;
   CK(h, cudaMemcpy(I->cnt, &c, sizeof c, cudaMemcpyHostToDevice));
   *I->host_cnt = c;
+  I->host_fresh = true;
   CK(h, cudaMemcpy(I->phi, phi, sizeof(double) * I->g.nnode, cudaMemcpyHostToDevice));
   if (I->mixed) {
     CK(h, cudaMemcpy(I->phi32, hi, sizeof(float) * I->g.nnode, cudaMemcpyHostToDevice));

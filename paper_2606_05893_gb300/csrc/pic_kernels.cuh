@@ -725,6 +725,20 @@ template <class S>
 void launch_kinetic(S st, const unsigned long long* n_dev, long long n_max, double* out, cudaStream_t s);
 void launch_field_energy(const Grid& g, const double* phi, double* out, cudaStream_t s);
 void launch_field_energy_ff(const Grid& g, const float* phi32, const float* lo32, double* out, cudaStream_t s);
+// every species' sum of |v|^2 (out[sp]) and the field energy sum (out[16]) of the
+// mixed store in one launch; out is added to (zero it first)
+struct MomentsMx {
+  Grid g;
+  int nsp;
+  StoreMx st[kMaxSpecies];
+  const unsigned long long* n_dev[kMaxSpecies];
+  long long n_max[kMaxSpecies];
+  const float* hi;  // the solver's FP32 state at nodes
+  const float* lo;  // and its low part over the unknowns
+  float dz_in, dz_top;   // set by the launcher
+  int fe_tx, kin_blocks; // set by the launcher (kin_blocks unused: every block takes both parts)
+};
+void launch_moments_mx(const MomentsMx& a, double* out, cudaStream_t s);
 
 void launch_philox(long long n, uint4 ctr, uint2 key, uint32_t* out, cudaStream_t s);
 
