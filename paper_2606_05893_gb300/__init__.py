@@ -101,11 +101,16 @@ class PicError(RuntimeError):
         self.status = status
 
 
-def load_library(path: str = LIB_PATH):
-    """Load libpic_gb300.so (built by ``_build.build()``); raises if it is missing."""
+def load_library(path: str = None):
+    """Load libpic_gb300.so (built by ``_build.build()``); raises if it is missing.
+    PIC_GB300_LIB names another build of the same library to load instead (the
+    checked build, ``_build.build(checked=True)``); the first load of a process
+    decides."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = os.environ.get("PIC_GB300_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"libpic_gb300.so not built ({path}); run __graft_entry__.build() or "
                           "python -m paper_2606_05893_gb300._build")

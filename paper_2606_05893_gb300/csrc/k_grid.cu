@@ -94,7 +94,8 @@ __global__ void __launch_bounds__(kDepBlock) k_deposit_mx(DepositArgs<StoreMx> a
   const float q = (float)a.qw_h3;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += gstride()) {
     const long long i = base + threadIdx.x;
-    const bool valid = i < n;
+    bool valid = i < n;
+    if (valid && !PIC_BOUNDS(a.st.cell[i] >= 0 && a.st.cell[i] < g.ncell, a.cnt)) valid = false;
     int cell = -1;
     float w[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (valid) {
@@ -125,10 +126,12 @@ __global__ void __launch_bounds__(kDepBlock) k_count_neutrals(DepositArgs<S> a) 
     float one[1] = {0.f};  // counts are exact in FP32 (a warp holds 32 at most)
     if (i < n) {
       const auto p = store_read(a.st, g, i);
-      cell = (int)particle_cell(p);
-      one[0] = p.pid != kPidDead ? 1.f : 0.f;
+      if (PIC_BOUNDS(particle_cell(p) >= 0 && particle_cell(p) < g.ncell, a.cnt)) {
+        cell = (int)particle_cell(p);
+        one[0] = p.pid != kPidDead ? 1.f : 0.f;
+      }
     }
-    if (warp_run_sum(cell, one) && i < n && one[0] > 0.f) atomicAdd(&a.ncount[cell], (int)one[0]);
+    if (warp_run_sum(cell, one) && cell >= 0 && one[0] > 0.f) atomicAdd(&a.ncount[cell], (int)one[0]);
   }
 }
 

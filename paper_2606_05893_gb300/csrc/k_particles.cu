@@ -419,6 +419,7 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
     for (int u = 0; u < kIlp; ++u) {
       if (!valid[u]) continue;
       if (p[u].pid == kPidDead) continue;  // neutrals and ions converted in the last step are dropped here
+      if (!PIC_BOUNDS(particle_cell(p[u]) >= 0 && particle_cell(p[u]) < g.ncell, a.cnt)) continue;
       cell_n[u] = (int)particle_cell(p[u]);
       if (CHARGED) {
         const auto e = p[u].gather(g, a);
@@ -437,6 +438,7 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
         }
         continue;
       }
+      if (!PIC_BOUNDS(particle_cell(p[u]) >= 0 && particle_cell(p[u]) < g.ncell, a.cnt)) continue;
       keep[u] = true;
       if (MCC) {
         const float nb = mcc_nu_bound(a.mc, cell_n[u], a.mc.count_in_field ? p[u].nc : -1.f);
@@ -752,8 +754,14 @@ __global__ void k_resolve_apply(ApplyArgs<S> a) {
   // then run on their own SM's FP64 pipe instead of queueing on one)
   for (long long r = blockIdx.x + (long long)gridDim.x * threadIdx.x; r < ns;
        r += (long long)gridDim.x * blockDim.x) {
+    if (!PIC_BOUNDS(a.sorted_vals[r] < (uint32_t)a.ev_cap, a.cnt)) continue;
     const Event ev = a.ev[a.sorted_vals[r]];
+    if (!PIC_BOUNDS(ev.victim >= 0 && ev.victim < a.cand_cap &&
+                        (long long)ev.slot < (ev.kind == XS_CHARGE_EXCHANGE ? a.i_cap : a.e_cap),
+                    a.cnt))
+      continue;
     const Cand cd = a.cand[ev.victim];
+    if (!PIC_BOUNDS(cd.slot < (uint32_t)a.n_cap, a.cnt)) continue;
     // victim neutral -> ion (position x^{n+1}, velocity and pid kept)
     const auto vn = store_read(a.n_st, a.g, cd.slot);
     const unsigned long long is = ni_out + r;

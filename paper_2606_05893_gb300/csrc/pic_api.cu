@@ -970,6 +970,7 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     ap.ev = I->ev;
     ap.ev_cap = I->ev_cap;
     ap.cand = I->cand;
+    ap.cand_cap = I->cand_cap;
     ap.sorted_vals = where ? I->evsort.vb : I->evsort.va;
     ap.key = key;
     // the ionization fixes electrons, victims and ions; without it the exchange
@@ -1588,6 +1589,7 @@ pic_status pic_step(pic_handle* h, int32_t nsteps) {
       }
       if (e & (ERR_CAPACITY | ERR_EVENTS)) return fail(h, PIC_ECAPACITY, "store or event capacity exceeded (flags %d)", e);
       if (e & ERR_TIMEOUT) return fail(h, PIC_ETIMEOUT, "device wait timed out");
+      if (e & ERR_BOUNDS) return fail(h, PIC_ESTATE, "checked build: an index out of range was skipped (flags %d)", e);
     }
   }
   if (h->sticky & 1) return fail(h, PIC_ENOCONV, "Poisson solve hit cg_maxit");

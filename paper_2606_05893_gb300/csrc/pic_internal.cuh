@@ -45,6 +45,16 @@ enum : int { XS_IONIZATION = 0, XS_ELASTIC = 1, XS_CHARGE_EXCHANGE = 2 };
 // device error bits (DevCounters::error)
 enum : int { ERR_CAPACITY = 1, ERR_EVENTS = 2, ERR_TIMEOUT = 4, ERR_NOCONV = 8, ERR_BOUNDS = 16 };
 
+// Checked build (compiled with -DPIC_CHECKED, libpic_gb300_checked.so): every
+// cell, slot and list index a particle kernel takes from memory is tested
+// before use; a bad one records ERR_BOUNDS and the access is skipped. In the
+// ordinary build the test is not compiled.
+#ifdef PIC_CHECKED
+#define PIC_BOUNDS(ok, cnt) ((ok) ? true : (atomicOr(&(cnt)->error, ERR_BOUNDS), false))
+#else
+#define PIC_BOUNDS(ok, cnt) true
+#endif
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
 // ---------------------------------------------------------------------------

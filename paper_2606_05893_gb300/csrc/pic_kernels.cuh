@@ -600,6 +600,7 @@ struct ApplyArgs {
   const Event* ev;
   int ev_cap;
   const Cand* cand;
+  int cand_cap;
   const uint32_t* sorted_vals;
   XsDev ch[kMaxXsec];
   uint2 key;
