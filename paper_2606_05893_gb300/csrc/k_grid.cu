@@ -728,21 +728,27 @@ __global__ void k_moments_mx(MomentsMx a, double* out) {
   {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (int sp = 0; sp < a.nsp; ++sp) {
-      const StoreMx& st = a.st[sp];
+      const float* __restrict__ vx = a.st[sp].vx;
+      const float* __restrict__ vy = a.st[sp].vy;
+      const float* __restrict__ vz = a.st[sp].vz;
+      const uint32_t* __restrict__ pid = a.st[sp].pid;
       const long long n = min((long long)*a.n_dev[sp], a.n_max[sp]);
       double acc = 0.0;
-      float part = 0.f;
-      int run = 0;
-      for (long long i = (long long)blockIdx.x * blockDim.x + t; i < n; i += stride) {
-        const float x = st.vx[i], y = st.vy[i], z = st.vz[i];
-        if (st.pid[i] != kPidDead) part += fmaf(x, x, fmaf(y, y, z * z));
-        if (++run == 8) {
-          acc += (double)part;
-          part = 0.f;
-          run = 0;
+      // four particles per pass (their loads in flight together), summed in FP32,
+      // the pass sums in FP64
+      for (long long i = (long long)blockIdx.x * blockDim.x + t; i < n; i += 4 * stride) {
+        float part = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const long long ii = i + q * stride;
+          if (ii < n) {
+            const float x = __ldg(vx + ii), y = __ldg(vy + ii), z = __ldg(vz + ii);
+            if (__ldg(pid + ii) != kPidDead) part += fmaf(x, x, fmaf(y, y, z * z));
+          }
         }
+        acc += (double)part;
       }
-      acc = block_total(acc + (double)part);
+      acc = block_total(acc);
       if (t == 0 && acc != 0.0) atomicAdd(out + sp, acc);
     }
   }
@@ -757,8 +763,8 @@ __global__ void k_moments_mx(MomentsMx a, double* out) {
   float part = 0.f;
   int run = 0;
   for (long long r = fb * ty + ly0; r < rows; r += nfb * ty) {
-    const int k = (int)(r / g.ny);
-    const int j = (int)(r - (long long)k * g.ny);
+    const int k = (int)r / g.ny;  // rows < 2^31
+    const int j = (int)r - k * g.ny;
     const long long c0 = (long long)j * g.nx;
     const long long cn = (long long)(j + 1 == g.ny ? 0 : j + 1) * g.nx;
     const float* H = a.hi + (long long)k * pl;
