@@ -841,6 +841,17 @@ def main():
                        "sort": f"every {wl.sort_interval} steps; the timed window holds ceil(steps / {wl.sort_interval}) sorts"},
             "e2e": e2e, "gpu_launches": r["launches"], "launch_ops": r["launch_ops"], "clocks": r["clocks"], "roofline": roofline,
             "phase_ms_per_step": phase_ms, "cg_iters_last_step": r["cg_iters"]}
+    # the whole step against HBM by the scope's byte model: particles (64 B each in the
+    # mixed store, 104 B in FP64) + per unknown node 12 B (charge, counts, potential)
+    # + 128 B per PCG iteration (mixed; 180 B in FP64)
+    nu = wl.nx * wl.ny * (wl.nz - 1)
+    pushes_step = a["pushes"] / args.steps
+    per_it = 128 if head == "mixed" else 180
+    step_bytes = pushes_step * BYTES_PER_PARTICLE[head] + nu * (12 + r["cg_iters"] * per_it)
+    step_gbs = step_bytes / (a["ms"] / args.steps * 1e-3) / 1e9
+    line["step_roofline"] = {"bound": "hbm", "achieved": step_gbs, "peak": peak, "unit": "GB/s",
+                             "frac": step_gbs / peak, "bytes_per_step": step_bytes,
+                             "model": f"{BYTES_PER_PARTICLE[head]} B per push + (12 + {per_it} x CG iterations) B per unknown node"}
     if "fp64" in results and head != "fp64":
         f, fa = results["fp64"], agg["fp64"]
         fph = f["phases"]
