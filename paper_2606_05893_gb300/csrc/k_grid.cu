@@ -705,9 +705,11 @@ void launch_field_energy_ff(const Grid& g, const float* phi32, const float* lo32
 }
 
 // The moments of the mixed store in one launch: every block sums |v|^2 of its
-// share of every species (FP32 runs of 8, then FP64, as k_kinetic_mx), then its
-// share of the field energy's node rows (as k_field_energy_ff); one FP64 atomic
-// per block and sum into out (out[sp] per species, out[16] the field).
+// share of every species (four particles per pass in FP32, the passes in FP64),
+// then its share of the field energy's node rows (as k_field_energy_ff), and
+// writes its totals to a.part; the last block to finish adds the blocks'
+// totals in block order (a sum that does not depend on timing) into out
+// (out[sp] per species, out[16] the field).
 __global__ void k_moments_mx(MomentsMx a, double* out) {
   __shared__ double sm[32];
   const int t = threadIdx.x, nw = blockDim.x >> 5;
@@ -749,7 +751,7 @@ __global__ void k_moments_mx(MomentsMx a, double* out) {
         acc += (double)part;
       }
       acc = block_total(acc);
-      if (t == 0 && acc != 0.0) atomicAdd(out + sp, acc);
+      if (t == 0) a.part[(long long)blockIdx.x * kMomSlots + sp] = acc;
     }
   }
   // field energy: edge differences of the solver's FP32 hi / lo state, rows of
@@ -801,7 +803,23 @@ __global__ void k_moments_mx(MomentsMx a, double* out) {
     }
   }
   acc = block_total(acc + (double)part);
-  if (t == 0 && acc != 0.0) atomicAdd(out + 16, acc);
+  if (t == 0) a.part[(long long)blockIdx.x * kMomSlots + kMaxSpecies] = acc;
+  // the last block: every block's totals are written
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int q = 0; q <= a.nsp; ++q) {
+    const int slot = q < a.nsp ? q : kMaxSpecies;
+    double v = 0.0;
+    for (int b = t; b < (int)gridDim.x; b += blockDim.x) v += a.part[(long long)b * kMomSlots + slot];
+    v = block_total(v);
+    if (t == 0) out[q < a.nsp ? q : 16] = v;
+  }
+  if (t == 0) *a.ticket = 0u;
 }
 void launch_moments_mx(const MomentsMx& a0, double* out, cudaStream_t s) {
   MomentsMx a = a0;
@@ -811,7 +829,7 @@ void launch_moments_mx(const MomentsMx& a0, double* out, cudaStream_t s) {
   a.dz_top = (float)(g.phi_a - (g.phi_c + dphi_dk * (double)(g.nz - 1)));
   a.fe_tx = g.nx >= 128 ? 128 : (g.nx >= 64 ? 64 : 32);
   a.kin_blocks = 0;
-  PIC_LAUNCH(152 * 8, kBlock, 0, s, k_moments_mx)(a, out);
+  PIC_LAUNCH(kMomBlocks, kBlock, 0, s, k_moments_mx)(a, out);
 }
 
 // Philox on the device (test hook)

@@ -207,6 +207,8 @@ struct Instance {
   int32_t* seg_big = nullptr;   // buckets for the block-wide sort (ncell + 1)
   void* scan_tmp = nullptr;
   double* red = nullptr;  // reduction scratch (moments)
+  double* mom_part = nullptr;        // per-block totals of the mixed store's moments
+  unsigned int* mom_ticket = nullptr;
   Solver solver;
   std::vector<Source> sources;
   uint32_t step = 0;
@@ -360,6 +362,8 @@ void free_instance(Instance* I) {
   if (I->seg_host) cudaFreeHost(I->seg_host);
   cudaFree(I->scan_tmp);
   cudaFree(I->red);
+  cudaFree(I->mom_part);
+  cudaFree(I->mom_ticket);
   cudaFree(I->stage_x);
   cudaFree(I->stage_v);
   if (I->hstage) cudaFreeHost(I->hstage);
@@ -649,6 +653,11 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
   CK(h, cudaMallocHost((void**)&I->seg_host, sizeof(SegCtl)));
   CK(h, cudaMalloc(&I->scan_tmp, scan_temp_bytes(g.ncell)));
   CK(h, dalloc(&I->red, 64));
+  if (I->mixed) {
+    CK(h, dalloc(&I->mom_part, (size_t)kMomBlocks * kMomSlots));
+    CK(h, dalloc(&I->mom_ticket, 1));
+    CK(h, cudaMemset(I->mom_ticket, 0, sizeof(unsigned int)));
+  }
 
   if (I->mixed) {
     CK(h, dalloc(&I->phi32, g.nnode));
@@ -1617,6 +1626,8 @@ pic_status pic_moments(pic_handle* h, int32_t inst, pic_moments_t* out) {
     }
     m.hi = I->phi32;
     m.lo = I->solver.lo32;
+    m.part = I->mom_part;
+    m.ticket = I->mom_ticket;
     launch_moments_mx(m, I->red, s);
   } else {
     for (int sp = 0; sp < I->nsp; ++sp) {

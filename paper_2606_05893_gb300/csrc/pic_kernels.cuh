@@ -727,7 +727,10 @@ void launch_kinetic(S st, const unsigned long long* n_dev, long long n_max, doub
 void launch_field_energy(const Grid& g, const double* phi, double* out, cudaStream_t s);
 void launch_field_energy_ff(const Grid& g, const float* phi32, const float* lo32, double* out, cudaStream_t s);
 // every species' sum of |v|^2 (out[sp]) and the field energy sum (out[16]) of the
-// mixed store in one launch; out is added to (zero it first)
+// mixed store in one launch (written, not added to); part holds kMomBlocks x
+// kMomSlots doubles, ticket one counter that is 0 between launches
+constexpr int kMomBlocks = 152 * 8;
+constexpr int kMomSlots = kMaxSpecies + 1;
 struct MomentsMx {
   Grid g;
   int nsp;
@@ -736,6 +739,8 @@ struct MomentsMx {
   long long n_max[kMaxSpecies];
   const float* hi;  // the solver's FP32 state at nodes
   const float* lo;  // and its low part over the unknowns
+  double* part;
+  unsigned int* ticket;
   float dz_in, dz_top;   // set by the launcher
   int fe_tx, kin_blocks; // set by the launcher (kin_blocks unused: every block takes both parts)
 };
