@@ -40,6 +40,7 @@ class OrCfg(C.Structure):
         ("nsp", C.c_int32),
         ("q", C.c_double * MAXSP), ("m", C.c_double * MAXSP), ("w", C.c_double * MAXSP),
         ("role", C.c_int32 * MAXSP),
+        ("variable_weights", C.c_int32),
     ]
 
 
@@ -100,6 +101,8 @@ def lib(omp: bool = False):
         L.or_set_source.argtypes = [P, C.c_int, C.c_double, C.c_double]
         L.or_set_circuit.argtypes = [P, C.c_double, C.c_double, C.c_double]
         L.or_load.argtypes = [P, C.c_int, C.c_int64, d, d]
+        L.or_load_m.argtypes = [P, C.c_int, C.c_int64, d, d, u32]
+        L.or_get_multiplicity.argtypes = [P, C.c_int, u32]
         L.or_count.restype = C.c_int64
         L.or_count.argtypes = [P, C.c_int]
         L.or_get_particles.argtypes = [P, C.c_int, d, d, u32]
@@ -231,6 +234,7 @@ class Oracle:
         c.nsp = len(wl.species)
         for i, s in enumerate(wl.species):
             c.q[i], c.m[i], c.w[i], c.role[i] = s.charge_C, s.mass_kg, s.weight, s.role
+        c.variable_weights = 1 if getattr(wl, "variable_weights", False) else 0
         self.wl = wl
         self.nsp = c.nsp
         self._h = L.or_create(C.byref(c))
@@ -246,8 +250,8 @@ class Oracle:
         if background_density > 0:
             L.or_set_background_density(self._h, background_density)
         if preload and wl.preload:
-            for sp, (x, v) in enumerate(wl.preload):
-                self.load(sp, x, v)
+            for sp, pre in enumerate(wl.preload):
+                self.load(sp, *pre)
 
     def close(self):
         if self._h:
@@ -260,13 +264,26 @@ class Oracle:
         except Exception:
             pass
 
-    def load(self, sp, x, v):
+    def load(self, sp, x, v, m=None):
+        """Append particles (pids from the next free one); m: their multiplicities
+        (variable-weight workloads), 1 each when None."""
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
         v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
         assert x.shape == v.shape
-        r = self._L.or_load(self._h, sp, x.shape[0], _dp(x), _dp(v))
+        if m is None:
+            r = self._L.or_load(self._h, sp, x.shape[0], _dp(x), _dp(v))
+        else:
+            m = np.ascontiguousarray(m, dtype=np.uint32).reshape(-1)
+            assert m.shape[0] == x.shape[0]
+            r = self._L.or_load_m(self._h, sp, x.shape[0], _dp(x), _dp(v), m.ctypes.data_as(C.POINTER(C.c_uint32)))
         if r != 0:
-            raise ValueError("bad species")
+            raise ValueError("bad species or multiplicities")
+
+    def multiplicity(self, sp):
+        """Multiplicities of species sp in store order (the order of particles())."""
+        out = np.zeros(self.count(sp), dtype=np.uint32)
+        self._L.or_get_multiplicity(self._h, sp, out.ctypes.data_as(C.POINTER(C.c_uint32)))
+        return out
 
     def step(self, n=1):
         for _ in range(n):

@@ -151,6 +151,7 @@ typedef struct {
   int64_t n, cap;
   double *x, *y, *z, *vx, *vy, *vz;
   uint32_t* pid;
+  uint32_t* mw; /* multiplicity: the particle stands for mw x w physical particles (1 unless uploaded otherwise) */
 } or_store_t;
 
 /* Public configuration (mirrors nothing in the GPU library; plain fields). */
@@ -165,6 +166,7 @@ typedef struct {
   int32_t nsp;
   double q[OR_MAXSP], m[OR_MAXSP], w[OR_MAXSP];
   int32_t role[OR_MAXSP];
+  int32_t variable_weights; /* 1: particles carry multiplicities (events between unequal ones split) */
 } or_cfg_t;
 
 typedef struct {
@@ -241,20 +243,22 @@ static void store_reserve(or_store_t* s, int64_t need) {
   s->vy = realloc(s->vy, cap * sizeof(double));
   s->vz = realloc(s->vz, cap * sizeof(double));
   s->pid = realloc(s->pid, cap * sizeof(uint32_t));
+  s->mw = realloc(s->mw, cap * sizeof(uint32_t));
   s->cap = cap;
 }
 
 static void store_push(or_store_t* s, double x, double y, double z, double vx, double vy, double vz,
-                       uint32_t pid) {
+                       uint32_t pid, uint32_t mw) {
   store_reserve(s, s->n + 1);
   int64_t i = s->n++;
   s->x[i] = x; s->y[i] = y; s->z[i] = z;
   s->vx[i] = vx; s->vy[i] = vy; s->vz[i] = vz;
   s->pid[i] = pid;
+  s->mw[i] = mw;
 }
 
 static void store_free(or_store_t* s) {
-  free(s->x); free(s->y); free(s->z); free(s->vx); free(s->vy); free(s->vz); free(s->pid);
+  free(s->x); free(s->y); free(s->z); free(s->vx); free(s->vy); free(s->vz); free(s->pid); free(s->mw);
   memset(s, 0, sizeof(*s));
 }
 
@@ -321,17 +325,29 @@ int or_set_source(or_state_t* s, int q, double flux, double T) {
 
 void or_set_background_density(or_state_t* s, double n) { s->bg_density = n; }
 
-/* Append particles; pids are assigned from next_pid in array order. */
-int or_load(or_state_t* s, int sp, int64_t n, const double* x, const double* v) {
+/* Append particles; pids are assigned from next_pid in array order. mw: their
+ * multiplicities (NULL: 1 each; other than 1 only with variable_weights). */
+int or_load_m(or_state_t* s, int sp, int64_t n, const double* x, const double* v, const uint32_t* mw) {
   if (sp < 0 || sp >= s->c.nsp) return -1;
   for (int64_t i = 0; i < n; ++i) {
+    if (mw && (mw[i] == 0 || (mw[i] != 1 && !s->c.variable_weights))) return -1;
+  }
+  for (int64_t i = 0; i < n; ++i) {
     store_push(&s->st[sp], x[3 * i], x[3 * i + 1], x[3 * i + 2], v[3 * i], v[3 * i + 1], v[3 * i + 2],
-               s->next_pid++);
+               s->next_pid++, mw ? mw[i] : 1u);
   }
   return 0;
 }
+int or_load(or_state_t* s, int sp, int64_t n, const double* x, const double* v) {
+  return or_load_m(s, sp, n, x, v, NULL);
+}
 
 int64_t or_count(const or_state_t* s, int sp) { return s->st[sp].n; }
+
+void or_get_multiplicity(const or_state_t* s, int sp, uint32_t* out) {
+  const or_store_t* t = &s->st[sp];
+  for (int64_t i = 0; i < t->n; ++i) out[i] = t->mw[i];
+}
 
 void or_get_particles(const or_state_t* s, int sp, double* x, double* v, uint32_t* pid) {
   const or_store_t* t = &s->st[sp];
@@ -461,7 +477,7 @@ int64_t or_inject(or_state_t* s) {
       double n3 = sqrt(-2.0 * log(d2.u0)) * cos(2.0 * OR_PI * d2.u1);
       double vx = sig * n1, vy = sig * n2, vz = sig * fabs(n3);
       double z = d3.u0 * vz * s->c.dt;
-      store_push(&s->st[src->species], x, y, z, vx, vy, vz, pid);
+      store_push(&s->st[src->species], x, y, z, vx, vy, vz, pid, 1u);
       s->mom.injected[src->species] += 1;
     }
     total += n;
@@ -501,6 +517,7 @@ void or_sort(or_state_t* s) {
       u.x[i] = t->x[o]; u.y[i] = t->y[o]; u.z[i] = t->z[o];
       u.vx[i] = t->vx[o]; u.vy[i] = t->vy[o]; u.vz[i] = t->vz[o];
       u.pid[i] = t->pid[o];
+      u.mw[i] = t->mw[o];
     }
     u.n = n;
     int64_t* cs = s->cell_start[sp];
@@ -527,7 +544,7 @@ void or_deposit(or_state_t* s) {
     or_store_t* t = &s->st[sp];
     if (s->sp[sp].role == OR_NEUTRAL) {
       memset(s->ncount[sp], 0, s->ncell * sizeof(int32_t));
-      for (int64_t p = 0; p < t->n; ++p) s->ncount[sp][cell_of(s, t->x[p], t->y[p], t->z[p])] += 1;
+      for (int64_t p = 0; p < t->n; ++p) s->ncount[sp][cell_of(s, t->x[p], t->y[p], t->z[p])] += (int32_t)t->mw[p];
     }
     double qw = s->sp[sp].q * s->sp[sp].w * inv_h3;
     if (qw == 0.0) continue;
@@ -541,7 +558,7 @@ void or_deposit(or_state_t* s) {
       for (int c = 0; c < 2; ++c)
         for (int b = 0; b < 2; ++b)
           for (int a = 0; a < 2; ++a)
-            s->rho[nidx(s, ic[a], jc[b], kc[c])] += qw * (wx[a] * wy[b] * wz[c]);
+            s->rho[nidx(s, ic[a], jc[b], kc[c])] += qw * ((double)t->mw[p] * (wx[a] * wy[b] * wz[c]));
     }
   }
 }
@@ -554,7 +571,7 @@ void or_deposit_points(int nx, int ny, int nz, double h, int64_t n, const double
   c.nx = nx; c.ny = ny; c.nz = nz; c.h = h; c.nsp = 1;
   c.q[0] = qw_total_per_particle; c.m[0] = 1.0; c.w[0] = 1.0; c.role[0] = OR_ELECTRON;
   or_state_t* s = or_create(&c);
-  for (int64_t p = 0; p < n; ++p) store_push(&s->st[0], xyz[3 * p], xyz[3 * p + 1], xyz[3 * p + 2], 0, 0, 0, (uint32_t)p);
+  for (int64_t p = 0; p < n; ++p) store_push(&s->st[0], xyz[3 * p], xyz[3 * p + 1], xyz[3 * p + 2], 0, 0, 0, (uint32_t)p, 1u);
   or_deposit(s);
   memcpy(rho_out, s->rho, s->nnode * sizeof(double));
   or_destroy(s);
@@ -904,9 +921,10 @@ void or_push_collide_resolve(or_state_t* s) {
       if (st == 1 || st == 2) {
         dead[sp][p] = 1;
         const double v2 = t->vx[p] * t->vx[p] + t->vy[p] * t->vy[p] + t->vz[p] * t->vz[p];
-        double ke = 0.5 * S->m * S->w * v2;
+        const double mwp = (double)t->mw[p];
+        double ke = 0.5 * S->m * S->w * (mwp * v2);
         if (st == 1) {
-          s->mom.abs_cathode[sp] += 1; s->mom.abs_energy_cathode[sp] += ke; q_cath += S->q * S->w;
+          s->mom.abs_cathode[sp] += 1; s->mom.abs_energy_cathode[sp] += ke; q_cath += S->q * S->w * mwp;
           if (S->role == OR_ION) {
             /* z^n >= 0 > z^{n+1}, so vz < 0: the path meets z = 0 at x^n - v z^n / vz */
             const double f = t->z[p] / t->vz[p];
@@ -914,7 +932,7 @@ void or_push_collide_resolve(or_state_t* s) {
                     t->vx[p], t->vy[p], t->vz[p]);
           }
         }
-        else { s->mom.abs_anode[sp] += 1; s->mom.abs_energy_anode[sp] += ke; q_anode += S->q * S->w; }
+        else { s->mom.abs_anode[sp] += 1; s->mom.abs_energy_anode[sp] += ke; q_anode += S->q * S->w * mwp; }
       } else if (st == 3) {
         s->mom.n_elastic += 1;
       } else if (st == 4) {
@@ -963,52 +981,96 @@ void or_push_collide_resolve(or_state_t* s) {
     free(cd);
     a0 = a1;
   }
-  /* apply in order of primary pid; secondaries take pids in that order */
+  /* apply in order of primary pid; secondaries take pids in that order.
+   * Events between unequal multiplicities (variable weights): the event moves
+   * ms = min(multiplicity of the primary, of the victim); the partner holding
+   * more keeps the rest in place, and the part that changes species becomes a
+   * new particle of multiplicity ms with a pid of its own. Successful events
+   * are numbered r in the order ionizations (by primary pid), then charge
+   * exchanges (by primary pid); a secondary takes pid0 + r, the victim's new
+   * ion pid0 + ns + 2r, an exchanging ion's new neutral pid0 + ns + 2r + 1
+   * (ns successful events; 3 ns pids are consumed). The primary electron of
+   * an ionization that moves less than its whole multiplicity loses the
+   * ionization energy with probability ms / multiplicity (a uniform of the
+   * ionization draw), so energy is conserved on average and charge and
+   * particle numbers exactly. With every multiplicity 1 this is the plain
+   * rule (and pid0 + nion pids are consumed). */
   qsort(ev, nev, sizeof(or_event_t), cmp_event_pid);
   s->nlog = 0;
   free(s->log);
   s->log = malloc((nev ? nev : 1) * 3 * sizeof(uint32_t));
+  const int vw = s->c.variable_weights;
+  const uint32_t pid0 = s->next_pid;
+  int64_t ns = 0, nion_s = 0;
+  for (int64_t a = 0; a < nev; ++a) {
+    if (ev[a].victim < 0) continue;
+    ++ns;
+    if (s->xs[ev[a].ch].kind != OR_XS_CX) ++nion_s;
+  }
+  int64_t ri = 0, rc = 0;
   for (int64_t a = 0; a < nev; ++a) {
     or_event_t* e = &ev[a];
     if (e->victim < 0) { s->mom.n_suppressed += 1; continue; }
     const or_xsec_t* X = &s->xs[e->ch];
     or_store_t* Ep = &s->st[e->proj];
     or_store_t* T = &s->st[X->target];
+    const int64_t p = e->e_idx, vi = e->victim;
+    const uint32_t mp = Ep->mw[p], mv = T->mw[vi];
+    const uint32_t ms = mp < mv ? mp : mv;
     if (X->kind == OR_XS_CX) {
       /* the ion becomes a neutral of the product species and the victim
        * neutral becomes an ion of the projectile species; both keep x^{n+1},
-       * v^{n+1/2} and their pids */
-      int64_t p = e->e_idx, vi = e->victim;
-      store_push(&s->st[X->product], Ep->x[p], Ep->y[p], Ep->z[p], Ep->vx[p], Ep->vy[p], Ep->vz[p], Ep->pid[p]);
-      store_push(Ep, T->x[vi], T->y[vi], T->z[vi], T->vx[vi], T->vy[vi], T->vz[vi], T->pid[vi]);
-      dead[e->proj][p] = 1;
-      dead[X->target][vi] = 1;
+       * v^{n+1/2} and their pids (with unequal multiplicities: the part ms) */
+      const int64_t r = nion_s + rc++;
+      if (ms == mp) {
+        store_push(&s->st[X->product], Ep->x[p], Ep->y[p], Ep->z[p], Ep->vx[p], Ep->vy[p], Ep->vz[p], Ep->pid[p], ms);
+        dead[e->proj][p] = 1;
+      } else {
+        store_push(&s->st[X->product], Ep->x[p], Ep->y[p], Ep->z[p], Ep->vx[p], Ep->vy[p], Ep->vz[p],
+                   pid0 + (uint32_t)(ns + 2 * r + 1), ms);
+        Ep->mw[p] = mp - ms;
+      }
+      if (ms == mv) {
+        store_push(Ep, T->x[vi], T->y[vi], T->z[vi], T->vx[vi], T->vy[vi], T->vz[vi], T->pid[vi], ms);
+        dead[X->target][vi] = 1;
+      } else {
+        store_push(Ep, T->x[vi], T->y[vi], T->z[vi], T->vx[vi], T->vy[vi], T->vz[vi], pid0 + (uint32_t)(ns + 2 * r), ms);
+        T->mw[vi] = mv - ms;
+      }
       s->mom.n_cx += 1;
       continue;
     }
+    const int64_t r = ri++;
     const double me = s->sp[e->proj].m;
-    int64_t p = e->e_idx;
     draw2 g0 = draw(s->c.seed, e->pid, s->step, TAG_IONIZE, 0);
     draw2 g1 = draw(s->c.seed, e->pid, s->step, TAG_IONIZE, 1);
     double Eex = e->E_eV - X->thr;            /* energy left after ionization */
     double E2 = g0.u0 * Eex;                  /* secondary */
     double E1 = (1.0 - g0.u0) * Eex;          /* primary, direction kept */
     double sc = sqrt(E1 / e->E_eV);
-    Ep->vx[p] *= sc; Ep->vy[p] *= sc; Ep->vz[p] *= sc;
+    if (ms == mp || g1.u1 < (double)ms / (double)mp) {
+      Ep->vx[p] *= sc; Ep->vy[p] *= sc; Ep->vz[p] *= sc;
+    }
     double us = sqrt(2.0 * E2 * OR_QE / me);
     double ct = 2.0 * g0.u1 - 1.0;
     double st = sqrt(fmax(0.0, 1.0 - ct * ct));
     double ph = 2.0 * OR_PI * g1.u0;
-    uint32_t spid = s->next_pid++;
-    store_push(Ep, Ep->x[p], Ep->y[p], Ep->z[p], us * st * cos(ph), us * st * sin(ph), us * ct, spid);
+    uint32_t spid = pid0 + (uint32_t)r;
+    store_push(Ep, Ep->x[p], Ep->y[p], Ep->z[p], us * st * cos(ph), us * st * sin(ph), us * ct, spid, ms);
     /* the victim neutral becomes an ion at its new position with its velocity */
-    int64_t vi = e->victim;
-    store_push(&s->st[X->product], T->x[vi], T->y[vi], T->z[vi], T->vx[vi], T->vy[vi], T->vz[vi], T->pid[vi]);
-    dead[X->target][vi] = 1;
+    if (ms == mv) {
+      store_push(&s->st[X->product], T->x[vi], T->y[vi], T->z[vi], T->vx[vi], T->vy[vi], T->vz[vi], T->pid[vi], ms);
+      dead[X->target][vi] = 1;
+    } else {
+      store_push(&s->st[X->product], T->x[vi], T->y[vi], T->z[vi], T->vx[vi], T->vy[vi], T->vz[vi],
+                 pid0 + (uint32_t)(ns + 2 * r), ms);
+      T->mw[vi] = mv - ms;
+    }
     s->log[3 * s->nlog] = e->pid; s->log[3 * s->nlog + 1] = T->pid[vi]; s->log[3 * s->nlog + 2] = spid;
     s->nlog++;
     s->mom.n_ionization += 1;
   }
+  s->next_pid = pid0 + (uint32_t)(vw ? 3 * ns : nion_s);
   free(ev);
 
   /* a10: compaction. The dead flags cover the pre-step population; entries
@@ -1021,6 +1083,7 @@ void or_push_collide_resolve(or_state_t* s) {
       t->x[w] = t->x[p]; t->y[w] = t->y[p]; t->z[w] = t->z[p];
       t->vx[w] = t->vx[p]; t->vy[w] = t->vy[p]; t->vz[w] = t->vz[p];
       t->pid[w] = t->pid[p];
+      t->mw[w] = t->mw[p];
       ++w;
     }
     t->n = w;
@@ -1042,11 +1105,13 @@ void or_compute_moments(or_state_t* s) {
   for (int sp = 0; sp < s->c.nsp; ++sp) {
     or_store_t* t = &s->st[sp];
     s->mom.count[sp] = t->n;
-    double ke = 0.0;
-    for (int64_t p = 0; p < t->n; ++p)
-      ke += t->vx[p] * t->vx[p] + t->vy[p] * t->vy[p] + t->vz[p] * t->vz[p];
+    double ke = 0.0, nphys = 0.0;
+    for (int64_t p = 0; p < t->n; ++p) {
+      ke += (double)t->mw[p] * (t->vx[p] * t->vx[p] + t->vy[p] * t->vy[p] + t->vz[p] * t->vz[p]);
+      nphys += (double)t->mw[p];
+    }
     s->mom.kinetic[sp] = 0.5 * s->sp[sp].m * s->sp[sp].w * ke;
-    qt += s->sp[sp].q * s->sp[sp].w * (double)t->n;
+    qt += s->sp[sp].q * s->sp[sp].w * nphys;
   }
   s->mom.total_charge = qt;
   int nx = s->c.nx, ny = s->c.ny, nz = s->c.nz;

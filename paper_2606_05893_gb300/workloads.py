@@ -90,9 +90,13 @@ class Workload:
     cg_rtol: float = 1e-8
     cg_maxit: int = 200
     rho_background: float = 0.0
-    # preloaded particles per species: (x[n,3], v[n,3]) float64
+    # preloaded particles per species: (x[n,3], v[n,3]) float64, or with
+    # variable weights (x, v, m[n]) with m the integer multiplicities
     preload: Optional[list] = None
     steps: int = 1000
+    # particles carry integer multiplicities (each stands for m x the species
+    # weight); events between unequal multiplicities split the heavier partner
+    variable_weights: bool = False
 
     @property
     def L(self):
@@ -102,6 +106,13 @@ class Workload:
         if not self.preload:
             return 0
         return int(sum(p[0].shape[0] for p in self.preload))
+
+    def n_physical(self):
+        """Physical particles the preload stands for, per species (multiplicity x weight)."""
+        if not self.preload:
+            return [0.0] * len(self.species)
+        return [float((p[2].sum() if len(p) > 2 else p[0].shape[0]) * sp.weight)
+                for p, sp in zip(self.preload, self.species)]
 
 
 def lotz_table(n: int = 2048, E_max: float = 1e5, P: float = CU_IONIZATION_EV):

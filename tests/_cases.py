@@ -119,3 +119,28 @@ def cx_cells_case(seed=21, sigma_cx=1e-10, sigma_ion=None, capacity=1 << 14, wit
         xe, ve = np.zeros((0, 3)), np.zeros((0, 3))
     wl.preload = [(xe, ve), (xn, vn), (xi, vi)]
     return wl
+
+
+def weighted_ionization_case(seed=3, m_e=(1, 4), m_n=(1, 4), E_eV=100.0, sigma_ion=1e-17, n_dense_e=300,
+                             n_dense_n=400):
+    """ionization_cells_case with variable weights: every electron and neutral
+    carries a multiplicity drawn uniformly from the given inclusive range, and
+    every ion the multiplicity of the electron it sits on (zero net charge at
+    t = 0)."""
+    wl = ionization_cells_case(seed=seed, sigma_ion=sigma_ion, E_eV=E_eV, n_dense_e=n_dense_e, n_dense_n=n_dense_n)
+    wl.variable_weights = True
+    rng = np.random.default_rng(seed + 1000)
+    (xe, ve), (xn, vn), (xi, vi) = wl.preload
+    me = rng.integers(m_e[0], m_e[1] + 1, xe.shape[0]).astype(np.uint32)
+    mn = rng.integers(m_n[0], m_n[1] + 1, xn.shape[0]).astype(np.uint32)
+    wl.preload = [(xe, ve, me), (xn, vn, mn), (xi, vi, me.copy())]
+    return wl
+
+
+def with_multiplicities(wl, lo=1, hi=4, seed=0):
+    """The same workload with variable weights: each preloaded particle gets a
+    multiplicity drawn uniformly from [lo, hi]."""
+    wl.variable_weights = True
+    rng = np.random.default_rng(seed)
+    wl.preload = [(p[0], p[1], rng.integers(lo, hi + 1, p[0].shape[0]).astype(np.uint32)) for p in wl.preload]
+    return wl
