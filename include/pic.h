@@ -125,6 +125,8 @@ typedef struct {
   int32_t nxsec;           /* 0..PIC_MAX_XSEC */
   const pic_xsec* xsec;
   int32_t warm_start;      /* PIC_WARM_PREV (previous phi) | PIC_WARM_ZERO */
+  int32_t variable_weights; /* 0 | 1: superparticles carry integer multiplicities
+                               (pic_inject_particles_m); see below */
 } pic_instance_cfg;
 
 /* Moments of one instance (a11). Cumulative counters run from pic_create. */
@@ -207,6 +209,34 @@ pic_status pic_inject(pic_handle* h, int32_t inst, int32_t species, double cx, d
  * would overflow (nothing is appended then). */
 pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n,
                                 const double* x, const double* v);
+
+/* Variable weights (the PIC/MCC paragraph's superparticles of weight w_SP,
+ * with the weight per particle an integer multiple mw >= 1 of the species'
+ * weight). Only for an instance created with variable_weights = 1.
+ * The particle's deposit, neutral count, absorbed charge and energy,
+ * kinetic energy and total charge are weighted by mw; the counts of
+ * superparticles and events are not. An ionization or charge exchange moves
+ * ms = min(mw of the primary, mw of the victim) physical multiples: the partner
+ * with more keeps the rest in place, and the part that changes species
+ * becomes a new superparticle of multiplicity ms with a pid of its own.
+ * Successful events are numbered r: ionizations by primary pid, then
+ * charge exchanges by primary pid. The secondary electron takes pid0 + r, the
+ * victim's new ion pid0 + ns + 2r, and the exchanging ion's new neutral pid0 +
+ * ns + 2r + 1, where pid0 is next_pid before the step and ns the successful
+ * events. next_pid advances by 3 ns. A primary electron that moves less than
+ * its whole multiplicity loses the ionization energy with probability ms / mw
+ * (the second uniform of the ionization's second draw): energy is conserved on
+ * average, charge and particle numbers exactly. pic_save and pic_load refuse
+ * such instances (PIC_EINVAL).
+ * pic_inject_particles_m: as pic_inject_particles, with mw[n] (host, copied).
+ * PIC_EINVAL if mw is NULL or an mw[i] is 0, or above 1 on an instance
+ * without variable weights. The call synchronises the stream.
+ * pic_get_multiplicity: the multiplicities of a species' live particles in the
+ * order pic_get_particles gives (cap, *n and errors as there). */
+pic_status pic_inject_particles_m(pic_handle* h, int32_t inst, int32_t species, int64_t n,
+                                  const double* x, const double* v, const uint32_t* mw);
+pic_status pic_get_multiplicity(pic_handle* h, int32_t inst, int32_t species, int64_t cap, int64_t* n,
+                                uint32_t* mw);
 
 /* Advance every instance by nsteps PIC steps of length dt (the PIC/MCC
  * paragraph: the field of Eq. (1) from the deposited charge, the push by

@@ -54,7 +54,8 @@ class pic_instance_cfg(C.Structure):
                 ("seed", C.c_uint64),
                 ("nspecies", C.c_int32), ("species", C.POINTER(pic_species)),
                 ("nxsec", C.c_int32), ("xsec", C.POINTER(pic_xsec)),
-                ("warm_start", C.c_int32)]
+                ("warm_start", C.c_int32),
+                ("variable_weights", C.c_int32)]
 
 
 class pic_moments_t(C.Structure):
@@ -80,7 +81,8 @@ PHASES = ["inject", "sort", "deposit", "solve", "efield", "push_electron", "push
 PIC_NPHASES = len(PHASES)
 
 
-EXPORTED = ["pic_create", "pic_inject", "pic_inject_particles", "pic_step", "pic_moments", "pic_destroy",
+EXPORTED = ["pic_create", "pic_inject", "pic_inject_particles", "pic_inject_particles_m", "pic_get_multiplicity",
+            "pic_step", "pic_moments", "pic_destroy",
             "pic_last_error", "pic_get_count", "pic_get_particles", "pic_get_field", "pic_set_phi", "pic_solve",
             "pic_sort_now", "pic_get_cell_start", "pic_get_ionization_log", "pic_philox",
             "pic_set_mcc_background", "pic_version", "pic_set_profiling", "pic_get_phase_times",
@@ -124,6 +126,8 @@ def load_library(path: str = None):
         "pic_create": ([C.POINTER(pic_instance_cfg), C.c_int32, P, C.POINTER(P)], st),
         "pic_inject": ([P, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double], st),
         "pic_inject_particles": ([P, C.c_int32, C.c_int32, C.c_int64, d, d], st),
+        "pic_inject_particles_m": ([P, C.c_int32, C.c_int32, C.c_int64, d, d, u32], st),
+        "pic_get_multiplicity": ([P, C.c_int32, C.c_int32, C.c_int64, i64, u32], st),
         "pic_step": ([P, C.c_int32], st),
         "pic_moments": ([P, C.c_int32, C.POINTER(pic_moments_t)], st),
         "pic_destroy": ([P], st),
@@ -220,6 +224,25 @@ def pic_inject_particles(h, inst, species, x, v):
     if x.shape != v.shape:
         raise ValueError("x and v must have the same shape [n, 3]")
     return _check(h, load_library().pic_inject_particles(h, inst, species, x.shape[0], _dp(x), _dp(v)))
+
+
+def pic_inject_particles_m(h, inst, species, x, v, mw):
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+    mw = np.ascontiguousarray(mw, dtype=np.uint32).reshape(-1)
+    if x.shape != v.shape or mw.shape[0] != x.shape[0]:
+        raise ValueError("x, v must have the shape [n, 3] and mw [n]")
+    return _check(h, load_library().pic_inject_particles_m(h, inst, species, x.shape[0], _dp(x), _dp(v),
+                                                           mw.ctypes.data_as(C.POINTER(C.c_uint32))))
+
+
+def pic_get_multiplicity(h, inst, species):
+    n = pic_get_count(h, inst, species)
+    mw = np.zeros(max(n, 1), dtype=np.uint32)
+    got = C.c_int64()
+    _check(h, load_library().pic_get_multiplicity(h, inst, species, mw.shape[0], C.byref(got),
+                                                  mw.ctypes.data_as(C.POINTER(C.c_uint32))))
+    return mw[:got.value]
 
 
 def pic_step(h, nsteps=1, check=True):
@@ -638,6 +661,7 @@ class _CfgHolder:
         c.nxsec = len(wl.xsec)
         c.xsec = xs
         c.warm_start = warm_start
+        c.variable_weights = 1 if getattr(wl, "variable_weights", False) else 0
         self.sp, self.xs, self.cfg = sp, xs, c
 
 
@@ -658,9 +682,13 @@ class Simulation:
             if background_density > 0:
                 pic_set_mcc_background(self.h, i, background_density)
             if preload and w.preload:
-                for sp, (x, v) in enumerate(w.preload):
-                    if len(x):
-                        pic_inject_particles(self.h, i, sp, x, v)
+                for sp, pre in enumerate(w.preload):
+                    if not len(pre[0]):
+                        continue
+                    if len(pre) == 3:  # with multiplicities
+                        pic_inject_particles_m(self.h, i, sp, pre[0], pre[1], pre[2])
+                    else:
+                        pic_inject_particles(self.h, i, sp, pre[0], pre[1])
 
     def save(self, path, inst=0):
         """Checkpoint of one instance (pic_save)."""
@@ -702,6 +730,9 @@ class Simulation:
 
     def particles(self, sp, inst=0):
         return pic_get_particles(self.h, inst, sp)
+
+    def multiplicity(self, sp, inst=0):
+        return pic_get_multiplicity(self.h, inst, sp)
 
     def count(self, sp, inst=0):
         return pic_get_count(self.h, inst, sp)

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kDepBlock) k_deposit_fp64(DepositArgs<Store64>
       cell = (int)p.cell;
       corner_nodes(g, p.l.i, p.l.j, p.l.k, idx);
       cic_weights(p.l.fx, p.l.fy, p.l.fz, w);
-      const double q = p.pid != kPidDead ? a.qw_h3 : 0.0;  // tombstones carry no charge
+      const double q = p.pid != kPidDead ? a.qw_h3 * (double)p.mw : 0.0;  // tombstones carry no charge
 #pragma unroll
       for (int c = 0; c < 8; ++c) w[c] *= q;
     }
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kDepBlock) k_deposit_mx(DepositArgs<StoreMx> a
     if (valid) {
       cell = a.st.cell[i];
       cic_weights(a.st.ox[i], a.st.oy[i], a.st.oz[i], w);
-      const float qi = a.st.pid[i] != kPidDead ? q : 0.f;  // tombstones carry no charge
+      const float qi = a.st.pid[i] != kPidDead ? q * (float)(a.st.mw ? a.st.mw[i] : 1u) : 0.f;  // tombstones carry no charge
 #pragma unroll
       for (int c = 0; c < 8; ++c) w[c] *= qi;
     }
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kDepBlock) k_count_neutrals(DepositArgs<S> a) 
       const auto p = store_read(a.st, g, i);
       if (PIC_BOUNDS(particle_cell(p) >= 0 && particle_cell(p) < g.ncell, a.cnt)) {
         cell = (int)particle_cell(p);
-        one[0] = p.pid != kPidDead ? 1.f : 0.f;
+        one[0] = p.pid != kPidDead ? (float)p.mw : 0.f;  // multiplicities: exact in FP32 below 2^24 per warp
       }
     }
     if (warp_run_sum(cell, one) && cell >= 0 && one[0] > 0.f) atomicAdd(&a.ncount[cell], (int)one[0]);
@@ -372,17 +372,18 @@ void launch_step_begin(DevCounters* cnt, const int* out_buf, int nsp, cudaStream
 // ---------------------------------------------------------------------------
 template <class S>
 __global__ void k_load(Grid g, S st, DevCounters* cnt, int cur, int species, long long cap, const double* __restrict__ x,
-                       const double* __restrict__ v, long long n, NextDeposit nd, int neutral) {
+                       const double* __restrict__ v, const uint32_t* __restrict__ mw, long long n, NextDeposit nd,
+                       int neutral) {
   const unsigned long long base = cnt->n[cur][species];
   const uint32_t pid0 = cnt->next_pid;
   for (long long i = gtid(); i < n; i += gstride()) {
     const unsigned long long slot = base + i;
     if (slot >= (unsigned long long)cap) continue;
     store_write(st, g, slot, x[3 * i], x[3 * i + 1], x[3 * i + 2], v[3 * i], v[3 * i + 1], v[3 * i + 2],
-                pid0 + (uint32_t)i);
+                pid0 + (uint32_t)i, mw ? mw[i] : 1u);
     if (nd.on) {  // the next step's deposit is being accumulated: add this particle
       const auto p = store_read(st, g, slot);
-      if (neutral) atomicAdd(&nd.ncount[species][cell_now(g, p)], 1);
+      if (neutral) atomicAdd(&nd.ncount[species][cell_now(g, p)], (int)p.mw);
       else if (nd.qw_h3[species] != 0.0) deposit_one(g, p, nd.rho32, nd.rho64, nd.qw_h3[species]);
     }
   }
@@ -396,27 +397,33 @@ __global__ void k_load_commit(DevCounters* cnt, int cur, int species, long long 
 }
 template <class S>
 void launch_load(const Grid& g, S st, DevCounters* cnt, int cur, int species, long long cap, const double* x,
-                 const double* v, long long n, const NextDeposit& nd, int neutral, cudaStream_t s) {
+                 const double* v, const uint32_t* mw, long long n, const NextDeposit& nd, int neutral, cudaStream_t s) {
   if (n <= 0) return;
-  PIC_LAUNCH(grid_for(n), kBlock, 0, s, k_load<S>)(g, st, cnt, cur, species, cap, x, v, n, nd, neutral);
+  PIC_LAUNCH(grid_for(n), kBlock, 0, s, k_load<S>)(g, st, cnt, cur, species, cap, x, v, mw, n, nd, neutral);
   PIC_LAUNCH(1, 1, 0, s, k_load_commit)(cnt, cur, species, n, cap);
 }
 
 template <class S>
-__global__ void k_download(Grid g, S st, long long n, double* x, double* v, uint32_t* pid) {
-  for (long long i = gtid(); i < n; i += gstride()) store_get(st, g, i, x + 3 * i, v + 3 * i, pid + i);
+__global__ void k_download(Grid g, S st, long long n, double* x, double* v, uint32_t* pid, uint32_t* mw) {
+  for (long long i = gtid(); i < n; i += gstride()) {
+    store_get(st, g, i, x + 3 * i, v + 3 * i, pid + i);
+    if (mw) mw[i] = st.mw ? st.mw[i] : 1u;
+  }
 }
 template <class S>
-void launch_download(const Grid& g, S st, long long n, double* x, double* v, uint32_t* pid, cudaStream_t s) {
+void launch_download(const Grid& g, S st, long long n, double* x, double* v, uint32_t* pid, uint32_t* mw,
+                     cudaStream_t s) {
   if (n <= 0) return;
-  PIC_LAUNCH(grid_for(n), kBlock, 0, s, k_download<S>)(g, st, n, x, v, pid);
+  PIC_LAUNCH(grid_for(n), kBlock, 0, s, k_download<S>)(g, st, n, x, v, pid, mw);
 }
 template void launch_load<Store64>(const Grid&, Store64, DevCounters*, int, int, long long, const double*,
-                                   const double*, long long, const NextDeposit&, int, cudaStream_t);
+                                   const double*, const uint32_t*, long long, const NextDeposit&, int, cudaStream_t);
 template void launch_load<StoreMx>(const Grid&, StoreMx, DevCounters*, int, int, long long, const double*,
-                                   const double*, long long, const NextDeposit&, int, cudaStream_t);
-template void launch_download<Store64>(const Grid&, Store64, long long, double*, double*, uint32_t*, cudaStream_t);
-template void launch_download<StoreMx>(const Grid&, StoreMx, long long, double*, double*, uint32_t*, cudaStream_t);
+                                   const double*, const uint32_t*, long long, const NextDeposit&, int, cudaStream_t);
+template void launch_download<Store64>(const Grid&, Store64, long long, double*, double*, uint32_t*, uint32_t*,
+                                       cudaStream_t);
+template void launch_download<StoreMx>(const Grid&, StoreMx, long long, double*, double*, uint32_t*, uint32_t*,
+                                       cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // a2 helpers: sort keys (cell << pid_bits | pid; tombstones sort last) and the
@@ -489,6 +496,7 @@ __device__ __forceinline__ void copy_slot(const Store64& s, const Store64& d, lo
   d.vy[to] = s.vy[from];
   d.vz[to] = s.vz[from];
   d.pid[to] = s.pid[from];
+  if (d.mw) d.mw[to] = s.mw[from];
 }
 __device__ __forceinline__ void copy_slot(const StoreMx& s, const StoreMx& d, long long from, long long to) {
   d.cell[to] = s.cell[from];
@@ -499,6 +507,7 @@ __device__ __forceinline__ void copy_slot(const StoreMx& s, const StoreMx& d, lo
   d.vy[to] = s.vy[from];
   d.vz[to] = s.vz[from];
   d.pid[to] = s.pid[from];
+  if (d.mw) d.mw[to] = s.mw[from];
 }
 template <class S>
 __global__ void k_gather(S src, S dst, const uint32_t* __restrict__ perm, const unsigned long long* n_dev, long long n_max) {
@@ -577,6 +586,41 @@ __global__ void k_kinetic_mx(StoreMx st, const unsigned long long* n_dev, long l
   acc = block_sum(acc);
   if (threadIdx.x == 0) atomicAdd(out, acc);
 }
+// Variable weights: sum of mw |v|^2 into out[0] and of mw into out[1] (both in
+// FP64, |v|^2 from the stored velocities).
+__device__ __forceinline__ double stored_v2(const Store64& st, long long i) {
+  return st.vx[i] * st.vx[i] + st.vy[i] * st.vy[i] + st.vz[i] * st.vz[i];
+}
+__device__ __forceinline__ double stored_v2(const StoreMx& st, long long i) {
+  const double a = st.vx[i], b = st.vy[i], c = st.vz[i];
+  return a * a + b * b + c * c;
+}
+template <class S>
+__global__ void k_kinetic_w(S st, const unsigned long long* n_dev, long long n_max, double* out_v2, double* out_m) {
+  const long long n = min((long long)*n_dev, n_max);
+  double acc = 0.0, m = 0.0;
+  for (long long i = gtid(); i < n; i += gstride()) {
+    if (st.pid[i] == kPidDead) continue;
+    const double w = (double)st.mw[i];
+    acc += w * stored_v2(st, i);
+    m += w;
+  }
+  acc = block_sum(acc);
+  __syncthreads();  // block_sum's shared buffer is reused
+  m = block_sum(m);
+  if (threadIdx.x == 0) {
+    atomicAdd(out_v2, acc);
+    atomicAdd(out_m, m);
+  }
+}
+template <class S>
+void launch_kinetic_w(S st, const unsigned long long* n_dev, long long n_max, double* out_v2, double* out_m,
+                      cudaStream_t s) {
+  PIC_LAUNCH(grid_for(n_max), kBlock, 0, s, k_kinetic_w<S>)(st, n_dev, n_max, out_v2, out_m);
+}
+template void launch_kinetic_w<Store64>(Store64, const unsigned long long*, long long, double*, double*, cudaStream_t);
+template void launch_kinetic_w<StoreMx>(StoreMx, const unsigned long long*, long long, double*, double*, cudaStream_t);
+
 template <class S>
 void launch_kinetic(S st, const unsigned long long* n_dev, long long n_max, double* out, cudaStream_t s);
 template <>

@@ -326,7 +326,7 @@ __device__ __forceinline__ void next_deposit(const PushArgs<StoreMx>& a, const P
     float w[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (stored) {
       cic_weights(p.ox, p.oy, p.oz, w);
-      const float q = (float)a.nd.qw_h3[a.species];
+      const float q = (float)a.nd.qw_h3[a.species] * (float)p.mw;
 #pragma unroll
       for (int c = 0; c < 8; ++c) w[c] *= q;
     }
@@ -349,13 +349,19 @@ __device__ __forceinline__ void next_deposit(const PushArgs<StoreMx>& a, const P
       cic_add_f32(a.nd.rho32, a.g, i, j, k, w, (a.g.nx & 3) == 0);
     }
   }
-  if (NEUTRAL && lead) atomicAdd(&a.nd.ncount[a.species][key], __popc(grp));
+  if (NEUTRAL) {
+    if (a.in.mw == nullptr) {
+      if (lead) atomicAdd(&a.nd.ncount[a.species][key], __popc(grp));
+    } else if (stored) {
+      atomicAdd(&a.nd.ncount[a.species][key], (int)p.mw);  // multiplicities
+    }
+  }
 }
 template <bool CHARGED, bool NEUTRAL>
 __device__ __forceinline__ void next_deposit(const PushArgs<Store64>& a, const Particle64& p, bool stored) {
   if (!stored) return;
   if (CHARGED) deposit_one(a.g, p, nullptr, a.nd.rho64, a.nd.qw_h3[a.species]);
-  if (NEUTRAL) atomicAdd(&a.nd.ncount[a.species][cell_now(a.g, p)], 1);
+  if (NEUTRAL) atomicAdd(&a.nd.ncount[a.species][cell_now(a.g, p)], (int)p.mw);
 }
 
 // One ion absorbed at the cathode into the hit log (rare: out of the push's
@@ -386,11 +392,13 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
   // per-thread tallies, each touched by its own thread only (no atomics, no
   // registers held): absorbed at cathode / anode, their sum of v^2, elastic
   // collisions; reduced once per block at the end
+  // (with variable weights v^2 is weighted by the multiplicity, and rows 3, 4
+  // sum the absorbed multiplicities for the charge)
   __shared__ double s_tv2[2][kPushBlock];
-  __shared__ unsigned int s_tn[3][kPushBlock];
+  __shared__ unsigned int s_tn[5][kPushBlock];
   const int tx = threadIdx.x;
   s_tv2[0][tx] = s_tv2[1][tx] = 0.0;
-  s_tn[0][tx] = s_tn[1][tx] = s_tn[2][tx] = 0u;
+  s_tn[0][tx] = s_tn[1][tx] = s_tn[2][tx] = s_tn[3][tx] = s_tn[4][tx] = 0u;
   const long long n = min((long long)a.cnt->n[a.cur_in][a.species], a.cap);
   const uint32_t step = a.cnt->step;
   if (blockIdx.x == 0 && threadIdx.x == 0)
@@ -429,7 +437,8 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
       if (side != 0) {
         const int b = side < 0 ? 0 : 1;
         s_tn[b][tx] += 1u;
-        s_tv2[b][tx] += p[u].v2();
+        s_tn[3 + b][tx] += p[u].mw;
+        s_tv2[b][tx] += (double)p[u].mw * p[u].v2();
         if (side < 0 && a.hits.n) {
           double xc, yc;
           p[u].cathode_point(g, xc, yc);
@@ -547,15 +556,19 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
   // v^2 only when the block absorbed something (FP64 is a narrow pipe on GB300)
   __syncthreads();
   if (warp == 0) {
-    unsigned int n0 = 0, n1 = 0, nel = 0;
+    unsigned int n0 = 0, n1 = 0, nel = 0, m0 = 0, m1 = 0;
     for (int t = lane; t < kPushBlock; t += 32) {
       n0 += s_tn[0][t];
       n1 += s_tn[1][t];
       nel += s_tn[2][t];
+      m0 += s_tn[3][t];
+      m1 += s_tn[4][t];
     }
     n0 = __reduce_add_sync(0xffffffffu, n0);
     n1 = __reduce_add_sync(0xffffffffu, n1);
     nel = __reduce_add_sync(0xffffffffu, nel);
+    m0 = __reduce_add_sync(0xffffffffu, m0);
+    m1 = __reduce_add_sync(0xffffffffu, m1);
     if (n0 + n1 > 0) {
       double v0 = 0.0, v1 = 0.0;
       for (int t = lane; t < kPushBlock; t += 32) {
@@ -573,12 +586,12 @@ __global__ void __launch_bounds__(kPushBlock, PTraits<S>::kMinBlocks) k_push(Pus
         if (n0) {
           atomicAdd(&a.cnt->abs_cathode[s], (unsigned long long)n0);
           atomicAdd(&a.cnt->abs_energy_cathode[s], ke * v0);
-          atomicAdd(&a.cnt->q_cathode_step, qw * (double)n0);
+          atomicAdd(&a.cnt->q_cathode_step, qw * (double)m0);
         }
         if (n1) {
           atomicAdd(&a.cnt->abs_anode[s], (unsigned long long)n1);
           atomicAdd(&a.cnt->abs_energy_anode[s], ke * v1);
-          atomicAdd(&a.cnt->q_anode_step, qw * (double)n1);
+          atomicAdd(&a.cnt->q_anode_step, qw * (double)m1);
         }
       }
     }
@@ -731,9 +744,12 @@ __device__ void resolve_commit(DevCounters* cnt, const ResolveCommit& c) {
   cnt->n[c.i_out][c.i_sp] = b > (unsigned long long)c.i_cap ? c.i_cap : b;
   const unsigned long long d = cnt->n[c.n_out][c.n_sp] + ncx;
   cnt->n[c.n_out][c.n_sp] = d > (unsigned long long)c.n_cap ? c.n_cap : d;
-  cnt->n_tomb[c.n_sp] = ns;
-  cnt->n_tomb[c.i_sp] = ncx;
-  cnt->next_pid += nion;
+  // tombstones: every victim and exchanging ion, or with variable weights the
+  // ones converted whole (the others only lost multiplicity)
+  cnt->n_tomb[c.n_sp] = c.weighted ? cnt->n_kill_n : ns;
+  cnt->n_tomb[c.i_sp] = c.weighted ? cnt->n_kill_i : ncx;
+  cnt->n_kill_n = cnt->n_kill_i = 0u;
+  cnt->next_pid += c.weighted ? 3u * ns : nion;
 }
 
 // Successful events in apply order: ionizations (rank r < nion) then charge
@@ -742,6 +758,13 @@ __device__ void resolve_commit(DevCounters* cnt, const ResolveCommit& c) {
 // slot from r, so secondaries take pids in increasing primary pid); an exchange
 // turns its primary ion into a neutral (slot nn_out + r - nion) and takes back
 // the charge the push deposited for it at x^{n+1}.
+// Variable weights: an event moves ms = min(multiplicity of the primary, of the
+// victim). The victim (or the exchanging ion) with more keeps the rest in its
+// slot and the moved part is written with a pid of its own (victim's part
+// pid0 + ns + 2r, exchanging ion's part pid0 + ns + 2r + 1); the secondary has
+// multiplicity ms; a primary electron moving less than its multiplicity loses
+// the ionization energy with probability ms / multiplicity (the second uniform
+// of the ionization's second draw).
 template <class S>
 __global__ void k_resolve_apply(ApplyArgs<S> a) {
   const unsigned int ns = a.cnt->n_success;
@@ -764,25 +787,43 @@ __global__ void k_resolve_apply(ApplyArgs<S> a) {
     if (!PIC_BOUNDS(cd.slot < (uint32_t)a.n_cap, a.cnt)) continue;
     // victim neutral -> ion (position x^{n+1}, velocity and pid kept)
     const auto vn = store_read(a.n_st, a.g, cd.slot);
+    const bool is_cx = r >= nion;
+    const uint32_t mp = a.commit.weighted ? (is_cx ? a.i_st.mw[ev.slot] : a.e_st.mw[ev.slot]) : 1u;
+    const uint32_t ms = min(mp, vn.mw);
+    auto vm = vn;  // the part that converts
+    if (ms == vn.mw) {
+      store_kill(a.n_st, cd.slot);
+      if (a.commit.weighted) atomicAdd(&a.cnt->n_kill_n, 1u);
+    } else {
+      a.n_st.mw[cd.slot] = vn.mw - ms;
+      vm.mw = ms;
+      vm.pid = pid0 + ns + 2u * (uint32_t)r;
+    }
     const unsigned long long is = ni_out + r;
     if (is < (unsigned long long)a.i_cap) {
-      store_write_p(a.i_st, is, vn);
-      if (a.nd.on) deposit_one(a.g, vn, a.nd.rho32, a.nd.rho64, a.nd.qw_h3[a.i_species]);
+      store_write_p(a.i_st, is, vm);
+      if (a.nd.on) deposit_one(a.g, vm, a.nd.rho32, a.nd.rho64, a.nd.qw_h3[a.i_species]);
     } else {
       atomicOr(&a.cnt->error, ERR_CAPACITY);
     }
-    store_kill(a.n_st, cd.slot);
-    if (a.nd.on) atomicSub(&a.nd.ncount[a.n_species][cell_now(a.g, vn)], 1);
-    if (r >= nion) {
+    if (a.nd.on) atomicSub(&a.nd.ncount[a.n_species][cell_now(a.g, vn)], (int)ms);
+    if (is_cx) {
       // charge exchange: the primary ion continues as a neutral
-      const auto pi = store_read(a.i_st, a.g, ev.slot);
-      store_kill(a.i_st, ev.slot);
+      auto pi = store_read(a.i_st, a.g, ev.slot);
+      if (ms == mp) {
+        store_kill(a.i_st, ev.slot);
+        if (a.commit.weighted) atomicAdd(&a.cnt->n_kill_i, 1u);
+      } else {
+        a.i_st.mw[ev.slot] = mp - ms;
+        pi.mw = ms;
+        pi.pid = pid0 + ns + 2u * (uint32_t)r + 1u;
+      }
       const unsigned long long os = nn_out + (r - nion);
       if (os < (unsigned long long)a.n_cap) {
         store_write_p(a.n_st, os, pi);
         if (a.nd.on) {
           deposit_one(a.g, pi, a.nd.rho32, a.nd.rho64, -a.nd.qw_h3[a.i_species]);
-          atomicAdd(&a.nd.ncount[a.n_species][cell_now(a.g, pi)], 1);
+          atomicAdd(&a.nd.ncount[a.n_species][cell_now(a.g, pi)], (int)ms);
         }
       } else {
         atomicOr(&a.cnt->error, ERR_CAPACITY);
@@ -799,8 +840,10 @@ __global__ void k_resolve_apply(ApplyArgs<S> a) {
     const double sc = sqrt(E1 / ev.E_eV);
     // primary: direction kept, energy (1-U) (E - thr)
     auto pr = store_read(a.e_st, a.g, ev.slot);
-    pr.scale_v(sc);
-    store_write_v(a.e_st, ev.slot, pr);
+    if (ms == mp || u01_64(g1.z, g1.w) < (double)ms / (double)mp) {
+      pr.scale_v(sc);
+      store_write_v(a.e_st, ev.slot, pr);
+    }
     // secondary at the primary's new position
     const double us = sqrt(2.0 * E2 * kQe / a.e_mass);
     const double ct = 2.0 * u01_64(g0.z, g0.w) - 1.0;
@@ -810,6 +853,7 @@ __global__ void k_resolve_apply(ApplyArgs<S> a) {
     auto sec = pr;
     sec.set_v(us * st * cos(ph), us * st * sin(ph), us * ct);
     sec.pid = spid;
+    sec.mw = ms;
     const unsigned long long es = ne_out + r;
     if (es < (unsigned long long)a.e_cap) {
       store_write_p(a.e_st, es, sec);

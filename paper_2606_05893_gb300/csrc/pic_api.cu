@@ -145,6 +145,7 @@ struct Instance {
   Grid g{};
   int nsp = 0;
   bool mixed = false;
+  bool weighted = false;  // variable weights: the stores carry multiplicities
   DevCounters* cnt = nullptr;
   DevCounters* host_cnt = nullptr;  // pinned mirror
   Store64 s64[kMaxSpecies][2]{};
@@ -223,6 +224,7 @@ struct Instance {
   cudaEvent_t done = nullptr;
   double* stage_x = nullptr;  // device staging of pic_inject_particles
   double* stage_v = nullptr;
+  uint32_t* stage_m = nullptr;  // multiplicities of an upload
   long long stage_cap = 0;
   // small uploads go through pinned host staging and return without waiting
   // for the device (kStageHost particles at most)
@@ -366,6 +368,7 @@ void free_instance(Instance* I) {
   cudaFree(I->mom_ticket);
   cudaFree(I->stage_x);
   cudaFree(I->stage_v);
+  cudaFree(I->stage_m);
   if (I->hstage) cudaFreeHost(I->hstage);
   if (I->hstage_done) cudaEventDestroy(I->hstage_done);
   I->timer.release();
@@ -399,6 +402,8 @@ pic_status validate(pic_handle* h, const pic_instance_cfg& c, int idx) {
   if (c.precision != PIC_FP64 && c.precision != PIC_MIXED) return fail(h, PIC_EINVAL, "instance %d: bad precision", idx);
   if (c.warm_start != PIC_WARM_PREV && c.warm_start != PIC_WARM_ZERO)
     return fail(h, PIC_EINVAL, "instance %d: bad warm_start", idx);
+  if (c.variable_weights != 0 && c.variable_weights != 1)
+    return fail(h, PIC_EINVAL, "instance %d: variable_weights must be 0 or 1", idx);
   if (!(c.cg_rtol > 0) || c.cg_maxit < 1) return fail(h, PIC_EINVAL, "instance %d: cg_rtol > 0 and cg_maxit >= 1 required", idx);
   if (c.sort_interval < 0) return fail(h, PIC_EINVAL, "instance %d: sort_interval >= 0 required", idx);
   for (int s = 0; s < c.nspecies; ++s) {
@@ -525,6 +530,7 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
   I->cfg.species = nullptr;
   I->cfg.xsec = nullptr;
   I->mixed = c.precision == PIC_MIXED;
+  I->weighted = c.variable_weights == 1;
   Grid& g = I->g;
   g.nx = c.nx;
   g.ny = c.ny;
@@ -579,7 +585,7 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
     maxcap = std::max(maxcap, cap);
     for (int b = 0; b < 2; ++b) {
       if (!I->mixed) {
-        const size_t bytes = (size_t)cap * (6 * sizeof(double) + sizeof(uint32_t));
+        const size_t bytes = (size_t)cap * (6 * sizeof(double) + (I->weighted ? 2 : 1) * sizeof(uint32_t));
         CK(h, cudaMalloc(&I->mem[s][b], bytes));
         char* p = (char*)I->mem[s][b];
         Store64& S = I->s64[s][b];
@@ -590,8 +596,9 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
         S.vy = S.vx + cap;
         S.vz = S.vy + cap;
         S.pid = (uint32_t*)(S.vz + cap);
+        S.mw = I->weighted ? S.pid + cap : nullptr;
       } else {
-        const size_t bytes = (size_t)cap * (sizeof(int32_t) + 6 * sizeof(float) + sizeof(uint32_t));
+        const size_t bytes = (size_t)cap * (sizeof(int32_t) + 6 * sizeof(float) + (I->weighted ? 2 : 1) * sizeof(uint32_t));
         CK(h, cudaMalloc(&I->mem[s][b], bytes));
         char* p = (char*)I->mem[s][b];
         StoreMx& S = I->smx[s][b];
@@ -603,6 +610,7 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
         S.vy = S.vx + cap;
         S.vz = S.vy + cap;
         S.pid = (uint32_t*)(S.vz + cap);
+        S.mw = I->weighted ? S.pid + cap : nullptr;
       }
     }
     if (I->species[s].role == PIC_NEUTRAL) {
@@ -1021,6 +1029,7 @@ pic_status step_instance(pic_handle* h, Instance* I) {
     rc.n_sp = n_sp;
     rc.n_cap = ap.n_cap;
     rc.ev_cap = I->ev_cap;
+    rc.weighted = I->weighted ? 1 : 0;
     launch_resolve_apply<S>(ap, rb, st);  // with the commit and the list-head reset
     T.end(st);
   }
@@ -1430,8 +1439,8 @@ pic_status pic_inject(pic_handle* h, int32_t inst, int32_t species, double cx, d
   return PIC_OK;
 }
 
-pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n, const double* x,
-                                const double* v) {
+static pic_status inject_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n, const double* x,
+                                   const double* v, const uint32_t* mw) {
   pic_status st = check(h, inst);
   if (st != PIC_OK) return st;
   Instance* I = h->inst[inst];
@@ -1444,6 +1453,9 @@ pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, in
       return fail(h, PIC_EINVAL, "particle %lld outside the domain", (long long)i);
     for (int c = 0; c < 3; ++c)
       if (!std::isfinite(v[3 * i + c])) return fail(h, PIC_EINVAL, "particle %lld has a non-finite velocity", (long long)i);
+    if (mw && (mw[i] == 0 || (mw[i] != 1 && !I->weighted)))
+      return fail(h, PIC_EINVAL, "particle %lld: multiplicity %u (must be >= 1, and 1 without variable weights)",
+                  (long long)i, mw[i]);
   }
   // the counters on the host are current unless device work changed them since
   // they were last read (a step, a sort)
@@ -1458,15 +1470,20 @@ pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, in
   if (n > I->stage_cap) {
     cudaFree(I->stage_x);
     cudaFree(I->stage_v);
+    cudaFree(I->stage_m);
     I->stage_x = I->stage_v = nullptr;
+    I->stage_m = nullptr;
     I->stage_cap = 0;
     CK(h, dalloc(&I->stage_x, 3 * (size_t)std::max<long long>(n, kStageHost)));
     CK(h, dalloc(&I->stage_v, 3 * (size_t)std::max<long long>(n, kStageHost)));
+    CK(h, dalloc(&I->stage_m, (size_t)std::max<long long>(n, kStageHost)));
     I->stage_cap = std::max<long long>(n, kStageHost);
   }
   double* dx = I->stage_x;
   double* dv = I->stage_v;
-  const bool small = n <= kStageHost;
+  // an upload with multiplicities takes the synchronous path (its third array
+  // has no pinned staging)
+  const bool small = n <= kStageHost && !mw;
   if (small) {
     // the caller's arrays are copied into pinned staging on the host, so the call
     // returns as soon as the copy and the upload kernel are queued
@@ -1484,16 +1501,18 @@ pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, in
   } else {
     CK(h, cudaMemcpyAsync(dx, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(dv, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+    if (mw) CK(h, cudaMemcpyAsync(I->stage_m, mw, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, h->stream));
   }
+  const uint32_t* dm = mw ? I->stage_m : nullptr;
   const int c = I->cur[species];
   // uploaded particles join the next step's accumulated deposit (if any)
   const NextDeposit nd = next_deposit_of(I, I->next_valid);
   const int neutral = I->species[species].role == PIC_NEUTRAL ? 1 : 0;
   if (I->mixed)
-    launch_load<StoreMx>(I->g, I->smx[species][c], I->cnt, c, species, I->cap[species], dx, dv, n, nd, neutral,
+    launch_load<StoreMx>(I->g, I->smx[species][c], I->cnt, c, species, I->cap[species], dx, dv, dm, n, nd, neutral,
                          h->stream);
   else
-    launch_load<Store64>(I->g, I->s64[species][c], I->cnt, c, species, I->cap[species], dx, dv, n, nd, neutral,
+    launch_load<Store64>(I->g, I->s64[species][c], I->cnt, c, species, I->cap[species], dx, dv, dm, n, nd, neutral,
                          h->stream);
   // what the upload does to the counters (checked above: no capacity clamp)
   I->host_cnt->n[c][species] += (unsigned long long)n;
@@ -1508,6 +1527,17 @@ pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, in
     return fail(h, PIC_ECUDA, "upload failed: %s", cudaGetErrorString(e));
   }
   return PIC_OK;
+}
+
+pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n, const double* x,
+                                const double* v) {
+  return inject_particles(h, inst, species, n, x, v, nullptr);
+}
+
+pic_status pic_inject_particles_m(pic_handle* h, int32_t inst, int32_t species, int64_t n, const double* x,
+                                  const double* v, const uint32_t* mw) {
+  if (n > 0 && !mw) return fail(h, PIC_EINVAL, "mw is NULL");
+  return inject_particles(h, inst, species, n, x, v, mw);
 }
 
 pic_status pic_step(pic_handle* h, int32_t nsteps) {
@@ -1612,7 +1642,29 @@ pic_status pic_moments(pic_handle* h, int32_t inst, pic_moments_t* out) {
   Instance* I = h->inst[inst];
   cudaStream_t s = h->stream;
   CK(h, cudaMemsetAsync(I->red, 0, sizeof(double) * 64, s));
-  if (I->mixed) {
+  if (I->weighted) {
+    // multiplicity-weighted sums (red[sp]: sum mw |v|^2, red[32 + sp]: sum mw),
+    // then the field energy
+    for (int sp = 0; sp < I->nsp; ++sp) {
+      const int c = I->cur[sp];
+      if (I->mixed)
+        launch_kinetic_w<StoreMx>(I->smx[sp][c], &I->cnt->n[c][sp], I->cap[sp], I->red + sp, I->red + 32 + sp, s);
+      else
+        launch_kinetic_w<Store64>(I->s64[sp][c], &I->cnt->n[c][sp], I->cap[sp], I->red + sp, I->red + 32 + sp, s);
+    }
+    if (I->mixed) {
+      MomentsMx m{};
+      m.g = I->g;
+      m.nsp = 0;  // the field energy only
+      m.hi = I->phi32;
+      m.lo = I->solver.lo32;
+      m.part = I->mom_part;
+      m.ticket = I->mom_ticket;
+      launch_moments_mx(m, I->red, s);
+    } else {
+      launch_field_energy(I->g, I->phi, I->red + 16, s);
+    }
+  } else if (I->mixed) {
     // one launch: kinetic sums and the field energy from the solver's
     // float-float state (the potential the last solve left)
     MomentsMx m{};
@@ -1653,7 +1705,7 @@ pic_status pic_moments(pic_handle* h, int32_t inst, pic_moments_t* out) {
     out->absorbed_energy_cathode_J[sp] = c.abs_energy_cathode[sp];
     out->absorbed_energy_anode_J[sp] = c.abs_energy_anode[sp];
     out->kinetic_J[sp] = 0.5 * S.mass_kg * S.weight * red[sp];
-    q += S.charge_C * S.weight * (double)out->count[sp];
+    q += S.charge_C * S.weight * (I->weighted ? red[32 + sp] : (double)out->count[sp]);
   }
   out->ionizations = (int64_t)c.n_ion;
   out->elastic = (int64_t)c.n_el;
@@ -1688,8 +1740,8 @@ pic_status pic_get_count(pic_handle* h, int32_t inst, int32_t species, int64_t* 
   return PIC_OK;
 }
 
-pic_status pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t cap, int64_t* n, uint32_t* pid,
-                             double* x, double* v) {
+static pic_status get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t cap, int64_t* n,
+                                uint32_t* pid, double* x, double* v, uint32_t* mw) {
   pic_status st = check(h, inst);
   if (st != PIC_OK) return st;
   Instance* I = h->inst[inst];
@@ -1702,22 +1754,25 @@ pic_status pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64
   if (cap < live) return fail(h, PIC_EINVAL, "cap %lld below count %lld", (long long)cap, live);
   if (slots == 0) return PIC_OK;
   double *dx = nullptr, *dv = nullptr;
-  uint32_t* dp = nullptr;
+  uint32_t *dp = nullptr, *dm = nullptr;
   CK(h, dalloc(&dx, 3 * (size_t)slots));
   CK(h, dalloc(&dv, 3 * (size_t)slots));
   CK(h, dalloc(&dp, (size_t)slots));
+  if (mw) CK(h, dalloc(&dm, (size_t)slots));
   const int c = I->cur[species];
-  if (I->mixed) launch_download<StoreMx>(I->g, I->smx[species][c], slots, dx, dv, dp, h->stream);
-  else launch_download<Store64>(I->g, I->s64[species][c], slots, dx, dv, dp, h->stream);
+  if (I->mixed) launch_download<StoreMx>(I->g, I->smx[species][c], slots, dx, dv, dp, dm, h->stream);
+  else launch_download<Store64>(I->g, I->s64[species][c], slots, dx, dv, dp, dm, h->stream);
   std::vector<double> hx(3 * slots), hv(3 * slots);
-  std::vector<uint32_t> hp(slots);
+  std::vector<uint32_t> hp(slots), hm(mw ? slots : 0);
   cudaMemcpyAsync(hx.data(), dx, sizeof(double) * 3 * slots, cudaMemcpyDeviceToHost, h->stream);
   cudaMemcpyAsync(hv.data(), dv, sizeof(double) * 3 * slots, cudaMemcpyDeviceToHost, h->stream);
   cudaMemcpyAsync(hp.data(), dp, sizeof(uint32_t) * slots, cudaMemcpyDeviceToHost, h->stream);
+  if (mw) cudaMemcpyAsync(hm.data(), dm, sizeof(uint32_t) * slots, cudaMemcpyDeviceToHost, h->stream);
   cudaError_t e = cudaStreamSynchronize(h->stream);
   cudaFree(dx);
   cudaFree(dv);
   cudaFree(dp);
+  cudaFree(dm);
   if (e != cudaSuccess) return fail(h, PIC_ECUDA, "download failed: %s", cudaGetErrorString(e));
   long long w = 0;
   for (long long i = 0; i < slots; ++i) {
@@ -1726,9 +1781,21 @@ pic_status pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64
     if (pid) pid[w] = hp[i];
     if (x) memcpy(x + 3 * w, &hx[3 * i], 3 * sizeof(double));
     if (v) memcpy(v + 3 * w, &hv[3 * i], 3 * sizeof(double));
+    if (mw) mw[w] = hm[i];
     ++w;
   }
   return PIC_OK;
+}
+
+pic_status pic_get_particles(pic_handle* h, int32_t inst, int32_t species, int64_t cap, int64_t* n, uint32_t* pid,
+                             double* x, double* v) {
+  return get_particles(h, inst, species, cap, n, pid, x, v, nullptr);
+}
+
+pic_status pic_get_multiplicity(pic_handle* h, int32_t inst, int32_t species, int64_t cap, int64_t* n,
+                                uint32_t* mw) {
+  if (!mw) return fail(h, PIC_EINVAL, "mw is NULL");
+  return get_particles(h, inst, species, cap, n, nullptr, nullptr, nullptr, mw);
 }
 
 pic_status pic_get_field(pic_handle* h, int32_t inst, int32_t which, int32_t species, void* host_out) {
@@ -2125,6 +2192,7 @@ pic_status pic_save(pic_handle* h, int32_t inst, const char* path) {
   if (st != PIC_OK) return st;
   if (!path) return fail(h, PIC_EINVAL, "path is NULL");
   Instance* I = h->inst[inst];
+  if (I->weighted) return fail(h, PIC_EINVAL, "checkpoints of instances with variable weights are not supported");
   st = download_carries(h, I);
   if (st != PIC_OK) return st;
   CK(h, cudaStreamSynchronize(I->stream));
@@ -2235,6 +2303,7 @@ pic_status pic_load(pic_handle* h, int32_t inst, const char* path) {
   if (st != PIC_OK) return st;
   if (!path) return fail(h, PIC_EINVAL, "path is NULL");
   Instance* I = h->inst[inst];
+  if (I->weighted) return fail(h, PIC_EINVAL, "checkpoints of instances with variable weights are not supported");
   std::vector<char> buf;
   {
     std::FILE* f = std::fopen(path, "rb");

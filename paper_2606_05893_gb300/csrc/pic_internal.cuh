@@ -142,14 +142,18 @@ __device__ __forceinline__ double wrap_coord(double x, double L, double invL) {
 // ---------------------------------------------------------------------------
 // Particle stores
 // ---------------------------------------------------------------------------
+// mw: integer multiplicities (a particle stands for mw x the species weight)
+// when the instance has variable weights, else nullptr (every particle 1)
 struct Store64 {
   double *x, *y, *z, *vx, *vy, *vz;
   uint32_t* pid;
+  uint32_t* mw;
 };
 struct StoreMx {
   int32_t* cell;
   float *ox, *oy, *oz, *vx, *vy, *vz;
   uint32_t* pid;
+  uint32_t* mw;
 };
 
 // ---------------------------------------------------------------------------
@@ -194,6 +198,7 @@ struct DevCounters {
   unsigned int step;                       // index of the step being taken (Philox counter word 1)
   double anode_V;                          // anode potential of the next solve (external circuit)
   unsigned int resolve_ticket;             // blocks of the resolve launch finished (0 between launches)
+  unsigned int n_kill_n, n_kill_i;         // variable weights: victims and exchanging ions wholly converted this step
 };
 
 // External circuit (the serial RC circuit between the electrodes): a source V0

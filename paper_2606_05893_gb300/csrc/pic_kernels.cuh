@@ -97,6 +97,7 @@ __device__ __forceinline__ bool warp_run_sum(int key, float (&w)[N]) {
 struct Particle64 {
   double x, y, z, vx, vy, vz;
   uint32_t pid;
+  uint32_t mw;     // multiplicity (1 without variable weights)
   long long cell;  // cell at read time (x^n)
   Loc l;
   float nc;        // neutral count of the cell (4th component of the node field)
@@ -169,6 +170,7 @@ struct ParticleMx {
   int32_t cell;
   float ox, oy, oz, vx, vy, vz;
   uint32_t pid;
+  uint32_t mw;     // multiplicity (1 without variable weights)
   float nc;  // neutral count of the cell (4th component of the node field)
 
   template <class A>
@@ -325,7 +327,7 @@ __device__ __forceinline__ void deposit_one(const Grid& g, const ParticleMx& p, 
   cell_ijk(g, p.cell, i, j, k);
   long long idx[8];
   corner_nodes(g, i, j, k, idx);
-  const float qf = (float)q;
+  const float qf = (float)q * (float)p.mw;
 #pragma unroll
   for (int c = 0; c < 8; ++c) atomicAdd(&rho32[idx[c]], w[c] * qf);
 }
@@ -336,8 +338,9 @@ __device__ __forceinline__ void deposit_one(const Grid& g, const Particle64& p, 
   cic_weights(l.fx, l.fy, l.fz, w);
   long long idx[8];
   corner_nodes(g, l.i, l.j, l.k, idx);
+  const double qm = q * (double)p.mw;
 #pragma unroll
-  for (int c = 0; c < 8; ++c) atomicAdd(&rho64[idx[c]], w[c] * q);
+  for (int c = 0; c < 8; ++c) atomicAdd(&rho64[idx[c]], w[c] * qm);
 }
 __device__ __forceinline__ int cell_now(const Grid& g, const ParticleMx& p) {
   (void)g;
@@ -381,6 +384,7 @@ __device__ __forceinline__ Particle64 store_read(const Store64& s, const Grid& g
   p.vy = s.vy[i];
   p.vz = s.vz[i];
   p.pid = s.pid[i];
+  p.mw = s.mw ? s.mw[i] : 1u;
   p.l = locate64(g, p.x, p.y, p.z);
   p.cell = ((long long)p.l.k * g.ny + p.l.j) * g.nx + p.l.i;
   return p;
@@ -395,6 +399,7 @@ __device__ __forceinline__ ParticleMx store_read(const StoreMx& s, const Grid& g
   p.vy = s.vy[i];
   p.vz = s.vz[i];
   p.pid = s.pid[i];
+  p.mw = s.mw ? s.mw[i] : 1u;
   return p;
 }
 __device__ __forceinline__ long long particle_cell(const Particle64& p) { return p.cell; }
@@ -408,6 +413,7 @@ __device__ __forceinline__ void store_write_p(const Store64& s, long long i, con
   s.vy[i] = p.vy;
   s.vz[i] = p.vz;
   s.pid[i] = p.pid;
+  if (s.mw) s.mw[i] = p.mw;
 }
 __device__ __forceinline__ void store_write_p(const StoreMx& s, long long i, const ParticleMx& p) {
   s.cell[i] = p.cell;
@@ -418,6 +424,7 @@ __device__ __forceinline__ void store_write_p(const StoreMx& s, long long i, con
   s.vy[i] = p.vy;
   s.vz[i] = p.vz;
   s.pid[i] = p.pid;
+  if (s.mw) s.mw[i] = p.mw;
 }
 __device__ __forceinline__ void store_write_v(const Store64& s, long long i, const Particle64& p) {
   s.vx[i] = p.vx;
@@ -434,8 +441,9 @@ __device__ __forceinline__ void store_kill(const StoreMx& s, long long i) { s.pi
 
 // Write from FP64 values (injection, host upload).
 __device__ __forceinline__ void store_write(const Store64& s, const Grid& g, long long i, double x, double y, double z,
-                                            double vx, double vy, double vz, uint32_t pid) {
+                                            double vx, double vy, double vz, uint32_t pid, uint32_t mw = 1u) {
   (void)g;
+  if (s.mw) s.mw[i] = mw;
   s.x[i] = x;
   s.y[i] = y;
   s.z[i] = z;
@@ -451,7 +459,8 @@ __device__ __forceinline__ float offset_of(double gcoord, int cell) {
   return o;
 }
 __device__ __forceinline__ void store_write(const StoreMx& s, const Grid& g, long long i, double x, double y, double z,
-                                            double vx, double vy, double vz, uint32_t pid) {
+                                            double vx, double vy, double vz, uint32_t pid, uint32_t mw = 1u) {
+  if (s.mw) s.mw[i] = mw;
   const Loc l = locate64(g, x, y, z);
   s.cell[i] = (l.k * g.ny + l.j) * g.nx + l.i;
   s.ox[i] = offset_of(x * g.inv_h, l.i);
@@ -591,6 +600,7 @@ struct ResolveCommit {
   int n_out, n_sp;
   long long n_cap;
   int ev_cap;
+  int weighted;  // variable weights: partial conversions, 3 pids per successful event
 };
 
 template <class S>
@@ -665,9 +675,10 @@ void launch_step_begin(DevCounters* cnt, const int* out_buf, int nsp, cudaStream
 
 template <class S>
 void launch_load(const Grid& g, S st, DevCounters* cnt, int cur, int species, long long cap, const double* x,
-                 const double* v, long long n, const NextDeposit& nd, int neutral, cudaStream_t s);
+                 const double* v, const uint32_t* mw, long long n, const NextDeposit& nd, int neutral, cudaStream_t s);
 template <class S>
-void launch_download(const Grid& g, S st, long long n, double* x, double* v, uint32_t* pid, cudaStream_t s);
+void launch_download(const Grid& g, S st, long long n, double* x, double* v, uint32_t* pid, uint32_t* mw,
+                     cudaStream_t s);
 
 template <class S>
 void launch_cell_keys(const Grid& g, S st, long long n_max, const unsigned long long* n_dev, int pid_bits,
@@ -745,6 +756,9 @@ struct MomentsMx {
   int fe_tx, kin_blocks; // set by the launcher (kin_blocks unused: every block takes both parts)
 };
 void launch_moments_mx(const MomentsMx& a, double* out, cudaStream_t s);
+template <class S>
+void launch_kinetic_w(S st, const unsigned long long* n_dev, long long n_max, double* out_v2, double* out_m,
+                      cudaStream_t s);
 
 void launch_philox(long long n, uint4 ctr, uint2 key, uint32_t* out, cudaStream_t s);
 
