@@ -438,7 +438,8 @@ uint64_t pic_kernel_count(void);
  * PIC_ENOCONV if the true residual is above rtol, PIC_ECUDA if a launch or copy
  * fails; pic_last_error(NULL) then says which. The first call on a device looks up the address of
  * the fixed array on that device (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture. All calls share
+ * current). No call can be captured into a CUDA graph: every iteration
+ * synchronises the stream (below). All calls share
  * the array and it keeps the last call's contents (each call writes every
  * vector before reading it); calls that overlap on the GPU -- on different
  * streams or from different host threads on the same device -- race on it.
