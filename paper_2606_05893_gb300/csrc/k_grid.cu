@@ -805,10 +805,9 @@ __global__ void k_moments_mx(MomentsMx a, double* out) {
   const long long rows = (long long)g.ny * (g.nz + 1);
   const int tx = a.fe_tx, ty = blockDim.x / tx, lx0 = t % tx, ly0 = t / tx;
   const long long fb = blockIdx.x, nfb = gridDim.x;
-  double acc = 0.0;
-  float part = 0.f;
-  int run = 0;
-  for (long long r = fb * ty + ly0; r < rows; r += nfb * ty) {
+  // the squared edge differences at node (i, row r); rows of the same thread
+  // are taken two at a time so that their loads are in flight together
+  auto node_sq = [&](long long r, int i) -> float {
     const int k = (int)r / g.ny;  // rows < 2^31
     const int j = (int)r - k * g.ny;
     const long long c0 = (long long)j * g.nx;
@@ -816,37 +815,40 @@ __global__ void k_moments_mx(MomentsMx a, double* out) {
     const float* H = a.hi + (long long)k * pl;
     const float* L = a.lo + (long long)(k - 1) * pl;
     const bool interior = k > 0 && k < g.nz;
+    const int ip = i + 1 == g.nx ? 0 : i + 1;
+    float h0 = 0.f, hx = 0.f, hy = 0.f, l0 = 0.f, lxv = 0.f, ly = 0.f, h1 = 0.f, l1 = 0.f;
+    if (k > 0) {
+      h0 = H[c0 + i];
+      hx = H[c0 + ip];
+      hy = H[cn + i];
+    }
+    if (interior) {
+      l0 = L[c0 + i];
+      lxv = L[c0 + ip];
+      ly = L[cn + i];
+    }
+    if (k < g.nz) h1 = H[pl + c0 + i];
+    if (k + 1 < g.nz) l1 = L[pl + c0 + i];
+    const float dx = (hx - h0) + (lxv - l0);
+    const float dy = (hy - h0) + (ly - l0);
+    float sq = fmaf(dx, dx, dy * dy);
+    if (k < g.nz) {
+      const float dz = (k + 1 == g.nz ? a.dz_top : a.dz_in) + ((h1 - h0) + (l1 - l0));
+      sq = fmaf(dz, dz, sq);
+    }
+    return sq;
+  };
+  double acc = 0.0;
+  const long long rstep = nfb * ty;
+  for (long long r = fb * ty + ly0; r < rows; r += 2 * rstep) {
+    const bool two = r + rstep < rows;
     for (int i = lx0; i < g.nx; i += tx) {
-      const int ip = i + 1 == g.nx ? 0 : i + 1;
-      float h0 = 0.f, hx = 0.f, hy = 0.f, l0 = 0.f, lxv = 0.f, ly = 0.f;
-      if (k > 0) {
-        h0 = H[c0 + i];
-        hx = H[c0 + ip];
-        hy = H[cn + i];
-      }
-      if (interior) {
-        l0 = L[c0 + i];
-        lxv = L[c0 + ip];
-        ly = L[cn + i];
-      }
-      const float dx = (hx - h0) + (lxv - l0);
-      const float dy = (hy - h0) + (ly - l0);
-      float sq = fmaf(dx, dx, dy * dy);
-      if (k < g.nz) {
-        const float h1 = H[pl + c0 + i];
-        const float l1 = k + 1 < g.nz ? L[pl + c0 + i] : 0.f;
-        const float dz = (k + 1 == g.nz ? a.dz_top : a.dz_in) + ((h1 - h0) + (l1 - l0));
-        sq = fmaf(dz, dz, sq);
-      }
-      part += sq;
-      if (++run == 8) {
-        acc += (double)part;
-        part = 0.f;
-        run = 0;
-      }
+      const float s0 = node_sq(r, i);
+      const float s1 = two ? node_sq(r + rstep, i) : 0.f;
+      acc += (double)(s0 + s1);
     }
   }
-  acc = block_total(acc + (double)part);
+  acc = block_total(acc);
   if (t == 0) a.part[(long long)blockIdx.x * kMomSlots + kMaxSpecies] = acc;
   // the last block: every block's totals are written
   __shared__ bool s_last;
@@ -873,7 +875,17 @@ void launch_moments_mx(const MomentsMx& a0, double* out, cudaStream_t s) {
   a.dz_top = (float)(g.phi_a - (g.phi_c + dphi_dk * (double)(g.nz - 1)));
   a.fe_tx = g.nx >= 128 ? 128 : (g.nx >= 64 ? 64 : 32);
   a.kin_blocks = 0;
-  PIC_LAUNCH(kMomBlocks, kBlock, 0, s, k_moments_mx)(a, out);
+  // one wave: every block resident at once (the blocks' shares are equal, so a
+  // second partial wave would take as long as the first)
+  static int grid = 0;
+  if (grid == 0) {
+    int occ = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_moments_mx, kBlock, 0);
+    grid = std::max(1, std::min(kMomBlocks, occ * sms));
+  }
+  PIC_LAUNCH(grid, kBlock, 0, s, k_moments_mx)(a, out);
 }
 
 // Philox on the device (test hook)
