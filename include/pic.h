@@ -226,8 +226,8 @@ pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, in
  * events. next_pid advances by 3 ns. A primary electron that moves less than
  * its whole multiplicity loses the ionization energy with probability ms / mw
  * (the second uniform of the ionization's second draw): energy is conserved on
- * average, charge and particle numbers exactly. pic_save and pic_load refuse
- * such instances (PIC_EINVAL).
+ * average, charge and particle numbers exactly. Checkpoints (pic_save)
+ * carry the multiplicities.
  * pic_inject_particles_m: as pic_inject_particles, with mw[n] (host, copied).
  * PIC_EINVAL if mw is NULL or an mw[i] is 0, or above 1 on an instance
  * without variable weights. The call synchronises the stream.
@@ -363,12 +363,14 @@ pic_status pic_get_hits(pic_handle* h, int32_t inst, int64_t cap, int64_t* n, in
  * state of a long run, kept so that it can stop and continue). pic_save writes
  * to `path` the live particles of every species in increasing pid (the store's
  * own representation: FP64 x, v; or cell, FP32 offsets and velocities of the
- * mixed store), the potential (and the mixed solver's FP32 state), the
+ * mixed store; with variable weights also the multiplicities), the potential
+ * (and the mixed solver's FP32 state), the
  * cumulative counters, step and next pid, the surface sources with their carry
  * accumulators, the sort interval, the external circuit and the background
  * test mode. The hit log and the ionization log are outputs, not state, and
  * are not saved. pic_load reads such a file into an instance created with the
- * same grid, precision, electrode potentials, time step, seed and species; it
+ * same grid, precision, electrode potentials, time step, seed, species and
+ * variable-weights setting; it
  * checks the whole file first and leaves the instance unchanged on any error
  * (PIC_EINVAL: unreadable, not a checkpoint, a different configuration, or
  * truncated; PIC_ECAPACITY: more particles than a species holds). Draws are

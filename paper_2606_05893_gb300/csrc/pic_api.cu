@@ -2136,7 +2136,7 @@ struct CkptHeader {
   double bg_density;
   int32_t circ_on, last_iters;
   double circ_R, circ_C, circ_V0, last_resid;
-  int32_t nsources, reserved2;
+  int32_t nsources, weighted;  // weighted: each species' records carry multiplicities after the pids
 };
 
 struct CkptSpecies {
@@ -2192,7 +2192,6 @@ pic_status pic_save(pic_handle* h, int32_t inst, const char* path) {
   if (st != PIC_OK) return st;
   if (!path) return fail(h, PIC_EINVAL, "path is NULL");
   Instance* I = h->inst[inst];
-  if (I->weighted) return fail(h, PIC_EINVAL, "checkpoints of instances with variable weights are not supported");
   st = download_carries(h, I);
   if (st != PIC_OK) return st;
   CK(h, cudaStreamSynchronize(I->stream));
@@ -2225,6 +2224,7 @@ pic_status pic_save(pic_handle* h, int32_t inst, const char* path) {
   hd.last_iters = I->last.iters;
   hd.last_resid = I->last.resid_rel;
   hd.nsources = (int32_t)I->sources.size();
+  hd.weighted = I->weighted ? 1 : 0;
 
   std::FILE* f = std::fopen(path, "wb");
   if (!f) return fail(h, PIC_EINVAL, "cannot open %s for writing", path);
@@ -2244,7 +2244,7 @@ pic_status pic_save(pic_handle* h, int32_t inst, const char* path) {
   for (int sp = 0; ok && sp < I->nsp; ++sp) {
     const int b = I->cur[sp];
     const long long slots = (long long)c.n[b][sp];
-    std::vector<uint32_t> pid;
+    std::vector<uint32_t> pid, mw;
     std::vector<long long> order;
     std::vector<double> d[6];
     std::vector<float> fl[6];
@@ -2253,12 +2253,14 @@ pic_status pic_save(pic_handle* h, int32_t inst, const char* path) {
       const StoreMx& S = I->smx[sp][b];
       float* src[6] = {S.ox, S.oy, S.oz, S.vx, S.vy, S.vz};
       if (!e) e = pull(pid, S.pid, slots);
+      if (!e && S.mw) e = pull(mw, S.mw, slots);
       if (!e) e = pull(cell, S.cell, slots);
       for (int a = 0; a < 6 && !e; ++a) e = pull(fl[a], src[a], slots);
     } else {
       const Store64& S = I->s64[sp][b];
       double* src[6] = {S.x, S.y, S.z, S.vx, S.vy, S.vz};
       if (!e) e = pull(pid, S.pid, slots);
+      if (!e && S.mw) e = pull(mw, S.mw, slots);
       for (int a = 0; a < 6 && !e; ++a) e = pull(d[a], src[a], slots);
     }
     if (e) break;
@@ -2273,6 +2275,7 @@ pic_status pic_save(pic_handle* h, int32_t inst, const char* path) {
     r.role = S.role;
     r.n = (int64_t)order.size();
     ok = ok && std::fwrite(&r, sizeof r, 1, f) == 1 && put(f, pid, order);
+    if (I->weighted) ok = ok && put(f, mw, order);
     if (I->mixed) {
       ok = ok && put(f, cell, order);
       for (int a = 0; a < 6; ++a) ok = ok && put(f, fl[a], order);
@@ -2303,7 +2306,6 @@ pic_status pic_load(pic_handle* h, int32_t inst, const char* path) {
   if (st != PIC_OK) return st;
   if (!path) return fail(h, PIC_EINVAL, "path is NULL");
   Instance* I = h->inst[inst];
-  if (I->weighted) return fail(h, PIC_EINVAL, "checkpoints of instances with variable weights are not supported");
   std::vector<char> buf;
   {
     std::FILE* f = std::fopen(path, "rb");
@@ -2327,6 +2329,9 @@ pic_status pic_load(pic_handle* h, int32_t inst, const char* path) {
     return fail(h, PIC_EINVAL, "%s: grid, precision, electrodes, time step or seed differ from instance %d", path, inst);
   if (hd.nsources < 0 || hd.nsources > kMaxSources || hd.sort_interval < 0)
     return fail(h, PIC_EINVAL, "%s: bad source count or sort interval", path);
+  if (hd.weighted != (I->weighted ? 1 : 0))
+    return fail(h, PIC_EINVAL, "%s: variable weights %s in the file, %s in instance %d", path,
+                hd.weighted ? "on" : "off", I->weighted ? "on" : "off", inst);
   std::vector<Source> sources;
   for (int q = 0; q < hd.nsources; ++q) {
     CkptSource r{};
@@ -2334,8 +2339,9 @@ pic_status pic_load(pic_handle* h, int32_t inst, const char* path) {
       return fail(h, PIC_EINVAL, "%s: bad source record", path);
     sources.push_back(Source{r.species, r.cx, r.cy, r.R, r.flux, r.T, r.acc});
   }
-  const size_t per64 = sizeof(uint32_t) + 6 * sizeof(double);
-  const size_t permx = sizeof(uint32_t) + sizeof(int32_t) + 6 * sizeof(float);
+  const size_t permw = I->weighted ? sizeof(uint32_t) : 0;
+  const size_t per64 = sizeof(uint32_t) + permw + 6 * sizeof(double);
+  const size_t permx = sizeof(uint32_t) + permw + sizeof(int32_t) + 6 * sizeof(float);
   std::vector<const char*> parts(I->nsp);
   std::vector<long long> counts(I->nsp);
   for (int sp = 0; sp < I->nsp; ++sp) {
@@ -2367,6 +2373,10 @@ pic_status pic_load(pic_handle* h, int32_t inst, const char* path) {
       const StoreMx& S = I->smx[sp][0];
       CK(h, cudaMemcpy(S.pid, p, sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
       p += sizeof(uint32_t) * n;
+      if (S.mw) {
+        CK(h, cudaMemcpy(S.mw, p, sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
+        p += sizeof(uint32_t) * n;
+      }
       CK(h, cudaMemcpy(S.cell, p, sizeof(int32_t) * n, cudaMemcpyHostToDevice));
       p += sizeof(int32_t) * n;
       float* dst[6] = {S.ox, S.oy, S.oz, S.vx, S.vy, S.vz};
@@ -2376,6 +2386,10 @@ pic_status pic_load(pic_handle* h, int32_t inst, const char* path) {
       const Store64& S = I->s64[sp][0];
       CK(h, cudaMemcpy(S.pid, p, sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
       p += sizeof(uint32_t) * n;
+      if (S.mw) {
+        CK(h, cudaMemcpy(S.mw, p, sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
+        p += sizeof(uint32_t) * n;
+      }
       double* dst[6] = {S.x, S.y, S.z, S.vx, S.vy, S.vz};
       for (int a = 0; a < 6; ++a, p += sizeof(double) * n)
         CK(h, cudaMemcpy(dst[a], p, sizeof(double) * n, cudaMemcpyHostToDevice));

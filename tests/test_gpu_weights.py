@@ -10,7 +10,8 @@ victims, secondaries of the moved part, the primary's energy loss drawn with
 probability ms / mp), charge exchange together with ionization, a plasma run
 with field, injection, absorption and sorting, and unit multiplicities. Mixed
 path: the same integer outcomes and multiplicities on the exchange case.
-Also the uploads and checkpoints that the library refuses.
+A weighted checkpoint resumes like the uninterrupted run. Also the uploads and
+the checkpoint loads that the library refuses.
 """
 import math
 
@@ -135,15 +136,46 @@ def test_weighted_mixed_store(pkg):
     ref.close()
 
 
-def test_refusals(pkg, tmp_path):
+def test_weighted_checkpoint_resumes(pkg, tmp_path):
+    wl = weighted_ionization_case(seed=10)
+    wl.sort_interval = 2
+    a = pkg.Simulation(wl, cg_rtol=RTOL_SOLVE, cg_maxit=5000)
+    a.step(2)
+    path = str(tmp_path / "w.ckpt")
+    a.save(path)
+    b = pkg.Simulation(weighted_ionization_case(seed=10), cg_rtol=RTOL_SOLVE, cg_maxit=5000, preload=False)
+    b.load(path)
+    for sp in range(3):  # the round trip is exact, multiplicities included
+        pa, ma = _mult_by_pid(a, sp)
+        pb, mb = _mult_by_pid(b, sp)
+        assert np.array_equal(pa, pb) and np.array_equal(ma, mb)
+    a.step(2)
+    b.step(2)
+    compare_integer_moments(b.moments(), a.moments())
+    for sp in range(3):
+        xa, va, pa = a.particles(sp)
+        xb, vb, pb = b.particles(sp)
+        oa, ob = np.argsort(pa), np.argsort(pb)
+        assert np.array_equal(pa[oa], pb[ob])
+        assert np.array_equal(_mult_by_pid(a, sp)[1], _mult_by_pid(b, sp)[1])
+        assert np.abs(xa[oa] - xb[ob]).max(initial=0.0) <= 1e-9 * max(wl.L)
+        assert np.abs(va[oa] - vb[ob]).max(initial=0.0) <= 1e-9 * np.abs(va).max(initial=1.0)
+    # a weighted checkpoint does not load into an instance without variable weights
+    plain = pkg.Simulation(ionization_cells_case(seed=10), cg_rtol=RTOL_SOLVE, cg_maxit=5000, preload=False)
+    with pytest.raises(pkg.PicError):
+        plain.load(path)
+    a.close()
+    b.close()
+    plain.close()
+
+
+def test_refusals(pkg):
     wl = weighted_ionization_case(seed=8)
     sim = pkg.Simulation(wl, cg_rtol=RTOL_SOLVE, cg_maxit=5000)
     x = np.full((1, 3), 1e-8)
     v = np.zeros((1, 3))
     with pytest.raises(pkg.PicError):
         pkg.pic_inject_particles_m(sim.h, 0, 0, x, v, np.zeros(1, dtype=np.uint32))
-    with pytest.raises(pkg.PicError):
-        sim.save(str(tmp_path / "w.ckpt"))
     sim.close()
     plain = pkg.Simulation(ionization_cells_case(seed=4), cg_rtol=RTOL_SOLVE, cg_maxit=5000)
     with pytest.raises(pkg.PicError):
