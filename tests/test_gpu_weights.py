@@ -183,3 +183,27 @@ def test_refusals(pkg):
     pkg.pic_inject_particles_m(plain.h, 0, 0, x, v, np.ones(1, dtype=np.uint32))
     assert np.all(plain.multiplicity(0) == 1)
     plain.close()
+
+
+def test_weighted_and_plain_instances_in_one_handle(pkg):
+    # per-instance flags: a weighted and a plain instance step together (the
+    # handle's ensemble step) and each matches its own oracle run
+    from tests.gpu_compare import compare_particles
+    wls = [weighted_ionization_case(seed=8), ionization_cells_case(seed=3)]
+    sim = pkg.Simulation(wls, precision=pkg.PIC_FP64, cg_rtol=RTOL_SOLVE, cg_maxit=5000)
+    refs = [O.Oracle(w, cg_rtol=RTOL_SOLVE) for w in wls]
+    for _ in range(2):
+        sim.step()
+        for r in refs:
+            r.step()
+    for i, (w, r) in enumerate(zip(wls, refs)):
+        compare_integer_moments(sim.moments(i), r.moments())
+        for sp in range(3):
+            compare_particles(sim, r, w, sp, 1e-9, 1e-9, inst=i)
+            pg = sim.particles(sp, inst=i)[2]
+            mg = sim.multiplicity(sp, inst=i)
+            po, mo = _mult_by_pid(r, sp)
+            o = np.argsort(pg, kind="stable")
+            assert np.array_equal(pg[o], po) and np.array_equal(mg[o], mo)
+        r.close()
+    sim.close()
