@@ -1484,6 +1484,13 @@ __global__ void __launch_bounds__(kSB) k_dot_bb(int n, const double* __restrict_
   if (grid_total(acc, part, &c->ticket, &bb)) fin_bb(bb, c, rtol, maxit);
 }
 
+// The mixed path's inner (FP32) solve stops once its recursive residual is
+// below 0.9 of the outer tolerance (kInnerMargin2 = 0.9^2 on r.r): the
+// float-float residual the outer loop then takes differs from it only by the
+// FP32 rounding of the correction, about 1e-7 of the residual the inner solve
+// started from, far inside the margin.
+constexpr double kInnerMargin2 = 0.81;
+
 // Outer-loop decision from the true residual r.r (last block of a residual kernel)
 __device__ __forceinline__ void fin_outer(double rr, SolveCtl* c, cudaGraphConditionalHandle h_outer,
                                           cudaGraphConditionalHandle h_inner, double inner_rtol, int mixed,
@@ -1495,7 +1502,7 @@ __device__ __forceinline__ void fin_outer(double rr, SolveCtl* c, cudaGraphCondi
   c->converged = (c->bb == 0.0 || rr <= c->tol2) ? 1 : 0;
   c->rr = rr;
   c->it_inner = 0;
-  c->tol_in2 = mixed ? fmax(inner_rtol * inner_rtol * rr, 0.25 * c->tol2) : c->tol2;
+  c->tol_in2 = mixed ? fmax(inner_rtol * inner_rtol * rr, kInnerMargin2 * c->tol2) : c->tol2;
   c->outer += 1;
   c->more = done ? 0 : 1;
   c->stopped = done ? 1 : 0;
