@@ -162,9 +162,10 @@ static dim3 grid3(const Grid& g, int planes) {
 }
 static const dim3 kBlk3(32, 8, 1);
 
+// s = h^2 / eps0, formed once on the host (an FP64 division in every thread
+// would queue on the narrow FP64 pipe)
 __global__ void __launch_bounds__(256) k_rhs(Grid g, const DevCounters* cnt, const double* __restrict__ rho64,
-                                             const float* __restrict__ rho32, double* __restrict__ b) {
-  const double s = g.h * g.h / kEps0;
+                                             const float* __restrict__ rho32, double* __restrict__ b, double s) {
   const float s32 = (float)s;
   const int kn = blockIdx.z + 1;  // node plane of this unknown plane
   const int i = blockIdx.x * 32 + threadIdx.x;
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(256) k_rhs(Grid g, const DevCounters* cnt, con
 }
 void launch_rhs(const Grid& g, const DevCounters* cnt, const double* rho64, const float* rho32, double* b,
                 cudaStream_t st) {
-  PIC_LAUNCH(grid3(g, g.nz - 1), kBlk3, 0, st, k_rhs)(g, cnt, rho64, rho32, b);
+  PIC_LAUNCH(grid3(g, g.nz - 1), kBlk3, 0, st, k_rhs)(g, cnt, rho64, rho32, b, g.h * g.h / kEps0);
 }
 
 // MIXED path: the FP32 charge term f = fl32(h^2/eps0 rho) over the unknowns,
@@ -196,8 +197,7 @@ void launch_rhs(const Grid& g, const DevCounters* cnt, const double* rho64, cons
 // the FP32 potential carries dV on the anode plane (the field kernel reads it).
 __global__ void __launch_bounds__(256) k_rhs_f32(Grid g, const DevCounters* cnt, const double* __restrict__ rho64,
                                                  const float* __restrict__ rho32, float* __restrict__ f,
-                                                 float* __restrict__ phi32) {
-  const double s = g.h * g.h / kEps0;
+                                                 float* __restrict__ phi32, double s) {
   const float s32 = (float)s;
   const long long nu = (long long)(g.nz - 1) * g.nplane;
   const long long last = nu - g.nplane;  // first unknown of the plane next to the anode
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256) k_rhs_f32(Grid g, const DevCounters* cnt,
 void launch_rhs_f32(const Grid& g, const DevCounters* cnt, const double* rho64, const float* rho32, float* f,
                     float* phi32, cudaStream_t st) {
   PIC_LAUNCH(grid_for((long long)(g.nz - 1) * g.nplane / 4 + 1), kBlock, 0, st, k_rhs_f32)(g, cnt, rho64, rho32, f,
-                                                                                          phi32);
+                                                                                          phi32, g.h * g.h / kEps0);
 }
 
 __global__ void k_phi_planes(Grid g, const DevCounters* cnt, double* phi) {

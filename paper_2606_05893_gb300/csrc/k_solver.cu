@@ -1598,19 +1598,34 @@ __device__ __forceinline__ void nb_sum_ff(const Lv& L, const float* __restrict__
   }
 }
 
-// sum f.f + folded terms -> tolerance (b = f + fold never materialised)
-__global__ void __launch_bounds__(256) k_dot_bb_ff(Lv L, const float* __restrict__ f, float fold_first, float fold_last,
+// sum f.f + folded terms -> tolerance (b = f + fold never materialised). f is
+// natural ([k][j][i], planes of nx ny) over the unknown planes, so this is a
+// flat pass: four values per thread (16-byte loads) where the plane size keeps
+// the planes 16-byte aligned (a float4 then never straddles two planes).
+__global__ void __launch_bounds__(kSB) k_dot_bb_ff(Lv L, const float* __restrict__ f, float fold_first, float fold_last,
                                                    double* part, SolveCtl* c, double rtol, int maxit) {
   pdl_enter();
+  const long long pl = L.pl;
+  const long long nu = (long long)(L.nz - 1) * pl;
+  const long long last = nu - pl;  // first unknown of the plane next to the anode
+  auto sq = [&](float bv, long long u) -> float {
+    if (u < pl) bv += fold_first;
+    if (u >= last) bv += fold_last;
+    return bv * bv;
+  };
   float acc = 0.f;
-  ROWS3K(L, L.nx) {
-    if (!in_x) continue;
-    const int u = k * L.pl + j * L.nx + i;
-    float bv = f[u];
-    if (k == 0) bv += fold_first;
-    if (k == L.nz - 2) bv += fold_last;
-    acc += bv * bv;
+  long long u0 = 0;
+  if ((pl & 3) == 0) {
+    const float4* f4 = reinterpret_cast<const float4*>(f);
+    const long long n4 = nu >> 2;
+    for (long long q = gtid(); q < n4; q += gstride()) {
+      const float4 v = f4[q];
+      const long long u = q << 2;
+      acc += (sq(v.x, u) + sq(v.y, u)) + (sq(v.z, u) + sq(v.w, u));
+    }
+    u0 = n4 << 2;
   }
+  for (long long u = u0 + gtid(); u < nu; u += gstride()) acc += sq(f[u], u);
   double bb;
   if (grid_total(acc, part, &c->ticket, &bb)) fin_bb(bb, c, rtol, maxit);
 }
@@ -1770,6 +1785,29 @@ __global__ void __launch_bounds__(256) k_apply_pq(Lv L, const T* __restrict__ p,
 
 // q = A p ; p.q -> alpha, on the split finest level (both colours per thread;
 // planes strided as in the natural kernel, at most one wave of blocks)
+// the centre and the six neighbours of one point (absent z neighbours 0)
+template <class T>
+struct Pt7 {
+  T c, xm, xp, ym, yp, zm, zp;
+};
+template <class T>
+__device__ __forceinline__ Pt7<T> load_pt7(const T* __restrict__ self, const T* __restrict__ o, int at, const SpNb& n) {
+  Pt7<T> v;
+  v.c = self[at];
+  v.xm = o[n.xm];
+  v.xp = o[n.xp];
+  v.ym = o[n.ym];
+  v.yp = o[n.yp];
+  v.zm = n.zm >= 0 ? o[n.zm] : (T)0;
+  v.zp = n.zp >= 0 ? o[n.zp] : (T)0;
+  return v;
+}
+// 6 c - the neighbours, summed in sp_sum's order (adding an absent 0 is exact)
+template <class T>
+__device__ __forceinline__ T apply_pt7(const Pt7<T>& v) {
+  return (T)6 * v.c - (((((v.xm + v.xp) + v.ym) + v.yp) + v.zm) + v.zp);
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_apply_pq_s(Lv L, const T* __restrict__ p, T* __restrict__ q, double* part,
                                                     SolveCtl* c) {
@@ -1778,17 +1816,19 @@ __global__ void __launch_bounds__(256) k_apply_pq_s(Lv L, const T* __restrict__ 
   const int m = blockIdx.x * kBX + threadIdx.x;
   const int hx = L.nx >> 1, half = L.nu >> 1;
   if (m < hx) {
+    // both colours of a point per pass, their fourteen loads issued together
     for (int k = blockIdx.z; k < L.nz - 1; k += gridDim.z)
       for (int j = blockIdx.y * kBY + threadIdx.y; j < L.ny; j += gridDim.y * kBY) {
         const int row = (k * L.ny + j) * hx + m;
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          const SpNb n = sp_nb(L, m, j, k, (j + k + 1 + cc) & 1);
-          const T pv = p[cc * half + row];
-          const T qv = (T)6 * pv - sp_sum(p + (cc ^ 1) * half, n);
-          q[cc * half + row] = qv;
-          acc += pv * qv;
-        }
+        const SpNb n0 = sp_nb(L, m, j, k, (j + k + 1) & 1);
+        const SpNb n1 = sp_nb(L, m, j, k, (j + k) & 1);
+        const Pt7<T> a = load_pt7(p, p + half, row, n0);
+        const Pt7<T> b = load_pt7(p + half, p, row, n1);
+        const T qa = apply_pt7(a), qb = apply_pt7(b);
+        q[row] = qa;
+        q[half + row] = qb;
+        acc += a.c * qa;
+        acc += b.c * qb;
       }
   }
   double pq;
@@ -2081,7 +2121,7 @@ cudaError_t Solver::record(cudaStream_t s0) {
   cudaGraphConditionalHandle h_outer, h_inner;
   cudaGraph_t outer_body = nullptr, inner_body = nullptr;
   if (mixed) {
-    SOLVER_LAUNCH(g3r(L), kB3, 0, s0, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, rtol, maxit);
+    SOLVER_LAUNCH(sgrid(L.nu / 4 + 1), kSB, 0, s0, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, rtol, maxit);
   } else {
     SOLVER_LAUNCH(G, kSB, 0, s0, k_dot_bb)(L.nu, b, part, ctl, rtol, maxit);
   }
@@ -2168,7 +2208,9 @@ cudaError_t Solver::run_host(cudaStream_t s) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return e;
   };
-  if (mixed) SOLVER_LAUNCH(g3r(L), kB3, 0, s, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, h_rtol, h_maxit);
+  if (mixed)
+    SOLVER_LAUNCH(sgrid(L.nu / 4 + 1), kSB, 0, s, k_dot_bb_ff)(L, f32, fold_first(), fold_last(), part, ctl, h_rtol,
+                                                              h_maxit);
   else SOLVER_LAUNCH(G, kSB, 0, s, k_dot_bb)(L.nu, b, part, ctl, h_rtol, h_maxit);
   for (int outer = 0; outer < max_outer + 1; ++outer) {
     if (mixed)
