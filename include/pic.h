@@ -259,6 +259,22 @@ pic_status pic_destroy(pic_handle* h);
 /* Text of the last error on this handle (static storage, never NULL). */
 const char* pic_last_error(pic_handle* h);
 
+/* Device memory from the caller's allocator (a pool such as PyTorch's caching
+ * allocator) instead of cudaMalloc / cudaFree. Resource management only: the
+ * paper has no counterpart. Process-wide: every device buffer that a PIC or
+ * U-Net handle created afterwards takes (stores, grids, solver, staging,
+ * scratch) comes from alloc(bytes, ctx) and goes back through
+ * free_fn(ptr, ctx); before each free_fn the library synchronises the device,
+ * as cudaFree does. alloc must return memory of the current device aligned to
+ * 256 bytes, or NULL (the library call then fails with PIC_ENOMEM or
+ * PIC_ECUDA). Both NULL restores cudaMalloc / cudaFree. PIC_EINVAL if exactly
+ * one is NULL; PIC_ESTATE while any PIC or U-Net handle is alive (memory must
+ * return to the allocator it came from). Not thread-safe against concurrent
+ * handle creation. */
+typedef void* (*pic_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*pic_free_fn)(void* ptr, void* ctx);
+pic_status pic_set_allocator(pic_alloc_fn alloc, pic_free_fn free_fn, void* ctx);
+
 /* ---- inspection, test and tuning hooks (synchronous) -----------------------
  * These have no counterpart in the paper: they read or set the state that the
  * steps above work on, so that tests can compare it with the oracle and

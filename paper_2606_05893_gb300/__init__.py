@@ -88,7 +88,7 @@ EXPORTED = ["pic_create", "pic_inject", "pic_inject_particles", "pic_inject_part
             "pic_set_mcc_background", "pic_version", "pic_set_profiling", "pic_get_phase_times",
             "pic_launch_count", "pic_kernel_count", "pic_poisson_solve_static", "pic_set_sort_interval",
             "pic_set_hit_log", "pic_get_hits", "pic_set_circuit", "pic_save", "pic_load",
-            "pic_set_warm_unet", "pic_get_phi_device", "pic_set_launch_shape",
+            "pic_set_warm_unet", "pic_get_phi_device", "pic_set_launch_shape", "pic_set_allocator",
             "unet_num_weights", "unet_create", "unet_destroy", "unet_set_weights", "unet_get_weights",
             "unet_forward", "unet_backward", "unet_get_grads", "unet_train_step", "unet_last_error",
             "unet_launch_count", "unet_make_sample", "unet_layer_forward", "unet_layer_backward",
@@ -144,6 +144,7 @@ def load_library(path: str = None):
         "pic_set_mcc_background": ([P, C.c_int32, C.c_double], st),
         "pic_set_sort_interval": ([P, C.c_int32, C.c_int32], st),
         "pic_set_launch_shape": ([P, C.c_int32, C.c_int32], st),
+        "pic_set_allocator": ([P, P, P], st),
         "pic_set_hit_log": ([P, C.c_int32, C.c_int64], st),
         "pic_set_circuit": ([P, C.c_int32, C.c_double, C.c_double, C.c_double], st),
         "pic_save": ([P, C.c_int32, C.c_char_p], st),
@@ -384,6 +385,44 @@ def pic_set_sort_interval(h, inst, interval):
 
 def pic_set_launch_shape(h, inst, blocks_per_sm):
     return _check(h, load_library().pic_set_launch_shape(h, inst, blocks_per_sm))
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+_allocator = None  # the registered callbacks, kept alive while the library may call them
+
+
+def pic_set_allocator(alloc=None, free=None):
+    """Route the library's device memory through Python callables alloc(nbytes) -> int
+    pointer (0 on failure) and free(ptr); both None restores cudaMalloc / cudaFree.
+    Only while no PIC or U-Net handle is alive (PicError otherwise)."""
+    global _allocator
+    if (alloc is None) != (free is None):
+        raise ValueError("give both alloc and free, or neither")
+    if alloc is None:
+        _check(None, load_library().pic_set_allocator(None, None, None))
+        _allocator = None
+        return
+    a = ALLOC_FN(lambda nbytes, ctx: alloc(int(nbytes)) or None)
+    f = FREE_FN(lambda ptr, ctx: free(int(ptr)))
+    _check(None, load_library().pic_set_allocator(C.cast(a, C.c_void_p), C.cast(f, C.c_void_p), None))
+    _allocator = (a, f)
+
+
+def use_torch_allocator(enable=True):
+    """Back the library's device memory by PyTorch's caching allocator (its
+    blocks count in torch.cuda.memory_allocated), or restore cudaMalloc."""
+    if not enable:
+        return pic_set_allocator()
+    import torch
+
+    def alloc(nbytes):
+        try:
+            return torch.cuda.caching_allocator_alloc(nbytes)
+        except RuntimeError:
+            return 0
+
+    return pic_set_allocator(alloc, torch.cuda.caching_allocator_delete)
 
 
 def pic_set_profiling(h, on=True):

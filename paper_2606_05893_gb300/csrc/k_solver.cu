@@ -23,6 +23,7 @@
 #include <cooperative_groups.h>
 #include <vector>
 
+#include "dev_mem.cuh"
 #include "pic_internal.cuh"
 #include "pic_kernels.cuh"
 #include "tc_ptx.cuh"
@@ -1118,17 +1119,17 @@ cudaError_t Mg<T>::init(const std::vector<MgLevel>& plan) {
   for (size_t l = 0; l < nl; ++l) {
     const size_t bytes = sizeof(T) * (size_t)(plan[l].nu > 0 ? plan[l].nu : 1);
     if (l > 0) {
-      if ((err = cudaMalloc(&e[l], bytes))) return err;
-      if ((err = cudaMalloc(&b[l], bytes))) return err;
+      if ((err = dev_malloc(&e[l], bytes))) return err;
+      if ((err = dev_malloc(&b[l], bytes))) return err;
     }
-    if ((err = cudaMalloc(&r[l], bytes))) return err;
+    if ((err = dev_malloc(&r[l], bytes))) return err;
   }
   const MgLevel& c = plan.back();
   coarse_dense = rb_ok && c.nu <= 1024 && nl >= 1;
   if (coarse_dense) {
     std::vector<double> inv = dense_inverse(c);
     std::vector<T> invT(inv.begin(), inv.end());
-    if ((err = cudaMalloc(&Ainv, sizeof(T) * invT.size()))) return err;
+    if ((err = dev_malloc(&Ainv, sizeof(T) * invT.size()))) return err;
     if ((err = cudaMemcpy(Ainv, invT.data(), sizeof(T) * invT.size(), cudaMemcpyHostToDevice))) return err;
   }
   // FP32: the coarse-grid correction is an exact fast-diagonalization solve at
@@ -1182,7 +1183,7 @@ cudaError_t Mg<T>::init(const std::vector<MgLevel>& plan) {
       for (int i = 0; i < M.nx; ++i) hlx[i] = (float)lx[i];
       for (int j = 0; j < M.ny; ++j) hly[j] = (float)ly[j];
       for (int r = 0; r < Pp; ++r) hlz[r] = r < P ? (float)lz[r] : 1.f;
-      if ((err = cudaMalloc(&spec_mem, sizeof(float) * h.size()))) return err;
+      if ((err = dev_malloc(&spec_mem, sizeof(float) * h.size()))) return err;
       if ((err = cudaMemcpy(spec_mem, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice))) return err;
       spec_smem_plane = sizeof(float) * (nxx + nyy + 2 * (size_t)M.ny * lxp);
       spec_smem_z = sizeof(float) * (2 * npp + 72 * (size_t)Pp);
@@ -1257,15 +1258,15 @@ cudaError_t Mg<T>::init(const std::vector<MgLevel>& plan) {
 
 template <class T>
 void Mg<T>::release() {
-  for (auto* p : e) cudaFree(p);
-  for (auto* p : b) cudaFree(p);
-  for (auto* p : r) cudaFree(p);
+  for (auto* p : e) dev_free(p);
+  for (auto* p : b) dev_free(p);
+  for (auto* p : r) dev_free(p);
   e.clear();
   b.clear();
   r.clear();
-  if (Ainv) cudaFree(Ainv);
+  if (Ainv) dev_free(Ainv);
   Ainv = nullptr;
-  if (spec_mem) cudaFree(spec_mem);
+  if (spec_mem) dev_free(spec_mem);
   spec_mem = nullptr;
   spectral_at = -1;
 }
@@ -1937,11 +1938,11 @@ cudaError_t Pcg<T>::init(const std::vector<MgLevel>& plan) {
   n = plan[0].nu;
   cudaError_t err;
   const size_t bytes = sizeof(T) * (size_t)(n > 0 ? n : 1);
-  if ((err = cudaMalloc(&r, bytes))) return err;
-  if ((err = cudaMalloc(&z, bytes))) return err;
-  if ((err = cudaMalloc(&p, bytes))) return err;
-  if ((err = cudaMalloc(&q, bytes))) return err;
-  if ((err = cudaMalloc(&d, bytes))) return err;
+  if ((err = dev_malloc(&r, bytes))) return err;
+  if ((err = dev_malloc(&z, bytes))) return err;
+  if ((err = dev_malloc(&p, bytes))) return err;
+  if ((err = dev_malloc(&q, bytes))) return err;
+  if ((err = dev_malloc(&d, bytes))) return err;
   if ((err = cudaMemset(p, 0, bytes))) return err;
   if ((err = cudaMemset(d, 0, bytes))) return err;
   return mg.init(plan);
@@ -1949,11 +1950,11 @@ cudaError_t Pcg<T>::init(const std::vector<MgLevel>& plan) {
 
 template <class T>
 void Pcg<T>::release() {
-  cudaFree(r);
-  cudaFree(z);
-  cudaFree(p);
-  cudaFree(q);
-  cudaFree(d);
+  dev_free(r);
+  dev_free(z);
+  dev_free(p);
+  dev_free(q);
+  dev_free(d);
   r = z = p = q = d = nullptr;
   mg.release();
 }
@@ -1970,17 +1971,17 @@ cudaError_t Solver::init(int nx, int ny, int nz, int precision_) {
   cudaError_t err;
   const size_t nn = (size_t)(n > 0 ? n : 1);
   if (precision == 0) {
-    if ((err = cudaMalloc(&b, sizeof(double) * nn))) return err;
+    if ((err = dev_malloc(&b, sizeof(double) * nn))) return err;
     if ((err = cudaMemset(b, 0, sizeof(double) * nn))) return err;
-    if ((err = cudaMalloc(&ax, sizeof(double) * nn))) return err;
+    if ((err = dev_malloc(&ax, sizeof(double) * nn))) return err;
   } else {
-    if ((err = cudaMalloc(&f32, sizeof(float) * nn))) return err;
+    if ((err = dev_malloc(&f32, sizeof(float) * nn))) return err;
     if ((err = cudaMemset(f32, 0, sizeof(float) * nn))) return err;
-    if ((err = cudaMalloc(&lo32, sizeof(float) * nn))) return err;
+    if ((err = dev_malloc(&lo32, sizeof(float) * nn))) return err;
     if ((err = cudaMemset(lo32, 0, sizeof(float) * nn))) return err;
   }
-  if ((err = cudaMalloc(&part, sizeof(double) * kPartsMax))) return err;
-  if ((err = cudaMalloc(&ctl, sizeof(SolveCtl)))) return err;
+  if ((err = dev_malloc(&part, sizeof(double) * kPartsMax))) return err;
+  if ((err = dev_malloc(&ctl, sizeof(SolveCtl)))) return err;
   if ((err = cudaMemset(ctl, 0, sizeof(SolveCtl)))) return err;
   if ((err = cudaMallocHost(&host_ctl, sizeof(SolveCtl)))) return err;
   memset(host_ctl, 0, sizeof(SolveCtl));
@@ -1995,12 +1996,12 @@ void Solver::release() {
   if (graph) cudaGraphDestroy(graph);
   exec = nullptr;
   graph = nullptr;
-  cudaFree(b);
-  cudaFree(ax);
-  cudaFree(f32);
-  cudaFree(lo32);
-  cudaFree(part);
-  cudaFree(ctl);
+  dev_free(b);
+  dev_free(ax);
+  dev_free(f32);
+  dev_free(lo32);
+  dev_free(part);
+  dev_free(ctl);
   if (host_ctl) cudaFreeHost(host_ctl);
   host_ctl = nullptr;
   for (auto& a : aux) {

@@ -10,12 +10,15 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "../../include/pic.h"
 #include "../../include/unet.h"
+#include "dev_mem.cuh"
 #include "pic_internal.cuh"
 #include "pic_kernels.cuh"
 #include "pic_solver.cuh"
@@ -26,6 +29,52 @@
 using namespace pic;
 
 namespace pic {
+
+// Device memory (dev_mem.cuh): cudaMalloc / cudaFree, or the caller's allocator.
+// The allocator may change only while no handle holds memory from it.
+namespace {
+std::mutex g_alloc_mu;
+pic_alloc_fn g_alloc_fn = nullptr;
+pic_free_fn g_free_fn = nullptr;
+void* g_alloc_ctx = nullptr;
+int g_live_handles = 0;
+}  // namespace
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (!g_alloc_fn) return cudaMalloc(p, bytes);
+  void* q = g_alloc_fn(bytes ? bytes : 1, g_alloc_ctx);
+  if (!q) return cudaErrorMemoryAllocation;
+  if (reinterpret_cast<uintptr_t>(q) & 255u) {  // the kernels' vector and bulk copies want cudaMalloc's alignment
+    g_free_fn(q, g_alloc_ctx);
+    return cudaErrorInvalidValue;
+  }
+  *p = q;
+  return cudaSuccess;
+}
+cudaError_t dev_free(void* p) {
+  if (!p) return cudaSuccess;
+  if (!g_free_fn) return cudaFree(p);
+  // as cudaFree does: no queued work may still use the memory once it is handed back
+  const cudaError_t e = cudaDeviceSynchronize();
+  g_free_fn(p, g_alloc_ctx);
+  return e;
+}
+void dev_handle_opened() {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  ++g_live_handles;
+}
+void dev_handle_closed() {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  --g_live_handles;
+}
+static bool set_device_allocator(pic_alloc_fn alloc, pic_free_fn free_fn, void* ctx) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  if (g_live_handles != 0) return false;
+  g_alloc_fn = alloc;
+  g_free_fn = free_fn;
+  g_alloc_ctx = ctx;
+  return true;
+}
 unsigned long long g_launches = 0;
 unsigned long long g_kernels = 0;
 void set_static_error(const char* msg);
@@ -289,7 +338,7 @@ template <class T>
 cudaError_t dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  return cudaMalloc((void**)p, sizeof(T) * count);
+  return dev_malloc((void**)p, sizeof(T) * count);
 }
 
 
@@ -306,69 +355,69 @@ void free_instance(Instance* I) {
   if (I->own_stream && I->stream) cudaStreamDestroy(I->stream);
   if (I->done) cudaEventDestroy(I->done);
   for (int s = 0; s < kMaxSpecies; ++s) {
-    for (int b = 0; b < 2; ++b) cudaFree(I->mem[s][b]);
-    cudaFree(I->ncount[s]);
-    cudaFree(I->ncount_next[s]);
-    cudaFree(I->cell_start[s]);
+    for (int b = 0; b < 2; ++b) dev_free(I->mem[s][b]);
+    dev_free(I->ncount[s]);
+    dev_free(I->ncount_next[s]);
+    dev_free(I->cell_start[s]);
   }
   for (auto& x : I->xs) {
-    cudaFree(x.dE);
-    cudaFree(x.dsig);
-    cudaFree(x.dEf);
-    cudaFree(x.dsigf);
-    cudaFree(x.dslopef);
-    cudaFree(x.dbucket);
+    dev_free(x.dE);
+    dev_free(x.dsig);
+    dev_free(x.dEf);
+    dev_free(x.dsigf);
+    dev_free(x.dslopef);
+    dev_free(x.dbucket);
   }
-  cudaFree(I->cnt);
+  dev_free(I->cnt);
   if (I->host_cnt) cudaFreeHost(I->host_cnt);
-  cudaFree(I->rho64);
-  cudaFree(I->rho32);
-  cudaFree(I->rho64_next);
-  cudaFree(I->rho32_next);
-  cudaFree(I->plan);
+  dev_free(I->rho64);
+  dev_free(I->rho32);
+  dev_free(I->rho64_next);
+  dev_free(I->rho32_next);
+  dev_free(I->plan);
   for (auto& e : I->step_exec)
     if (e) cudaGraphExecDestroy(e);
   if (I->cap_stream) cudaStreamDestroy(I->cap_stream);
   if (I->cap_done) cudaEventDestroy(I->cap_done);
-  cudaFree(I->phi);
-  cudaFree(I->E64);
-  cudaFree(I->E32);
-  cudaFree(I->phi32);
-  cudaFree(I->acc8);
-  cudaFree(I->ev);
-  cudaFree(I->cand);
-  cudaFree(I->cand_cell);
-  cudaFree(I->ev_head);
-  cudaFree(I->cand_head);
-  cudaFree(I->ion_log);
-  cudaFree(I->evsort.ka);
-  cudaFree(I->evsort.kb);
-  cudaFree(I->evsort.va);
-  cudaFree(I->evsort.vb);
-  cudaFree(I->evsort.hist);
-  cudaFree(I->evsort.digit_tot);
-  cudaFree(I->evsort.small_done);
+  dev_free(I->phi);
+  dev_free(I->E64);
+  dev_free(I->E32);
+  dev_free(I->phi32);
+  dev_free(I->acc8);
+  dev_free(I->ev);
+  dev_free(I->cand);
+  dev_free(I->cand_cell);
+  dev_free(I->ev_head);
+  dev_free(I->cand_head);
+  dev_free(I->ion_log);
+  dev_free(I->evsort.ka);
+  dev_free(I->evsort.kb);
+  dev_free(I->evsort.va);
+  dev_free(I->evsort.vb);
+  dev_free(I->evsort.hist);
+  dev_free(I->evsort.digit_tot);
+  dev_free(I->evsort.small_done);
   if (I->evsort.aux) cudaStreamDestroy(I->evsort.aux);
-  cudaFree(I->csort.ka);
-  cudaFree(I->csort.kb);
-  cudaFree(I->csort.va);
-  cudaFree(I->csort.vb);
-  cudaFree(I->csort.hist);
-  cudaFree(I->csort.digit_tot);
-  cudaFree(I->csort.small_done);
+  dev_free(I->csort.ka);
+  dev_free(I->csort.kb);
+  dev_free(I->csort.va);
+  dev_free(I->csort.vb);
+  dev_free(I->csort.hist);
+  dev_free(I->csort.digit_tot);
+  dev_free(I->csort.small_done);
   if (I->csort.aux) cudaStreamDestroy(I->csort.aux);
   free_hit_log(I);
-  cudaFree(I->cell_count);
-  cudaFree(I->seg_ctl);
-  cudaFree(I->seg_big);
+  dev_free(I->cell_count);
+  dev_free(I->seg_ctl);
+  dev_free(I->seg_big);
   if (I->seg_host) cudaFreeHost(I->seg_host);
-  cudaFree(I->scan_tmp);
-  cudaFree(I->red);
-  cudaFree(I->mom_part);
-  cudaFree(I->mom_ticket);
-  cudaFree(I->stage_x);
-  cudaFree(I->stage_v);
-  cudaFree(I->stage_m);
+  dev_free(I->scan_tmp);
+  dev_free(I->red);
+  dev_free(I->mom_part);
+  dev_free(I->mom_ticket);
+  dev_free(I->stage_x);
+  dev_free(I->stage_v);
+  dev_free(I->stage_m);
   if (I->hstage) cudaFreeHost(I->hstage);
   if (I->hstage_done) cudaEventDestroy(I->hstage_done);
   I->timer.release();
@@ -586,7 +635,7 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
     for (int b = 0; b < 2; ++b) {
       if (!I->mixed) {
         const size_t bytes = (size_t)cap * (6 * sizeof(double) + (I->weighted ? 2 : 1) * sizeof(uint32_t));
-        CK(h, cudaMalloc(&I->mem[s][b], bytes));
+        CK(h, dev_malloc(&I->mem[s][b], bytes));
         char* p = (char*)I->mem[s][b];
         Store64& S = I->s64[s][b];
         S.x = (double*)p;
@@ -599,7 +648,7 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
         S.mw = I->weighted ? S.pid + cap : nullptr;
       } else {
         const size_t bytes = (size_t)cap * (sizeof(int32_t) + 6 * sizeof(float) + (I->weighted ? 2 : 1) * sizeof(uint32_t));
-        CK(h, cudaMalloc(&I->mem[s][b], bytes));
+        CK(h, dev_malloc(&I->mem[s][b], bytes));
         char* p = (char*)I->mem[s][b];
         StoreMx& S = I->smx[s][b];
         S.cell = (int32_t*)p;
@@ -659,7 +708,7 @@ pic_status create_instance(pic_handle* h, const pic_instance_cfg& c, Instance** 
   CK(h, dalloc(&I->seg_ctl, 1));
   CK(h, dalloc(&I->seg_big, g.ncell + 1));
   CK(h, cudaMallocHost((void**)&I->seg_host, sizeof(SegCtl)));
-  CK(h, cudaMalloc(&I->scan_tmp, scan_temp_bytes(g.ncell)));
+  CK(h, dev_malloc(&I->scan_tmp, scan_temp_bytes(g.ncell)));
   CK(h, dalloc(&I->red, 64));
   if (I->mixed) {
     CK(h, dalloc(&I->mom_part, (size_t)kMomBlocks * kMomSlots));
@@ -1070,12 +1119,12 @@ pic_status download_carries(pic_handle* h, Instance* I) {
 
 void free_hit_log(Instance* I) {
   HitLog& L = I->hits;
-  cudaFree(L.n);
-  cudaFree(L.pid);
-  cudaFree(L.species);
-  cudaFree(L.step);
-  cudaFree(L.xy);
-  cudaFree(L.v);
+  dev_free(L.n);
+  dev_free(L.pid);
+  dev_free(L.species);
+  dev_free(L.step);
+  dev_free(L.xy);
+  dev_free(L.v);
   L = HitLog{};
 }
 
@@ -1358,9 +1407,11 @@ pic_status pic_create(const pic_instance_cfg* cfgs, int32_t n_instances, void* c
     if (st != PIC_OK) return st;
   }
   pic_handle* h = new pic_handle();
+  dev_handle_opened();
   h->stream = (cudaStream_t)cuda_stream;
   if (n_instances > 1 && cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess) {
     delete h;
+    dev_handle_closed();
     return fail(nullptr, PIC_ECUDA, "event creation failed");
   }
   for (int i = 0; i < n_instances; ++i) {
@@ -1381,6 +1432,7 @@ pic_status pic_create(const pic_instance_cfg* cfgs, int32_t n_instances, void* c
       g_static_err = h->err;
       for (auto* p : h->inst) free_instance(p);
       delete h;
+      dev_handle_closed();
       return st;
     }
     launch_phi_planes(I->g, I->cnt, I->phi, h->stream);
@@ -1391,6 +1443,7 @@ pic_status pic_create(const pic_instance_cfg* cfgs, int32_t n_instances, void* c
     g_static_err = std::string("initialisation failed: ") + cudaGetErrorString(e);
     for (auto* p : h->inst) free_instance(p);
     delete h;
+    dev_handle_closed();
     return PIC_ECUDA;
   }
   *out = h;
@@ -1408,6 +1461,15 @@ pic_status pic_destroy(pic_handle* h) {
   for (auto* I : h->inst) free_instance(I);
   if (h->fork) cudaEventDestroy(h->fork);
   delete h;
+  dev_handle_closed();
+  return PIC_OK;
+}
+
+pic_status pic_set_allocator(pic_alloc_fn alloc, pic_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(nullptr, PIC_EINVAL, "pic_set_allocator: give both functions or neither");
+  if (!set_device_allocator(alloc, free_fn, ctx))
+    return fail(nullptr, PIC_ESTATE, "pic_set_allocator: PIC or U-Net handles are alive");
   return PIC_OK;
 }
 
@@ -1468,9 +1530,9 @@ static pic_status inject_particles(pic_handle* h, int32_t inst, int32_t species,
   if ((unsigned long long)I->host_cnt->next_pid + (unsigned long long)n > 0xFFFFFFFEull)
     return fail(h, PIC_ECAPACITY, "pid space exhausted");
   if (n > I->stage_cap) {
-    cudaFree(I->stage_x);
-    cudaFree(I->stage_v);
-    cudaFree(I->stage_m);
+    dev_free(I->stage_x);
+    dev_free(I->stage_v);
+    dev_free(I->stage_m);
     I->stage_x = I->stage_v = nullptr;
     I->stage_m = nullptr;
     I->stage_cap = 0;
@@ -1769,10 +1831,10 @@ static pic_status get_particles(pic_handle* h, int32_t inst, int32_t species, in
   cudaMemcpyAsync(hp.data(), dp, sizeof(uint32_t) * slots, cudaMemcpyDeviceToHost, h->stream);
   if (mw) cudaMemcpyAsync(hm.data(), dm, sizeof(uint32_t) * slots, cudaMemcpyDeviceToHost, h->stream);
   cudaError_t e = cudaStreamSynchronize(h->stream);
-  cudaFree(dx);
-  cudaFree(dv);
-  cudaFree(dp);
-  cudaFree(dm);
+  dev_free(dx);
+  dev_free(dv);
+  dev_free(dp);
+  dev_free(dm);
   if (e != cudaSuccess) return fail(h, PIC_ECUDA, "download failed: %s", cudaGetErrorString(e));
   long long w = 0;
   for (long long i = 0; i < slots; ++i) {
@@ -1887,10 +1949,10 @@ pic_status pic_solve(pic_handle* h, int32_t inst, const double* rho, double* phi
     CK(h, I->solver.invalidate(s));
   }
   cudaError_t e = cudaStreamSynchronize(s);
-  cudaFree(save_lo);
-  cudaFree(save32);
-  cudaFree(drho);
-  cudaFree(save_phi);
+  dev_free(save_lo);
+  dev_free(save32);
+  dev_free(drho);
+  dev_free(save_phi);
   if (e != cudaSuccess) return fail(h, PIC_ECUDA, "solve failed: %s", cudaGetErrorString(e));
   if (iters) *iters = r.iters;
   if (resid_rel) *resid_rel = r.resid_rel;
@@ -1948,7 +2010,7 @@ pic_status pic_philox(pic_handle* h, int64_t n, const uint32_t ctr[4], const uin
   launch_philox(n, make_uint4(ctr[0], ctr[1], ctr[2], ctr[3]), make_uint2(key[0], key[1]), d, h->stream);
   CK(h, cudaMemcpyAsync(out, d, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost, h->stream));
   cudaError_t e = cudaStreamSynchronize(h->stream);
-  cudaFree(d);
+  dev_free(d);
   if (e != cudaSuccess) return fail(h, PIC_ECUDA, "philox failed: %s", cudaGetErrorString(e));
   return PIC_OK;
 }

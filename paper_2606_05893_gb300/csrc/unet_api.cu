@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/unet.h"
+#include "dev_mem.cuh"
 #include "unet_internal.cuh"
 #include "unet_warm.cuh"
 
@@ -933,6 +934,7 @@ extern "C" pic_status unet_create(int32_t D, int32_t H, int32_t W, void* cuda_st
   *out = nullptr;
   if (D < 8 || H < 8 || W < 8 || D % 8 || H % 8 || W % 8 || W > 512 || H > 4096 || D > 4096) return PIC_EINVAL;
   unet_handle* n = new unet_handle();
+  pic::dev_handle_opened();
   n->D = D;
   n->H = H;
   n->W = W;
@@ -940,7 +942,7 @@ extern "C" pic_status unet_create(int32_t D, int32_t H, int32_t W, void* cuda_st
   for (int l = 0; l < 4; ++l) n->vol[l] = make_vol(D >> l, H >> l, W >> l);
   auto dev_alloc = [&](size_t bytes) -> void* {
     void* p = nullptr;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    if (pic::dev_malloc(&p, bytes) != cudaSuccess) return nullptr;
     n->allocs.push_back(p);
     if (cudaMemsetAsync(p, 0, bytes, n->stream) != cudaSuccess) return nullptr;
     return p;
@@ -1041,8 +1043,9 @@ extern "C" pic_status unet_destroy(unet_handle* n) {
   if (n->stream) cudaStreamSynchronize(n->stream);
   collect_times(n);
   for (cudaEvent_t e : n->ev_pool) cudaEventDestroy(e);
-  for (void* p : n->allocs) cudaFree(p);
+  for (void* p : n->allocs) pic::dev_free(p);
   delete n;
+  pic::dev_handle_closed();
   return PIC_OK;
 }
 
@@ -1122,14 +1125,14 @@ namespace {
 struct Scratch {
   std::vector<void*> p;
   ~Scratch() {
-    for (void* q : p) cudaFree(q);
+    for (void* q : p) pic::dev_free(q);
   }
   Tensor tensor(const Vol& v, int C, int level, cudaStream_t st) {
     Tensor t;
     t.C = C;
     t.level = level;
     const size_t bytes = sizeof(__nv_bfloat16) * 8ull * (C / 8) * v.rows;
-    if (cudaMalloc((void**)&t.p, bytes) != cudaSuccess) {
+    if (pic::dev_malloc((void**)&t.p, bytes) != cudaSuccess) {
       t.p = nullptr;
       return t;
     }

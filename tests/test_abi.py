@@ -78,3 +78,17 @@ def test_invalid_configuration_is_rejected_without_gpu_work(lib):
     st = lib.pic_create(C.byref(cfg), 1, None, C.byref(h))
     assert st == pkg.PIC_EINVAL
     assert not h.value
+
+
+def test_allocator_argument_checks(lib):
+    # pic_set_allocator touches no device: exactly one function is refused, both or
+    # neither are taken (and neither restores cudaMalloc / cudaFree)
+    import paper_2606_05893_gb300 as pkg
+    keep = pkg.ALLOC_FN(lambda n, ctx: None)
+    assert lib.pic_set_allocator(C.cast(keep, C.c_void_p), None, None) == pkg.PIC_EINVAL
+    assert "both" in pkg.pic_last_error(None)
+    with pytest.raises(ValueError):
+        pkg.pic_set_allocator(lambda n: 0, None)
+    pkg.pic_set_allocator(lambda n: 0, lambda p: None)
+    pkg.pic_set_allocator()
+    assert lib.pic_set_allocator(None, None, None) == pkg.PIC_OK
