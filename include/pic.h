@@ -66,7 +66,11 @@ typedef enum {
 enum { PIC_ELECTRON = 0, PIC_NEUTRAL = 1, PIC_ION = 2 };
 enum { PIC_XS_IONIZATION = 0, PIC_XS_ELASTIC = 1, PIC_XS_CHARGE_EXCHANGE = 2 };
 enum { PIC_FP64 = 0, PIC_MIXED = 1 };
-enum { PIC_WARM_PREV = 0, PIC_WARM_ZERO = 1 };
+/* PIC_WARM_UNET: the instance is meant to start its solves from the learned
+ * warm start attached with pic_set_warm_unet (include/unet.h; a network handle
+ * cannot live in this plain-data configuration); until one is attached it
+ * starts from the previous potential, as PIC_WARM_PREV. */
+enum { PIC_WARM_PREV = 0, PIC_WARM_ZERO = 1, PIC_WARM_UNET = 2 };
 enum { PIC_FIELD_RHO = 0, PIC_FIELD_PHI = 1, PIC_FIELD_NCOUNT = 2 };
 
 /* One species of superparticles (PIC/MCC paragraph: SPs of weight w_SP). */
@@ -124,7 +128,7 @@ typedef struct {
   const pic_species* species;
   int32_t nxsec;           /* 0..PIC_MAX_XSEC */
   const pic_xsec* xsec;
-  int32_t warm_start;      /* PIC_WARM_PREV (previous phi) | PIC_WARM_ZERO */
+  int32_t warm_start;      /* PIC_WARM_PREV (previous phi) | PIC_WARM_ZERO | PIC_WARM_UNET */
   int32_t variable_weights; /* 0 | 1: superparticles carry integer multiplicities
                                (pic_inject_particles_m); see below */
 } pic_instance_cfg;

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECAPAC
 PIC_ELECTRON, PIC_NEUTRAL, PIC_ION = 0, 1, 2
 PIC_XS_IONIZATION, PIC_XS_ELASTIC, PIC_XS_CHARGE_EXCHANGE = 0, 1, 2
 PIC_FP64, PIC_MIXED = 0, 1
-PIC_WARM_PREV, PIC_WARM_ZERO = 0, 1
+PIC_WARM_PREV, PIC_WARM_ZERO, PIC_WARM_UNET = 0, 1, 2
 PIC_FIELD_RHO, PIC_FIELD_PHI, PIC_FIELD_NCOUNT = 0, 1, 2
 
 

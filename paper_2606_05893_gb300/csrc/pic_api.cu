@@ -449,7 +449,7 @@ pic_status validate(pic_handle* h, const pic_instance_cfg& c, int idx) {
   if (c.nxsec < 0 || c.nxsec > PIC_MAX_XSEC || (c.nxsec > 0 && !c.xsec))
     return fail(h, PIC_EINVAL, "instance %d: nxsec must be 0..%d", idx, PIC_MAX_XSEC);
   if (c.precision != PIC_FP64 && c.precision != PIC_MIXED) return fail(h, PIC_EINVAL, "instance %d: bad precision", idx);
-  if (c.warm_start != PIC_WARM_PREV && c.warm_start != PIC_WARM_ZERO)
+  if (c.warm_start != PIC_WARM_PREV && c.warm_start != PIC_WARM_ZERO && c.warm_start != PIC_WARM_UNET)
     return fail(h, PIC_EINVAL, "instance %d: bad warm_start", idx);
   if (c.variable_weights != 0 && c.variable_weights != 1)
     return fail(h, PIC_EINVAL, "instance %d: variable_weights must be 0 or 1", idx);

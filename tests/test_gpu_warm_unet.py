@@ -9,6 +9,8 @@
    and both solves run to a 1e-13 residual, the FP64 store still matches the CPU
    oracle (which starts from the previous potential) within the parity
    tolerances of tests/test_gpu_parity.py.
+ - An instance configured with PIC_WARM_UNET and no network attached starts
+   from the previous potential, as PIC_WARM_PREV.
  - What training gains: a network trained for a few hundred steps on samples
    of 32x32x64-cell runs leaves, on held-out samples, a smaller starting
    residual than the previous potential does, and in a held-out run the solve
@@ -108,3 +110,20 @@ def test_trained_network_lowers_the_starting_residual(pkg):
     assert np.mean(losses[-20:]) < np.mean(losses[:20])
     assert np.mean(after) < 0.8
     assert max(ev["unet"]["resid"]) <= 1e-8 and max(ev["plain"]["resid"]) <= 1e-8
+
+
+def test_unet_mode_without_a_network_starts_from_the_previous_potential(pkg):
+    # PIC_WARM_UNET marks the instance for a network; with none attached it is
+    # PIC_WARM_PREV: the same integers and iterations, phi within FP64 parity
+    wl = W.config_tiny(seed=4)
+    a = pkg.Simulation(wl, precision=0, warm_start=pkg.PIC_WARM_PREV)
+    b = pkg.Simulation(wl, precision=0, warm_start=pkg.PIC_WARM_UNET)
+    for _ in range(4):
+        a.step(1)
+        b.step(1)
+    ma, mb = a.moments(), b.moments()
+    compare_integer_moments(mb, ma)
+    assert ma["cg_iters"] == mb["cg_iters"]
+    assert rel_inf(b.phi(), a.phi()) <= 1e-10
+    a.close()
+    b.close()
