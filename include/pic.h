@@ -233,8 +233,10 @@ pic_status pic_inject_particles(pic_handle* h, int32_t inst, int32_t species, in
  * average, charge and particle numbers exactly. Checkpoints (pic_save)
  * carry the multiplicities.
  * pic_inject_particles_m: as pic_inject_particles, with mw[n] (host, copied).
- * PIC_EINVAL if mw is NULL or an mw[i] is 0, or above 1 on an instance
- * without variable weights. The call synchronises the stream.
+ * PIC_EINVAL if mw is NULL or an mw[i] is 0 or above 2^24, or above 1 on an
+ * instance without variable weights. The multiplicities of the neutrals in one
+ * cell must sum below 2^31 (the per-cell counts are int32). The call
+ * synchronises the stream.
  * pic_get_multiplicity: the multiplicities of a species' live particles in the
  * order pic_get_particles gives (cap, *n and errors as there). */
 pic_status pic_inject_particles_m(pic_handle* h, int32_t inst, int32_t species, int64_t n,

@@ -124,14 +124,20 @@ __global__ void __launch_bounds__(kDepBlock) k_count_neutrals(DepositArgs<S> a) 
     const long long i = base + threadIdx.x;
     int cell = -1;
     float one[1] = {0.f};  // counts are exact in FP32 (a warp holds 32 at most)
+    uint32_t mw = 0u;
     if (i < n) {
       const auto p = store_read(a.st, g, i);
       if (PIC_BOUNDS(particle_cell(p) >= 0 && particle_cell(p) < g.ncell, a.cnt)) {
         cell = (int)particle_cell(p);
-        one[0] = p.pid != kPidDead ? (float)p.mw : 0.f;  // multiplicities: exact in FP32 below 2^24 per warp
+        one[0] = p.pid != kPidDead ? 1.f : 0.f;
+        mw = p.pid != kPidDead ? p.mw : 0u;
       }
     }
-    if (warp_run_sum(cell, one) && cell >= 0 && one[0] > 0.f) atomicAdd(&a.ncount[cell], (int)one[0]);
+    if (a.st.mw) {  // multiplicities: integer adds per particle (an FP32 run sum could round)
+      if (cell >= 0 && mw) atomicAdd(&a.ncount[cell], (int)mw);
+    } else if (warp_run_sum(cell, one) && cell >= 0 && one[0] > 0.f) {
+      atomicAdd(&a.ncount[cell], (int)one[0]);
+    }
   }
 }
 

@@ -1501,6 +1501,10 @@ pic_status pic_inject(pic_handle* h, int32_t inst, int32_t species, double cx, d
   return PIC_OK;
 }
 
+// Largest multiplicity of an upload: a charge q w mw stays exact in the FP32
+// deposit of the mixed store.
+constexpr uint32_t kMaxMultiplicity = 1u << 24;
+
 static pic_status inject_particles(pic_handle* h, int32_t inst, int32_t species, int64_t n, const double* x,
                                    const double* v, const uint32_t* mw) {
   pic_status st = check(h, inst);
@@ -1515,9 +1519,10 @@ static pic_status inject_particles(pic_handle* h, int32_t inst, int32_t species,
       return fail(h, PIC_EINVAL, "particle %lld outside the domain", (long long)i);
     for (int c = 0; c < 3; ++c)
       if (!std::isfinite(v[3 * i + c])) return fail(h, PIC_EINVAL, "particle %lld has a non-finite velocity", (long long)i);
-    if (mw && (mw[i] == 0 || (mw[i] != 1 && !I->weighted)))
-      return fail(h, PIC_EINVAL, "particle %lld: multiplicity %u (must be >= 1, and 1 without variable weights)",
-                  (long long)i, mw[i]);
+    if (mw && (mw[i] == 0 || mw[i] > kMaxMultiplicity || (mw[i] != 1 && !I->weighted)))
+      return fail(h, PIC_EINVAL,
+                  "particle %lld: multiplicity %u (must be 1..2^24, and 1 without variable weights)", (long long)i,
+                  mw[i]);
   }
   // the counters on the host are current unless device work changed them since
   // they were last read (a step, a sort)

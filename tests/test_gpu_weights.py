@@ -176,6 +176,8 @@ def test_refusals(pkg):
     v = np.zeros((1, 3))
     with pytest.raises(pkg.PicError):
         pkg.pic_inject_particles_m(sim.h, 0, 0, x, v, np.zeros(1, dtype=np.uint32))
+    with pytest.raises(pkg.PicError):  # above 2^24 (the FP32 deposit's exact range)
+        pkg.pic_inject_particles_m(sim.h, 0, 0, x, v, np.full(1, (1 << 24) + 1, dtype=np.uint32))
     sim.close()
     plain = pkg.Simulation(ionization_cells_case(seed=4), cg_rtol=RTOL_SOLVE, cg_maxit=5000)
     with pytest.raises(pkg.PicError):
