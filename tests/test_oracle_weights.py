@@ -21,6 +21,10 @@ probability ms / mp.
    in a quarter of the events (binomial bound).
 5. Charge exchange and ionization together with unequal multiplicities keep
    the same invariants.
+6. In a field-free box, where every particle crosses the cathode at a known
+   step, the absorbed energy and the charge collected in a step are the closed
+   sums over the crossing particles weighted by their multiplicities, and the
+   absorbed counts stay counts of superparticles.
 """
 import math
 
@@ -175,4 +179,35 @@ def test_exchange_and_ionization_invariants_with_unequal_multiplicities():
     assert m["next_pid"] - before["next_pid"] == 3 * ns
     pids = np.concatenate([o.particles(sp)[2] for sp in range(3)])
     assert np.unique(pids).size == pids.size
+    o.close()
+
+
+def test_weighted_absorption_closed_form():
+    # field-free box (weight 1e-30, both electrodes at 0 V): every particle moves
+    # in a straight line and crosses the cathode at a known step. Absorbed counts
+    # stay counts of superparticles; the absorbed energy sums (1/2) m w mw |v|^2
+    # and the charge collected in a step q w mw over the particles crossing in it
+    from tests._cases import cathode_hits_case
+    wl, k = cathode_hits_case()
+    wl = with_multiplicities(wl, 1, 7, seed=21)
+    (xe, ve, me), (xn, vn, mn), (xi, vi, mi) = wl.preload
+    o = O.Oracle(wl)
+    s_chk = 5
+    o.step(s_chk)
+    before = o.moments()
+    o.step(1)  # step s_chk: only the ions with k == s_chk cross
+    m = o.moments()
+    sel = k == s_chk
+    assert sel.sum() > 0
+    qi = wl.species[2].charge_C * wl.species[2].weight
+    assert math.isclose(m["charge_to_cathode_last"], qi * float(mi[sel].sum()), rel_tol=1e-14)
+    o.step(20)
+    m = o.moments()
+    assert m["abs_cathode"] == [xe.shape[0], xn.shape[0], xi.shape[0]]
+    for sp, (v, mw) in enumerate([(ve, me), (vn, mn), (vi, mi)]):
+        s = wl.species[sp]
+        want = 0.5 * s.mass_kg * s.weight * float(np.sum(mw * np.sum(v * v, axis=1)))
+        assert math.isclose(m["abs_energy_cathode"][sp], want, rel_tol=1e-12), sp
+    assert m["total_charge"] == 0.0 and m["count"] == [0, 0, 0]
+    assert before["abs_cathode"][2] < xi.shape[0]
     o.close()
