@@ -53,14 +53,15 @@ BYTES_PER_PARTICLE = {"mixed": 32 + 32, "fp64": 52 + 52}
 # (profiles/unet_conv_d0a_forward_128x128x256.md); layers without a capture are absent
 UNET_NCU_TRAFFIC = {"d0a": 536.2e6}
 # DRAM bytes (read + write) per pushed electron of the same kernel from one ncu capture of the
-# current kernel (profiles/k_push_mixed_electrons_128x128x256.md: 145.18 MB for 2 593 379
-# electrons); None where no capture of the current kernel exists
-NCU_TRAFFIC_PER_PARTICLE = {"mixed": 56.07, "fp64": 102.68}
+# current kernel (profiles/k_push_mixed_electrons_128x128x256.md: 145.12 MB for 2 593 379
+# electrons; profiles/k_push_fp64_electrons_128x128x256.md: 266.88 MB); None where no
+# capture of the current kernel exists
+NCU_TRAFFIC_PER_PARTICLE = {"mixed": 55.96, "fp64": 102.91}
 # The FP64 electron push is bound by GB300's FP64 pipe (2 FP64 operations per cycle
 # and SM), not by HBM: FP64 warp instructions x 32 per pushed electron from one ncu
 # capture of the current kernel (profiles/k_push_fp64_electrons_128x128x256.md:
-# 9 081 415 instructions for 2 593 379 electrons, the pipe active 84 % of cycles)
-FP64_PIPE_SLOTS_PER_ELECTRON = 112.06
+# 9 274 288 instructions for 2 593 379 electrons, the pipe active 84 % of cycles)
+FP64_PIPE_SLOTS_PER_ELECTRON = 114.44
 FP64_OPS_PER_SM_CYCLE = 2
 
 
